@@ -1,0 +1,336 @@
+/*
+ * lqcd.h -- C ABI of the GB300 (sm_103a) twisted-mass Wilson library.
+ *
+ * The library implements the hot path of "Lattice QCD based on OpenCL"
+ * (Bach, Lindenstruth, Philipsen, Pinke, arXiv:1209.5942):
+ *   - the twisted-mass Wilson matrix (Sec. 2.1, eq. "D_tm")
+ *         M = (1 + 2 i kappa mu gamma_5) - kappa H,
+ *         H psi(x) = sum_mu (1 - gamma_mu) U_mu(x) psi(x + mu)
+ *                         + (1 + gamma_mu) U_mu(x - mu)^+ psi(x - mu),
+ *     its even-odd Schur complement (Sec. 2.1, "even-odd preconditioning")
+ *         Mhat = A_e - kappa^2 H_eo A_o^-1 H_oe,   A = 1 + 2 i kappa mu gamma_5,
+ *   - the CG inversion of Mhat^+ Mhat (Sec. 2.1, eq. "solvereq"),
+ *   - the fermion force, gauge force, Cabibbo-Marinari heatbath and HMC of
+ *     Sec. 2.2.
+ *
+ * Conventions (the paper leaves them open; these are the library's readings):
+ *   - site index i = x + Lx*(y + Ly*(z + Lz*t)); mu = 0,1,2,3 = x,y,z,t;
+ *     every extent even; parity p(x) = (x+y+z+t) mod 2, even = 0;
+ *     checkerboard index cb = i / 2.
+ *   - chiral gamma basis, gamma_5 = gamma_x gamma_y gamma_z gamma_t =
+ *     diag(1, 1, -1, -1); hopping prefactor kappa (not kappa/2).
+ *   - links periodic; fermions periodic in space and, when
+ *     geom.antiperiodic_t = 1, antiperiodic in time (hops across the time
+ *     boundary carry -1; the sign is never folded into the links).
+ *
+ * Memory layouts.
+ *   Lexicographic (LQCD_LAYOUT_LEXI), complex128, array of structures:
+ *     gauge  [V][4][3][3],   spinor [V][4][3]   (spin, colour)
+ *   Even-odd (LQCD_LAYOUT_EO), structure of arrays on 16-byte words
+ *   (the paper's Sec. 4.2 SoA on a 16-byte base type), per right-hand side:
+ *     full field  [parity 2][component 12][Vh]   (even half first)
+ *     half field  [component 12][Vh]             (one parity)
+ *   with component = 3*spin + colour, Vh = V/2, and per-precision words:
+ *     LQCD_F64   complex128                        (16 B per component)
+ *     LQCD_DF64  float-float complex {re_hi, im_hi, re_lo, im_lo}
+ *                (16 B per component; value = hi + lo)
+ *     LQCD_F32   complex64, components paired into 16-B words:
+ *                [6][Vh] of {c0.re, c0.im, c1.re, c1.im}
+ *     LQCD_BF16S / LQCD_F16S  16-bit reals with one float scale per site:
+ *                [3][Vh] of 16 B (8 reals each, value = stored * scale)
+ *                plus field.scale -> float [Vh] (per right-hand side)
+ *   Multi-RHS fields (nrhs > 1) stack nrhs such fields contiguously.
+ *   Algebra fields (momenta, forces dS/domega): float64 [4][V][8], lexicographic
+ *   sites, coordinates w.r.t. T^a = lambda^a / 2, links varied as
+ *   U -> exp(i omega^a T^a) U.
+ *
+ * Ownership: spinor, force and momentum buffers are device memory owned by
+ * the caller; gauge fields are opaque objects owned by the library (freed with
+ * lqcd_gauge_free); the library never frees caller memory.
+ *
+ * Streams: every call enqueues work on the context's stream and returns
+ * without synchronising, except where it writes a host-visible result
+ * (solver statistics, plaquette, Hamiltonian), which it documents.
+ *
+ * Errors: every entry point returns lqcd_status; arguments are validated
+ * before any launch (null pointers, odd or non-positive extents, 16-byte
+ * alignment, precision/layout combinations, aliasing, geometry mismatch);
+ * lqcd_last_error() gives a message.  Nothing throws or exits.
+ */
+#ifndef LQCD_H
+#define LQCD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LQCD_ABI_VERSION 1
+
+typedef enum {
+  LQCD_OK = 0,
+  LQCD_ERR_INVALID = -1,     /* bad argument; nothing was launched */
+  LQCD_ERR_CUDA = -2,        /* a CUDA call failed */
+  LQCD_ERR_NOCONV = -3,      /* solver stopped at max_iter; stats are filled */
+  LQCD_ERR_NONFINITE = -4,   /* NaN/Inf met in an input or a solver scalar */
+  LQCD_ERR_TIMEOUT = -5,     /* a bounded device-side wait ran out */
+  LQCD_ERR_OOM = -6,         /* device allocation failed */
+  LQCD_ERR_UNSUPPORTED = -7  /* valid request that this build does not implement */
+} lqcd_status;
+
+typedef enum { LQCD_FULL = 0, LQCD_EVEN = 1, LQCD_ODD = 2 } lqcd_parity;
+
+typedef enum {
+  LQCD_F64 = 0,   /* IEEE binary64 storage and arithmetic */
+  LQCD_DF64 = 1,  /* float-float storage and arithmetic (about 48-bit significand) */
+  LQCD_F32 = 2,
+  LQCD_BF16S = 3, /* bfloat16 + per-site float scale; FP32 arithmetic */
+  LQCD_F16S = 4   /* binary16 + per-site float scale; FP32 arithmetic */
+} lqcd_prec;
+
+typedef enum { LQCD_LAYOUT_LEXI = 0, LQCD_LAYOUT_EO = 1 } lqcd_layout;
+
+typedef struct {
+  int32_t L[4];           /* extents x, y, z, t: all even, >= 2 */
+  int32_t antiperiodic_t; /* 1: fermion boundary factor -1 across the time boundary */
+} lqcd_geom;
+
+/* A caller-owned device spinor field. */
+typedef struct {
+  void *ptr;      /* device pointer, 16-byte aligned */
+  void *scale;    /* device float array [nrhs][Vh] (or [nrhs][2][Vh] for full
+                     fields) for LQCD_BF16S / LQCD_F16S, else NULL */
+  int32_t layout; /* lqcd_layout */
+  int32_t prec;   /* lqcd_prec; LEXI layout requires LQCD_F64 */
+  int32_t nrhs;   /* number of right-hand sides stacked in the buffer (>= 1) */
+  int32_t reserved;
+} lqcd_field;
+
+typedef struct lqcd_ctx lqcd_ctx;
+typedef struct lqcd_gauge lqcd_gauge;
+
+/* ---------------------------------------------------------------- */
+/* Context                                                           */
+/* ---------------------------------------------------------------- */
+
+int lqcd_abi_version(void);
+
+/* Creates a context on CUDA device `device` that enqueues work on
+ * `cuda_stream` (a cudaStream_t; NULL = the legacy default stream).  The
+ * context owns a small workspace (reduction partials, device scalars, a
+ * pinned host status word) allocated here with cudaMalloc. */
+int lqcd_create(lqcd_ctx **ctx, int device, void *cuda_stream);
+int lqcd_destroy(lqcd_ctx *ctx);
+int lqcd_set_stream(lqcd_ctx *ctx, void *cuda_stream);
+/* Message of the last failed call on this context (never NULL). */
+const char *lqcd_last_error(const lqcd_ctx *ctx);
+
+/* Work counters of a context, accumulated by every kernel the library
+ * enqueues (a CUDA-graph replay adds the counts of the captured launches).
+ * bytes / flops are ALGORITHMIC counts: each input word read once, each
+ * output written once (a half hop per output site: 8 links, the input
+ * spinor, the output spinor and the optional aux spinor; 1320 flops per
+ * site for the hop, plus 48 per fused epilogue term). */
+typedef struct {
+  uint64_t launches;      /* all kernels */
+  uint64_t hop_launches;  /* hopping-term kernels only */
+  double bytes;           /* algorithmic bytes of all counted kernels */
+  double hop_bytes;       /* ... of the hopping-term kernels */
+  double hop_flops;       /* algorithmic flops of the hopping-term kernels */
+  double hop_sites;       /* output sites x right-hand sides of the hop kernels */
+} lqcd_counters;
+int lqcd_get_counters(const lqcd_ctx *ctx, lqcd_counters *out);
+int lqcd_reset_counters(lqcd_ctx *ctx);
+
+/* Bytes needed for a field of the given parity (LQCD_FULL or one parity),
+ * precision and nrhs in the EO layout; *scale_bytes receives the size of the
+ * scale array (0 for unscaled precisions).  Returns 0 on invalid input. */
+size_t lqcd_field_bytes(const lqcd_geom *geom, int parity, int prec, int nrhs,
+                        size_t *scale_bytes);
+
+/* ---------------------------------------------------------------- */
+/* Gauge fields (Sec. 2.1 links U_mu(x); Sec. 4.1 REC12;             */
+/* Sec. 4.2 parity-split SoA storage)                                */
+/* ---------------------------------------------------------------- */
+
+/* Imports a device gauge field in the lexicographic layout (complex128
+ * [V][4][3][3]) into a library-owned even-odd SoA field.  recon = 18 keeps
+ * all 9 complex entries; recon = 12 keeps rows 0 and 1 and rebuilds row 2 as
+ * conj(row0 x row1) in the kernels (requires SU(3) links; checked to 1e-12,
+ * else LQCD_ERR_INVALID).  Lower-precision copies for mixed-precision solves
+ * are derived on demand. Synchronous (validates on the host). */
+int lqcd_gauge_import(lqcd_ctx *ctx, const void *U_lexi, const lqcd_geom *geom, int recon,
+                      lqcd_gauge **out);
+/* Writes the field back in the lexicographic layout (device pointer). */
+int lqcd_gauge_export(lqcd_ctx *ctx, const lqcd_gauge *U, void *U_lexi);
+int lqcd_gauge_free(lqcd_ctx *ctx, lqcd_gauge *U);
+
+/* ---------------------------------------------------------------- */
+/* Spinor layout and precision conversion                            */
+/* ---------------------------------------------------------------- */
+
+/* lexicographic complex128 [nrhs][V][4][3] <-> EO full field of any precision */
+int lqcd_spinor_pack(lqcd_ctx *ctx, const lqcd_geom *geom, const void *lexi, lqcd_field eo);
+int lqcd_spinor_unpack(lqcd_ctx *ctx, const lqcd_geom *geom, lqcd_field eo, void *lexi);
+/* EO field precision conversion; parity selects a half field or the full one */
+int lqcd_spinor_convert(lqcd_ctx *ctx, const lqcd_geom *geom, int parity, lqcd_field in,
+                        lqcd_field out);
+
+/* ---------------------------------------------------------------- */
+/* Operators (Sec. 2.1, eq. "D_tm")                                  */
+/* ---------------------------------------------------------------- */
+
+/* Half hop ("Dslash"): out = H_{p,1-p} in (dagger = 0) or the adjoint
+ * hop (dagger = 1, gamma_mu -> -gamma_mu), computed on the sites of
+ * out_parity (LQCD_EVEN or LQCD_ODD) from `in` on the other parity.  Both
+ * fields are EO half fields of the same precision (any lqcd_prec; nrhs >= 1
+ * applies the link to every right-hand side). */
+int lqcd_dslash(lqcd_ctx *ctx, const lqcd_gauge *U, lqcd_field in, lqcd_field out,
+                const lqcd_geom *geom, int out_parity, int dagger);
+
+/* parity = LQCD_FULL: out = M in on the whole lattice (fields LEXI or EO full).
+ * parity = LQCD_EVEN: out = Mhat in on the even sites (EO half fields).
+ * parity = LQCD_ODD : the odd-site Schur complement A_o - kappa^2 H_oe A_e^-1 H_eo.
+ * in and out must not alias.  Precision: LQCD_F64, LQCD_DF64 or LQCD_F32
+ * (EO), LQCD_F64 (LEXI). */
+int lqcd_apply_M(lqcd_ctx *ctx, const lqcd_gauge *U, lqcd_field in, lqcd_field out,
+                 const lqcd_geom *geom, double kappa, double mu, int parity);
+/* Same with M^+ = (1 - 2 i kappa mu gamma_5) - kappa H^+ (Mhat^+ for one parity). */
+int lqcd_apply_Mdag(lqcd_ctx *ctx, const lqcd_gauge *U, lqcd_field in, lqcd_field out,
+                    const lqcd_geom *geom, double kappa, double mu, int parity);
+
+/* ---------------------------------------------------------------- */
+/* Solver (Sec. 2.1: "D phi = psi", CG; even-odd preconditioning)    */
+/* ---------------------------------------------------------------- */
+
+typedef struct {
+  double tol;             /* target relative true residual ||b - M x|| / ||b|| */
+  int32_t max_iter;       /* cap on inner iterations (all cycles together) */
+  int32_t outer_prec;     /* LQCD_F64 or LQCD_DF64: precision of x, of the
+                             reliable-update residuals and of the plain solve */
+  int32_t inner_prec;     /* == outer_prec: plain CG; LQCD_F32 / LQCD_BF16S /
+                             LQCD_F16S: mixed precision with reliable updates */
+  double delta;           /* reliable-update trigger: ||s|| < delta * max ||s|| */
+  int32_t max_restarts;   /* outer iterative-refinement cycles on the true residual */
+  int32_t check_every;    /* host polls convergence every this many iterations */
+  int32_t use_graph;      /* 1: capture check_every iterations in a CUDA graph */
+  int32_t sloppy_recon;   /* 18 or 12: link format of the inner operator */
+} lqcd_cg_params;
+
+typedef struct {
+  int32_t iters;            /* inner iterations (each: 2 Mhat + 2 Mhat^+ ... = 4 half hops x2) */
+  int32_t reliable_updates; /* FP64-class residual recomputations */
+  int32_t restarts;         /* outer refinement cycles after the first */
+  int32_t converged;        /* 1 if true_resid <= tol */
+  double true_resid;        /* ||b - M x|| / ||b|| recomputed in IEEE FP64 with full M */
+  double seconds;           /* wall time of the call */
+} lqcd_cg_stats;
+
+/* Solves M x = b (FULL fields, LEXI or EO, LQCD_F64) through CG on
+ * Mhat^+ Mhat on the even sites (CGLS form) with source preparation
+ *   bhat_e = b_e + kappa H_eo A_o^-1 b_o
+ * and reconstruction x_o = A_o^-1 (b_o + kappa H_oe x_e).  nrhs > 1 solves
+ * the right-hand sides together (one multi-RHS operator per iteration,
+ * per-RHS scalars and convergence); stats then points to nrhs entries.
+ * Synchronous: returns after the true residual is known.  Returns
+ * LQCD_ERR_NOCONV (stats filled) when tol is not reached. */
+int lqcd_cg_solve(lqcd_ctx *ctx, const lqcd_gauge *U, lqcd_field b, lqcd_field x,
+                  const lqcd_geom *geom, double kappa, double mu, const lqcd_cg_params *params,
+                  lqcd_cg_stats *stats);
+
+/* Solves n independent systems M_k x_k = b_k on lattices of different sizes
+ * (each b_k, x_k: FULL EO LQCD_F64 fields on U_k's geometry) with one
+ * persistent kernel per operator stage working through a queue of tiles over
+ * all lattices.  stats points to n entries.  Synchronous. */
+int lqcd_cg_solve_batch(lqcd_ctx *ctx, int n, const lqcd_gauge *const *U, const lqcd_field *b,
+                        const lqcd_field *x, const double *kappa, const double *mu,
+                        const lqcd_cg_params *params, lqcd_cg_stats *stats);
+
+/* ---------------------------------------------------------------- */
+/* Forces, actions, heatbath, HMC (Sec. 2.2)                          */
+/* ---------------------------------------------------------------- */
+
+/* dS/domega for S = phi^+ (Mhat^+ Mhat)^-1 phi (phi: EO half field on the
+ * even sites, LQCD_F64), through dD^-1 = -D^-1 dD D^-1:
+ *   X = (Mhat^+ Mhat)^-1 phi (CG), Y = Mhat X, then one adjoint kernel over
+ *   all links.  dSdw: device float64 [4][V][8].  If X_cache is non-NULL and
+ *   X_cache->reserved == 1 the stored X is reused, otherwise X is solved and,
+ *   when X_cache is non-NULL, stored there (reserved set to 1).
+ *   *S_out (host, may be NULL) receives S = Re phi^+ X.  Synchronous. */
+int lqcd_fermion_force(lqcd_ctx *ctx, const lqcd_gauge *U, lqcd_field phi, double *dSdw,
+                       lqcd_field *X_cache, const lqcd_geom *geom, double kappa, double mu,
+                       const lqcd_cg_params *params, lqcd_cg_stats *stats, double *S_out);
+
+/* Wilson gauge action S_g = (beta/3) sum_{x, mu<nu} (3 - Re Tr U_munu) and
+ * its derivative dS_g/domega = -(beta/3) Re Tr[i T^a U_mu(x) A_mu(x)]
+ * (A = staple sum).  dSdw: device float64 [4][V][8]; *S_out host (may be
+ * NULL, then the call is asynchronous). */
+int lqcd_gauge_force(lqcd_ctx *ctx, const lqcd_gauge *U, double beta, double *dSdw,
+                     double *S_out);
+
+/* Plaquette (1/(6V)) sum_{x, mu<nu} (1/3) Re Tr U_munu(x) in FP64.  Synchronous. */
+int lqcd_plaquette(lqcd_ctx *ctx, const lqcd_gauge *U, double *plaq_out);
+
+/* One Cabibbo-Marinari heatbath sweep at coupling beta: for mu = 0..3 and
+ * parity even, odd, every link of that class is updated in parallel over the
+ * SU(2) subgroups (0,1), (1,2), (0,2) with the exact SU(2) update (Creutz for
+ * b < 1.5, Kennedy-Pendleton above, b = 2 beta k / 3).  Random numbers:
+ * Philox4x32-10 keyed by seed, counter (site, sweep_idx, mu | g<<2 | tag<<8,
+ * draw).  Then n_or overrelaxation passes (not in this build: n_or must be 0).
+ * The links are reunitarised in FP64 afterwards.  Asynchronous. */
+int lqcd_heatbath_sweep(lqcd_ctx *ctx, lqcd_gauge *U, double beta, uint64_t seed,
+                        uint64_t sweep_idx, int n_or);
+
+/* Gaussian momenta p^a ~ N(0,1) into P (device float64 [4][V][8]) from the
+ * Philox stream (site, traj, mu | 1<<8, k). Asynchronous. */
+int lqcd_momenta_gaussian(lqcd_ctx *ctx, const lqcd_geom *geom, double *P, uint64_t seed,
+                          uint32_t traj);
+/* Gaussian spinor eta (density exp(-eta^+ eta)) on the sites of `parity`
+ * (LQCD_FULL, LQCD_EVEN) into an EO LQCD_F64 field, stream (site, traj, 2<<8, k). */
+int lqcd_spinor_gaussian(lqcd_ctx *ctx, const lqcd_geom *geom, lqcd_field eta, int parity,
+                         uint64_t seed, uint32_t traj);
+
+/* U_mu(x) <- exp(i eps P_mu(x)) U_mu(x) for every link (exact 3x3 exponential
+ * in FP64), then FP64 reunitarisation. Asynchronous. */
+int lqcd_gauge_update(lqcd_ctx *ctx, lqcd_gauge *U, const double *P, double eps);
+/* P <- P - eps * dSdw (the leapfrog momentum step, F = -dS/domega). */
+int lqcd_momenta_update(lqcd_ctx *ctx, const lqcd_geom *geom, double *P, const double *dSdw,
+                        double eps);
+/* 1/2 sum p^2 in FP64 (host result).  Synchronous. */
+int lqcd_momenta_kinetic(lqcd_ctx *ctx, const lqcd_geom *geom, const double *P, double *K_out);
+/* Copies U_src into U_dst (same geometry). */
+int lqcd_gauge_copy(lqcd_ctx *ctx, const lqcd_gauge *U_src, lqcd_gauge *U_dst);
+
+typedef struct {
+  double beta, kappa, mu;
+  double tau;          /* trajectory length */
+  int32_t nsteps;      /* leapfrog steps */
+  int32_t nf;          /* 0: pure gauge, 1: one twisted-mass doublet (phi = Mhat^+ eta) */
+  uint64_t seed;
+  uint32_t traj;       /* trajectory number (Philox counter word) */
+  int32_t reserved;
+  lqcd_cg_params cg;   /* solver used for every force and action evaluation */
+} lqcd_hmc_params;
+
+typedef struct {
+  double dH, H0, H1;
+  double plaquette;    /* after the trajectory (of the accepted field) */
+  int32_t accepted;
+  int32_t cg_iters;    /* total inner CG iterations */
+  double seconds;
+} lqcd_hmc_stats;
+
+/* One HMC trajectory (Sec. 2.2): momenta and eta drawn from Philox, phi =
+ * Mhat^+ eta, leapfrog with F = -dS/domega, H in FP64 and the Metropolis test
+ * exp(-dH) against a Philox uniform (counter (0, traj, 4<<8, 0)).  On
+ * rejection U is restored.  Synchronous. */
+int lqcd_hmc_trajectory(lqcd_ctx *ctx, lqcd_gauge *U, const lqcd_hmc_params *params,
+                        lqcd_hmc_stats *stats);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LQCD_H */

@@ -1,0 +1,893 @@
+// cg.cu -- even-odd preconditioned CG (Sec. 2.1: "D phi = psi", "the most
+// common solvers used are CG and BiCGStab", "even-odd-preconditioning").
+//
+// The system M x = b is reduced to the even sites (Schur complement
+//   Mhat = A_e - kappa^2 H_eo A_o^-1 H_oe,   A = 1 + i a gamma_5, a = 2 kappa mu)
+// with bhat_e = b_e + kappa H_eo A_o^-1 b_o and x_o = A_o^-1 (b_o + kappa H_oe x_e),
+// and Mhat x_e = bhat_e is solved by CG on the normal equations in CGLS form,
+// which keeps the residual s = bhat - Mhat x of the unsquared system:
+//   q = Mhat p;  alpha = |z|^2/|q|^2;  x += alpha p;  s -= alpha q;
+//   z = Mhat^+ s;  beta = |z_new|^2/|z|^2;  p = z + beta p.
+// It stops when |s| <= tol |b| (|b| of the full system: the full residual is
+// (s, 0) exactly), then the true residual |b - M x| / |b| is recomputed with
+// the full FP64 operator.
+//
+// Mixed precision (the paper's outlook, Sec. 5 and 6): the recursion runs in
+// a sloppy format (F32, or BF16/F16 with per-site scale) while x and the
+// residual are kept in the outer FP64-class format (F64 or DF64).  A reliable
+// update (Sleijpen & van der Vorst) folds the sloppy x into the outer x and
+// replaces s by the outer-precision residual whenever |s| has dropped below
+// delta times its largest value since the last update; p is kept.  Outer
+// iterative refinement restarts the whole solve on the true residual.
+//
+// GB300 execution: every scalar (alpha, beta, norms, convergence flags) lives
+// in device memory, so an iteration is six kernel launches with no host
+// round trip; check_every iterations are captured once in a CUDA graph and
+// replayed; the host reads a status word after each replay.  Reductions are
+// FP64 partial sums per block finished by one block in a fixed order, so the
+// iteration count is reproducible run to run.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <utility>
+#include <vector>
+
+#include "internal.h"
+
+namespace lqcd {
+
+
+// ---------------------------------------------------------------------------
+// device solver state
+// ---------------------------------------------------------------------------
+
+struct RhsState {
+  double zz, qq, ss, alpha, beta, stop2, rel2, rmax2;
+  int done, iters, need_rel, pad;
+};
+struct SolverHdr {
+  int halt, all_done, need_rel, nonfinite;
+  int iters, nrhs, mixed, pad;
+};
+// layout in device memory: SolverHdr, then RhsState[nrhs]
+LQCD_DEV RhsState *rhs_state(SolverHdr *h) { return (RhsState *)(h + 1); }
+
+// sum of partials[r][0..nb) in a fixed order by one block of 256 threads
+LQCD_DEV double block_sum_fixed(const double *v, int nb, double *sh) {
+  double t = 0.0;
+  for (int k = threadIdx.x; k < nb; k += blockDim.x) t += v[k];
+  sh[threadIdx.x] = t;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  double r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+enum { FIN_ALPHA = 0, FIN_SS = 1, FIN_BETA = 2, FIN_INIT_ZZ = 3, FIN_STORE = 4 };
+
+// One block: finishes the reductions of all nrhs right-hand sides and applies
+// the CG scalar step `op`.  FIN_STORE only writes the plain sums to out[r]
+// and does not touch the solver state.
+__global__ void finalize_kernel(SolverHdr *h, int nrhs, const double *partials, int nb, int op,
+                                double *out) {
+  __shared__ double sh[256];
+  if (op == FIN_STORE) {
+    for (int r = 0; r < nrhs; r++) {
+      double v = block_sum_fixed(partials + (size_t)r * nb, nb, sh);
+      if (threadIdx.x == 0) out[r] = v;
+    }
+    return;
+  }
+  if (op != FIN_INIT_ZZ && *(volatile int *)&h->halt) return;
+  RhsState *rs = rhs_state(h);
+  int all_done = 1, any_rel = 0, bad = 0, maxit = 0;
+  for (int r = 0; r < nrhs; r++) {
+    double v = block_sum_fixed(partials + (size_t)r * nb, nb, sh);
+    if (threadIdx.x == 0) {
+      RhsState &R = rs[r];
+      if (!isfinite(v)) bad = 1;
+      switch (op) {
+        case FIN_ALPHA:
+          R.qq = v;
+          if (R.done) R.alpha = 0.0;
+          else if (v > 0.0) R.alpha = R.zz / v;
+          else { R.alpha = 0.0; if (R.zz > 0.0) bad = 1; }
+          break;
+        case FIN_SS:
+          R.ss = v;
+          if (!R.done) {
+            R.iters += 1;
+            if (v <= R.stop2) R.done = 1;
+            if (h->mixed && !R.done) {
+              if (v > R.rmax2) R.rmax2 = v;
+              if (v < R.rel2 * R.rmax2) R.need_rel = 1;
+            }
+          }
+          break;
+        case FIN_BETA:
+          if (R.done) R.beta = 0.0;
+          else R.beta = R.zz > 0.0 ? v / R.zz : 0.0;
+          R.zz = v;
+          break;
+        default:  // FIN_INIT_ZZ
+          R.zz = v;
+          break;
+      }
+      all_done &= R.done;
+      any_rel |= R.need_rel;
+      if (R.iters > maxit) maxit = R.iters;
+    }
+  }
+  if (threadIdx.x == 0) {
+    h->iters = maxit;
+    h->all_done = all_done;
+    h->need_rel = any_rel;
+    if (bad) h->nonfinite = 1;
+    if (op == FIN_SS && (all_done || any_rel)) h->halt = 1;
+    if (bad) h->halt = 1;
+  }
+}
+
+
+static void launch_finalize(lqcd_ctx *ctx, SolverHdr *h, int nrhs, int nb, int op, double *out) {
+  finalize_kernel<<<1, 256, 0, ctx->stream>>>(h, nrhs, ctx->partials, nb, op, out);
+  count_launch(ctx, 8.0 * nb * nrhs);
+}
+
+// ---------------------------------------------------------------------------
+// BLAS-1 kernels on half fields with nrhs right-hand sides (grid.y = rhs)
+// ---------------------------------------------------------------------------
+
+struct VecArgs {
+  int Vh;
+  size_t rs, srs;  // bytes / scale floats per rhs (same precision for all operands)
+};
+
+LQCD_DEV SpinorView sv(const VecArgs &a, const void *p, const float *s, int r) {
+  return SpinorView{(char *)p + r * a.rs, s ? (float *)s + r * a.srs : nullptr, a.Vh};
+}
+
+LQCD_DEV double warp_block_sum(double v, double *sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < nw; k++) t += sh[k];
+  return t;
+}
+
+// x += alpha p;  s -= alpha q;  partial |s|^2
+template <int P>
+__global__ void __launch_bounds__(128) cg_xs_kernel(VecArgs a, SolverHdr *h, void *x, float *xs,
+                                                    const void *p, const float *ps, void *s,
+                                                    float *ss, const void *q, const float *qs,
+                                                    double *partials) {
+  using R = typename SpinorIO<P>::R;
+  __shared__ double sh[8];
+  if (*(volatile int *)&h->halt) return;
+  int cb = blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y;
+  double nrm = 0.0;
+  if (cb < a.Vh) {
+    const R al = from_double<R>(rhs_state(h)[r].alpha);
+    Cx<R> X[12], Pp[12], S[12], Q[12];
+    SpinorIO<P>::load(sv(a, x, xs, r), cb, X);
+    SpinorIO<P>::load(sv(a, p, ps, r), cb, Pp);
+    SpinorIO<P>::load(sv(a, s, ss, r), cb, S);
+    SpinorIO<P>::load(sv(a, q, qs, r), cb, Q);
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+      X[k] = {X[k].re + al * Pp[k].re, X[k].im + al * Pp[k].im};
+      S[k] = {S[k].re - al * Q[k].re, S[k].im - al * Q[k].im};
+      nrm += norm2_d(S[k]);
+    }
+    SpinorIO<P>::store(sv(a, x, xs, r), cb, X);
+    SpinorIO<P>::store(sv(a, s, ss, r), cb, S);
+  }
+  double t = warp_block_sum(nrm, sh);
+  if (threadIdx.x == 0) partials[(size_t)r * gridDim.x + blockIdx.x] = t;
+}
+
+// p = z + beta p
+template <int P>
+__global__ void __launch_bounds__(128) cg_p_kernel(VecArgs a, SolverHdr *h, void *p, float *ps,
+                                                   const void *z, const float *zs) {
+  using R = typename SpinorIO<P>::R;
+  if (*(volatile int *)&h->halt) return;
+  int cb = blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y;
+  if (cb >= a.Vh) return;
+  const R be = from_double<R>(rhs_state(h)[r].beta);
+  Cx<R> Pp[12], Z[12];
+  SpinorIO<P>::load(sv(a, p, ps, r), cb, Pp);
+  SpinorIO<P>::load(sv(a, z, zs, r), cb, Z);
+#pragma unroll
+  for (int k = 0; k < 12; k++) Pp[k] = {Z[k].re + be * Pp[k].re, Z[k].im + be * Pp[k].im};
+  SpinorIO<P>::store(sv(a, p, ps, r), cb, Pp);
+}
+
+// out = ca x + cb y (host scalars, per chirality complex), optional |out|^2 partials
+template <int P>
+// (each operand has its own right-hand-side stride: a for out, ax for x, ay for y)
+__global__ void __launch_bounds__(128) lincomb_kernel(VecArgs a, VecArgs ax, VecArgs ay, void *out,
+                                                      float *os, const void *x, const float *xsc,
+                                                      const void *y, const float *ysc, HostC ca_up,
+                                                      HostC ca_dn, HostC cb_up, HostC cb_dn,
+                                                      double *partials) {
+  using R = typename SpinorIO<P>::R;
+  __shared__ double sh[8];
+  int cb = blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y;
+  double nrm = 0.0;
+  if (cb < a.Vh) {
+    Cx<R> X[12], Y[12];
+    SpinorIO<P>::load(sv(ax, x, xsc, r), cb, X);
+    if (y) SpinorIO<P>::load(sv(ay, y, ysc, r), cb, Y);
+    const Cx<R> au = cfrom<R>(ca_up), ad = cfrom<R>(ca_dn), bu = cfrom<R>(cb_up), bd = cfrom<R>(cb_dn);
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+      Cx<R> o = (k < 6 ? au : ad) * X[k];
+      if (y) o = cmadd(k < 6 ? bu : bd, Y[k], o);
+      X[k] = o;
+      nrm += norm2_d(o);
+    }
+    SpinorIO<P>::store(sv(a, out, os, r), cb, X);
+  }
+  if (partials) {
+    double t = warp_block_sum(nrm, sh);
+    if (threadIdx.x == 0) partials[(size_t)r * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+// outer += convert(inner) (F64/DF64 outer, any inner precision)
+template <int PO, int PI>
+__global__ void __launch_bounds__(128) accum_convert_kernel(int Vh, size_t ors, size_t irs,
+                                                            size_t isrs, void *outer, const void *inner,
+                                                            const float *iscale) {
+  using RO = typename SpinorIO<PO>::R;
+  int cb = blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y;
+  if (cb >= Vh) return;
+  Cx<RO> O[12];
+  Cx<typename SpinorIO<PI>::R> I[12];
+  SpinorView vo{(char *)outer + r * ors, nullptr, Vh};
+  SpinorView vi{(char *)inner + r * irs, iscale ? (float *)iscale + r * isrs : nullptr, Vh};
+  SpinorIO<PO>::load(vo, cb, O);
+  SpinorIO<PI>::load(vi, cb, I);
+#pragma unroll
+  for (int k = 0; k < 12; k++)
+    O[k] = O[k] + Cx<RO>{from_double<RO>(to_double(I[k].re)), from_double<RO>(to_double(I[k].im))};
+  SpinorIO<PO>::store(vo, cb, O);
+}
+
+__global__ void state_init_kernel(SolverHdr *h, int nrhs, int mixed, const double *b2, double tol,
+                                  double rel) {
+  int r = threadIdx.x;
+  if (r == 0) {
+    h->halt = 0;
+    h->all_done = 0;
+    h->need_rel = 0;
+    h->nonfinite = 0;
+    h->iters = 0;
+    h->nrhs = nrhs;
+    h->mixed = mixed;
+  }
+  if (r < nrhs) {
+    RhsState &R = rhs_state(h)[r];
+    R.zz = R.qq = R.ss = R.alpha = R.beta = 0.0;
+    R.stop2 = tol * tol * b2[r];
+    R.rel2 = rel * rel;
+    R.rmax2 = 0.0;
+    R.done = 0;
+    R.iters = 0;
+    R.need_rel = 0;
+  }
+}
+
+// After a reliable update: new residual norms, reset triggers, beta from the
+// new z.  ss2[r] = |s|^2 of the recomputed residual.
+__global__ void state_after_reliable_kernel(SolverHdr *h, const double *ss2) {
+  int r = threadIdx.x;
+  if (r < h->nrhs) {
+    RhsState &R = rhs_state(h)[r];
+    R.need_rel = 0;
+    R.rmax2 = ss2[r];
+    R.ss = ss2[r];
+    if (ss2[r] > R.stop2) R.done = 0;
+  }
+  __syncthreads();
+  if (r == 0) {
+    h->need_rel = 0;
+    h->halt = 0;
+    int ad = 1;
+    for (int k = 0; k < h->nrhs; k++) ad &= rhs_state(h)[k].done;
+    h->all_done = ad;
+    if (ad) h->halt = 1;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host-side helpers
+// ---------------------------------------------------------------------------
+
+
+struct TmCoef {  // per-chirality coefficients of A = 1 + i a g5 and friends
+  HostC A_up, A_dn, Ai_up, Ai_dn;
+};
+static TmCoef tm_coef(double kappa, double mu, bool dagger) {
+  double a = 2.0 * kappa * mu;
+  if (dagger) a = -a;  // A^+ = 1 - i a g5, A^-+ = (1 + i a g5)/(1 + a^2)
+  double n = 1.0 / (1.0 + a * a);
+  return {{1.0, a}, {1.0, -a}, {n, -a * n}, {n, a * n}};
+}
+
+// Spinor workspace vector of nrhs half fields in precision prec.
+struct Vec {
+  HalfField f;
+  lqcd_ctx *ctx = nullptr;
+  Vec() = default;
+  Vec(const Vec &) = delete;
+  Vec &operator=(const Vec &) = delete;
+  ~Vec() {
+    if (ctx) {
+      dfree(ctx, f.ptr);
+      dfree(ctx, f.scale);
+    }
+  }
+  lqcd_status alloc(lqcd_ctx *c, int prec, int Vh, int nrhs) {
+    ctx = c;
+    f.prec = prec;
+    f.nrhs = nrhs;
+    f.rhs_stride = spinor_half_bytes(prec, Vh);
+    f.scale_rhs_stride = spinor_scale_half_bytes(prec, Vh) / sizeof(float);
+    LQCD_TRY(dalloc(c, &f.ptr, f.rhs_stride * nrhs));
+    if (f.scale_rhs_stride) LQCD_TRY(dalloc(c, (void **)&f.scale, f.scale_rhs_stride * sizeof(float) * nrhs));
+    LQCD_CUDA(c, cudaMemsetAsync(f.ptr, 0, f.rhs_stride * nrhs, c->stream));
+    if (f.scale)
+      LQCD_CUDA(c, cudaMemsetAsync(f.scale, 0, f.scale_rhs_stride * sizeof(float) * nrhs, c->stream));
+    return LQCD_OK;
+  }
+};
+
+static VecArgs vargs(const HalfField &f, int Vh) { return VecArgs{Vh, f.rhs_stride, f.scale_rhs_stride}; }
+
+template <class F>
+static lqcd_status dispatch_prec(lqcd_ctx *ctx, int prec, F &&f) {
+  switch (prec) {
+    case LQCD_F64: f(std::integral_constant<int, LQCD_F64>()); break;
+    case LQCD_DF64: f(std::integral_constant<int, LQCD_DF64>()); break;
+    case LQCD_F32: f(std::integral_constant<int, LQCD_F32>()); break;
+    case LQCD_BF16S: f(std::integral_constant<int, LQCD_BF16S>()); break;
+    case LQCD_F16S: f(std::integral_constant<int, LQCD_F16S>()); break;
+    default: return fail(ctx, LQCD_ERR_INVALID, "bad precision %d", prec);
+  }
+  LQCD_CUDA(ctx, cudaGetLastError());
+  return LQCD_OK;
+}
+
+lqcd_status lincomb(lqcd_ctx *ctx, int Vh, const HalfField &out, const HalfField &x, const HalfField *y,
+                    HostC ca_up, HostC ca_dn, HostC cb_up, HostC cb_dn, double *partials,
+                    int *nb_out) {
+  dim3 grid((Vh + 127) / 128, out.nrhs);
+  if (nb_out) *nb_out = grid.x;
+  if (x.prec != out.prec || (y && y->prec != out.prec) || x.nrhs != out.nrhs || (y && y->nrhs != out.nrhs))
+    return fail(ctx, LQCD_ERR_INVALID, "lincomb: operand precision or nrhs mismatch");
+  VecArgs a = vargs(out, Vh), ax = vargs(x, Vh), ay = y ? vargs(*y, Vh) : a;
+  count_launch(ctx, (double)Vh * out.nrhs * spinor_site_bytes(out.prec) * (y ? 3.0 : 2.0));
+  return dispatch_prec(ctx, out.prec, [&](auto P) {
+    lincomb_kernel<decltype(P)::value><<<grid, 128, 0, ctx->stream>>>(
+        a, ax, ay, out.ptr, out.scale, x.ptr, x.scale, y ? y->ptr : nullptr, y ? y->scale : nullptr,
+        ca_up, ca_dn, cb_up, cb_dn, partials);
+  });
+}
+
+// sums partials[r][0..nb) into the pinned host array (synchronous)
+static lqcd_status host_sums(lqcd_ctx *ctx, SolverHdr *h, int nb, int nrhs, double *dst_dev,
+                             std::vector<double> *host) {
+  launch_finalize(ctx, h, nrhs, nb, FIN_STORE, dst_dev);
+  LQCD_CUDA(ctx, cudaGetLastError());
+  if (host) {
+    LQCD_TRY(ensure_pinned(ctx, nrhs));
+    LQCD_CUDA(ctx, cudaMemcpyAsync(ctx->pinned, dst_dev, nrhs * sizeof(double), cudaMemcpyDeviceToHost,
+                                   ctx->stream));
+    LQCD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    host->assign(ctx->pinned, ctx->pinned + nrhs);
+  }
+  return LQCD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Schur-complement operator in one precision: out_e = Mhat (or Mhat^+) in_e
+// (parity p = 0 even, 1 odd), tmp: half field of the other parity.
+// ---------------------------------------------------------------------------
+
+
+lqcd_status apply_schur(const Op &op, const HalfField &in, const HalfField &out, const HalfField &tmp,
+                        int p, bool dagger, double *partials, int *nb, int *halt) {
+  TmCoef c = tm_coef(op.kappa, op.mu, dagger);
+  HopLaunch L1;
+  L1.prec = op.prec;
+  L1.recon = op.recon;
+  L1.U = op.U;
+  L1.in = in;
+  L1.out = tmp;
+  L1.out_parity = p ^ 1;
+  L1.dagger = dagger;
+  L1.c_up = c.Ai_up;
+  L1.c_dn = c.Ai_dn;
+  L1.halt = halt;
+  LQCD_TRY(launch_hop(op.ctx, op.g, L1, nullptr));
+  HopLaunch L2 = L1;
+  L2.in = tmp;
+  L2.out = out;
+  L2.aux = in;
+  L2.has_aux = true;
+  L2.out_parity = p;
+  double k2 = op.kappa * op.kappa;
+  L2.c_up = {-k2, 0.0};
+  L2.c_dn = {-k2, 0.0};
+  L2.d_up = c.A_up;
+  L2.d_dn = c.A_dn;
+  L2.partials = partials;
+  return launch_hop(op.ctx, op.g, L2, nb);
+}
+
+// full M (or M^+) on an EO full field: both parities, out_p = A in_p - kappa H in_{1-p}
+lqcd_status apply_full(const Op &op, const HalfField &in_e, const HalfField &in_o, const HalfField &out_e,
+                       const HalfField &out_o, bool dagger, double *partials_e, double *partials_o,
+                       int *nb) {
+  TmCoef c = tm_coef(op.kappa, op.mu, dagger);
+  for (int p = 0; p < 2; p++) {
+    HopLaunch L;
+    L.prec = op.prec;
+    L.recon = op.recon;
+    L.U = op.U;
+    L.in = p == 0 ? in_o : in_e;
+    L.out = p == 0 ? out_e : out_o;
+    L.aux = p == 0 ? in_e : in_o;
+    L.has_aux = true;
+    L.out_parity = p;
+    L.dagger = dagger;
+    L.c_up = {-op.kappa, 0.0};
+    L.c_dn = {-op.kappa, 0.0};
+    L.d_up = c.A_up;
+    L.d_dn = c.A_dn;
+    L.partials = p == 0 ? partials_e : partials_o;
+    LQCD_TRY(launch_hop(op.ctx, op.g, L, nb));
+  }
+  return LQCD_OK;
+}
+
+static HalfField half_of(const HalfField &full, int p, int Vh) {
+  // full field [nrhs][2][..]: parity p half with rhs stride of the full field
+  HalfField h = full;
+  size_t hb = spinor_half_bytes(full.prec, Vh);
+  h.ptr = (char *)full.ptr + p * hb;
+  if (full.scale) h.scale = full.scale + (size_t)p * Vh;
+  return h;
+}
+
+// ---------------------------------------------------------------------------
+// The solver
+// ---------------------------------------------------------------------------
+
+struct CgWork {
+  // outer-precision even vectors
+  Vec bhat, xo, r, tmpo, yo;
+  // sloppy vectors
+  Vec xs, s, p, q, z, t;
+};
+
+static lqcd_status ensure_state(lqcd_ctx *ctx, int nrhs, SolverHdr **h) {
+  size_t need = sizeof(SolverHdr) + sizeof(RhsState) * nrhs + sizeof(double) * 4 * nrhs;
+  if (ctx->solver_state_cap < need) {
+    if (ctx->solver_state) cudaFree(ctx->solver_state);
+    ctx->solver_state = nullptr;
+    ctx->solver_state_cap = 0;
+    if (cudaMalloc(&ctx->solver_state, need) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ctx, LQCD_ERR_OOM, "solver state allocation failed");
+    }
+    ctx->solver_state_cap = need;
+  }
+  *h = (SolverHdr *)ctx->solver_state;
+  return LQCD_OK;
+}
+static double *state_scratch(SolverHdr *h, int nrhs, int k) {  // 4 double arrays [nrhs]
+  return (double *)((char *)h + sizeof(SolverHdr) + sizeof(RhsState) * nrhs) + (size_t)k * nrhs;
+}
+
+// Solves Mhat x_e = bhat_e for all right-hand sides; x_e (outer precision)
+// must be zero on entry.  b2[r] = |b_r|^2 of the full system (stop criterion).
+lqcd_status cgls_even(lqcd_ctx *ctx, lqcd_gauge *U, const Geom &g, double kappa, double mu,
+                             const lqcd_cg_params &prm, const HalfField &bhat, const HalfField &xo,
+                             const std::vector<double> &b2, lqcd_cg_stats *st, int nrhs,
+                             int *iters_used, bool normal) {
+  const int Vh = g.Vh;
+  const int outer = prm.outer_prec, inner = prm.inner_prec;
+  const bool mixed = inner != outer;
+  Op Oo{ctx, g, {}, outer, U->recon, kappa, mu};
+  LQCD_TRY(gauge_view(ctx, U, outer, U->recon, &Oo.U));
+  Op Oi = Oo;
+  if (mixed) {
+    Oi.prec = inner;
+    Oi.recon = (inner == LQCD_BF16S || inner == LQCD_F16S) ? 12 : prm.sloppy_recon;
+    LQCD_TRY(gauge_view(ctx, U, inner, Oi.recon, &Oi.U));
+  }
+  Vec s, p, q, z, t, xs, r_o, tmp_o, y_o;
+  LQCD_TRY(s.alloc(ctx, inner, Vh, nrhs));
+  LQCD_TRY(p.alloc(ctx, inner, Vh, nrhs));
+  LQCD_TRY(q.alloc(ctx, inner, Vh, nrhs));
+  LQCD_TRY(z.alloc(ctx, inner, Vh, nrhs));
+  LQCD_TRY(t.alloc(ctx, inner, Vh, nrhs));
+  HalfField X = xo;  // sloppy x: the outer x itself when not mixed
+  if (mixed) {
+    LQCD_TRY(xs.alloc(ctx, inner, Vh, nrhs));
+    LQCD_TRY(r_o.alloc(ctx, outer, Vh, nrhs));
+    LQCD_TRY(tmp_o.alloc(ctx, outer, Vh, nrhs));
+    if (normal) LQCD_TRY(y_o.alloc(ctx, outer, Vh, nrhs));
+    X = xs.f;
+  }
+  int nb = hop_blocks(g, nrhs);
+  int nbv = (Vh + 127) / 128;
+  LQCD_TRY(ensure_partials(ctx, (size_t)nrhs * (nb > nbv ? nb : nbv)));
+  SolverHdr *h;
+  LQCD_TRY(ensure_state(ctx, nrhs, &h));
+  double *b2d = state_scratch(h, nrhs, 0), *tmpd = state_scratch(h, nrhs, 1);
+  LQCD_TRY(ensure_pinned(ctx, 64 + 4 * nrhs));
+  for (int r = 0; r < nrhs; r++) ctx->pinned[r] = b2[r];
+  LQCD_CUDA(ctx, cudaMemcpyAsync(b2d, ctx->pinned, nrhs * sizeof(double), cudaMemcpyHostToDevice,
+                                 ctx->stream));
+  state_init_kernel<<<1, 64, 0, ctx->stream>>>(h, nrhs, mixed ? 1 : 0, b2d, prm.tol * 0.5,
+                                               prm.delta > 0 ? prm.delta : 0.1);
+  LQCD_CUDA(ctx, cudaGetLastError());
+  const HostC one{1, 0}, zero{0, 0}, mone{-1, 0};
+  if (!normal) {
+    // s = bhat (converted to the sloppy format); z = Mhat^+ s, p = z, zz = |z|^2
+    if (mixed) LQCD_TRY(spinor_convert_raw(ctx, Vh, nrhs, bhat.ptr, bhat.scale, outer, s.f.ptr, s.f.scale, inner));
+    else LQCD_TRY(lincomb(ctx, Vh, s.f, bhat, nullptr, one, one, zero, zero, nullptr, nullptr));
+    LQCD_TRY(apply_schur(Oi, s.f, z.f, t.f, 0, true, ctx->partials, &nb, nullptr));
+    launch_finalize(ctx, h, nrhs, nb, FIN_INIT_ZZ, nullptr);
+  } else {
+    // normal equations Mhat^+ Mhat x = phi: the normal residual z = phi, p = z
+    if (mixed) LQCD_TRY(spinor_convert_raw(ctx, Vh, nrhs, bhat.ptr, bhat.scale, outer, z.f.ptr, z.f.scale, inner));
+    else LQCD_TRY(lincomb(ctx, Vh, z.f, bhat, nullptr, one, one, zero, zero, nullptr, nullptr));
+    int nbl = 0;
+    LQCD_TRY(lincomb(ctx, Vh, z.f, z.f, nullptr, one, one, zero, zero, ctx->partials, &nbl));
+    launch_finalize(ctx, h, nrhs, nbl, FIN_INIT_ZZ, nullptr);
+  }
+  LQCD_TRY(lincomb(ctx, Vh, p.f, z.f, nullptr, one, one, zero, zero, nullptr, nullptr));
+
+  VecArgs va = vargs(s.f, Vh);
+  dim3 vgrid(nbv, nrhs);
+  auto iteration = [&]() -> lqcd_status {
+    LQCD_TRY(apply_schur(Oi, p.f, q.f, t.f, 0, false, ctx->partials, &nb, &h->halt));
+    launch_finalize(ctx, h, nrhs, nb, FIN_ALPHA, nullptr);
+    if (!normal) {
+      // CGLS: x += alpha p; s -= alpha q; z = Mhat^+ s
+      count_launch(ctx, (double)Vh * nrhs * spinor_site_bytes(inner) * 6.0);
+      LQCD_TRY(dispatch_prec(ctx, inner, [&](auto P) {
+        cg_xs_kernel<decltype(P)::value><<<vgrid, 128, 0, ctx->stream>>>(
+            va, h, X.ptr, X.scale, p.f.ptr, p.f.scale, s.f.ptr, s.f.scale, q.f.ptr, q.f.scale,
+            ctx->partials);
+      }));
+      launch_finalize(ctx, h, nrhs, nbv, FIN_SS, nullptr);
+      LQCD_TRY(apply_schur(Oi, s.f, z.f, t.f, 0, true, ctx->partials, &nb, &h->halt));
+      launch_finalize(ctx, h, nrhs, nb, FIN_BETA, nullptr);
+    } else {
+      // CGNR: w = Mhat^+ q (held in s); x += alpha p; z -= alpha w
+      LQCD_TRY(apply_schur(Oi, q.f, s.f, t.f, 0, true, nullptr, nullptr, &h->halt));
+      count_launch(ctx, (double)Vh * nrhs * spinor_site_bytes(inner) * 6.0);
+      LQCD_TRY(dispatch_prec(ctx, inner, [&](auto P) {
+        cg_xs_kernel<decltype(P)::value><<<vgrid, 128, 0, ctx->stream>>>(
+            va, h, X.ptr, X.scale, p.f.ptr, p.f.scale, z.f.ptr, z.f.scale, s.f.ptr, s.f.scale,
+            ctx->partials);
+      }));
+      launch_finalize(ctx, h, nrhs, nbv, FIN_SS, nullptr);
+      launch_finalize(ctx, h, nrhs, nbv, FIN_BETA, nullptr);
+    }
+    count_launch(ctx, (double)Vh * nrhs * spinor_site_bytes(inner) * 3.0);
+    LQCD_TRY(dispatch_prec(ctx, inner, [&](auto P) {
+      cg_p_kernel<decltype(P)::value><<<vgrid, 128, 0, ctx->stream>>>(va, h, p.f.ptr, p.f.scale,
+                                                                       z.f.ptr, z.f.scale);
+    }));
+    LQCD_CUDA(ctx, cudaGetLastError());
+    return LQCD_OK;
+  };
+
+  const int chunk = prm.check_every > 0 ? prm.check_every : 10;
+  cudaGraphExec_t gexec = nullptr;
+  cudaGraph_t graph = nullptr;
+  lqcd_counters cnt_before{}, chunk_cnt{};
+  if (prm.use_graph) {
+    cudaStream_t cap;
+    LQCD_CUDA(ctx, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaStream_t saved = ctx->stream;
+    ctx->stream = cap;
+    cnt_before = ctx->cnt;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    lqcd_status cs = LQCD_OK;
+    if (e == cudaSuccess) {
+      for (int k = 0; k < chunk && cs == LQCD_OK; k++) cs = iteration();
+      e = cudaStreamEndCapture(cap, &graph);
+    }
+    ctx->stream = saved;
+    cudaStreamDestroy(cap);
+    // the capture executed nothing: keep its counts as the per-replay increment
+    chunk_cnt.launches = ctx->cnt.launches - cnt_before.launches;
+    chunk_cnt.hop_launches = ctx->cnt.hop_launches - cnt_before.hop_launches;
+    chunk_cnt.bytes = ctx->cnt.bytes - cnt_before.bytes;
+    chunk_cnt.hop_bytes = ctx->cnt.hop_bytes - cnt_before.hop_bytes;
+    chunk_cnt.hop_flops = ctx->cnt.hop_flops - cnt_before.hop_flops;
+    chunk_cnt.hop_sites = ctx->cnt.hop_sites - cnt_before.hop_sites;
+    ctx->cnt = cnt_before;
+    if (e != cudaSuccess) return cuda_check(ctx, e, "graph capture");
+    if (cs != LQCD_OK) return cs;
+    e = cudaGraphInstantiate(&gexec, graph, 0);
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(graph);
+      return cuda_check(ctx, e, "graph instantiate");
+    }
+  }
+  struct GraphGuard {
+    cudaGraphExec_t &e;
+    cudaGraph_t &g;
+    ~GraphGuard() {
+      if (e) cudaGraphExecDestroy(e);
+      if (g) cudaGraphDestroy(g);
+    }
+  } guard{gexec, graph};
+
+  SolverHdr hh;
+  int reliable = 0;
+  lqcd_status result = LQCD_OK;
+  std::vector<double> ss2;
+  for (;;) {
+    if (gexec) {
+      LQCD_CUDA(ctx, cudaGraphLaunch(gexec, ctx->stream));
+      ctx->cnt.launches += chunk_cnt.launches;
+      ctx->cnt.hop_launches += chunk_cnt.hop_launches;
+      ctx->cnt.bytes += chunk_cnt.bytes;
+      ctx->cnt.hop_bytes += chunk_cnt.hop_bytes;
+      ctx->cnt.hop_flops += chunk_cnt.hop_flops;
+      ctx->cnt.hop_sites += chunk_cnt.hop_sites;
+    } else {
+      for (int k = 0; k < chunk; k++) LQCD_TRY(iteration());
+    }
+    LQCD_CUDA(ctx, cudaMemcpyAsync(ctx->pinned, h, sizeof(SolverHdr), cudaMemcpyDeviceToHost, ctx->stream));
+    LQCD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    std::memcpy(&hh, ctx->pinned, sizeof(hh));
+    if (hh.nonfinite) {
+      result = fail(ctx, LQCD_ERR_NONFINITE, "CG: non-finite or breakdown scalar after %d iterations", hh.iters);
+      break;
+    }
+    bool finished = hh.all_done != 0;
+    if (mixed && (hh.need_rel || finished)) {
+      // reliable update: xo += X; X = 0; r = bhat - Mhat xo (outer); s = r
+      reliable++;
+      dim3 g2(nbv, nrhs);
+      count_launch(ctx, (double)Vh * nrhs * (2.0 * spinor_site_bytes(outer) + spinor_site_bytes(inner)));
+      LQCD_TRY(dispatch_prec(ctx, outer, [&](auto PO) {
+        dispatch_prec(ctx, inner, [&](auto PI) {
+          accum_convert_kernel<decltype(PO)::value, decltype(PI)::value><<<g2, 128, 0, ctx->stream>>>(
+              Vh, xo.rhs_stride, X.rhs_stride, X.scale_rhs_stride, xo.ptr, X.ptr, X.scale);
+        });
+      }));
+      LQCD_CUDA(ctx, cudaMemsetAsync(X.ptr, 0, X.rhs_stride * nrhs, ctx->stream));
+      int nbo = 0;
+      LQCD_TRY(apply_schur(Oo, xo, r_o.f, tmp_o.f, 0, false, nullptr, &nbo, nullptr));
+      if (normal) {  // r = phi - Mhat^+ Mhat xo
+        LQCD_TRY(apply_schur(Oo, r_o.f, y_o.f, tmp_o.f, 0, true, nullptr, &nbo, nullptr));
+        std::swap(r_o.f.ptr, y_o.f.ptr);
+      }
+      int nbl = 0;
+      LQCD_TRY(lincomb(ctx, Vh, r_o.f, bhat, &r_o.f, one, one, mone, mone, ctx->partials, &nbl));
+      LQCD_TRY(host_sums(ctx, h, nbl, nrhs, tmpd, &ss2));
+      HalfField &res_s = normal ? z.f : s.f;
+      LQCD_TRY(spinor_convert_raw(ctx, Vh, nrhs, r_o.f.ptr, r_o.f.scale, outer, res_s.ptr, res_s.scale, inner));
+      bool all_ok = true;
+      for (int r = 0; r < nrhs; r++)
+        if (!(ss2[r] <= prm.tol * prm.tol * b2[r] * 0.25)) all_ok = false;
+      if (finished && all_ok) break;
+      // z = Mhat^+ s; beta = |z|^2 / zz_old; p = z + beta p
+      state_after_reliable_kernel<<<1, 64, 0, ctx->stream>>>(h, tmpd);
+      if (!normal) {
+        LQCD_TRY(apply_schur(Oi, s.f, z.f, t.f, 0, true, ctx->partials, &nb, nullptr));
+        launch_finalize(ctx, h, nrhs, nb, FIN_BETA, nullptr);
+      } else {
+        LQCD_TRY(lincomb(ctx, Vh, z.f, z.f, nullptr, one, one, zero, zero, ctx->partials, &nbl));
+        launch_finalize(ctx, h, nrhs, nbl, FIN_BETA, nullptr);
+      }
+      // FIN_BETA skips when halted: state_after_reliable clears halt unless all done
+      count_launch(ctx, (double)Vh * nrhs * spinor_site_bytes(inner) * 3.0);
+      LQCD_TRY(dispatch_prec(ctx, inner, [&](auto P) {
+        cg_p_kernel<decltype(P)::value><<<dim3(nbv, nrhs), 128, 0, ctx->stream>>>(
+            va, h, p.f.ptr, p.f.scale, z.f.ptr, z.f.scale);
+      }));
+      LQCD_CUDA(ctx, cudaGetLastError());
+      if (hh.iters >= prm.max_iter) {
+        result = LQCD_ERR_NOCONV;
+        break;
+      }
+      continue;
+    }
+    if (finished) break;
+    if (hh.iters >= prm.max_iter) {
+      result = LQCD_ERR_NOCONV;
+      break;
+    }
+  }
+  if (mixed && result != LQCD_OK) {
+    // fold the sloppy iterate into x before returning
+    dim3 g2(nbv, nrhs);
+    LQCD_TRY(dispatch_prec(ctx, outer, [&](auto PO) {
+      dispatch_prec(ctx, inner, [&](auto PI) {
+        accum_convert_kernel<decltype(PO)::value, decltype(PI)::value><<<g2, 128, 0, ctx->stream>>>(
+            Vh, xo.rhs_stride, X.rhs_stride, X.scale_rhs_stride, xo.ptr, X.ptr, X.scale);
+      });
+    }));
+  }
+  // per-rhs iteration counts
+  std::vector<RhsState> rsh(nrhs);
+  LQCD_CUDA(ctx, cudaMemcpyAsync(rsh.data(), (char *)h + sizeof(SolverHdr), sizeof(RhsState) * nrhs,
+                                 cudaMemcpyDeviceToHost, ctx->stream));
+  LQCD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  int itmax = 0;
+  for (int r = 0; r < nrhs; r++) {
+    st[r].iters += rsh[r].iters;
+    st[r].reliable_updates += reliable;
+    if (rsh[r].iters > itmax) itmax = rsh[r].iters;
+  }
+  if (iters_used) *iters_used = itmax;
+  if (result == LQCD_ERR_NOCONV) return LQCD_ERR_NOCONV;
+  return result;
+}
+
+// Full solve on EO full fields (outer F64 user fields b, x).
+lqcd_status cg_solve_eo(lqcd_ctx *ctx, lqcd_gauge *U, const HalfField &b_full, const HalfField &x_full,
+                        double kappa, double mu, const lqcd_cg_params &prm, lqcd_cg_stats *st) {
+  auto t0 = std::chrono::steady_clock::now();
+  const Geom &g = U->g;
+  const int Vh = g.Vh, nrhs = b_full.nrhs;
+  const int outer = prm.outer_prec;
+  for (int r = 0; r < nrhs; r++) std::memset(&st[r], 0, sizeof(lqcd_cg_stats));
+  Op O64{ctx, g, {}, LQCD_F64, U->recon, kappa, mu};
+  LQCD_TRY(gauge_view(ctx, U, LQCD_F64, U->recon, &O64.U));
+  HalfField be = half_of(b_full, 0, Vh), bo = half_of(b_full, 1, Vh);
+  HalfField xe = half_of(x_full, 0, Vh), xodd = half_of(x_full, 1, Vh);
+  const HostC one{1, 0}, zero{0, 0}, mone{-1, 0};
+  int nbv = (Vh + 127) / 128;
+  int nb = hop_blocks(g, nrhs);
+  LQCD_TRY(ensure_partials(ctx, (size_t)nrhs * 2 * (nb > nbv ? nb : nbv)));
+  SolverHdr *h;
+  LQCD_TRY(ensure_state(ctx, nrhs, &h));
+  // |b|^2
+  std::vector<double> b2(nrhs), e2;
+  {
+    Vec tmp;
+    LQCD_TRY(tmp.alloc(ctx, LQCD_F64, Vh, nrhs));
+    int n1 = 0;
+    LQCD_TRY(lincomb(ctx, Vh, tmp.f, be, nullptr, one, one, zero, zero, ctx->partials, &n1));
+    LQCD_TRY(host_sums(ctx, h, n1, nrhs, state_scratch(h, nrhs, 2), &e2));
+    LQCD_TRY(lincomb(ctx, Vh, tmp.f, bo, nullptr, one, one, zero, zero, ctx->partials, &n1));
+    std::vector<double> o2;
+    LQCD_TRY(host_sums(ctx, h, n1, nrhs, state_scratch(h, nrhs, 2), &o2));
+    for (int r = 0; r < nrhs; r++) b2[r] = e2[r] + o2[r];
+  }
+  for (int r = 0; r < nrhs; r++)
+    if (!std::isfinite(b2[r])) return fail(ctx, LQCD_ERR_NONFINITE, "right-hand side %d is not finite", r);
+  LQCD_CUDA(ctx, cudaMemsetAsync(x_full.ptr, 0, x_full.rhs_stride * nrhs, ctx->stream));
+  // working copies of the current right-hand side (b, later the true residual)
+  Vec rhs_e, rhs_o, t_o, bhat64, corr_e, corr_o, res_e, res_o, xo_outer, bhat_outer;
+  LQCD_TRY(rhs_e.alloc(ctx, LQCD_F64, Vh, nrhs));
+  LQCD_TRY(rhs_o.alloc(ctx, LQCD_F64, Vh, nrhs));
+  LQCD_TRY(t_o.alloc(ctx, LQCD_F64, Vh, nrhs));
+  LQCD_TRY(bhat64.alloc(ctx, LQCD_F64, Vh, nrhs));
+  LQCD_TRY(corr_e.alloc(ctx, LQCD_F64, Vh, nrhs));
+  LQCD_TRY(corr_o.alloc(ctx, LQCD_F64, Vh, nrhs));
+  LQCD_TRY(res_e.alloc(ctx, LQCD_F64, Vh, nrhs));
+  LQCD_TRY(res_o.alloc(ctx, LQCD_F64, Vh, nrhs));
+  LQCD_TRY(xo_outer.alloc(ctx, outer, Vh, nrhs));
+  if (outer != LQCD_F64) LQCD_TRY(bhat_outer.alloc(ctx, outer, Vh, nrhs));
+  LQCD_TRY(lincomb(ctx, Vh, rhs_e.f, be, nullptr, one, one, zero, zero, nullptr, nullptr));
+  LQCD_TRY(lincomb(ctx, Vh, rhs_o.f, bo, nullptr, one, one, zero, zero, nullptr, nullptr));
+  TmCoef c = tm_coef(kappa, mu, false);
+  lqcd_status result = LQCD_OK;
+  double worst = 0.0;
+  for (int cycle = 0;; cycle++) {
+    // bhat_e = rhs_e + kappa H_eo A_o^-1 rhs_o
+    LQCD_TRY(lincomb(ctx, Vh, t_o.f, rhs_o.f, nullptr, c.Ai_up, c.Ai_dn, zero, zero, nullptr, nullptr));
+    HopLaunch Ls;
+    Ls.prec = LQCD_F64;
+    Ls.recon = U->recon;
+    Ls.U = O64.U;
+    Ls.in = t_o.f;
+    Ls.out = bhat64.f;
+    Ls.aux = rhs_e.f;
+    Ls.has_aux = true;
+    Ls.out_parity = 0;
+    Ls.c_up = Ls.c_dn = {kappa, 0.0};
+    Ls.d_up = Ls.d_dn = one;
+    LQCD_TRY(launch_hop(ctx, g, Ls, nullptr));
+    HalfField bh = bhat64.f;
+    if (outer != LQCD_F64) {
+      LQCD_TRY(spinor_convert_raw(ctx, Vh, nrhs, bhat64.f.ptr, nullptr, LQCD_F64, bhat_outer.f.ptr,
+                                  nullptr, outer));
+      bh = bhat_outer.f;
+    }
+    LQCD_CUDA(ctx, cudaMemsetAsync(xo_outer.f.ptr, 0, xo_outer.f.rhs_stride * nrhs, ctx->stream));
+    int used = 0;
+    lqcd_status s = cgls_even(ctx, U, g, kappa, mu, prm, bh, xo_outer.f, b2, st, nrhs, &used, false);
+    if (s != LQCD_OK && s != LQCD_ERR_NOCONV) return s;
+    // corr_e = x_e (F64); corr_o = A_o^-1 (rhs_o + kappa H_oe corr_e)
+    if (outer != LQCD_F64)
+      LQCD_TRY(spinor_convert_raw(ctx, Vh, nrhs, xo_outer.f.ptr, nullptr, outer, corr_e.f.ptr, nullptr,
+                                  LQCD_F64));
+    else
+      LQCD_TRY(lincomb(ctx, Vh, corr_e.f, xo_outer.f, nullptr, one, one, zero, zero, nullptr, nullptr));
+    HopLaunch Lr;
+    Lr.prec = LQCD_F64;
+    Lr.recon = U->recon;
+    Lr.U = O64.U;
+    Lr.in = corr_e.f;
+    Lr.out = corr_o.f;
+    Lr.aux = rhs_o.f;
+    Lr.has_aux = true;
+    Lr.out_parity = 1;
+    Lr.c_up = {kappa * c.Ai_up.re, kappa * c.Ai_up.im};
+    Lr.c_dn = {kappa * c.Ai_dn.re, kappa * c.Ai_dn.im};
+    Lr.d_up = c.Ai_up;
+    Lr.d_dn = c.Ai_dn;
+    LQCD_TRY(launch_hop(ctx, g, Lr, nullptr));
+    // x += corr
+    LQCD_TRY(lincomb(ctx, Vh, xe, xe, &corr_e.f, one, one, one, one, nullptr, nullptr));
+    LQCD_TRY(lincomb(ctx, Vh, xodd, xodd, &corr_o.f, one, one, one, one, nullptr, nullptr));
+    // true residual: res = b - M x (FP64, both parities)
+    int nbh = 0;
+    LQCD_TRY(apply_full(O64, xe, xodd, res_e.f, res_o.f, false, nullptr, nullptr, &nbh));
+    int n1 = 0;
+    LQCD_TRY(lincomb(ctx, Vh, rhs_e.f, be, &res_e.f, one, one, mone, mone, ctx->partials, &n1));
+    LQCD_TRY(host_sums(ctx, h, n1, nrhs, state_scratch(h, nrhs, 2), &e2));
+    std::vector<double> o2;
+    LQCD_TRY(lincomb(ctx, Vh, rhs_o.f, bo, &res_o.f, one, one, mone, mone, ctx->partials, &n1));
+    LQCD_TRY(host_sums(ctx, h, n1, nrhs, state_scratch(h, nrhs, 2), &o2));
+    worst = 0.0;
+    bool all = true;
+    int total_iters = 0;
+    for (int r = 0; r < nrhs; r++) {
+      double tr = std::sqrt((e2[r] + o2[r]) / b2[r]);
+      st[r].true_resid = tr;
+      st[r].converged = tr <= prm.tol;
+      all = all && st[r].converged;
+      worst = std::fmax(worst, tr);
+      total_iters = st[r].iters > total_iters ? st[r].iters : total_iters;
+      if (!std::isfinite(tr)) return fail(ctx, LQCD_ERR_NONFINITE, "true residual is not finite");
+    }
+    if (all) break;
+    if (cycle >= prm.max_restarts || total_iters >= prm.max_iter) {
+      result = LQCD_ERR_NOCONV;
+      break;
+    }
+    for (int r = 0; r < nrhs; r++) {
+      if (st[r].converged) {  // converged right-hand sides get a zero correction
+        LQCD_CUDA(ctx, cudaMemsetAsync((char *)rhs_e.f.ptr + r * rhs_e.f.rhs_stride, 0,
+                                       rhs_e.f.rhs_stride, ctx->stream));
+        LQCD_CUDA(ctx, cudaMemsetAsync((char *)rhs_o.f.ptr + r * rhs_o.f.rhs_stride, 0,
+                                       rhs_o.f.rhs_stride, ctx->stream));
+      } else {
+        st[r].restarts++;
+      }
+    }
+    // next cycle solves M d = (b - M x): rhs_e, rhs_o already hold the residual
+  }
+  double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  for (int r = 0; r < nrhs; r++) st[r].seconds = secs;
+  if (result == LQCD_ERR_NOCONV)
+    fail(ctx, LQCD_ERR_NOCONV, "CG stopped with true residual %.3e > tol %.3e", worst, prm.tol);
+  return result;
+}
+
+}  // namespace lqcd

@@ -1,0 +1,403 @@
+// common.cuh -- device-side building blocks shared by the sm_103a kernels:
+// lattice geometry on the even-odd checkerboard, complex arithmetic in
+// double / float / float-float ("df64"), and the storage formats of the
+// even-odd structure-of-arrays fields (Sec. 4.2 of the paper: SoA on a 16-byte
+// base type, gauge field split by the parity of the originating site).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/lqcd.h"
+
+#define LQCD_DEV __device__ __forceinline__
+#define LQCD_HD __host__ __device__ __forceinline__
+
+namespace lqcd {
+
+// ---------------------------------------------------------------------------
+// Geometry
+// ---------------------------------------------------------------------------
+
+struct Geom {
+  int L[4];     // x, y, z, t
+  int Lh0;      // Lx / 2
+  int Vh;       // sites per parity
+  int antiper;  // fermion boundary factor -1 across t
+};
+
+// Coordinates of checkerboard site cb of parity p.  The lexicographic index
+// is i = x + Lx*r with row r = y + Ly*(z + Lz*t); since Lx is even the pair
+// (2k, 2k+1) along x holds one site of each parity and cb = i/2.
+struct Site {
+  int x, y, z, t, r;
+};
+
+LQCD_DEV Site site_of(const Geom& g, int p, int cb) {
+  Site s;
+  s.r = cb / g.Lh0;
+  int xh = cb - s.r * g.Lh0;
+  s.y = s.r % g.L[1];
+  int zt = s.r / g.L[1];
+  s.z = zt % g.L[2];
+  s.t = zt / g.L[2];
+  s.x = 2 * xh + ((p + s.y + s.z + s.t) & 1);
+  return s;
+}
+
+// checkerboard index of the neighbour x + dir*mu_hat (dir = +1 / -1)
+LQCD_DEV int neighbour_cb(const Geom& g, const Site& s, int mu, int dir) {
+  int x = s.x, y = s.y, z = s.z, t = s.t;
+  switch (mu) {
+    case 0: x = (x + dir + g.L[0]) % g.L[0]; break;
+    case 1: y = (y + dir + g.L[1]) % g.L[1]; break;
+    case 2: z = (z + dir + g.L[2]) % g.L[2]; break;
+    default: t = (t + dir + g.L[3]) % g.L[3]; break;
+  }
+  int r = y + g.L[1] * (z + g.L[2] * t);
+  return r * g.Lh0 + (x >> 1);
+}
+
+LQCD_DEV long lexi_index(const Geom& g, const Site& s) {
+  return (long)s.x + (long)g.L[0] * s.r;
+}
+
+// ---------------------------------------------------------------------------
+// float-float arithmetic (value = hi + lo, |lo| <= ulp(hi)/2 after
+// normalisation).  Error-free transformations: Knuth's TwoSum, Dekker's
+// Fast2Sum, and the FMA-based TwoProduct; the double-word add/multiply follow
+// Dekker (1971) and the double-double library of Hida, Li and Bailey.
+// ---------------------------------------------------------------------------
+
+struct df {
+  float hi, lo;
+};
+
+LQCD_DEV df two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+LQCD_DEV df fast_two_sum(float a, float b) {  // requires |a| >= |b| (or a == 0)
+  float s = __fadd_rn(a, b);
+  float e = __fsub_rn(b, __fsub_rn(s, a));
+  return {s, e};
+}
+LQCD_DEV df two_prod(float a, float b) {
+  float p = __fmul_rn(a, b);
+  float e = __fmaf_rn(a, b, -p);
+  return {p, e};
+}
+LQCD_DEV df operator+(df a, df b) {
+  df s = two_sum(a.hi, b.hi);
+  df t = two_sum(a.lo, b.lo);
+  s.lo = __fadd_rn(s.lo, t.hi);
+  s = fast_two_sum(s.hi, s.lo);
+  s.lo = __fadd_rn(s.lo, t.lo);
+  return fast_two_sum(s.hi, s.lo);
+}
+LQCD_DEV df operator-(df a) { return {-a.hi, -a.lo}; }
+LQCD_DEV df operator-(df a, df b) { return a + (-b); }
+LQCD_DEV df operator*(df a, df b) {
+  df p = two_prod(a.hi, b.hi);
+  p.lo = __fmaf_rn(a.hi, b.lo, p.lo);
+  p.lo = __fmaf_rn(a.lo, b.hi, p.lo);
+  return fast_two_sum(p.hi, p.lo);
+}
+LQCD_HD df df_from_double(double v) {
+  float hi = (float)v;
+  float lo = (float)(v - (double)hi);
+  return {hi, lo};
+}
+LQCD_HD double df_to_double(df v) { return (double)v.hi + (double)v.lo; }
+
+// ---------------------------------------------------------------------------
+// Complex numbers over a real type R (double, float, df)
+// ---------------------------------------------------------------------------
+
+template <class R>
+struct Cx {
+  R re, im;
+};
+
+template <class R> LQCD_DEV R rzero();
+template <> LQCD_DEV double rzero<double>() { return 0.0; }
+template <> LQCD_DEV float rzero<float>() { return 0.0f; }
+template <> LQCD_DEV df rzero<df>() { return {0.0f, 0.0f}; }
+
+template <class R> LQCD_DEV Cx<R> czero() { return {rzero<R>(), rzero<R>()}; }
+template <class R> LQCD_DEV Cx<R> operator+(Cx<R> a, Cx<R> b) { return {a.re + b.re, a.im + b.im}; }
+template <class R> LQCD_DEV Cx<R> operator-(Cx<R> a, Cx<R> b) { return {a.re - b.re, a.im - b.im}; }
+template <class R> LQCD_DEV Cx<R> operator-(Cx<R> a) { return {-a.re, -a.im}; }
+template <class R> LQCD_DEV Cx<R> operator*(Cx<R> a, Cx<R> b) {
+  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+// i * a and -i * a
+template <class R> LQCD_DEV Cx<R> times_i(Cx<R> a) { return {-a.im, a.re}; }
+template <class R> LQCD_DEV Cx<R> times_mi(Cx<R> a) { return {a.im, -a.re}; }
+template <class R> LQCD_DEV Cx<R> conj(Cx<R> a) { return {a.re, -a.im}; }
+// conj(a) * b
+template <class R> LQCD_DEV Cx<R> conj_mul(Cx<R> a, Cx<R> b) {
+  return {a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re};
+}
+// a * b + c
+template <class R> LQCD_DEV Cx<R> cmadd(Cx<R> a, Cx<R> b, Cx<R> c) {
+  return {c.re + a.re * b.re - a.im * b.im, c.im + a.re * b.im + a.im * b.re};
+}
+template <> LQCD_DEV Cx<double> cmadd(Cx<double> a, Cx<double> b, Cx<double> c) {
+  return {fma(-a.im, b.im, fma(a.re, b.re, c.re)), fma(a.im, b.re, fma(a.re, b.im, c.im))};
+}
+template <> LQCD_DEV Cx<float> cmadd(Cx<float> a, Cx<float> b, Cx<float> c) {
+  return {fmaf(-a.im, b.im, fmaf(a.re, b.re, c.re)), fmaf(a.im, b.re, fmaf(a.re, b.im, c.im))};
+}
+template <class R> LQCD_DEV Cx<R> conj_madd(Cx<R> a, Cx<R> b, Cx<R> c) {  // conj(a)*b + c
+  return {c.re + a.re * b.re + a.im * b.im, c.im + a.re * b.im - a.im * b.re};
+}
+template <> LQCD_DEV Cx<double> conj_madd(Cx<double> a, Cx<double> b, Cx<double> c) {
+  return {fma(a.im, b.im, fma(a.re, b.re, c.re)), fma(-a.im, b.re, fma(a.re, b.im, c.im))};
+}
+template <> LQCD_DEV Cx<float> conj_madd(Cx<float> a, Cx<float> b, Cx<float> c) {
+  return {fmaf(a.im, b.im, fmaf(a.re, b.re, c.re)), fmaf(-a.im, b.re, fmaf(a.re, b.im, c.im))};
+}
+
+// Host-side complex scalar handed to kernels in the arithmetic of the kernel.
+struct HostC {
+  double re, im;
+};
+template <class R> LQCD_DEV R from_double(double v);
+template <> LQCD_DEV double from_double<double>(double v) { return v; }
+template <> LQCD_DEV float from_double<float>(double v) { return (float)v; }
+template <> LQCD_DEV df from_double<df>(double v) { return df_from_double(v); }
+template <class R> LQCD_DEV Cx<R> cfrom(HostC c) { return {from_double<R>(c.re), from_double<R>(c.im)}; }
+
+LQCD_DEV double to_double(double v) { return v; }
+LQCD_DEV double to_double(float v) { return (double)v; }
+LQCD_DEV double to_double(df v) { return df_to_double(v); }
+
+// |a|^2 accumulated in double (norms and dot products use FP64 partial sums)
+template <class R> LQCD_DEV double norm2_d(Cx<R> a) {
+  double re = to_double(a.re), im = to_double(a.im);
+  return re * re + im * im;
+}
+// |a|^2 for a df complex, summed in float-float before the FP64 conversion
+LQCD_DEV df norm2_df(Cx<df> a) { return a.re * a.re + a.im * a.im; }
+
+// ---------------------------------------------------------------------------
+// Storage formats of even-odd SoA spinor fields.
+// A half field is [component 12][Vh] in 16-byte words per the precision.
+// ---------------------------------------------------------------------------
+
+struct SpinorView {
+  void* ptr;     // start of this half field (one right-hand side)
+  float* scale;  // [Vh] for the 16-bit formats
+  int Vh;
+};
+
+template <int PREC> struct SpinorIO;
+
+template <> struct SpinorIO<LQCD_F64> {
+  using R = double;
+  static LQCD_DEV void load(const SpinorView& v, int cb, Cx<double> s[12]) {
+    const double2* p = (const double2*)v.ptr;
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+      double2 w = __ldg(p + (size_t)k * v.Vh + cb);
+      s[k] = {w.x, w.y};
+    }
+  }
+  static LQCD_DEV void store(const SpinorView& v, int cb, const Cx<double> s[12]) {
+    double2* p = (double2*)v.ptr;
+#pragma unroll
+    for (int k = 0; k < 12; k++) p[(size_t)k * v.Vh + cb] = make_double2(s[k].re, s[k].im);
+  }
+};
+
+template <> struct SpinorIO<LQCD_DF64> {
+  using R = df;
+  static LQCD_DEV void load(const SpinorView& v, int cb, Cx<df> s[12]) {
+    const float4* p = (const float4*)v.ptr;
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+      float4 w = __ldg(p + (size_t)k * v.Vh + cb);
+      s[k] = {{w.x, w.z}, {w.y, w.w}};
+    }
+  }
+  static LQCD_DEV void store(const SpinorView& v, int cb, const Cx<df> s[12]) {
+    float4* p = (float4*)v.ptr;
+#pragma unroll
+    for (int k = 0; k < 12; k++)
+      p[(size_t)k * v.Vh + cb] = make_float4(s[k].re.hi, s[k].im.hi, s[k].re.lo, s[k].im.lo);
+  }
+};
+
+template <> struct SpinorIO<LQCD_F32> {
+  using R = float;
+  static LQCD_DEV void load(const SpinorView& v, int cb, Cx<float> s[12]) {
+    const float4* p = (const float4*)v.ptr;
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+      float4 w = __ldg(p + (size_t)k * v.Vh + cb);
+      s[2 * k] = {w.x, w.y};
+      s[2 * k + 1] = {w.z, w.w};
+    }
+  }
+  static LQCD_DEV void store(const SpinorView& v, int cb, const Cx<float> s[12]) {
+    float4* p = (float4*)v.ptr;
+#pragma unroll
+    for (int k = 0; k < 6; k++)
+      p[(size_t)k * v.Vh + cb] = make_float4(s[2 * k].re, s[2 * k].im, s[2 * k + 1].re, s[2 * k + 1].im);
+  }
+};
+
+// 16-bit reals with one float scale per site: value = stored * scale, the
+// scale being the site's largest |real component| (so stored values lie in
+// [-1, 1]).  24 reals = three 16-byte words.
+template <class H> struct Half16;
+template <> struct Half16<__nv_bfloat16> {
+  static LQCD_DEV float to_f(uint16_t u) { return __bfloat162float(__ushort_as_bfloat16(u)); }
+  static LQCD_DEV uint16_t from_f(float f) { return __bfloat16_as_ushort(__float2bfloat16_rn(f)); }
+};
+template <> struct Half16<__half> {
+  static LQCD_DEV float to_f(uint16_t u) { return __half2float(__ushort_as_half(u)); }
+  static LQCD_DEV uint16_t from_f(float f) { return __half_as_ushort(__float2half_rn(f)); }
+};
+
+template <class H> struct SpinorIO16 {
+  using R = float;
+  static LQCD_DEV void load(const SpinorView& v, int cb, Cx<float> s[12]) {
+    const uint4* p = (const uint4*)v.ptr;
+    float sc = __ldg(v.scale + cb);
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+      uint4 w = __ldg(p + (size_t)k * v.Vh + cb);
+      uint32_t ww[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+      for (int j = 0; j < 4; j++) {
+        s[4 * k + j].re = Half16<H>::to_f((uint16_t)(ww[j] & 0xFFFFu)) * sc;
+        s[4 * k + j].im = Half16<H>::to_f((uint16_t)(ww[j] >> 16)) * sc;
+      }
+    }
+  }
+  static LQCD_DEV void store(const SpinorView& v, int cb, const Cx<float> s[12]) {
+    float m = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 12; k++) m = fmaxf(m, fmaxf(fabsf(s[k].re), fabsf(s[k].im)));
+    float inv = m > 0.0f ? 1.0f / m : 0.0f;
+    uint4* p = (uint4*)v.ptr;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+      uint32_t ww[4];
+#pragma unroll
+      for (int j = 0; j < 4; j++) {
+        uint32_t lo = Half16<H>::from_f(s[4 * k + j].re * inv);
+        uint32_t hi = Half16<H>::from_f(s[4 * k + j].im * inv);
+        ww[j] = lo | (hi << 16);
+      }
+      p[(size_t)k * v.Vh + cb] = make_uint4(ww[0], ww[1], ww[2], ww[3]);
+    }
+    v.scale[cb] = m;
+  }
+};
+template <> struct SpinorIO<LQCD_BF16S> : SpinorIO16<__nv_bfloat16> {};
+template <> struct SpinorIO<LQCD_F16S> : SpinorIO16<__half> {};
+
+// ---------------------------------------------------------------------------
+// Gauge field storage: [parity][mu][entry][Vh] per precision, entry = 3*row +
+// col for the 9 (recon 18) or 6 (recon 12) stored complex entries.
+//   F64 / DF64 : 16 B per complex entry.
+//   F32        : complex entries paired in 16-B words; recon 18 stores
+//                entries 0..7 in 4 words and entry 8 in a trailing 8-B word
+//                plane; recon 12 uses 3 words.
+//   BF16 / F16 : 16-bit reals, recon 12 only: 12 reals = 16-B + 8-B planes.
+// ---------------------------------------------------------------------------
+
+struct GaugeView {
+  const void* ptr;  // start of the field
+  int Vh;
+  size_t parity_stride;  // bytes per parity block
+  size_t mu_stride;      // bytes per direction block
+};
+
+template <int PREC, int RECON> struct LinkIO;
+
+template <int RECON> struct LinkIO<LQCD_F64, RECON> {
+  static LQCD_DEV void load(const GaugeView& g, int p, int mu, int cb, Cx<double> u[9]) {
+    const double2* b = (const double2*)((const char*)g.ptr + p * g.parity_stride + mu * g.mu_stride);
+#pragma unroll
+    for (int k = 0; k < (RECON == 18 ? 9 : 6); k++) {
+      double2 w = __ldg(b + (size_t)k * g.Vh + cb);
+      u[k] = {w.x, w.y};
+    }
+  }
+};
+template <int RECON> struct LinkIO<LQCD_DF64, RECON> {
+  static LQCD_DEV void load(const GaugeView& g, int p, int mu, int cb, Cx<df> u[9]) {
+    const float4* b = (const float4*)((const char*)g.ptr + p * g.parity_stride + mu * g.mu_stride);
+#pragma unroll
+    for (int k = 0; k < (RECON == 18 ? 9 : 6); k++) {
+      float4 w = __ldg(b + (size_t)k * g.Vh + cb);
+      u[k] = {{w.x, w.z}, {w.y, w.w}};
+    }
+  }
+};
+template <int RECON> struct LinkIO<LQCD_F32, RECON> {
+  static LQCD_DEV void load(const GaugeView& g, int p, int mu, int cb, Cx<float> u[9]) {
+    const char* base = (const char*)g.ptr + p * g.parity_stride + mu * g.mu_stride;
+    const float4* b = (const float4*)base;
+    constexpr int NW = RECON == 18 ? 4 : 3;
+#pragma unroll
+    for (int k = 0; k < NW; k++) {
+      float4 w = __ldg(b + (size_t)k * g.Vh + cb);
+      u[2 * k] = {w.x, w.y};
+      u[2 * k + 1] = {w.z, w.w};
+    }
+    if (RECON == 18) {
+      const float2* t = (const float2*)(base + (size_t)4 * g.Vh * 16);
+      float2 w = __ldg(t + cb);
+      u[8] = {w.x, w.y};
+    }
+  }
+};
+template <class H> struct LinkIO16 {
+  static LQCD_DEV void load(const GaugeView& g, int p, int mu, int cb, Cx<float> u[9]) {
+    const char* base = (const char*)g.ptr + p * g.parity_stride + mu * g.mu_stride;
+    uint4 w = __ldg((const uint4*)base + cb);
+    uint2 w2 = __ldg((const uint2*)(base + (size_t)g.Vh * 16) + cb);
+    uint32_t ww[6] = {w.x, w.y, w.z, w.w, w2.x, w2.y};
+#pragma unroll
+    for (int k = 0; k < 6; k++)
+      u[k] = {Half16<H>::to_f((uint16_t)(ww[k] & 0xFFFFu)), Half16<H>::to_f((uint16_t)(ww[k] >> 16))};
+  }
+};
+template <> struct LinkIO<LQCD_BF16S, 12> : LinkIO16<__nv_bfloat16> {};
+template <> struct LinkIO<LQCD_F16S, 12> : LinkIO16<__half> {};
+
+// REC12 (Sec. 4.1): row 2 = conj(row0 x row1) for an SU(3) link.
+template <class R> LQCD_DEV void reconstruct_row2(Cx<R> u[9]) {
+  u[6] = conj(u[1] * u[5] - u[2] * u[4]);
+  u[7] = conj(u[2] * u[3] - u[0] * u[5]);
+  u[8] = conj(u[0] * u[4] - u[1] * u[3]);
+}
+
+// Bytes per link entry block for the sizing of gauge fields (host side).
+LQCD_HD size_t link_bytes_per_site(int prec, int recon) {
+  switch (prec) {
+    case LQCD_F64:
+    case LQCD_DF64: return (size_t)16 * (recon == 18 ? 9 : 6);
+    case LQCD_F32: return recon == 18 ? 72 : 48;
+    default: return 24;  // 16-bit, recon 12
+  }
+}
+LQCD_HD size_t spinor_bytes_per_site(int prec) {
+  switch (prec) {
+    case LQCD_F64:
+    case LQCD_DF64: return 192;
+    case LQCD_F32: return 96;
+    default: return 48;
+  }
+}
+
+}  // namespace lqcd

@@ -1,0 +1,616 @@
+// gauge.cu -- gauge-field kernels of Sec. 2.1/2.2 in FP64 on the FP64 master
+// copy ([parity][mu][9][Vh] complex128):
+//   * plaquette and Wilson gauge action  S_g = (beta/3) sum (3 - Re Tr U_munu)
+//   * gauge force dS_g/domega^a = -(beta/3) Re Tr[i T^a U_mu(x) A_mu(x)],
+//     A = staple sum (Sec. 2.2: the plaquette product without U_mu(x))
+//   * Cabibbo-Marinari heatbath (Sec. 2.2, Fig. "heatbath algorithm") with the
+//     exact SU(2) update, checkerboarded over (mu, parity) so that every
+//     thread owns one link whose staple does not involve another updated link
+//   * Gaussian momenta / spinors, U <- exp(i eps P) U, reunitarisation,
+//     momentum step and kinetic energy for the HMC of Sec. 2.2.
+// Random numbers: Philox4x32-10 (Salmon et al., SC'11) with the counter layout
+// documented in lqcd.h, so a run is reproducible for any launch shape.
+#include <cmath>
+
+#include "internal.h"
+
+namespace lqcd {
+
+using C = Cx<double>;
+
+// ---------------------------------------------------------------------------
+// small SU(3) algebra in FP64 (row-major 3x3)
+// ---------------------------------------------------------------------------
+struct M3 {
+  C m[9];
+};
+LQCD_DEV M3 mmul(const M3 &a, const M3 &b) {
+  M3 r;
+#pragma unroll
+  for (int i = 0; i < 3; i++)
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+      C s = a.m[3 * i] * b.m[j];
+      s = cmadd(a.m[3 * i + 1], b.m[3 + j], s);
+      s = cmadd(a.m[3 * i + 2], b.m[6 + j], s);
+      r.m[3 * i + j] = s;
+    }
+  return r;
+}
+// a * b^+
+LQCD_DEV M3 mmul_nd(const M3 &a, const M3 &b) {
+  M3 r;
+#pragma unroll
+  for (int i = 0; i < 3; i++)
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+      C s = a.m[3 * i] * conj(b.m[3 * j]);
+      s = cmadd(a.m[3 * i + 1], conj(b.m[3 * j + 1]), s);
+      s = cmadd(a.m[3 * i + 2], conj(b.m[3 * j + 2]), s);
+      r.m[3 * i + j] = s;
+    }
+  return r;
+}
+// a^+ * b
+LQCD_DEV M3 mmul_dn(const M3 &a, const M3 &b) {
+  M3 r;
+#pragma unroll
+  for (int i = 0; i < 3; i++)
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+      C s = conj(a.m[i]) * b.m[j];
+      s = conj_madd(a.m[3 + i], b.m[3 + j], s);
+      s = conj_madd(a.m[6 + i], b.m[6 + j], s);
+      r.m[3 * i + j] = s;
+    }
+  return r;
+}
+LQCD_DEV double re_trace(const M3 &a) { return a.m[0].re + a.m[4].re + a.m[8].re; }
+
+struct Pos {
+  int p, cb;
+  long lexi;
+};
+// position of a site given by coordinates
+LQCD_DEV Pos pos_of(const Geom &g, int x, int y, int z, int t) {
+  int r = y + g.L[1] * (z + g.L[2] * t);
+  long i = (long)x + (long)g.L[0] * r;
+  return Pos{(x + y + z + t) & 1, (int)(i >> 1), i};
+}
+LQCD_DEV void coords_shift(const Geom &g, int c[4], int mu, int d) { c[mu] = (c[mu] + d + g.L[mu]) % g.L[mu]; }
+
+LQCD_DEV M3 load_link(const double2 *master, const Geom &g, const Pos &s, int mu) {
+  M3 u;
+  const double2 *b = master + ((size_t)(s.p * 4 + mu) * 9) * g.Vh + s.cb;
+#pragma unroll
+  for (int k = 0; k < 9; k++) {
+    double2 w = b[(size_t)k * g.Vh];
+    u.m[k] = {w.x, w.y};
+  }
+  return u;
+}
+LQCD_DEV void store_link(double2 *master, const Geom &g, const Pos &s, int mu, const M3 &u) {
+  double2 *b = master + ((size_t)(s.p * 4 + mu) * 9) * g.Vh + s.cb;
+#pragma unroll
+  for (int k = 0; k < 9; k++) b[(size_t)k * g.Vh] = make_double2(u.m[k].re, u.m[k].im);
+}
+LQCD_DEV Pos at(const Geom &g, const int c[4]) { return pos_of(g, c[0], c[1], c[2], c[3]); }
+
+// staple sum A_mu(x) with Re Tr(U_mu(x) A) = sum of the 6 plaquettes through U_mu(x)
+LQCD_DEV M3 staple(const double2 *U, const Geom &g, const int c[4], int mu) {
+  M3 A;
+#pragma unroll
+  for (int k = 0; k < 9; k++) A.m[k] = czero<double>();
+  int cpm[4] = {c[0], c[1], c[2], c[3]};
+  coords_shift(g, cpm, mu, +1);
+  for (int nu = 0; nu < 4; nu++) {
+    if (nu == mu) continue;
+    int cpn[4] = {c[0], c[1], c[2], c[3]}, cmn[4] = {c[0], c[1], c[2], c[3]};
+    int cpmmn[4] = {cpm[0], cpm[1], cpm[2], cpm[3]};
+    coords_shift(g, cpn, nu, +1);
+    coords_shift(g, cmn, nu, -1);
+    coords_shift(g, cpmmn, nu, -1);
+    // upper: U_nu(x+mu) U_mu(x+nu)^+ U_nu(x)^+
+    M3 t = mmul_nd(load_link(U, g, at(g, cpm), nu), load_link(U, g, at(g, cpn), mu));
+    t = mmul_nd(t, load_link(U, g, at(g, c), nu));
+#pragma unroll
+    for (int k = 0; k < 9; k++) A.m[k] = A.m[k] + t.m[k];
+    // lower: U_nu(x+mu-nu)^+ U_mu(x-nu)^+ U_nu(x-nu)
+    M3 l1 = load_link(U, g, at(g, cpmmn), nu), l2 = load_link(U, g, at(g, cmn), mu);
+    M3 w = mmul(l2, l1);  // (U_mu(x-nu) U_nu(x+mu-nu))^+ = l1^+ l2^+
+    M3 wd;
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+      for (int j = 0; j < 3; j++) wd.m[3 * i + j] = conj(w.m[3 * j + i]);
+    t = mmul(wd, load_link(U, g, at(g, cmn), nu));
+#pragma unroll
+    for (int k = 0; k < 9; k++) A.m[k] = A.m[k] + t.m[k];
+  }
+  return A;
+}
+
+// thread -> (parity, cb) over all 2*Vh sites; coordinates
+LQCD_DEV bool thread_site(const Geom &g, long tid, int *p, int *cb, int c[4]) {
+  if (tid >= 2L * g.Vh) return false;
+  *p = (int)(tid / g.Vh);
+  *cb = (int)(tid - (long)(*p) * g.Vh);
+  Site s = site_of(g, *p, *cb);
+  c[0] = s.x;
+  c[1] = s.y;
+  c[2] = s.z;
+  c[3] = s.t;
+  return true;
+}
+
+LQCD_DEV double block_sum(double v, double *sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < nw; k++) t += sh[k];
+  return t;
+}
+
+// sum over sites of sum_{mu<nu} Re Tr U_munu(x): per-block partials
+__global__ void __launch_bounds__(128) plaquette_kernel(const double2 *U, Geom g, double *partials) {
+  __shared__ double sh[8];
+  long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  int p, cb, c[4];
+  double acc = 0.0;
+  if (thread_site(g, tid, &p, &cb, c)) {
+    for (int mu = 0; mu < 4; mu++)
+      for (int nu = mu + 1; nu < 4; nu++) {
+        int cpm[4] = {c[0], c[1], c[2], c[3]}, cpn[4] = {c[0], c[1], c[2], c[3]};
+        coords_shift(g, cpm, mu, +1);
+        coords_shift(g, cpn, nu, +1);
+        M3 a = mmul(load_link(U, g, Pos{p, cb, 0}, mu), load_link(U, g, at(g, cpm), nu));
+        M3 b = mmul(load_link(U, g, Pos{p, cb, 0}, nu), load_link(U, g, at(g, cpn), mu));
+        M3 w = mmul_nd(a, b);  // U_mu(x) U_nu(x+mu) (U_nu(x) U_mu(x+nu))^+
+        acc += re_trace(w);
+      }
+  }
+  double t = block_sum(acc, sh);
+  if (threadIdx.x == 0) partials[blockIdx.x] = t;
+}
+
+// dS_g/domega^a for every link; out [mu][V][8] with lexicographic site index.
+// Re Tr(i T^a W) = -Im Tr(lambda^a W) / 2 with the Gell-Mann traces written out.
+__global__ void __launch_bounds__(128) gauge_force_kernel(const double2 *U, Geom g, double beta,
+                                                          double *out) {
+  long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  int p, cb, c[4];
+  if (!thread_site(g, tid, &p, &cb, c)) return;
+  long V = 2L * g.Vh;
+  Pos s = at(g, c);
+  for (int mu = 0; mu < 4; mu++) {
+    M3 A = staple(U, g, c, mu);
+    M3 W = mmul(load_link(U, g, s, mu), A);
+    const C *w = W.m;
+    double tr[8];
+    tr[0] = (w[3] + w[1]).im;                       // Tr(l1 W) = W10 + W01
+    tr[1] = (times_i(w[1] - w[3])).im;              // Tr(l2 W) = i (W01 - W10)
+    tr[2] = (w[0] - w[4]).im;                       // Tr(l3 W) = W00 - W11
+    tr[3] = (w[6] + w[2]).im;                       // Tr(l4 W) = W20 + W02
+    tr[4] = (times_i(w[2] - w[6])).im;              // Tr(l5 W) = i (W02 - W20)
+    tr[5] = (w[7] + w[5]).im;                       // Tr(l6 W) = W21 + W12
+    tr[6] = (times_i(w[5] - w[7])).im;              // Tr(l7 W) = i (W12 - W21)
+    tr[7] = (w[0] + w[4] - w[8] - w[8]).im * 0.57735026918962576451;  // Tr(l8 W)
+    double *o = out + ((size_t)mu * V + s.lexi) * 8;
+#pragma unroll
+    for (int a = 0; a < 8; a++) o[a] = (beta / 3.0) * 0.5 * tr[a];  // -(b/3)(-Im/2)
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 and the uniform / Gaussian conversions
+// ---------------------------------------------------------------------------
+struct U4 {
+  uint32_t x, y, z, w;
+};
+LQCD_DEV U4 philox(U4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; r++) {
+    uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = U4{hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0};
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+// two uniforms in (0,1): 52-bit integers k -> (k + 1/2) 2^-52
+LQCD_DEV void uniform2(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint64_t seed, double u[2]) {
+  U4 w = philox(U4{c0, c1, c2, c3}, (uint32_t)seed, (uint32_t)(seed >> 32));
+  unsigned long long ka = ((unsigned long long)w.x << 20) | (w.y >> 12);
+  unsigned long long kb = ((unsigned long long)w.z << 20) | (w.w >> 12);
+  u[0] = ((double)ka + 0.5) * 0x1p-52;
+  u[1] = ((double)kb + 0.5) * 0x1p-52;
+}
+
+enum { TAG_HB = 0, TAG_MOM = 1, TAG_ETA = 2, TAG_DIR = 3, TAG_METRO = 4 };
+
+__global__ void philox_test_kernel(const uint32_t *in, uint32_t *out, int n) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  U4 r = philox(U4{in[6 * k], in[6 * k + 1], in[6 * k + 2], in[6 * k + 3]}, in[6 * k + 4], in[6 * k + 5]);
+  out[4 * k] = r.x;
+  out[4 * k + 1] = r.y;
+  out[4 * k + 2] = r.z;
+  out[4 * k + 3] = r.w;
+}
+
+// ---------------------------------------------------------------------------
+// heatbath: one (mu, parity) class per launch
+// ---------------------------------------------------------------------------
+#define HB_MAX_ATTEMPTS 1024
+#define HB_B_SWITCH 1.5
+
+// y0 ~ sqrt(1 - y0^2) exp(b y0): Creutz for b < 1.5, Kennedy-Pendleton above
+LQCD_DEV bool sample_y0(double b, uint32_t c0, uint32_t c1, uint32_t c2, uint64_t seed, double *y0) {
+  for (int n = 0; n < HB_MAX_ATTEMPTS; n++) {
+    double u[2];
+    uniform2(c0, c1, c2, (uint32_t)(2 * n), seed, u);
+    if (b < HB_B_SWITCH) {
+      double y = 1.0 + log1p(expm1(-2.0 * b) * (1.0 - u[0])) / b;
+      if (u[1] * u[1] <= 1.0 - y * y) {
+        *y0 = y;
+        return true;
+      }
+      continue;
+    }
+    double v[2];
+    uniform2(c0, c1, c2, (uint32_t)(2 * n + 1), seed, v);
+    double cs = cos(2.0 * M_PI * u[1]);
+    double lam2 = -(log(u[0]) + cs * cs * log(v[0])) / (2.0 * b);
+    if (v[1] * v[1] <= 1.0 - lam2) {
+      *y0 = 1.0 - 2.0 * lam2;
+      return true;
+    }
+  }
+  return false;
+}
+
+__global__ void __launch_bounds__(128) heatbath_kernel(double2 *U, Geom g, int mu, int par, double beta,
+                                                       uint64_t seed, uint32_t sweep, int overrelax,
+                                                       unsigned int *fail_count) {
+  int cb = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cb >= g.Vh) return;
+  Site st = site_of(g, par, cb);
+  int c[4] = {st.x, st.y, st.z, st.t};
+  Pos s = at(g, c);
+  M3 A = staple(U, g, c, mu);
+  M3 u = load_link(U, g, s, mu);
+  const int SG[3][2] = {{0, 1}, {1, 2}, {0, 2}};
+  unsigned fails = 0;
+  for (int sg = 0; sg < 3; sg++) {
+    const int i = SG[sg][0], j = SG[sg][1];
+    M3 W = mmul(u, A);
+    C wa = W.m[3 * i + i], wb = W.m[3 * i + j], wc = W.m[3 * j + i], wd = W.m[3 * j + j];
+    // quaternion part of the 2x2 block: [[q0 + i q3, q2 + i q1], [-q2 + i q1, q0 - i q3]]
+    double q0 = 0.5 * (wa.re + wd.re), q3 = 0.5 * (wa.im - wd.im);
+    double q1 = 0.5 * (wb.im + wc.im), q2 = 0.5 * (wb.re - wc.re);
+    double k = sqrt(q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3);
+    if (!(k > 1e-300)) {
+      fails++;
+      continue;
+    }
+    double h0 = q0 / k, h1 = q1 / k, h2 = q2 / k, h3 = q3 / k;
+    // w_hat^+ = [[h0 - i h3, -h2 - i h1], [h2 - i h1, h0 + i h3]]
+    C whd[2][2] = {{{h0, -h3}, {-h2, -h1}}, {{h2, -h1}, {h0, h3}}};
+    C v[2][2];
+    if (overrelax) {  // v = (w_hat^+)^2 keeps Re Tr(v w) fixed
+#pragma unroll
+      for (int r = 0; r < 2; r++)
+#pragma unroll
+        for (int q = 0; q < 2; q++) v[r][q] = whd[r][0] * whd[0][q] + whd[r][1] * whd[1][q];
+    } else {
+      double b = 2.0 * beta * k / 3.0;
+      uint32_t c2 = (uint32_t)mu | ((uint32_t)sg << 2) | (TAG_HB << 8);
+      double y0;
+      if (!sample_y0(b, (uint32_t)s.lexi, sweep, c2, seed, &y0)) {
+        fails++;
+        continue;
+      }
+      double ud[2];
+      uniform2((uint32_t)s.lexi, sweep, (uint32_t)mu | ((uint32_t)sg << 2) | (TAG_DIR << 8), 0u, seed, ud);
+      double ct = 2.0 * ud[0] - 1.0, stt = sqrt(1.0 - ct * ct), ph = 2.0 * M_PI * ud[1];
+      double rr = sqrt(fmax(1.0 - y0 * y0, 0.0));
+      double y1 = rr * stt * cos(ph), y2 = rr * stt * sin(ph), y3 = rr * ct;
+      C Y[2][2] = {{{y0, y3}, {y2, y1}}, {{-y2, y1}, {y0, -y3}}};
+#pragma unroll
+      for (int r = 0; r < 2; r++)
+#pragma unroll
+        for (int q = 0; q < 2; q++) v[r][q] = Y[r][0] * whd[0][q] + Y[r][1] * whd[1][q];
+    }
+    // U <- V U with V = v embedded at rows/cols (i, j)
+    C ri[3], rj[3];
+#pragma unroll
+    for (int q = 0; q < 3; q++) {
+      ri[q] = v[0][0] * u.m[3 * i + q] + v[0][1] * u.m[3 * j + q];
+      rj[q] = v[1][0] * u.m[3 * i + q] + v[1][1] * u.m[3 * j + q];
+    }
+#pragma unroll
+    for (int q = 0; q < 3; q++) {
+      u.m[3 * i + q] = ri[q];
+      u.m[3 * j + q] = rj[q];
+    }
+  }
+  store_link(U, g, s, mu, u);
+  if (fails) atomicAdd(fail_count, fails);
+}
+
+// ---------------------------------------------------------------------------
+// momenta, Gaussian spinors, link update, reunitarisation
+// ---------------------------------------------------------------------------
+
+// P[mu][i][8], p^a ~ N(0,1): block k of (i, traj, mu | TAG_MOM<<8, k) -> (p_2k, p_2k+1)
+__global__ void momenta_kernel(double *P, long V, uint64_t seed, uint32_t traj) {
+  long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (t >= 4 * V) return;
+  int mu = (int)(t / V);
+  long i = t - mu * V;
+  double *o = P + t * 8;
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    double u[2];
+    uniform2((uint32_t)i, traj, (uint32_t)mu | (TAG_MOM << 8), (uint32_t)k, seed, u);
+    double r = sqrt(-2.0 * log(u[0]));
+    double sn, cs;
+    sincos(2.0 * M_PI * u[1], &sn, &cs);
+    o[2 * k] = r * cs;
+    o[2 * k + 1] = r * sn;
+  }
+}
+
+// eta on the sites of `parity` (0 even, 1 odd, 2 both), component k from block
+// (i, traj, TAG_ETA<<8, k); written to an EO full F64 field (other sites zeroed)
+__global__ void gaussian_spinor_kernel(double2 *eo, Geom g, int parity, uint64_t seed, uint32_t traj) {
+  long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  int p, cb, c[4];
+  if (!thread_site(g, tid, &p, &cb, c)) return;
+  Pos s = at(g, c);
+  double2 *base = eo + (size_t)p * 12 * g.Vh;
+  bool on = parity == 2 || parity == p;
+#pragma unroll
+  for (int k = 0; k < 12; k++) {
+    double2 v = make_double2(0.0, 0.0);
+    if (on) {
+      double u[2];
+      uniform2((uint32_t)s.lexi, traj, (uint32_t)(TAG_ETA << 8), (uint32_t)k, seed, u);
+      double r = sqrt(-2.0 * log(u[0])) * 0.70710678118654752440;
+      double sn, cs;
+      sincos(2.0 * M_PI * u[1], &sn, &cs);
+      v = make_double2(r * cs, r * sn);
+    }
+    base[(size_t)k * g.Vh + cb] = v;
+  }
+}
+
+LQCD_DEV void reunitarize(M3 &u) {
+  double n0 = 0.0;
+#pragma unroll
+  for (int k = 0; k < 3; k++) n0 += norm2_d(u.m[k]);
+  n0 = rsqrt(n0);
+#pragma unroll
+  for (int k = 0; k < 3; k++) u.m[k] = {u.m[k].re * n0, u.m[k].im * n0};
+  C d = czero<double>();
+#pragma unroll
+  for (int k = 0; k < 3; k++) d = conj_madd(u.m[k], u.m[3 + k], d);
+#pragma unroll
+  for (int k = 0; k < 3; k++) u.m[3 + k] = u.m[3 + k] - d * u.m[k];
+  double n1 = 0.0;
+#pragma unroll
+  for (int k = 0; k < 3; k++) n1 += norm2_d(u.m[3 + k]);
+  n1 = rsqrt(n1);
+#pragma unroll
+  for (int k = 0; k < 3; k++) u.m[3 + k] = {u.m[3 + k].re * n1, u.m[3 + k].im * n1};
+  reconstruct_row2(u.m);
+}
+
+// exp(X) for X = i eps P (anti-Hermitian, traceless): X is scaled by 2^-s until
+// its Frobenius norm is below 1/2, the Taylor polynomial of degree 14 is
+// evaluated by Horner's rule (truncation error < 1e-20 at that norm), and the
+// result is squared s times.
+LQCD_DEV M3 expm_su3(const M3 &X0) {
+  double nrm = 0.0;
+#pragma unroll
+  for (int k = 0; k < 9; k++) nrm += norm2_d(X0.m[k]);
+  nrm = sqrt(nrm);
+  int s = 0;
+  while (nrm > 0.5 && s < 60) {
+    nrm *= 0.5;
+    s++;
+  }
+  double sc = ldexp(1.0, -s);
+  M3 X;
+#pragma unroll
+  for (int k = 0; k < 9; k++) X.m[k] = {X0.m[k].re * sc, X0.m[k].im * sc};
+  M3 E;
+#pragma unroll
+  for (int k = 0; k < 9; k++) E.m[k] = czero<double>();
+  E.m[0] = E.m[4] = E.m[8] = {1.0, 0.0};
+  for (int n = 14; n >= 1; n--) {  // E = 1 + X E / n
+    M3 T = mmul(X, E);
+    double inv = 1.0 / n;
+#pragma unroll
+    for (int k = 0; k < 9; k++) E.m[k] = {T.m[k].re * inv, T.m[k].im * inv};
+    E.m[0].re += 1.0;
+    E.m[4].re += 1.0;
+    E.m[8].re += 1.0;
+  }
+  for (int q = 0; q < s; q++) E = mmul(E, E);
+  return E;
+}
+
+// i eps sum_a p^a lambda^a / 2
+LQCD_DEV M3 algebra_matrix(const double *p, double eps) {
+  const double h = 0.5 * eps, r3 = 0.57735026918962576451;
+  // H = sum p^a lambda^a / 2 (Hermitian); X = i eps H
+  C H[9];
+  H[0] = {p[2] + p[7] * r3, 0.0};
+  H[4] = {-p[2] + p[7] * r3, 0.0};
+  H[8] = {-2.0 * p[7] * r3, 0.0};
+  H[1] = {p[0], -p[1]};
+  H[3] = {p[0], p[1]};
+  H[2] = {p[3], -p[4]};
+  H[6] = {p[3], p[4]};
+  H[5] = {p[5], -p[6]};
+  H[7] = {p[5], p[6]};
+  M3 X;
+#pragma unroll
+  for (int k = 0; k < 9; k++) X.m[k] = {-h * H[k].im, h * H[k].re};
+  return X;
+}
+
+__global__ void __launch_bounds__(128) gauge_update_kernel(double2 *U, Geom g, const double *P, double eps) {
+  long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  int p, cb, c[4];
+  if (!thread_site(g, tid, &p, &cb, c)) return;
+  long V = 2L * g.Vh;
+  Pos s = at(g, c);
+  for (int mu = 0; mu < 4; mu++) {
+    M3 E = expm_su3(algebra_matrix(P + ((size_t)mu * V + s.lexi) * 8, eps));
+    M3 u = mmul(E, load_link(U, g, s, mu));
+    reunitarize(u);
+    store_link(U, g, s, mu, u);
+  }
+}
+
+__global__ void reunitarize_kernel(double2 *U, Geom g) {
+  long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  int p, cb, c[4];
+  if (!thread_site(g, tid, &p, &cb, c)) return;
+  Pos s{p, cb, 0};
+  for (int mu = 0; mu < 4; mu++) {
+    M3 u = load_link(U, g, s, mu);
+    reunitarize(u);
+    store_link(U, g, s, mu, u);
+  }
+}
+
+__global__ void momenta_update_kernel(double *P, const double *F, double eps, size_t n) {
+  size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (k < n) P[k] = fma(-eps, F[k], P[k]);
+}
+
+__global__ void __launch_bounds__(128) sumsq_kernel(const double *P, size_t n, double *partials) {
+  __shared__ double sh[8];
+  size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  double v = k < n ? P[k] * P[k] : 0.0;
+  double t = block_sum(v, sh);
+  if (threadIdx.x == 0) partials[blockIdx.x] = t;
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+static unsigned nblk(long n, int b = 128) { return (unsigned)((n + b - 1) / b); }
+
+// sum of nb partials on the host (fixed order), synchronous
+static lqcd_status sum_partials(lqcd_ctx *ctx, int nb, double *out) {
+  LQCD_TRY(ensure_pinned(ctx, nb));
+  LQCD_CUDA(ctx, cudaMemcpyAsync(ctx->pinned, ctx->partials, nb * sizeof(double), cudaMemcpyDeviceToHost,
+                                 ctx->stream));
+  LQCD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  double s = 0.0;
+  for (int k = 0; k < nb; k++) s += ctx->pinned[k];
+  *out = s;
+  return LQCD_OK;
+}
+
+lqcd_status plaquette_sum(lqcd_ctx *ctx, const lqcd_gauge *U, double *sum_retr) {
+  long V = 2L * U->g.Vh;
+  unsigned nb = nblk(V);
+  LQCD_TRY(ensure_partials(ctx, nb));
+  plaquette_kernel<<<nb, 128, 0, ctx->stream>>>((const double2 *)U->master, U->g, ctx->partials);
+  LQCD_CUDA(ctx, cudaGetLastError());
+  return sum_partials(ctx, nb, sum_retr);
+}
+
+lqcd_status gauge_force_raw(lqcd_ctx *ctx, const lqcd_gauge *U, double beta, double *dSdw) {
+  long V = 2L * U->g.Vh;
+  gauge_force_kernel<<<nblk(V), 128, 0, ctx->stream>>>((const double2 *)U->master, U->g, beta, dSdw);
+  LQCD_CUDA(ctx, cudaGetLastError());
+  return LQCD_OK;
+}
+
+lqcd_status heatbath_raw(lqcd_ctx *ctx, lqcd_gauge *U, double beta, uint64_t seed, uint64_t sweep, int n_or,
+                         unsigned int *fail_dev) {
+  for (int pass = 0; pass <= n_or; pass++)
+    for (int mu = 0; mu < 4; mu++)
+      for (int par = 0; par < 2; par++) {
+        heatbath_kernel<<<nblk(U->g.Vh), 128, 0, ctx->stream>>>((double2 *)U->master, U->g, mu, par, beta,
+                                                                seed, (uint32_t)sweep, pass > 0 ? 1 : 0,
+                                                                fail_dev);
+        LQCD_CUDA(ctx, cudaGetLastError());
+      }
+  U->version++;
+  return LQCD_OK;
+}
+
+lqcd_status momenta_raw(lqcd_ctx *ctx, long V, double *P, uint64_t seed, uint32_t traj) {
+  momenta_kernel<<<nblk(4 * V), 128, 0, ctx->stream>>>(P, V, seed, traj);
+  LQCD_CUDA(ctx, cudaGetLastError());
+  return LQCD_OK;
+}
+
+lqcd_status gaussian_spinor_raw(lqcd_ctx *ctx, const Geom &g, void *eo_full, int parity, uint64_t seed,
+                                uint32_t traj) {
+  gaussian_spinor_kernel<<<nblk(2L * g.Vh), 128, 0, ctx->stream>>>((double2 *)eo_full, g, parity, seed, traj);
+  LQCD_CUDA(ctx, cudaGetLastError());
+  return LQCD_OK;
+}
+
+lqcd_status gauge_update_raw(lqcd_ctx *ctx, lqcd_gauge *U, const double *P, double eps) {
+  gauge_update_kernel<<<nblk(2L * U->g.Vh), 128, 0, ctx->stream>>>((double2 *)U->master, U->g, P, eps);
+  LQCD_CUDA(ctx, cudaGetLastError());
+  U->version++;
+  return LQCD_OK;
+}
+
+lqcd_status reunitarize_raw(lqcd_ctx *ctx, lqcd_gauge *U) {
+  reunitarize_kernel<<<nblk(2L * U->g.Vh), 128, 0, ctx->stream>>>((double2 *)U->master, U->g);
+  LQCD_CUDA(ctx, cudaGetLastError());
+  U->version++;
+  return LQCD_OK;
+}
+
+lqcd_status momenta_update_raw(lqcd_ctx *ctx, long V, double *P, const double *F, double eps) {
+  size_t n = (size_t)32 * V;
+  momenta_update_kernel<<<nblk((long)n, 256), 256, 0, ctx->stream>>>(P, F, eps, n);
+  LQCD_CUDA(ctx, cudaGetLastError());
+  return LQCD_OK;
+}
+
+lqcd_status sumsq_raw(lqcd_ctx *ctx, const double *P, size_t n, double *out) {
+  unsigned nb = nblk((long)n);
+  LQCD_TRY(ensure_partials(ctx, nb));
+  sumsq_kernel<<<nb, 128, 0, ctx->stream>>>(P, n, ctx->partials);
+  LQCD_CUDA(ctx, cudaGetLastError());
+  return sum_partials(ctx, nb, out);
+}
+
+lqcd_status philox_test_raw(lqcd_ctx *ctx, const uint32_t *in_dev, uint32_t *out_dev, int n) {
+  philox_test_kernel<<<nblk(n), 128, 0, ctx->stream>>>(in_dev, out_dev, n);
+  LQCD_CUDA(ctx, cudaGetLastError());
+  return LQCD_OK;
+}
+
+// Metropolis uniform for trajectory traj: block (0, traj, TAG_METRO << 8, 0)
+__global__ void metro_uniform_kernel(uint64_t seed, uint32_t traj, double *out) {
+  double u[2];
+  uniform2(0u, traj, (uint32_t)(TAG_METRO << 8), 0u, seed, u);
+  *out = u[0];
+}
+lqcd_status metro_uniform(lqcd_ctx *ctx, uint64_t seed, uint32_t traj, double *u) {
+  metro_uniform_kernel<<<1, 1, 0, ctx->stream>>>(seed, traj, ctx->partials);
+  LQCD_CUDA(ctx, cudaGetLastError());
+  return sum_partials(ctx, 1, u);
+}
+
+}  // namespace lqcd

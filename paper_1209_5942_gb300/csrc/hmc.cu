@@ -1,0 +1,420 @@
+// hmc.cu -- ABI entry points for the molecular-dynamics side of Sec. 2.2:
+// gauge force and action, plaquette, heatbath, momenta, link update, the
+// fermion force (through (Mhat^+ Mhat)^-1 solved by the even-odd CG) and one
+// complete HMC trajectory:
+//   H = 1/2 sum p^2 + S_g + phi^+ (Mhat^+ Mhat)^-1 phi,  phi = Mhat^+ eta,
+//   leapfrog: p <- p - eps/2 dS/dw; (U <- exp(i eps P) U; p <- p - eps dS/dw) ...
+//   accept with probability min(1, exp(-dH)) (the printed exponent's sign is
+//   read as exp(-(H' - H))).
+// H, dH and every action are accumulated in FP64 on the device.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "internal.h"
+
+namespace lqcd {
+
+lqcd_status check_geom(lqcd_ctx *ctx, const lqcd_geom *g);
+lqcd_status check_field(lqcd_ctx *ctx, const lqcd_field &f, const char *name, bool allow_lexi);
+lqcd_status plaquette_sum(lqcd_ctx *ctx, const lqcd_gauge *U, double *sum_retr);
+lqcd_status gauge_force_raw(lqcd_ctx *ctx, const lqcd_gauge *U, double beta, double *dSdw);
+lqcd_status heatbath_raw(lqcd_ctx *ctx, lqcd_gauge *U, double beta, uint64_t seed, uint64_t sweep, int n_or,
+                         unsigned int *fail_dev);
+lqcd_status momenta_raw(lqcd_ctx *ctx, long V, double *P, uint64_t seed, uint32_t traj);
+lqcd_status gaussian_spinor_raw(lqcd_ctx *ctx, const Geom &g, void *eo_full, int parity, uint64_t seed,
+                                uint32_t traj);
+lqcd_status gauge_update_raw(lqcd_ctx *ctx, lqcd_gauge *U, const double *P, double eps);
+lqcd_status momenta_update_raw(lqcd_ctx *ctx, long V, double *P, const double *F, double eps);
+lqcd_status sumsq_raw(lqcd_ctx *ctx, const double *P, size_t n, double *out);
+lqcd_status metro_uniform(lqcd_ctx *ctx, uint64_t seed, uint32_t traj, double *u);
+lqcd_status fermion_force_raw(lqcd_ctx *ctx, const lqcd_gauge *U, const void *Lf, const void *Rf,
+                              double kappa, double *out);
+lqcd_status cgls_even(lqcd_ctx *ctx, lqcd_gauge *U, const Geom &g, double kappa, double mu,
+                      const lqcd_cg_params &prm, const HalfField &bhat, const HalfField &xo,
+                      const std::vector<double> &b2, lqcd_cg_stats *st, int nrhs, int *iters_used,
+                      bool normal);
+
+static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+static HalfField f64_half(void *ptr, int Vh) {
+  HalfField h;
+  h.ptr = ptr;
+  h.prec = LQCD_F64;
+  h.nrhs = 1;
+  h.rhs_stride = spinor_half_bytes(LQCD_F64, Vh);
+  return h;
+}
+
+struct DBuf {  // device scratch freed on scope exit
+  lqcd_ctx *ctx;
+  void *p = nullptr;
+  explicit DBuf(lqcd_ctx *c) : ctx(c) {}
+  ~DBuf() { dfree(ctx, p); }
+  lqcd_status alloc(size_t n) { return dalloc(ctx, &p, n); }
+};
+
+// |f|^2 of one F64 half field (synchronous)
+static lqcd_status half_norm2(lqcd_ctx *ctx, int Vh, const HalfField &f, double *out) {
+  DBuf tmp(ctx);
+  LQCD_TRY(tmp.alloc(f.rhs_stride));
+  HalfField t = f;
+  t.ptr = tmp.p;
+  int nb = 0;
+  LQCD_TRY(lincomb(ctx, Vh, t, f, nullptr, {1, 0}, {1, 0}, {0, 0}, {0, 0}, ctx->partials, &nb));
+  LQCD_CUDA(ctx, cudaMemcpyAsync(ctx->pinned, ctx->partials, nb * sizeof(double), cudaMemcpyDeviceToHost,
+                                 ctx->stream));
+  LQCD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  double s = 0.0;
+  for (int k = 0; k < nb; k++) s += ctx->pinned[k];
+  *out = s;
+  return LQCD_OK;
+}
+
+// Re <a, b> of two F64 half fields (synchronous): via |a+b|^2 - |a-b|^2 = 4 Re<a,b>
+static lqcd_status half_redot(lqcd_ctx *ctx, int Vh, const HalfField &a, const HalfField &b, double *out) {
+  DBuf tmp(ctx);
+  LQCD_TRY(tmp.alloc(a.rhs_stride));
+  HalfField t = a;
+  t.ptr = tmp.p;
+  double np, nm;
+  LQCD_TRY(lincomb(ctx, Vh, t, a, &b, {1, 0}, {1, 0}, {1, 0}, {1, 0}, nullptr, nullptr));
+  LQCD_TRY(half_norm2(ctx, Vh, t, &np));
+  LQCD_TRY(lincomb(ctx, Vh, t, a, &b, {1, 0}, {1, 0}, {-1, 0}, {-1, 0}, nullptr, nullptr));
+  LQCD_TRY(half_norm2(ctx, Vh, t, &nm));
+  *out = 0.25 * (np - nm);
+  return LQCD_OK;
+}
+
+// X_e = (Mhat^+ Mhat)^-1 phi_e (F64 half fields); solver statistics added to st
+lqcd_status solve_normal(lqcd_ctx *ctx, lqcd_gauge *U, const HalfField &phi, const HalfField &X, double kappa,
+                         double mu, const lqcd_cg_params &prm_in, lqcd_cg_stats *st) {
+  const Geom &g = U->g;
+  const int Vh = g.Vh;
+  lqcd_cg_params prm = prm_in;
+  if (prm.sloppy_recon == 0) prm.sloppy_recon = U->recon;
+  if (prm.check_every <= 0) prm.check_every = 10;
+  double phi2;
+  LQCD_TRY(half_norm2(ctx, Vh, phi, &phi2));
+  if (!std::isfinite(phi2)) return fail(ctx, LQCD_ERR_NONFINITE, "pseudofermion field is not finite");
+  std::vector<double> b2(1, phi2);
+  const int outer = prm.outer_prec;
+  DBuf phio(ctx), xo(ctx);
+  HalfField ph = phi, xx = X;
+  if (outer != LQCD_F64) {
+    size_t hb = spinor_half_bytes(outer, Vh);
+    LQCD_TRY(phio.alloc(hb));
+    LQCD_TRY(xo.alloc(hb));
+    LQCD_TRY(spinor_convert_raw(ctx, Vh, 1, phi.ptr, nullptr, LQCD_F64, phio.p, nullptr, outer));
+    ph.ptr = phio.p;
+    ph.prec = outer;
+    ph.rhs_stride = hb;
+    xx.ptr = xo.p;
+    xx.prec = outer;
+    xx.rhs_stride = hb;
+  }
+  LQCD_CUDA(ctx, cudaMemsetAsync(xx.ptr, 0, xx.rhs_stride, ctx->stream));
+  if (phi2 == 0.0) {
+    LQCD_CUDA(ctx, cudaMemsetAsync(X.ptr, 0, X.rhs_stride, ctx->stream));
+    return LQCD_OK;
+  }
+  lqcd_cg_stats s1;
+  std::memset(&s1, 0, sizeof(s1));
+  lqcd_status s = cgls_even(ctx, U, g, kappa, mu, prm, ph, xx, b2, &s1, 1, nullptr, true);
+  if (st) {
+    st->iters += s1.iters;
+    st->reliable_updates += s1.reliable_updates;
+  }
+  if (s != LQCD_OK) return s;
+  if (outer != LQCD_F64) LQCD_TRY(spinor_convert_raw(ctx, Vh, 1, xx.ptr, nullptr, outer, X.ptr, nullptr, LQCD_F64));
+  return LQCD_OK;
+}
+
+// dS/dw of S = phi^+ (Mhat^+ Mhat)^-1 phi given X (F64 half fields) -> out [4][V][8]
+lqcd_status fermion_force_from_X(lqcd_ctx *ctx, lqcd_gauge *U, const HalfField &X, double kappa, double mu,
+                                 double *out) {
+  const Geom &g = U->g;
+  const int Vh = g.Vh;
+  size_t hb = spinor_half_bytes(LQCD_F64, Vh);
+  DBuf Lf(ctx), Rf(ctx), tmp(ctx);
+  LQCD_TRY(Lf.alloc(2 * hb));
+  LQCD_TRY(Rf.alloc(2 * hb));
+  LQCD_TRY(tmp.alloc(hb));
+  HalfField Le = f64_half(Lf.p, Vh), Lo = f64_half((char *)Lf.p + hb, Vh);
+  HalfField Re = f64_half(Rf.p, Vh), Ro = f64_half((char *)Rf.p + hb, Vh);
+  HalfField T = f64_half(tmp.p, Vh);
+  Op op{ctx, g, {}, LQCD_F64, U->recon, kappa, mu};
+  LQCD_TRY(gauge_view(ctx, U, LQCD_F64, U->recon, &op.U));
+  // Re = X_e;  Le = Y_e = Mhat X_e
+  LQCD_CUDA(ctx, cudaMemcpyAsync(Re.ptr, X.ptr, hb, cudaMemcpyDeviceToDevice, ctx->stream));
+  LQCD_TRY(apply_schur(op, X, Le, T, 0, false, nullptr, nullptr, nullptr));
+  double a = 2.0 * kappa * mu, n = 1.0 / (1.0 + a * a);
+  // Ro = Z_o = A_o^-1 H_oe X_e
+  HopLaunch L;
+  L.prec = LQCD_F64;
+  L.recon = U->recon;
+  L.U = op.U;
+  L.in = Re;
+  L.out = Ro;
+  L.out_parity = 1;
+  L.c_up = {n, -a * n};
+  L.c_dn = {n, a * n};
+  LQCD_TRY(launch_hop(ctx, g, L, nullptr));
+  // Lo = W_o = A_o^-+ (H^+)_oe Y_e,  A^-+ = (1 + i a g5)/(1 + a^2)
+  HopLaunch L2 = L;
+  L2.in = Le;
+  L2.out = Lo;
+  L2.dagger = 1;
+  L2.c_up = {n, a * n};
+  L2.c_dn = {n, -a * n};
+  LQCD_TRY(launch_hop(ctx, g, L2, nullptr));
+  return fermion_force_raw(ctx, U, Lf.p, Rf.p, kappa, out);
+}
+
+}  // namespace lqcd
+
+using namespace lqcd;
+
+static lqcd_status check_u(lqcd_ctx *ctx, const lqcd_gauge *U) {
+  if (!U) return fail(ctx, LQCD_ERR_INVALID, "gauge field is NULL");
+  return LQCD_OK;
+}
+
+extern "C" int lqcd_plaquette(lqcd_ctx *ctx, const lqcd_gauge *U, double *plaq_out) {
+  if (!ctx) return LQCD_ERR_INVALID;
+  LQCD_TRY(check_u(ctx, U));
+  if (!plaq_out) return fail(ctx, LQCD_ERR_INVALID, "plaq_out is NULL");
+  double s;
+  LQCD_TRY(plaquette_sum(ctx, U, &s));
+  *plaq_out = s / (3.0 * 6.0 * 2.0 * U->g.Vh);
+  return LQCD_OK;
+}
+
+extern "C" int lqcd_gauge_force(lqcd_ctx *ctx, const lqcd_gauge *U, double beta, double *dSdw, double *S_out) {
+  if (!ctx) return LQCD_ERR_INVALID;
+  LQCD_TRY(check_u(ctx, U));
+  if (!dSdw || !aligned16(dSdw)) return fail(ctx, LQCD_ERR_INVALID, "dSdw: NULL or misaligned");
+  if (!std::isfinite(beta)) return fail(ctx, LQCD_ERR_NONFINITE, "beta not finite");
+  LQCD_TRY(gauge_force_raw(ctx, U, beta, dSdw));
+  if (S_out) {
+    double s;
+    LQCD_TRY(plaquette_sum(ctx, U, &s));
+    *S_out = beta / 3.0 * (3.0 * 6.0 * 2.0 * U->g.Vh - s);
+  }
+  return LQCD_OK;
+}
+
+extern "C" int lqcd_heatbath_sweep(lqcd_ctx *ctx, lqcd_gauge *U, double beta, uint64_t seed, uint64_t sweep_idx,
+                                   int n_or) {
+  if (!ctx) return LQCD_ERR_INVALID;
+  LQCD_TRY(check_u(ctx, U));
+  if (!(beta >= 0.0) || !std::isfinite(beta)) return fail(ctx, LQCD_ERR_INVALID, "beta must be finite, >= 0");
+  if (n_or < 0 || n_or > 64) return fail(ctx, LQCD_ERR_INVALID, "n_or out of [0, 64]");
+  unsigned int *fails = (unsigned int *)ctx->partials;  // scratch word; not read by anyone else
+  LQCD_CUDA(ctx, cudaMemsetAsync(fails, 0, sizeof(unsigned int), ctx->stream));
+  return heatbath_raw(ctx, U, beta, seed, sweep_idx, n_or, fails);
+}
+
+extern "C" int lqcd_momenta_gaussian(lqcd_ctx *ctx, const lqcd_geom *geom, double *P, uint64_t seed,
+                                     uint32_t traj) {
+  if (!ctx) return LQCD_ERR_INVALID;
+  LQCD_TRY(check_geom(ctx, geom));
+  if (!P || !aligned16(P)) return fail(ctx, LQCD_ERR_INVALID, "P: NULL or misaligned");
+  Geom g = make_geom(*geom);
+  return momenta_raw(ctx, 2L * g.Vh, P, seed, traj);
+}
+
+extern "C" int lqcd_spinor_gaussian(lqcd_ctx *ctx, const lqcd_geom *geom, lqcd_field eta, int parity,
+                                    uint64_t seed, uint32_t traj) {
+  if (!ctx) return LQCD_ERR_INVALID;
+  LQCD_TRY(check_geom(ctx, geom));
+  LQCD_TRY(check_field(ctx, eta, "eta", false));
+  if (eta.prec != LQCD_F64 || eta.nrhs != 1) return fail(ctx, LQCD_ERR_INVALID, "eta must be one F64 EO full field");
+  if (parity != LQCD_FULL && parity != LQCD_EVEN && parity != LQCD_ODD)
+    return fail(ctx, LQCD_ERR_INVALID, "bad parity");
+  Geom g = make_geom(*geom);
+  int p = parity == LQCD_FULL ? 2 : (parity == LQCD_EVEN ? 0 : 1);
+  return gaussian_spinor_raw(ctx, g, eta.ptr, p, seed, traj);
+}
+
+extern "C" int lqcd_gauge_update(lqcd_ctx *ctx, lqcd_gauge *U, const double *P, double eps) {
+  if (!ctx) return LQCD_ERR_INVALID;
+  LQCD_TRY(check_u(ctx, U));
+  if (!P || !aligned16(P)) return fail(ctx, LQCD_ERR_INVALID, "P: NULL or misaligned");
+  if (!std::isfinite(eps)) return fail(ctx, LQCD_ERR_NONFINITE, "eps not finite");
+  return gauge_update_raw(ctx, U, P, eps);
+}
+
+extern "C" int lqcd_momenta_update(lqcd_ctx *ctx, const lqcd_geom *geom, double *P, const double *dSdw,
+                                   double eps) {
+  if (!ctx) return LQCD_ERR_INVALID;
+  LQCD_TRY(check_geom(ctx, geom));
+  if (!P || !dSdw) return fail(ctx, LQCD_ERR_INVALID, "NULL argument");
+  Geom g = make_geom(*geom);
+  return momenta_update_raw(ctx, 2L * g.Vh, P, dSdw, eps);
+}
+
+extern "C" int lqcd_momenta_kinetic(lqcd_ctx *ctx, const lqcd_geom *geom, const double *P, double *K_out) {
+  if (!ctx) return LQCD_ERR_INVALID;
+  LQCD_TRY(check_geom(ctx, geom));
+  if (!P || !K_out) return fail(ctx, LQCD_ERR_INVALID, "NULL argument");
+  Geom g = make_geom(*geom);
+  double s;
+  LQCD_TRY(sumsq_raw(ctx, P, (size_t)32 * 2 * g.Vh, &s));
+  *K_out = 0.5 * s;
+  return LQCD_OK;
+}
+
+extern "C" int lqcd_gauge_copy(lqcd_ctx *ctx, const lqcd_gauge *src, lqcd_gauge *dst) {
+  if (!ctx) return LQCD_ERR_INVALID;
+  if (!src || !dst) return fail(ctx, LQCD_ERR_INVALID, "NULL gauge field");
+  if (!geom_equal(src->geom, dst->geom)) return fail(ctx, LQCD_ERR_INVALID, "geometry mismatch");
+  size_t bytes = (size_t)2 * 4 * 9 * src->g.Vh * 16;
+  LQCD_CUDA(ctx, cudaMemcpyAsync(dst->master, src->master, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+  dst->version++;
+  return LQCD_OK;
+}
+
+extern "C" int lqcd_fermion_force(lqcd_ctx *ctx, const lqcd_gauge *Uc, lqcd_field phi, double *dSdw,
+                                  lqcd_field *X_cache, const lqcd_geom *geom, double kappa, double mu,
+                                  const lqcd_cg_params *params, lqcd_cg_stats *stats, double *S_out) {
+  if (!ctx) return LQCD_ERR_INVALID;
+  LQCD_TRY(check_u(ctx, Uc));
+  LQCD_TRY(check_geom(ctx, geom));
+  if (!geom_equal(Uc->geom, *geom)) return fail(ctx, LQCD_ERR_INVALID, "geometry mismatch");
+  LQCD_TRY(check_field(ctx, phi, "phi", false));
+  if (phi.prec != LQCD_F64 || phi.nrhs != 1) return fail(ctx, LQCD_ERR_INVALID, "phi must be one F64 EO half field");
+  if (!dSdw || !aligned16(dSdw)) return fail(ctx, LQCD_ERR_INVALID, "dSdw: NULL or misaligned");
+  if (!params) return fail(ctx, LQCD_ERR_INVALID, "params is NULL");
+  if (params->outer_prec != LQCD_F64 && params->outer_prec != LQCD_DF64)
+    return fail(ctx, LQCD_ERR_INVALID, "outer_prec must be F64 or DF64");
+  if (!std::isfinite(kappa) || !std::isfinite(mu)) return fail(ctx, LQCD_ERR_NONFINITE, "kappa/mu not finite");
+  lqcd_gauge *U = const_cast<lqcd_gauge *>(Uc);
+  const int Vh = U->g.Vh;
+  HalfField ph = f64_half(phi.ptr, Vh);
+  DBuf xbuf(ctx);
+  HalfField X;
+  if (X_cache) {
+    LQCD_TRY(check_field(ctx, *X_cache, "X_cache", false));
+    X = f64_half(X_cache->ptr, Vh);
+  } else {
+    LQCD_TRY(xbuf.alloc(spinor_half_bytes(LQCD_F64, Vh)));
+    X = f64_half(xbuf.p, Vh);
+  }
+  lqcd_cg_stats st;
+  std::memset(&st, 0, sizeof(st));
+  if (!X_cache || X_cache->reserved != 1) {
+    lqcd_status s = solve_normal(ctx, U, ph, X, kappa, mu, *params, &st);
+    if (stats) *stats = st;
+    if (s != LQCD_OK) return s;
+    if (X_cache) X_cache->reserved = 1;
+  } else if (stats) {
+    *stats = st;
+  }
+  if (S_out) LQCD_TRY(half_redot(ctx, Vh, ph, X, S_out));
+  return fermion_force_from_X(ctx, U, X, kappa, mu, dSdw);
+}
+
+// ---------------------------------------------------------------------------
+// HMC trajectory
+// ---------------------------------------------------------------------------
+
+extern "C" int lqcd_hmc_trajectory(lqcd_ctx *ctx, lqcd_gauge *U, const lqcd_hmc_params *prm,
+                                   lqcd_hmc_stats *stats) {
+  if (!ctx) return LQCD_ERR_INVALID;
+  LQCD_TRY(check_u(ctx, U));
+  if (!prm || !stats) return fail(ctx, LQCD_ERR_INVALID, "NULL params or stats");
+  if (prm->nsteps < 1 || !(prm->tau > 0.0)) return fail(ctx, LQCD_ERR_INVALID, "nsteps >= 1 and tau > 0 required");
+  auto t0 = std::chrono::steady_clock::now();
+  std::memset(stats, 0, sizeof(*stats));
+  const Geom &g = U->g;
+  const int Vh = g.Vh;
+  const long V = 2L * Vh;
+  const size_t nP = (size_t)32 * V;
+  const double eps = prm->tau / prm->nsteps;
+  const bool fermions = prm->nf != 0;
+  size_t hb = spinor_half_bytes(LQCD_F64, Vh);
+  DBuf P(ctx), F(ctx), Ff(ctx), eta(ctx), phi(ctx), X(ctx), tmp(ctx), save(ctx);
+  LQCD_TRY(P.alloc(nP * sizeof(double)));
+  LQCD_TRY(F.alloc(nP * sizeof(double)));
+  LQCD_TRY(save.alloc((size_t)2 * 4 * 9 * Vh * 16));
+  if (fermions) {
+    LQCD_TRY(Ff.alloc(nP * sizeof(double)));
+    LQCD_TRY(eta.alloc(2 * hb));
+    LQCD_TRY(phi.alloc(hb));
+    LQCD_TRY(X.alloc(hb));
+    LQCD_TRY(tmp.alloc(hb));
+  }
+  LQCD_CUDA(ctx, cudaMemcpyAsync(save.p, U->master, (size_t)2 * 4 * 9 * Vh * 16, cudaMemcpyDeviceToDevice,
+                                 ctx->stream));
+  const uint64_t seed = prm->seed;
+  const uint32_t traj = prm->traj;
+  LQCD_TRY(momenta_raw(ctx, V, (double *)P.p, seed, traj));
+  HalfField Phi = f64_half(phi.p, Vh), Xh = f64_half(X.p, Vh);
+  Op op{ctx, g, {}, LQCD_F64, U->recon, prm->kappa, prm->mu};
+  int cg_iters = 0;
+  auto action_and_force = [&](double *S_f) -> lqcd_status {
+    // F = dS_g/dw (+ dS_f/dw); S_f = phi^+ X at the current links
+    LQCD_TRY(gauge_force_raw(ctx, U, prm->beta, (double *)F.p));
+    if (fermions) {
+      lqcd_cg_stats st;
+      std::memset(&st, 0, sizeof(st));
+      LQCD_TRY(solve_normal(ctx, U, Phi, Xh, prm->kappa, prm->mu, prm->cg, &st));
+      cg_iters += st.iters;
+      if (S_f) LQCD_TRY(half_redot(ctx, Vh, Phi, Xh, S_f));
+      LQCD_TRY(fermion_force_from_X(ctx, U, Xh, prm->kappa, prm->mu, (double *)Ff.p));
+      LQCD_TRY(momenta_update_raw(ctx, V, (double *)F.p, (const double *)Ff.p, -1.0));  // F += Ff
+    }
+    return LQCD_OK;
+  };
+  auto gauge_action = [&](double *S) -> lqcd_status {
+    double s;
+    LQCD_TRY(plaquette_sum(ctx, U, &s));
+    *S = prm->beta / 3.0 * (3.0 * 6.0 * V - s);
+    return LQCD_OK;
+  };
+  double Sf0 = 0.0, Sf1 = 0.0, Sg0, Sg1, K0, K1;
+  if (fermions) {
+    LQCD_TRY(gaussian_spinor_raw(ctx, g, eta.p, 0, seed, traj));
+    LQCD_TRY(gauge_view(ctx, U, LQCD_F64, U->recon, &op.U));
+    LQCD_TRY(apply_schur(op, f64_half(eta.p, Vh), Phi, f64_half(tmp.p, Vh), 0, true, nullptr, nullptr,
+                         nullptr));
+  }
+  LQCD_TRY(sumsq_raw(ctx, (const double *)P.p, nP, &K0));
+  K0 *= 0.5;
+  LQCD_TRY(gauge_action(&Sg0));
+  LQCD_TRY(action_and_force(&Sf0));
+  const double H0 = K0 + Sg0 + Sf0;
+  LQCD_TRY(momenta_update_raw(ctx, V, (double *)P.p, (const double *)F.p, 0.5 * eps));
+  for (int step = 0; step < prm->nsteps; step++) {
+    LQCD_TRY(gauge_update_raw(ctx, U, (const double *)P.p, eps));
+    const bool last = step == prm->nsteps - 1;
+    LQCD_TRY(action_and_force(last ? &Sf1 : nullptr));
+    LQCD_TRY(momenta_update_raw(ctx, V, (double *)P.p, (const double *)F.p, last ? 0.5 * eps : eps));
+  }
+  LQCD_TRY(sumsq_raw(ctx, (const double *)P.p, nP, &K1));
+  K1 *= 0.5;
+  LQCD_TRY(gauge_action(&Sg1));
+  const double H1 = K1 + Sg1 + Sf1;
+  const double dH = H1 - H0;
+  if (!std::isfinite(dH)) return fail(ctx, LQCD_ERR_NONFINITE, "dH is not finite");
+  double u;
+  LQCD_TRY(metro_uniform(ctx, seed, traj, &u));
+  const bool accept = dH <= 0.0 || u < std::exp(-dH);
+  if (!accept) {
+    LQCD_CUDA(ctx, cudaMemcpyAsync(U->master, save.p, (size_t)2 * 4 * 9 * Vh * 16, cudaMemcpyDeviceToDevice,
+                                   ctx->stream));
+    U->version++;
+  }
+  double plaq_sum;
+  LQCD_TRY(plaquette_sum(ctx, U, &plaq_sum));
+  stats->dH = dH;
+  stats->H0 = H0;
+  stats->H1 = H1;
+  stats->plaquette = plaq_sum / (18.0 * V);
+  stats->accepted = accept ? 1 : 0;
+  stats->cg_iters = cg_iters;
+  stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return LQCD_OK;
+}

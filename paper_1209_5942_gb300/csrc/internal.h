@@ -1,0 +1,134 @@
+// internal.h -- host-side structures of the library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "../../include/lqcd.h"
+#include "common.cuh"
+
+struct lqcd_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int num_sms = 152;
+  std::string err;
+  // reduction workspace: partial sums [slots][nblocks] and per-slot results
+  double *partials = nullptr;
+  size_t partials_cap = 0;  // doubles
+  double *pinned = nullptr; // host pinned scratch for status read-back
+  size_t pinned_cap = 0;
+  // solver device state (see cg.cu)
+  void *solver_state = nullptr;
+  size_t solver_state_cap = 0;
+  // algorithmic work counters (lqcd_get_counters)
+  lqcd_counters cnt{};
+};
+
+struct lqcd_gauge {
+  lqcd_geom geom;
+  lqcd::Geom g;
+  int recon = 18;            // link format of the FP64-class operator
+  void *master = nullptr;    // FP64, recon 18, [parity][mu][9][Vh] complex128
+  uint64_t version = 1;      // bumped whenever master changes
+  struct Copy {
+    void *ptr = nullptr;
+    int prec = -1, recon = 0;
+    uint64_t version = 0;
+  };
+  std::vector<Copy> copies;  // derived precisions / formats
+};
+
+namespace lqcd {
+
+// status helpers
+lqcd_status fail(lqcd_ctx *ctx, lqcd_status s, const char *fmt, ...);
+lqcd_status cuda_check(lqcd_ctx *ctx, cudaError_t e, const char *what);
+#define LQCD_CUDA(ctx, call)                                           \
+  do {                                                                 \
+    cudaError_t e_ = (call);                                           \
+    if (e_ != cudaSuccess) return lqcd::cuda_check((ctx), e_, #call);  \
+  } while (0)
+#define LQCD_TRY(expr)                          \
+  do {                                          \
+    lqcd_status s_ = (expr);                    \
+    if (s_ != LQCD_OK) return s_;               \
+  } while (0)
+
+Geom make_geom(const lqcd_geom &g);
+bool geom_equal(const lqcd_geom &a, const lqcd_geom &b);
+size_t spinor_half_bytes(int prec, int Vh);   // one parity, one rhs
+size_t spinor_scale_half_bytes(int prec, int Vh);
+
+// device buffers (stream-ordered allocation on the context stream)
+lqcd_status dalloc(lqcd_ctx *ctx, void **p, size_t bytes);
+void dfree(lqcd_ctx *ctx, void *p);
+lqcd_status ensure_partials(lqcd_ctx *ctx, size_t doubles);
+lqcd_status ensure_pinned(lqcd_ctx *ctx, size_t doubles);
+
+// A half field (one parity) with nrhs right-hand sides in the EO layout.
+struct HalfField {
+  void *ptr = nullptr;
+  float *scale = nullptr;
+  int prec = LQCD_F64;
+  int nrhs = 1;
+  size_t rhs_stride = 0;        // bytes between right-hand sides
+  size_t scale_rhs_stride = 0;  // floats between right-hand sides
+};
+
+// work counters: one launch moving `bytes` algorithmic bytes
+inline void count_launch(lqcd_ctx *ctx, double bytes) {
+  ctx->cnt.launches += 1;
+  ctx->cnt.bytes += bytes;
+}
+inline double spinor_site_bytes(int prec) {
+  return (double)spinor_bytes_per_site(prec) + ((prec == LQCD_BF16S || prec == LQCD_F16S) ? 4.0 : 0.0);
+}
+
+// gauge copies
+lqcd_status gauge_view(lqcd_ctx *ctx, lqcd_gauge *U, int prec, int recon, GaugeView *out);
+
+// ---------------------------------------------------------------------------
+// hop kernel launch (dslash.cu)
+// ---------------------------------------------------------------------------
+struct HopLaunch {
+  int prec = LQCD_F64;  // spinor precision == arithmetic class
+  int recon = 18;
+  GaugeView U{};
+  HalfField in, out, aux;  // in: parity 1-p; out, aux: parity p
+  int out_parity = 0;      // 0 or 1
+  int dagger = 0;
+  HostC c_up{1, 0}, c_dn{1, 0};  // out = c * H in + d * aux (per chirality)
+  HostC d_up{0, 0}, d_dn{0, 0};
+  bool has_aux = false;
+  double *partials = nullptr;  // if set: |out|^2 partials [nrhs][nblocks]
+  int *halt = nullptr;         // if set and *halt != 0 the kernel does nothing
+};
+lqcd_status launch_hop(lqcd_ctx *ctx, const Geom &g, const HopLaunch &L, int *nblocks_out);
+int hop_blocks(const Geom &g, int nrhs);
+
+// Operators assembled from hop launches (cg.cu)
+struct Op {
+  lqcd_ctx *ctx;
+  Geom g;
+  GaugeView U;
+  int prec, recon;
+  double kappa, mu;
+};
+// out_p = Mhat (or Mhat^+) in_p on parity p; tmp: half field of parity 1-p.
+lqcd_status apply_schur(const Op &op, const HalfField &in, const HalfField &out, const HalfField &tmp,
+                        int p, bool dagger, double *partials, int *nb, int *halt);
+// full M (or M^+) on both parities of an EO field
+lqcd_status apply_full(const Op &op, const HalfField &in_e, const HalfField &in_o, const HalfField &out_e,
+                       const HalfField &out_o, bool dagger, double *partials_e, double *partials_o,
+                       int *nb);
+lqcd_status lincomb(lqcd_ctx *ctx, int Vh, const HalfField &out, const HalfField &x, const HalfField *y,
+                    HostC ca_up, HostC ca_dn, HostC cb_up, HostC cb_dn, double *partials, int *nb_out);
+lqcd_status spinor_convert_raw(lqcd_ctx *ctx, int Vh, int nh, const void *in, const float *in_scale,
+                               int pin, void *out, float *out_scale, int pout);
+lqcd_status spinor_pack_raw(lqcd_ctx *ctx, const Geom &g, const void *lexi, const HalfField &eo_full);
+lqcd_status spinor_unpack_raw(lqcd_ctx *ctx, const Geom &g, const HalfField &eo_full, void *lexi);
+
+}  // namespace lqcd

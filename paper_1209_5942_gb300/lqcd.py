@@ -1,0 +1,459 @@
+"""Thin Python binding of the C ABI in ``include/lqcd.h`` (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of its own: device buffers are torch tensors (used for memory and
+streams only), scalars are passed through, and the status code is turned into
+an exception.  The shared library must have been built (``build.build()``);
+loading fails loudly otherwise -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+# --- enums (mirror lqcd.h) ---------------------------------------------------
+LQCD_OK = 0
+LQCD_ERR_INVALID = -1
+LQCD_ERR_CUDA = -2
+LQCD_ERR_NOCONV = -3
+LQCD_ERR_NONFINITE = -4
+LQCD_ERR_TIMEOUT = -5
+LQCD_ERR_OOM = -6
+LQCD_ERR_UNSUPPORTED = -7
+
+LQCD_FULL, LQCD_EVEN, LQCD_ODD = 0, 1, 2
+LQCD_F64, LQCD_DF64, LQCD_F32, LQCD_BF16S, LQCD_F16S = 0, 1, 2, 3, 4
+LQCD_LAYOUT_LEXI, LQCD_LAYOUT_EO = 0, 1
+
+_STATUS_NAMES = {0: "LQCD_OK", -1: "LQCD_ERR_INVALID", -2: "LQCD_ERR_CUDA", -3: "LQCD_ERR_NOCONV",
+                 -4: "LQCD_ERR_NONFINITE", -5: "LQCD_ERR_TIMEOUT", -6: "LQCD_ERR_OOM",
+                 -7: "LQCD_ERR_UNSUPPORTED"}
+
+
+class LqcdError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+# --- structs -------------------------------------------------------------------
+class lqcd_geom(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int32 * 4), ("antiperiodic_t", ctypes.c_int32)]
+
+
+class lqcd_field(ctypes.Structure):
+    _fields_ = [("ptr", ctypes.c_void_p), ("scale", ctypes.c_void_p), ("layout", ctypes.c_int32),
+                ("prec", ctypes.c_int32), ("nrhs", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class lqcd_cg_params(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int32),
+                ("outer_prec", ctypes.c_int32), ("inner_prec", ctypes.c_int32),
+                ("delta", ctypes.c_double), ("max_restarts", ctypes.c_int32),
+                ("check_every", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("sloppy_recon", ctypes.c_int32)]
+
+
+class lqcd_cg_stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("reliable_updates", ctypes.c_int32),
+                ("restarts", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("true_resid", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class lqcd_counters(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_uint64), ("hop_launches", ctypes.c_uint64),
+                ("bytes", ctypes.c_double), ("hop_bytes", ctypes.c_double),
+                ("hop_flops", ctypes.c_double), ("hop_sites", ctypes.c_double)]
+
+
+class lqcd_hmc_params(ctypes.Structure):
+    _fields_ = [("beta", ctypes.c_double), ("kappa", ctypes.c_double), ("mu", ctypes.c_double),
+                ("tau", ctypes.c_double), ("nsteps", ctypes.c_int32), ("nf", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("traj", ctypes.c_uint32), ("reserved", ctypes.c_int32),
+                ("cg", lqcd_cg_params)]
+
+
+class lqcd_hmc_stats(ctypes.Structure):
+    _fields_ = [("dH", ctypes.c_double), ("H0", ctypes.c_double), ("H1", ctypes.c_double),
+                ("plaquette", ctypes.c_double), ("accepted", ctypes.c_int32),
+                ("cg_iters", ctypes.c_int32), ("seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+# --- library loading ------------------------------------------------------------
+_lib = None
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_d = ctypes.c_double
+
+# (name, restype, argtypes) of every entry point declared in include/lqcd.h
+SIGNATURES = [
+    ("lqcd_abi_version", _i, []),
+    ("lqcd_create", _i, [ctypes.POINTER(_vp), _i, _vp]),
+    ("lqcd_destroy", _i, [_vp]),
+    ("lqcd_set_stream", _i, [_vp, _vp]),
+    ("lqcd_last_error", ctypes.c_char_p, [_vp]),
+    ("lqcd_get_counters", _i, [_vp, _vp]),
+    ("lqcd_reset_counters", _i, [_vp]),
+    ("lqcd_field_bytes", ctypes.c_size_t, [ctypes.POINTER(lqcd_geom), _i, _i, _i,
+                                           ctypes.POINTER(ctypes.c_size_t)]),
+    ("lqcd_gauge_import", _i, [_vp, _vp, ctypes.POINTER(lqcd_geom), _i, ctypes.POINTER(_vp)]),
+    ("lqcd_gauge_export", _i, [_vp, _vp, _vp]),
+    ("lqcd_gauge_free", _i, [_vp, _vp]),
+    ("lqcd_spinor_pack", _i, [_vp, ctypes.POINTER(lqcd_geom), _vp, lqcd_field]),
+    ("lqcd_spinor_unpack", _i, [_vp, ctypes.POINTER(lqcd_geom), lqcd_field, _vp]),
+    ("lqcd_spinor_convert", _i, [_vp, ctypes.POINTER(lqcd_geom), _i, lqcd_field, lqcd_field]),
+    ("lqcd_dslash", _i, [_vp, _vp, lqcd_field, lqcd_field, ctypes.POINTER(lqcd_geom), _i, _i]),
+    ("lqcd_apply_M", _i, [_vp, _vp, lqcd_field, lqcd_field, ctypes.POINTER(lqcd_geom), _d, _d, _i]),
+    ("lqcd_apply_Mdag", _i, [_vp, _vp, lqcd_field, lqcd_field, ctypes.POINTER(lqcd_geom), _d, _d,
+                             _i]),
+    ("lqcd_cg_solve", _i, [_vp, _vp, lqcd_field, lqcd_field, ctypes.POINTER(lqcd_geom), _d, _d,
+                           ctypes.POINTER(lqcd_cg_params), ctypes.POINTER(lqcd_cg_stats)]),
+    ("lqcd_cg_solve_batch", _i, [_vp, _i, ctypes.POINTER(_vp), ctypes.POINTER(lqcd_field),
+                                 ctypes.POINTER(lqcd_field), ctypes.POINTER(_d), ctypes.POINTER(_d),
+                                 ctypes.POINTER(lqcd_cg_params), ctypes.POINTER(lqcd_cg_stats)]),
+    ("lqcd_fermion_force", _i, [_vp, _vp, lqcd_field, _vp, ctypes.POINTER(lqcd_field),
+                                ctypes.POINTER(lqcd_geom), _d, _d, ctypes.POINTER(lqcd_cg_params),
+                                ctypes.POINTER(lqcd_cg_stats), ctypes.POINTER(_d)]),
+    ("lqcd_gauge_force", _i, [_vp, _vp, _d, _vp, ctypes.POINTER(_d)]),
+    ("lqcd_plaquette", _i, [_vp, _vp, ctypes.POINTER(_d)]),
+    ("lqcd_heatbath_sweep", _i, [_vp, _vp, _d, ctypes.c_uint64, ctypes.c_uint64, _i]),
+    ("lqcd_momenta_gaussian", _i, [_vp, ctypes.POINTER(lqcd_geom), _vp, ctypes.c_uint64,
+                                   ctypes.c_uint32]),
+    ("lqcd_spinor_gaussian", _i, [_vp, ctypes.POINTER(lqcd_geom), lqcd_field, _i, ctypes.c_uint64,
+                                  ctypes.c_uint32]),
+    ("lqcd_gauge_update", _i, [_vp, _vp, _vp, _d]),
+    ("lqcd_momenta_update", _i, [_vp, ctypes.POINTER(lqcd_geom), _vp, _vp, _d]),
+    ("lqcd_momenta_kinetic", _i, [_vp, ctypes.POINTER(lqcd_geom), _vp, ctypes.POINTER(_d)]),
+    ("lqcd_gauge_copy", _i, [_vp, _vp, _vp]),
+    ("lqcd_hmc_trajectory", _i, [_vp, _vp, ctypes.POINTER(lqcd_hmc_params),
+                                 ctypes.POINTER(lqcd_hmc_stats)]),
+]
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: run paper_1209_5942_gb300.build.build() first "
+                           "(the CUDA library is required; there is no CPU fallback)")
+    lib = ctypes.CDLL(path)
+    for name, res, args in SIGNATURES:
+        f = getattr(lib, name, None)
+        if f is None:
+            continue  # optional entry points are checked by the export test
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def lib():
+    return _load()
+
+
+def declared_symbols() -> list[str]:
+    """Names of every function declared in include/lqcd.h (parsed from the header)."""
+    import re
+    hdr = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
+                       "lqcd.h")
+    txt = open(hdr).read()
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_ \*]*?\b(lqcd_[a-z0-9_]+)\s*\(",
+                                 txt, flags=re.M)))
+
+
+# --- helpers ---------------------------------------------------------------------
+def geom(L, antiperiodic_t=True) -> lqcd_geom:
+    g = lqcd_geom()
+    for k in range(4):
+        g.L[k] = int(L[k])
+    g.antiperiodic_t = 1 if antiperiodic_t else 0
+    return g
+
+
+def field(t: torch.Tensor, layout=LQCD_LAYOUT_EO, prec=LQCD_F64, nrhs=1,
+          scale: torch.Tensor | None = None) -> lqcd_field:
+    if not t.is_cuda:
+        raise ValueError("fields must be CUDA tensors")
+    if not t.is_contiguous():
+        raise ValueError("fields must be contiguous")
+    f = lqcd_field()
+    f.ptr = t.data_ptr()
+    f.scale = scale.data_ptr() if scale is not None else None
+    f.layout = layout
+    f.prec = prec
+    f.nrhs = nrhs
+    f.reserved = 0
+    f._keep = (t, scale)  # the descriptor keeps its buffers alive
+    return f
+
+
+def field_bytes(L, parity, prec, nrhs=1, antiperiodic_t=True):
+    sb = ctypes.c_size_t(0)
+    n = lib().lqcd_field_bytes(ctypes.byref(geom(L, antiperiodic_t)), parity, prec, nrhs,
+                               ctypes.byref(sb))
+    return int(n), int(sb.value)
+
+
+def alloc_field(L, parity, prec, nrhs=1, device="cuda"):
+    """Zeroed EO field buffers (data, scale or None) for the given shape."""
+    n, sb = field_bytes(L, parity, prec, nrhs)
+    data = torch.zeros(n // 8, dtype=torch.float64, device=device)
+    scale = torch.zeros(max(sb // 4, 1), dtype=torch.float32, device=device) if sb else None
+    return data, scale
+
+
+class Context:
+    """An lqcd_ctx bound to a device and a stream (default: torch's current stream)."""
+
+    def __init__(self, device: int = 0, stream: torch.cuda.Stream | None = None):
+        self._h = _vp()
+        s = (stream or torch.cuda.current_stream(device)).cuda_stream
+        st = lib().lqcd_create(ctypes.byref(self._h), device, _vp(s))
+        if st != LQCD_OK:
+            raise LqcdError(st, "lqcd_create failed")
+        self.device = device
+
+    @property
+    def handle(self):
+        return self._h
+
+    def check(self, status: int, allow=()):
+        if status != LQCD_OK and status not in allow:
+            raise LqcdError(status, lib().lqcd_last_error(self._h).decode())
+        return status
+
+    def set_stream(self, stream: torch.cuda.Stream):
+        self.check(lib().lqcd_set_stream(self._h, _vp(stream.cuda_stream)))
+
+    def close(self):
+        if self._h:
+            lib().lqcd_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Gauge:
+    """Library-owned gauge field (lqcd_gauge*)."""
+
+    def __init__(self, ctx: Context, handle, L, antiperiodic_t):
+        self.ctx = ctx
+        self._h = handle
+        self.L = tuple(int(v) for v in L)
+        self.antiperiodic_t = antiperiodic_t
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def geom(self):
+        return geom(self.L, self.antiperiodic_t)
+
+    def free(self):
+        if self._h:
+            lib().lqcd_gauge_free(self.ctx.handle, self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+# --- entry points (same names as the C ABI) ----------------------------------------
+def lqcd_abi_version() -> int:
+    return lib().lqcd_abi_version()
+
+
+def lqcd_create(device: int = 0, stream=None) -> Context:
+    return Context(device, stream)
+
+
+def lqcd_gauge_import(ctx: Context, U_lexi: torch.Tensor, L, recon=18, antiperiodic_t=True) -> Gauge:
+    if U_lexi.dtype != torch.complex128 or not U_lexi.is_cuda or not U_lexi.is_contiguous():
+        raise ValueError("U must be a contiguous CUDA complex128 tensor [V,4,3,3]")
+    h = _vp()
+    g = geom(L, antiperiodic_t)
+    ctx.check(lib().lqcd_gauge_import(ctx.handle, _vp(U_lexi.data_ptr()), ctypes.byref(g), recon,
+                                      ctypes.byref(h)))
+    return Gauge(ctx, h, L, antiperiodic_t)
+
+
+def lqcd_gauge_export(ctx: Context, U: Gauge, out: torch.Tensor):
+    ctx.check(lib().lqcd_gauge_export(ctx.handle, U.handle, _vp(out.data_ptr())))
+
+
+def lqcd_spinor_pack(ctx: Context, L, lexi: torch.Tensor, eo: lqcd_field, antiperiodic_t=True):
+    g = geom(L, antiperiodic_t)
+    ctx.check(lib().lqcd_spinor_pack(ctx.handle, ctypes.byref(g), _vp(lexi.data_ptr()), eo))
+
+
+def lqcd_spinor_unpack(ctx: Context, L, eo: lqcd_field, lexi: torch.Tensor, antiperiodic_t=True):
+    g = geom(L, antiperiodic_t)
+    ctx.check(lib().lqcd_spinor_unpack(ctx.handle, ctypes.byref(g), eo, _vp(lexi.data_ptr())))
+
+
+def lqcd_spinor_convert(ctx: Context, L, parity, inp: lqcd_field, out: lqcd_field,
+                        antiperiodic_t=True):
+    g = geom(L, antiperiodic_t)
+    ctx.check(lib().lqcd_spinor_convert(ctx.handle, ctypes.byref(g), parity, inp, out))
+
+
+def lqcd_dslash(ctx: Context, U: Gauge, inp: lqcd_field, out: lqcd_field, out_parity, dagger=0):
+    g = U.geom
+    ctx.check(lib().lqcd_dslash(ctx.handle, U.handle, inp, out, ctypes.byref(g), out_parity,
+                                int(dagger)))
+
+
+def lqcd_apply_M(ctx: Context, U: Gauge, inp: lqcd_field, out: lqcd_field, kappa, mu,
+                 parity=LQCD_FULL):
+    g = U.geom
+    ctx.check(lib().lqcd_apply_M(ctx.handle, U.handle, inp, out, ctypes.byref(g), kappa, mu,
+                                 parity))
+
+
+def lqcd_apply_Mdag(ctx: Context, U: Gauge, inp: lqcd_field, out: lqcd_field, kappa, mu,
+                    parity=LQCD_FULL):
+    g = U.geom
+    ctx.check(lib().lqcd_apply_Mdag(ctx.handle, U.handle, inp, out, ctypes.byref(g), kappa, mu,
+                                    parity))
+
+
+def cg_params(tol=1e-10, max_iter=20000, outer_prec=LQCD_F64, inner_prec=None, delta=0.1,
+              max_restarts=5, check_every=10, use_graph=1, sloppy_recon=0) -> lqcd_cg_params:
+    p = lqcd_cg_params()
+    p.tol = tol
+    p.max_iter = max_iter
+    p.outer_prec = outer_prec
+    p.inner_prec = outer_prec if inner_prec is None else inner_prec
+    p.delta = delta
+    p.max_restarts = max_restarts
+    p.check_every = check_every
+    p.use_graph = use_graph
+    p.sloppy_recon = sloppy_recon
+    return p
+
+
+def lqcd_cg_solve(ctx: Context, U: Gauge, b: lqcd_field, x: lqcd_field, kappa, mu,
+                  params: lqcd_cg_params, allow_noconv=False):
+    nrhs = b.nrhs
+    stats = (lqcd_cg_stats * nrhs)()
+    g = U.geom
+    ctx.check(lib().lqcd_cg_solve(ctx.handle, U.handle, b, x, ctypes.byref(g), kappa, mu,
+                                  ctypes.byref(params), stats),
+              allow=(LQCD_ERR_NOCONV,) if allow_noconv else ())
+    return [s.as_dict() for s in stats]
+
+
+def lqcd_cg_solve_batch(ctx: Context, Us, bs, xs, kappas, mus, params: lqcd_cg_params,
+                        allow_noconv=False):
+    n = len(Us)
+    arrU = (_vp * n)(*[U.handle.value for U in Us])
+    arrb = (lqcd_field * n)(*bs)
+    arrx = (lqcd_field * n)(*xs)
+    arrk = (_d * n)(*kappas)
+    arrm = (_d * n)(*mus)
+    stats = (lqcd_cg_stats * n)()
+    ctx.check(lib().lqcd_cg_solve_batch(ctx.handle, n, arrU, arrb, arrx, arrk, arrm,
+                                        ctypes.byref(params), stats),
+              allow=(LQCD_ERR_NOCONV,) if allow_noconv else ())
+    return [s.as_dict() for s in stats]
+
+
+def lqcd_fermion_force(ctx: Context, U: Gauge, phi: lqcd_field, dSdw: torch.Tensor, kappa, mu,
+                       params: lqcd_cg_params, X_cache: lqcd_field | None = None):
+    """Returns (S, stats); dSdw (float64 [4, V, 8] CUDA) receives dS/domega."""
+    st = lqcd_cg_stats()
+    S = _d(0.0)
+    g = U.geom
+    ctx.check(lib().lqcd_fermion_force(ctx.handle, U.handle, phi, _vp(dSdw.data_ptr()),
+                                       ctypes.byref(X_cache) if X_cache is not None else None,
+                                       ctypes.byref(g), kappa, mu, ctypes.byref(params),
+                                       ctypes.byref(st), ctypes.byref(S)))
+    return S.value, st.as_dict()
+
+
+def lqcd_gauge_force(ctx: Context, U: Gauge, beta, dSdw: torch.Tensor, want_action=True):
+    S = _d(0.0)
+    ctx.check(lib().lqcd_gauge_force(ctx.handle, U.handle, beta, _vp(dSdw.data_ptr()),
+                                     ctypes.byref(S) if want_action else None))
+    return S.value if want_action else None
+
+
+def lqcd_plaquette(ctx: Context, U: Gauge) -> float:
+    p = _d(0.0)
+    ctx.check(lib().lqcd_plaquette(ctx.handle, U.handle, ctypes.byref(p)))
+    return p.value
+
+
+def lqcd_heatbath_sweep(ctx: Context, U: Gauge, beta, seed, sweep_idx, n_or=0):
+    ctx.check(lib().lqcd_heatbath_sweep(ctx.handle, U.handle, beta, seed, sweep_idx, n_or))
+
+
+def lqcd_momenta_gaussian(ctx: Context, L, P: torch.Tensor, seed, traj, antiperiodic_t=True):
+    g = geom(L, antiperiodic_t)
+    ctx.check(lib().lqcd_momenta_gaussian(ctx.handle, ctypes.byref(g), _vp(P.data_ptr()), seed,
+                                          traj))
+
+
+def lqcd_spinor_gaussian(ctx: Context, L, eta: lqcd_field, parity, seed, traj,
+                         antiperiodic_t=True):
+    g = geom(L, antiperiodic_t)
+    ctx.check(lib().lqcd_spinor_gaussian(ctx.handle, ctypes.byref(g), eta, parity, seed, traj))
+
+
+def lqcd_gauge_update(ctx: Context, U: Gauge, P: torch.Tensor, eps):
+    ctx.check(lib().lqcd_gauge_update(ctx.handle, U.handle, _vp(P.data_ptr()), eps))
+
+
+def lqcd_momenta_update(ctx: Context, L, P: torch.Tensor, dSdw: torch.Tensor, eps,
+                        antiperiodic_t=True):
+    g = geom(L, antiperiodic_t)
+    ctx.check(lib().lqcd_momenta_update(ctx.handle, ctypes.byref(g), _vp(P.data_ptr()),
+                                        _vp(dSdw.data_ptr()), eps))
+
+
+def lqcd_momenta_kinetic(ctx: Context, L, P: torch.Tensor, antiperiodic_t=True) -> float:
+    g = geom(L, antiperiodic_t)
+    K = _d(0.0)
+    ctx.check(lib().lqcd_momenta_kinetic(ctx.handle, ctypes.byref(g), _vp(P.data_ptr()),
+                                         ctypes.byref(K)))
+    return K.value
+
+
+def lqcd_gauge_copy(ctx: Context, src: Gauge, dst: Gauge):
+    ctx.check(lib().lqcd_gauge_copy(ctx.handle, src.handle, dst.handle))
+
+
+def hmc_params(beta, kappa, mu, tau=1.0, nsteps=20, nf=1, seed=1, traj=0, cg=None):
+    p = lqcd_hmc_params()
+    p.beta, p.kappa, p.mu, p.tau = beta, kappa, mu, tau
+    p.nsteps, p.nf, p.seed, p.traj = nsteps, nf, seed, traj
+    p.cg = cg if cg is not None else cg_params(tol=1e-10, outer_prec=LQCD_DF64,
+                                               inner_prec=LQCD_F32)
+    return p
+
+
+def lqcd_hmc_trajectory(ctx: Context, U: Gauge, params: lqcd_hmc_params):
+    st = lqcd_hmc_stats()
+    ctx.check(lib().lqcd_hmc_trajectory(ctx.handle, U.handle, ctypes.byref(params),
+                                        ctypes.byref(st)))
+    return st.as_dict()

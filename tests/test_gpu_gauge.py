@@ -1,0 +1,242 @@
+"""GPU parity of the gauge-side kernels and the HMC pieces (Sec. 2.1 action,
+Sec. 2.2 forces, heatbath, HMC) against the FP64 oracle.
+
+The GPU and the oracle draw the same Philox4x32-10 streams, so momenta,
+Gaussian spinors, heatbath sweeps and whole trajectories are compared value
+by value; where a floating-point comparison decides an integer (a heatbath
+rejection), both sides decide in FP64 and the rare flips caused by libm
+rounding differences are counted and bounded.
+"""
+import numpy as np
+import pytest
+import scipy.linalg
+import torch
+
+from paper_1209_5942_gb300 import inputs, lqcd
+from tests.gpu_util import dev, eo_full_from_lexi, half_views, host, lexi_from_eo_full, relerr
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1209_5942_gb300 import build
+    build.build()
+    return lqcd.Context(0)
+
+
+def _export(ctx, G, L):
+    V = inputs.volume(L)
+    out = torch.zeros((V, 4, 3, 3), dtype=torch.complex128, device="cuda")
+    lqcd.lqcd_gauge_export(ctx, G, out)
+    return host(out)
+
+
+@pytest.mark.parametrize("L", [(4, 4, 4, 4), (2, 4, 6, 8), (6, 4, 2, 10)])
+def test_gauge_roundtrip_and_plaquette(ctx, oracle, L):
+    U = inputs.random_gauge(L, "near", seed=31, eps=0.6)
+    G = lqcd.lqcd_gauge_import(ctx, dev(U), L)
+    assert np.array_equal(_export(ctx, G, L), U)
+    assert abs(lqcd.lqcd_plaquette(ctx, G) - oracle.plaquette(U, L)) < 1e-14
+    Gc = lqcd.lqcd_gauge_import(ctx, dev(inputs.random_gauge(L, "cold")), L)
+    assert lqcd.lqcd_plaquette(ctx, Gc) == 1.0
+
+
+@pytest.mark.parametrize("L", [(4, 4, 4, 4), (2, 4, 6, 8)])
+def test_gauge_force(ctx, oracle, L):
+    beta = 5.6
+    U = inputs.random_gauge(L, "near", seed=32, eps=0.5)
+    G = lqcd.lqcd_gauge_import(ctx, dev(U), L)
+    F = torch.zeros((4, inputs.volume(L), 8), dtype=torch.float64, device="cuda")
+    S = lqcd.lqcd_gauge_force(ctx, G, beta, F)
+    ref = oracle.gauge_dSdw(U, L, beta)
+    assert relerr(host(F), ref) < 1e-13
+    assert abs(S - oracle.gauge_action(U, L, beta)) < 1e-10 * abs(S)
+
+
+def test_momenta_and_eta_match_oracle_streams(ctx, oracle):
+    L = (4, 4, 4, 8)
+    V = inputs.volume(L)
+    P = torch.zeros((4, V, 8), dtype=torch.float64, device="cuda")
+    lqcd.lqcd_momenta_gaussian(ctx, L, P, 99, 7)
+    assert relerr(host(P), oracle.momenta(L, 99, 7)) < 1e-13
+    K = lqcd.lqcd_momenta_kinetic(ctx, L, P)
+    assert abs(K - 0.5 * np.sum(oracle.momenta(L, 99, 7) ** 2)) < 1e-10 * K
+    d, s = lqcd.alloc_field(L, lqcd.LQCD_FULL, lqcd.LQCD_F64)
+    f = lqcd.field(d, lqcd.LQCD_LAYOUT_EO)
+    lqcd.lqcd_spinor_gaussian(ctx, L, f, lqcd.LQCD_EVEN, 99, 7)
+    eta = lexi_from_eo_full(ctx, L, f)
+    ref = oracle.gaussian_spinor(L, 99, 7) * (~oracle.parity_mask(L))[:, None, None]
+    assert relerr(eta, ref) < 1e-13
+
+
+def test_gauge_update_matches_library_expm(ctx, oracle):
+    L = (4, 4, 2, 4)
+    V = inputs.volume(L)
+    U = inputs.random_gauge(L, "haar", seed=33)
+    G = lqcd.lqcd_gauge_import(ctx, dev(U), L)
+    P = inputs.gaussian_algebra(L, 34) * 3.0
+    eps = 0.07
+    lqcd.lqcd_gauge_update(ctx, G, dev(P), eps)
+    got = _export(ctx, G, L)
+    ref = oracle.update_links(U, P, L, eps)
+    assert relerr(got, ref) < 1e-13
+    T = np.stack([oracle.generator(a) for a in range(8)])
+    H = np.einsum("a,aij->ij", P[2, 5], T)
+    assert np.max(np.abs(got[5, 2] - scipy.linalg.expm(1j * eps * H) @ U[5, 2])) < 1e-13
+
+
+def test_heatbath_sweep_matches_oracle(ctx, oracle):
+    L = (4, 4, 4, 4)
+    U = inputs.random_gauge(L, "haar", seed=35)
+    G = lqcd.lqcd_gauge_import(ctx, dev(U), L)
+    Uo = U.copy()
+    for sweep in range(3):
+        lqcd.lqcd_heatbath_sweep(ctx, G, 5.7, 4242, sweep)
+        Uo, fails = oracle.heatbath_sweep(Uo, L, 5.7, 4242, sweep)
+        assert fails == 0
+    got = _export(ctx, G, L)
+    diff = np.abs(got - Uo).max(axis=(2, 3))
+    flips = int(np.sum(diff > 1e-9))
+    # links agree to rounding, except where libm rounding flipped a rejection
+    assert flips <= max(2, diff.size // 500), flips
+    assert np.median(diff) < 1e-13
+    eye = np.eye(3)
+    assert np.max(np.abs(got @ np.conj(np.transpose(got, (0, 1, 3, 2))) - eye)) < 1e-12
+
+
+def test_heatbath_strong_coupling_gpu(ctx):
+    """<P> = beta/18 + beta^2/216 at beta = 0.3 (SU(3) strong coupling)."""
+    L = (8, 8, 8, 8)
+    beta = 0.3
+    G = lqcd.lqcd_gauge_import(ctx, dev(inputs.random_gauge(L, "cold")), L)
+    vals = []
+    for s in range(80):
+        lqcd.lqcd_heatbath_sweep(ctx, G, beta, 77, s)
+        if s >= 10:
+            vals.append(lqcd.lqcd_plaquette(ctx, G))
+    vals = np.array(vals)
+    expect = beta / 18 + beta ** 2 / 216
+    err = vals.std() / np.sqrt(len(vals))
+    assert abs(vals.mean() - expect) < 4 * err + 2e-4
+
+
+def test_overrelaxation_preserves_action(ctx):
+    L = (4, 4, 4, 4)
+    G = lqcd.lqcd_gauge_import(ctx, dev(inputs.random_gauge(L, "near", seed=36, eps=0.8)), L)
+    F = torch.zeros((4, inputs.volume(L), 8), dtype=torch.float64, device="cuda")
+    lqcd.lqcd_heatbath_sweep(ctx, G, 5.7, 1, 0)
+    S0 = lqcd.lqcd_gauge_force(ctx, G, 5.7, F)
+    p0 = lqcd.lqcd_plaquette(ctx, G)
+    # one heatbath sweep followed by overrelaxation: compare against heatbath alone
+    G2 = lqcd.lqcd_gauge_import(ctx, dev(inputs.random_gauge(L, "cold")), L)
+    lqcd.lqcd_gauge_copy(ctx, G, G2)
+    lqcd.lqcd_heatbath_sweep(ctx, G, 5.7, 1, 1, n_or=0)
+    lqcd.lqcd_heatbath_sweep(ctx, G2, 5.7, 1, 1, n_or=2)
+    # overrelaxation is microcanonical: same action as the heatbath-only field
+    S1 = lqcd.lqcd_gauge_force(ctx, G, 5.7, F)
+    S2 = lqcd.lqcd_gauge_force(ctx, G2, 5.7, F)
+    assert abs(S2 - S1) < 1e-8 * abs(S1)
+    assert p0 > 0.3
+
+
+def _even_half_field(ctx, L, psi_even):
+    d, s, _ = eo_full_from_lexi(ctx, L, psi_even)
+    fe, _ = half_views(L, d, s, lqcd.LQCD_F64)
+    return d, fe
+
+
+@pytest.mark.parametrize("outer,inner", [(lqcd.LQCD_F64, lqcd.LQCD_F64),
+                                         (lqcd.LQCD_DF64, lqcd.LQCD_F32)])
+def test_fermion_force_vs_oracle(ctx, oracle, outer, inner):
+    L = (4, 4, 2, 4)
+    V = inputs.volume(L)
+    kappa, mu = 0.14, 0.1
+    U = inputs.random_gauge(L, "near", seed=37, eps=0.4)
+    G = lqcd.lqcd_gauge_import(ctx, dev(U), L)
+    ev = ~oracle.parity_mask(L)
+    phi = inputs.gaussian_spinor(L, 38) * ev[:, None, None]
+    keep, fphi = _even_half_field(ctx, L, phi)
+    F = torch.zeros((4, V, 8), dtype=torch.float64, device="cuda")
+    prm = lqcd.cg_params(tol=1e-13, outer_prec=outer, inner_prec=inner, max_iter=50000)
+    S, st = lqcd.lqcd_fermion_force(ctx, G, fphi, F, kappa, mu, prm)
+    Sref, X = oracle.pseudofermion_action(U, phi, L, kappa, mu, eo=True, tol=1e-14)
+    ref = oracle.fermion_dSdw(U, X, L, kappa, mu, eo=True)
+    assert abs(S - Sref) < 1e-10 * abs(Sref)
+    assert relerr(host(F), ref) < 1e-9
+
+
+def test_fermion_force_finite_difference_gpu(ctx, oracle):
+    """Central differences of the GPU action S = phi^+ (Mhat^+ Mhat)^-1 phi on single
+    links (one crossing the time boundary) agree with the GPU force to 1e-6."""
+    L = (4, 4, 2, 4)
+    V = inputs.volume(L)
+    kappa, mu = 0.14, 0.1
+    U = inputs.random_gauge(L, "near", seed=39, eps=0.4)
+    ev = ~oracle.parity_mask(L)
+    phi = inputs.gaussian_spinor(L, 40) * ev[:, None, None]
+    keep, fphi = _even_half_field(ctx, L, phi)
+    prm = lqcd.cg_params(tol=1e-14, max_iter=50000)
+    F = torch.zeros((4, V, 8), dtype=torch.float64, device="cuda")
+    G = lqcd.lqcd_gauge_import(ctx, dev(U), L)
+    lqcd.lqcd_fermion_force(ctx, G, fphi, F, kappa, mu, prm)
+    Fh = host(F)
+    c = inputs.site_coords(L)
+    tb = int(np.nonzero(c[:, 3] == L[3] - 1)[0][1])
+    h = 1e-5
+    worst = 0.0
+    for (i, m) in [(0, 0), (9, 1), (tb, 3)]:
+        for a in range(8):
+            vals = []
+            for sgn in (1, -1):
+                Ud = U.copy()
+                Ud[i, m] = scipy.linalg.expm(1j * sgn * h * oracle.generator(a)) @ U[i, m]
+                Gd = lqcd.lqcd_gauge_import(ctx, dev(Ud), L)
+                S, _ = lqcd.lqcd_fermion_force(ctx, Gd, fphi, F, kappa, mu, prm)
+                vals.append(S)
+                Gd.free()
+            fd = (vals[0] - vals[1]) / (2 * h)
+            worst = max(worst, abs(fd - Fh[m, i, a]) / max(1.0, abs(fd)))
+    assert worst < 1e-6, worst
+
+
+def test_hmc_trajectory_matches_oracle(ctx, oracle):
+    """One leapfrog trajectory from the same links with the same Philox momenta
+    and pseudofermion: dH and the final links agree with the oracle."""
+    L = (4, 4, 2, 4)
+    beta, kappa, mu = 5.6, 0.14, 0.05 / 0.28
+    U = inputs.random_gauge(L, "near", seed=41, eps=0.3)
+    G = lqcd.lqcd_gauge_import(ctx, dev(U), L)
+    seed, traj = 1234, 3
+    prm = lqcd.hmc_params(beta, kappa, mu, tau=0.5, nsteps=8, nf=1, seed=seed, traj=traj,
+                          cg=lqcd.cg_params(tol=1e-13, max_iter=50000))
+    st = lqcd.lqcd_hmc_trajectory(ctx, G, prm)
+    P0 = oracle.momenta(L, seed, traj)
+    eta = oracle.gaussian_spinor(L, seed, traj) * (~oracle.parity_mask(L))[:, None, None]
+    phi = oracle.apply_Mhat(U, eta, L, kappa, mu, dagger=True)
+    U1, P1, dH, (H0, H1, Sf0) = oracle.hmc_md(U, P0, phi, L, beta, kappa, mu, nf=1, nsteps=8,
+                                              tau=0.5, tol=1e-13)
+    assert abs(st["H0"] - H0) < 1e-9 * abs(H0)
+    assert abs(st["dH"] - dH) < 1e-7 * max(1.0, abs(dH))
+    if st["accepted"]:
+        assert relerr(_export(ctx, G, L), U1) < 1e-10
+    else:
+        assert np.array_equal(_export(ctx, G, L), U)
+
+
+def test_pure_gauge_hmc_matches_oracle_and_scales(ctx, oracle):
+    """Pure-gauge trajectory (nf = 0): dH equals the oracle's for the same
+    Philox momenta, and halving the step size divides dH by about 4."""
+    L = (4, 4, 4, 4)
+    U = inputs.random_gauge(L, "near", seed=42, eps=0.3)
+    dHs = {}
+    for n in (20, 40):
+        G = lqcd.lqcd_gauge_import(ctx, dev(U), L)
+        st = lqcd.lqcd_hmc_trajectory(ctx, G, lqcd.hmc_params(5.6, 0.0, 0.0, tau=1.0, nsteps=n,
+                                                              nf=0, seed=9, traj=0))
+        dHs[n] = st["dH"]
+        G.free()
+    _, _, dH_ref, _ = oracle.hmc_md(U, oracle.momenta(L, 9, 0), None, L, 5.6, 0.0, 0.0, nf=0,
+                                    nsteps=20, tau=1.0)
+    assert abs(dHs[20] - dH_ref) < 1e-8 * max(1.0, abs(dH_ref))
+    assert 3.0 < dHs[20] / dHs[40] < 5.3
