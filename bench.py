@@ -431,7 +431,7 @@ def main():
     ap.add_argument("--inner", default=None, choices=list(PREC_NAMES))
     ap.add_argument("--recon", type=int, default=18)
     ap.add_argument("--check-every", type=int, default=20)
-    ap.add_argument("--ref-iters", type=int, default=3)
+    ap.add_argument("--ref-iters", type=int, default=5)
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per launch of the half hop, if captured")
     ap.add_argument("--no-cpu-baseline", action="store_true")

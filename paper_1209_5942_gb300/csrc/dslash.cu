@@ -101,6 +101,62 @@ LQCD_DEV void mul_link_dag(const Cx<R> u[9], const Cx<R> h[6], Cx<R> v[6]) {
     }
 }
 
+// Float-float specialisation of the colour products.  Each real output is a
+// sum of six products a*b of double-words; every product contributes its
+// exact leading part p = a.hi*b.hi (TwoProduct: the rounding error comes from
+// one FMA) plus the first-order cross terms a.hi*b.lo + a.lo*b.hi, and the
+// leading parts are summed by a TwoSum chain whose errors join the low-order
+// accumulator.  The dropped a.lo*b.lo terms are below 2^-46 of each product.
+struct DfAcc {
+  float s, e;
+};
+LQCD_DEV void dfacc_add_prod(DfAcc &A, df a, df b, bool neg) {
+  float ah = neg ? -a.hi : a.hi, al = neg ? -a.lo : a.lo;
+  float p = __fmul_rn(ah, b.hi);
+  float pe = __fmaf_rn(ah, b.hi, -p);
+  pe = __fmaf_rn(ah, b.lo, pe);
+  pe = __fmaf_rn(al, b.hi, pe);
+  df t = two_sum(A.s, p);
+  A.s = t.hi;
+  A.e = __fadd_rn(A.e, __fadd_rn(t.lo, pe));
+}
+LQCD_DEV df dfacc_result(const DfAcc &A) { return fast_two_sum(A.s, A.e); }
+
+// sum_j x_j * y_j (conjugating x when CONJ), complex double-words
+template <bool CONJ>
+LQCD_DEV Cx<df> dfdot3(const Cx<df> x0, const Cx<df> x1, const Cx<df> x2, const Cx<df> y0,
+                       const Cx<df> y1, const Cx<df> y2) {
+  DfAcc re{0.0f, 0.0f}, im{0.0f, 0.0f};
+  const Cx<df> xs[3] = {x0, x1, x2}, ys[3] = {y0, y1, y2};
+#pragma unroll
+  for (int j = 0; j < 3; j++) {
+    // (a + ib)(c + id) = (ac - bd) + i(ad + bc);  conj: (ac + bd) + i(ad - bc)
+    dfacc_add_prod(re, xs[j].re, ys[j].re, false);
+    dfacc_add_prod(re, xs[j].im, ys[j].im, !CONJ);
+    dfacc_add_prod(im, xs[j].re, ys[j].im, false);
+    dfacc_add_prod(im, xs[j].im, ys[j].re, CONJ);
+  }
+  return {dfacc_result(re), dfacc_result(im)};
+}
+
+template <>
+LQCD_DEV void mul_link<df>(const Cx<df> u[9], const Cx<df> h[6], Cx<df> v[6]) {
+#pragma unroll
+  for (int k = 0; k < 2; k++)
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+      v[3 * k + a] = dfdot3<false>(u[3 * a], u[3 * a + 1], u[3 * a + 2], h[3 * k], h[3 * k + 1],
+                                   h[3 * k + 2]);
+}
+template <>
+LQCD_DEV void mul_link_dag<df>(const Cx<df> u[9], const Cx<df> h[6], Cx<df> v[6]) {
+#pragma unroll
+  for (int k = 0; k < 2; k++)
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+      v[3 * k + a] = dfdot3<true>(u[a], u[3 + a], u[6 + a], h[3 * k], h[3 * k + 1], h[3 * k + 2]);
+}
+
 struct HopArgs {
   Geom g;
   GaugeView U;
