@@ -329,6 +329,30 @@ typedef struct {
 int lqcd_hmc_trajectory(lqcd_ctx *ctx, lqcd_gauge *U, const lqcd_hmc_params *params,
                         lqcd_hmc_stats *stats);
 
+/* ---------------------------------------------------------------- */
+/* No-allocation entry point (the paper has no counterpart)          */
+/* ---------------------------------------------------------------- */
+
+/* Plaquette (1/(6V)) sum_{x, mu<nu} (1/3) Re Tr U_munu(x) of a lexicographic
+ * complex128 gauge field [V][4][3][3] (device pointer, 16-byte aligned),
+ * written to *plaq_dev (device pointer to one double), for callers that
+ * cannot allocate device memory (their allocator belongs to another
+ * framework, their memory budget is fixed, or allocation is off limits while
+ * they record work).  It needs no context and allocates nothing: the block
+ * partial sums go to a fixed file-scope device array of 32768 doubles
+ * (256 KiB) that each GPU using the library keeps until the process exits,
+ * so V <= 4194304 sites; larger lattices, odd extents and misaligned or NULL
+ * pointers return LQCD_ERR_INVALID without launching anything.  Work is
+ * enqueued on cuda_stream (a cudaStream_t; NULL = legacy default stream) and
+ * the call returns without synchronising.  All calls share the one array,
+ * which keeps the last call's partial sums (each call overwrites every slot
+ * it reads, so nothing needs clearing): calls whose work overlaps on the GPU
+ * race, so order them on one stream.  The first call made while a device is
+ * current looks up the array's device address (cudaGetSymbolAddress); make
+ * that first call before any stream capture. */
+int lqcd_plaquette_noalloc(const void *U_lexi, const lqcd_geom *geom, double *plaq_dev,
+                           void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -137,6 +137,7 @@ SIGNATURES = [
     ("lqcd_gauge_copy", _i, [_vp, _vp, _vp]),
     ("lqcd_hmc_trajectory", _i, [_vp, _vp, ctypes.POINTER(lqcd_hmc_params),
                                  ctypes.POINTER(lqcd_hmc_stats)]),
+    ("lqcd_plaquette_noalloc", _i, [_vp, ctypes.POINTER(lqcd_geom), _vp, _vp]),
 ]
 
 
