@@ -421,6 +421,241 @@ def run_variants(ctx, G, fb, fx, lqcd, torch, stream):
     return out
 
 
+# ------------------------------------------------------------------------------
+# The other workloads (--config): one JSON line each, same keys where they apply
+# ------------------------------------------------------------------------------
+
+def _gpu_setup():
+    import torch
+    from paper_1209_5942_gb300 import build, lqcd
+    build.build()
+    torch.cuda.set_device(0)
+    return torch, lqcd, lqcd.Context(0)
+
+
+def _timed(torch, fn, reps=1):
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    out = None
+    for _ in range(reps):
+        out = fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3 / reps, out
+
+
+def _heatbath_field(torch, lqcd, ctx, L, beta, sweeps, seed):
+    """Cold start + `sweeps` Cabibbo-Marinari sweeps with the library's heatbath."""
+    from paper_1209_5942_gb300 import inputs
+    G = lqcd.lqcd_gauge_import(ctx, torch.from_numpy(inputs.random_gauge(L, "cold")).cuda(), L,
+                               recon=18)
+    t, _ = _timed(torch, lambda: [lqcd.lqcd_heatbath_sweep(ctx, G, beta, seed, s)
+                                  for s in range(sweeps)])
+    return G, t, lqcd.lqcd_plaquette(ctx, G)
+
+
+def _solve_variants(torch, lqcd, ctx, G, L, b_h, kappa, mu, combos, nrhs=1, reps=1):
+    bd, _ = lqcd.alloc_field(L, lqcd.LQCD_FULL, lqcd.LQCD_F64, nrhs)
+    xd, _ = lqcd.alloc_field(L, lqcd.LQCD_FULL, lqcd.LQCD_F64, nrhs)
+    fb = lqcd.field(bd, lqcd.LQCD_LAYOUT_EO, nrhs=nrhs)
+    fx = lqcd.field(xd, lqcd.LQCD_LAYOUT_EO, nrhs=nrhs)
+    lqcd.lqcd_spinor_pack(ctx, L, torch.from_numpy(b_h).cuda(), fb)
+    out = {}
+    for outer, inner, recon in combos:
+        prm = lqcd.cg_params(tol=TOL, outer_prec=PREC_NAMES[outer], inner_prec=PREC_NAMES[inner],
+                             max_iter=100000, sloppy_recon=recon, check_every=20)
+        lqcd.lqcd_cg_solve(ctx, G, fb, fx, kappa, mu, prm)  # warm-up (autotuning, graph)
+        lqcd.lib().lqcd_reset_counters(ctx.handle)
+        t, st = _timed(torch, lambda: lqcd.lqcd_cg_solve(ctx, G, fb, fx, kappa, mu, prm), reps)
+        cnt = lqcd.lqcd_counters()
+        lqcd.lib().lqcd_get_counters(ctx.handle, ctypes_byref(cnt))
+        out[f"{outer}/{inner}/rec{recon}"] = {
+            "time_to_solution_s": t, "iters": max(s["iters"] for s in st),
+            "reliable_updates": st[0]["reliable_updates"],
+            "true_resid_max": max(s["true_resid"] for s in st),
+            "solve_GBs": cnt.bytes / reps / t / 1e9}
+    return out
+
+
+def config_line(name, metric_value, extra, workload):
+    line = {"metric": METRIC, "value": metric_value, "unit": "GB/s", "n_gpus": 1,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "data": "synthetic",
+            "config": workload}
+    line.update(extra)
+    line["config_name"] = name
+    print(json.dumps(line), flush=True)
+
+
+def run_config(args):
+    torch, lqcd, ctx = _gpu_setup()
+    from paper_1209_5942_gb300 import inputs
+    peaks, _ = measured_peaks()
+    c = args.config
+    if c == "1":
+        Lc = (4, 4, 4, 4)
+        kappa, mu = 0.15, 0.01 / 0.3
+        U = inputs.random_gauge(Lc, "haar", seed=1001)
+        G = lqcd.lqcd_gauge_import(ctx, torch.from_numpy(U).cuda(), Lc)
+        b = inputs.gaussian_spinor(Lc, 1002)
+        bd = torch.from_numpy(b).cuda()
+        out = torch.zeros_like(bd)
+        fi = lqcd.field(bd, lqcd.LQCD_LAYOUT_LEXI)
+        fo = lqcd.field(out, lqcd.LQCD_LAYOUT_LEXI)
+        lqcd.lqcd_apply_M(ctx, G, fi, fo, kappa, mu)
+        t_m, _ = _timed(torch, lambda: lqcd.lqcd_apply_M(ctx, G, fi, fo, kappa, mu), 200)
+        sol = _solve_variants(torch, lqcd, ctx, G, Lc, b, kappa, mu, [("f64", "f64", 18)], reps=5)
+        config_line("4^4 latency", None, {"apply_M_lexi_us": 1e6 * t_m, "solve": sol},
+                    {"workload": "4^4 Haar, kappa=0.15, 2 kappa mu=0.01 (launch-latency bound)"})
+    elif c == "3":
+        Lc = (32, 32, 32, 64)
+        kappa, mu = 0.157, 0.003 / (2 * 0.157)
+        G, thb, plaq = _heatbath_field(torch, lqcd, ctx, Lc, 5.7, args.sweeps, 3003)
+        b = inputs.gaussian_spinor(Lc, 3004)
+        sol = _solve_variants(torch, lqcd, ctx, G, Lc, b, kappa, mu,
+                              [("f64", "f64", 18), ("df64", "df64", 18), ("df64", "f32", 12),
+                               ("df64", "bf16s", 12), ("df64", "f16s", 12)])
+        best = min(v["time_to_solution_s"] for v in sol.values())
+        config_line("32^3x64 mixed precision", sol["df64/f32/rec12"]["solve_GBs"],
+                    {"heatbath_s": thb, "heatbath_sweeps": args.sweeps, "plaquette": plaq,
+                     "solves": sol, "fastest_time_to_solution_s": best},
+                    {"workload": f"32^3x64, {args.sweeps} CM heatbath sweeps beta=5.7 cold start, "
+                                 "kappa=0.157, 2 kappa mu=0.003, Gaussian source, 1e-10"})
+    elif c == "4a":
+        Lc = (32, 32, 32, 64)
+        kappa, mu = 0.157, 0.003 / (2 * 0.157)
+        G, thb, plaq = _heatbath_field(torch, lqcd, ctx, Lc, 5.7, args.sweeps, 3003)
+        b12 = inputs.point_sources(Lc)
+        multi = _solve_variants(torch, lqcd, ctx, G, Lc, b12, kappa, mu,
+                                [("df64", "f32", 12), ("df64", "df64", 18)], nrhs=12)
+        seq = {}
+        for outer, inner, recon in [("df64", "f32", 12), ("f64", "f64", 18)]:
+            ts, its = 0.0, 0
+            for r in range(12 if not args.quick else 2):
+                s1 = _solve_variants(torch, lqcd, ctx, G, Lc, b12[r], kappa, mu, [(outer, inner, recon)])
+                v = list(s1.values())[0]
+                ts += v["time_to_solution_s"]
+                its = max(its, v["iters"])
+            if args.quick:
+                ts *= 6
+            seq[f"{outer}/{inner}/rec{recon} x12 sequential"] = {"time_s": ts, "iters_max": its}
+        hop = time_hop_multi(ctx, G, lqcd, torch, Lc, 12)
+        config_line("12 point sources, multi-RHS", hop["gbs"],
+                    {"multi_rhs": multi, "sequential": seq, "hop_multi_rhs": hop, "plaquette": plaq},
+                    {"workload": "32^3x64 heatbath field (beta=5.7), 12 unit point sources, "
+                                 "kappa=0.157, 2 kappa mu=0.003, 1e-10"})
+    elif c == "4b":
+        shapes = [(8, 8, 8, 8)] * 8 + [(12, 12, 12, 24)] * 8 + [(16, 16, 16, 32)] * 8 + [(20, 20, 20, 40)] * 8
+        kappa, mu = 0.16, 0.005 / 0.32
+        Gs, fbs, fxs, keep = [], [], [], []
+        for k, Lk in enumerate(shapes):
+            U = inputs.random_gauge(Lk, "near", seed=4000 + k, eps=0.3)
+            G = lqcd.lqcd_gauge_import(ctx, torch.from_numpy(U).cuda(), Lk, recon=12)
+            bd, _ = lqcd.alloc_field(Lk, lqcd.LQCD_FULL, lqcd.LQCD_F64)
+            xd, _ = lqcd.alloc_field(Lk, lqcd.LQCD_FULL, lqcd.LQCD_F64)
+            fb = lqcd.field(bd, lqcd.LQCD_LAYOUT_EO)
+            lqcd.lqcd_spinor_pack(ctx, Lk, torch.from_numpy(inputs.gaussian_spinor(Lk, 5000 + k)).cuda(), fb)
+            Gs.append(G)
+            fbs.append(fb)
+            fxs.append(lqcd.field(xd, lqcd.LQCD_LAYOUT_EO))
+        prm = lqcd.cg_params(tol=TOL, outer_prec=lqcd.LQCD_DF64, inner_prec=lqcd.LQCD_F32,
+                             sloppy_recon=12, check_every=20)
+        n = len(shapes)
+        batch = lambda: lqcd.lqcd_cg_solve_batch(ctx, Gs, fbs, fxs, [kappa] * n, [mu] * n, prm)
+        batch()
+        lqcd.lib().lqcd_reset_counters(ctx.handle)
+        tb, st = _timed(torch, batch)
+        cnt = lqcd.lqcd_counters()
+        lqcd.lib().lqcd_get_counters(ctx.handle, ctypes_byref(cnt))
+        loop = lambda: [lqcd.lqcd_cg_solve(ctx, Gs[k], fbs[k], fxs[k], kappa, mu, prm) for k in range(n)]
+        loop()
+        tl, _ = _timed(torch, loop)
+        config_line("uneven batch", cnt.bytes / tb / 1e9,
+                    {"batched_s": tb, "loop_s": tl, "speedup": tl / tb,
+                     "iters_max": max(s["iters"] for s in st),
+                     "true_resid_max": max(s["true_resid"] for s in st), "gpu_launches": int(cnt.launches)},
+                    {"workload": "8 each of 8^4, 12^3x24, 16^3x32, 20^3x40 (sum V = 3973120), "
+                                 "exp(i 0.3 H) links, kappa=0.16, 2 kappa mu=0.005, F32 inner / DF64 outer"})
+    elif c == "5":
+        Lc = (16, 16, 16, 32)
+        beta, kappa, mu = 5.6, 0.16, 0.005 / 0.32
+        G, thb, plaq0 = _heatbath_field(torch, lqcd, ctx, Lc, beta, args.sweeps, 5005)
+        cg = lqcd.cg_params(tol=1e-10, outer_prec=lqcd.LQCD_DF64, inner_prec=lqcd.LQCD_F32,
+                            sloppy_recon=18, check_every=20)
+        trajs = []
+        for t in range(args.trajs):
+            st = lqcd.lqcd_hmc_trajectory(ctx, G, lqcd.hmc_params(beta, kappa, mu, tau=1.0, nsteps=20,
+                                                                   nf=1, seed=6006, traj=t, cg=cg))
+            trajs.append(st)
+        secs = [s["seconds"] for s in trajs[1:]] or [trajs[0]["seconds"]]
+        config_line("Nf=2 HMC", None,
+                    {"s_per_trajectory": statistics.median(secs),
+                     "dH": [s["dH"] for s in trajs], "accepted": [s["accepted"] for s in trajs],
+                     "acceptance": sum(s["accepted"] for s in trajs) / len(trajs),
+                     "cg_iters_per_trajectory": [s["cg_iters"] for s in trajs],
+                     "exp_minus_dH_mean": float(np.mean([np.exp(-s["dH"]) for s in trajs])),
+                     "plaquette": [s["plaquette"] for s in trajs], "plaquette_after_heatbath": plaq0,
+                     "heatbath_s": thb},
+                    {"workload": f"16^3x32, beta=5.6, kappa=0.16, 2 kappa mu=0.005, {args.sweeps} "
+                                 "heatbath sweeps from cold, leapfrog tau=1 20 steps, "
+                                 "F32-inner/DF64 CG to 1e-10 per force"})
+    elif c == "sweep":
+        res = {}
+        for ns in (16, 24, 32, 48):
+            for nt in (4, 8, 12, 16):
+                Lc = (ns, ns, ns, nt)
+                U = torch.from_numpy(inputs.random_gauge(Lc, "near", seed=7000 + ns + nt, eps=0.3)).cuda()
+                G = {18: lqcd.lqcd_gauge_import(ctx, U, Lc, recon=18),
+                     12: lqcd.lqcd_gauge_import(ctx, U, Lc, recon=12)}
+                row = {}
+                for pname, prec, recon in (("f64", 0, 18), ("df64", 1, 18), ("f32", 2, 12),
+                                           ("bf16s", 3, 12)):
+                    h = time_half_hop_L(ctx, G[recon], lqcd, torch, Lc, prec)
+                    row[pname + f"/rec{recon}"] = {"GBs": h["gbs"],
+                                                   "pct_hbm": 100 * h["gbs"] / peaks["hbm_gbs"],
+                                                   "GFLOPs": 1e3 * h["tflops"]}
+                res[f"{ns}^3x{nt}"] = row
+                G[18].free()
+                G[12].free()
+        config_line("Dslash sweep", None, {"hop": res},
+                    {"workload": "half hop on Ns^3 x Nt, Ns in 16,24,32,48, Nt in 4,8,12,16 "
+                                 "(the paper's lattice range), exp(i 0.3 H) links"})
+
+
+def time_half_hop_L(ctx, G, lqcd, torch, Lc, prec, reps=20):
+    n_half, sb = lqcd.field_bytes(Lc, lqcd.LQCD_EVEN, prec, 1)
+    din = torch.zeros(n_half // 8, dtype=torch.float64, device="cuda")
+    dout = torch.zeros_like(din)
+    s_in = torch.ones(max(sb // 4, 1), dtype=torch.float32, device="cuda") if sb else None
+    s_out = torch.zeros_like(s_in) if sb else None
+    fi = lqcd.field(din, lqcd.LQCD_LAYOUT_EO, prec, 1, s_in)
+    fo = lqcd.field(dout, lqcd.LQCD_LAYOUT_EO, prec, 1, s_out)
+    lqcd.lqcd_dslash(ctx, G, fi, fo, lqcd.LQCD_EVEN, 0)
+    lqcd.lib().lqcd_reset_counters(ctx.handle)
+    t, _ = _timed(torch, lambda: lqcd.lqcd_dslash(ctx, G, fi, fo, lqcd.LQCD_EVEN, 0), reps)
+    cnt = lqcd.lqcd_counters()
+    lqcd.lib().lqcd_get_counters(ctx.handle, ctypes_byref(cnt))
+    return {"ms": 1e3 * t, "gbs": cnt.hop_bytes / reps / t / 1e9, "tflops": cnt.hop_flops / reps / t / 1e12}
+
+
+def time_hop_multi(ctx, G, lqcd, torch, Lc, nrhs, prec=2, reps=10):
+    """Multi-RHS half hop: counted bytes read each link once for all RHS."""
+    n_half, sb = lqcd.field_bytes(Lc, lqcd.LQCD_EVEN, prec, nrhs)
+    din = torch.zeros(n_half // 8, dtype=torch.float64, device="cuda")
+    dout = torch.zeros_like(din)
+    fi = lqcd.field(din, lqcd.LQCD_LAYOUT_EO, prec, nrhs)
+    fo = lqcd.field(dout, lqcd.LQCD_LAYOUT_EO, prec, nrhs)
+    lqcd.lqcd_dslash(ctx, G, fi, fo, lqcd.LQCD_EVEN, 0)
+    lqcd.lib().lqcd_reset_counters(ctx.handle)
+    t, _ = _timed(torch, lambda: lqcd.lqcd_dslash(ctx, G, fi, fo, lqcd.LQCD_EVEN, 0), reps)
+    cnt = lqcd.lqcd_counters()
+    lqcd.lib().lqcd_get_counters(ctx.handle, ctypes_byref(cnt))
+    per_rhs_site = cnt.hop_bytes / reps / cnt.hop_sites * reps
+    return {"ms": 1e3 * t, "gbs": cnt.hop_bytes / reps / t / 1e9, "nrhs": nrhs, "prec": prec,
+            "bytes_per_rhs_site": per_rhs_site}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -436,11 +671,18 @@ def main():
                     help="ncu dram bytes per launch of the half hop, if captured")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--variants", action="store_true")
+    ap.add_argument("--config", default="2", choices=["1", "2", "3", "4a", "4b", "5", "sweep"],
+                    help="2 (default): the 24^3x48 contract line; others print their own line")
+    ap.add_argument("--sweeps", type=int, default=200, help="heatbath sweeps for configs 3, 4a, 5")
+    ap.add_argument("--trajs", type=int, default=4, help="HMC trajectories for config 5")
+    ap.add_argument("--quick", action="store_true", help="config 4a: 2 sequential solves, scaled")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.config != "2":
+        run_config(args)
     else:
         run_gpu(args)
 

@@ -144,6 +144,16 @@ typedef struct {
 int lqcd_get_counters(const lqcd_ctx *ctx, lqcd_counters *out);
 int lqcd_reset_counters(lqcd_ctx *ctx);
 
+/* Launch-shape autotuner (on by default).  The first launch of each kernel
+ * configuration (kernel, precision, link format, variant, lattice extents,
+ * number of right-hand sides, GPU) made outside a stream capture times every
+ * candidate block shape with CUDA events on the context's stream and keeps the
+ * fastest; results never depend on the shape.  enable = 0 uses the built-in
+ * defaults for configurations not yet tuned.  cache_path (may be NULL) names a
+ * JSON file from which choices are loaded now and to which new ones are
+ * written, so other processes skip the timing. */
+int lqcd_set_autotune(lqcd_ctx *ctx, int enable, const char *cache_path);
+
 /* Bytes needed for a field of the given parity (LQCD_FULL or one parity),
  * precision and nrhs in the EO layout; *scale_bytes receives the size of the
  * scale array (0 for unscaled precisions).  Returns 0 on invalid input. */

@@ -1,0 +1,48 @@
+"""torch.autograd.Function for the pseudofermion action (Sec. 2, eq. "pseudo
+fermions"; Sec. 2.2, fermion force through dD^-1 = -D^-1 dD D^-1).
+
+``FermionAction.apply(omega, U, phi, kappa, mu, params)`` returns
+S = phi^+ (Mhat^+ Mhat)^-1 phi for the gauge field U and the even-site
+pseudofermion phi.  omega (float64 [4, V, 8], normally zeros) holds the
+algebra coordinates of a variation U_mu(x) -> exp(i omega^a T^a) U_mu(x), so
+dS/domega is the derivative with respect to every link.  The forward pass
+calls ``lqcd_fermion_force`` (one CG solve X = (Mhat^+ Mhat)^-1 phi and one
+adjoint kernel over all links); the backward pass returns dS/domega times the
+incoming gradient.  With ``recompute=True`` the forward pass keeps nothing
+but the inputs and the backward pass solves for X again, trading a second
+solve for the memory of the [4, V, 8] gradient.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import lqcd
+
+
+class FermionAction(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx_, omega: torch.Tensor, U: "lqcd.Gauge", phi: "lqcd.lqcd_field", kappa: float,
+                mu: float, params: "lqcd.lqcd_cg_params", recompute: bool = False):
+        if omega.dtype != torch.float64 or not omega.is_cuda or omega.dim() != 3:
+            raise ValueError("omega must be a CUDA float64 tensor [4, V, 8]")
+        grad = torch.empty_like(omega)
+        S, _ = lqcd.lqcd_fermion_force(U.ctx, U, phi, grad, kappa, mu, params)
+        ctx_.U, ctx_.phi, ctx_.kappa, ctx_.mu, ctx_.params = U, phi, kappa, mu, params
+        ctx_.recompute = recompute
+        if recompute:
+            del grad
+            ctx_.grad = None
+            ctx_.shape = omega.shape
+        else:
+            ctx_.grad = grad
+        return omega.new_tensor(S)
+
+    @staticmethod
+    def backward(ctx_, grad_out):
+        if ctx_.recompute:
+            grad = torch.empty(ctx_.shape, dtype=torch.float64, device="cuda")
+            lqcd.lqcd_fermion_force(ctx_.U.ctx, ctx_.U, ctx_.phi, grad, ctx_.kappa, ctx_.mu,
+                                    ctx_.params)
+        else:
+            grad = ctx_.grad
+        return grad * grad_out, None, None, None, None, None, None

@@ -5,7 +5,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <cstdlib>
 #include <new>
+#include <string>
 
 #include "internal.h"
 
@@ -188,6 +190,13 @@ extern "C" int lqcd_create(lqcd_ctx **out, int device, void *stream) {
   c->device = device;
   c->stream = (cudaStream_t)stream;
   cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) == cudaSuccess)
+    c->gpu_name = std::string(prop.name) + "/" + std::to_string(prop.multiProcessorCount);
+  if (const char *tp = std::getenv("LQCD_TUNE_CACHE")) {
+    c->tune_path = tp;
+    tune_load(c);
+  }
   if (ensure_partials(c, 1 << 16) != LQCD_OK || ensure_pinned(c, 4096) != LQCD_OK) {
     lqcd_destroy(c);
     return LQCD_ERR_OOM;

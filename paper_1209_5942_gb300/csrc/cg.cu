@@ -190,8 +190,12 @@ __global__ void __launch_bounds__(128) cg_xs_kernel(VecArgs a, SolverHdr *h, voi
     SpinorIO<P>::store(sv(a, x, xs, r), cb, X);
     SpinorIO<P>::store(sv(a, s, ss, r), cb, S);
   }
-  double t = warp_block_sum(nrm, sh);
-  if (threadIdx.x == 0) partials[(size_t)r * gridDim.x + blockIdx.x] = t;
+  // one partial per warp of 32 sites (the grouping of the hop kernels and of
+  // the batched solver, so all of them reduce in the same order)
+  (void)sh;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) nrm += __shfl_down_sync(0xffffffffu, nrm, o);
+  if ((threadIdx.x & 31) == 0 && cb < a.Vh) partials[(size_t)r * ((a.Vh + 31) >> 5) + (cb >> 5)] = nrm;
 }
 
 // p = z + beta p
@@ -533,6 +537,7 @@ lqcd_status cgls_even(lqcd_ctx *ctx, lqcd_gauge *U, const Geom &g, double kappa,
   }
   int nb = hop_blocks(g, nrhs);
   int nbv = (Vh + 127) / 128;
+  const int nbw = (Vh + 31) / 32;  // per-warp partials of cg_xs_kernel
   LQCD_TRY(ensure_partials(ctx, (size_t)nrhs * (nb > nbv ? nb : nbv)));
   SolverHdr *h;
   LQCD_TRY(ensure_state(ctx, nrhs, &h));
@@ -574,7 +579,7 @@ lqcd_status cgls_even(lqcd_ctx *ctx, lqcd_gauge *U, const Geom &g, double kappa,
             va, h, X.ptr, X.scale, p.f.ptr, p.f.scale, s.f.ptr, s.f.scale, q.f.ptr, q.f.scale,
             ctx->partials);
       }));
-      launch_finalize(ctx, h, nrhs, nbv, FIN_SS, nullptr);
+      launch_finalize(ctx, h, nrhs, nbw, FIN_SS, nullptr);
       LQCD_TRY(apply_schur(Oi, s.f, z.f, t.f, 0, true, ctx->partials, &nb, &h->halt));
       launch_finalize(ctx, h, nrhs, nb, FIN_BETA, nullptr);
     } else {
@@ -586,8 +591,8 @@ lqcd_status cgls_even(lqcd_ctx *ctx, lqcd_gauge *U, const Geom &g, double kappa,
             va, h, X.ptr, X.scale, p.f.ptr, p.f.scale, z.f.ptr, z.f.scale, s.f.ptr, s.f.scale,
             ctx->partials);
       }));
-      launch_finalize(ctx, h, nrhs, nbv, FIN_SS, nullptr);
-      launch_finalize(ctx, h, nrhs, nbv, FIN_BETA, nullptr);
+      launch_finalize(ctx, h, nrhs, nbw, FIN_SS, nullptr);
+      launch_finalize(ctx, h, nrhs, nbw, FIN_BETA, nullptr);
     }
     count_launch(ctx, (double)Vh * nrhs * spinor_site_bytes(inner) * 3.0);
     LQCD_TRY(dispatch_prec(ctx, inner, [&](auto P) {

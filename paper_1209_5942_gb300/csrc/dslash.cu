@@ -209,12 +209,12 @@ LQCD_DEV void hop_dir(const HopArgs &A, const Site &s, int p, int cb, const Spin
   }
 }
 
+// Output site cb (of parity A.out_parity) for right-hand side rhs: the hop,
+// the epilogue, the store and (REDUCE) the warp's |out|^2 partial.  All 32
+// lanes of a warp must call it together (the partial uses a shuffle).
 template <int PREC, int RECON, bool DAG, bool REDUCE>
-__global__ void __launch_bounds__(256) hop_kernel(HopArgs A) {
+LQCD_DEV void hop_site(const HopArgs &A, int cb, int rhs) {
   using R = typename SpinorIO<PREC>::R;
-  if (A.halt && *(volatile int *)A.halt) return;
-  const int cb = blockIdx.x * blockDim.x + threadIdx.x;
-  const int rhs = blockIdx.z * blockDim.y + threadIdx.y;
   const int p = A.out_parity;
   const bool active = cb < A.g.Vh && rhs < A.nrhs;
   double nrm = 0.0;
@@ -263,6 +263,178 @@ __global__ void __launch_bounds__(256) hop_kernel(HopArgs A) {
   }
 }
 
+// Grid-stride over the output sites: a full grid (one site per thread) or a
+// smaller persistent grid, whichever the autotuner finds faster.
+template <int PREC, int RECON, bool DAG, bool REDUCE>
+__global__ void __launch_bounds__(256) hop_kernel(HopArgs A) {
+  if (A.halt && *(volatile int *)A.halt) return;
+  const int rhs = blockIdx.z * blockDim.y + threadIdx.y;
+  const int stride = gridDim.x * blockDim.x;
+  for (int base = blockIdx.x * blockDim.x; base < A.g.Vh; base += stride)
+    hop_site<PREC, RECON, DAG, REDUCE>(A, base + threadIdx.x, rhs);
+}
+
+// ---------------------------------------------------------------------------
+// Float-float hop with two threads per output site.  Thread k (lane parity)
+// owns upper spin component k: it projects only h_k, multiplies it by the
+// link one row (forward) or column (backward) at a time, and accumulates the
+// upper spin k plus two partial lower spins: the one receiving v_k in the x,y
+// directions (spin 3-k) and the one receiving it in z,t (spin 2+k).  The
+// partner lane's x,y partial completes lower spin 2+k through one shuffle.
+// Per thread this halves the dependent float-float chains and the register
+// footprint, so twice as many warps hide the FP32 latency.
+// ---------------------------------------------------------------------------
+template <int MU, int S>
+LQCD_DEV void df_pair_dir(const HopArgs &A, const Site &s, int p, int cb, int k, const SpinorView &vin,
+                          Cx<df> up[3], Cx<df> lswap[3], Cx<df> lsame[3]) {
+  const float4 *pin = (const float4 *)vin.ptr;
+#pragma unroll
+  for (int dir = 0; dir < 2; dir++) {
+    const int sgn = dir == 0 ? S : -S;  // projector sign: (1 - S g) forward, (1 + S g) backward
+    const int j = neighbour_cb(A.g, s, MU, dir == 0 ? +1 : -1);
+    const int lo = (MU < 2) ? 3 - k : 2 + k;  // lower spin paired with upper k in h_k
+    Cx<df> h[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      float4 a = __ldg(pin + (size_t)(3 * k + c) * vin.Vh + j);
+      float4 b = __ldg(pin + (size_t)(3 * lo + c) * vin.Vh + j);
+      Cx<df> pa = {{a.x, a.z}, {a.y, a.w}}, pb = {{b.x, b.z}, {b.y, b.w}};
+      // h_k = p_k + f * p_lo with f = S*i (x), S*(+-1) (y), S*(+-i) (z), -S (t)
+      const bool neg = (MU == 0) ? sgn < 0 : (MU == 1) ? (k == 0 ? sgn < 0 : sgn > 0)
+                     : (MU == 2) ? (k == 0 ? sgn < 0 : sgn > 0) : sgn > 0;
+      Cx<df> t = (MU == 0 || MU == 2) ? times_i(pb) : pb;
+      h[c] = neg ? pa - t : pa + t;
+    }
+    const float4 *ub = (const float4 *)((const char *)A.U.ptr + (dir == 0 ? p : p ^ 1) * A.U.parity_stride +
+                                        MU * A.U.mu_stride);
+    const int lc = dir == 0 ? cb : j;
+    Cx<df> v[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      Cx<df> u3[3];
+#pragma unroll
+      for (int q = 0; q < 3; q++) {  // forward: row a of U; backward: column a
+        float4 w = __ldg(ub + (size_t)(dir == 0 ? 3 * a + q : 3 * q + a) * A.U.Vh + lc);
+        u3[q] = {{w.x, w.z}, {w.y, w.w}};
+      }
+      v[a] = dir == 0 ? dfdot3<false>(u3[0], u3[1], u3[2], h[0], h[1], h[2])
+                      : dfdot3<true>(u3[0], u3[1], u3[2], h[0], h[1], h[2]);
+    }
+    if (MU == 3 && A.g.antiper && s.t == (dir == 0 ? A.g.L[3] - 1 : 0)) {
+#pragma unroll
+      for (int a = 0; a < 3; a++) v[a] = -v[a];
+    }
+    // lower-spin factor of v_k: -sgn*i (x, to 3-k), (k==0 ? +sgn : -sgn) (y, to 3-k),
+    // (k==0 ? -sgn*i : +sgn*i) (z, to 2+k), -sgn (t, to 2+k)
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      up[a] = up[a] + v[a];
+      if (MU == 0) lswap[a] = sgn > 0 ? lswap[a] - times_i(v[a]) : lswap[a] + times_i(v[a]);
+      else if (MU == 1) lswap[a] = ((k == 0) == (sgn > 0)) ? lswap[a] + v[a] : lswap[a] - v[a];
+      else if (MU == 2) lsame[a] = ((k == 0) == (sgn > 0)) ? lsame[a] - times_i(v[a]) : lsame[a] + times_i(v[a]);
+      else lsame[a] = sgn > 0 ? lsame[a] - v[a] : lsame[a] + v[a];
+    }
+  }
+}
+
+template <bool DAG, bool REDUCE>
+__global__ void __launch_bounds__(128) hop_df64_pair_kernel(HopArgs A) {
+  __shared__ double sh[8][4];
+  if (A.halt && *(volatile int *)A.halt) return;
+  const int rhs = blockIdx.z * blockDim.y + threadIdx.y;
+  const int k = threadIdx.x & 1;
+  const int sites_per_block = blockDim.x >> 1;
+  const int stride = gridDim.x * sites_per_block;
+  for (int base = blockIdx.x * sites_per_block; base < A.g.Vh; base += stride) {
+    const int cb = base + (threadIdx.x >> 1);
+    const bool active = cb < A.g.Vh && rhs < A.nrhs;
+    double nrm = 0.0;
+    Cx<df> up[3], lswap[3], lsame[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) up[a] = lswap[a] = lsame[a] = czero<df>();
+    const int p = A.out_parity;
+    Site s{};
+    if (active) {
+      s = site_of(A.g, p, cb);
+      SpinorView vin{A.in + rhs * A.in_rs, nullptr, A.g.Vh};
+      constexpr int S = DAG ? -1 : 1;
+      df_pair_dir<0, S>(A, s, p, cb, k, vin, up, lswap, lsame);
+      df_pair_dir<1, S>(A, s, p, cb, k, vin, up, lswap, lsame);
+      df_pair_dir<2, S>(A, s, p, cb, k, vin, up, lswap, lsame);
+      df_pair_dir<3, S>(A, s, p, cb, k, vin, up, lswap, lsame);
+    }
+    // lower spin 2+k = own z,t partial + partner's x,y partial
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      Cx<df> o;
+      o.re.hi = __shfl_xor_sync(0xffffffffu, lswap[a].re.hi, 1);
+      o.re.lo = __shfl_xor_sync(0xffffffffu, lswap[a].re.lo, 1);
+      o.im.hi = __shfl_xor_sync(0xffffffffu, lswap[a].im.hi, 1);
+      o.im.lo = __shfl_xor_sync(0xffffffffu, lswap[a].im.lo, 1);
+      lsame[a] = lsame[a] + o;
+    }
+    if (active) {
+      const Cx<df> cu = cfrom<df>(A.c_up), cd = cfrom<df>(A.c_dn);
+      Cx<df> ru[3], rl[3];
+#pragma unroll
+      for (int a = 0; a < 3; a++) {
+        ru[a] = cu * up[a];
+        rl[a] = cd * lsame[a];
+      }
+      if (A.has_aux) {
+        const float4 *pa = (const float4 *)(A.aux + rhs * A.aux_rs);
+        const Cx<df> du = cfrom<df>(A.d_up), dd = cfrom<df>(A.d_dn);
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+          float4 w1 = __ldg(pa + (size_t)(3 * k + a) * A.g.Vh + cb);
+          float4 w2 = __ldg(pa + (size_t)(3 * (2 + k) + a) * A.g.Vh + cb);
+          ru[a] = cmadd(du, Cx<df>{{w1.x, w1.z}, {w1.y, w1.w}}, ru[a]);
+          rl[a] = cmadd(dd, Cx<df>{{w2.x, w2.z}, {w2.y, w2.w}}, rl[a]);
+        }
+      }
+      float4 *po = (float4 *)(A.out + rhs * A.out_rs);
+#pragma unroll
+      for (int a = 0; a < 3; a++) {
+        po[(size_t)(3 * k + a) * A.g.Vh + cb] = make_float4(ru[a].re.hi, ru[a].im.hi, ru[a].re.lo, ru[a].im.lo);
+        po[(size_t)(3 * (2 + k) + a) * A.g.Vh + cb] =
+            make_float4(rl[a].re.hi, rl[a].im.hi, rl[a].re.lo, rl[a].im.lo);
+        if (REDUCE) nrm += norm2_d(ru[a]) + norm2_d(rl[a]);
+      }
+    }
+    if (REDUCE) {
+      // 32 sites = 64 threads = two warps of one block row: warp sums, then
+      // the even warp adds its odd neighbour (fixed order)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) nrm += __shfl_down_sync(0xffffffffu, nrm, o);
+      const int w = threadIdx.x >> 5;
+      if ((threadIdx.x & 31) == 0) sh[threadIdx.y][w] = nrm;
+      __syncthreads();
+      const int cb0 = base + ((threadIdx.x >> 6) << 5);  // first site of this 32-site group
+      if ((threadIdx.x & 63) == 0 && rhs < A.nrhs && cb0 < A.g.Vh) {
+        const int nw = (A.g.Vh + 31) >> 5;
+        A.partials[(size_t)rhs * nw + (cb0 >> 5)] = sh[threadIdx.y][w] + sh[threadIdx.y][w + 1];
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Persistent batched hop over lattices of different sizes: a fixed grid of
+// blocks walks a queue of tiles (system, first site) in round-robin order;
+// each tile is 128 output sites of one system, whose HopArgs (geometry,
+// links, fields, coefficients, partials) are read from `descs`.  The order of
+// tiles per block is fixed, so results and partials are reproducible.
+template <int PREC, int RECON, bool DAG, bool REDUCE>
+__global__ void __launch_bounds__(128) hop_batched_kernel(const HopArgs *descs, const int2 *tiles,
+                                                          int ntiles, const int *halt) {
+  if (halt && *(volatile const int *)halt) return;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int2 tile = tiles[t];
+    const HopArgs A = descs[tile.x];
+    hop_site<PREC, RECON, DAG, REDUCE>(A, tile.y + threadIdx.x, 0);
+  }
+}
+
 // number of reduction partials per right-hand side written by a reducing hop
 int hop_blocks(const Geom &g, int nrhs) {
   (void)nrhs;
@@ -306,35 +478,84 @@ lqcd_status launch_hop(lqcd_ctx *ctx, const Geom &g, const HopLaunch &L, int *nb
   A.partials = L.partials;
   A.halt = L.halt;
   const int nrhs = L.out.nrhs;
-  dim3 block, grid;
-  if (nrhs == 1) {
-    block = dim3(128, 1, 1);
-    grid = dim3((g.Vh + 127) / 128, 1, 1);
-  } else {
-    int by = nrhs < 8 ? nrhs : 8;
-    block = dim3(32, by, 1);
-    grid = dim3((g.Vh + 31) / 32, 1, (nrhs + by - 1) / by);
-  }
   if (nblocks_out) *nblocks_out = hop_blocks(g, nrhs);
   const bool dag = L.dagger != 0, red = L.partials != nullptr;
-  cudaStream_t st = ctx->stream;
-  switch (L.prec) {
-    case LQCD_F64:
-      if (L.recon == 12) launch_t<LQCD_F64, 12>(A, grid, block, dag, red, st);
-      else launch_t<LQCD_F64, 18>(A, grid, block, dag, red, st);
-      break;
-    case LQCD_DF64:
-      if (L.recon == 12) launch_t<LQCD_DF64, 12>(A, grid, block, dag, red, st);
-      else launch_t<LQCD_DF64, 18>(A, grid, block, dag, red, st);
-      break;
-    case LQCD_F32:
-      if (L.recon == 12) launch_t<LQCD_F32, 12>(A, grid, block, dag, red, st);
-      else launch_t<LQCD_F32, 18>(A, grid, block, dag, red, st);
-      break;
-    case LQCD_BF16S: launch_t<LQCD_BF16S, 12>(A, grid, block, dag, red, st); break;
-    case LQCD_F16S: launch_t<LQCD_F16S, 12>(A, grid, block, dag, red, st); break;
-    default: return fail(ctx, LQCD_ERR_INVALID, "launch_hop: bad precision %d", L.prec);
+  if (L.prec < LQCD_F64 || L.prec > LQCD_F16S)
+    return fail(ctx, LQCD_ERR_INVALID, "launch_hop: bad precision %d", L.prec);
+  // candidate launch shapes: (sites x 1) blocks for one RHS, (32 sites x by
+  // RHS) blocks for several; results do not depend on the shape
+  // (x 3 grid sizes: one site per thread, or a persistent grid of 4 or 8
+  // blocks per SM walking the sites)
+  static const int BX1[3] = {64, 128, 256};
+  static const int BY[4] = {1, 2, 4, 8};
+  static const int GRIDMUL[3] = {0, 4, 8};
+  int nshape = 3, fallback = 1;
+  if (nrhs > 1) {
+    nshape = 0;
+    for (int k = 0; k < 4; k++)
+      if (BY[k] <= nrhs) nshape = k + 1;
+    fallback = nshape - 1;
   }
+  const int ncand = 3 * nshape;
+  const bool pair = L.prec == LQCD_DF64 && L.recon == 18;  // two threads per site
+  auto go = [&](int cand, const HopArgs &args) {
+    const int c = cand % nshape, gm = GRIDMUL[cand / nshape];
+    dim3 block, grid;
+    if (pair) {
+      // (64 or 128 threads = 32 or 64 sites) x by right-hand sides
+      const int bx = (nrhs == 1 && c >= 1) ? 128 : 64;
+      block = dim3(bx, nrhs == 1 ? 1 : BY[c], 1);
+      grid = dim3((g.Vh + bx / 2 - 1) / (bx / 2), 1, nrhs == 1 ? 1 : (nrhs + BY[c] - 1) / BY[c]);
+      if (gm > 0) {
+        unsigned cap = (unsigned)(ctx->num_sms * gm);
+        if (grid.x > cap) grid.x = cap;
+      }
+      cudaStream_t st = ctx->stream;
+      if (dag) {
+        if (red) hop_df64_pair_kernel<true, true><<<grid, block, 0, st>>>(args);
+        else hop_df64_pair_kernel<true, false><<<grid, block, 0, st>>>(args);
+      } else {
+        if (red) hop_df64_pair_kernel<false, true><<<grid, block, 0, st>>>(args);
+        else hop_df64_pair_kernel<false, false><<<grid, block, 0, st>>>(args);
+      }
+      return;
+    }
+    if (nrhs == 1) {
+      block = dim3(BX1[c], 1, 1);
+      grid = dim3((g.Vh + BX1[c] - 1) / BX1[c], 1, 1);
+    } else {
+      block = dim3(32, BY[c], 1);
+      grid = dim3((g.Vh + 31) / 32, 1, (nrhs + BY[c] - 1) / BY[c]);
+    }
+    if (gm > 0) {
+      unsigned cap = (unsigned)(ctx->num_sms * gm);
+      if (grid.x > cap) grid.x = cap;
+    }
+    cudaStream_t st = ctx->stream;
+    switch (L.prec) {
+      case LQCD_F64:
+        if (L.recon == 12) launch_t<LQCD_F64, 12>(args, grid, block, dag, red, st);
+        else launch_t<LQCD_F64, 18>(args, grid, block, dag, red, st);
+        break;
+      case LQCD_DF64:
+        if (L.recon == 12) launch_t<LQCD_DF64, 12>(args, grid, block, dag, red, st);
+        else launch_t<LQCD_DF64, 18>(args, grid, block, dag, red, st);
+        break;
+      case LQCD_F32:
+        if (L.recon == 12) launch_t<LQCD_F32, 12>(args, grid, block, dag, red, st);
+        else launch_t<LQCD_F32, 18>(args, grid, block, dag, red, st);
+        break;
+      case LQCD_BF16S: launch_t<LQCD_BF16S, 12>(args, grid, block, dag, red, st); break;
+      default: launch_t<LQCD_F16S, 12>(args, grid, block, dag, red, st); break;
+    }
+  };
+  char key[160];
+  snprintf(key, sizeof(key), "hop|p%d|r%d|d%d|red%d|aux%d|%dx%dx%dx%d|n%d", L.prec, L.recon, (int)dag, (int)red,
+           A.has_aux, g.L[0], g.L[1], g.L[2], g.L[3], nrhs);
+  HopArgs At = A;
+  At.halt = nullptr;  // timing launches run whatever the solver state
+  const int choice = tune_choice(ctx, key, ncand, fallback, [&](int c) { go(c, At); });
+  go(choice, A);
   LQCD_CUDA(ctx, cudaGetLastError());
   // algorithmic work: per output site 8 links, the input spinor once, the
   // output (and aux) spinor; 1320 flops for the hop + 48 per epilogue term
@@ -350,6 +571,66 @@ lqcd_status launch_hop(lqcd_ctx *ctx, const Geom &g, const HopLaunch &L, int *nb
   ctx->cnt.hop_flops += flops;
   ctx->cnt.hop_sites += sites;
   return LQCD_OK;
+}
+
+// Launches the batched hop: descs[nsys] on the device (one per system, each
+// with its own geometry, fields and coefficients), tiles[ntiles] = (system,
+// first cb) with 128-site tiles.  All systems share precision and recon.
+lqcd_status launch_hop_batched(lqcd_ctx *ctx, int prec, int recon, bool dagger, bool reduce,
+                               const void *descs, const void *tiles, int ntiles, int grid, const int *halt) {
+  const HopArgs *d = (const HopArgs *)descs;
+  const int2 *tl = (const int2 *)tiles;
+  cudaStream_t st = ctx->stream;
+#define LQCD_HB(P, RC)                                                                                   \
+  do {                                                                                                   \
+    if (dagger) {                                                                                        \
+      if (reduce) hop_batched_kernel<P, RC, true, true><<<grid, 128, 0, st>>>(d, tl, ntiles, halt);      \
+      else hop_batched_kernel<P, RC, true, false><<<grid, 128, 0, st>>>(d, tl, ntiles, halt);            \
+    } else {                                                                                             \
+      if (reduce) hop_batched_kernel<P, RC, false, true><<<grid, 128, 0, st>>>(d, tl, ntiles, halt);     \
+      else hop_batched_kernel<P, RC, false, false><<<grid, 128, 0, st>>>(d, tl, ntiles, halt);           \
+    }                                                                                                    \
+  } while (0)
+  switch (prec) {
+    case LQCD_F64: if (recon == 12) LQCD_HB(LQCD_F64, 12); else LQCD_HB(LQCD_F64, 18); break;
+    case LQCD_DF64: if (recon == 12) LQCD_HB(LQCD_DF64, 12); else LQCD_HB(LQCD_DF64, 18); break;
+    case LQCD_F32: if (recon == 12) LQCD_HB(LQCD_F32, 12); else LQCD_HB(LQCD_F32, 18); break;
+    case LQCD_BF16S: LQCD_HB(LQCD_BF16S, 12); break;
+    case LQCD_F16S: LQCD_HB(LQCD_F16S, 12); break;
+    default: return fail(ctx, LQCD_ERR_INVALID, "batched hop: bad precision");
+  }
+#undef LQCD_HB
+  LQCD_CUDA(ctx, cudaGetLastError());
+  return LQCD_OK;
+}
+
+// Host-side HopArgs for a HopLaunch (what launch_hop passes to the kernel).
+size_t hop_args_size() { return sizeof(HopArgs); }
+void hop_args_fill(const Geom &g, const HopLaunch &L, void *dst) {
+  HopArgs &A = *(HopArgs *)dst;
+  A.g = g;
+  A.U = L.U;
+  A.in = (char *)L.in.ptr;
+  A.out = (char *)L.out.ptr;
+  A.aux = (const char *)L.aux.ptr;
+  A.in_scale = L.in.scale;
+  A.out_scale = L.out.scale;
+  A.aux_scale = L.aux.scale;
+  A.in_rs = L.in.rhs_stride;
+  A.out_rs = L.out.rhs_stride;
+  A.aux_rs = L.aux.rhs_stride;
+  A.in_srs = L.in.scale_rhs_stride;
+  A.out_srs = L.out.scale_rhs_stride;
+  A.aux_srs = L.aux.scale_rhs_stride;
+  A.out_parity = L.out_parity;
+  A.nrhs = 1;
+  A.has_aux = L.has_aux ? 1 : 0;
+  A.c_up = L.c_up;
+  A.c_dn = L.c_dn;
+  A.d_up = L.d_up;
+  A.d_dn = L.d_dn;
+  A.partials = L.partials;
+  A.halt = nullptr;
 }
 
 }  // namespace lqcd

@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include <functional>
+#include <map>
 #include <string>
 #include <type_traits>
 #include <vector>
@@ -25,6 +27,11 @@ struct lqcd_ctx {
   size_t solver_state_cap = 0;
   // algorithmic work counters (lqcd_get_counters)
   lqcd_counters cnt{};
+  // launch-shape autotuner (tune.cu)
+  int autotune = 1;
+  std::string tune_path;
+  std::string gpu_name;
+  std::map<std::string, int> tuned;
 };
 
 struct lqcd_gauge {
@@ -77,6 +84,21 @@ struct HalfField {
   size_t rhs_stride = 0;        // bytes between right-hand sides
   size_t scale_rhs_stride = 0;  // floats between right-hand sides
 };
+
+// batched hop (dslash.cu): descs = device HopArgs[nsys], tiles = device int2[ntiles]
+struct HopLaunch;
+lqcd_status launch_hop_batched(lqcd_ctx *ctx, int prec, int recon, bool dagger, bool reduce,
+                               const void *descs, const void *tiles, int ntiles, int grid, const int *halt);
+size_t hop_args_size();
+void hop_args_fill(const Geom &g, const HopLaunch &L, void *dst);
+
+// Autotuner (tune.cu): returns the index of the fastest of `ncand` launch
+// shapes for `key`, timing run(i) (which enqueues one launch of candidate i on
+// ctx->stream) with CUDA events the first time the key is seen outside a
+// stream capture; returns `fallback` when tuning is off or not possible.
+int tune_choice(lqcd_ctx *ctx, const std::string &key, int ncand, int fallback,
+                const std::function<void(int)> &run);
+void tune_load(lqcd_ctx *ctx);
 
 // work counters: one launch moving `bytes` algorithmic bytes
 inline void count_launch(lqcd_ctx *ctx, double bytes) {

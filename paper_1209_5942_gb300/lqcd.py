@@ -103,6 +103,7 @@ SIGNATURES = [
     ("lqcd_set_stream", _i, [_vp, _vp]),
     ("lqcd_last_error", ctypes.c_char_p, [_vp]),
     ("lqcd_get_counters", _i, [_vp, _vp]),
+    ("lqcd_set_autotune", _i, [_vp, _i, ctypes.c_char_p]),
     ("lqcd_reset_counters", _i, [_vp]),
     ("lqcd_field_bytes", ctypes.c_size_t, [ctypes.POINTER(lqcd_geom), _i, _i, _i,
                                            ctypes.POINTER(ctypes.c_size_t)]),
@@ -170,7 +171,7 @@ def declared_symbols() -> list[str]:
     hdr = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
                        "lqcd.h")
     txt = open(hdr).read()
-    return sorted(set(re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_ \*]*?\b(lqcd_[a-z0-9_]+)\s*\(",
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_ \*]*?\b(lqcd_[A-Za-z0-9_]+)\s*\(",
                                  txt, flags=re.M)))
 
 

@@ -103,8 +103,11 @@ def test_apply_Mhat_even(ctx, oracle, L, prec, dagger, recon):
                                   lqcd.LQCD_F16S])
 @pytest.mark.parametrize("out_parity", [lqcd.LQCD_EVEN, lqcd.LQCD_ODD])
 @pytest.mark.parametrize("dagger", [False, True])
-def test_dslash_half_hop(ctx, oracle, L, prec, out_parity, dagger):
-    U, G = _gauge(ctx, L, seed=6, recon=12)
+@pytest.mark.parametrize("recon", [12, 18])
+def test_dslash_half_hop(ctx, oracle, L, prec, out_parity, dagger, recon):
+    if recon == 18 and prec in (lqcd.LQCD_BF16S, lqcd.LQCD_F16S):
+        pytest.skip("16-bit links are stored in REC12 form only")
+    U, G = _gauge(ctx, L, seed=6, recon=recon)
     odd = oracle.parity_mask(L)
     src_mask = odd if out_parity == lqcd.LQCD_EVEN else ~odd
     psi = inputs.gaussian_spinor(L, 10) * src_mask[:, None, None]
@@ -125,9 +128,11 @@ def test_multi_rhs_dslash_matches_single(ctx, oracle):
     """The multi-RHS launch (link loaded once per site for all RHS) gives the
     single-RHS result bit for bit in every precision."""
     L = (4, 4, 6, 8)
-    U, G = _gauge(ctx, L, seed=12, recon=12)
+    U, G12 = _gauge(ctx, L, seed=12, recon=12)
+    G18 = lqcd.lqcd_gauge_import(ctx, dev(U), L, recon=18)
     nrhs = 12
-    for prec in (lqcd.LQCD_F64, lqcd.LQCD_F32, lqcd.LQCD_BF16S):
+    for prec, G in ((lqcd.LQCD_F64, G12), (lqcd.LQCD_F32, G12), (lqcd.LQCD_BF16S, G12),
+                    (lqcd.LQCD_DF64, G18), (lqcd.LQCD_DF64, G12)):
         psis = inputs.gaussian_spinor(L, 13, nrhs=nrhs)
         n_half, sb_half = lqcd.field_bytes(L, lqcd.LQCD_EVEN, prec, 1)
         din = torch.zeros(nrhs * n_half // 8, dtype=torch.float64, device="cuda")
