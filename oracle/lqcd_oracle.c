@@ -980,7 +980,8 @@ static int su2_sample_y0(double b, uint32_t c0, uint32_t c1, uint32_t c2, uint64
     double u12[2], u34[2];
     philox_uniform2(c0, c1, c2, (uint32_t)(2 * n), seed, u12);
     if (b < HB_B_SWITCH) {
-      double y = 1.0 + log1p(expm1(-2.0 * b) * (1.0 - u12[0])) / b;
+      /* b -> 0 limit of the inversion (beta = 0): y0 uniform on [-1, 1] */
+      double y = b > 1e-300 ? 1.0 + log1p(expm1(-2.0 * b) * (1.0 - u12[0])) / b : 2.0 * u12[0] - 1.0;
       if (u12[1] * u12[1] <= 1.0 - y * y) {
         *y0 = y;
         return n + 1;

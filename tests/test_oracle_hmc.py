@@ -115,6 +115,22 @@ def test_heatbath_strong_coupling(oracle):
     assert np.max(np.abs(np.linalg.det(U) - 1)) < 1e-12
 
 
+def test_heatbath_beta_zero_is_haar(oracle):
+    """beta = 0: the heatbath samples the Haar measure, so <P> = 0 and every link
+    stays in SU(3) (the degenerate b = 0 case of the SU(2) update)."""
+    L = (4, 4, 4, 4)
+    U = inputs.random_gauge(L, "cold")
+    vals = []
+    for s in range(20):
+        U, fails = oracle.heatbath_sweep(U, L, 0.0, 31, s)
+        assert fails == 0
+        vals.append(oracle.plaquette(U, L))
+    vals = np.array(vals[2:])
+    assert abs(vals.mean()) < 4 * (1 / np.sqrt(18 * 6 * 256)) / np.sqrt(len(vals)) + 1e-3
+    assert np.all(np.isfinite(U))
+    assert np.max(np.abs(np.linalg.det(U) - 1)) < 1e-12
+
+
 def test_heatbath_weak_coupling_orders(oracle):
     """At large beta the heatbath drives a Haar start towards plaquette ~ 1 - c/beta."""
     L = (4, 4, 4, 4)
