@@ -131,8 +131,8 @@ __global__ void __launch_bounds__(128) bxs_kernel(BHdr *h, const VecDesc *d, con
       SpinorIO<P>::load({D.q, D.qs, D.Vh}, cb, Q);
 #pragma unroll
       for (int k = 0; k < 12; k++) {
-        X[k] = {X[k].re + al * Pp[k].re, X[k].im + al * Pp[k].im};
-        S[k] = {S[k].re - al * Q[k].re, S[k].im - al * Q[k].im};
+        X[k] = {rfma(al, Pp[k].re, X[k].re), rfma(al, Pp[k].im, X[k].im)};
+        S[k] = {rfma(-al, Q[k].re, S[k].re), rfma(-al, Q[k].im, S[k].im)};
         nrm += norm2_d(S[k]);
       }
       SpinorIO<P>::store({D.x, D.xs, D.Vh}, cb, X);
@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(128) bp_kernel(BHdr *h, const VecDesc *d, cons
     SpinorIO<P>::load({D.p, D.ps, D.Vh}, cb, Pp);
     SpinorIO<P>::load({D.z, D.zs, D.Vh}, cb, Z);
 #pragma unroll
-    for (int k = 0; k < 12; k++) Pp[k] = {Z[k].re + be * Pp[k].re, Z[k].im + be * Pp[k].im};
+    for (int k = 0; k < 12; k++) Pp[k] = {rfma(be, Pp[k].re, Z[k].re), rfma(be, Pp[k].im, Z[k].im)};
     SpinorIO<P>::store({D.p, D.ps, D.Vh}, cb, Pp);
   }
 }
@@ -582,7 +582,7 @@ lqcd_status cg_solve_batch_impl(lqcd_ctx *ctx, int n, lqcd_gauge *const *U, cons
     } gg{graph, gexec};
 
     BHdr hh;
-    int reliable = 0;
+    int reliable = 0, last_rel_iter = 0;
     std::vector<BState> bs(n);
     for (;;) {
       if (gexec) {
@@ -601,8 +601,11 @@ lqcd_status cg_solve_batch_impl(lqcd_ctx *ctx, int n, lqcd_gauge *const *U, cons
       std::memcpy(&hh, ctx->pinned, sizeof(hh));
       if (hh.nonfinite) return fail(ctx, LQCD_ERR_NONFINITE, "batched CG: non-finite scalar");
       const bool finished = hh.all_done != 0;
-      if (mixed && (hh.need_rel || finished)) {
+      // stalled low-precision recursion: force a reliable update and restart p
+      const bool stalled = mixed && !finished && !hh.need_rel && hh.iters - last_rel_iter >= 200;
+      if (mixed && (hh.need_rel || finished || stalled)) {
         reliable++;
+        last_rel_iter = hh.iters;
         bool all_ok = true;
         for (int k = 0; k < n; k++) {
           Sys &s = S[k];
@@ -636,10 +639,16 @@ lqcd_status cg_solve_batch_impl(lqcd_ctx *ctx, int n, lqcd_gauge *const *U, cons
         count_hop(false, false);
         LQCD_TRY(stage(3, true, true, nullptr));
         count_hop(true, false);
-        fin(BF_BETA);
-        LQCD_TRY(dispatch(ctx, inner, [&](auto P) {
-          bp_kernel<decltype(P)::value><<<grid, 128, 0, ctx->stream>>>(h, d_vdesc, d_tiles, ntiles);
-        }));
+        if (stalled) {  // beta = 0: p = z
+          fin(BF_INIT_ZZ);
+          for (int k = 0; k < n; k++)
+            LQCD_TRY(lincomb(ctx, S[k].Vh, S[k].p, S[k].z, nullptr, one, one, zero, zero, nullptr, nullptr));
+        } else {
+          fin(BF_BETA);
+          LQCD_TRY(dispatch(ctx, inner, [&](auto P) {
+            bp_kernel<decltype(P)::value><<<grid, 128, 0, ctx->stream>>>(h, d_vdesc, d_tiles, ntiles);
+          }));
+        }
         if (hh.iters >= prm.max_iter) {
           result = LQCD_ERR_NOCONV;
           break;
@@ -695,7 +704,7 @@ lqcd_status cg_solve_batch_impl(lqcd_ctx *ctx, int n, lqcd_gauge *const *U, cons
       LQCD_TRY(lincomb(ctx, s.Vh, s.rhs_o, s.bo, &s.res_o, one, one, mone, mone, nullptr, nullptr));
       double r2;
       LQCD_TRY(norm2_full(k, s.rhs_e, s.rhs_o, &r2));
-      st[k].true_resid = std::sqrt(r2 / s.b2);
+      st[k].true_resid = s.b2 > 0.0 ? std::sqrt(r2 / s.b2) : std::sqrt(r2);  // b = 0: x = 0
       st[k].converged = st[k].true_resid <= prm.tol;
       if (!std::isfinite(st[k].true_resid)) return fail(ctx, LQCD_ERR_NONFINITE, "true residual not finite");
       all = all && st[k].converged;

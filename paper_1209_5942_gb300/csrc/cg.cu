@@ -183,8 +183,8 @@ __global__ void __launch_bounds__(128) cg_xs_kernel(VecArgs a, SolverHdr *h, voi
     SpinorIO<P>::load(sv(a, q, qs, r), cb, Q);
 #pragma unroll
     for (int k = 0; k < 12; k++) {
-      X[k] = {X[k].re + al * Pp[k].re, X[k].im + al * Pp[k].im};
-      S[k] = {S[k].re - al * Q[k].re, S[k].im - al * Q[k].im};
+      X[k] = {rfma(al, Pp[k].re, X[k].re), rfma(al, Pp[k].im, X[k].im)};
+      S[k] = {rfma(-al, Q[k].re, S[k].re), rfma(-al, Q[k].im, S[k].im)};
       nrm += norm2_d(S[k]);
     }
     SpinorIO<P>::store(sv(a, x, xs, r), cb, X);
@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(128) cg_p_kernel(VecArgs a, SolverHdr *h, void
   SpinorIO<P>::load(sv(a, p, ps, r), cb, Pp);
   SpinorIO<P>::load(sv(a, z, zs, r), cb, Z);
 #pragma unroll
-  for (int k = 0; k < 12; k++) Pp[k] = {Z[k].re + be * Pp[k].re, Z[k].im + be * Pp[k].im};
+  for (int k = 0; k < 12; k++) Pp[k] = {rfma(be, Pp[k].re, Z[k].re), rfma(be, Pp[k].im, Z[k].im)};
   SpinorIO<P>::store(sv(a, p, ps, r), cb, Pp);
 }
 
@@ -648,6 +648,8 @@ lqcd_status cgls_even(lqcd_ctx *ctx, lqcd_gauge *U, const Geom &g, double kappa,
 
   SolverHdr hh;
   int reliable = 0;
+  int last_rel_iter = 0;
+  const int kStallIters = 200;
   lqcd_status result = LQCD_OK;
   std::vector<double> ss2;
   for (;;) {
@@ -670,9 +672,14 @@ lqcd_status cgls_even(lqcd_ctx *ctx, lqcd_gauge *U, const Geom &g, double kappa,
       break;
     }
     bool finished = hh.all_done != 0;
-    if (mixed && (hh.need_rel || finished)) {
+    // A low-precision recursion can stall before its residual drops by delta
+    // (16-bit links perturb the operator by ~1e-3): after kStallIters
+    // iterations without a reliable update, force one and restart p = z.
+    const bool stalled = mixed && !finished && !hh.need_rel && hh.iters - last_rel_iter >= kStallIters;
+    if (mixed && (hh.need_rel || finished || stalled)) {
       // reliable update: xo += X; X = 0; r = bhat - Mhat xo (outer); s = r
       reliable++;
+      last_rel_iter = hh.iters;
       dim3 g2(nbv, nrhs);
       count_launch(ctx, (double)Vh * nrhs * (2.0 * spinor_site_bytes(outer) + spinor_site_bytes(inner)));
       LQCD_TRY(dispatch_prec(ctx, outer, [&](auto PO) {
@@ -699,12 +706,22 @@ lqcd_status cgls_even(lqcd_ctx *ctx, lqcd_gauge *U, const Geom &g, double kappa,
       if (finished && all_ok) break;
       // z = Mhat^+ s; beta = |z|^2 / zz_old; p = z + beta p
       state_after_reliable_kernel<<<1, 64, 0, ctx->stream>>>(h, tmpd);
+      // keep p (beta from the new z) -- or, after a stall, restart with beta = 0
+      const int zop = stalled ? FIN_INIT_ZZ : FIN_BETA;
       if (!normal) {
         LQCD_TRY(apply_schur(Oi, s.f, z.f, t.f, 0, true, ctx->partials, &nb, nullptr));
-        launch_finalize(ctx, h, nrhs, nb, FIN_BETA, nullptr);
+        launch_finalize(ctx, h, nrhs, nb, zop, nullptr);
       } else {
         LQCD_TRY(lincomb(ctx, Vh, z.f, z.f, nullptr, one, one, zero, zero, ctx->partials, &nbl));
-        launch_finalize(ctx, h, nrhs, nbl, FIN_BETA, nullptr);
+        launch_finalize(ctx, h, nrhs, nbl, zop, nullptr);
+      }
+      if (stalled) LQCD_TRY(lincomb(ctx, Vh, p.f, z.f, nullptr, one, one, zero, zero, nullptr, nullptr));
+      if (stalled) {
+        if (hh.iters >= prm.max_iter) {
+          result = LQCD_ERR_NOCONV;
+          break;
+        }
+        continue;
       }
       // FIN_BETA skips when halted: state_after_reliable clears halt unless all done
       count_launch(ctx, (double)Vh * nrhs * spinor_site_bytes(inner) * 3.0);
@@ -863,7 +880,8 @@ lqcd_status cg_solve_eo(lqcd_ctx *ctx, lqcd_gauge *U, const HalfField &b_full, c
     bool all = true;
     int total_iters = 0;
     for (int r = 0; r < nrhs; r++) {
-      double tr = std::sqrt((e2[r] + o2[r]) / b2[r]);
+      // a zero right-hand side has the solution x = 0 and an absolute residual
+      double tr = b2[r] > 0.0 ? std::sqrt((e2[r] + o2[r]) / b2[r]) : std::sqrt(e2[r] + o2[r]);
       st[r].true_resid = tr;
       st[r].converged = tr <= prm.tol;
       all = all && st[r].converged;

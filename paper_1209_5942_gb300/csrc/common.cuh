@@ -137,6 +137,32 @@ template <class R> LQCD_DEV Cx<R> operator-(Cx<R> a) { return {-a.re, -a.im}; }
 template <class R> LQCD_DEV Cx<R> operator*(Cx<R> a, Cx<R> b) {
   return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
 }
+// FP32 / FP64: every rounding step written out with intrinsics, so the compiler
+// cannot contract differently in different kernels or launch variants and all
+// of them give bit-identical results.
+template <> LQCD_DEV Cx<float> operator+(Cx<float> a, Cx<float> b) {
+  return {__fadd_rn(a.re, b.re), __fadd_rn(a.im, b.im)};
+}
+template <> LQCD_DEV Cx<float> operator-(Cx<float> a, Cx<float> b) {
+  return {__fsub_rn(a.re, b.re), __fsub_rn(a.im, b.im)};
+}
+template <> LQCD_DEV Cx<float> operator*(Cx<float> a, Cx<float> b) {
+  return {__fmaf_rn(a.re, b.re, -__fmul_rn(a.im, b.im)), __fmaf_rn(a.re, b.im, __fmul_rn(a.im, b.re))};
+}
+template <> LQCD_DEV Cx<double> operator+(Cx<double> a, Cx<double> b) {
+  return {__dadd_rn(a.re, b.re), __dadd_rn(a.im, b.im)};
+}
+template <> LQCD_DEV Cx<double> operator-(Cx<double> a, Cx<double> b) {
+  return {__dsub_rn(a.re, b.re), __dsub_rn(a.im, b.im)};
+}
+template <> LQCD_DEV Cx<double> operator*(Cx<double> a, Cx<double> b) {
+  return {__fma_rn(a.re, b.re, -__dmul_rn(a.im, b.im)), __fma_rn(a.re, b.im, __dmul_rn(a.im, b.re))};
+}
+// a * b + c for reals with a single rounding where the hardware fuses
+LQCD_DEV float rfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+LQCD_DEV double rfma(double a, double b, double c) { return __fma_rn(a, b, c); }
+LQCD_DEV df rfma(df a, df b, df c) { return a * b + c; }
+
 // i * a and -i * a
 template <class R> LQCD_DEV Cx<R> times_i(Cx<R> a) { return {-a.im, a.re}; }
 template <class R> LQCD_DEV Cx<R> times_mi(Cx<R> a) { return {a.im, -a.re}; }
@@ -182,7 +208,7 @@ LQCD_DEV double to_double(df v) { return df_to_double(v); }
 // |a|^2 accumulated in double (norms and dot products use FP64 partial sums)
 template <class R> LQCD_DEV double norm2_d(Cx<R> a) {
   double re = to_double(a.re), im = to_double(a.im);
-  return re * re + im * im;
+  return __fma_rn(re, re, __dmul_rn(im, im));
 }
 // |a|^2 for a df complex, summed in float-float before the FP64 conversion
 LQCD_DEV df norm2_df(Cx<df> a) { return a.re * a.re + a.im * a.im; }
@@ -278,8 +304,8 @@ template <class H> struct SpinorIO16 {
       uint32_t ww[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
       for (int j = 0; j < 4; j++) {
-        s[4 * k + j].re = Half16<H>::to_f((uint16_t)(ww[j] & 0xFFFFu)) * sc;
-        s[4 * k + j].im = Half16<H>::to_f((uint16_t)(ww[j] >> 16)) * sc;
+        s[4 * k + j].re = __fmul_rn(Half16<H>::to_f((uint16_t)(ww[j] & 0xFFFFu)), sc);
+        s[4 * k + j].im = __fmul_rn(Half16<H>::to_f((uint16_t)(ww[j] >> 16)), sc);
       }
     }
   }
@@ -294,8 +320,8 @@ template <class H> struct SpinorIO16 {
       uint32_t ww[4];
 #pragma unroll
       for (int j = 0; j < 4; j++) {
-        uint32_t lo = Half16<H>::from_f(s[4 * k + j].re * inv);
-        uint32_t hi = Half16<H>::from_f(s[4 * k + j].im * inv);
+        uint32_t lo = Half16<H>::from_f(__fmul_rn(s[4 * k + j].re, inv));
+        uint32_t hi = Half16<H>::from_f(__fmul_rn(s[4 * k + j].im, inv));
         ww[j] = lo | (hi << 16);
       }
       p[(size_t)k * v.Vh + cb] = make_uint4(ww[0], ww[1], ww[2], ww[3]);

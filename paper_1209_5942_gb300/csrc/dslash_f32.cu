@@ -1,0 +1,18 @@
+// dslash_f32.cu -- FP32 instantiations of the hop kernels (both load orders).
+#include "hop_kernels.cuh"
+
+namespace lqcd {
+
+void hop_launch_f32(const HopArgs &A, int recon, dim3 grid, dim3 block, bool dag, bool red, bool lf,
+                    cudaStream_t st) {
+  if (recon == 12) launch_t<LQCD_F32, 12>(A, grid, block, dag, red, st, lf);
+  else launch_t<LQCD_F32, 18>(A, grid, block, dag, red, st, lf);
+}
+
+void hop_batched_f32(int recon, bool dag, bool red, const HopArgs *d, const int2 *tl, int ntiles, int grid,
+                     const int *halt, cudaStream_t st) {
+  if (recon == 12) batched_t<LQCD_F32, 12>(dag, red, d, tl, ntiles, grid, halt, st);
+  else batched_t<LQCD_F32, 18>(dag, red, d, tl, ntiles, grid, halt, st);
+}
+
+}  // namespace lqcd

@@ -255,7 +255,8 @@ LQCD_DEV bool sample_y0(double b, uint32_t c0, uint32_t c1, uint32_t c2, uint64_
     double u[2];
     uniform2(c0, c1, c2, (uint32_t)(2 * n), seed, u);
     if (b < HB_B_SWITCH) {
-      double y = 1.0 + log1p(expm1(-2.0 * b) * (1.0 - u[0])) / b;
+      // b -> 0 (beta = 0): the inversion's limit is y0 uniform on [-1, 1]
+      double y = b > 1e-300 ? 1.0 + log1p(expm1(-2.0 * b) * (1.0 - u[0])) / b : 2.0 * u[0] - 1.0;
       if (u[1] * u[1] <= 1.0 - y * y) {
         *y0 = y;
         return true;
