@@ -154,6 +154,13 @@ int lqcd_reset_counters(lqcd_ctx *ctx);
  * written, so other processes skip the timing. */
 int lqcd_set_autotune(lqcd_ctx *ctx, int enable, const char *cache_path);
 
+/* Forces candidate number `choice` (taken modulo each configuration's
+ * candidate count) for every tuned launch of this context, bypassing the
+ * tuner and its cache; choice < 0 restores tuning.  For reproducible
+ * performance experiments and for tests that every launch shape gives the
+ * same bits.  Returns LQCD_ERR_INVALID for a NULL context. */
+int lqcd_set_launch_choice(lqcd_ctx *ctx, int choice);
+
 /* Bytes needed for a field of the given parity (LQCD_FULL or one parity),
  * precision and nrhs in the EO layout; *scale_bytes receives the size of the
  * scale array (0 for unscaled precisions).  Returns 0 on invalid input. */
@@ -288,8 +295,10 @@ int lqcd_plaquette(lqcd_ctx *ctx, const lqcd_gauge *U, double *plaq_out);
  * SU(2) subgroups (0,1), (1,2), (0,2) with the exact SU(2) update (Creutz for
  * b < 1.5, Kennedy-Pendleton above, b = 2 beta k / 3).  Random numbers:
  * Philox4x32-10 keyed by seed, counter (site, sweep_idx, mu | g<<2 | tag<<8,
- * draw).  Then n_or overrelaxation passes (not in this build: n_or must be 0).
- * The links are reunitarised in FP64 afterwards.  Asynchronous. */
+ * draw).  Then n_or overrelaxation passes (0 <= n_or <= 64, else
+ * LQCD_ERR_INVALID): the same checkerboard order, each SU(2) subgroup
+ * replaced by its reflection v = (w^+/k)^2 (microcanonical: the action is
+ * unchanged).  The links are reunitarised in FP64 afterwards.  Asynchronous. */
 int lqcd_heatbath_sweep(lqcd_ctx *ctx, lqcd_gauge *U, double beta, uint64_t seed,
                         uint64_t sweep_idx, int n_or);
 

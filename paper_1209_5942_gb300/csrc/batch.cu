@@ -38,22 +38,14 @@ enum { BF_ALPHA = 0, BF_SS = 1, BF_BETA = 2, BF_INIT_ZZ = 3 };
 
 // One block per system: fixed-order sum of that system's partials and the CG
 // scalar step; the last block to finish sets the batch-wide flags.
-__global__ void bfinalize_kernel(BHdr *h, const double *partials, const long *poff, const int *pnb, int op) {
-  __shared__ double sh[256];
+__global__ void __launch_bounds__(FIN_THREADS) bfinalize_kernel(BHdr *h, const double *partials, const long *poff, const int *pnb, int op) {
+  __shared__ double sh[33];
   __shared__ int last;
   if (op != BF_INIT_ZZ && *(volatile int *)&h->halt) return;
   const int k = blockIdx.x;
-  const double *v = partials + poff[k];
-  double t = 0.0;
-  for (int i = threadIdx.x; i < pnb[k]; i += blockDim.x) t += v[i];
-  sh[threadIdx.x] = t;
-  __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
-    __syncthreads();
-  }
+  // the same fixed-order sum as the single-system solver's finalize
+  const double x = block_sum_fixed(partials + poff[k], pnb[k], sh);
   if (threadIdx.x == 0) {
-    const double x = sh[0];
     BState &R = bstate(h)[k];
     int bad = !isfinite(x);
     switch (op) {
@@ -133,8 +125,8 @@ __global__ void __launch_bounds__(128) bxs_kernel(BHdr *h, const VecDesc *d, con
       for (int k = 0; k < 12; k++) {
         X[k] = {rfma(al, Pp[k].re, X[k].re), rfma(al, Pp[k].im, X[k].im)};
         S[k] = {rfma(-al, Q[k].re, S[k].re), rfma(-al, Q[k].im, S[k].im)};
-        nrm += norm2_d(S[k]);
       }
+      nrm = site_norm2<R, 12>(S);
       SpinorIO<P>::store({D.x, D.xs, D.Vh}, cb, X);
       SpinorIO<P>::store({D.s, D.ss, D.Vh}, cb, S);
     }
@@ -364,19 +356,23 @@ lqcd_status cg_solve_batch_impl(lqcd_ctx *ctx, int n, lqcd_gauge *const *U, cons
     L.prec = inner;
     L.recon = mixed ? irecon : U[k]->recon;
     L.U = s.Ui;
-    // stage 0: t = A^-1 H p     stage 1: q = A p - k^2 H t   (partials)
+    // stage 0: t = -k^2 A^-1 H p     stage 1: q = A p + H t   (partials)
     L.in = s.p; L.out = s.t; L.out_parity = 1; L.dagger = 0;
-    L.c_up = c.Ai_up; L.c_dn = c.Ai_dn; L.has_aux = false; L.partials = nullptr;
+    L.c_up = {-k2 * c.Ai_up.re, -k2 * c.Ai_up.im};
+    L.c_dn = {-k2 * c.Ai_dn.re, -k2 * c.Ai_dn.im};
+    L.has_aux = false; L.partials = nullptr;
     hop_args_fill(s.g, L, &hdesc[(0 * n + k) * ha]);
     L.in = s.t; L.out = s.q; L.aux = s.p; L.has_aux = true; L.out_parity = 0;
-    L.c_up = L.c_dn = {-k2, 0.0}; L.d_up = c.A_up; L.d_dn = c.A_dn; L.partials = part;
+    L.c_up = L.c_dn = {1.0, 0.0}; L.d_up = c.A_up; L.d_dn = c.A_dn; L.partials = part;
     hop_args_fill(s.g, L, &hdesc[(1 * n + k) * ha]);
-    // stage 2: t = A^-+ H^+ s   stage 3: z = A^+ s - k^2 H^+ t (partials)
+    // stage 2: t = -k^2 A^-+ H^+ s   stage 3: z = A^+ s + H^+ t (partials)
     L.in = s.s; L.out = s.t; L.has_aux = false; L.out_parity = 1; L.dagger = 1;
-    L.c_up = cd.Ai_up; L.c_dn = cd.Ai_dn; L.partials = nullptr;
+    L.c_up = {-k2 * cd.Ai_up.re, -k2 * cd.Ai_up.im};
+    L.c_dn = {-k2 * cd.Ai_dn.re, -k2 * cd.Ai_dn.im};
+    L.partials = nullptr;
     hop_args_fill(s.g, L, &hdesc[(2 * n + k) * ha]);
     L.in = s.t; L.out = s.z; L.aux = s.s; L.has_aux = true; L.out_parity = 0;
-    L.c_up = L.c_dn = {-k2, 0.0}; L.d_up = cd.A_up; L.d_dn = cd.A_dn; L.partials = part;
+    L.c_up = L.c_dn = {1.0, 0.0}; L.d_up = cd.A_up; L.d_dn = cd.A_dn; L.partials = part;
     hop_args_fill(s.g, L, &hdesc[(3 * n + k) * ha]);
     VecDesc &v = vdesc[k];
     v.Vh = s.Vh;
@@ -437,7 +433,7 @@ lqcd_status cg_solve_batch_impl(lqcd_ctx *ctx, int n, lqcd_gauge *const *U, cons
     ctx->cnt.hop_sites += sites_total;
   };
   auto fin = [&](int op) {
-    bfinalize_kernel<<<n, 256, 0, ctx->stream>>>(h, ctx->partials, d_poff, d_pnb, op);
+    bfinalize_kernel<<<n, FIN_THREADS, 0, ctx->stream>>>(h, ctx->partials, d_poff, d_pnb, op);
     count_launch(ctx, 8.0 * ptotal);
   };
 
@@ -509,7 +505,7 @@ lqcd_status cg_solve_batch_impl(lqcd_ctx *ctx, int n, lqcd_gauge *const *U, cons
     LQCD_TRY(stage(2, true, false, nullptr));
     count_hop(false, false);
     LQCD_TRY(stage(3, true, true, nullptr));
-    count_hop(true, false);
+    count_hop(true, true);
     fin(BF_INIT_ZZ);
     for (int k = 0; k < n; k++)
       LQCD_TRY(lincomb(ctx, S[k].Vh, S[k].p, S[k].z, nullptr, one, one, zero, zero, nullptr, nullptr));
@@ -518,7 +514,7 @@ lqcd_status cg_solve_batch_impl(lqcd_ctx *ctx, int n, lqcd_gauge *const *U, cons
       LQCD_TRY(stage(0, false, false, &h->halt));
       count_hop(false, false);
       LQCD_TRY(stage(1, false, true, &h->halt));
-      count_hop(true, false);
+      count_hop(true, true);
       fin(BF_ALPHA);
       LQCD_TRY(dispatch(ctx, inner, [&](auto P) {
         bxs_kernel<decltype(P)::value><<<grid, 128, 0, ctx->stream>>>(h, d_vdesc, d_tiles, ntiles);
@@ -528,7 +524,7 @@ lqcd_status cg_solve_batch_impl(lqcd_ctx *ctx, int n, lqcd_gauge *const *U, cons
       LQCD_TRY(stage(2, true, false, &h->halt));
       count_hop(false, false);
       LQCD_TRY(stage(3, true, true, &h->halt));
-      count_hop(true, false);
+      count_hop(true, true);
       fin(BF_BETA);
       LQCD_TRY(dispatch(ctx, inner, [&](auto P) {
         bp_kernel<decltype(P)::value><<<grid, 128, 0, ctx->stream>>>(h, d_vdesc, d_tiles, ntiles);
@@ -638,7 +634,7 @@ lqcd_status cg_solve_batch_impl(lqcd_ctx *ctx, int n, lqcd_gauge *const *U, cons
         LQCD_TRY(stage(2, true, false, nullptr));
         count_hop(false, false);
         LQCD_TRY(stage(3, true, true, nullptr));
-        count_hop(true, false);
+        count_hop(true, true);
         if (stalled) {  // beta = 0: p = z
           fin(BF_INIT_ZZ);
           for (int k = 0; k < n; k++)

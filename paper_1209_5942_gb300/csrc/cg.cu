@@ -52,29 +52,14 @@ struct SolverHdr {
 // layout in device memory: SolverHdr, then RhsState[nrhs]
 LQCD_DEV RhsState *rhs_state(SolverHdr *h) { return (RhsState *)(h + 1); }
 
-// sum of partials[r][0..nb) in a fixed order by one block of 256 threads
-LQCD_DEV double block_sum_fixed(const double *v, int nb, double *sh) {
-  double t = 0.0;
-  for (int k = threadIdx.x; k < nb; k += blockDim.x) t += v[k];
-  sh[threadIdx.x] = t;
-  __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
-    __syncthreads();
-  }
-  double r = sh[0];
-  __syncthreads();
-  return r;
-}
-
 enum { FIN_ALPHA = 0, FIN_SS = 1, FIN_BETA = 2, FIN_INIT_ZZ = 3, FIN_STORE = 4 };
 
 // One block: finishes the reductions of all nrhs right-hand sides and applies
 // the CG scalar step `op`.  FIN_STORE only writes the plain sums to out[r]
 // and does not touch the solver state.
-__global__ void finalize_kernel(SolverHdr *h, int nrhs, const double *partials, int nb, int op,
-                                double *out) {
-  __shared__ double sh[256];
+__global__ void __launch_bounds__(FIN_THREADS) finalize_kernel(SolverHdr *h, int nrhs, const double *partials,
+                                                              int nb, int op, double *out) {
+  __shared__ double sh[33];
   if (op == FIN_STORE) {
     for (int r = 0; r < nrhs; r++) {
       double v = block_sum_fixed(partials + (size_t)r * nb, nb, sh);
@@ -134,7 +119,7 @@ __global__ void finalize_kernel(SolverHdr *h, int nrhs, const double *partials, 
 
 
 static void launch_finalize(lqcd_ctx *ctx, SolverHdr *h, int nrhs, int nb, int op, double *out) {
-  finalize_kernel<<<1, 256, 0, ctx->stream>>>(h, nrhs, ctx->partials, nb, op, out);
+  finalize_kernel<<<1, FIN_THREADS, 0, ctx->stream>>>(h, nrhs, ctx->partials, nb, op, out);
   count_launch(ctx, 8.0 * nb * nrhs);
 }
 
@@ -185,8 +170,8 @@ __global__ void __launch_bounds__(128) cg_xs_kernel(VecArgs a, SolverHdr *h, voi
     for (int k = 0; k < 12; k++) {
       X[k] = {rfma(al, Pp[k].re, X[k].re), rfma(al, Pp[k].im, X[k].im)};
       S[k] = {rfma(-al, Q[k].re, S[k].re), rfma(-al, Q[k].im, S[k].im)};
-      nrm += norm2_d(S[k]);
     }
+    nrm = site_norm2<R, 12>(S);
     SpinorIO<P>::store(sv(a, x, xs, r), cb, X);
     SpinorIO<P>::store(sv(a, s, ss, r), cb, S);
   }
@@ -237,8 +222,8 @@ __global__ void __launch_bounds__(128) lincomb_kernel(VecArgs a, VecArgs ax, Vec
       Cx<R> o = (k < 6 ? au : ad) * X[k];
       if (y) o = cmadd(k < 6 ? bu : bd, Y[k], o);
       X[k] = o;
-      nrm += norm2_d(o);
     }
+    nrm = site_norm2<R, 12>(X);
     SpinorIO<P>::store(sv(a, out, os, r), cb, X);
   }
   if (partials) {
@@ -420,8 +405,11 @@ lqcd_status apply_schur(const Op &op, const HalfField &in, const HalfField &out,
   L1.out = tmp;
   L1.out_parity = p ^ 1;
   L1.dagger = dagger;
-  L1.c_up = c.Ai_up;
-  L1.c_dn = c.Ai_dn;
+  // -kappa^2 is folded into the first hop's factor, so the second hop's
+  // epilogue is out = H tmp + A in with no multiplication of the hop sum
+  const double k2 = op.kappa * op.kappa;
+  L1.c_up = {-k2 * c.Ai_up.re, -k2 * c.Ai_up.im};
+  L1.c_dn = {-k2 * c.Ai_dn.re, -k2 * c.Ai_dn.im};
   L1.halt = halt;
   LQCD_TRY(launch_hop(op.ctx, op.g, L1, nullptr));
   HopLaunch L2 = L1;
@@ -430,9 +418,8 @@ lqcd_status apply_schur(const Op &op, const HalfField &in, const HalfField &out,
   L2.aux = in;
   L2.has_aux = true;
   L2.out_parity = p;
-  double k2 = op.kappa * op.kappa;
-  L2.c_up = {-k2, 0.0};
-  L2.c_dn = {-k2, 0.0};
+  L2.c_up = {1.0, 0.0};
+  L2.c_dn = {1.0, 0.0};
   L2.d_up = c.A_up;
   L2.d_dn = c.A_dn;
   L2.partials = partials;

@@ -210,8 +210,60 @@ template <class R> LQCD_DEV double norm2_d(Cx<R> a) {
   double re = to_double(a.re), im = to_double(a.im);
   return __fma_rn(re, re, __dmul_rn(im, im));
 }
+// |v|^2 of one site's n complex components, returned as a double.  FP64 and
+// float-float values are squared and summed in FP64.  FP32 values (the
+// sloppy formats, whose components carry 24-bit mantissas at best) are
+// squared and summed in FP32 with FMAs, relative error <= 2n u_32, and
+// converted once: the per-site FP64 conversions and products would otherwise
+// keep GB300's FP64 pipe (1/64 of the FP32 rate) busier than the stencil.
+// Cross-site sums are FP64 in every case.
+template <class R, int N> LQCD_DEV double site_norm2(const Cx<R> v[N]) {
+  double t = 0.0;
+#pragma unroll
+  for (int k = 0; k < N; k++) t += norm2_d(v[k]);
+  return t;
+}
+template <> LQCD_DEV double site_norm2<float, 12>(const Cx<float> v[12]) {
+  float t = 0.0f;
+#pragma unroll
+  for (int k = 0; k < 12; k++) {
+    t = __fmaf_rn(v[k].re, v[k].re, t);
+    t = __fmaf_rn(v[k].im, v[k].im, t);
+  }
+  return (double)t;
+}
 // |a|^2 for a df complex, summed in float-float before the FP64 conversion
 LQCD_DEV df norm2_df(Cx<df> a) { return a.re * a.re + a.im * a.im; }
+
+// Sum of v[0..nb) in a fixed order by one block of FIN_THREADS threads:
+// thread t adds v[t], v[t + FIN_THREADS], ... in that order (the loop is
+// unrolled, so a thread has several independent loads in flight and the
+// whole sum costs a few L2 latencies), then a fixed shuffle tree per warp and
+// one over the warps.  The order depends on nb only, so the result is
+// reproducible for any launch shape of the kernels that wrote the partials,
+// and the single and the batched solver reduce identically.  Call with
+// blockDim.x == FIN_THREADS; sh holds 33 doubles.
+constexpr int FIN_THREADS = 1024;
+LQCD_DEV double block_sum_fixed(const double *v, int nb, double *sh) {
+  double t = 0.0;
+#pragma unroll 8
+  for (int k = threadIdx.x; k < nb; k += FIN_THREADS) t += v[k];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) sh[w] = t;
+  __syncthreads();
+  if (w == 0) {
+    double r = sh[l];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+    if (l == 0) sh[32] = r;
+  }
+  __syncthreads();
+  const double r = sh[32];
+  __syncthreads();
+  return r;
+}
 
 // ---------------------------------------------------------------------------
 // Storage formats of even-odd SoA spinor fields.
@@ -287,14 +339,40 @@ template <class H> struct Half16;
 template <> struct Half16<__nv_bfloat16> {
   static LQCD_DEV float to_f(uint16_t u) { return __bfloat162float(__ushort_as_bfloat16(u)); }
   static LQCD_DEV uint16_t from_f(float f) { return __bfloat16_as_ushort(__float2bfloat16_rn(f)); }
+  // (lo, hi) rounded to nearest and packed in one conversion
+  static LQCD_DEV uint32_t pack2(float lo, float hi) {
+    __nv_bfloat162 t = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&t);
+  }
 };
 template <> struct Half16<__half> {
   static LQCD_DEV float to_f(uint16_t u) { return __half2float(__ushort_as_half(u)); }
   static LQCD_DEV uint16_t from_f(float f) { return __half_as_ushort(__float2half_rn(f)); }
+  static LQCD_DEV uint32_t pack2(float lo, float hi) {
+    __half2 t = __floats2half2_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&t);
+  }
 };
 
 template <class H> struct SpinorIO16 {
   using R = float;
+  // the stored values without the site scale, which is returned: the hop
+  // applies it in its accumulation FMAs instead of to every component
+  static LQCD_DEV float load_unscaled(const SpinorView& v, int cb, Cx<float> s[12]) {
+    const uint4* p = (const uint4*)v.ptr;
+    const float sc = __ldg(v.scale + cb);
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+      uint4 w = __ldg(p + (size_t)k * v.Vh + cb);
+      uint32_t ww[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+      for (int j = 0; j < 4; j++) {
+        s[4 * k + j].re = Half16<H>::to_f((uint16_t)(ww[j] & 0xFFFFu));
+        s[4 * k + j].im = Half16<H>::to_f((uint16_t)(ww[j] >> 16));
+      }
+    }
+    return sc;
+  }
   static LQCD_DEV void load(const SpinorView& v, int cb, Cx<float> s[12]) {
     const uint4* p = (const uint4*)v.ptr;
     float sc = __ldg(v.scale + cb);
@@ -319,11 +397,8 @@ template <class H> struct SpinorIO16 {
     for (int k = 0; k < 3; k++) {
       uint32_t ww[4];
 #pragma unroll
-      for (int j = 0; j < 4; j++) {
-        uint32_t lo = Half16<H>::from_f(__fmul_rn(s[4 * k + j].re, inv));
-        uint32_t hi = Half16<H>::from_f(__fmul_rn(s[4 * k + j].im, inv));
-        ww[j] = lo | (hi << 16);
-      }
+      for (int j = 0; j < 4; j++)
+        ww[j] = Half16<H>::pack2(__fmul_rn(s[4 * k + j].re, inv), __fmul_rn(s[4 * k + j].im, inv));
       p[(size_t)k * v.Vh + cb] = make_uint4(ww[0], ww[1], ww[2], ww[3]);
     }
     v.scale[cb] = m;
@@ -331,6 +406,7 @@ template <class H> struct SpinorIO16 {
 };
 template <> struct SpinorIO<LQCD_BF16S> : SpinorIO16<__nv_bfloat16> {};
 template <> struct SpinorIO<LQCD_F16S> : SpinorIO16<__half> {};
+template <int PREC> constexpr bool kScaled16 = PREC == LQCD_BF16S || PREC == LQCD_F16S;
 
 // ---------------------------------------------------------------------------
 // Gauge field storage: [parity][mu][entry][Vh] per precision, entry = 3*row +

@@ -20,7 +20,9 @@
 // site-ordered SoA planes, so each warp load is fully coalesced; neighbour
 // spinors are reused through the 126 MB L2.  For nrhs > 1 the block is
 // (32 sites) x (RHS), so the warps of all right-hand sides fetch the same link
-// words back to back and L1 serves all but the first.  The spin projection
+// words back to back and L1 serves all but the first; for the memory-bound
+// formats a thread may also own 2 or 4 right-hand sides and apply each loaded
+// link to all of them (register blocking).  The spin projection
 // uses the chiral basis: (1 - s gamma_mu) psi = [h; -s B^+ h] with
 // h = psi_up - s B psi_dn, gamma_mu = [[0, B], [B^+, 0]], so only the two
 // upper spin components are multiplied by the link.
@@ -46,59 +48,75 @@ lqcd_status launch_hop(lqcd_ctx *ctx, const Geom &g, const HopLaunch &L, int *nb
   const bool dag = L.dagger != 0, red = L.partials != nullptr;
   if (L.prec < LQCD_F64 || L.prec > LQCD_F16S)
     return fail(ctx, LQCD_ERR_INVALID, "launch_hop: bad precision %d", L.prec);
-  // candidate launch shapes: (sites x 1) blocks for one RHS, (32 sites x by
-  // RHS) blocks for several; x 3 grid sizes (one site per thread, or a
-  // persistent grid of 4 or 8 blocks per SM walking the sites); x 2 load
-  // orders for the memory-bound formats.  Results do not depend on the shape.
-  static const int BX1[3] = {64, 128, 256};
-  static const int BY[4] = {1, 2, 4, 8};
-  static const int GRIDMUL[3] = {0, 4, 8};
-  int nshape = 3, fallback = 1;
-  if (nrhs > 1) {
-    nshape = 0;
-    for (int k = 0; k < 4; k++)
-      if (BY[k] <= nrhs) nshape = k + 1;
-    fallback = nshape - 1;
-  }
+  if (nrhs < 1) return fail(ctx, LQCD_ERR_INVALID, "launch_hop: nrhs %d", nrhs);
+  // Candidate launches (results never depend on the choice):
+  //  - one RHS: blocks of 64/128/256 sites;
+  //  - several RHS: blocks of 32 sites x {1,2,4,8} RHS, one RHS per thread,
+  //    and for the memory-bound formats also 32 sites x {1,2,4} groups of
+  //    rt = 2 or 4 RHS per thread (the register-blocked kernel);
+  //  each with a full grid (one site per thread) or a persistent grid of 4 or
+  //  8 blocks per SM, and for the memory-bound one-RHS-per-thread kernels both
+  //  load orders.  The float-float kernel with 18-real links runs two threads
+  //  per site and is bounded to 128 threads per block.
+  struct Cand {
+    short bx, by, gm, rt;
+    bool lf;
+  };
+  Cand cands[96];
+  int ncand = 0, fallback = 0;
   const bool low = L.prec == LQCD_F32 || L.prec == LQCD_BF16S || L.prec == LQCD_F16S;
-  const bool pair = L.prec == LQCD_DF64 && L.recon == 18;  // two threads per site
-  if (pair) {
-    // the pair kernel is bounded to 128 threads: 64 x {1, 2} for several RHS,
-    // 64 or 128 x 1 for one
-    nshape = 2;
-    fallback = 1;
-  }
-  const int ncand = 3 * nshape * (low ? 2 : 1);
-  auto go = [&](int cand0, const HopArgs &args) {
-    const bool lf = cand0 >= 3 * nshape;
-    const int cand = cand0 % (3 * nshape);
-    const int c = cand % nshape, gm = GRIDMUL[cand / nshape];
-    dim3 block, grid;
-    if (pair) {
-      const int bx = (nrhs == 1 && c >= 1) ? 128 : 64;
-      block = dim3(bx, nrhs == 1 ? 1 : BY[c], 1);
-      grid = dim3((g.Vh + bx / 2 - 1) / (bx / 2), 1, nrhs == 1 ? 1 : (nrhs + BY[c] - 1) / BY[c]);
-    } else if (nrhs == 1) {
-      block = dim3(BX1[c], 1, 1);
-      grid = dim3((g.Vh + BX1[c] - 1) / BX1[c], 1, 1);
-    } else {
-      block = dim3(32, BY[c], 1);
-      grid = dim3((g.Vh + 31) / 32, 1, (nrhs + BY[c] - 1) / BY[c]);
+  const bool pair = L.prec == LQCD_DF64 && L.recon == 18;
+  static const short GM[3] = {0, 4, 8};
+  for (int gi = 0; gi < 3; gi++)
+    for (int lf = 0; lf < (low ? 2 : 1); lf++) {
+      if (pair) {
+        if (nrhs == 1) {
+          cands[ncand++] = {64, 1, GM[gi], 1, false};
+          cands[ncand++] = {128, 1, GM[gi], 1, false};
+        } else {
+          cands[ncand++] = {64, 1, GM[gi], 1, false};
+          cands[ncand++] = {64, 2, GM[gi], 1, false};
+        }
+      } else if (nrhs == 1) {
+        for (short bx : {64, 128, 256}) cands[ncand++] = {bx, 1, GM[gi], 1, lf != 0};
+      } else {
+        for (short by : {1, 2, 4, 8})
+          if (by <= nrhs) cands[ncand++] = {32, by, GM[gi], 1, lf != 0};
+      }
     }
-    if (gm > 0) {
-      unsigned cap = (unsigned)(ctx->num_sms * gm);
+  if (low && nrhs > 1)
+    for (int gi = 0; gi < 3; gi++)
+      for (short rt : {2, 4})
+        for (short by : {1, 2, 4})
+          if (rt * by <= nrhs) cands[ncand++] = {32, by, GM[gi], rt, false};
+  // default without tuning: the full-grid, one-RHS-per-thread candidate with
+  // 128-site blocks for one RHS, or with the most RHS per block for several
+  for (int c = 0; c < ncand; c++) {
+    const Cand &k = cands[c];
+    if (k.gm != 0 || k.lf || k.rt != 1) continue;
+    if (nrhs == 1 ? k.bx == 128 : k.by >= cands[fallback].by) fallback = c;
+  }
+  auto go = [&](int ci, const HopArgs &args) {
+    const Cand &k = cands[ci];
+    const int rt = k.rt;
+    dim3 block(k.bx, k.by, 1), grid;
+    const int per_block = pair ? k.bx / 2 : k.bx;  // sites per block row
+    const int groups = (nrhs + rt - 1) / rt;       // RHS groups (of rt) to cover
+    grid = dim3((g.Vh + per_block - 1) / per_block, 1, (groups + k.by - 1) / k.by);
+    if (k.gm > 0) {
+      unsigned cap = (unsigned)(ctx->num_sms * k.gm);
       if (grid.x > cap) grid.x = cap;
     }
     cudaStream_t st = ctx->stream;
     switch (L.prec) {
       case LQCD_F64: hop_launch_f64(args, L.recon, grid, block, dag, red, st); break;
       case LQCD_DF64: hop_launch_df64(args, L.recon, pair, grid, block, dag, red, st); break;
-      case LQCD_F32: hop_launch_f32(args, L.recon, grid, block, dag, red, lf, st); break;
-      default: hop_launch_h16(args, L.prec, grid, block, dag, red, lf, st); break;
+      case LQCD_F32: hop_launch_f32(args, L.recon, grid, block, dag, red, k.lf, rt, st); break;
+      default: hop_launch_h16(args, L.prec, grid, block, dag, red, k.lf, rt, st); break;
     }
   };
   char key[160];
-  snprintf(key, sizeof(key), "hop|p%d|r%d|d%d|red%d|aux%d|%dx%dx%dx%d|n%d", L.prec, L.recon, (int)dag, (int)red,
+  snprintf(key, sizeof(key), "hop2|p%d|r%d|d%d|red%d|aux%d|%dx%dx%dx%d|n%d", L.prec, L.recon, (int)dag, (int)red,
            A.has_aux, g.L[0], g.L[1], g.L[2], g.L[3], nrhs);
   HopArgs At = A;
   At.halt = nullptr;  // timing launches run whatever the solver state
@@ -164,6 +182,7 @@ void hop_args_fill(const Geom &g, const HopLaunch &L, void *dst) {
   A.has_aux = L.has_aux ? 1 : 0;
   A.c_up = L.c_up;
   A.c_dn = L.c_dn;
+  A.c_one = L.c_up.re == 1.0 && L.c_up.im == 0.0 && L.c_dn.re == 1.0 && L.c_dn.im == 0.0;
   A.d_up = L.d_up;
   A.d_dn = L.d_dn;
   A.partials = L.partials;

@@ -1,10 +1,16 @@
-// dslash_f32.cu -- FP32 instantiations of the hop kernels (both load orders).
+// dslash_f32.cu -- FP32 instantiations of the hop kernels (both load orders,
+// and the register-blocked multi-RHS kernel).
 #include "hop_kernels.cuh"
 
 namespace lqcd {
 
-void hop_launch_f32(const HopArgs &A, int recon, dim3 grid, dim3 block, bool dag, bool red, bool lf,
+void hop_launch_f32(const HopArgs &A, int recon, dim3 grid, dim3 block, bool dag, bool red, bool lf, int rt,
                     cudaStream_t st) {
+  if (rt > 1) {
+    if (recon == 12) launch_rt<LQCD_F32, 12>(A, rt, grid, block, dag, red, st);
+    else launch_rt<LQCD_F32, 18>(A, rt, grid, block, dag, red, st);
+    return;
+  }
   if (recon == 12) launch_t<LQCD_F32, 12>(A, grid, block, dag, red, st, lf);
   else launch_t<LQCD_F32, 18>(A, grid, block, dag, red, st, lf);
 }

@@ -1,11 +1,17 @@
 // dslash_h16.cu -- BF16 / FP16 (per-site scaled spinors, REC12 links)
-// instantiations of the hop kernels (both load orders).
+// instantiations of the hop kernels (both load orders, and the
+// register-blocked multi-RHS kernel).
 #include "hop_kernels.cuh"
 
 namespace lqcd {
 
-void hop_launch_h16(const HopArgs &A, int prec, dim3 grid, dim3 block, bool dag, bool red, bool lf,
+void hop_launch_h16(const HopArgs &A, int prec, dim3 grid, dim3 block, bool dag, bool red, bool lf, int rt,
                     cudaStream_t st) {
+  if (rt > 1) {
+    if (prec == LQCD_BF16S) launch_rt<LQCD_BF16S, 12>(A, rt, grid, block, dag, red, st);
+    else launch_rt<LQCD_F16S, 12>(A, rt, grid, block, dag, red, st);
+    return;
+  }
   if (prec == LQCD_BF16S) launch_t<LQCD_BF16S, 12>(A, grid, block, dag, red, st, lf);
   else launch_t<LQCD_F16S, 12>(A, grid, block, dag, red, st, lf);
 }

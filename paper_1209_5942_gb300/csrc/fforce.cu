@@ -16,7 +16,9 @@
 //   C1 = sum_{k=0,1} (U hR_k) hL_k^+,  hR = proj+(Rf(x+mu)), hL = proj+(Lf(x))
 //   C2 = sum_{k=0,1} h'R_k (U h'L_k)^+, h'R = proj-(Rf(x)),   h'L = proj-(Lf(x+mu))
 // where proj_s(psi) = psi_up - s B psi_dn (gamma_mu = [[0,B],[B^+,0]]).
-// One thread per site computes the four links of that site (FP64).
+// One thread per site computes the four links of that site (FP64), reading
+// 18-real links or, for a field imported with recon = 12, 12-real links with
+// the third row rebuilt (the paper suggests REC12 for this kernel too).
 #include "internal.h"
 
 namespace lqcd {
@@ -53,17 +55,13 @@ LQCD_DEV void load12(const double2 *f, int Vh, int p, int cb, C s[12]) {
   }
 }
 
-template <int MU>
-LQCD_DEV void link_force(const double2 *U, const double2 *Lf, const double2 *Rf, const Geom &g, const Site &s,
+template <int MU, int RECON>
+LQCD_DEV void link_force(const GaugeView &U, const double2 *Lf, const double2 *Rf, const Geom &g, const Site &s,
                          int p, int cb, long lexi, double pref, double *out) {
   const int j = neighbour_cb(g, s, MU, +1);
   C u[9];
-  const double2 *ub = U + ((size_t)(p * 4 + MU) * 9) * g.Vh + cb;
-#pragma unroll
-  for (int k = 0; k < 9; k++) {
-    double2 w = ub[(size_t)k * g.Vh];
-    u[k] = {w.x, w.y};
-  }
+  LinkIO<LQCD_F64, RECON>::load(U, p, MU, cb, u);
+  if (RECON == 12) reconstruct_row2(u);  // Sec. 4.1 applied to the force (the paper's outlook)
   C a[12], hR[6], hL[6], hR2[6], hL2[6];
   load12(Rf, g.Vh, p ^ 1, j, a);
   proj<MU, 1>(a, hR);
@@ -119,26 +117,32 @@ LQCD_DEV void link_force(const double2 *U, const double2 *Lf, const double2 *Rf,
   for (int k = 0; k < 8; k++) o[k] = -pref * bc * tr[k];
 }
 
-__global__ void __launch_bounds__(128) fermion_force_kernel(const double2 *U, const double2 *Lf,
-                                                            const double2 *Rf, Geom g, double pref,
-                                                            double *out) {
+template <int RECON>
+__global__ void __launch_bounds__(128) fermion_force_kernel(GaugeView U, const double2 *Lf, const double2 *Rf,
+                                                            Geom g, double pref, double *out) {
   long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (tid >= 2L * g.Vh) return;
   int p = (int)(tid / g.Vh), cb = (int)(tid - (long)p * g.Vh);
   Site s = site_of(g, p, cb);
   long lexi = lexi_index(g, s);
-  link_force<0>(U, Lf, Rf, g, s, p, cb, lexi, pref, out);
-  link_force<1>(U, Lf, Rf, g, s, p, cb, lexi, pref, out);
-  link_force<2>(U, Lf, Rf, g, s, p, cb, lexi, pref, out);
-  link_force<3>(U, Lf, Rf, g, s, p, cb, lexi, pref, out);
+  link_force<0, RECON>(U, Lf, Rf, g, s, p, cb, lexi, pref, out);
+  link_force<1, RECON>(U, Lf, Rf, g, s, p, cb, lexi, pref, out);
+  link_force<2, RECON>(U, Lf, Rf, g, s, p, cb, lexi, pref, out);
+  link_force<3, RECON>(U, Lf, Rf, g, s, p, cb, lexi, pref, out);
 }
 
-// dS/dw into out [4][V][8] from EO full F64 fields Lf, Rf; pref = kappa^2
-lqcd_status fermion_force_raw(lqcd_ctx *ctx, const lqcd_gauge *U, const void *Lf, const void *Rf,
-                              double kappa, double *out) {
+// dS/dw into out [4][V][8] from EO full F64 fields Lf, Rf; pref = kappa^2.
+// Uv: the FP64 links in format recon (18, or 12 with the third row rebuilt).
+lqcd_status fermion_force_raw(lqcd_ctx *ctx, const lqcd_gauge *U, const GaugeView &Uv, int recon, const void *Lf,
+                              const void *Rf, double kappa, double *out) {
   long V = 2L * U->g.Vh;
-  fermion_force_kernel<<<(unsigned)((V + 127) / 128), 128, 0, ctx->stream>>>(
-      (const double2 *)U->master, (const double2 *)Lf, (const double2 *)Rf, U->g, kappa * kappa, out);
+  const unsigned grid = (unsigned)((V + 127) / 128);
+  if (recon == 12)
+    fermion_force_kernel<12><<<grid, 128, 0, ctx->stream>>>(Uv, (const double2 *)Lf, (const double2 *)Rf, U->g,
+                                                            kappa * kappa, out);
+  else
+    fermion_force_kernel<18><<<grid, 128, 0, ctx->stream>>>(Uv, (const double2 *)Lf, (const double2 *)Rf, U->g,
+                                                            kappa * kappa, out);
   LQCD_CUDA(ctx, cudaGetLastError());
   return LQCD_OK;
 }

@@ -29,8 +29,8 @@ lqcd_status gauge_update_raw(lqcd_ctx *ctx, lqcd_gauge *U, const double *P, doub
 lqcd_status momenta_update_raw(lqcd_ctx *ctx, long V, double *P, const double *F, double eps);
 lqcd_status sumsq_raw(lqcd_ctx *ctx, const double *P, size_t n, double *out);
 lqcd_status metro_uniform(lqcd_ctx *ctx, uint64_t seed, uint32_t traj, double *u);
-lqcd_status fermion_force_raw(lqcd_ctx *ctx, const lqcd_gauge *U, const void *Lf, const void *Rf,
-                              double kappa, double *out);
+lqcd_status fermion_force_raw(lqcd_ctx *ctx, const lqcd_gauge *U, const GaugeView &Uv, int recon, const void *Lf,
+                              const void *Rf, double kappa, double *out);
 lqcd_status cgls_even(lqcd_ctx *ctx, lqcd_gauge *U, const Geom &g, double kappa, double mu,
                       const lqcd_cg_params &prm, const HalfField &bhat, const HalfField &xo,
                       const std::vector<double> &b2, lqcd_cg_stats *st, int nrhs, int *iters_used,
@@ -169,7 +169,7 @@ lqcd_status fermion_force_from_X(lqcd_ctx *ctx, lqcd_gauge *U, const HalfField &
   L2.c_up = {n, a * n};
   L2.c_dn = {n, -a * n};
   LQCD_TRY(launch_hop(ctx, g, L2, nullptr));
-  return fermion_force_raw(ctx, U, Lf.p, Rf.p, kappa, out);
+  return fermion_force_raw(ctx, U, op.U, U->recon, Lf.p, Rf.p, kappa, out);
 }
 
 }  // namespace lqcd

@@ -52,6 +52,40 @@ LQCD_DEV void accumulate(const Cx<R> v[6], Cx<R> acc[12]) {
   }
 }
 
+// acc += f sc w for f = +1, -1, +i, -i (F_P1, F_M1, F_PI, F_MI), in FMAs
+enum { F_P1 = 0, F_M1 = 1, F_PI = 2, F_MI = 3 };
+template <int F> LQCD_DEV void add_f(Cx<float> &acc, float sc, Cx<float> w) {
+  if (F == F_P1) acc = {__fmaf_rn(sc, w.re, acc.re), __fmaf_rn(sc, w.im, acc.im)};
+  else if (F == F_M1) acc = {__fmaf_rn(-sc, w.re, acc.re), __fmaf_rn(-sc, w.im, acc.im)};
+  else if (F == F_PI) acc = {__fmaf_rn(-sc, w.im, acc.re), __fmaf_rn(sc, w.re, acc.im)};
+  else acc = {__fmaf_rn(sc, w.im, acc.re), __fmaf_rn(-sc, w.re, acc.im)};
+}
+
+// acc += sc [v; -s B^+ v]: accumulate<MU, S> with the neighbour's 16-bit
+// storage scale (and the boundary sign) applied in the accumulation FMAs
+template <int MU, int S>
+LQCD_DEV void accumulate_scaled(const Cx<float> v[6], float sc, Cx<float> acc[12]) {
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    const Cx<float> v0 = v[c], v1 = v[3 + c];
+    add_f<F_P1>(acc[c], sc, v0);
+    add_f<F_P1>(acc[3 + c], sc, v1);
+    if (MU == 0) {
+      add_f<(S > 0 ? F_MI : F_PI)>(acc[6 + c], sc, v1);
+      add_f<(S > 0 ? F_MI : F_PI)>(acc[9 + c], sc, v0);
+    } else if (MU == 1) {
+      add_f<(S > 0 ? F_M1 : F_P1)>(acc[6 + c], sc, v1);
+      add_f<(S > 0 ? F_P1 : F_M1)>(acc[9 + c], sc, v0);
+    } else if (MU == 2) {
+      add_f<(S > 0 ? F_MI : F_PI)>(acc[6 + c], sc, v0);
+      add_f<(S > 0 ? F_PI : F_MI)>(acc[9 + c], sc, v1);
+    } else {
+      add_f<(S > 0 ? F_M1 : F_P1)>(acc[6 + c], sc, v0);
+      add_f<(S > 0 ? F_M1 : F_P1)>(acc[9 + c], sc, v1);
+    }
+  }
+}
+
 // v = U h (forward) for both upper spin components
 template <class R>
 LQCD_DEV void mul_link(const Cx<R> u[9], const Cx<R> h[6], Cx<R> v[6]) {
@@ -98,23 +132,57 @@ LQCD_DEV void dfacc_add_prod(DfAcc &A, df a, df b, bool neg) {
   A.s = t.hi;
   A.e = __fadd_rn(A.e, __fadd_rn(t.lo, pe));
 }
+// the first product of a sum starts the accumulator (no TwoSum with zero)
+LQCD_DEV DfAcc dfacc_first(df a, df b, bool neg) {
+  float ah = neg ? -a.hi : a.hi, al = neg ? -a.lo : a.lo;
+  float p = __fmul_rn(ah, b.hi);
+  float pe = __fmaf_rn(ah, b.hi, -p);
+  pe = __fmaf_rn(ah, b.lo, pe);
+  pe = __fmaf_rn(al, b.hi, pe);
+  return {p, pe};
+}
 LQCD_DEV df dfacc_result(const DfAcc &A) { return fast_two_sum(A.s, A.e); }
 
-// sum_j x_j * y_j (conjugating x when CONJ), complex double-words
-template <bool CONJ>
+// sum_j x_j * y_j (conjugating x when CONJ), complex double-words.  LAZY
+// returns the accumulators unnormalised (value hi + lo exact, |lo| a few
+// ulp(hi) at most), for callers that only add the result to other
+// double-words before normalising.
+template <bool CONJ, bool LAZY = false>
 LQCD_DEV Cx<df> dfdot3(const Cx<df> x0, const Cx<df> x1, const Cx<df> x2, const Cx<df> y0,
                        const Cx<df> y1, const Cx<df> y2) {
-  DfAcc re{0.0f, 0.0f}, im{0.0f, 0.0f};
   const Cx<df> xs[3] = {x0, x1, x2}, ys[3] = {y0, y1, y2};
+  // (a + ib)(c + id) = (ac - bd) + i(ad + bc);  conj: (ac + bd) + i(ad - bc)
+  DfAcc re = dfacc_first(xs[0].re, ys[0].re, false);
+  DfAcc im = dfacc_first(xs[0].re, ys[0].im, false);
+  dfacc_add_prod(re, xs[0].im, ys[0].im, !CONJ);
+  dfacc_add_prod(im, xs[0].im, ys[0].re, CONJ);
 #pragma unroll
-  for (int j = 0; j < 3; j++) {
-    // (a + ib)(c + id) = (ac - bd) + i(ad + bc);  conj: (ac + bd) + i(ad - bc)
+  for (int j = 1; j < 3; j++) {
     dfacc_add_prod(re, xs[j].re, ys[j].re, false);
     dfacc_add_prod(re, xs[j].im, ys[j].im, !CONJ);
     dfacc_add_prod(im, xs[j].re, ys[j].im, false);
     dfacc_add_prod(im, xs[j].im, ys[j].re, CONJ);
   }
+  if (LAZY) return {{re.s, re.e}, {im.s, im.e}};
   return {dfacc_result(re), dfacc_result(im)};
+}
+
+// Double-word sum without the final renormalisation (TwoSum of the high
+// parts, low parts added in float: 8 operations).  The value hi + lo is the
+// same as with renormalisation; the hop accumulates its sums this way and
+// renormalises each accumulator once, before the epilogue.
+LQCD_DEV df add_lazy(df a, df b) {
+  df s = two_sum(a.hi, b.hi);
+  s.lo = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+  return s;
+}
+LQCD_DEV df neg_df(df a) { return {-a.hi, -a.lo}; }
+LQCD_DEV Cx<df> cadd_lazy(Cx<df> a, Cx<df> b) { return {add_lazy(a.re, b.re), add_lazy(a.im, b.im)}; }
+LQCD_DEV Cx<df> csub_lazy(Cx<df> a, Cx<df> b) {
+  return {add_lazy(a.re, neg_df(b.re)), add_lazy(a.im, neg_df(b.im))};
+}
+LQCD_DEV Cx<df> cnormalise(Cx<df> a) {
+  return {fast_two_sum(a.re.hi, a.re.lo), fast_two_sum(a.im.hi, a.im.lo)};
 }
 
 template <>
@@ -145,6 +213,7 @@ struct HopArgs {
   size_t in_rs, out_rs, aux_rs;       // bytes per rhs
   size_t in_srs, out_srs, aux_srs;    // floats per rhs
   int out_parity, nrhs, has_aux;
+  int c_one;  // c_up = c_dn = 1: the epilogue skips the multiplication
   HostC c_up, c_dn, d_up, d_dn;
   double *partials;
   int *halt;
@@ -158,53 +227,115 @@ LQCD_DEV void negate_if(Cx<R> v[6], bool neg) {
   }
 }
 
+// Neighbour spinor load: 16-bit formats return their values unscaled with
+// the site scale, which acc_nb applies; other formats return scale 1.
+template <int PREC>
+LQCD_DEV float load_nb(const SpinorView &vin, int j, Cx<typename SpinorIO<PREC>::R> ps[12]) {
+  if constexpr (kScaled16<PREC>) {
+    return SpinorIO<PREC>::load_unscaled(vin, j, ps);
+  } else {
+    SpinorIO<PREC>::load(vin, j, ps);
+    return 1.0f;
+  }
+}
+// acc += (neg ? -1 : 1) sc [v; -s B^+ v]
+template <int PREC, int MU, int S>
+LQCD_DEV void acc_nb(Cx<typename SpinorIO<PREC>::R> v[6], float sc, bool neg,
+                     Cx<typename SpinorIO<PREC>::R> acc[12]) {
+  if constexpr (kScaled16<PREC>) {
+    accumulate_scaled<MU, S>(v, neg ? -sc : sc, acc);
+  } else {
+    (void)sc;
+    negate_if(v, neg);
+    accumulate<MU, S>(v, acc);
+  }
+}
+
 template <int PREC, int RECON, int MU, int S, bool LF = true>
 LQCD_DEV void hop_dir(const HopArgs &A, const Site &s, int p, int cb, const SpinorView &vin,
                       Cx<typename SpinorIO<PREC>::R> acc[12]) {
   using R = typename SpinorIO<PREC>::R;
   Cx<R> ps[12], h[6], v[6], u[9];
+  const bool negf = MU == 3 && A.g.antiper && s.t == A.g.L[3] - 1;
+  const bool negb = MU == 3 && A.g.antiper && s.t == 0;
   if (LF && (PREC == LQCD_F32 || PREC == LQCD_BF16S || PREC == LQCD_F16S)) {
     // memory-bound formats: issue both neighbours' spinor and link loads
     // before any arithmetic, so one thread has four load groups in flight
     const int jf = neighbour_cb(A.g, s, MU, +1), jb = neighbour_cb(A.g, s, MU, -1);
     Cx<R> pb[12], ub[9];
-    SpinorIO<PREC>::load(vin, jf, ps);
+    const float scf = load_nb<PREC>(vin, jf, ps);
     LinkIO<PREC, RECON>::load(A.U, p, MU, cb, u);
-    SpinorIO<PREC>::load(vin, jb, pb);
+    const float scb = load_nb<PREC>(vin, jb, pb);
     LinkIO<PREC, RECON>::load(A.U, p ^ 1, MU, jb, ub);
     project<MU, S>(ps, h);
     if (RECON == 12) reconstruct_row2(u);
     mul_link(u, h, v);
-    negate_if(v, MU == 3 && A.g.antiper && s.t == A.g.L[3] - 1);
-    accumulate<MU, S>(v, acc);
+    acc_nb<PREC, MU, S>(v, scf, negf, acc);
     project<MU, -S>(pb, h);
     if (RECON == 12) reconstruct_row2(ub);
     mul_link_dag(ub, h, v);
-    negate_if(v, MU == 3 && A.g.antiper && s.t == 0);
-    accumulate<MU, -S>(v, acc);
+    acc_nb<PREC, MU, -S>(v, scb, negb, acc);
     return;
   }
   // forward: (1 - S gamma_mu) U_mu(x) in(x + mu)
   {
     int j = neighbour_cb(A.g, s, MU, +1);
-    SpinorIO<PREC>::load(vin, j, ps);
+    const float sc = load_nb<PREC>(vin, j, ps);
     project<MU, S>(ps, h);
     LinkIO<PREC, RECON>::load(A.U, p, MU, cb, u);
     if (RECON == 12) reconstruct_row2(u);
     mul_link(u, h, v);
-    negate_if(v, MU == 3 && A.g.antiper && s.t == A.g.L[3] - 1);
-    accumulate<MU, S>(v, acc);
+    acc_nb<PREC, MU, S>(v, sc, negf, acc);
   }
   // backward: (1 + S gamma_mu) U_mu(x - mu)^+ in(x - mu)
   {
     int j = neighbour_cb(A.g, s, MU, -1);
-    SpinorIO<PREC>::load(vin, j, ps);
+    const float sc = load_nb<PREC>(vin, j, ps);
     project<MU, -S>(ps, h);
     LinkIO<PREC, RECON>::load(A.U, p ^ 1, MU, j, u);
     if (RECON == 12) reconstruct_row2(u);
     mul_link_dag(u, h, v);
-    negate_if(v, MU == 3 && A.g.antiper && s.t == 0);
-    accumulate<MU, -S>(v, acc);
+    acc_nb<PREC, MU, -S>(v, sc, negb, acc);
+  }
+}
+
+// Epilogue of one output site and right-hand side: out = c * acc + d * aux,
+// the store, and the site's |out|^2 (the REDUCE partial's summand).
+template <int PREC, bool REDUCE>
+LQCD_DEV double hop_epilogue(const HopArgs &A, int cb, int rhs, const Cx<typename SpinorIO<PREC>::R> acc[12]) {
+  using R = typename SpinorIO<PREC>::R;
+  const Cx<R> cu = cfrom<R>(A.c_up), cd = cfrom<R>(A.c_dn);
+  Cx<R> res[12];
+  if (A.c_one) {
+#pragma unroll
+    for (int k = 0; k < 12; k++) res[k] = acc[k];
+  } else {
+#pragma unroll
+    for (int k = 0; k < 12; k++) res[k] = (k < 6 ? cu : cd) * acc[k];
+  }
+  if (A.has_aux) {
+    SpinorView vaux{(void *)(A.aux + rhs * A.aux_rs),
+                    A.aux_scale ? (float *)A.aux_scale + rhs * A.aux_srs : nullptr, A.g.Vh};
+    Cx<R> ax[12];
+    SpinorIO<PREC>::load(vaux, cb, ax);
+    const Cx<R> du = cfrom<R>(A.d_up), dd = cfrom<R>(A.d_dn);
+#pragma unroll
+    for (int k = 0; k < 12; k++) res[k] = cmadd(k < 6 ? du : dd, ax[k], res[k]);
+  }
+  SpinorView vout{A.out + rhs * A.out_rs, A.out_scale ? A.out_scale + rhs * A.out_srs : nullptr, A.g.Vh};
+  SpinorIO<PREC>::store(vout, cb, res);
+  return REDUCE ? site_norm2<R, 12>(res) : 0.0;
+}
+
+// One partial per warp of 32 consecutive sites, whatever the block shape or
+// the number of right-hand sides per thread, so every launch shape reduces in
+// the same order.  All 32 lanes of the warp call it together.
+LQCD_DEV void hop_warp_partial(const HopArgs &A, int cb, int rhs, double nrm) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) nrm += __shfl_down_sync(0xffffffffu, nrm, o);
+  if ((threadIdx.x & 31) == 0 && rhs < A.nrhs && cb < A.g.Vh) {
+    const int nw = (A.g.Vh + 31) >> 5;
+    A.partials[(size_t)rhs * nw + (cb >> 5)] = nrm;
   }
 }
 
@@ -228,38 +359,98 @@ LQCD_DEV void hop_site(const HopArgs &A, int cb, int rhs) {
     hop_dir<PREC, RECON, 1, S, LF>(A, s, p, cb, vin, acc);
     hop_dir<PREC, RECON, 2, S, LF>(A, s, p, cb, vin, acc);
     hop_dir<PREC, RECON, 3, S, LF>(A, s, p, cb, vin, acc);
-    // epilogue: out = c * acc + d * aux
-    const Cx<R> cu = cfrom<R>(A.c_up), cd = cfrom<R>(A.c_dn);
-    Cx<R> res[12];
+    nrm = hop_epilogue<PREC, REDUCE>(A, cb, rhs, acc);
+  }
+  if (REDUCE) hop_warp_partial(A, cb, rhs, nrm);
+}
+
+// ---------------------------------------------------------------------------
+// Register-blocked multi-RHS hop: one thread owns one output site and RT
+// consecutive right-hand sides.  Each link is loaded (and its third row
+// rebuilt) once per direction and applied to the RT neighbour spinors, which
+// cuts the per-RHS load and reconstruction instructions by RT.  Every RHS goes
+// through the same arithmetic, in the same order, as in hop_site, so the
+// results are bitwise those of single-RHS launches.  Right-hand sides past
+// nrhs (a ragged last group) recompute the last valid one and are not stored.
+// ---------------------------------------------------------------------------
+template <int PREC, int RECON, int MU, int S, int RT>
+LQCD_DEV void hop_dir_rt(const HopArgs &A, const Site &s, int p, int cb, const int rhs[RT],
+                         Cx<typename SpinorIO<PREC>::R> acc[RT][12]) {
+  using R = typename SpinorIO<PREC>::R;
 #pragma unroll
-    for (int k = 0; k < 12; k++) res[k] = (k < 6 ? cu : cd) * acc[k];
-    if (A.has_aux) {
-      SpinorView vaux{(void *)(A.aux + rhs * A.aux_rs),
-                      A.aux_scale ? (float *)A.aux_scale + rhs * A.aux_srs : nullptr, A.g.Vh};
-      Cx<R> ax[12];
-      SpinorIO<PREC>::load(vaux, cb, ax);
-      const Cx<R> du = cfrom<R>(A.d_up), dd = cfrom<R>(A.d_dn);
+  for (int dir = 0; dir < 2; dir++) {
+    const int j = neighbour_cb(A.g, s, MU, dir == 0 ? +1 : -1);
+    Cx<R> u[9];
+    LinkIO<PREC, RECON>::load(A.U, dir == 0 ? p : p ^ 1, MU, dir == 0 ? cb : j, u);
+    // project each neighbour spinor as soon as it arrives: only the RT
+    // half spinors (6 complex each) stay live across the link product
+    Cx<R> h[RT][6];
+    float sc[RT];
 #pragma unroll
-      for (int k = 0; k < 12; k++) res[k] = cmadd(k < 6 ? du : dd, ax[k], res[k]);
+    for (int r = 0; r < RT; r++) {
+      SpinorView vin{A.in + rhs[r] * A.in_rs, A.in_scale ? A.in_scale + rhs[r] * A.in_srs : nullptr, A.g.Vh};
+      Cx<R> ps[12];
+      sc[r] = load_nb<PREC>(vin, j, ps);
+      if (dir == 0) project<MU, S>(ps, h[r]);
+      else project<MU, -S>(ps, h[r]);
     }
-    SpinorView vout{A.out + rhs * A.out_rs, A.out_scale ? A.out_scale + rhs * A.out_srs : nullptr,
-                    A.g.Vh};
-    SpinorIO<PREC>::store(vout, cb, res);
-    if (REDUCE) {
+    if (RECON == 12) reconstruct_row2(u);
+    const bool neg = MU == 3 && A.g.antiper && s.t == (dir == 0 ? A.g.L[3] - 1 : 0);
 #pragma unroll
-      for (int k = 0; k < 12; k++) nrm += norm2_d(res[k]);
+    for (int r = 0; r < RT; r++) {
+      Cx<R> v[6];
+      if (dir == 0) {
+        mul_link(u, h[r], v);
+        acc_nb<PREC, MU, S>(v, sc[r], neg, acc[r]);
+      } else {
+        mul_link_dag(u, h[r], v);
+        acc_nb<PREC, MU, -S>(v, sc[r], neg, acc[r]);
+      }
     }
+  }
+}
+
+template <int PREC, int RECON, bool DAG, bool REDUCE, int RT>
+LQCD_DEV void hop_site_rt(const HopArgs &A, int cb, int rhs0) {
+  using R = typename SpinorIO<PREC>::R;
+  const int p = A.out_parity;
+  int rhs[RT];
+#pragma unroll
+  for (int r = 0; r < RT; r++) rhs[r] = min(rhs0 + r, A.nrhs - 1);
+  double nrm[RT];
+#pragma unroll
+  for (int r = 0; r < RT; r++) nrm[r] = 0.0;
+  if (cb < A.g.Vh) {
+    const Site s = site_of(A.g, p, cb);
+    Cx<R> acc[RT][12];
+#pragma unroll
+    for (int r = 0; r < RT; r++)
+#pragma unroll
+      for (int k = 0; k < 12; k++) acc[r][k] = czero<R>();
+    constexpr int S = DAG ? -1 : 1;
+    hop_dir_rt<PREC, RECON, 0, S, RT>(A, s, p, cb, rhs, acc);
+    hop_dir_rt<PREC, RECON, 1, S, RT>(A, s, p, cb, rhs, acc);
+    hop_dir_rt<PREC, RECON, 2, S, RT>(A, s, p, cb, rhs, acc);
+    hop_dir_rt<PREC, RECON, 3, S, RT>(A, s, p, cb, rhs, acc);
+#pragma unroll
+    for (int r = 0; r < RT; r++)
+      if (rhs0 + r < A.nrhs) nrm[r] = hop_epilogue<PREC, REDUCE>(A, cb, rhs0 + r, acc[r]);
   }
   if (REDUCE) {
-    // one partial per warp of 32 consecutive sites, whatever the block shape,
-    // so single- and multi-RHS launches reduce in the same order
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) nrm += __shfl_down_sync(0xffffffffu, nrm, o);
-    if ((threadIdx.x & 31) == 0 && rhs < A.nrhs && cb < A.g.Vh) {
-      const int nw = (A.g.Vh + 31) >> 5;
-      A.partials[(size_t)rhs * nw + (cb >> 5)] = nrm;
-    }
+    for (int r = 0; r < RT; r++) hop_warp_partial(A, cb, rhs0 + r, nrm[r]);
   }
+}
+
+// Blocks of 32 sites x blockDim.y RHS groups of RT; grid z covers the groups.
+template <int PREC, int RECON, bool DAG, bool REDUCE, int RT>
+__global__ void __launch_bounds__(128) hop_rt_kernel(HopArgs A) {
+  if (A.halt && *(volatile int *)A.halt) return;
+  const int rhs0 = (blockIdx.z * blockDim.y + threadIdx.y) * RT;
+  if (rhs0 >= A.nrhs) return;  // whole warps: blockDim.x is 32
+  const int stride = gridDim.x * blockDim.x;
+  for (int base = blockIdx.x * blockDim.x; base < A.g.Vh; base += stride)
+    hop_site_rt<PREC, RECON, DAG, REDUCE, RT>(A, base + threadIdx.x, rhs0);
 }
 
 // Grid-stride over the output sites: a full grid (one site per thread) or a
@@ -304,7 +495,7 @@ LQCD_DEV void df_pair_dir(const HopArgs &A, const Site &s, int p, int cb, int k,
       const bool neg = (MU == 0) ? sgn < 0 : (MU == 1) ? (k == 0 ? sgn < 0 : sgn > 0)
                      : (MU == 2) ? (k == 0 ? sgn < 0 : sgn > 0) : sgn > 0;
       Cx<df> t = (MU == 0 || MU == 2) ? times_i(pb) : pb;
-      h[c] = neg ? pa - t : pa + t;
+      h[c] = neg ? csub_lazy(pa, t) : cadd_lazy(pa, t);
     }
     const float4 *ub = (const float4 *)((const char *)A.U.ptr + (dir == 0 ? p : p ^ 1) * A.U.parity_stride +
                                         MU * A.U.mu_stride);
@@ -318,8 +509,8 @@ LQCD_DEV void df_pair_dir(const HopArgs &A, const Site &s, int p, int cb, int k,
         float4 w = __ldg(ub + (size_t)(dir == 0 ? 3 * a + q : 3 * q + a) * A.U.Vh + lc);
         u3[q] = {{w.x, w.z}, {w.y, w.w}};
       }
-      v[a] = dir == 0 ? dfdot3<false>(u3[0], u3[1], u3[2], h[0], h[1], h[2])
-                      : dfdot3<true>(u3[0], u3[1], u3[2], h[0], h[1], h[2]);
+      v[a] = dir == 0 ? dfdot3<false, true>(u3[0], u3[1], u3[2], h[0], h[1], h[2])
+                      : dfdot3<true, true>(u3[0], u3[1], u3[2], h[0], h[1], h[2]);
     }
     if (MU == 3 && A.g.antiper && s.t == (dir == 0 ? A.g.L[3] - 1 : 0)) {
 #pragma unroll
@@ -329,11 +520,12 @@ LQCD_DEV void df_pair_dir(const HopArgs &A, const Site &s, int p, int cb, int k,
     // (k==0 ? -sgn*i : +sgn*i) (z, to 2+k), -sgn (t, to 2+k)
 #pragma unroll
     for (int a = 0; a < 3; a++) {
-      up[a] = up[a] + v[a];
-      if (MU == 0) lswap[a] = sgn > 0 ? lswap[a] - times_i(v[a]) : lswap[a] + times_i(v[a]);
-      else if (MU == 1) lswap[a] = ((k == 0) == (sgn > 0)) ? lswap[a] + v[a] : lswap[a] - v[a];
-      else if (MU == 2) lsame[a] = ((k == 0) == (sgn > 0)) ? lsame[a] - times_i(v[a]) : lsame[a] + times_i(v[a]);
-      else lsame[a] = sgn > 0 ? lsame[a] - v[a] : lsame[a] + v[a];
+      up[a] = cadd_lazy(up[a], v[a]);
+      if (MU == 0) lswap[a] = sgn > 0 ? csub_lazy(lswap[a], times_i(v[a])) : cadd_lazy(lswap[a], times_i(v[a]));
+      else if (MU == 1) lswap[a] = ((k == 0) == (sgn > 0)) ? cadd_lazy(lswap[a], v[a]) : csub_lazy(lswap[a], v[a]);
+      else if (MU == 2)
+        lsame[a] = ((k == 0) == (sgn > 0)) ? csub_lazy(lsame[a], times_i(v[a])) : cadd_lazy(lsame[a], times_i(v[a]));
+      else lsame[a] = sgn > 0 ? csub_lazy(lsame[a], v[a]) : cadd_lazy(lsame[a], v[a]);
     }
   }
 }
@@ -372,15 +564,16 @@ __global__ void __launch_bounds__(128) hop_df64_pair_kernel(HopArgs A) {
       o.re.lo = __shfl_xor_sync(0xffffffffu, lswap[a].re.lo, 1);
       o.im.hi = __shfl_xor_sync(0xffffffffu, lswap[a].im.hi, 1);
       o.im.lo = __shfl_xor_sync(0xffffffffu, lswap[a].im.lo, 1);
-      lsame[a] = lsame[a] + o;
+      lsame[a] = cnormalise(cadd_lazy(lsame[a], o));
+      up[a] = cnormalise(up[a]);
     }
     if (active) {
       const Cx<df> cu = cfrom<df>(A.c_up), cd = cfrom<df>(A.c_dn);
       Cx<df> ru[3], rl[3];
 #pragma unroll
       for (int a = 0; a < 3; a++) {
-        ru[a] = cu * up[a];
-        rl[a] = cd * lsame[a];
+        ru[a] = A.c_one ? up[a] : cu * up[a];
+        rl[a] = A.c_one ? lsame[a] : cd * lsame[a];
       }
       if (A.has_aux) {
         const float4 *pa = (const float4 *)(A.aux + rhs * A.aux_rs);
@@ -446,6 +639,23 @@ inline void launch_t2(const HopArgs &A, dim3 grid, dim3 block, bool dag, bool re
     else hop_kernel<PREC, RECON, false, false, LF><<<grid, block, 0, st>>>(A);
   }
 }
+template <int PREC, int RECON, int RT>
+inline void launch_rt2(const HopArgs &A, dim3 grid, dim3 block, bool dag, bool red, cudaStream_t st) {
+  if (dag) {
+    if (red) hop_rt_kernel<PREC, RECON, true, true, RT><<<grid, block, 0, st>>>(A);
+    else hop_rt_kernel<PREC, RECON, true, false, RT><<<grid, block, 0, st>>>(A);
+  } else {
+    if (red) hop_rt_kernel<PREC, RECON, false, true, RT><<<grid, block, 0, st>>>(A);
+    else hop_rt_kernel<PREC, RECON, false, false, RT><<<grid, block, 0, st>>>(A);
+  }
+}
+// RHS per thread: 2 or 4 (the register-blocked kernel), else the plain one
+template <int PREC, int RECON>
+inline void launch_rt(const HopArgs &A, int rt, dim3 grid, dim3 block, bool dag, bool red, cudaStream_t st) {
+  if (rt == 4) launch_rt2<PREC, RECON, 4>(A, grid, block, dag, red, st);
+  else launch_rt2<PREC, RECON, 2>(A, grid, block, dag, red, st);
+}
+
 // the loads-first variant exists only for the memory-bound formats
 template <int PREC, int RECON>
 inline void launch_t(const HopArgs &A, dim3 grid, dim3 block, bool dag, bool red, cudaStream_t st,
@@ -464,9 +674,9 @@ inline void launch_t(const HopArgs &A, dim3 grid, dim3 block, bool dag, bool red
 void hop_launch_f64(const HopArgs &A, int recon, dim3 grid, dim3 block, bool dag, bool red, cudaStream_t st);
 void hop_launch_df64(const HopArgs &A, int recon, bool pair, dim3 grid, dim3 block, bool dag, bool red,
                      cudaStream_t st);
-void hop_launch_f32(const HopArgs &A, int recon, dim3 grid, dim3 block, bool dag, bool red, bool lf,
+void hop_launch_f32(const HopArgs &A, int recon, dim3 grid, dim3 block, bool dag, bool red, bool lf, int rt,
                     cudaStream_t st);
-void hop_launch_h16(const HopArgs &A, int prec, dim3 grid, dim3 block, bool dag, bool red, bool lf,
+void hop_launch_h16(const HopArgs &A, int prec, dim3 grid, dim3 block, bool dag, bool red, bool lf, int rt,
                     cudaStream_t st);
 void hop_batched_f64(int recon, bool dag, bool red, const HopArgs *d, const int2 *tl, int ntiles, int grid,
                      const int *halt, cudaStream_t st);

@@ -29,6 +29,7 @@ struct lqcd_ctx {
   lqcd_counters cnt{};
   // launch-shape autotuner (tune.cu)
   int autotune = 1;
+  int forced_choice = -1;  // lqcd_set_launch_choice: >= 0 overrides the tuner
   std::string tune_path;
   std::string gpu_name;
   std::map<std::string, int> tuned;

@@ -56,6 +56,7 @@ static void tune_save(lqcd_ctx *ctx) {
 
 int tune_choice(lqcd_ctx *ctx, const std::string &key0, int ncand, int fallback,
                 const std::function<void(int)> &run) {
+  if (ctx->forced_choice >= 0) return ncand > 0 ? ctx->forced_choice % ncand : fallback;
   const std::string key = ctx->gpu_name + "|" + key0;
   auto it = ctx->tuned.find(key);
   if (it != ctx->tuned.end() && it->second >= 0 && it->second < ncand) return it->second;
@@ -105,5 +106,11 @@ extern "C" int lqcd_set_autotune(lqcd_ctx *ctx, int enable, const char *cache_pa
     ctx->tune_path = cache_path;
     tune_load(ctx);
   }
+  return LQCD_OK;
+}
+
+extern "C" int lqcd_set_launch_choice(lqcd_ctx *ctx, int choice) {
+  if (!ctx) return LQCD_ERR_INVALID;
+  ctx->forced_choice = choice < 0 ? -1 : choice;
   return LQCD_OK;
 }

@@ -104,6 +104,7 @@ SIGNATURES = [
     ("lqcd_last_error", ctypes.c_char_p, [_vp]),
     ("lqcd_get_counters", _i, [_vp, _vp]),
     ("lqcd_set_autotune", _i, [_vp, _i, ctypes.c_char_p]),
+    ("lqcd_set_launch_choice", _i, [_vp, _i]),
     ("lqcd_reset_counters", _i, [_vp]),
     ("lqcd_field_bytes", ctypes.c_size_t, [ctypes.POINTER(lqcd_geom), _i, _i, _i,
                                            ctypes.POINTER(ctypes.c_size_t)]),
@@ -287,6 +288,15 @@ def lqcd_abi_version() -> int:
 
 def lqcd_create(device: int = 0, stream=None) -> Context:
     return Context(device, stream)
+
+
+def lqcd_set_autotune(ctx: Context, enable=True, cache_path=None):
+    ctx.check(lib().lqcd_set_autotune(ctx.handle, int(bool(enable)),
+                                      cache_path.encode() if cache_path else None))
+
+
+def lqcd_set_launch_choice(ctx: Context, choice: int):
+    ctx.check(lib().lqcd_set_launch_choice(ctx.handle, int(choice)))
 
 
 def lqcd_gauge_import(ctx: Context, U_lexi: torch.Tensor, L, recon=18, antiperiodic_t=True) -> Gauge:

@@ -166,6 +166,76 @@ def test_multi_rhs_dslash_matches_single(ctx, oracle):
                                    singles[r][1])
 
 
+@pytest.mark.parametrize("nrhs", [1, 5, 12])
+def test_every_launch_shape_gives_the_same_bits(ctx, nrhs):
+    """Every candidate the autotuner can pick (block shape, grid size, load
+    order, RHS per thread) writes the same bits: the multi-RHS hop of each
+    candidate equals the default launch in every precision, including ragged
+    RHS groups (5 = 2 + 2 + 1, 4 + 1)."""
+    L = (4, 4, 6, 8)
+    U, G12 = _gauge(ctx, L, seed=21, recon=12)
+    G18 = lqcd.lqcd_gauge_import(ctx, dev(U), L, recon=18)
+    for prec, G in ((lqcd.LQCD_F64, G18), (lqcd.LQCD_DF64, G18), (lqcd.LQCD_DF64, G12),
+                    (lqcd.LQCD_F32, G12), (lqcd.LQCD_F32, G18), (lqcd.LQCD_BF16S, G12),
+                    (lqcd.LQCD_F16S, G12)):
+        psis = inputs.gaussian_spinor(L, 22, nrhs=nrhs)
+        n_half, sb_half = lqcd.field_bytes(L, lqcd.LQCD_EVEN, prec, 1)
+        din = torch.zeros(nrhs * n_half // 8, dtype=torch.float64, device="cuda")
+        sin = torch.zeros(max(nrhs * sb_half // 4, 1), dtype=torch.float32, device="cuda")
+        for r in range(nrhs):
+            d, s, _ = eo_full_from_lexi(ctx, L, psis[r], prec)
+            din.view(torch.uint8)[r * n_half:(r + 1) * n_half].copy_(d.view(torch.uint8)[n_half:2 * n_half])
+            if sb_half:
+                sin.view(torch.uint8)[r * sb_half:(r + 1) * sb_half].copy_(
+                    s.view(torch.uint8)[sb_half:2 * sb_half])
+        fi = lqcd.field(din, lqcd.LQCD_LAYOUT_EO, prec, nrhs, sin if sb_half else None)
+
+        def run(choice):
+            dout = torch.full_like(din, float("nan"))
+            sout = torch.full_like(sin, float("nan"))
+            fo = lqcd.field(dout, lqcd.LQCD_LAYOUT_EO, prec, nrhs, sout if sb_half else None)
+            lqcd.lqcd_set_launch_choice(ctx, choice)
+            try:
+                lqcd.lqcd_dslash(ctx, G, fi, fo, lqcd.LQCD_EVEN, 1)
+            finally:
+                lqcd.lqcd_set_launch_choice(ctx, -1)
+            torch.cuda.synchronize()
+            return dout.view(torch.uint8).clone(), (sout.view(torch.uint8).clone() if sb_half else None)
+
+        ref = run(-1)
+        for choice in range(48):
+            got = run(choice)
+            assert torch.equal(got[0], ref[0]), (prec, choice)
+            if sb_half:
+                assert torch.equal(got[1], ref[1]), (prec, choice)
+
+
+def test_cg_iterates_do_not_depend_on_launch_shape(ctx):
+    """A mixed-precision multi-RHS solve (reducing hops, per-warp partials)
+    returns the same bits and iteration counts whatever launch the tuner
+    picks."""
+    L = (4, 4, 6, 8)
+    U, G = _gauge(ctx, L, seed=23, recon=12)
+    nrhs = 3
+    b = dev(inputs.gaussian_spinor(L, 24, nrhs=nrhs))
+    prm = lqcd.cg_params(tol=1e-10, outer_prec=lqcd.LQCD_DF64, inner_prec=lqcd.LQCD_F32,
+                         sloppy_recon=12)
+    outs = []
+    for choice in (-1, 0, 7, 19, 33):
+        x = torch.zeros_like(b)
+        lqcd.lqcd_set_launch_choice(ctx, choice)
+        try:
+            st = lqcd.lqcd_cg_solve(ctx, G, lqcd.field(b, lqcd.LQCD_LAYOUT_LEXI, nrhs=nrhs),
+                                    lqcd.field(x, lqcd.LQCD_LAYOUT_LEXI, nrhs=nrhs), 0.15, 0.01 / 0.3, prm)
+        finally:
+            lqcd.lqcd_set_launch_choice(ctx, -1)
+        torch.cuda.synchronize()
+        outs.append((x.clone(), [s["iters"] for s in st]))
+    for x, its in outs[1:]:
+        assert its == outs[0][1]
+        assert torch.equal(x, outs[0][0])
+
+
 def test_full_size_24x48_apply_M(ctx, oracle):
     """The 24^3 x 48 workload: M and Mhat on every site against the oracle."""
     L = (24, 24, 24, 48)

@@ -146,14 +146,17 @@ def _even_half_field(ctx, L, psi_even):
     return d, fe
 
 
-@pytest.mark.parametrize("outer,inner", [(lqcd.LQCD_F64, lqcd.LQCD_F64),
-                                         (lqcd.LQCD_DF64, lqcd.LQCD_F32)])
-def test_fermion_force_vs_oracle(ctx, oracle, outer, inner):
+@pytest.mark.parametrize("outer,inner,recon", [(lqcd.LQCD_F64, lqcd.LQCD_F64, 18),
+                                               (lqcd.LQCD_DF64, lqcd.LQCD_F32, 18),
+                                               (lqcd.LQCD_F64, lqcd.LQCD_F64, 12)])
+def test_fermion_force_vs_oracle(ctx, oracle, outer, inner, recon):
+    """The adjoint force kernel against the oracle's, with 18-real links and
+    with REC12 links (third row rebuilt inside the force kernel)."""
     L = (4, 4, 2, 4)
     V = inputs.volume(L)
     kappa, mu = 0.14, 0.1
     U = inputs.random_gauge(L, "near", seed=37, eps=0.4)
-    G = lqcd.lqcd_gauge_import(ctx, dev(U), L)
+    G = lqcd.lqcd_gauge_import(ctx, dev(U), L, recon=recon)
     ev = ~oracle.parity_mask(L)
     phi = inputs.gaussian_spinor(L, 38) * ev[:, None, None]
     keep, fphi = _even_half_field(ctx, L, phi)
