@@ -20,9 +20,12 @@
  *
  * Sections of the paper followed:
  *   Sec. 2.1, eq. "D_tm"          : twisted-mass Wilson matrix, hopping term
- *   Sec. 2.1, eq. "S_tlsym" (c1=0): Wilson plaquette gauge action
+ *   Sec. 2.1, eq. "S_tlsym"       : Wilson plaquette action (c1 = 0) and the
+ *                                   tree-level Symanzik action with 2x1 loops
  *   Sec. 2.1, eq. "solvereq"      : D phi = psi solved by CG
- *   Sec. 2.2                      : HMC (Hamiltonian, leapfrog, Metropolis),
+ *   Sec. 2.2, Sec. 5.3            : HMC (Hamiltonian, leapfrog, the 2MN scheme
+ *                                   on separate gauge and fermion time scales,
+ *                                   Metropolis),
  *                                   fermion force through dD^-1 = -D^-1 dD D^-1,
  *                                   Cabibbo-Marinari heatbath with the exact
  *                                   SU(2) update (Fig. "heatbath algorithm")
@@ -635,6 +638,161 @@ void or_gauge_dSdw(const double *U, const int *L, double beta, double *out) {
 }
 
 /* ------------------------------------------------------------------ */
+/* Tree-level Symanzik gauge action (Sec. 2.1, eq. "S_tlsym"):            */
+/*   S = (beta/3) sum_x [ c0 sum_{mu<nu} (3 - Re Tr P_munu(x))             */
+/*                       + c1 sum_{mu != nu} (3 - Re Tr R_munu(x)) ]        */
+/* with c0 = 1 - 8 c1 and R_munu(x) the 2x1 loop that runs two links along  */
+/* mu, one along nu, two back along mu and one back along nu.  The paper's  */
+/* printed c1 = 1/12 is read as the tree-level value c1 = -1/12; c1 is an   */
+/* argument here, and c1 = 0 gives the Wilson action above.                 */
+/*                                                                          */
+/* A loop is a list of steps (direction, sign); a step +d from site s uses  */
+/* U_d(s), a step -d uses U_d(s - d)^+.  The derivative is assembled loop by */
+/* loop, straight from the definition: U_mu(x) -> exp(i w T^a) U_mu(x)       */
+/* changes Re Tr(loop) = Re Tr(U_mu(x) W) at rate -Im Tr(T^a U_mu(x) W),      */
+/* where W is the product of the loop's other links in loop order (taken    */
+/* daggered when the loop runs through U_mu(x) backwards).                  */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+  int dir, sgn;
+} step_t;
+
+/* the matrix of step st taken from site s (into M); returns the next site */
+static long loop_step(const double *U, long s, step_t st, const int *L, cplx *M) {
+  if (st.sgn > 0) {
+    memcpy(M, link_at(U, s, st.dir), 9 * sizeof(cplx));
+    return neighbour(s, st.dir, 1, L);
+  }
+  long b = neighbour(s, st.dir, -1, L);
+  mat_dag(link_at(U, b, st.dir), M);
+  return b;
+}
+
+/* site reached from y after the first k steps */
+static long loop_walk(long y, const step_t *st, int k, const int *L) {
+  for (int j = 0; j < k; j++) y = neighbour(y, st[j].dir, st[j].sgn, L);
+  return y;
+}
+
+/* product of `count` consecutive steps of the closed loop (y, st[0..n)),
+ * starting with step k0 (indices taken cyclically) */
+static void loop_product(const double *U, long y, const step_t *st, int n, int k0, int count,
+                         const int *L, cplx *out) {
+  cplx M[9];
+  long s = loop_walk(y, st, k0, L);
+  for (int k = 0; k < 9; k++) out[k] = (k % 4 == 0) ? 1.0 : 0.0;
+  for (int j = 0; j < count; j++) {
+    s = loop_step(U, s, st[(k0 + j) % n], L, M);
+    mat_mul(out, M, out);
+  }
+}
+
+static void plaquette_steps(int mu, int nu, step_t st[4]) {
+  st[0] = (step_t){mu, 1}; st[1] = (step_t){nu, 1}; st[2] = (step_t){mu, -1}; st[3] = (step_t){nu, -1};
+}
+static void rectangle_steps(int mu, int nu, step_t st[6]) {
+  st[0] = (step_t){mu, 1}; st[1] = (step_t){mu, 1}; st[2] = (step_t){nu, 1};
+  st[3] = (step_t){mu, -1}; st[4] = (step_t){mu, -1}; st[5] = (step_t){nu, -1};
+}
+
+static double re_tr_loop(const double *U, long y, const step_t *st, int n, const int *L) {
+  cplx P[9];
+  loop_product(U, y, st, n, 0, n, L, P);
+  return creal(mat_trace(P));
+}
+
+/* sum_{x, mu != nu} (3 - Re Tr R_munu(x)) */
+double or_rectangle_sum(const double *U, const int *L) {
+  long V = volume(L);
+  double s = 0;
+#pragma omp parallel for reduction(+ : s) schedule(static)
+  for (long i = 0; i < V; i++)
+    for (int mu = 0; mu < 4; mu++)
+      for (int nu = 0; nu < 4; nu++) {
+        if (nu == mu) continue;
+        step_t st[6];
+        rectangle_steps(mu, nu, st);
+        s += 3.0 - re_tr_loop(U, i, st, 6, L);
+      }
+  return s;
+}
+
+double or_gauge_action_sym(const double *U, const int *L, double beta, double c1) {
+  long V = volume(L);
+  double sp = 0;
+#pragma omp parallel for reduction(+ : sp) schedule(static)
+  for (long i = 0; i < V; i++)
+    for (int mu = 0; mu < 4; mu++)
+      for (int nu = mu + 1; nu < 4; nu++) {
+        step_t st[4];
+        plaquette_steps(mu, nu, st);
+        sp += 3.0 - re_tr_loop(U, i, st, 4, L);
+      }
+  double sr = c1 != 0.0 ? or_rectangle_sum(U, L) : 0.0;
+  return beta / 3.0 * ((1.0 - 8.0 * c1) * sp + c1 * sr);
+}
+
+/* W_mu(x) += coef * (other links of loop (y, st)) for every position of the
+ * loop at which it runs through a link; accumulated serially into W[V][4][9] */
+static void add_loop_staples(const double *U, long y, const step_t *st, int n, double coef, const int *L,
+                             cplx *W) {
+  long s = y;
+  for (int k = 0; k < n; k++) {
+    long x;
+    int back = st[k].sgn < 0;
+    if (!back) x = s;                                  /* runs through U_d(s) forwards   */
+    else x = neighbour(s, st[k].dir, -1, L);           /* runs through U_d(s - d) back   */
+    cplx R[9], Rd[9];
+    loop_product(U, y, st, n, (k + 1) % n, n - 1, L, R);
+    cplx *w = W + ((size_t)x * 4 + st[k].dir) * 9;
+    if (back) {
+      mat_dag(R, Rd);
+      for (int q = 0; q < 9; q++) w[q] += coef * Rd[q];
+    } else {
+      for (int q = 0; q < 9; q++) w[q] += coef * R[q];
+    }
+    s = neighbour(s, st[k].dir, st[k].sgn, L);
+  }
+}
+
+/* dS/domega^a_mu(x) of the tlSym action, [mu][V][8]:
+ *   dS/domega^a = -(beta/3) Re Tr[i T^a U_mu(x) W_mu(x)],
+ *   W = c0 (plaquette staples) + c1 (rectangle staples).                   */
+void or_gauge_dSdw_sym(const double *U, const int *L, double beta, double c1, double *out) {
+  build_generators();
+  build_gammas();
+  long V = volume(L);
+  cplx *W = calloc((size_t)V * 4 * 9, sizeof(cplx));
+  for (long y = 0; y < V; y++)
+    for (int mu = 0; mu < 4; mu++)
+      for (int nu = 0; nu < 4; nu++) {
+        if (nu == mu) continue;
+        if (nu > mu) {
+          step_t sp[4];
+          plaquette_steps(mu, nu, sp);
+          add_loop_staples(U, y, sp, 4, 1.0 - 8.0 * c1, L, W);
+        }
+        if (c1 != 0.0) {
+          step_t sr[6];
+          rectangle_steps(mu, nu, sr);
+          add_loop_staples(U, y, sr, 6, c1, L, W);
+        }
+      }
+#pragma omp parallel for schedule(static)
+  for (long i = 0; i < V; i++)
+    for (int mu = 0; mu < 4; mu++) {
+      cplx UW[9], TW[9];
+      mat_mul(link_at(U, i, mu), W + ((size_t)i * 4 + mu) * 9, UW);
+      for (int a = 0; a < 8; a++) {
+        mat_mul(Tgen[a], UW, TW);
+        out[((long)mu * V + i) * 8 + a] = -(beta / 3.0) * creal(I * mat_trace(TW));
+      }
+    }
+  free(W);
+}
+
+/* ------------------------------------------------------------------ */
 /* Fermion force (Sec. 2.2: dD^-1 = -D^-1 (dD) D^-1; only the hopping     */
 /* term depends on U).  For S_pf = phi^+ (Mhat^+ Mhat)^-1 phi on the even */
 /* sites, with X = (Mhat^+ Mhat)^-1 phi and Y = Mhat X,                   */
@@ -1141,5 +1299,88 @@ double or_hmc_md(double *U, double *P, const double *phi, const int *L, double b
   }
   free(F);
   free(X);
+  return H1 - H0;
+}
+
+/* ------------------------------------------------------------------ */
+/* HMC with the second-order minimum-norm (2MN, Omelyan) integrator on   */
+/* two time scales (Sec. 2.2: "2MN scheme", "multiple timescales"; Sec.  */
+/* 5.3: separate scales for the gauge and fermion parts, 2MN on each).   */
+/* One 2MN step of size e for a force F and position update Q(h):        */
+/*   P -= lambda e dS;  Q(e/2);  P -= (1 - 2 lambda) e dS;  Q(e/2);       */
+/*   P -= lambda e dS.                                                    */
+/* Outer scale: the fermion force, n_f steps over tau.  Every outer      */
+/* position update Q(h) is the inner integration of the gauge force over  */
+/* time h with n_g 2MN steps, whose own position update is               */
+/* U <- exp(i h' P) U.  Each force is evaluated where the scheme needs it */
+/* (no merging of consecutive momentum updates).  With nf = 0 only the    */
+/* gauge force acts.  Returns dH; h_out = (H0, H1, S_pf0).                */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+  const int *L;
+  double beta, c1, kappa, mu, lambda, tol;
+  int nf, ng, max_iter;
+  const double *phi;
+  double *X, *F;
+  long nP;
+} md_ctx;
+
+static void p_update(double *P, const double *F, double w, long n) {
+  for (long k = 0; k < n; k++) P[k] -= w * F[k];
+}
+
+static void inner_gauge_2mn(md_ctx *c, double *U, double *P, double h) {
+  double d = h / c->ng;
+  for (int s = 0; s < c->ng; s++) {
+    or_gauge_dSdw_sym(U, c->L, c->beta, c->c1, c->F);
+    p_update(P, c->F, c->lambda * d, c->nP);
+    or_update_links(U, P, c->L, 0.5 * d);
+    or_gauge_dSdw_sym(U, c->L, c->beta, c->c1, c->F);
+    p_update(P, c->F, (1.0 - 2.0 * c->lambda) * d, c->nP);
+    or_update_links(U, P, c->L, 0.5 * d);
+    or_gauge_dSdw_sym(U, c->L, c->beta, c->c1, c->F);
+    p_update(P, c->F, c->lambda * d, c->nP);
+  }
+}
+
+static void fermion_step(md_ctx *c, const double *U, double *P, double w) {
+  if (!c->nf) return;
+  double resid;
+  or_cg(U, c->phi, c->X, c->L, 1, c->kappa, c->mu, c->tol, c->max_iter, 1, &resid);
+  or_fermion_dSdw(U, c->X, c->L, 1, c->kappa, c->mu, 1, c->F);
+  p_update(P, c->F, w, c->nP);
+}
+
+double or_hmc_md_2mn(double *U, double *P, const double *phi, const int *L, double beta, double c1,
+                     double kappa, double mu, int nf, int nsteps_f, int nsteps_g, double lambda,
+                     double tau, double tol, int max_iter, double *h_out) {
+  build_gammas();
+  build_generators();
+  long V = volume(L);
+  md_ctx c = {L, beta, c1, kappa, mu, lambda, tol, nf, nsteps_g, max_iter, phi, NULL, NULL, 32 * V};
+  c.F = malloc(c.nP * sizeof(double));
+  c.X = calloc((size_t)V * 24, sizeof(double));
+  double S0 = or_gauge_action_sym(U, L, beta, c1), Sf0 = 0;
+  if (nf) Sf0 = or_pseudofermion_action(U, phi, c.X, L, 1, kappa, mu, 1, tol, max_iter);
+  double H0 = kinetic(P, c.nP) + S0 + Sf0;
+  double e = tau / nsteps_f;
+  for (int s = 0; s < nsteps_f; s++) {
+    fermion_step(&c, U, P, lambda * e);
+    inner_gauge_2mn(&c, U, P, 0.5 * e);
+    fermion_step(&c, U, P, (1.0 - 2.0 * lambda) * e);
+    inner_gauge_2mn(&c, U, P, 0.5 * e);
+    fermion_step(&c, U, P, lambda * e);
+  }
+  double S1 = or_gauge_action_sym(U, L, beta, c1), Sf1 = 0;
+  if (nf) Sf1 = or_pseudofermion_action(U, phi, c.X, L, 1, kappa, mu, 1, tol, max_iter);
+  double H1 = kinetic(P, c.nP) + S1 + Sf1;
+  if (h_out) {
+    h_out[0] = H0;
+    h_out[1] = H1;
+    h_out[2] = Sf0;
+  }
+  free(c.F);
+  free(c.X);
   return H1 - H0;
 }

@@ -101,6 +101,15 @@ def _declare(L):
                             ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                             ctypes.c_double, ctypes.c_int, _dp]
     L.or_hmc_md.restype = ctypes.c_double
+    L.or_rectangle_sum.argtypes = [_dp, _ip]
+    L.or_rectangle_sum.restype = ctypes.c_double
+    L.or_gauge_action_sym.argtypes = [_dp, _ip, ctypes.c_double, ctypes.c_double]
+    L.or_gauge_action_sym.restype = ctypes.c_double
+    L.or_gauge_dSdw_sym.argtypes = [_dp, _ip, ctypes.c_double, ctypes.c_double, _dp]
+    L.or_hmc_md_2mn.argtypes = [_dp, _dp, _dp, _ip, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int, _dp]
+    L.or_hmc_md_2mn.restype = ctypes.c_double
 
 
 def _p(a: np.ndarray):
@@ -368,4 +377,45 @@ def hmc_md(U, P, phi, L, beta, kappa, mu, nf=1, nsteps=10, tau=1.0, tol=1e-12,
     h = np.zeros(3, np.float64)
     dH = lib().or_hmc_md(_p(U), _p(P), _p(phi), _dims(L), beta, kappa, mu, int(nf), int(nsteps),
                          tau, tol, int(max_iter), _p(h))
+    return U, P, dH, tuple(h)
+
+
+# -- tree-level Symanzik gauge action and the 2MN integrator (Sec. 2.1 eq.
+# "S_tlsym", Sec. 2.2) -------------------------------------------------------
+
+TLSYM_C1 = -1.0 / 12.0  # tree-level value (the printed +1/12 is read as -1/12)
+OMELYAN_LAMBDA = 0.1931833275037836  # 2MN parameter (Omelyan, Mryglod, Folk 2003)
+
+
+def rectangle_sum(U, L) -> float:
+    """sum_{x, mu != nu} (3 - Re Tr R_munu(x)) over the 2x1 loops."""
+    V = volume(L)
+    U = _cplx(U, (V, 4, 3, 3))
+    return lib().or_rectangle_sum(_p(U), _dims(L))
+
+
+def gauge_action_sym(U, L, beta, c1=TLSYM_C1) -> float:
+    V = volume(L)
+    U = _cplx(U, (V, 4, 3, 3))
+    return lib().or_gauge_action_sym(_p(U), _dims(L), beta, c1)
+
+
+def gauge_dSdw_sym(U, L, beta, c1=TLSYM_C1) -> np.ndarray:
+    V = volume(L)
+    U = _cplx(U, (V, 4, 3, 3))
+    out = np.zeros((4, V, 8), np.float64)
+    lib().or_gauge_dSdw_sym(_p(U), _dims(L), beta, c1, _p(out))
+    return out
+
+
+def hmc_md_2mn(U, P, phi, L, beta, kappa, mu, c1=TLSYM_C1, nf=1, nsteps_f=10, nsteps_g=10,
+               lam=OMELYAN_LAMBDA, tau=1.0, tol=1e-12, max_iter=100000):
+    """Nested 2MN molecular dynamics.  Returns (U', P', dH, (H0, H1, Spf0))."""
+    V = volume(L)
+    U = np.array(_cplx(U, (V, 4, 3, 3)), copy=True)
+    P = np.array(P, dtype=np.float64, copy=True, order="C")
+    phi = _cplx(phi if phi is not None else np.zeros((V, 4, 3)), (V, 4, 3))
+    h = np.zeros(3, np.float64)
+    dH = lib().or_hmc_md_2mn(_p(U), _p(P), _p(phi), _dims(L), beta, c1, kappa, mu, int(nf),
+                             int(nsteps_f), int(nsteps_g), lam, tau, tol, int(max_iter), _p(h))
     return U, P, dH, tuple(h)
