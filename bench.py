@@ -212,7 +212,9 @@ def run_gpu(args):
     V = int(np.prod(L))
     Vh = V // 2
     U_d = torch.from_numpy(U_h).cuda()
-    G = lqcd.lqcd_gauge_import(ctx, U_d, L, recon=recon)
+    # a mixed solve keeps 18-real links for its FP64-class operator (ALU-bound
+    # on GB300, so rebuilding rows costs time) and uses `recon` for the sloppy one
+    G = lqcd.lqcd_gauge_import(ctx, U_d, L, recon=recon if inner == prec else 18)
     del U_d
     b_d = torch.from_numpy(b_h).cuda()
     bd, _ = lqcd.alloc_field(L, lqcd.LQCD_FULL, lqcd.LQCD_F64)
@@ -272,6 +274,8 @@ def run_gpu(args):
     e2e = run_e2e(ctx, lqcd, torch, U_h, b_h, prm, recon, args, stream)
 
     peaks, peak_kind = measured_peaks()
+    if args.traffic is None:
+        args.traffic = NCU_TRAFFIC.get((hop["kernel"], tuple(L), inner, recon))
     if inner == lqcd.LQCD_F64:
         roof = {"bound": "alu", "achieved": hop["tflops"], "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": hop["tflops"] / FP64_PEAK_TFLOPS, "traffic": args.traffic,
@@ -316,10 +320,38 @@ def ctypes_byref(x):
     return ctypes.byref(x)
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
+# half hop timed by time_half_hop, from one ncu capture of that launch
+# (profiles/hop_f64_24x48_ncu.md); valid only for the kernel as captured.
+NCU_TRAFFIC = {("hop_kernel prec=0 recon=18", (24, 24, 24, 48), 0, 18): 527603712.0}
+
+
+def nvtx_push(name):
+    try:
+        import torch
+        torch.cuda.nvtx.range_push(name)
+    except Exception:
+        pass
+
+
+def nvtx_pop():
+    try:
+        import torch
+        torch.cuda.nvtx.range_pop()
+    except Exception:
+        pass
+
+
 def time_half_hop(ctx, G, lqcd, torch, prec, recon, stream, reps=30):
     """Average duration of the half hop (no epilogue) with CUDA events."""
     n_half, sb = lqcd.field_bytes(L, lqcd.LQCD_EVEN, prec, 1)
-    din = torch.zeros(n_half // 8, dtype=torch.float64, device="cuda")
+    gen = torch.Generator(device="cuda").manual_seed(7)
+    if sb:  # 16-bit values in [-1, 1) with unit site scales
+        din = torch.zeros(n_half // 8, dtype=torch.float64, device="cuda")
+    else:   # Gaussian reals (F64 / F32; DF64 high and low words alike)
+        din = torch.randn(n_half // 8, dtype=torch.float64, device="cuda", generator=gen)
+        if prec != lqcd.LQCD_F64:
+            din = torch.randn(n_half // 4, dtype=torch.float32, device="cuda", generator=gen).view(torch.float64)
     dout = torch.zeros_like(din)
     s_in = torch.ones(max(sb // 4, 1), dtype=torch.float32, device="cuda") if sb else None
     s_out = torch.zeros_like(s_in) if sb else None
@@ -331,10 +363,12 @@ def time_half_hop(ctx, G, lqcd, torch, prec, recon, stream, reps=30):
     lqcd.lib().lqcd_reset_counters(ctx.handle)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    nvtx_push("half_hop")  # ncu --nvtx --nvtx-include half_hop/ captures these launches
     e0.record(stream)
     for _ in range(reps):
         lqcd.lqcd_dslash(ctx, G, fi, fo, lqcd.LQCD_EVEN, 0)
     e1.record(stream)
+    nvtx_pop()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / reps
     cnt = lqcd.lqcd_counters()
@@ -347,6 +381,7 @@ def time_half_hop(ctx, G, lqcd, torch, prec, recon, stream, reps=30):
 
 def run_e2e(ctx, lqcd, torch, U_h, b_h, prm, recon, args, stream):
     """Public-API step with host buffers: H2D of links and source, import, solve, D2H."""
+    import_recon = recon if prm.inner_prec == prm.outer_prec else 18
     U_pin = torch.from_numpy(U_h).pin_memory()
     b_pin = torch.from_numpy(b_h).pin_memory()
     x_pin = torch.empty_like(b_pin).pin_memory()
@@ -357,7 +392,7 @@ def run_e2e(ctx, lqcd, torch, U_h, b_h, prm, recon, args, stream):
     def step():
         U_dev.copy_(U_pin, non_blocking=True)
         b_dev.copy_(b_pin, non_blocking=True)
-        G = lqcd.lqcd_gauge_import(ctx, U_dev, L, recon=recon)
+        G = lqcd.lqcd_gauge_import(ctx, U_dev, L, recon=import_recon)
         lqcd.lqcd_cg_solve(ctx, G, lqcd.field(b_dev, lqcd.LQCD_LAYOUT_LEXI),
                            lqcd.field(x_dev, lqcd.LQCD_LAYOUT_LEXI), KAPPA, MU, prm)
         x_pin.copy_(x_dev, non_blocking=True)
@@ -560,7 +595,7 @@ def run_config(args):
         Gs, fbs, fxs, keep = [], [], [], []
         for k, Lk in enumerate(shapes):
             U = inputs.random_gauge(Lk, "near", seed=4000 + k, eps=0.3)
-            G = lqcd.lqcd_gauge_import(ctx, torch.from_numpy(U).cuda(), Lk, recon=12)
+            G = lqcd.lqcd_gauge_import(ctx, torch.from_numpy(U).cuda(), Lk, recon=18)
             bd, _ = lqcd.alloc_field(Lk, lqcd.LQCD_FULL, lqcd.LQCD_F64)
             xd, _ = lqcd.alloc_field(Lk, lqcd.LQCD_FULL, lqcd.LQCD_F64)
             fb = lqcd.field(bd, lqcd.LQCD_LAYOUT_EO)
@@ -611,6 +646,41 @@ def run_config(args):
                     {"workload": f"16^3x32, beta=5.6, kappa=0.16, 2 kappa mu=0.005, {args.sweeps} "
                                  "heatbath sweeps from cold, leapfrog tau=1 20 steps, "
                                  "F32-inner/DF64 CG to 1e-10 per force"})
+    elif c == "C":
+        # the paper's HMC setup C (Table "setup", Sec. 5.3): tlSym action, beta = 3.9,
+        # kappa = kappa_c = 0.160856, a mu = 0.1, 2MN with 10 steps on the fermion and
+        # on the gauge time scale, tau = 1, on 24^3 x 8; started from our own
+        # configuration (Wilson heatbath at beta = 6.0, whose plaquette is near the
+        # tlSym beta = 3.9 value) and thermalised with HMC before measuring
+        Lc = (24, 24, 24, 8)
+        beta, kappa, mu, c1 = 3.9, 0.160856, 0.1, lqcd.TLSYM_C1
+        G, thb, plaq0 = _heatbath_field(torch, lqcd, ctx, Lc, 6.0, min(args.sweeps, 100), 5105)
+        cg = lqcd.cg_params(tol=1e-10, outer_prec=lqcd.LQCD_DF64, inner_prec=lqcd.LQCD_F32,
+                            sloppy_recon=18, check_every=20)
+        trajs, therm = [], []
+        for t in range(args.therm + args.trajs):
+            st = lqcd.lqcd_hmc_trajectory(ctx, G, lqcd.hmc_params(
+                beta, kappa, mu, tau=1.0, nsteps=10, nf=1, seed=6106, traj=t, cg=cg,
+                integrator=lqcd.LQCD_2MN, c1=c1, nsteps_gauge=10))
+            (therm if t < args.therm else trajs).append(st)
+        secs = [s["seconds"] for s in trajs[1:]] or [trajs[0]["seconds"]]
+        F = torch.zeros((4, int(np.prod(Lc)), 8), dtype=torch.float64, device="cuda")
+        tgf, _ = _timed(torch, lambda: lqcd.lqcd_gauge_force(ctx, G, beta, F, want_action=False, c1=c1), 5)
+        tgw, _ = _timed(torch, lambda: lqcd.lqcd_gauge_force(ctx, G, beta, F, want_action=False), 5)
+        config_line("HMC setup C", None,
+                    {"s_per_trajectory": statistics.median(secs),
+                     "dH": [s["dH"] for s in trajs], "accepted": [s["accepted"] for s in trajs],
+                     "acceptance": sum(s["accepted"] for s in trajs) / len(trajs),
+                     "cg_iters_per_trajectory": [s["cg_iters"] for s in trajs],
+                     "exp_minus_dH_mean": float(np.mean([np.exp(-s["dH"]) for s in trajs])),
+                     "plaquette": [s["plaquette"] for s in trajs], "plaquette_after_heatbath": plaq0,
+                     "heatbath_s": thb, "thermalisation_trajectories": len(therm),
+                     "thermalisation_dH": [s["dH"] for s in therm],
+                     "thermalisation_plaquette": [s["plaquette"] for s in therm],
+                     "gauge_force_ms": {"tlsym": 1e3 * tgf, "wilson": 1e3 * tgw}},
+                    {"workload": "24^3x8, tlSym beta=3.9, kappa=0.160856, a mu=0.1, 2MN 10 fermion x 10 "
+                                 "gauge steps, tau=1, F32-inner/DF64 CG to 1e-10 per force; start: "
+                                 f"{min(args.sweeps, 100)} Wilson heatbath sweeps at beta=6.0 from cold"})
     elif c == "sweep":
         res = {}
         for ns in (16, 24, 32, 48):
@@ -682,7 +752,7 @@ def main():
                     help="ncu dram bytes per launch of the half hop, if captured")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--variants", action="store_true")
-    ap.add_argument("--config", default="2", choices=["1", "2", "3", "4a", "4b", "5", "sweep"],
+    ap.add_argument("--config", default="2", choices=["1", "2", "3", "4a", "4b", "5", "C", "sweep"],
                     help="2 (default): the 24^3x48 contract line; others print their own line")
     ap.add_argument("--sweeps", type=int, default=200, help="heatbath sweeps for configs 3, 4a, 5")
     ap.add_argument("--trajs", type=int, default=10, help="measured HMC trajectories for config 5")

@@ -280,11 +280,17 @@ int lqcd_fermion_force(lqcd_ctx *ctx, const lqcd_gauge *U, lqcd_field phi, doubl
                        lqcd_field *X_cache, const lqcd_geom *geom, double kappa, double mu,
                        const lqcd_cg_params *params, lqcd_cg_stats *stats, double *S_out);
 
-/* Wilson gauge action S_g = (beta/3) sum_{x, mu<nu} (3 - Re Tr U_munu) and
- * its derivative dS_g/domega = -(beta/3) Re Tr[i T^a U_mu(x) A_mu(x)]
- * (A = staple sum).  dSdw: device float64 [4][V][8]; *S_out host (may be
- * NULL, then the call is asynchronous). */
-int lqcd_gauge_force(lqcd_ctx *ctx, const lqcd_gauge *U, double beta, double *dSdw,
+/* Gauge action (Sec. 2.1, eq. "S_tlsym")
+ *   S_g = (beta/3) sum_x [ c0 sum_{mu<nu} (3 - Re Tr P_munu(x))
+ *                        + c1 sum_{mu != nu} (3 - Re Tr R_munu(x)) ],
+ * c0 = 1 - 8 c1, P the plaquette, R the 2x1 loop (two links along mu, one
+ * along nu); c1 = 0 is the Wilson action, c1 = -1/12 tree-level Symanzik.
+ * dSdw (device float64 [4][V][8]) receives the derivative
+ *   dS_g/domega^a = -(beta/3) Re Tr[i T^a U_mu(x) W_mu(x)],
+ * W = c0 (6 plaquette staples) + c1 (18 rectangle staples).  *S_out host (may
+ * be NULL, then the call is asynchronous).  Non-finite beta or c1:
+ * LQCD_ERR_NONFINITE. */
+int lqcd_gauge_force(lqcd_ctx *ctx, const lqcd_gauge *U, double beta, double c1, double *dSdw,
                      double *S_out);
 
 /* Plaquette (1/(6V)) sum_{x, mu<nu} (1/3) Re Tr U_munu(x) in FP64.  Synchronous. */
@@ -325,13 +331,18 @@ int lqcd_gauge_copy(lqcd_ctx *ctx, const lqcd_gauge *U_src, lqcd_gauge *U_dst);
 typedef struct {
   double beta, kappa, mu;
   double tau;          /* trajectory length */
-  int32_t nsteps;      /* leapfrog steps */
+  int32_t nsteps;      /* leapfrog steps, or 2MN steps of the outer (fermion) scale */
   int32_t nf;          /* 0: pure gauge, 1: one twisted-mass doublet (phi = Mhat^+ eta) */
   uint64_t seed;
   uint32_t traj;       /* trajectory number (Philox counter word) */
+  int32_t integrator;  /* LQCD_LEAPFROG or LQCD_2MN (two time scales) */
+  double c1;           /* rectangle coefficient of the gauge action (0: Wilson) */
+  int32_t nsteps_gauge;/* 2MN: inner gauge steps per outer position update (>= 1) */
   int32_t reserved;
+  double lambda;       /* 2MN parameter; 0 selects 0.1931833275037836 */
   lqcd_cg_params cg;   /* solver used for every force and action evaluation */
 } lqcd_hmc_params;
+enum { LQCD_LEAPFROG = 0, LQCD_2MN = 1 };
 
 typedef struct {
   double dH, H0, H1;
@@ -342,9 +353,18 @@ typedef struct {
 } lqcd_hmc_stats;
 
 /* One HMC trajectory (Sec. 2.2): momenta and eta drawn from Philox, phi =
- * Mhat^+ eta, leapfrog with F = -dS/domega, H in FP64 and the Metropolis test
- * exp(-dH) against a Philox uniform (counter (0, traj, 4<<8, 0)).  On
- * rejection U is restored.  Synchronous. */
+ * Mhat^+ eta, molecular dynamics with F = -dS/domega, H in FP64 and the
+ * Metropolis test exp(-dH) against a Philox uniform (counter (0, traj, 4<<8,
+ * 0)).  On rejection U is restored.
+ *   LQCD_LEAPFROG: nsteps steps of eps = tau/nsteps, gauge and fermion force
+ *     together:  P -= eps/2 dS; (U <- exp(i eps P) U; P -= eps dS) ...
+ *   LQCD_2MN (Sec. 2.2 "2MN", "multiple timescales"; Sec. 5.3): the
+ *     minimum-norm step  P -= l e dS; Q(e/2); P -= (1-2l) e dS; Q(e/2);
+ *     P -= l e dS  on two scales: the fermion force with nsteps steps of
+ *     e = tau/nsteps outside, and every position update Q(h) an inner 2MN
+ *     integration of the gauge force over h with nsteps_gauge steps.
+ * Momentum updates at the same links are merged, so each force is
+ * evaluated once per distinct field.  Synchronous. */
 int lqcd_hmc_trajectory(lqcd_ctx *ctx, lqcd_gauge *U, const lqcd_hmc_params *params,
                         lqcd_hmc_stats *stats);
 

@@ -206,7 +206,7 @@ template <int P>
 __global__ void __launch_bounds__(128) lincomb_kernel(VecArgs a, VecArgs ax, VecArgs ay, void *out,
                                                       float *os, const void *x, const float *xsc,
                                                       const void *y, const float *ysc, HostC ca_up,
-                                                      HostC ca_dn, HostC cb_up, HostC cb_dn,
+                                                      HostC ca_dn, HostC cb_up, HostC cb_dn, int unit,
                                                       double *partials) {
   using R = typename SpinorIO<P>::R;
   __shared__ double sh[8];
@@ -216,12 +216,20 @@ __global__ void __launch_bounds__(128) lincomb_kernel(VecArgs a, VecArgs ax, Vec
     Cx<R> X[12], Y[12];
     SpinorIO<P>::load(sv(ax, x, xsc, r), cb, X);
     if (y) SpinorIO<P>::load(sv(ay, y, ysc, r), cb, Y);
-    const Cx<R> au = cfrom<R>(ca_up), ad = cfrom<R>(ca_dn), bu = cfrom<R>(cb_up), bd = cfrom<R>(cb_dn);
+    if (unit) {
+      // ca = 1 and cb = +-1 (copies, residuals b - q): no multiplications
+      if (y) {
 #pragma unroll
-    for (int k = 0; k < 12; k++) {
-      Cx<R> o = (k < 6 ? au : ad) * X[k];
-      if (y) o = cmadd(k < 6 ? bu : bd, Y[k], o);
-      X[k] = o;
+        for (int k = 0; k < 12; k++) X[k] = unit > 0 ? X[k] + Y[k] : X[k] - Y[k];
+      }
+    } else {
+      const Cx<R> au = cfrom<R>(ca_up), ad = cfrom<R>(ca_dn), bu = cfrom<R>(cb_up), bd = cfrom<R>(cb_dn);
+#pragma unroll
+      for (int k = 0; k < 12; k++) {
+        Cx<R> o = (k < 6 ? au : ad) * X[k];
+        if (y) o = cmadd(k < 6 ? bu : bd, Y[k], o);
+        X[k] = o;
+      }
     }
     nrm = site_norm2<R, 12>(X);
     SpinorIO<P>::store(sv(a, out, os, r), cb, X);
@@ -366,10 +374,17 @@ lqcd_status lincomb(lqcd_ctx *ctx, int Vh, const HalfField &out, const HalfField
     return fail(ctx, LQCD_ERR_INVALID, "lincomb: operand precision or nrhs mismatch");
   VecArgs a = vargs(out, Vh), ax = vargs(x, Vh), ay = y ? vargs(*y, Vh) : a;
   count_launch(ctx, (double)Vh * out.nrhs * spinor_site_bytes(out.prec) * (y ? 3.0 : 2.0));
+  auto is = [](HostC c, double v) { return c.re == v && c.im == 0.0; };
+  int unit = 0;  // +1: x + y (or x alone), -1: x - y
+  if (is(ca_up, 1.0) && is(ca_dn, 1.0)) {
+    if (!y) unit = 1;
+    else if (is(cb_up, 1.0) && is(cb_dn, 1.0)) unit = 1;
+    else if (is(cb_up, -1.0) && is(cb_dn, -1.0)) unit = -1;
+  }
   return dispatch_prec(ctx, out.prec, [&](auto P) {
     lincomb_kernel<decltype(P)::value><<<grid, 128, 0, ctx->stream>>>(
         a, ax, ay, out.ptr, out.scale, x.ptr, x.scale, y ? y->ptr : nullptr, y ? y->scale : nullptr,
-        ca_up, ca_dn, cb_up, cb_dn, partials);
+        ca_up, ca_dn, cb_up, cb_dn, unit, partials);
   });
 }
 

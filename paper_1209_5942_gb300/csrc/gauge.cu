@@ -130,6 +130,60 @@ LQCD_DEV M3 staple(const double2 *U, const Geom &g, const int c[4], int mu) {
   return A;
 }
 
+// ---------------------------------------------------------------------------
+// Rectangles of the tree-level Symanzik action (Sec. 2.1, eq. "S_tlsym").
+// A step of a path from site c in direction sgn*dir uses U_dir(c) forwards
+// or U_dir(c - dir)^+ backwards.
+// ---------------------------------------------------------------------------
+LQCD_DEV M3 step_link(const double2 *U, const Geom &g, int c[4], int dir, int sgn) {
+  if (sgn > 0) {
+    M3 u = load_link(U, g, at(g, c), dir);
+    coords_shift(g, c, dir, +1);
+    return u;
+  }
+  coords_shift(g, c, dir, -1);
+  M3 u = load_link(U, g, at(g, c), dir), d;
+#pragma unroll
+  for (int i = 0; i < 3; i++)
+#pragma unroll
+    for (int j = 0; j < 3; j++) d.m[3 * i + j] = conj(u.m[3 * j + i]);
+  return d;
+}
+
+// product of the 5 steps (dirs[k], sgns[k]) of a path starting at c
+LQCD_DEV M3 path5(const double2 *U, const Geom &g, const int c0[4], const int dirs[5], const int sgns[5]) {
+  int c[4] = {c0[0], c0[1], c0[2], c0[3]};
+  M3 r = step_link(U, g, c, dirs[0], sgns[0]);
+  for (int k = 1; k < 5; k++) r = mmul(r, step_link(U, g, c, dirs[k], sgns[k]));
+  return r;
+}
+
+// Sum of the 18 rectangle staples of U_mu(x): with W it, Re Tr(U_mu(x) W) is
+// the sum of Re Tr over the 2x1 loops through U_mu(x).  Each path starts at
+// x + mu and returns to x; for every nu != mu and sign s of the nu steps:
+//   two links along mu, link first:  +mu, s nu, -mu, -mu, -s nu
+//   two links along mu, link second: s nu, -mu, -mu, -s nu, +mu
+//   two links along nu:              s nu, s nu, -mu, -s nu, -s nu
+LQCD_DEV M3 rect_staple(const double2 *U, const Geom &g, const int c[4], int mu) {
+  M3 A;
+#pragma unroll
+  for (int k = 0; k < 9; k++) A.m[k] = czero<double>();
+  int cpm[4] = {c[0], c[1], c[2], c[3]};
+  coords_shift(g, cpm, mu, +1);
+  for (int nu = 0; nu < 4; nu++) {
+    if (nu == mu) continue;
+    for (int s = -1; s <= 1; s += 2) {
+      const int d1[5] = {mu, nu, mu, mu, nu}, s1[5] = {+1, s, -1, -1, -s};
+      const int d2[5] = {nu, mu, mu, nu, mu}, s2[5] = {s, -1, -1, -s, +1};
+      const int d3[5] = {nu, nu, mu, nu, nu}, s3[5] = {s, s, -1, -s, -s};
+      const M3 a = path5(U, g, cpm, d1, s1), b = path5(U, g, cpm, d2, s2), e = path5(U, g, cpm, d3, s3);
+#pragma unroll
+      for (int k = 0; k < 9; k++) A.m[k] = A.m[k] + a.m[k] + b.m[k] + e.m[k];
+    }
+  }
+  return A;
+}
+
 // thread -> (parity, cb) over all 2*Vh sites; coordinates
 LQCD_DEV bool thread_site(const Geom &g, long tid, int *p, int *cb, int c[4]) {
   if (tid >= 2L * g.Vh) return false;
@@ -177,9 +231,34 @@ __global__ void __launch_bounds__(128) plaquette_kernel(const double2 *U, Geom g
   if (threadIdx.x == 0) partials[blockIdx.x] = t;
 }
 
+// sum over sites of sum_{mu != nu} Re Tr R_munu(x) (R: two links along mu,
+// one along nu): per-block partials
+__global__ void __launch_bounds__(128) rectangle_kernel(const double2 *U, Geom g, double *partials) {
+  __shared__ double sh[8];
+  long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  int p, cb, c[4];
+  double acc = 0.0;
+  if (thread_site(g, tid, &p, &cb, c)) {
+    for (int mu = 0; mu < 4; mu++)
+      for (int nu = 0; nu < 4; nu++) {
+        if (nu == mu) continue;
+        // U_mu(x) times the path +mu, +nu, -mu, -mu, -nu from x + mu
+        const int d[5] = {mu, nu, mu, mu, nu}, sg[5] = {+1, +1, -1, -1, -1};
+        int cpm[4] = {c[0], c[1], c[2], c[3]};
+        coords_shift(g, cpm, mu, +1);
+        M3 w = mmul(load_link(U, g, Pos{p, cb, 0}, mu), path5(U, g, cpm, d, sg));
+        acc += re_trace(w);
+      }
+  }
+  double t = block_sum(acc, sh);
+  if (threadIdx.x == 0) partials[blockIdx.x] = t;
+}
+
 // dS_g/domega^a for every link; out [mu][V][8] with lexicographic site index.
 // Re Tr(i T^a W) = -Im Tr(lambda^a W) / 2 with the Gell-Mann traces written out.
-__global__ void __launch_bounds__(128) gauge_force_kernel(const double2 *U, Geom g, double beta,
+// With c1 != 0 the staple is c0 (plaquette staples) + c1 (rectangle staples),
+// c0 = 1 - 8 c1 (tree-level Symanzik action).
+__global__ void __launch_bounds__(128) gauge_force_kernel(const double2 *U, Geom g, double beta, double c1,
                                                           double *out) {
   long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
   int p, cb, c[4];
@@ -188,6 +267,12 @@ __global__ void __launch_bounds__(128) gauge_force_kernel(const double2 *U, Geom
   Pos s = at(g, c);
   for (int mu = 0; mu < 4; mu++) {
     M3 A = staple(U, g, c, mu);
+    if (c1 != 0.0) {
+      const M3 R = rect_staple(U, g, c, mu);
+      const double c0 = 1.0 - 8.0 * c1;
+#pragma unroll
+      for (int k = 0; k < 9; k++) A.m[k] = {c0 * A.m[k].re + c1 * R.m[k].re, c0 * A.m[k].im + c1 * R.m[k].im};
+    }
     M3 W = mmul(load_link(U, g, s, mu), A);
     const C *w = W.m;
     double tr[8];
@@ -533,9 +618,18 @@ lqcd_status plaquette_sum(lqcd_ctx *ctx, const lqcd_gauge *U, double *sum_retr) 
   return sum_partials(ctx, nb, sum_retr);
 }
 
-lqcd_status gauge_force_raw(lqcd_ctx *ctx, const lqcd_gauge *U, double beta, double *dSdw) {
+lqcd_status rectangle_sum(lqcd_ctx *ctx, const lqcd_gauge *U, double *sum_retr) {
   long V = 2L * U->g.Vh;
-  gauge_force_kernel<<<nblk(V), 128, 0, ctx->stream>>>((const double2 *)U->master, U->g, beta, dSdw);
+  int nb = (int)nblk(V);
+  LQCD_TRY(ensure_partials(ctx, nb));
+  rectangle_kernel<<<nb, 128, 0, ctx->stream>>>((const double2 *)U->master, U->g, ctx->partials);
+  LQCD_CUDA(ctx, cudaGetLastError());
+  return sum_partials(ctx, nb, sum_retr);
+}
+
+lqcd_status gauge_force_raw(lqcd_ctx *ctx, const lqcd_gauge *U, double beta, double c1, double *dSdw) {
+  long V = 2L * U->g.Vh;
+  gauge_force_kernel<<<nblk(V), 128, 0, ctx->stream>>>((const double2 *)U->master, U->g, beta, c1, dSdw);
   LQCD_CUDA(ctx, cudaGetLastError());
   return LQCD_OK;
 }

@@ -19,7 +19,8 @@ namespace lqcd {
 lqcd_status check_geom(lqcd_ctx *ctx, const lqcd_geom *g);
 lqcd_status check_field(lqcd_ctx *ctx, const lqcd_field &f, const char *name, bool allow_lexi);
 lqcd_status plaquette_sum(lqcd_ctx *ctx, const lqcd_gauge *U, double *sum_retr);
-lqcd_status gauge_force_raw(lqcd_ctx *ctx, const lqcd_gauge *U, double beta, double *dSdw);
+lqcd_status gauge_force_raw(lqcd_ctx *ctx, const lqcd_gauge *U, double beta, double c1, double *dSdw);
+lqcd_status rectangle_sum(lqcd_ctx *ctx, const lqcd_gauge *U, double *sum_retr);
 lqcd_status heatbath_raw(lqcd_ctx *ctx, lqcd_gauge *U, double beta, uint64_t seed, uint64_t sweep, int n_or,
                          unsigned int *fail_dev);
 lqcd_status momenta_raw(lqcd_ctx *ctx, long V, double *P, uint64_t seed, uint32_t traj);
@@ -191,17 +192,24 @@ extern "C" int lqcd_plaquette(lqcd_ctx *ctx, const lqcd_gauge *U, double *plaq_o
   return LQCD_OK;
 }
 
-extern "C" int lqcd_gauge_force(lqcd_ctx *ctx, const lqcd_gauge *U, double beta, double *dSdw, double *S_out) {
+// S_g = (beta/3) [c0 (18 V - sum Re Tr P) + c1 (36 V - sum Re Tr R)]
+static lqcd_status gauge_action_sym(lqcd_ctx *ctx, const lqcd_gauge *U, double beta, double c1, double *S) {
+  const double V = 2.0 * U->g.Vh;
+  double sp, sr = 36.0 * V;
+  LQCD_TRY(plaquette_sum(ctx, U, &sp));
+  if (c1 != 0.0) LQCD_TRY(rectangle_sum(ctx, U, &sr));
+  *S = beta / 3.0 * ((1.0 - 8.0 * c1) * (18.0 * V - sp) + c1 * (36.0 * V - sr));
+  return LQCD_OK;
+}
+
+extern "C" int lqcd_gauge_force(lqcd_ctx *ctx, const lqcd_gauge *U, double beta, double c1, double *dSdw,
+                                double *S_out) {
   if (!ctx) return LQCD_ERR_INVALID;
   LQCD_TRY(check_u(ctx, U));
   if (!dSdw || !aligned16(dSdw)) return fail(ctx, LQCD_ERR_INVALID, "dSdw: NULL or misaligned");
-  if (!std::isfinite(beta)) return fail(ctx, LQCD_ERR_NONFINITE, "beta not finite");
-  LQCD_TRY(gauge_force_raw(ctx, U, beta, dSdw));
-  if (S_out) {
-    double s;
-    LQCD_TRY(plaquette_sum(ctx, U, &s));
-    *S_out = beta / 3.0 * (3.0 * 6.0 * 2.0 * U->g.Vh - s);
-  }
+  if (!std::isfinite(beta) || !std::isfinite(c1)) return fail(ctx, LQCD_ERR_NONFINITE, "beta or c1 not finite");
+  LQCD_TRY(gauge_force_raw(ctx, U, beta, c1, dSdw));
+  if (S_out) LQCD_TRY(gauge_action_sym(ctx, U, beta, c1, S_out));
   return LQCD_OK;
 }
 
@@ -326,21 +334,27 @@ extern "C" int lqcd_hmc_trajectory(lqcd_ctx *ctx, lqcd_gauge *U, const lqcd_hmc_
   LQCD_TRY(check_u(ctx, U));
   if (!prm || !stats) return fail(ctx, LQCD_ERR_INVALID, "NULL params or stats");
   if (prm->nsteps < 1 || !(prm->tau > 0.0)) return fail(ctx, LQCD_ERR_INVALID, "nsteps >= 1 and tau > 0 required");
+  if (prm->integrator != LQCD_LEAPFROG && prm->integrator != LQCD_2MN)
+    return fail(ctx, LQCD_ERR_INVALID, "integrator must be LQCD_LEAPFROG or LQCD_2MN");
+  if (prm->integrator == LQCD_2MN && prm->nsteps_gauge < 1)
+    return fail(ctx, LQCD_ERR_INVALID, "2MN needs nsteps_gauge >= 1");
+  if (!std::isfinite(prm->c1) || !std::isfinite(prm->lambda) || prm->lambda < 0.0 || prm->lambda >= 0.5)
+    return fail(ctx, LQCD_ERR_INVALID, "c1 must be finite and lambda in [0, 0.5)");
   auto t0 = std::chrono::steady_clock::now();
   std::memset(stats, 0, sizeof(*stats));
   const Geom &g = U->g;
   const int Vh = g.Vh;
   const long V = 2L * Vh;
   const size_t nP = (size_t)32 * V;
-  const double eps = prm->tau / prm->nsteps;
   const bool fermions = prm->nf != 0;
+  const bool two_mn = prm->integrator == LQCD_2MN;
+  const double lam = prm->lambda != 0.0 ? prm->lambda : 0.1931833275037836;
   size_t hb = spinor_half_bytes(LQCD_F64, Vh);
-  DBuf P(ctx), F(ctx), Ff(ctx), eta(ctx), phi(ctx), X(ctx), tmp(ctx), save(ctx);
+  DBuf P(ctx), F(ctx), eta(ctx), phi(ctx), X(ctx), tmp(ctx), save(ctx);
   LQCD_TRY(P.alloc(nP * sizeof(double)));
   LQCD_TRY(F.alloc(nP * sizeof(double)));
   LQCD_TRY(save.alloc((size_t)2 * 4 * 9 * Vh * 16));
   if (fermions) {
-    LQCD_TRY(Ff.alloc(nP * sizeof(double)));
     LQCD_TRY(eta.alloc(2 * hb));
     LQCD_TRY(phi.alloc(hb));
     LQCD_TRY(X.alloc(hb));
@@ -354,25 +368,56 @@ extern "C" int lqcd_hmc_trajectory(lqcd_ctx *ctx, lqcd_gauge *U, const lqcd_hmc_
   HalfField Phi = f64_half(phi.p, Vh), Xh = f64_half(X.p, Vh);
   Op op{ctx, g, {}, LQCD_F64, U->recon, prm->kappa, prm->mu};
   int cg_iters = 0;
-  auto action_and_force = [&](double *S_f) -> lqcd_status {
-    // F = dS_g/dw (+ dS_f/dw); S_f = phi^+ X at the current links
-    LQCD_TRY(gauge_force_raw(ctx, U, prm->beta, (double *)F.p));
-    if (fermions) {
-      lqcd_cg_stats st;
-      std::memset(&st, 0, sizeof(st));
-      LQCD_TRY(solve_normal(ctx, U, Phi, Xh, prm->kappa, prm->mu, prm->cg, &st));
-      cg_iters += st.iters;
-      if (S_f) LQCD_TRY(half_redot(ctx, Vh, Phi, Xh, S_f));
-      LQCD_TRY(fermion_force_from_X(ctx, U, Xh, prm->kappa, prm->mu, (double *)Ff.p));
-      LQCD_TRY(momenta_update_raw(ctx, V, (double *)F.p, (const double *)Ff.p, -1.0));  // F += Ff
+  // X = (Mhat^+ Mhat)^-1 phi at the current links, solved once per field
+  uint64_t x_version = 0;
+  auto solve_x = [&]() -> lqcd_status {
+    if (x_version == U->version) return LQCD_OK;
+    lqcd_cg_stats st;
+    std::memset(&st, 0, sizeof(st));
+    LQCD_TRY(solve_normal(ctx, U, Phi, Xh, prm->kappa, prm->mu, prm->cg, &st));
+    cg_iters += st.iters;
+    x_version = U->version;
+    return LQCD_OK;
+  };
+  // Momentum kicks are collected and applied when the links are about to
+  // change (or at the end): P -= wg dS_g/dw + wf dS_f/dw, one force
+  // evaluation per field and kind.
+  double wg = 0.0, wf = 0.0;
+  auto flush = [&]() -> lqcd_status {
+    if (wg != 0.0) {
+      LQCD_TRY(gauge_force_raw(ctx, U, prm->beta, prm->c1, (double *)F.p));
+      LQCD_TRY(momenta_update_raw(ctx, V, (double *)P.p, (const double *)F.p, wg));
+      wg = 0.0;
+    }
+    if (wf != 0.0 && fermions) {
+      LQCD_TRY(solve_x());
+      LQCD_TRY(fermion_force_from_X(ctx, U, Xh, prm->kappa, prm->mu, (double *)F.p));
+      LQCD_TRY(momenta_update_raw(ctx, V, (double *)P.p, (const double *)F.p, wf));
+    }
+    wf = 0.0;
+    return LQCD_OK;
+  };
+  auto drift = [&](double h) -> lqcd_status {
+    LQCD_TRY(flush());
+    return gauge_update_raw(ctx, U, (const double *)P.p, h);
+  };
+  // inner 2MN integration of the gauge force over time h
+  auto inner = [&](double h) -> lqcd_status {
+    const double d = h / prm->nsteps_gauge;
+    for (int j = 0; j < prm->nsteps_gauge; j++) {
+      wg += lam * d;
+      LQCD_TRY(drift(0.5 * d));
+      wg += (1.0 - 2.0 * lam) * d;
+      LQCD_TRY(drift(0.5 * d));
+      wg += lam * d;
     }
     return LQCD_OK;
   };
-  auto gauge_action = [&](double *S) -> lqcd_status {
-    double s;
-    LQCD_TRY(plaquette_sum(ctx, U, &s));
-    *S = prm->beta / 3.0 * (3.0 * 6.0 * V - s);
-    return LQCD_OK;
+  auto fermion_action = [&](double *S) -> lqcd_status {
+    *S = 0.0;
+    if (!fermions) return LQCD_OK;
+    LQCD_TRY(solve_x());
+    return half_redot(ctx, Vh, Phi, Xh, S);
   };
   double Sf0 = 0.0, Sf1 = 0.0, Sg0, Sg1, K0, K1;
   if (fermions) {
@@ -383,19 +428,32 @@ extern "C" int lqcd_hmc_trajectory(lqcd_ctx *ctx, lqcd_gauge *U, const lqcd_hmc_
   }
   LQCD_TRY(sumsq_raw(ctx, (const double *)P.p, nP, &K0));
   K0 *= 0.5;
-  LQCD_TRY(gauge_action(&Sg0));
-  LQCD_TRY(action_and_force(&Sf0));
+  LQCD_TRY(gauge_action_sym(ctx, U, prm->beta, prm->c1, &Sg0));
+  LQCD_TRY(fermion_action(&Sf0));
   const double H0 = K0 + Sg0 + Sf0;
-  LQCD_TRY(momenta_update_raw(ctx, V, (double *)P.p, (const double *)F.p, 0.5 * eps));
-  for (int step = 0; step < prm->nsteps; step++) {
-    LQCD_TRY(gauge_update_raw(ctx, U, (const double *)P.p, eps));
-    const bool last = step == prm->nsteps - 1;
-    LQCD_TRY(action_and_force(last ? &Sf1 : nullptr));
-    LQCD_TRY(momenta_update_raw(ctx, V, (double *)P.p, (const double *)F.p, last ? 0.5 * eps : eps));
+  const double e = prm->tau / prm->nsteps;
+  if (two_mn) {
+    for (int step = 0; step < prm->nsteps; step++) {
+      wf += lam * e;
+      LQCD_TRY(inner(0.5 * e));
+      wf += (1.0 - 2.0 * lam) * e;
+      LQCD_TRY(inner(0.5 * e));
+      wf += lam * e;
+    }
+  } else {
+    for (int step = 0; step < prm->nsteps; step++) {
+      wg += 0.5 * e;
+      wf += 0.5 * e;
+      LQCD_TRY(drift(e));
+      wg += 0.5 * e;
+      wf += 0.5 * e;
+    }
   }
+  LQCD_TRY(flush());
   LQCD_TRY(sumsq_raw(ctx, (const double *)P.p, nP, &K1));
   K1 *= 0.5;
-  LQCD_TRY(gauge_action(&Sg1));
+  LQCD_TRY(gauge_action_sym(ctx, U, prm->beta, prm->c1, &Sg1));
+  LQCD_TRY(fermion_action(&Sf1));
   const double H1 = K1 + Sg1 + Sf1;
   const double dH = H1 - H0;
   if (!std::isfinite(dH)) return fail(ctx, LQCD_ERR_NONFINITE, "dH is not finite");

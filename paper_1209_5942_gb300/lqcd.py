@@ -76,8 +76,9 @@ class lqcd_counters(ctypes.Structure):
 class lqcd_hmc_params(ctypes.Structure):
     _fields_ = [("beta", ctypes.c_double), ("kappa", ctypes.c_double), ("mu", ctypes.c_double),
                 ("tau", ctypes.c_double), ("nsteps", ctypes.c_int32), ("nf", ctypes.c_int32),
-                ("seed", ctypes.c_uint64), ("traj", ctypes.c_uint32), ("reserved", ctypes.c_int32),
-                ("cg", lqcd_cg_params)]
+                ("seed", ctypes.c_uint64), ("traj", ctypes.c_uint32), ("integrator", ctypes.c_int32),
+                ("c1", ctypes.c_double), ("nsteps_gauge", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("lam", ctypes.c_double), ("cg", lqcd_cg_params)]
 
 
 class lqcd_hmc_stats(ctypes.Structure):
@@ -126,7 +127,7 @@ SIGNATURES = [
     ("lqcd_fermion_force", _i, [_vp, _vp, lqcd_field, _vp, ctypes.POINTER(lqcd_field),
                                 ctypes.POINTER(lqcd_geom), _d, _d, ctypes.POINTER(lqcd_cg_params),
                                 ctypes.POINTER(lqcd_cg_stats), ctypes.POINTER(_d)]),
-    ("lqcd_gauge_force", _i, [_vp, _vp, _d, _vp, ctypes.POINTER(_d)]),
+    ("lqcd_gauge_force", _i, [_vp, _vp, _d, _d, _vp, ctypes.POINTER(_d)]),
     ("lqcd_plaquette", _i, [_vp, _vp, ctypes.POINTER(_d)]),
     ("lqcd_heatbath_sweep", _i, [_vp, _vp, _d, ctypes.c_uint64, ctypes.c_uint64, _i]),
     ("lqcd_momenta_gaussian", _i, [_vp, ctypes.POINTER(lqcd_geom), _vp, ctypes.c_uint64,
@@ -403,9 +404,9 @@ def lqcd_fermion_force(ctx: Context, U: Gauge, phi: lqcd_field, dSdw: torch.Tens
     return S.value, st.as_dict()
 
 
-def lqcd_gauge_force(ctx: Context, U: Gauge, beta, dSdw: torch.Tensor, want_action=True):
+def lqcd_gauge_force(ctx: Context, U: Gauge, beta, dSdw: torch.Tensor, want_action=True, c1=0.0):
     S = _d(0.0)
-    ctx.check(lib().lqcd_gauge_force(ctx.handle, U.handle, beta, _vp(dSdw.data_ptr()),
+    ctx.check(lib().lqcd_gauge_force(ctx.handle, U.handle, beta, c1, _vp(dSdw.data_ptr()),
                                      ctypes.byref(S) if want_action else None))
     return S.value if want_action else None
 
@@ -455,10 +456,16 @@ def lqcd_gauge_copy(ctx: Context, src: Gauge, dst: Gauge):
     ctx.check(lib().lqcd_gauge_copy(ctx.handle, src.handle, dst.handle))
 
 
-def hmc_params(beta, kappa, mu, tau=1.0, nsteps=20, nf=1, seed=1, traj=0, cg=None):
+LQCD_LEAPFROG, LQCD_2MN = 0, 1
+TLSYM_C1 = -1.0 / 12.0
+
+
+def hmc_params(beta, kappa, mu, tau=1.0, nsteps=20, nf=1, seed=1, traj=0, cg=None,
+               integrator=LQCD_LEAPFROG, c1=0.0, nsteps_gauge=1, lam=0.0):
     p = lqcd_hmc_params()
     p.beta, p.kappa, p.mu, p.tau = beta, kappa, mu, tau
     p.nsteps, p.nf, p.seed, p.traj = nsteps, nf, seed, traj
+    p.integrator, p.c1, p.nsteps_gauge, p.lam = integrator, c1, nsteps_gauge, lam
     p.cg = cg if cg is not None else cg_params(tol=1e-10, outer_prec=LQCD_DF64,
                                                inner_prec=LQCD_F32)
     return p

@@ -243,3 +243,62 @@ def test_pure_gauge_hmc_matches_oracle_and_scales(ctx, oracle):
                                     nsteps=20, tau=1.0)
     assert abs(dHs[20] - dH_ref) < 1e-8 * max(1.0, abs(dH_ref))
     assert 3.0 < dHs[20] / dHs[40] < 5.3
+
+
+@pytest.mark.parametrize("L", [(4, 4, 4, 4), (2, 4, 6, 8)])
+def test_tlsym_gauge_force_and_action(ctx, oracle, L):
+    """Tree-level Symanzik action (c1 = -1/12, Sec. 2.1 eq. S_tlsym): the GPU
+    rectangle staples against the oracle's loop-by-loop derivative, and the
+    action against the oracle's plaquette + rectangle sums."""
+    beta, c1 = 3.9, lqcd.TLSYM_C1
+    U = inputs.random_gauge(L, "near", seed=43, eps=0.5)
+    G = lqcd.lqcd_gauge_import(ctx, dev(U), L)
+    F = torch.zeros((4, inputs.volume(L), 8), dtype=torch.float64, device="cuda")
+    S = lqcd.lqcd_gauge_force(ctx, G, beta, F, c1=c1)
+    assert relerr(host(F), oracle.gauge_dSdw_sym(U, L, beta, c1)) < 1e-13
+    Sref = oracle.gauge_action_sym(U, L, beta, c1)
+    assert abs(S - Sref) < 1e-11 * abs(Sref)
+
+
+def test_hmc_2mn_tlsym_trajectory_matches_oracle(ctx, oracle):
+    """One trajectory of the paper's HMC setup kind (Sec. 5.3): tlSym gauge
+    action, 2MN on separate fermion and gauge time scales, from the same links
+    and Philox streams as the oracle; dH and the final links agree."""
+    L = (4, 4, 2, 4)
+    beta, kappa, mu, c1 = 3.9, 0.14, 0.1 / 0.28, lqcd.TLSYM_C1
+    U = inputs.random_gauge(L, "near", seed=44, eps=0.3)
+    G = lqcd.lqcd_gauge_import(ctx, dev(U), L)
+    seed, traj = 77, 5
+    prm = lqcd.hmc_params(beta, kappa, mu, tau=0.5, nsteps=3, nf=1, seed=seed, traj=traj,
+                          cg=lqcd.cg_params(tol=1e-13, max_iter=50000), integrator=lqcd.LQCD_2MN,
+                          c1=c1, nsteps_gauge=2)
+    st = lqcd.lqcd_hmc_trajectory(ctx, G, prm)
+    P0 = oracle.momenta(L, seed, traj)
+    eta = oracle.gaussian_spinor(L, seed, traj) * (~oracle.parity_mask(L))[:, None, None]
+    phi = oracle.apply_Mhat(U, eta, L, kappa, mu, dagger=True)
+    U1, P1, dH, (H0, H1, Sf0) = oracle.hmc_md_2mn(U, P0, phi, L, beta, kappa, mu, c1=c1, nf=1,
+                                                  nsteps_f=3, nsteps_g=2, tau=0.5, tol=1e-13)
+    assert abs(st["H0"] - H0) < 1e-9 * abs(H0)
+    assert abs(st["dH"] - dH) < 1e-7 * max(1.0, abs(dH))
+    if st["accepted"]:
+        assert relerr(_export(ctx, G, L), U1) < 1e-10
+    else:
+        assert np.array_equal(_export(ctx, G, L), U)
+
+
+def test_hmc_2mn_pure_gauge_scaling(ctx, oracle):
+    """Pure-gauge 2MN (tlSym): dH equals the oracle's and is second order."""
+    L = (4, 4, 4, 4)
+    U = inputs.random_gauge(L, "near", seed=45, eps=0.3)
+    c1 = lqcd.TLSYM_C1
+    dHs = {}
+    for ng in (2, 4):
+        G = lqcd.lqcd_gauge_import(ctx, dev(U), L)
+        prm = lqcd.hmc_params(3.9, 0.0, 0.0, tau=1.0, nsteps=2, nf=0, seed=10, traj=0,
+                              integrator=lqcd.LQCD_2MN, c1=c1, nsteps_gauge=ng)
+        dHs[ng] = lqcd.lqcd_hmc_trajectory(ctx, G, prm)["dH"]
+        G.free()
+    _, _, dH_ref, _ = oracle.hmc_md_2mn(U, oracle.momenta(L, 10, 0), None, L, 3.9, 0.0, 0.0, c1=c1, nf=0,
+                                        nsteps_f=2, nsteps_g=2, tau=1.0)
+    assert abs(dHs[2] - dH_ref) < 1e-8 * max(1.0, abs(dH_ref))
+    assert 3.0 < dHs[2] / dHs[4] < 5.3, dHs
