@@ -66,6 +66,19 @@ def dist_env():
             int(os.environ.get("WORLD_SIZE", "1")))
 
 
+def reduce_over_ranks(dist, t_local, bytes_local, device):
+    """Whole-job figures of N independent replicas: the slowest rank's time
+    (max) and the bytes of all ranks (sum).  dist = None for one process."""
+    if dist is None:
+        return t_local, bytes_local
+    import torch
+    tt = torch.tensor([t_local], device=device, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    bb = torch.tensor([bytes_local], device=device, dtype=torch.float64)
+    dist.all_reduce(bb, op=dist.ReduceOp.SUM)
+    return float(tt.item()), float(bb.item())
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
 
@@ -253,18 +266,7 @@ def run_gpu(args):
     ms = e0.elapsed_time(e1)
     cnt = lqcd.lqcd_counters()
     lqcd.lib().lqcd_get_counters(ctx.handle, ctypes_byref(cnt))
-    t_local = ms / 1e3
-    t = t_local
-    bytes_local = cnt.bytes
-    if dist:
-        tt = torch.tensor([t_local], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt.item())
-        bb = torch.tensor([bytes_local], device="cuda", dtype=torch.float64)
-        dist.all_reduce(bb, op=dist.ReduceOp.SUM)
-        bytes_total = float(bb.item())
-    else:
-        bytes_total = bytes_local
+    t, bytes_total = reduce_over_ranks(dist, ms / 1e3, cnt.bytes, "cuda")
     value = bytes_total / t / 1e9
 
     # dominant kernel: the half hop of the solve, timed alone on the library stream
@@ -438,21 +440,26 @@ def run_variants(ctx, G, fb, fx, lqcd, torch, stream):
     solve and one timed solve each)."""
     out = {}
     combos = [("f64", "f64"), ("df64", "df64"), ("df64", "f32"), ("df64", "bf16s"),
-              ("df64", "f16s")]
-    for outer, inner in combos:
+              ("df64", "f16s"), ("f64", "f64", "bicgstab"), ("df64", "df64", "bicgstab"),
+              ("df64", "f32", "bicgstab")]
+    for combo in combos:
+        outer, inner = combo[:2]
+        bicg = len(combo) > 2
         prm = lqcd.cg_params(tol=TOL, outer_prec=PREC_NAMES[outer], inner_prec=PREC_NAMES[inner],
-                             max_iter=50000)
+                             max_iter=50000, max_restarts=10,
+                             solver=lqcd.LQCD_SOLVER_BICGSTAB if bicg else lqcd.LQCD_SOLVER_CG)
+        key = f"{outer}/{inner}" + ("/bicgstab" if bicg else "")
         try:
             lqcd.lqcd_cg_solve(ctx, G, fb, fx, KAPPA, MU, prm)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             st = lqcd.lqcd_cg_solve(ctx, G, fb, fx, KAPPA, MU, prm)[0]
             dt = time.perf_counter() - t0
-            out[f"{outer}/{inner}"] = {"time_to_solution_s": dt, "iters": st["iters"],
-                                       "reliable_updates": st["reliable_updates"],
-                                       "true_resid": st["true_resid"]}
+            out[key] = {"time_to_solution_s": dt, "iters": st["iters"],
+                        "reliable_updates": st["reliable_updates"], "restarts": st["restarts"],
+                        "true_resid": st["true_resid"]}
         except Exception as e:  # report, do not hide
-            out[f"{outer}/{inner}"] = {"error": str(e)}
+            out[key] = {"error": str(e)}
     return out
 
 
@@ -498,10 +505,13 @@ def _solve_variants(torch, lqcd, ctx, G, L, b_h, kappa, mu, combos, nrhs=1, reps
     fx = lqcd.field(xd, lqcd.LQCD_LAYOUT_EO, nrhs=nrhs)
     lqcd.lqcd_spinor_pack(ctx, L, torch.from_numpy(b_h).cuda(), fb)
     out = {}
-    for outer, inner, recon in combos:
+    for combo in combos:
+        outer, inner, recon = combo[:3]
+        solver = combo[3] if len(combo) > 3 else "cg"
         prm = lqcd.cg_params(tol=TOL, outer_prec=PREC_NAMES[outer], inner_prec=PREC_NAMES[inner],
-                             max_iter=100000, sloppy_recon=recon, check_every=20)
-        name = f"{outer}/{inner}/rec{recon}"
+                             max_iter=100000, sloppy_recon=recon, check_every=20, max_restarts=10,
+                             solver=lqcd.LQCD_SOLVER_BICGSTAB if solver == "bicgstab" else lqcd.LQCD_SOLVER_CG)
+        name = f"{outer}/{inner}/rec{recon}" + ("/bicgstab" if solver == "bicgstab" else "")
         try:
             # warm-up (autotuning, graph); non-convergence is reported, not hidden
             lqcd.lqcd_cg_solve(ctx, G, fb, fx, kappa, mu, prm, allow_noconv=True)
@@ -558,7 +568,9 @@ def run_config(args):
         b = inputs.gaussian_spinor(Lc, 3004)
         sol = _solve_variants(torch, lqcd, ctx, G, Lc, b, kappa, mu,
                               [("f64", "f64", 18), ("df64", "df64", 18), ("df64", "f32", 12),
-                               ("df64", "bf16s", 12), ("df64", "f16s", 12)])
+                               ("df64", "bf16s", 12), ("df64", "f16s", 12),
+                               ("f64", "f64", 18, "bicgstab"), ("df64", "df64", 18, "bicgstab"),
+                               ("df64", "f32", 12, "bicgstab"), ("df64", "f16s", 12, "bicgstab")])
         ok = [v for v in sol.values() if v.get("converged")]
         best = min(v["time_to_solution_s"] for v in ok) if ok else None
         config_line("32^3x64 mixed precision", sol["df64/f32/rec12"].get("solve_GBs"),
@@ -681,6 +693,28 @@ def run_config(args):
                     {"workload": "24^3x8, tlSym beta=3.9, kappa=0.160856, a mu=0.1, 2MN 10 fermion x 10 "
                                  "gauge steps, tau=1, F32-inner/DF64 CG to 1e-10 per force; start: "
                                  f"{min(args.sweeps, 100)} Wilson heatbath sweeps at beta=6.0 from cold"})
+    elif c == "hb":
+        # heatbath and overrelaxation throughput (Sec. 5.1) in FP64, counted with the
+        # paper's per-link flop figures (Table "rw_flops": 3912 heatbath, 3846 overrelax)
+        res = {}
+        for Lc in ((16, 16, 16, 16), (24, 24, 24, 24), (32, 32, 32, 32), (32, 32, 32, 64)):
+            V = int(np.prod(Lc))
+            G = lqcd.lqcd_gauge_import(ctx, torch.from_numpy(inputs.random_gauge(Lc, "cold")).cuda(), Lc,
+                                       recon=18)
+            for s_ in range(5):
+                lqcd.lqcd_heatbath_sweep(ctx, G, 5.7, 9, s_)
+            th, _ = _timed(torch, lambda: lqcd.lqcd_heatbath_sweep(ctx, G, 5.7, 9, 100), 5)
+            tho, _ = _timed(torch, lambda: lqcd.lqcd_heatbath_sweep(ctx, G, 5.7, 9, 101, n_or=4), 5)
+            tor = (tho - th) / 4
+            res["x".join(map(str, Lc))] = {
+                "heatbath_ms": 1e3 * th, "overrelax_ms": 1e3 * tor,
+                "heatbath_GFLOPs": 4 * V * 3912 / th / 1e9, "overrelax_GFLOPs": 4 * V * 3846 / tor / 1e9,
+                "heatbath_GBs_paper_count": 4 * V * 2880 / th / 1e9,
+                "plaquette": lqcd.lqcd_plaquette(ctx, G)}
+            G.free()
+        config_line("heatbath", None, {"hb": res},
+                    {"workload": "Cabibbo-Marinari heatbath and overrelaxation sweeps, FP64, beta=5.7, "
+                                 "GFLOP/s with the paper's 3912 / 3846 flop per link"})
     elif c == "sweep":
         res = {}
         for ns in (16, 24, 32, 48):
@@ -752,7 +786,7 @@ def main():
                     help="ncu dram bytes per launch of the half hop, if captured")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--variants", action="store_true")
-    ap.add_argument("--config", default="2", choices=["1", "2", "3", "4a", "4b", "5", "C", "sweep"],
+    ap.add_argument("--config", default="2", choices=["1", "2", "3", "4a", "4b", "5", "C", "hb", "sweep"],
                     help="2 (default): the 24^3x48 contract line; others print their own line")
     ap.add_argument("--sweeps", type=int, default=200, help="heatbath sweeps for configs 3, 4a, 5")
     ap.add_argument("--trajs", type=int, default=10, help="measured HMC trajectories for config 5")

@@ -234,7 +234,12 @@ typedef struct {
   int32_t check_every;    /* host polls convergence every this many iterations */
   int32_t use_graph;      /* 1: capture check_every iterations in a CUDA graph */
   int32_t sloppy_recon;   /* 18 or 12: link format of the inner operator */
+  int32_t solver;         /* LQCD_SOLVER_CG (default) or LQCD_SOLVER_BICGSTAB */
+  double inner_tol;       /* BiCGStab with inner_prec != outer_prec: relative
+                             residual each refinement cycle reaches in the inner
+                             format (0 selects 1e-5) */
 } lqcd_cg_params;
+enum { LQCD_SOLVER_CG = 0, LQCD_SOLVER_BICGSTAB = 1 };
 
 typedef struct {
   int32_t iters;            /* inner iterations (each: 2 Mhat + 2 Mhat^+ ... = 4 half hops x2) */
@@ -246,7 +251,11 @@ typedef struct {
 } lqcd_cg_stats;
 
 /* Solves M x = b (FULL fields, LEXI or EO, LQCD_F64) through CG on
- * Mhat^+ Mhat on the even sites (CGLS form) with source preparation
+ * Mhat^+ Mhat on the even sites (CGLS form), or with params->solver =
+ * LQCD_SOLVER_BICGSTAB through BiCGStab on Mhat itself (Sec. 2.1 names CG and
+ * BiCGStab; nrhs = 1 only, else LQCD_ERR_UNSUPPORTED; a mixed-precision
+ * BiCGStab runs in inner_prec to inner_tol per cycle and the FP64 true
+ * residual drives outer refinement), with source preparation
  *   bhat_e = b_e + kappa H_eo A_o^-1 b_o
  * and reconstruction x_o = A_o^-1 (b_o + kappa H_oe x_e).  nrhs > 1 solves
  * the right-hand sides together (one multi-RHS operator per iteration,

@@ -211,6 +211,7 @@ extern "C" int lqcd_destroy(lqcd_ctx *ctx) {
   if (ctx->partials) cudaFree(ctx->partials);
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
   if (ctx->solver_state) cudaFree(ctx->solver_state);
+  if (ctx->staples) cudaFree(ctx->staples);
   delete ctx;
   return LQCD_OK;
 }
@@ -459,6 +460,10 @@ static lqcd_status check_cg_params(lqcd_ctx *ctx, const lqcd_cg_params *p) {
   if (p->sloppy_recon != 18 && p->sloppy_recon != 12 && p->sloppy_recon != 0)
     return fail(ctx, LQCD_ERR_INVALID, "sloppy_recon must be 18 or 12");
   if (p->max_restarts < 0) return fail(ctx, LQCD_ERR_INVALID, "max_restarts must be >= 0");
+  if (p->solver != LQCD_SOLVER_CG && p->solver != LQCD_SOLVER_BICGSTAB)
+    return fail(ctx, LQCD_ERR_INVALID, "solver must be LQCD_SOLVER_CG or LQCD_SOLVER_BICGSTAB");
+  if (!std::isfinite(p->inner_tol) || p->inner_tol < 0.0 || p->inner_tol >= 1.0)
+    return fail(ctx, LQCD_ERR_INVALID, "inner_tol must be in [0, 1)");
   return LQCD_OK;
 }
 
@@ -473,6 +478,8 @@ extern "C" int lqcd_cg_solve(lqcd_ctx *ctx, const lqcd_gauge *U, lqcd_field b, l
   if (!stats) return fail(ctx, LQCD_ERR_INVALID, "stats is NULL");
   if (b.prec != LQCD_F64 || x.prec != LQCD_F64) return fail(ctx, LQCD_ERR_INVALID, "b and x must be LQCD_F64");
   if (b.layout != x.layout || b.nrhs != x.nrhs) return fail(ctx, LQCD_ERR_INVALID, "b/x layout or nrhs differ");
+  if (params->solver == LQCD_SOLVER_BICGSTAB && b.nrhs != 1)
+    return fail(ctx, LQCD_ERR_UNSUPPORTED, "BiCGStab solves one right-hand side at a time");
   if (!std::isfinite(kappa) || !std::isfinite(mu)) return fail(ctx, LQCD_ERR_NONFINITE, "kappa/mu not finite");
   Geom g = make_geom(*geom);
   size_t bytes = 2 * spinor_half_bytes(LQCD_F64, g.Vh) * b.nrhs;

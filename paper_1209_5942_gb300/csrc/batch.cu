@@ -741,6 +741,7 @@ extern "C" int lqcd_cg_solve_batch(lqcd_ctx *ctx, int n, const lqcd_gauge *const
   if (!U || !b || !x || !kappa || !mu || !params || !stats) return fail(ctx, LQCD_ERR_INVALID, "NULL array");
   const lqcd_cg_params &p = *params;
   if (!(p.tol > 0.0) || p.max_iter < 1 || p.max_restarts < 0) return fail(ctx, LQCD_ERR_INVALID, "bad params");
+  if (p.solver != LQCD_SOLVER_CG) return fail(ctx, LQCD_ERR_UNSUPPORTED, "the batched solver is CG only");
   if (p.outer_prec != LQCD_F64 && p.outer_prec != LQCD_DF64) return fail(ctx, LQCD_ERR_INVALID, "bad outer_prec");
   if (p.inner_prec < LQCD_F64 || p.inner_prec > LQCD_F16S) return fail(ctx, LQCD_ERR_INVALID, "bad inner_prec");
   if (p.inner_prec == LQCD_F64 && p.outer_prec != LQCD_F64) return fail(ctx, LQCD_ERR_INVALID, "inner F64 needs outer F64");

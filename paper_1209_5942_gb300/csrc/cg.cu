@@ -27,6 +27,7 @@
 // FP64 partial sums per block finished by one block in a fixed order, so the
 // iteration count is reproducible run to run.
 #include <chrono>
+#include <complex>
 #include <cmath>
 #include <cstring>
 #include <utility>
@@ -770,6 +771,176 @@ lqcd_status cgls_even(lqcd_ctx *ctx, lqcd_gauge *U, const Geom &g, double kappa,
   return result;
 }
 
+// ---------------------------------------------------------------------------
+// BiCGStab on Mhat x = bhat (Sec. 2.1 names CG and BiCGStab as the common
+// solvers; van der Vorst 1992), one right-hand side, in precision P of the
+// vectors r, r0, p, v, s, t, x:
+//   r = bhat - Mhat x;  r0 = r;  rho = alpha = omega = 1;  v = p = 0
+//   repeat:  rho' = (r0, r);  beta = (rho'/rho)(alpha/omega)
+//            p = r + beta (p - omega v);  v = Mhat p;  alpha = rho' / (r0, v)
+//            s = r - alpha v;  t = Mhat s;  omega = (t, s) / (t, t)
+//            x += alpha p + omega s;  r = s - omega t
+// until |r| <= tol |b|.  The scalars are complex; the dot products are FP64
+// partial sums per block, finished on the host (three reads per iteration).
+// ---------------------------------------------------------------------------
+
+// per block: Re, Im of sum conj(x) y and sum |y|^2  -> partials[3 * block + k]
+template <int P>
+__global__ void __launch_bounds__(128) cdot_kernel(int Vh, const void *x, const float *xs, const void *y,
+                                                   const float *ys, double *partials) {
+  using R = typename SpinorIO<P>::R;
+  __shared__ double sh[3][8];
+  const int cb = blockIdx.x * blockDim.x + threadIdx.x;
+  double re = 0.0, im = 0.0, yy = 0.0;
+  if (cb < Vh) {
+    Cx<R> X[12], Y[12];
+    SpinorIO<P>::load(SpinorView{(void *)x, (float *)xs, Vh}, cb, X);
+    SpinorIO<P>::load(SpinorView{(void *)y, (float *)ys, Vh}, cb, Y);
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+      const double xr = to_double(X[k].re), xi = to_double(X[k].im);
+      const double yr = to_double(Y[k].re), yi = to_double(Y[k].im);
+      re = __fma_rn(xr, yr, __fma_rn(xi, yi, re));
+      im = __fma_rn(xr, yi, __fma_rn(-xi, yr, im));
+      yy = __fma_rn(yr, yr, __fma_rn(yi, yi, yy));
+    }
+  }
+  const double a = warp_block_sum(re, sh[0]);
+  const double b = warp_block_sum(im, sh[1]);
+  const double c = warp_block_sum(yy, sh[2]);
+  if (threadIdx.x == 0) {
+    partials[3 * blockIdx.x] = a;
+    partials[3 * blockIdx.x + 1] = b;
+    partials[3 * blockIdx.x + 2] = c;
+  }
+}
+
+// (x, y) and |y|^2 on the host (synchronous)
+static lqcd_status cdot(lqcd_ctx *ctx, int Vh, const HalfField &x, const HalfField &y, std::complex<double> *xy,
+                        double *yy) {
+  const int nb = (Vh + 127) / 128;
+  LQCD_TRY(ensure_partials(ctx, (size_t)3 * nb));
+  count_launch(ctx, (double)Vh * 2.0 * spinor_site_bytes(x.prec));
+  LQCD_TRY(dispatch_prec(ctx, x.prec, [&](auto P) {
+    cdot_kernel<decltype(P)::value><<<nb, 128, 0, ctx->stream>>>(Vh, x.ptr, x.scale, y.ptr, y.scale,
+                                                                 ctx->partials);
+  }));
+  LQCD_CUDA(ctx, cudaGetLastError());
+  LQCD_TRY(ensure_pinned(ctx, (size_t)3 * nb));
+  LQCD_CUDA(ctx, cudaMemcpyAsync(ctx->pinned, ctx->partials, sizeof(double) * 3 * nb, cudaMemcpyDeviceToHost,
+                                 ctx->stream));
+  LQCD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  double a = 0.0, b = 0.0, c = 0.0;
+  for (int k = 0; k < nb; k++) {
+    a += ctx->pinned[3 * k];
+    b += ctx->pinned[3 * k + 1];
+    c += ctx->pinned[3 * k + 2];
+  }
+  if (xy) *xy = {a, b};
+  if (yy) *yy = c;
+  return LQCD_OK;
+}
+
+static HostC hc(std::complex<double> z) { return HostC{z.real(), z.imag()}; }
+
+// Solves Mhat xo = bhat (outer-format fields, one RHS) with BiCGStab in the
+// inner format to the relative residual tol_rel * |b| / |bhat| of the
+// current cycle; xo receives the solution.  st->iters counts iterations.
+lqcd_status bicgstab_even(lqcd_ctx *ctx, lqcd_gauge *U, const Geom &g, double kappa, double mu,
+                          const lqcd_cg_params &prm, const HalfField &bhat, const HalfField &xo, double b2,
+                          lqcd_cg_stats *st, int *iters_used) {
+  const int Vh = g.Vh;
+  const int outer = prm.outer_prec, P = prm.inner_prec;
+  const bool mixed = P != outer;
+  Op Oi{ctx, g, {}, P, U->recon, kappa, mu};
+  if (mixed) Oi.recon = (P == LQCD_BF16S || P == LQCD_F16S) ? 12 : (prm.sloppy_recon ? prm.sloppy_recon : 18);
+  LQCD_TRY(gauge_view(ctx, U, P, Oi.recon, &Oi.U));
+  Vec r, r0, p, v, sv_, t, tmp, xs;
+  for (Vec *w : {&r, &r0, &p, &v, &sv_, &t, &tmp}) LQCD_TRY(w->alloc(ctx, P, Vh, 1));
+  HalfField X = xo;
+  if (mixed) {
+    LQCD_TRY(xs.alloc(ctx, P, Vh, 1));
+    X = xs.f;
+  }
+  const HostC one{1, 0}, zero{0, 0};
+  // x = 0, r = bhat
+  if (mixed) LQCD_TRY(spinor_convert_raw(ctx, Vh, 1, bhat.ptr, bhat.scale, outer, r.f.ptr, r.f.scale, P));
+  else LQCD_TRY(lincomb(ctx, Vh, r.f, bhat, nullptr, one, one, zero, zero, nullptr, nullptr));
+  LQCD_TRY(lincomb(ctx, Vh, r0.f, r.f, nullptr, one, one, zero, zero, nullptr, nullptr));
+  std::complex<double> rho(1.0, 0.0), alpha(1.0, 0.0), omega(1.0, 0.0), rho_new, rv, ts;
+  double rr = 0.0, tt = 0.0;
+  LQCD_TRY(cdot(ctx, Vh, r0.f, r.f, &rho_new, &rr));
+  // stop on |r|^2 <= (tol/2)^2 |b|^2 (|b| of the full system, as the CG does);
+  // a mixed solve stops earlier, once |r| <= inner_tol times this cycle's |bhat|
+  const double rr0 = rr;
+  double stop2 = 0.25 * prm.tol * prm.tol * b2;
+  if (mixed) {
+    const double itol = prm.inner_tol > 0.0 ? prm.inner_tol : 1e-5;
+    stop2 = std::fmax(stop2, itol * itol * rr);
+  }
+  int it = 0;
+  lqcd_status result = LQCD_OK;
+  while (rr > stop2) {
+    if (it >= prm.max_iter) {
+      result = LQCD_ERR_NOCONV;
+      break;
+    }
+    if (it == 0) {
+      LQCD_TRY(lincomb(ctx, Vh, p.f, r.f, nullptr, one, one, zero, zero, nullptr, nullptr));
+    } else {
+      const std::complex<double> beta = (rho_new / rho) * (alpha / omega);
+      // p = r + beta p - beta omega v
+      LQCD_TRY(lincomb(ctx, Vh, tmp.f, p.f, &v.f, hc(beta), hc(beta), hc(-beta * omega), hc(-beta * omega),
+                       nullptr, nullptr));
+      LQCD_TRY(lincomb(ctx, Vh, p.f, r.f, &tmp.f, one, one, one, one, nullptr, nullptr));
+    }
+    rho = rho_new;
+    LQCD_TRY(apply_schur(Oi, p.f, v.f, tmp.f, 0, false, nullptr, nullptr, nullptr));
+    LQCD_TRY(cdot(ctx, Vh, r0.f, v.f, &rv, nullptr));
+    if (std::abs(rv) == 0.0 || !std::isfinite(std::abs(rv))) break;  // breakdown: refinement restarts
+    alpha = rho / rv;
+    // s = r - alpha v
+    LQCD_TRY(lincomb(ctx, Vh, sv_.f, r.f, &v.f, one, one, hc(-alpha), hc(-alpha), nullptr, nullptr));
+    LQCD_TRY(apply_schur(Oi, sv_.f, t.f, tmp.f, 0, false, nullptr, nullptr, nullptr));
+    std::complex<double> st_;
+    LQCD_TRY(cdot(ctx, Vh, sv_.f, t.f, &st_, &tt));  // (s, t) and |t|^2
+    ts = std::conj(st_);
+    omega = tt > 0.0 ? ts / tt : std::complex<double>(0.0, 0.0);
+    // x += alpha p + omega s
+    LQCD_TRY(lincomb(ctx, Vh, X, X, &p.f, one, one, hc(alpha), hc(alpha), nullptr, nullptr));
+    LQCD_TRY(lincomb(ctx, Vh, X, X, &sv_.f, one, one, hc(omega), hc(omega), nullptr, nullptr));
+    // r = s - omega t
+    LQCD_TRY(lincomb(ctx, Vh, r.f, sv_.f, &t.f, one, one, hc(-omega), hc(-omega), nullptr, nullptr));
+    LQCD_TRY(cdot(ctx, Vh, r0.f, r.f, &rho_new, &rr));
+    ++it;
+    if (!std::isfinite(rr)) {
+      result = fail(ctx, LQCD_ERR_NONFINITE, "BiCGStab: non-finite residual after %d iterations", it);
+      break;
+    }
+    // BiCGStab needs a spectrum of Mhat that does not surround the origin (it
+    // does for near-free fields beyond kappa_c = 1/8): stop once the residual
+    // has grown a millionfold and report non-convergence
+    if (rr > 1e12 * rr0) {
+      result = LQCD_ERR_NOCONV;
+      break;
+    }
+    if (std::abs(omega) == 0.0 || std::abs(rho_new) == 0.0) break;  // breakdown: refinement restarts
+  }
+  if (mixed) {
+    dim3 g2((Vh + 127) / 128, 1);
+    LQCD_TRY(dispatch_prec(ctx, outer, [&](auto PO) {
+      dispatch_prec(ctx, P, [&](auto PI) {
+        accum_convert_kernel<decltype(PO)::value, decltype(PI)::value><<<g2, 128, 0, ctx->stream>>>(
+            Vh, xo.rhs_stride, X.rhs_stride, X.scale_rhs_stride, xo.ptr, X.ptr, X.scale);
+      });
+    }));
+    LQCD_CUDA(ctx, cudaGetLastError());
+  }
+  st->iters += it;
+  if (iters_used) *iters_used = it;
+  return result;
+}
+
 // Full solve on EO full fields (outer F64 user fields b, x).
 lqcd_status cg_solve_eo(lqcd_ctx *ctx, lqcd_gauge *U, const HalfField &b_full, const HalfField &x_full,
                         double kappa, double mu, const lqcd_cg_params &prm, lqcd_cg_stats *st) {
@@ -844,7 +1015,9 @@ lqcd_status cg_solve_eo(lqcd_ctx *ctx, lqcd_gauge *U, const HalfField &b_full, c
     }
     LQCD_CUDA(ctx, cudaMemsetAsync(xo_outer.f.ptr, 0, xo_outer.f.rhs_stride * nrhs, ctx->stream));
     int used = 0;
-    lqcd_status s = cgls_even(ctx, U, g, kappa, mu, prm, bh, xo_outer.f, b2, st, nrhs, &used, false);
+    lqcd_status s = prm.solver == LQCD_SOLVER_BICGSTAB
+                        ? bicgstab_even(ctx, U, g, kappa, mu, prm, bh, xo_outer.f, b2[0], st, &used)
+                        : cgls_even(ctx, U, g, kappa, mu, prm, bh, xo_outer.f, b2, st, nrhs, &used, false);
     if (s != LQCD_OK && s != LQCD_ERR_NOCONV) return s;
     // corr_e = x_e (F64); corr_o = A_o^-1 (rhs_o + kappa H_oe corr_e)
     if (outer != LQCD_F64)
@@ -892,7 +1065,7 @@ lqcd_status cg_solve_eo(lqcd_ctx *ctx, lqcd_gauge *U, const HalfField &b_full, c
       if (!std::isfinite(tr)) return fail(ctx, LQCD_ERR_NONFINITE, "true residual is not finite");
     }
     if (all) break;
-    if (cycle >= prm.max_restarts || total_iters >= prm.max_iter) {
+    if (cycle >= prm.max_restarts || total_iters >= prm.max_iter || (s == LQCD_ERR_NOCONV && worst > 1.0)) {
       result = LQCD_ERR_NOCONV;
       break;
     }
@@ -911,7 +1084,8 @@ lqcd_status cg_solve_eo(lqcd_ctx *ctx, lqcd_gauge *U, const HalfField &b_full, c
   double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   for (int r = 0; r < nrhs; r++) st[r].seconds = secs;
   if (result == LQCD_ERR_NOCONV)
-    fail(ctx, LQCD_ERR_NOCONV, "CG stopped with true residual %.3e > tol %.3e", worst, prm.tol);
+    fail(ctx, LQCD_ERR_NOCONV, "%s stopped with true residual %.3e > tol %.3e",
+         prm.solver == LQCD_SOLVER_BICGSTAB ? "BiCGStab" : "CG", worst, prm.tol);
   return result;
 }
 

@@ -158,32 +158,6 @@ LQCD_DEV M3 path5(const double2 *U, const Geom &g, const int c0[4], const int di
   return r;
 }
 
-// Sum of the 18 rectangle staples of U_mu(x): with W it, Re Tr(U_mu(x) W) is
-// the sum of Re Tr over the 2x1 loops through U_mu(x).  Each path starts at
-// x + mu and returns to x; for every nu != mu and sign s of the nu steps:
-//   two links along mu, link first:  +mu, s nu, -mu, -mu, -s nu
-//   two links along mu, link second: s nu, -mu, -mu, -s nu, +mu
-//   two links along nu:              s nu, s nu, -mu, -s nu, -s nu
-LQCD_DEV M3 rect_staple(const double2 *U, const Geom &g, const int c[4], int mu) {
-  M3 A;
-#pragma unroll
-  for (int k = 0; k < 9; k++) A.m[k] = czero<double>();
-  int cpm[4] = {c[0], c[1], c[2], c[3]};
-  coords_shift(g, cpm, mu, +1);
-  for (int nu = 0; nu < 4; nu++) {
-    if (nu == mu) continue;
-    for (int s = -1; s <= 1; s += 2) {
-      const int d1[5] = {mu, nu, mu, mu, nu}, s1[5] = {+1, s, -1, -1, -s};
-      const int d2[5] = {nu, mu, mu, nu, mu}, s2[5] = {s, -1, -1, -s, +1};
-      const int d3[5] = {nu, nu, mu, nu, nu}, s3[5] = {s, s, -1, -s, -s};
-      const M3 a = path5(U, g, cpm, d1, s1), b = path5(U, g, cpm, d2, s2), e = path5(U, g, cpm, d3, s3);
-#pragma unroll
-      for (int k = 0; k < 9; k++) A.m[k] = A.m[k] + a.m[k] + b.m[k] + e.m[k];
-    }
-  }
-  return A;
-}
-
 // thread -> (parity, cb) over all 2*Vh sites; coordinates
 LQCD_DEV bool thread_site(const Geom &g, long tid, int *p, int *cb, int c[4]) {
   if (tid >= 2L * g.Vh) return false;
@@ -231,6 +205,118 @@ __global__ void __launch_bounds__(128) plaquette_kernel(const double2 *U, Geom g
   if (threadIdx.x == 0) partials[blockIdx.x] = t;
 }
 
+// ---------------------------------------------------------------------------
+// Rectangle staples from plaquette staples.  With the plaquette staple
+//   S(y; mu, nu, s) = U_{s nu}(y + mu) U_mu(y + s nu)^+ U_{s nu}(y)^+
+// (s = +-1, U_{-nu}(y) = U_nu(y - nu)^+) and unitary links, the three
+// rectangle staples of U_mu(x) in the (mu, s nu) half plane are
+//   link first along mu:  U_mu(x + mu) S(x + mu) S(x)
+//   link second along mu: S(x) S(x - mu) U_mu(x - mu)
+//   long side along nu:   U_{s nu}(x + mu) S(x + s nu) U_{s nu}(x)^+
+// (the inner U_{s nu} U_{s nu}^+ pairs cancel), two products each instead of
+// four.  A first kernel stores the 6 plaquette staples of every link.
+// ---------------------------------------------------------------------------
+// staple field layout: [mu][k = 2 * (nu index) + (s < 0)][entry 9][V] complex,
+// nu index = nu - (nu > mu), lexicographic V
+LQCD_DEV size_t stap_index(long V, int mu, int k, int e, long lexi) {
+  return (((size_t)mu * 6 + k) * 9 + e) * (size_t)V + lexi;
+}
+LQCD_DEV M3 load_stap(const double2 *S, long V, int mu, int k, long lexi) {
+  M3 r;
+#pragma unroll
+  for (int e = 0; e < 9; e++) {
+    double2 w = S[stap_index(V, mu, k, e, lexi)];
+    r.m[e] = {w.x, w.y};
+  }
+  return r;
+}
+LQCD_DEV int stap_k(int mu, int nu, int s) { return 2 * (nu - (nu > mu ? 1 : 0)) + (s < 0 ? 1 : 0); }
+
+// U_{s nu}(y) as a matrix
+LQCD_DEV M3 signed_link(const double2 *U, const Geom &g, const int c[4], int nu, int s) {
+  int d[4] = {c[0], c[1], c[2], c[3]};
+  return step_link(U, g, d, nu, s);
+}
+
+__global__ void __launch_bounds__(128) staple6_kernel(const double2 *U, Geom g, double2 *S) {
+  long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  int p, cb, c[4];
+  if (!thread_site(g, tid, &p, &cb, c)) return;
+  const long V = 2L * g.Vh;
+  const long lexi = at(g, c).lexi;
+  for (int mu = 0; mu < 4; mu++) {
+    int cpm[4] = {c[0], c[1], c[2], c[3]};
+    coords_shift(g, cpm, mu, +1);
+    for (int nu = 0; nu < 4; nu++) {
+      if (nu == mu) continue;
+      for (int s = -1; s <= 1; s += 2) {
+        int cps[4] = {c[0], c[1], c[2], c[3]};
+        coords_shift(g, cps, nu, s);
+        // U_{s nu}(x + mu) U_mu(x + s nu)^+ U_{s nu}(x)^+
+        M3 t = mmul_nd(signed_link(U, g, cpm, nu, s), load_link(U, g, at(g, cps), mu));
+        t = mmul_nd(t, signed_link(U, g, c, nu, s));
+        const int k = stap_k(mu, nu, s);
+#pragma unroll
+        for (int e = 0; e < 9; e++) S[stap_index(V, mu, k, e, lexi)] = make_double2(t.m[e].re, t.m[e].im);
+      }
+    }
+  }
+}
+
+LQCD_DEV void add_scaled(M3 &A, double c, const M3 &t) {
+#pragma unroll
+  for (int e = 0; e < 9; e++) A.m[e] = {fma(c, t.m[e].re, A.m[e].re), fma(c, t.m[e].im, A.m[e].im)};
+}
+
+// dS/domega of the tlSym action from the stored plaquette staples: one
+// accumulator A = c0 sum S + c1 sum (rectangle staples), the (nu, s) loop
+// kept rolled so only a few 3x3 matrices are live at a time.
+__global__ void __launch_bounds__(128) gauge_force_sym_kernel(const double2 *U, const double2 *S, Geom g,
+                                                              double beta, double c1, double *out) {
+  long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  int p, cb, c[4];
+  if (!thread_site(g, tid, &p, &cb, c)) return;
+  const long V = 2L * g.Vh;
+  const Pos s0 = at(g, c);
+  const double c0 = 1.0 - 8.0 * c1;
+#pragma unroll 1
+  for (int mu = 0; mu < 4; mu++) {
+    int cpm[4] = {c[0], c[1], c[2], c[3]}, cmm[4] = {c[0], c[1], c[2], c[3]};
+    coords_shift(g, cpm, mu, +1);
+    coords_shift(g, cmm, mu, -1);
+    const Pos spm = at(g, cpm), smm = at(g, cmm);
+    M3 A;
+#pragma unroll
+    for (int e = 0; e < 9; e++) A.m[e] = czero<double>();
+#pragma unroll 1
+    for (int k = 0; k < 6; k++) {
+      const int nu = (k >> 1) + ((k >> 1) >= mu ? 1 : 0), s = (k & 1) ? -1 : 1;
+      const M3 Sx = load_stap(S, V, mu, k, s0.lexi);
+      add_scaled(A, c0, Sx);
+      add_scaled(A, c1, mmul(mmul(load_link(U, g, spm, mu), load_stap(S, V, mu, k, spm.lexi)), Sx));
+      add_scaled(A, c1, mmul(mmul(Sx, load_stap(S, V, mu, k, smm.lexi)), load_link(U, g, smm, mu)));
+      int cps[4] = {c[0], c[1], c[2], c[3]};
+      coords_shift(g, cps, nu, s);
+      add_scaled(A, c1, mmul_nd(mmul(signed_link(U, g, cpm, nu, s), load_stap(S, V, mu, k, at(g, cps).lexi)),
+                                signed_link(U, g, c, nu, s)));
+    }
+    const M3 W = mmul(load_link(U, g, s0, mu), A);
+    const C *w = W.m;
+    double tr[8];
+    tr[0] = (w[3] + w[1]).im;
+    tr[1] = (times_i(w[1] - w[3])).im;
+    tr[2] = (w[0] - w[4]).im;
+    tr[3] = (w[6] + w[2]).im;
+    tr[4] = (times_i(w[2] - w[6])).im;
+    tr[5] = (w[7] + w[5]).im;
+    tr[6] = (times_i(w[5] - w[7])).im;
+    tr[7] = (w[0] + w[4] - w[8] - w[8]).im * 0.57735026918962576451;
+    double *o = out + ((size_t)mu * V + s0.lexi) * 8;
+#pragma unroll
+    for (int a = 0; a < 8; a++) o[a] = (beta / 3.0) * 0.5 * tr[a];
+  }
+}
+
 // sum over sites of sum_{mu != nu} Re Tr R_munu(x) (R: two links along mu,
 // one along nu): per-block partials
 __global__ void __launch_bounds__(128) rectangle_kernel(const double2 *U, Geom g, double *partials) {
@@ -256,10 +342,8 @@ __global__ void __launch_bounds__(128) rectangle_kernel(const double2 *U, Geom g
 
 // dS_g/domega^a for every link; out [mu][V][8] with lexicographic site index.
 // Re Tr(i T^a W) = -Im Tr(lambda^a W) / 2 with the Gell-Mann traces written out.
-// With c1 != 0 the staple is c0 (plaquette staples) + c1 (rectangle staples),
-// c0 = 1 - 8 c1 (tree-level Symanzik action).
-__global__ void __launch_bounds__(128) gauge_force_kernel(const double2 *U, Geom g, double beta, double c1,
-                                                          double *out) {
+// Wilson action (c1 = 0); the tlSym force is gauge_force_sym_kernel.
+__global__ void __launch_bounds__(128) gauge_force_kernel(const double2 *U, Geom g, double beta, double *out) {
   long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
   int p, cb, c[4];
   if (!thread_site(g, tid, &p, &cb, c)) return;
@@ -267,12 +351,6 @@ __global__ void __launch_bounds__(128) gauge_force_kernel(const double2 *U, Geom
   Pos s = at(g, c);
   for (int mu = 0; mu < 4; mu++) {
     M3 A = staple(U, g, c, mu);
-    if (c1 != 0.0) {
-      const M3 R = rect_staple(U, g, c, mu);
-      const double c0 = 1.0 - 8.0 * c1;
-#pragma unroll
-      for (int k = 0; k < 9; k++) A.m[k] = {c0 * A.m[k].re + c1 * R.m[k].re, c0 * A.m[k].im + c1 * R.m[k].im};
-    }
     M3 W = mmul(load_link(U, g, s, mu), A);
     const C *w = W.m;
     double tr[8];
@@ -629,7 +707,25 @@ lqcd_status rectangle_sum(lqcd_ctx *ctx, const lqcd_gauge *U, double *sum_retr) 
 
 lqcd_status gauge_force_raw(lqcd_ctx *ctx, const lqcd_gauge *U, double beta, double c1, double *dSdw) {
   long V = 2L * U->g.Vh;
-  gauge_force_kernel<<<nblk(V), 128, 0, ctx->stream>>>((const double2 *)U->master, U->g, beta, c1, dSdw);
+  if (c1 != 0.0) {
+    // plaquette staples of every link (6 x 144 B per link), then the force
+    const size_t need = (size_t)4 * 6 * 9 * V * sizeof(double2);
+    if (ctx->staple_cap < need) {
+      if (ctx->staples) cudaFreeAsync(ctx->staples, ctx->stream);
+      ctx->staples = nullptr;
+      ctx->staple_cap = 0;
+      LQCD_CUDA(ctx, cudaMallocAsync(&ctx->staples, need, ctx->stream));
+      ctx->staple_cap = need;
+    }
+    staple6_kernel<<<nblk(V), 128, 0, ctx->stream>>>((const double2 *)U->master, U->g,
+                                                     (double2 *)ctx->staples);
+    gauge_force_sym_kernel<<<nblk(V), 128, 0, ctx->stream>>>((const double2 *)U->master,
+                                                             (const double2 *)ctx->staples, U->g, beta, c1,
+                                                             dSdw);
+    LQCD_CUDA(ctx, cudaGetLastError());
+    return LQCD_OK;
+  }
+  gauge_force_kernel<<<nblk(V), 128, 0, ctx->stream>>>((const double2 *)U->master, U->g, beta, dSdw);
   LQCD_CUDA(ctx, cudaGetLastError());
   return LQCD_OK;
 }

@@ -28,6 +28,9 @@ struct lqcd_ctx {
   // algorithmic work counters (lqcd_get_counters)
   lqcd_counters cnt{};
   // launch-shape autotuner (tune.cu)
+  // plaquette-staple workspace of the tlSym gauge force (gauge.cu)
+  void *staples = nullptr;
+  size_t staple_cap = 0;
   int autotune = 1;
   int forced_choice = -1;  // lqcd_set_launch_choice: >= 0 overrides the tuner
   std::string tune_path;

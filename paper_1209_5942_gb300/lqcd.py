@@ -28,6 +28,7 @@ LQCD_ERR_UNSUPPORTED = -7
 LQCD_FULL, LQCD_EVEN, LQCD_ODD = 0, 1, 2
 LQCD_F64, LQCD_DF64, LQCD_F32, LQCD_BF16S, LQCD_F16S = 0, 1, 2, 3, 4
 LQCD_LAYOUT_LEXI, LQCD_LAYOUT_EO = 0, 1
+LQCD_SOLVER_CG, LQCD_SOLVER_BICGSTAB = 0, 1
 
 _STATUS_NAMES = {0: "LQCD_OK", -1: "LQCD_ERR_INVALID", -2: "LQCD_ERR_CUDA", -3: "LQCD_ERR_NOCONV",
                  -4: "LQCD_ERR_NONFINITE", -5: "LQCD_ERR_TIMEOUT", -6: "LQCD_ERR_OOM",
@@ -55,7 +56,8 @@ class lqcd_cg_params(ctypes.Structure):
                 ("outer_prec", ctypes.c_int32), ("inner_prec", ctypes.c_int32),
                 ("delta", ctypes.c_double), ("max_restarts", ctypes.c_int32),
                 ("check_every", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("sloppy_recon", ctypes.c_int32)]
+                ("sloppy_recon", ctypes.c_int32), ("solver", ctypes.c_int32),
+                ("inner_tol", ctypes.c_double)]
 
 
 class lqcd_cg_stats(ctypes.Structure):
@@ -351,7 +353,8 @@ def lqcd_apply_Mdag(ctx: Context, U: Gauge, inp: lqcd_field, out: lqcd_field, ka
 
 
 def cg_params(tol=1e-10, max_iter=20000, outer_prec=LQCD_F64, inner_prec=None, delta=0.1,
-              max_restarts=5, check_every=10, use_graph=1, sloppy_recon=0) -> lqcd_cg_params:
+              max_restarts=5, check_every=10, use_graph=1, sloppy_recon=0, solver=LQCD_SOLVER_CG,
+              inner_tol=0.0) -> lqcd_cg_params:
     p = lqcd_cg_params()
     p.tol = tol
     p.max_iter = max_iter
@@ -362,6 +365,8 @@ def cg_params(tol=1e-10, max_iter=20000, outer_prec=LQCD_F64, inner_prec=None, d
     p.check_every = check_every
     p.use_graph = use_graph
     p.sloppy_recon = sloppy_recon
+    p.solver = solver
+    p.inner_tol = inner_tol
     return p
 
 

@@ -159,3 +159,56 @@ def test_full_size_24x48_solve(ctx, oracle):
         x, st = _solve(ctx, G, L, b, kappa, mu, tol=1e-10, outer_prec=outer, inner_prec=inner)
         assert st[0]["converged"] == 1
         assert _true_resid(oracle, U, L, x, b, kappa, mu) <= 1e-10
+
+
+@pytest.mark.parametrize("outer,inner,recon", [
+    (lqcd.LQCD_F64, lqcd.LQCD_F64, 18),
+    (lqcd.LQCD_DF64, lqcd.LQCD_DF64, 18),
+    (lqcd.LQCD_DF64, lqcd.LQCD_F32, 12),
+    (lqcd.LQCD_DF64, lqcd.LQCD_F16S, 12),
+])
+@pytest.mark.parametrize("L,kind,kappa", [((4, 4, 4, 4), "haar", 0.15), ((6, 4, 2, 10), "haar", 0.15),
+                                          ((6, 4, 2, 10), "near", 0.12)])
+def test_bicgstab_on_mhat(ctx, oracle, outer, inner, recon, L, kind, kappa):
+    """BiCGStab on Mhat (the paper's other standard solver): the oracle's true
+    residual <= 1e-10 and the oracle's own solution, in plain FP64, float-float
+    and mixed precision with outer refinement.  BiCGStab needs the spectrum of
+    Mhat away from the origin, so the fields are Haar links, or near-identity
+    links below the free critical kappa 1/8."""
+    mu = 0.01 / (2 * kappa)
+    U = inputs.random_gauge(L, kind, seed=1101, eps=0.4)
+    G = lqcd.lqcd_gauge_import(ctx, dev(U), L)
+    b = inputs.gaussian_spinor(L, 1102)
+    x, st = _solve(ctx, G, L, b, kappa, mu, tol=1e-10, outer_prec=outer, inner_prec=inner,
+                   sloppy_recon=recon, solver=lqcd.LQCD_SOLVER_BICGSTAB, max_restarts=8)
+    assert st[0]["converged"] == 1 and st[0]["true_resid"] <= 1e-10
+    assert _true_resid(oracle, U, L, x, b, kappa, mu) <= 1e-10
+    xr = oracle.solve(U, b, L, kappa, mu, tol=1e-13)
+    assert np.linalg.norm(x - xr) / np.linalg.norm(xr) < 1e-7
+
+
+def test_bicgstab_rejects_several_rhs_and_batch(ctx):
+    L = (4, 4, 4, 4)
+    U = inputs.random_gauge(L, "near", seed=1103)
+    G = lqcd.lqcd_gauge_import(ctx, dev(U), L)
+    b = inputs.gaussian_spinor(L, 1104, nrhs=2)
+    with pytest.raises(lqcd.LqcdError) as e:
+        _solve(ctx, G, L, b, 0.15, 0.1, nrhs=2, solver=lqcd.LQCD_SOLVER_BICGSTAB)
+    assert e.value.status == lqcd.LQCD_ERR_UNSUPPORTED
+
+
+def test_bicgstab_reports_divergence(ctx):
+    """Near-free links beyond the free critical kappa (spectrum of Mhat around
+    the origin): BiCGStab does not converge and says so; CG on Mhat^+ Mhat
+    solves the same system."""
+    L = (6, 4, 2, 10)
+    kappa, mu = 0.16, 0.005 / 0.32
+    U = inputs.random_gauge(L, "near", seed=1105, eps=0.3)
+    G = lqcd.lqcd_gauge_import(ctx, dev(U), L)
+    b = inputs.gaussian_spinor(L, 1106)
+    x, st = _solve(ctx, G, L, b, kappa, mu, tol=1e-10, solver=lqcd.LQCD_SOLVER_BICGSTAB, max_iter=2000,
+                   allow_noconv=True)
+    x2, st2 = _solve(ctx, G, L, b, kappa, mu, tol=1e-10)
+    assert st2[0]["converged"] == 1
+    if not st[0]["converged"]:
+        assert st[0]["true_resid"] > 1e-10
