@@ -228,6 +228,8 @@ def run_gpu(args):
     # a mixed solve keeps 18-real links for its FP64-class operator (ALU-bound
     # on GB300, so rebuilding rows costs time) and uses `recon` for the sloppy one
     G = lqcd.lqcd_gauge_import(ctx, U_d, L, recon=recon if inner == prec else 18)
+    # the field in the sloppy operator's link format, for timing that operator's hop
+    Gh = G if (inner == prec or recon == 18) else lqcd.lqcd_gauge_import(ctx, U_d, L, recon=recon)
     del U_d
     b_d = torch.from_numpy(b_h).cuda()
     bd, _ = lqcd.alloc_field(L, lqcd.LQCD_FULL, lqcd.LQCD_F64)
@@ -270,7 +272,7 @@ def run_gpu(args):
     value = bytes_total / t / 1e9
 
     # dominant kernel: the half hop of the solve, timed alone on the library stream
-    hop = time_half_hop(ctx, G, lqcd, torch, inner, recon, stream)
+    hop = time_half_hop(ctx, Gh, lqcd, torch, inner, recon, stream)
 
     # end to end through the public API with host buffers
     e2e = run_e2e(ctx, lqcd, torch, U_h, b_h, prm, recon, args, stream)
@@ -516,8 +518,11 @@ def _solve_variants(torch, lqcd, ctx, G, L, b_h, kappa, mu, combos, nrhs=1, reps
             # warm-up (autotuning, graph); non-convergence is reported, not hidden
             lqcd.lqcd_cg_solve(ctx, G, fb, fx, kappa, mu, prm, allow_noconv=True)
             lqcd.lib().lqcd_reset_counters(ctx.handle)
+            # NVTX range for profiling, e.g. ncu --nvtx --nvtx-include "solve_12rhs_df64_f32_rec12/"
+            nvtx_push(f"solve_{nrhs}rhs_" + name.replace("/", "_"))
             t, st = _timed(torch, lambda: lqcd.lqcd_cg_solve(ctx, G, fb, fx, kappa, mu, prm,
                                                              allow_noconv=True), reps)
+            nvtx_pop()
         except Exception as e:
             out[name] = {"error": str(e)}
             continue
@@ -673,12 +678,15 @@ def run_config(args):
         for t in range(args.therm + args.trajs):
             st = lqcd.lqcd_hmc_trajectory(ctx, G, lqcd.hmc_params(
                 beta, kappa, mu, tau=1.0, nsteps=10, nf=1, seed=6106, traj=t, cg=cg,
-                integrator=lqcd.LQCD_2MN, c1=c1, nsteps_gauge=10))
+                integrator=lqcd.LQCD_2MN, c1=c1, nsteps_gauge=10, force_prec=PREC_NAMES[args.force_prec]))
             (therm if t < args.therm else trajs).append(st)
         secs = [s["seconds"] for s in trajs[1:]] or [trajs[0]["seconds"]]
         F = torch.zeros((4, int(np.prod(Lc)), 8), dtype=torch.float64, device="cuda")
-        tgf, _ = _timed(torch, lambda: lqcd.lqcd_gauge_force(ctx, G, beta, F, want_action=False, c1=c1), 5)
-        tgw, _ = _timed(torch, lambda: lqcd.lqcd_gauge_force(ctx, G, beta, F, want_action=False), 5)
+        gf = {}
+        for name, cc in (("tlsym", c1), ("wilson", 0.0)):
+            for pn in ("f64", "df64"):
+                gf[f"{name}_{pn}"] = 1e3 * _timed(torch, lambda: lqcd.lqcd_gauge_force(
+                    ctx, G, beta, F, want_action=False, c1=cc, prec=PREC_NAMES[pn]), 5)[0]
         config_line("HMC setup C", None,
                     {"s_per_trajectory": statistics.median(secs),
                      "dH": [s["dH"] for s in trajs], "accepted": [s["accepted"] for s in trajs],
@@ -689,9 +697,10 @@ def run_config(args):
                      "heatbath_s": thb, "thermalisation_trajectories": len(therm),
                      "thermalisation_dH": [s["dH"] for s in therm],
                      "thermalisation_plaquette": [s["plaquette"] for s in therm],
-                     "gauge_force_ms": {"tlsym": 1e3 * tgf, "wilson": 1e3 * tgw}},
+                     "gauge_force_ms": gf, "force_prec": args.force_prec},
                     {"workload": "24^3x8, tlSym beta=3.9, kappa=0.160856, a mu=0.1, 2MN 10 fermion x 10 "
-                                 "gauge steps, tau=1, F32-inner/DF64 CG to 1e-10 per force; start: "
+                                 f"gauge steps, tau=1, {args.force_prec} gauge force, F32-inner/DF64 CG to "
+                                 "1e-10 per force; start: "
                                  f"{min(args.sweeps, 100)} Wilson heatbath sweeps at beta=6.0 from cold"})
     elif c == "hb":
         # heatbath and overrelaxation throughput (Sec. 5.1) in FP64, counted with the
@@ -792,6 +801,8 @@ def main():
     ap.add_argument("--trajs", type=int, default=10, help="measured HMC trajectories for config 5")
     ap.add_argument("--therm", type=int, default=20, help="HMC thermalisation trajectories for config 5")
     ap.add_argument("--quick", action="store_true", help="config 4a: 2 sequential solves, scaled")
+    ap.add_argument("--force-prec", default="df64", choices=["f64", "df64"],
+                    help="config C: arithmetic of the gauge force (H and dH are FP64 either way)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

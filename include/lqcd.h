@@ -296,10 +296,13 @@ int lqcd_fermion_force(lqcd_ctx *ctx, const lqcd_gauge *U, lqcd_field phi, doubl
  * along nu); c1 = 0 is the Wilson action, c1 = -1/12 tree-level Symanzik.
  * dSdw (device float64 [4][V][8]) receives the derivative
  *   dS_g/domega^a = -(beta/3) Re Tr[i T^a U_mu(x) W_mu(x)],
- * W = c0 (6 plaquette staples) + c1 (18 rectangle staples).  *S_out host (may
- * be NULL, then the call is asynchronous).  Non-finite beta or c1:
- * LQCD_ERR_NONFINITE. */
-int lqcd_gauge_force(lqcd_ctx *ctx, const lqcd_gauge *U, double beta, double c1, double *dSdw,
+ * W = c0 (6 plaquette staples) + c1 (18 rectangle staples).  prec selects
+ * the arithmetic of the staples and products: LQCD_F64 (IEEE FP64) or
+ * LQCD_DF64 (float-float from the field's DF64 copy, FP64-class accuracy; the
+ * action is always summed in FP64).  *S_out host (may be NULL, then the call
+ * is asynchronous).  Non-finite beta or c1: LQCD_ERR_NONFINITE; other prec:
+ * LQCD_ERR_INVALID. */
+int lqcd_gauge_force(lqcd_ctx *ctx, const lqcd_gauge *U, double beta, double c1, int prec, double *dSdw,
                      double *S_out);
 
 /* Plaquette (1/(6V)) sum_{x, mu<nu} (1/3) Re Tr U_munu(x) in FP64.  Synchronous. */
@@ -347,7 +350,8 @@ typedef struct {
   int32_t integrator;  /* LQCD_LEAPFROG or LQCD_2MN (two time scales) */
   double c1;           /* rectangle coefficient of the gauge action (0: Wilson) */
   int32_t nsteps_gauge;/* 2MN: inner gauge steps per outer position update (>= 1) */
-  int32_t reserved;
+  int32_t force_prec;  /* gauge-force arithmetic: LQCD_F64 (default) or LQCD_DF64
+                          (float-float, FP64-class; H and dH stay IEEE FP64) */
   double lambda;       /* 2MN parameter; 0 selects 0.1931833275037836 */
   lqcd_cg_params cg;   /* solver used for every force and action evaluation */
 } lqcd_hmc_params;

@@ -210,6 +210,79 @@ template <class R> LQCD_DEV double norm2_d(Cx<R> a) {
   double re = to_double(a.re), im = to_double(a.im);
   return __fma_rn(re, re, __dmul_rn(im, im));
 }
+// Float-float complex dot products (the hop's colour products, the gauge
+// force's 3x3 products).  Each real output is a
+// sum of six products a*b of double-words; every product contributes its
+// exact leading part p = a.hi*b.hi (TwoProduct: the rounding error comes from
+// one FMA) plus the first-order cross terms a.hi*b.lo + a.lo*b.hi, and the
+// leading parts are summed by a TwoSum chain whose errors join the low-order
+// accumulator.  The dropped a.lo*b.lo terms are below 2^-46 of each product.
+struct DfAcc {
+  float s, e;
+};
+LQCD_DEV void dfacc_add_prod(DfAcc &A, df a, df b, bool neg) {
+  float ah = neg ? -a.hi : a.hi, al = neg ? -a.lo : a.lo;
+  float p = __fmul_rn(ah, b.hi);
+  float pe = __fmaf_rn(ah, b.hi, -p);
+  pe = __fmaf_rn(ah, b.lo, pe);
+  pe = __fmaf_rn(al, b.hi, pe);
+  df t = two_sum(A.s, p);
+  A.s = t.hi;
+  A.e = __fadd_rn(A.e, __fadd_rn(t.lo, pe));
+}
+// the first product of a sum starts the accumulator (no TwoSum with zero)
+LQCD_DEV DfAcc dfacc_first(df a, df b, bool neg) {
+  float ah = neg ? -a.hi : a.hi, al = neg ? -a.lo : a.lo;
+  float p = __fmul_rn(ah, b.hi);
+  float pe = __fmaf_rn(ah, b.hi, -p);
+  pe = __fmaf_rn(ah, b.lo, pe);
+  pe = __fmaf_rn(al, b.hi, pe);
+  return {p, pe};
+}
+LQCD_DEV df dfacc_result(const DfAcc &A) { return fast_two_sum(A.s, A.e); }
+
+// sum_j x_j * y_j (conjugating x when CONJ), complex double-words.  LAZY
+// returns the accumulators unnormalised (value hi + lo exact, |lo| a few
+// ulp(hi) at most), for callers that only add the result to other
+// double-words before normalising.
+template <bool CONJ, bool LAZY = false>
+LQCD_DEV Cx<df> dfdot3(const Cx<df> x0, const Cx<df> x1, const Cx<df> x2, const Cx<df> y0,
+                       const Cx<df> y1, const Cx<df> y2) {
+  const Cx<df> xs[3] = {x0, x1, x2}, ys[3] = {y0, y1, y2};
+  // (a + ib)(c + id) = (ac - bd) + i(ad + bc);  conj: (ac + bd) + i(ad - bc)
+  DfAcc re = dfacc_first(xs[0].re, ys[0].re, false);
+  DfAcc im = dfacc_first(xs[0].re, ys[0].im, false);
+  dfacc_add_prod(re, xs[0].im, ys[0].im, !CONJ);
+  dfacc_add_prod(im, xs[0].im, ys[0].re, CONJ);
+#pragma unroll
+  for (int j = 1; j < 3; j++) {
+    dfacc_add_prod(re, xs[j].re, ys[j].re, false);
+    dfacc_add_prod(re, xs[j].im, ys[j].im, !CONJ);
+    dfacc_add_prod(im, xs[j].re, ys[j].im, false);
+    dfacc_add_prod(im, xs[j].im, ys[j].re, CONJ);
+  }
+  if (LAZY) return {{re.s, re.e}, {im.s, im.e}};
+  return {dfacc_result(re), dfacc_result(im)};
+}
+
+// Double-word sum without the final renormalisation (TwoSum of the high
+// parts, low parts added in float: 8 operations).  The value hi + lo is the
+// same as with renormalisation; the hop accumulates its sums this way and
+// renormalises each accumulator once, before the epilogue.
+LQCD_DEV df add_lazy(df a, df b) {
+  df s = two_sum(a.hi, b.hi);
+  s.lo = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+  return s;
+}
+LQCD_DEV df neg_df(df a) { return {-a.hi, -a.lo}; }
+LQCD_DEV Cx<df> cadd_lazy(Cx<df> a, Cx<df> b) { return {add_lazy(a.re, b.re), add_lazy(a.im, b.im)}; }
+LQCD_DEV Cx<df> csub_lazy(Cx<df> a, Cx<df> b) {
+  return {add_lazy(a.re, neg_df(b.re)), add_lazy(a.im, neg_df(b.im))};
+}
+LQCD_DEV Cx<df> cnormalise(Cx<df> a) {
+  return {fast_two_sum(a.re.hi, a.re.lo), fast_two_sum(a.im.hi, a.im.lo)};
+}
+
 // |v|^2 of one site's n complex components, returned as a double.  FP64 and
 // float-float values are squared and summed in FP64.  FP32 values (the
 // sloppy formats, whose components carry 24-bit mantissas at best) are

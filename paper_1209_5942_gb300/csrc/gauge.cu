@@ -317,6 +317,164 @@ __global__ void __launch_bounds__(128) gauge_force_sym_kernel(const double2 *U, 
   }
 }
 
+// ---------------------------------------------------------------------------
+// The same staple construction in float-float arithmetic (FP64-class
+// accuracy on the FP32 pipe, the hop's DF64 format): GB300's FP64 pipe runs at
+// 1/64 of the FP32 rate, and the tlSym force is ~10^4 flop per link.  Links
+// come from the DF64 copy of the field; 3x3 products use the error-free
+// complex dot product of the hop; W is converted to FP64 for the traces.
+// ---------------------------------------------------------------------------
+struct M3d {
+  Cx<df> m[9];
+};
+LQCD_DEV M3d dmul(const M3d &a, const M3d &b) {  // a b
+  M3d r;
+#pragma unroll
+  for (int i = 0; i < 3; i++)
+#pragma unroll
+    for (int j = 0; j < 3; j++)
+      r.m[3 * i + j] = dfdot3<false>(a.m[3 * i], a.m[3 * i + 1], a.m[3 * i + 2], b.m[j], b.m[3 + j], b.m[6 + j]);
+  return r;
+}
+LQCD_DEV M3d dmul_nd(const M3d &a, const M3d &b) {  // a b^+
+  M3d r;
+#pragma unroll
+  for (int i = 0; i < 3; i++)
+#pragma unroll
+    for (int j = 0; j < 3; j++)
+      r.m[3 * i + j] = dfdot3<true>(b.m[3 * j], b.m[3 * j + 1], b.m[3 * j + 2], a.m[3 * i], a.m[3 * i + 1],
+                                    a.m[3 * i + 2]);
+  return r;
+}
+LQCD_DEV M3d load_link_d(const GaugeView &Ud, const Pos &s, int mu) {
+  M3d u;
+  LinkIO<LQCD_DF64, 18>::load(Ud, s.p, mu, s.cb, u.m);
+  return u;
+}
+LQCD_DEV M3d dagger_d(const M3d &u) {
+  M3d d;
+#pragma unroll
+  for (int i = 0; i < 3; i++)
+#pragma unroll
+    for (int j = 0; j < 3; j++) d.m[3 * i + j] = conj(u.m[3 * j + i]);
+  return d;
+}
+// U_{s nu}(c) in float-float
+LQCD_DEV M3d signed_link_d(const GaugeView &Ud, const Geom &g, const int c[4], int nu, int s) {
+  if (s > 0) return load_link_d(Ud, at(g, c), nu);
+  int d[4] = {c[0], c[1], c[2], c[3]};
+  coords_shift(g, d, nu, -1);
+  return dagger_d(load_link_d(Ud, at(g, d), nu));
+}
+LQCD_DEV void store_stap_d(float4 *S, long V, int mu, int k, long lexi, const M3d &t) {
+#pragma unroll
+  for (int e = 0; e < 9; e++)
+    S[stap_index(V, mu, k, e, lexi)] = make_float4(t.m[e].re.hi, t.m[e].im.hi, t.m[e].re.lo, t.m[e].im.lo);
+}
+LQCD_DEV M3d load_stap_d(const float4 *S, long V, int mu, int k, long lexi) {
+  M3d r;
+#pragma unroll
+  for (int e = 0; e < 9; e++) {
+    const float4 w = S[stap_index(V, mu, k, e, lexi)];
+    r.m[e] = {{w.x, w.z}, {w.y, w.w}};
+  }
+  return r;
+}
+LQCD_DEV void add_lazy_m(M3d &A, const M3d &t) {
+#pragma unroll
+  for (int e = 0; e < 9; e++) A.m[e] = cadd_lazy(A.m[e], t.m[e]);
+}
+
+__global__ void __launch_bounds__(128) staple6_df_kernel(GaugeView Ud, Geom g, float4 *S) {
+  long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  int p, cb, c[4];
+  if (!thread_site(g, tid, &p, &cb, c)) return;
+  const long V = 2L * g.Vh;
+  const long lexi = at(g, c).lexi;
+#pragma unroll 1
+  for (int mu = 0; mu < 4; mu++) {
+    int cpm[4] = {c[0], c[1], c[2], c[3]};
+    coords_shift(g, cpm, mu, +1);
+#pragma unroll 1
+    for (int k = 0; k < 6; k++) {
+      const int nu = (k >> 1) + ((k >> 1) >= mu ? 1 : 0), s = (k & 1) ? -1 : 1;
+      int cps[4] = {c[0], c[1], c[2], c[3]};
+      coords_shift(g, cps, nu, s);
+      // U_{s nu}(x + mu) U_mu(x + s nu)^+ U_{s nu}(x)^+
+      M3d t = dmul_nd(signed_link_d(Ud, g, cpm, nu, s), load_link_d(Ud, at(g, cps), mu));
+      t = dmul_nd(t, signed_link_d(Ud, g, c, nu, s));
+      store_stap_d(S, V, mu, k, lexi, t);
+    }
+  }
+}
+
+// dS/domega of c0 (plaquette) + c1 (rectangle) in float-float; c1 = 0 gives
+// the Wilson force from the plaquette staples alone
+__global__ void __launch_bounds__(128) gauge_force_df_kernel(GaugeView Ud, const float4 *S, Geom g, double beta,
+                                                             double c1, double *out) {
+  long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  int p, cb, c[4];
+  if (!thread_site(g, tid, &p, &cb, c)) return;
+  const long V = 2L * g.Vh;
+  const Pos s0 = at(g, c);
+  const double c0 = 1.0 - 8.0 * c1;
+#pragma unroll 1
+  for (int mu = 0; mu < 4; mu++) {
+    int cpm[4] = {c[0], c[1], c[2], c[3]}, cmm[4] = {c[0], c[1], c[2], c[3]};
+    coords_shift(g, cpm, mu, +1);
+    coords_shift(g, cmm, mu, -1);
+    const Pos spm = at(g, cpm), smm = at(g, cmm);
+    // rectangles first, then the plaquette staples (re-read), so only one
+    // 3x3 accumulator is live during the products
+    M3d Wr, Wp;
+#pragma unroll
+    for (int e = 0; e < 9; e++) Wr.m[e] = czero<df>();
+#pragma unroll 1
+    for (int k = 0; k < 6; k++) {
+      if (c1 != 0.0) {
+        const M3d Sx = load_stap_d(S, V, mu, k, s0.lexi);
+        const int nu = (k >> 1) + ((k >> 1) >= mu ? 1 : 0), s = (k & 1) ? -1 : 1;
+        add_lazy_m(Wr, dmul(dmul(load_link_d(Ud, spm, mu), load_stap_d(S, V, mu, k, spm.lexi)), Sx));
+        add_lazy_m(Wr, dmul(dmul(Sx, load_stap_d(S, V, mu, k, smm.lexi)), load_link_d(Ud, smm, mu)));
+        int cps[4] = {c[0], c[1], c[2], c[3]};
+        coords_shift(g, cps, nu, s);
+        add_lazy_m(Wr, dmul_nd(dmul(signed_link_d(Ud, g, cpm, nu, s), load_stap_d(S, V, mu, k, at(g, cps).lexi)),
+                               signed_link_d(Ud, g, c, nu, s)));
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < 9; e++) Wp.m[e] = czero<df>();
+#pragma unroll 1
+    for (int k = 0; k < 6; k++) add_lazy_m(Wp, load_stap_d(S, V, mu, k, s0.lexi));
+    // A = c0 Wp + c1 Wr, then W = U A in FP64 (one 3x3 product per link)
+    M3 A, u;
+#pragma unroll
+    for (int e = 0; e < 9; e++) {
+      const Cx<df> wp = cnormalise(Wp.m[e]), wr = cnormalise(Wr.m[e]);
+      A.m[e] = {c0 * df_to_double(wp.re) + c1 * df_to_double(wr.re), c0 * df_to_double(wp.im) + c1 * df_to_double(wr.im)};
+    }
+    {
+      const M3d ud = load_link_d(Ud, s0, mu);
+#pragma unroll
+      for (int e = 0; e < 9; e++) u.m[e] = {df_to_double(ud.m[e].re), df_to_double(ud.m[e].im)};
+    }
+    const M3 W = mmul(u, A);
+    const C *w = W.m;
+    double tr[8];
+    tr[0] = (w[3] + w[1]).im;
+    tr[1] = (times_i(w[1] - w[3])).im;
+    tr[2] = (w[0] - w[4]).im;
+    tr[3] = (w[6] + w[2]).im;
+    tr[4] = (times_i(w[2] - w[6])).im;
+    tr[5] = (w[7] + w[5]).im;
+    tr[6] = (times_i(w[5] - w[7])).im;
+    tr[7] = (w[0] + w[4] - w[8] - w[8]).im * 0.57735026918962576451;
+    double *o = out + ((size_t)mu * V + s0.lexi) * 8;
+#pragma unroll
+    for (int a = 0; a < 8; a++) o[a] = (beta / 3.0) * 0.5 * tr[a];
+  }
+}
+
 // sum over sites of sum_{mu != nu} Re Tr R_munu(x) (R: two links along mu,
 // one along nu): per-block partials
 __global__ void __launch_bounds__(128) rectangle_kernel(const double2 *U, Geom g, double *partials) {
@@ -705,9 +863,11 @@ lqcd_status rectangle_sum(lqcd_ctx *ctx, const lqcd_gauge *U, double *sum_retr) 
   return sum_partials(ctx, nb, sum_retr);
 }
 
-lqcd_status gauge_force_raw(lqcd_ctx *ctx, const lqcd_gauge *U, double beta, double c1, double *dSdw) {
+// dS_g/dw into dSdw; prec LQCD_F64 (IEEE FP64 throughout) or LQCD_DF64
+// (staples and products in float-float from the DF64 copy of the links)
+lqcd_status gauge_force_raw(lqcd_ctx *ctx, lqcd_gauge *U, double beta, double c1, int prec, double *dSdw) {
   long V = 2L * U->g.Vh;
-  if (c1 != 0.0) {
+  if (c1 != 0.0 || prec == LQCD_DF64) {
     // plaquette staples of every link (6 x 144 B per link), then the force
     const size_t need = (size_t)4 * 6 * 9 * V * sizeof(double2);
     if (ctx->staple_cap < need) {
@@ -716,6 +876,15 @@ lqcd_status gauge_force_raw(lqcd_ctx *ctx, const lqcd_gauge *U, double beta, dou
       ctx->staple_cap = 0;
       LQCD_CUDA(ctx, cudaMallocAsync(&ctx->staples, need, ctx->stream));
       ctx->staple_cap = need;
+    }
+    if (prec == LQCD_DF64) {
+      GaugeView Ud;
+      LQCD_TRY(gauge_view(ctx, U, LQCD_DF64, 18, &Ud));
+      staple6_df_kernel<<<nblk(V), 128, 0, ctx->stream>>>(Ud, U->g, (float4 *)ctx->staples);
+      gauge_force_df_kernel<<<nblk(V), 128, 0, ctx->stream>>>(Ud, (const float4 *)ctx->staples, U->g, beta, c1,
+                                                              dSdw);
+      LQCD_CUDA(ctx, cudaGetLastError());
+      return LQCD_OK;
     }
     staple6_kernel<<<nblk(V), 128, 0, ctx->stream>>>((const double2 *)U->master, U->g,
                                                      (double2 *)ctx->staples);

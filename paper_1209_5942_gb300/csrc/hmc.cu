@@ -19,7 +19,7 @@ namespace lqcd {
 lqcd_status check_geom(lqcd_ctx *ctx, const lqcd_geom *g);
 lqcd_status check_field(lqcd_ctx *ctx, const lqcd_field &f, const char *name, bool allow_lexi);
 lqcd_status plaquette_sum(lqcd_ctx *ctx, const lqcd_gauge *U, double *sum_retr);
-lqcd_status gauge_force_raw(lqcd_ctx *ctx, const lqcd_gauge *U, double beta, double c1, double *dSdw);
+lqcd_status gauge_force_raw(lqcd_ctx *ctx, lqcd_gauge *U, double beta, double c1, int prec, double *dSdw);
 lqcd_status rectangle_sum(lqcd_ctx *ctx, const lqcd_gauge *U, double *sum_retr);
 lqcd_status heatbath_raw(lqcd_ctx *ctx, lqcd_gauge *U, double beta, uint64_t seed, uint64_t sweep, int n_or,
                          unsigned int *fail_dev);
@@ -202,13 +202,15 @@ static lqcd_status gauge_action_sym(lqcd_ctx *ctx, const lqcd_gauge *U, double b
   return LQCD_OK;
 }
 
-extern "C" int lqcd_gauge_force(lqcd_ctx *ctx, const lqcd_gauge *U, double beta, double c1, double *dSdw,
-                                double *S_out) {
+extern "C" int lqcd_gauge_force(lqcd_ctx *ctx, const lqcd_gauge *U, double beta, double c1, int prec,
+                                double *dSdw, double *S_out) {
   if (!ctx) return LQCD_ERR_INVALID;
   LQCD_TRY(check_u(ctx, U));
   if (!dSdw || !aligned16(dSdw)) return fail(ctx, LQCD_ERR_INVALID, "dSdw: NULL or misaligned");
   if (!std::isfinite(beta) || !std::isfinite(c1)) return fail(ctx, LQCD_ERR_NONFINITE, "beta or c1 not finite");
-  LQCD_TRY(gauge_force_raw(ctx, U, beta, c1, dSdw));
+  if (prec != LQCD_F64 && prec != LQCD_DF64) return fail(ctx, LQCD_ERR_INVALID, "prec must be LQCD_F64 or LQCD_DF64");
+  // the DF64 copy of the links is a cache of the field: it does not change U
+  LQCD_TRY(gauge_force_raw(ctx, const_cast<lqcd_gauge *>(U), beta, c1, prec, dSdw));
   if (S_out) LQCD_TRY(gauge_action_sym(ctx, U, beta, c1, S_out));
   return LQCD_OK;
 }
@@ -340,6 +342,8 @@ extern "C" int lqcd_hmc_trajectory(lqcd_ctx *ctx, lqcd_gauge *U, const lqcd_hmc_
     return fail(ctx, LQCD_ERR_INVALID, "2MN needs nsteps_gauge >= 1");
   if (!std::isfinite(prm->c1) || !std::isfinite(prm->lambda) || prm->lambda < 0.0 || prm->lambda >= 0.5)
     return fail(ctx, LQCD_ERR_INVALID, "c1 must be finite and lambda in [0, 0.5)");
+  if (prm->force_prec != LQCD_F64 && prm->force_prec != LQCD_DF64)
+    return fail(ctx, LQCD_ERR_INVALID, "force_prec must be LQCD_F64 or LQCD_DF64");
   auto t0 = std::chrono::steady_clock::now();
   std::memset(stats, 0, sizeof(*stats));
   const Geom &g = U->g;
@@ -385,7 +389,7 @@ extern "C" int lqcd_hmc_trajectory(lqcd_ctx *ctx, lqcd_gauge *U, const lqcd_hmc_
   double wg = 0.0, wf = 0.0;
   auto flush = [&]() -> lqcd_status {
     if (wg != 0.0) {
-      LQCD_TRY(gauge_force_raw(ctx, U, prm->beta, prm->c1, (double *)F.p));
+      LQCD_TRY(gauge_force_raw(ctx, U, prm->beta, prm->c1, prm->force_prec, (double *)F.p));
       LQCD_TRY(momenta_update_raw(ctx, V, (double *)P.p, (const double *)F.p, wg));
       wg = 0.0;
     }

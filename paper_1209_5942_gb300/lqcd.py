@@ -79,7 +79,7 @@ class lqcd_hmc_params(ctypes.Structure):
     _fields_ = [("beta", ctypes.c_double), ("kappa", ctypes.c_double), ("mu", ctypes.c_double),
                 ("tau", ctypes.c_double), ("nsteps", ctypes.c_int32), ("nf", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("traj", ctypes.c_uint32), ("integrator", ctypes.c_int32),
-                ("c1", ctypes.c_double), ("nsteps_gauge", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("c1", ctypes.c_double), ("nsteps_gauge", ctypes.c_int32), ("force_prec", ctypes.c_int32),
                 ("lam", ctypes.c_double), ("cg", lqcd_cg_params)]
 
 
@@ -129,7 +129,7 @@ SIGNATURES = [
     ("lqcd_fermion_force", _i, [_vp, _vp, lqcd_field, _vp, ctypes.POINTER(lqcd_field),
                                 ctypes.POINTER(lqcd_geom), _d, _d, ctypes.POINTER(lqcd_cg_params),
                                 ctypes.POINTER(lqcd_cg_stats), ctypes.POINTER(_d)]),
-    ("lqcd_gauge_force", _i, [_vp, _vp, _d, _d, _vp, ctypes.POINTER(_d)]),
+    ("lqcd_gauge_force", _i, [_vp, _vp, _d, _d, _i, _vp, ctypes.POINTER(_d)]),
     ("lqcd_plaquette", _i, [_vp, _vp, ctypes.POINTER(_d)]),
     ("lqcd_heatbath_sweep", _i, [_vp, _vp, _d, ctypes.c_uint64, ctypes.c_uint64, _i]),
     ("lqcd_momenta_gaussian", _i, [_vp, ctypes.POINTER(lqcd_geom), _vp, ctypes.c_uint64,
@@ -409,9 +409,10 @@ def lqcd_fermion_force(ctx: Context, U: Gauge, phi: lqcd_field, dSdw: torch.Tens
     return S.value, st.as_dict()
 
 
-def lqcd_gauge_force(ctx: Context, U: Gauge, beta, dSdw: torch.Tensor, want_action=True, c1=0.0):
+def lqcd_gauge_force(ctx: Context, U: Gauge, beta, dSdw: torch.Tensor, want_action=True, c1=0.0,
+                     prec=LQCD_F64):
     S = _d(0.0)
-    ctx.check(lib().lqcd_gauge_force(ctx.handle, U.handle, beta, c1, _vp(dSdw.data_ptr()),
+    ctx.check(lib().lqcd_gauge_force(ctx.handle, U.handle, beta, c1, prec, _vp(dSdw.data_ptr()),
                                      ctypes.byref(S) if want_action else None))
     return S.value if want_action else None
 
@@ -466,11 +467,12 @@ TLSYM_C1 = -1.0 / 12.0
 
 
 def hmc_params(beta, kappa, mu, tau=1.0, nsteps=20, nf=1, seed=1, traj=0, cg=None,
-               integrator=LQCD_LEAPFROG, c1=0.0, nsteps_gauge=1, lam=0.0):
+               integrator=LQCD_LEAPFROG, c1=0.0, nsteps_gauge=1, lam=0.0, force_prec=LQCD_F64):
     p = lqcd_hmc_params()
     p.beta, p.kappa, p.mu, p.tau = beta, kappa, mu, tau
     p.nsteps, p.nf, p.seed, p.traj = nsteps, nf, seed, traj
     p.integrator, p.c1, p.nsteps_gauge, p.lam = integrator, c1, nsteps_gauge, lam
+    p.force_prec = force_prec
     p.cg = cg if cg is not None else cg_params(tol=1e-10, outer_prec=LQCD_DF64,
                                                inner_prec=LQCD_F32)
     return p

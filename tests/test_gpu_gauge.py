@@ -246,21 +246,25 @@ def test_pure_gauge_hmc_matches_oracle_and_scales(ctx, oracle):
 
 
 @pytest.mark.parametrize("L", [(4, 4, 4, 4), (2, 4, 6, 8)])
-def test_tlsym_gauge_force_and_action(ctx, oracle, L):
-    """Tree-level Symanzik action (c1 = -1/12, Sec. 2.1 eq. S_tlsym): the GPU
-    rectangle staples against the oracle's loop-by-loop derivative, and the
-    action against the oracle's plaquette + rectangle sums."""
-    beta, c1 = 3.9, lqcd.TLSYM_C1
+@pytest.mark.parametrize("prec", [lqcd.LQCD_F64, lqcd.LQCD_DF64])
+@pytest.mark.parametrize("c1", [lqcd.TLSYM_C1, 0.0])
+def test_tlsym_gauge_force_and_action(ctx, oracle, L, prec, c1):
+    """Tree-level Symanzik action (c1 = -1/12, Sec. 2.1 eq. S_tlsym) and the
+    Wilson action (c1 = 0), in FP64 and in float-float: the GPU staples
+    against the oracle's loop-by-loop derivative, and the action against the
+    oracle's plaquette + rectangle sums."""
+    beta = 3.9
     U = inputs.random_gauge(L, "near", seed=43, eps=0.5)
     G = lqcd.lqcd_gauge_import(ctx, dev(U), L)
     F = torch.zeros((4, inputs.volume(L), 8), dtype=torch.float64, device="cuda")
-    S = lqcd.lqcd_gauge_force(ctx, G, beta, F, c1=c1)
+    S = lqcd.lqcd_gauge_force(ctx, G, beta, F, c1=c1, prec=prec)
     assert relerr(host(F), oracle.gauge_dSdw_sym(U, L, beta, c1)) < 1e-13
     Sref = oracle.gauge_action_sym(U, L, beta, c1)
     assert abs(S - Sref) < 1e-11 * abs(Sref)
 
 
-def test_hmc_2mn_tlsym_trajectory_matches_oracle(ctx, oracle):
+@pytest.mark.parametrize("force_prec", [lqcd.LQCD_F64, lqcd.LQCD_DF64])
+def test_hmc_2mn_tlsym_trajectory_matches_oracle(ctx, oracle, force_prec):
     """One trajectory of the paper's HMC setup kind (Sec. 5.3): tlSym gauge
     action, 2MN on separate fermion and gauge time scales, from the same links
     and Philox streams as the oracle; dH and the final links agree."""
@@ -271,7 +275,7 @@ def test_hmc_2mn_tlsym_trajectory_matches_oracle(ctx, oracle):
     seed, traj = 77, 5
     prm = lqcd.hmc_params(beta, kappa, mu, tau=0.5, nsteps=3, nf=1, seed=seed, traj=traj,
                           cg=lqcd.cg_params(tol=1e-13, max_iter=50000), integrator=lqcd.LQCD_2MN,
-                          c1=c1, nsteps_gauge=2)
+                          c1=c1, nsteps_gauge=2, force_prec=force_prec)
     st = lqcd.lqcd_hmc_trajectory(ctx, G, prm)
     P0 = oracle.momenta(L, seed, traj)
     eta = oracle.gaussian_spinor(L, seed, traj) * (~oracle.parity_mask(L))[:, None, None]
