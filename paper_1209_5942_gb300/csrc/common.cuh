@@ -191,6 +191,41 @@ template <> LQCD_DEV Cx<float> conj_madd(Cx<float> a, Cx<float> b, Cx<float> c) 
   return {fmaf(a.im, b.im, fmaf(a.re, b.re, c.re)), fmaf(-a.im, b.re, fmaf(a.re, b.im, c.im))};
 }
 
+// ---------------------------------------------------------------------------
+// Two lanes of FP32 in one register pair (float2: lane x, lane y), operated on
+// with the packed FP32x2 instructions of sm_100+ (__fadd2_rn, __fmul2_rn,
+// __ffma2_rn: two IEEE single-precision operations, each rounded as the
+// scalar one).  The hop uses Cx<float2> for two output sites at once; every
+// packed expression below mirrors the FP32 specialisation above operation by
+// operation, so each lane's result is bit-identical to the scalar kernel's.
+// ---------------------------------------------------------------------------
+LQCD_DEV float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+template <> LQCD_DEV float2 rzero<float2>() { return make_float2(0.0f, 0.0f); }
+template <> LQCD_DEV Cx<float2> operator+(Cx<float2> a, Cx<float2> b) {
+  return {__fadd2_rn(a.re, b.re), __fadd2_rn(a.im, b.im)};
+}
+template <> LQCD_DEV Cx<float2> operator-(Cx<float2> a, Cx<float2> b) {
+  return {__fadd2_rn(a.re, neg2(b.re)), __fadd2_rn(a.im, neg2(b.im))};
+}
+template <> LQCD_DEV Cx<float2> operator-(Cx<float2> a) { return {neg2(a.re), neg2(a.im)}; }
+template <> LQCD_DEV Cx<float2> operator*(Cx<float2> a, Cx<float2> b) {
+  return {__ffma2_rn(a.re, b.re, neg2(__fmul2_rn(a.im, b.im))), __ffma2_rn(a.re, b.im, __fmul2_rn(a.im, b.re))};
+}
+template <> LQCD_DEV Cx<float2> cmadd(Cx<float2> a, Cx<float2> b, Cx<float2> c) {
+  return {__ffma2_rn(neg2(a.im), b.im, __ffma2_rn(a.re, b.re, c.re)),
+          __ffma2_rn(a.im, b.re, __ffma2_rn(a.re, b.im, c.im))};
+}
+template <> LQCD_DEV Cx<float2> conj_madd(Cx<float2> a, Cx<float2> b, Cx<float2> c) {
+  return {__ffma2_rn(a.im, b.im, __ffma2_rn(a.re, b.re, c.re)),
+          __ffma2_rn(neg2(a.im), b.re, __ffma2_rn(a.re, b.im, c.im))};
+}
+template <> LQCD_DEV Cx<float2> times_i(Cx<float2> a) { return {neg2(a.im), a.re}; }
+template <> LQCD_DEV Cx<float2> conj(Cx<float2> a) { return {a.re, neg2(a.im)}; }
+// the pair (a, b) of two scalar complex numbers, and its lanes
+LQCD_DEV Cx<float2> cpair(Cx<float> a, Cx<float> b) { return {make_float2(a.re, b.re), make_float2(a.im, b.im)}; }
+LQCD_DEV Cx<float> lane_x(Cx<float2> a) { return {a.re.x, a.im.x}; }
+LQCD_DEV Cx<float> lane_y(Cx<float2> a) { return {a.re.y, a.im.y}; }
+
 // Host-side complex scalar handed to kernels in the arithmetic of the kernel.
 struct HostC {
   double re, im;

@@ -60,7 +60,7 @@ lqcd_status launch_hop(lqcd_ctx *ctx, const Geom &g, const HopLaunch &L, int *nb
   //  per site and is bounded to 128 threads per block.
   struct Cand {
     short bx, by, gm, rt;
-    bool lf;
+    bool lf, two;  // two: two sites per thread in packed FP32x2
   };
   Cand cands[96];
   int ncand = 0, fallback = 0;
@@ -89,19 +89,22 @@ lqcd_status launch_hop(lqcd_ctx *ctx, const Geom &g, const HopLaunch &L, int *nb
       for (short rt : {2, 4})
         for (short by : {1, 2, 4})
           if (rt * by <= nrhs) cands[ncand++] = {32, by, GM[gi], rt, false};
+  // packed two-site kernel: blocks of 64 threads = 128 sites, one RHS per block row
+  if (low)
+    for (int gi = 0; gi < 3; gi++) cands[ncand++] = {64, 1, GM[gi], 1, false, true};
   // default without tuning: the full-grid, one-RHS-per-thread candidate with
   // 128-site blocks for one RHS, or with the most RHS per block for several
   for (int c = 0; c < ncand; c++) {
     const Cand &k = cands[c];
-    if (k.gm != 0 || k.lf || k.rt != 1) continue;
+    if (k.gm != 0 || k.lf || k.rt != 1 || k.two) continue;
     if (nrhs == 1 ? k.bx == 128 : k.by >= cands[fallback].by) fallback = c;
   }
   auto go = [&](int ci, const HopArgs &args) {
     const Cand &k = cands[ci];
     const int rt = k.rt;
     dim3 block(k.bx, k.by, 1), grid;
-    const int per_block = pair ? k.bx / 2 : k.bx;  // sites per block row
-    const int groups = (nrhs + rt - 1) / rt;       // RHS groups (of rt) to cover
+    const int per_block = pair ? k.bx / 2 : (k.two ? 2 * k.bx : k.bx);  // sites per block row
+    const int groups = (nrhs + rt - 1) / rt;                             // RHS groups (of rt) to cover
     grid = dim3((g.Vh + per_block - 1) / per_block, 1, (groups + k.by - 1) / k.by);
     if (k.gm > 0) {
       unsigned cap = (unsigned)(ctx->num_sms * k.gm);
@@ -111,12 +114,12 @@ lqcd_status launch_hop(lqcd_ctx *ctx, const Geom &g, const HopLaunch &L, int *nb
     switch (L.prec) {
       case LQCD_F64: hop_launch_f64(args, L.recon, grid, block, dag, red, st); break;
       case LQCD_DF64: hop_launch_df64(args, L.recon, pair, grid, block, dag, red, st); break;
-      case LQCD_F32: hop_launch_f32(args, L.recon, grid, block, dag, red, k.lf, rt, st); break;
-      default: hop_launch_h16(args, L.prec, grid, block, dag, red, k.lf, rt, st); break;
+      case LQCD_F32: hop_launch_f32(args, L.recon, grid, block, dag, red, k.lf, rt, k.two, st); break;
+      default: hop_launch_h16(args, L.prec, grid, block, dag, red, k.lf, rt, k.two, st); break;
     }
   };
   char key[160];
-  snprintf(key, sizeof(key), "hop2|p%d|r%d|d%d|red%d|aux%d|%dx%dx%dx%d|n%d", L.prec, L.recon, (int)dag, (int)red,
+  snprintf(key, sizeof(key), "hop3|p%d|r%d|d%d|red%d|aux%d|%dx%dx%dx%d|n%d", L.prec, L.recon, (int)dag, (int)red,
            A.has_aux, g.L[0], g.L[1], g.L[2], g.L[3], nrhs);
   HopArgs At = A;
   At.halt = nullptr;  // timing launches run whatever the solver state

@@ -5,7 +5,12 @@
 namespace lqcd {
 
 void hop_launch_f32(const HopArgs &A, int recon, dim3 grid, dim3 block, bool dag, bool red, bool lf, int rt,
-                    cudaStream_t st) {
+                    bool two, cudaStream_t st) {
+  if (two) {
+    if (recon == 12) launch_pair2<LQCD_F32, 12>(A, grid, block, dag, red, st);
+    else launch_pair2<LQCD_F32, 18>(A, grid, block, dag, red, st);
+    return;
+  }
   if (rt > 1) {
     if (recon == 12) launch_rt<LQCD_F32, 12>(A, rt, grid, block, dag, red, st);
     else launch_rt<LQCD_F32, 18>(A, rt, grid, block, dag, red, st);

@@ -6,7 +6,12 @@
 namespace lqcd {
 
 void hop_launch_h16(const HopArgs &A, int prec, dim3 grid, dim3 block, bool dag, bool red, bool lf, int rt,
-                    cudaStream_t st) {
+                    bool two, cudaStream_t st) {
+  if (two) {
+    if (prec == LQCD_BF16S) launch_pair2<LQCD_BF16S, 12>(A, grid, block, dag, red, st);
+    else launch_pair2<LQCD_F16S, 12>(A, grid, block, dag, red, st);
+    return;
+  }
   if (rt > 1) {
     if (prec == LQCD_BF16S) launch_rt<LQCD_BF16S, 12>(A, rt, grid, block, dag, red, st);
     else launch_rt<LQCD_F16S, 12>(A, rt, grid, block, dag, red, st);

@@ -61,13 +61,23 @@ template <int F> LQCD_DEV void add_f(Cx<float> &acc, float sc, Cx<float> w) {
   else acc = {__fmaf_rn(sc, w.im, acc.re), __fmaf_rn(-sc, w.re, acc.im)};
 }
 
+// the same on two lanes (two output sites) with the packed FP32x2 FMA
+template <int F> LQCD_DEV void add_f(Cx<float2> &acc, float2 sc, Cx<float2> w) {
+  const float2 ms = neg2(sc);
+  if (F == F_P1) acc = {__ffma2_rn(sc, w.re, acc.re), __ffma2_rn(sc, w.im, acc.im)};
+  else if (F == F_M1) acc = {__ffma2_rn(ms, w.re, acc.re), __ffma2_rn(ms, w.im, acc.im)};
+  else if (F == F_PI) acc = {__ffma2_rn(ms, w.im, acc.re), __ffma2_rn(sc, w.re, acc.im)};
+  else acc = {__ffma2_rn(sc, w.im, acc.re), __ffma2_rn(ms, w.re, acc.im)};
+}
+
 // acc += sc [v; -s B^+ v]: accumulate<MU, S> with the neighbour's 16-bit
-// storage scale (and the boundary sign) applied in the accumulation FMAs
-template <int MU, int S>
-LQCD_DEV void accumulate_scaled(const Cx<float> v[6], float sc, Cx<float> acc[12]) {
+// storage scale (and the boundary sign) applied in the accumulation FMAs.
+// With sc = +-1 it is accumulate<MU, S> of (+-v) with the same roundings.
+template <int MU, int S, class RV, class RS>
+LQCD_DEV void accumulate_scaled(const Cx<RV> v[6], RS sc, Cx<RV> acc[12]) {
 #pragma unroll
   for (int c = 0; c < 3; c++) {
-    const Cx<float> v0 = v[c], v1 = v[3 + c];
+    const Cx<RV> v0 = v[c], v1 = v[3 + c];
     add_f<F_P1>(acc[c], sc, v0);
     add_f<F_P1>(acc[3 + c], sc, v1);
     if (MU == 0) {
@@ -396,6 +406,117 @@ __global__ void __launch_bounds__(256) hop_kernel(HopArgs A) {
 }
 
 // ---------------------------------------------------------------------------
+// Two output sites per thread in packed FP32x2 arithmetic (F32 and 16-bit
+// formats): lane x of every float2 belongs to site cb, lane y to site cb + 32,
+// so a warp covers 64 consecutive sites as two groups of 32 and writes the
+// same per-warp partials as the one-site kernels.  Every packed operation
+// rounds as its scalar counterpart, and the F32 format accumulates through
+// the scaled form with scale +-1 (the same roundings as negate + add), so the
+// results are bitwise those of hop_site.  Half the FP32 instructions per site
+// for the same loads.
+// ---------------------------------------------------------------------------
+template <int PREC, int RECON>
+LQCD_DEV void load_link2(const GaugeView &U, int p, int mu, int cbA, int cbB, Cx<float2> u[9]) {
+  Cx<float> a[9], b[9];
+  LinkIO<PREC, RECON>::load(U, p, mu, cbA, a);
+  LinkIO<PREC, RECON>::load(U, p, mu, cbB, b);
+#pragma unroll
+  for (int k = 0; k < (RECON == 18 ? 9 : 6); k++) u[k] = cpair(a[k], b[k]);
+}
+template <int PREC>
+LQCD_DEV float2 load_nb2(const SpinorView &vin, int jA, int jB, Cx<float2> ps[12]) {
+  Cx<float> a[12], b[12];
+  const float sa = load_nb<PREC>(vin, jA, a), sb = load_nb<PREC>(vin, jB, b);
+#pragma unroll
+  for (int k = 0; k < 12; k++) ps[k] = cpair(a[k], b[k]);
+  return make_float2(sa, sb);
+}
+
+template <int PREC, int RECON, int MU, int S>
+LQCD_DEV void hop_dir2(const HopArgs &A, const Site &sA, const Site &sB, int p, int cbA, int cbB,
+                       const SpinorView &vin, Cx<float2> acc[12]) {
+#pragma unroll
+  for (int dir = 0; dir < 2; dir++) {
+    const int d = dir == 0 ? +1 : -1;
+    const int jA = neighbour_cb(A.g, sA, MU, d), jB = neighbour_cb(A.g, sB, MU, d);
+    Cx<float2> ps[12], h[6], v[6], u[9];
+    float2 sc = load_nb2<PREC>(vin, jA, jB, ps);
+    if (dir == 0) load_link2<PREC, RECON>(A.U, p, MU, cbA, cbB, u);
+    else load_link2<PREC, RECON>(A.U, p ^ 1, MU, jA, jB, u);
+    const int tb = dir == 0 ? A.g.L[3] - 1 : 0;
+    if (MU == 3 && A.g.antiper) {
+      if (sA.t == tb) sc.x = -sc.x;
+      if (sB.t == tb) sc.y = -sc.y;
+    }
+    if (dir == 0) {
+      project<MU, S>(ps, h);
+      if (RECON == 12) reconstruct_row2(u);
+      mul_link(u, h, v);
+      accumulate_scaled<MU, S>(v, sc, acc);
+    } else {
+      project<MU, -S>(ps, h);
+      if (RECON == 12) reconstruct_row2(u);
+      mul_link_dag(u, h, v);
+      accumulate_scaled<MU, -S>(v, sc, acc);
+    }
+  }
+}
+
+template <int PREC, int RECON, bool DAG, bool REDUCE>
+__global__ void __launch_bounds__(64) hop_pair2_kernel(HopArgs A) {
+  if (A.halt && *(volatile int *)A.halt) return;
+  const int rhs = blockIdx.z;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int p = A.out_parity;
+  const int stride = gridDim.x * 128;
+  for (int base = blockIdx.x * 128; base < A.g.Vh; base += stride) {
+    const int cbA = base + 64 * w + lane, cbB = cbA + 32;
+    const bool okA = cbA < A.g.Vh && rhs < A.nrhs, okB = cbB < A.g.Vh && rhs < A.nrhs;
+    // lanes past the end recompute a valid site and store nothing
+    const int cA = okA ? cbA : A.g.Vh - 1, cB = okB ? cbB : A.g.Vh - 1;
+    const int r = rhs < A.nrhs ? rhs : A.nrhs - 1;
+    const Site sA = site_of(A.g, p, cA), sB = site_of(A.g, p, cB);
+    SpinorView vin{A.in + r * A.in_rs, A.in_scale ? A.in_scale + r * A.in_srs : nullptr, A.g.Vh};
+    Cx<float2> acc[12];
+#pragma unroll
+    for (int k = 0; k < 12; k++) acc[k] = czero<float2>();
+    constexpr int S = DAG ? -1 : 1;
+    hop_dir2<PREC, RECON, 0, S>(A, sA, sB, p, cA, cB, vin, acc);
+    hop_dir2<PREC, RECON, 1, S>(A, sA, sB, p, cA, cB, vin, acc);
+    hop_dir2<PREC, RECON, 2, S>(A, sA, sB, p, cA, cB, vin, acc);
+    hop_dir2<PREC, RECON, 3, S>(A, sA, sB, p, cA, cB, vin, acc);
+    double nA = 0.0, nB = 0.0;
+    {
+      Cx<float> a[12];
+#pragma unroll
+      for (int k = 0; k < 12; k++) a[k] = lane_x(acc[k]);
+      if (okA) nA = hop_epilogue<PREC, REDUCE>(A, cbA, rhs, a);
+    }
+    {
+      Cx<float> b[12];
+#pragma unroll
+      for (int k = 0; k < 12; k++) b[k] = lane_y(acc[k]);
+      if (okB) nB = hop_epilogue<PREC, REDUCE>(A, cbB, rhs, b);
+    }
+    if (REDUCE) {
+      hop_warp_partial(A, cbA, rhs, nA);
+      hop_warp_partial(A, cbB, rhs, nB);
+    }
+  }
+}
+
+template <int PREC, int RECON>
+inline void launch_pair2(const HopArgs &A, dim3 grid, dim3 block, bool dag, bool red, cudaStream_t st) {
+  if (dag) {
+    if (red) hop_pair2_kernel<PREC, RECON, true, true><<<grid, block, 0, st>>>(A);
+    else hop_pair2_kernel<PREC, RECON, true, false><<<grid, block, 0, st>>>(A);
+  } else {
+    if (red) hop_pair2_kernel<PREC, RECON, false, true><<<grid, block, 0, st>>>(A);
+    else hop_pair2_kernel<PREC, RECON, false, false><<<grid, block, 0, st>>>(A);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Float-float hop with two threads per output site.  Thread k (lane parity)
 // owns upper spin component k: it projects only h_k, multiplies it by the
 // link one row (forward) or column (backward) at a time, and accumulates the
@@ -603,10 +724,11 @@ inline void launch_t(const HopArgs &A, dim3 grid, dim3 block, bool dag, bool red
 void hop_launch_f64(const HopArgs &A, int recon, dim3 grid, dim3 block, bool dag, bool red, cudaStream_t st);
 void hop_launch_df64(const HopArgs &A, int recon, bool pair, dim3 grid, dim3 block, bool dag, bool red,
                      cudaStream_t st);
+// rt: right-hand sides per thread (1, 2, 4); two: two sites per thread (packed FP32x2)
 void hop_launch_f32(const HopArgs &A, int recon, dim3 grid, dim3 block, bool dag, bool red, bool lf, int rt,
-                    cudaStream_t st);
+                    bool two, cudaStream_t st);
 void hop_launch_h16(const HopArgs &A, int prec, dim3 grid, dim3 block, bool dag, bool red, bool lf, int rt,
-                    cudaStream_t st);
+                    bool two, cudaStream_t st);
 void hop_batched_f64(int recon, bool dag, bool red, const HopArgs *d, const int2 *tl, int ntiles, int grid,
                      const int *halt, cudaStream_t st);
 void hop_batched_df64(int recon, bool dag, bool red, const HopArgs *d, const int2 *tl, int ntiles, int grid,
