@@ -48,79 +48,89 @@ struct RhsState {
 };
 struct SolverHdr {
   int halt, all_done, need_rel, nonfinite;
-  int iters, nrhs, mixed, pad;
+  int iters, nrhs, mixed;
+  unsigned ticket;  // blocks of the current finalize that have finished
 };
 // layout in device memory: SolverHdr, then RhsState[nrhs]
 LQCD_DEV RhsState *rhs_state(SolverHdr *h) { return (RhsState *)(h + 1); }
 
 enum { FIN_ALPHA = 0, FIN_SS = 1, FIN_BETA = 2, FIN_INIT_ZZ = 3, FIN_STORE = 4 };
 
-// One block: finishes the reductions of all nrhs right-hand sides and applies
-// the CG scalar step `op`.  FIN_STORE only writes the plain sums to out[r]
-// and does not touch the solver state.
+// One block per right-hand side finishes its reduction and applies the CG
+// scalar step `op`; the last block to finish (ticket) sets the flags over all
+// right-hand sides.  FIN_STORE only writes the plain sums to out[r] and does
+// not touch the solver state.
 __global__ void __launch_bounds__(FIN_THREADS) finalize_kernel(SolverHdr *h, int nrhs, const double *partials,
                                                               int nb, int op, double *out) {
   __shared__ double sh[33];
+  __shared__ int last;
+  const int r = blockIdx.x;  // one block per right-hand side
+  const double v = (op == FIN_STORE || op == FIN_INIT_ZZ || !*(volatile int *)&h->halt)
+                       ? block_sum_fixed(partials + (size_t)r * nb, nb, sh)
+                       : 0.0;
   if (op == FIN_STORE) {
-    for (int r = 0; r < nrhs; r++) {
-      double v = block_sum_fixed(partials + (size_t)r * nb, nb, sh);
-      if (threadIdx.x == 0) out[r] = v;
-    }
+    if (threadIdx.x == 0) out[r] = v;
     return;
   }
   if (op != FIN_INIT_ZZ && *(volatile int *)&h->halt) return;
   RhsState *rs = rhs_state(h);
-  int all_done = 1, any_rel = 0, bad = 0, maxit = 0;
-  for (int r = 0; r < nrhs; r++) {
-    double v = block_sum_fixed(partials + (size_t)r * nb, nb, sh);
-    if (threadIdx.x == 0) {
-      RhsState &R = rs[r];
-      if (!isfinite(v)) bad = 1;
-      switch (op) {
-        case FIN_ALPHA:
-          R.qq = v;
-          if (R.done) R.alpha = 0.0;
-          else if (v > 0.0) R.alpha = R.zz / v;
-          else { R.alpha = 0.0; if (R.zz > 0.0) bad = 1; }
-          break;
-        case FIN_SS:
-          R.ss = v;
-          if (!R.done) {
-            R.iters += 1;
-            if (v <= R.stop2) R.done = 1;
-            if (h->mixed && !R.done) {
-              if (v > R.rmax2) R.rmax2 = v;
-              if (v < R.rel2 * R.rmax2) R.need_rel = 1;
-            }
+  if (threadIdx.x == 0) {
+    RhsState &R = rs[r];
+    int bad = !isfinite(v);
+    switch (op) {
+      case FIN_ALPHA:
+        R.qq = v;
+        if (R.done) R.alpha = 0.0;
+        else if (v > 0.0) R.alpha = R.zz / v;
+        else { R.alpha = 0.0; if (R.zz > 0.0) bad = 1; }
+        break;
+      case FIN_SS:
+        R.ss = v;
+        if (!R.done) {
+          R.iters += 1;
+          if (v <= R.stop2) R.done = 1;
+          if (h->mixed && !R.done) {
+            if (v > R.rmax2) R.rmax2 = v;
+            if (v < R.rel2 * R.rmax2) R.need_rel = 1;
           }
-          break;
-        case FIN_BETA:
-          if (R.done) R.beta = 0.0;
-          else R.beta = R.zz > 0.0 ? v / R.zz : 0.0;
-          R.zz = v;
-          break;
-        default:  // FIN_INIT_ZZ
-          R.zz = v;
-          break;
-      }
+        }
+        break;
+      case FIN_BETA:
+        if (R.done) R.beta = 0.0;
+        else R.beta = R.zz > 0.0 ? v / R.zz : 0.0;
+        R.zz = v;
+        break;
+      default:  // FIN_INIT_ZZ
+        R.zz = v;
+        break;
+    }
+    if (bad) atomicOr(&h->nonfinite, 1);
+    __threadfence();
+    last = atomicAdd(&h->ticket, 1u) == (unsigned)(nrhs - 1);
+  }
+  __syncthreads();
+  // the last block to finish sets the flags over all right-hand sides
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    int all_done = 1, any_rel = 0, maxit = 0;
+    for (int k = 0; k < nrhs; k++) {
+      const volatile RhsState &R = rs[k];
       all_done &= R.done;
       any_rel |= R.need_rel;
       if (R.iters > maxit) maxit = R.iters;
     }
-  }
-  if (threadIdx.x == 0) {
     h->iters = maxit;
     h->all_done = all_done;
     h->need_rel = any_rel;
-    if (bad) h->nonfinite = 1;
     if (op == FIN_SS && (all_done || any_rel)) h->halt = 1;
-    if (bad) h->halt = 1;
+    if (*(volatile int *)&h->nonfinite) h->halt = 1;
+    h->ticket = 0u;
   }
 }
 
 
 static void launch_finalize(lqcd_ctx *ctx, SolverHdr *h, int nrhs, int nb, int op, double *out) {
-  finalize_kernel<<<1, FIN_THREADS, 0, ctx->stream>>>(h, nrhs, ctx->partials, nb, op, out);
+  finalize_kernel<<<nrhs, FIN_THREADS, 0, ctx->stream>>>(h, nrhs, ctx->partials, nb, op, out);
   count_launch(ctx, 8.0 * nb * nrhs);
 }
 
@@ -272,6 +282,7 @@ __global__ void state_init_kernel(SolverHdr *h, int nrhs, int mixed, const doubl
     h->iters = 0;
     h->nrhs = nrhs;
     h->mixed = mixed;
+    h->ticket = 0u;
   }
   if (r < nrhs) {
     RhsState &R = rhs_state(h)[r];
