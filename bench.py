@@ -687,6 +687,23 @@ def run_config(args):
             for pn in ("f64", "df64"):
                 gf[f"{name}_{pn}"] = 1e3 * _timed(torch, lambda: lqcd.lqcd_gauge_force(
                     ctx, G, beta, F, want_action=False, c1=cc, prec=PREC_NAMES[pn]), 5)[0]
+        # the fermion force with a cached solution X: the adjoint kernel plus the
+        # operators that build Y = Mhat X, W_o and Z_o (no CG); the paper counts
+        # 4736 B and 1748 flop per site and direction for its force kernel
+        Vc = int(np.prod(Lc))
+        full_d, _ = lqcd.alloc_field(Lc, lqcd.LQCD_FULL, lqcd.LQCD_F64)  # Gaussian on the even sites
+        lqcd.lqcd_spinor_gaussian(ctx, Lc, lqcd.field(full_d, lqcd.LQCD_LAYOUT_EO), lqcd.LQCD_EVEN, 7, 0)
+        n_half, _ = lqcd.field_bytes(Lc, lqcd.LQCD_EVEN, lqcd.LQCD_F64)
+        phi_d = full_d[: n_half // 8]  # the even half of the EO field
+        x_d = torch.zeros_like(phi_d)
+        fphi = lqcd.field(phi_d, lqcd.LQCD_LAYOUT_EO)
+        xc = lqcd.field(x_d, lqcd.LQCD_LAYOUT_EO)
+        lqcd.lqcd_fermion_force(ctx, G, fphi, F, kappa, mu, cg, X_cache=xc)
+        tff, _ = _timed(torch, lambda: lqcd.lqcd_fermion_force(ctx, G, fphi, F, kappa, mu, cg, X_cache=xc), 5)
+        tpl, _ = _timed(torch, lambda: lqcd.lqcd_plaquette(ctx, G), 5)
+        misc = {"fermion_force_ms": 1e3 * tff,
+                "fermion_force_GBs_paper_count": 4 * Vc * 4736 / tff / 1e9,
+                "plaquette_ms": 1e3 * tpl}
         config_line("HMC setup C", None,
                     {"s_per_trajectory": statistics.median(secs),
                      "dH": [s["dH"] for s in trajs], "accepted": [s["accepted"] for s in trajs],
@@ -697,7 +714,7 @@ def run_config(args):
                      "heatbath_s": thb, "thermalisation_trajectories": len(therm),
                      "thermalisation_dH": [s["dH"] for s in therm],
                      "thermalisation_plaquette": [s["plaquette"] for s in therm],
-                     "gauge_force_ms": gf, "force_prec": args.force_prec},
+                     "gauge_force_ms": gf, "force_prec": args.force_prec, "kernels": misc},
                     {"workload": "24^3x8, tlSym beta=3.9, kappa=0.160856, a mu=0.1, 2MN 10 fermion x 10 "
                                  f"gauge steps, tau=1, {args.force_prec} gauge force, F32-inner/DF64 CG to "
                                  "1e-10 per force; start: "
@@ -712,17 +729,22 @@ def run_config(args):
                                        recon=18)
             for s_ in range(5):
                 lqcd.lqcd_heatbath_sweep(ctx, G, 5.7, 9, s_)
-            th, _ = _timed(torch, lambda: lqcd.lqcd_heatbath_sweep(ctx, G, 5.7, 9, 100), 5)
-            tho, _ = _timed(torch, lambda: lqcd.lqcd_heatbath_sweep(ctx, G, 5.7, 9, 101, n_or=4), 5)
-            tor = (tho - th) / 4
-            res["x".join(map(str, Lc))] = {
-                "heatbath_ms": 1e3 * th, "overrelax_ms": 1e3 * tor,
-                "heatbath_GFLOPs": 4 * V * 3912 / th / 1e9, "overrelax_GFLOPs": 4 * V * 3846 / tor / 1e9,
-                "heatbath_GBs_paper_count": 4 * V * 2880 / th / 1e9,
-                "plaquette": lqcd.lqcd_plaquette(ctx, G)}
+            row = {}
+            for pn in ("f64", "f32"):
+                pr = PREC_NAMES[pn]
+                th, _ = _timed(torch, lambda: lqcd.lqcd_heatbath_sweep(ctx, G, 5.7, 9, 100, prec=pr), 5)
+                tho, _ = _timed(torch, lambda: lqcd.lqcd_heatbath_sweep(ctx, G, 5.7, 9, 101, n_or=4, prec=pr), 5)
+                tor = (tho - th) / 4
+                row[pn] = {"heatbath_ms": 1e3 * th, "overrelax_ms": 1e3 * tor,
+                           "heatbath_GFLOPs": 4 * V * 3912 / th / 1e9,
+                           "overrelax_GFLOPs": 4 * V * 3846 / tor / 1e9,
+                           "heatbath_GBs_paper_count": 4 * V * 2880 / th / 1e9}
+            row["plaquette"] = lqcd.lqcd_plaquette(ctx, G)
+            res["x".join(map(str, Lc))] = row
             G.free()
         config_line("heatbath", None, {"hb": res},
-                    {"workload": "Cabibbo-Marinari heatbath and overrelaxation sweeps, FP64, beta=5.7, "
+                    {"workload": "Cabibbo-Marinari heatbath and overrelaxation sweeps, FP64 and FP32 "
+                                 "(FP32 times include the copy back into the FP64 field), beta=5.7, "
                                  "GFLOP/s with the paper's 3912 / 3846 flop per link"})
     elif c == "sweep":
         res = {}

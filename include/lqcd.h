@@ -144,6 +144,24 @@ typedef struct {
 int lqcd_get_counters(const lqcd_ctx *ctx, lqcd_counters *out);
 int lqcd_reset_counters(lqcd_ctx *ctx);
 
+/* Device memory.  By default the library allocates its workspace and gauge
+ * fields with cudaMallocAsync / cudaFreeAsync on the context's stream.
+ * lqcd_set_allocator routes every later device allocation of the context
+ * (workspace, solver vectors, gauge fields imported afterwards and their
+ * derived copies) through alloc(bytes, user) and free(ptr, user) instead --
+ * e.g. PyTorch's caching allocator -- so one pool backs everything.  alloc
+ * must return memory aligned to at least 256 bytes that may be used on the
+ * context's stream, or NULL (the call then fails with LQCD_ERR_OOM).  Call it
+ * before importing gauge fields: it releases the context's current workspace
+ * (synchronising the stream) and reallocates it through the new pair.  A
+ * gauge field keeps the pair it was imported with and is freed through it.
+ * Passing NULL for both restores the default.  Mixing one non-NULL function
+ * with a NULL one is LQCD_ERR_INVALID.  The library never frees memory it did
+ * not allocate. */
+typedef void *(*lqcd_alloc_fn)(size_t bytes, void *user);
+typedef void (*lqcd_free_fn)(void *ptr, void *user);
+int lqcd_set_allocator(lqcd_ctx *ctx, lqcd_alloc_fn alloc, lqcd_free_fn free_fn, void *user);
+
 /* Launch-shape autotuner (on by default).  The first launch of each kernel
  * configuration (kernel, precision, link format, variant, lattice extents,
  * number of right-hand sides, GPU) made outside a stream capture times every
@@ -316,9 +334,14 @@ int lqcd_plaquette(lqcd_ctx *ctx, const lqcd_gauge *U, double *plaq_out);
  * draw).  Then n_or overrelaxation passes (0 <= n_or <= 64, else
  * LQCD_ERR_INVALID): the same checkerboard order, each SU(2) subgroup
  * replaced by its reflection v = (w^+/k)^2 (microcanonical: the action is
- * unchanged).  The links are reunitarised in FP64 afterwards.  Asynchronous. */
+ * unchanged).  prec = LQCD_F64 updates the FP64 field in place (the SU(2)
+ * left multiplications keep it unitary to rounding); prec = LQCD_F32 runs
+ * the same sweep in single precision on the field's FP32 copy and writes the
+ * result back into the FP64 field, reunitarised in FP64 (Sec. 5.1 measures
+ * the single-precision kernels).  Other prec: LQCD_ERR_INVALID.
+ * Asynchronous. */
 int lqcd_heatbath_sweep(lqcd_ctx *ctx, lqcd_gauge *U, double beta, uint64_t seed,
-                        uint64_t sweep_idx, int n_or);
+                        uint64_t sweep_idx, int n_or, int prec);
 
 /* Gaussian momenta p^a ~ N(0,1) into P (device float64 [4][V][8]) from the
  * Philox stream (site, traj, mu | 1<<8, k). Asynchronous. */

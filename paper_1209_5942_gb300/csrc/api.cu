@@ -59,9 +59,19 @@ size_t spinor_scale_half_bytes(int prec, int Vh) {
   return (prec == LQCD_BF16S || prec == LQCD_F16S) ? sizeof(float) * (size_t)Vh : 0;
 }
 
-lqcd_status dalloc(lqcd_ctx *ctx, void **p, size_t bytes) {
+lqcd_status raw_alloc(lqcd_ctx *ctx, const DevAllocator &A, void **p, size_t bytes) {
   *p = nullptr;
   if (bytes == 0) return LQCD_OK;
+  if (A.alloc) {
+    *p = A.alloc(bytes, A.user);
+    if (!*p) return fail(ctx, LQCD_ERR_OOM, "caller allocator returned NULL for %zu bytes", bytes);
+    if ((uintptr_t)*p % 256 != 0) {
+      A.free(*p, A.user);
+      *p = nullptr;
+      return fail(ctx, LQCD_ERR_INVALID, "caller allocator returned memory not aligned to 256 bytes");
+    }
+    return LQCD_OK;
+  }
   cudaError_t e = cudaMallocAsync(p, bytes, ctx->stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -70,23 +80,24 @@ lqcd_status dalloc(lqcd_ctx *ctx, void **p, size_t bytes) {
   }
   return LQCD_OK;
 }
-void dfree(lqcd_ctx *ctx, void *p) {
-  if (p) cudaFreeAsync(p, ctx->stream);
+void raw_free(lqcd_ctx *ctx, const DevAllocator &A, void *p) {
+  if (!p) return;
+  if (A.free) A.free(p, A.user);
+  else cudaFreeAsync(p, ctx->stream);
 }
+lqcd_status dalloc(lqcd_ctx *ctx, void **p, size_t bytes) { return raw_alloc(ctx, ctx->A, p, bytes); }
+void dfree(lqcd_ctx *ctx, void *p) { raw_free(ctx, ctx->A, p); }
 
 lqcd_status ensure_partials(lqcd_ctx *ctx, size_t doubles) {
   if (ctx->partials_cap >= doubles) return LQCD_OK;
   if (ctx->partials) {
     cudaStreamSynchronize(ctx->stream);
-    cudaFree(ctx->partials);
+    dfree(ctx, ctx->partials);
   }
   ctx->partials = nullptr;
   ctx->partials_cap = 0;
   size_t n = doubles < 4096 ? 4096 : doubles;
-  if (cudaMalloc(&ctx->partials, n * sizeof(double)) != cudaSuccess) {
-    cudaGetLastError();
-    return fail(ctx, LQCD_ERR_OOM, "partials allocation failed");
-  }
+  LQCD_TRY(dalloc(ctx, (void **)&ctx->partials, n * sizeof(double)));
   ctx->partials_cap = n;
   return LQCD_OK;
 }
@@ -205,15 +216,38 @@ extern "C" int lqcd_create(lqcd_ctx **out, int device, void *stream) {
   return LQCD_OK;
 }
 
+// releases the context's device workspace (through its current allocator)
+static void release_workspace(lqcd_ctx *ctx) {
+  cudaStreamSynchronize(ctx->stream);
+  dfree(ctx, ctx->partials);
+  dfree(ctx, ctx->solver_state);
+  dfree(ctx, ctx->staples);
+  cudaStreamSynchronize(ctx->stream);
+  ctx->partials = nullptr;
+  ctx->partials_cap = 0;
+  ctx->solver_state = nullptr;
+  ctx->solver_state_cap = 0;
+  ctx->staples = nullptr;
+  ctx->staple_cap = 0;
+}
+
 extern "C" int lqcd_destroy(lqcd_ctx *ctx) {
   if (!ctx) return LQCD_ERR_INVALID;
-  cudaStreamSynchronize(ctx->stream);
-  if (ctx->partials) cudaFree(ctx->partials);
+  release_workspace(ctx);
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
-  if (ctx->solver_state) cudaFree(ctx->solver_state);
-  if (ctx->staples) cudaFree(ctx->staples);
   delete ctx;
   return LQCD_OK;
+}
+
+extern "C" int lqcd_set_allocator(lqcd_ctx *ctx, lqcd_alloc_fn alloc, lqcd_free_fn free_fn, void *user) {
+  if (!ctx) return LQCD_ERR_INVALID;
+  if ((alloc == nullptr) != (free_fn == nullptr))
+    return fail(ctx, LQCD_ERR_INVALID, "alloc and free must both be set or both be NULL");
+  release_workspace(ctx);
+  ctx->A.alloc = alloc;
+  ctx->A.free = free_fn;
+  ctx->A.user = user;
+  return ensure_partials(ctx, 1 << 16);
 }
 
 extern "C" int lqcd_set_stream(lqcd_ctx *ctx, void *stream) {
@@ -269,8 +303,8 @@ extern "C" int lqcd_gauge_import(lqcd_ctx *ctx, const void *U_lexi, const lqcd_g
   U->g = make_geom(*geom);
   U->recon = recon;
   size_t bytes = (size_t)2 * 4 * 9 * U->g.Vh * 16;
-  if (cudaMalloc(&U->master, bytes) != cudaSuccess) {
-    cudaGetLastError();
+  U->A = ctx->A;
+  if (raw_alloc(ctx, U->A, &U->master, bytes) != LQCD_OK) {
     delete U;
     return fail(ctx, LQCD_ERR_OOM, "gauge allocation of %zu bytes failed", bytes);
   }
@@ -283,7 +317,8 @@ extern "C" int lqcd_gauge_import(lqcd_ctx *ctx, const void *U_lexi, const lqcd_g
   }
   if (s == LQCD_OK) s = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "gauge import");
   if (s != LQCD_OK) {
-    cudaFree(U->master);
+    cudaStreamSynchronize(ctx->stream);
+    raw_free(ctx, U->A, U->master);
     delete U;
     return s;
   }
@@ -299,9 +334,11 @@ extern "C" int lqcd_gauge_export(lqcd_ctx *ctx, const lqcd_gauge *U, void *U_lex
 
 extern "C" int lqcd_gauge_free(lqcd_ctx *ctx, lqcd_gauge *U) {
   if (!U) return ctx ? fail(ctx, LQCD_ERR_INVALID, "U is NULL") : LQCD_ERR_INVALID;
-  if (ctx) cudaStreamSynchronize(ctx->stream);
-  cudaFree(U->master);
-  for (auto &c : U->copies) cudaFree(c.ptr);
+  if (!ctx) return LQCD_ERR_INVALID;
+  cudaStreamSynchronize(ctx->stream);
+  raw_free(ctx, U->A, U->master);
+  for (auto &c : U->copies) raw_free(ctx, U->A, c.ptr);
+  cudaStreamSynchronize(ctx->stream);
   delete U;
   return LQCD_OK;
 }

@@ -502,13 +502,13 @@ struct CgWork {
 static lqcd_status ensure_state(lqcd_ctx *ctx, int nrhs, SolverHdr **h) {
   size_t need = sizeof(SolverHdr) + sizeof(RhsState) * nrhs + sizeof(double) * 4 * nrhs;
   if (ctx->solver_state_cap < need) {
-    if (ctx->solver_state) cudaFree(ctx->solver_state);
+    if (ctx->solver_state) {
+      cudaStreamSynchronize(ctx->stream);
+      dfree(ctx, ctx->solver_state);
+    }
     ctx->solver_state = nullptr;
     ctx->solver_state_cap = 0;
-    if (cudaMalloc(&ctx->solver_state, need) != cudaSuccess) {
-      cudaGetLastError();
-      return fail(ctx, LQCD_ERR_OOM, "solver state allocation failed");
-    }
+    LQCD_TRY(dalloc(ctx, &ctx->solver_state, need));
     ctx->solver_state_cap = need;
   }
   *h = (SolverHdr *)ctx->solver_state;

@@ -666,6 +666,183 @@ __global__ void __launch_bounds__(128) heatbath_kernel(double2 *U, Geom g, int m
 }
 
 // ---------------------------------------------------------------------------
+// The heatbath and overrelaxation in single precision (the paper's main
+// heatbath measurements are FP32): the same update, counters and random
+// numbers, on the FP32 copy of the links (18 reals), with FP32 staples, SU(2)
+// projection and sampling.  The caller writes the copy back into the FP64
+// field and reunitarises it in FP64.
+// ---------------------------------------------------------------------------
+struct M3s {
+  Cx<float> m[9];
+};
+LQCD_DEV M3s smul(const M3s &a, const M3s &b) {
+  M3s r;
+#pragma unroll
+  for (int i = 0; i < 3; i++)
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+      Cx<float> t = a.m[3 * i] * b.m[j];
+      t = cmadd(a.m[3 * i + 1], b.m[3 + j], t);
+      t = cmadd(a.m[3 * i + 2], b.m[6 + j], t);
+      r.m[3 * i + j] = t;
+    }
+  return r;
+}
+LQCD_DEV M3s sdag(const M3s &u) {
+  M3s d;
+#pragma unroll
+  for (int i = 0; i < 3; i++)
+#pragma unroll
+    for (int j = 0; j < 3; j++) d.m[3 * i + j] = conj(u.m[3 * j + i]);
+  return d;
+}
+LQCD_DEV M3s load_link_s(const GaugeView &Uf, const Pos &s, int mu) {
+  M3s u;
+  LinkIO<LQCD_F32, 18>::load(Uf, s.p, mu, s.cb, u.m);
+  return u;
+}
+LQCD_DEV void store_link_s(const GaugeView &Uf, const Pos &s, int mu, const M3s &u) {
+  char *base = (char *)Uf.ptr + s.p * Uf.parity_stride + mu * Uf.mu_stride;
+  float4 *b = (float4 *)base;
+#pragma unroll
+  for (int k = 0; k < 4; k++)
+    b[(size_t)k * Uf.Vh + s.cb] = make_float4(u.m[2 * k].re, u.m[2 * k].im, u.m[2 * k + 1].re, u.m[2 * k + 1].im);
+  ((float2 *)(base + (size_t)4 * Uf.Vh * 16))[s.cb] = make_float2(u.m[8].re, u.m[8].im);
+}
+// staple sum as staple(), in FP32
+LQCD_DEV M3s staple_s(const GaugeView &Uf, const Geom &g, const int c[4], int mu) {
+  M3s A;
+#pragma unroll
+  for (int k = 0; k < 9; k++) A.m[k] = czero<float>();
+  int cpm[4] = {c[0], c[1], c[2], c[3]};
+  coords_shift(g, cpm, mu, +1);
+  for (int nu = 0; nu < 4; nu++) {
+    if (nu == mu) continue;
+    int cpn[4] = {c[0], c[1], c[2], c[3]}, cmn[4] = {c[0], c[1], c[2], c[3]};
+    int cpmmn[4] = {cpm[0], cpm[1], cpm[2], cpm[3]};
+    coords_shift(g, cpn, nu, +1);
+    coords_shift(g, cmn, nu, -1);
+    coords_shift(g, cpmmn, nu, -1);
+    // upper: U_nu(x+mu) U_mu(x+nu)^+ U_nu(x)^+
+    M3s t = smul(smul(load_link_s(Uf, at(g, cpm), nu), sdag(load_link_s(Uf, at(g, cpn), mu))),
+                 sdag(load_link_s(Uf, at(g, c), nu)));
+#pragma unroll
+    for (int k = 0; k < 9; k++) A.m[k] = A.m[k] + t.m[k];
+    // lower: U_nu(x+mu-nu)^+ U_mu(x-nu)^+ U_nu(x-nu)
+    t = smul(sdag(smul(load_link_s(Uf, at(g, cmn), mu), load_link_s(Uf, at(g, cpmmn), nu))),
+             load_link_s(Uf, at(g, cmn), nu));
+#pragma unroll
+    for (int k = 0; k < 9; k++) A.m[k] = A.m[k] + t.m[k];
+  }
+  return A;
+}
+
+LQCD_DEV bool sample_y0_f(float b, uint32_t c0, uint32_t c1, uint32_t c2, uint64_t seed, float *y0) {
+  for (int n = 0; n < HB_MAX_ATTEMPTS; n++) {
+    double ud[2];
+    uniform2(c0, c1, c2, (uint32_t)(2 * n), seed, ud);
+    const float u0 = (float)ud[0], u1 = (float)ud[1];
+    if (b < (float)HB_B_SWITCH) {
+      float y = b > 1e-30f ? 1.0f + log1pf(expm1f(-2.0f * b) * (1.0f - u0)) / b : 2.0f * u0 - 1.0f;
+      if (u1 * u1 <= 1.0f - y * y) {
+        *y0 = y;
+        return true;
+      }
+      continue;
+    }
+    double vd[2];
+    uniform2(c0, c1, c2, (uint32_t)(2 * n + 1), seed, vd);
+    const float cs = cospif(2.0f * u1);
+    const float lam2 = -(logf(u0) + cs * cs * logf((float)vd[0])) / (2.0f * b);
+    if ((float)vd[1] * (float)vd[1] <= 1.0f - lam2) {
+      *y0 = 1.0f - 2.0f * lam2;
+      return true;
+    }
+  }
+  return false;
+}
+
+__global__ void __launch_bounds__(128) heatbath_f32_kernel(GaugeView Uf, Geom g, int mu, int par, float beta,
+                                                           uint64_t seed, uint32_t sweep, int overrelax,
+                                                           unsigned int *fail_count) {
+  int cb = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cb >= g.Vh) return;
+  Site st = site_of(g, par, cb);
+  int c[4] = {st.x, st.y, st.z, st.t};
+  Pos s = at(g, c);
+  const M3s A = staple_s(Uf, g, c, mu);
+  M3s u = load_link_s(Uf, s, mu);
+  const int SG[3][2] = {{0, 1}, {1, 2}, {0, 2}};
+  unsigned fails = 0;
+  for (int sg = 0; sg < 3; sg++) {
+    const int i = SG[sg][0], j = SG[sg][1];
+    const M3s W = smul(u, A);
+    const Cx<float> wa = W.m[3 * i + i], wb = W.m[3 * i + j], wc = W.m[3 * j + i], wd = W.m[3 * j + j];
+    const float q0 = 0.5f * (wa.re + wd.re), q3 = 0.5f * (wa.im - wd.im);
+    const float q1 = 0.5f * (wb.im + wc.im), q2 = 0.5f * (wb.re - wc.re);
+    const float k = sqrtf(q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3);
+    if (!(k > 1e-30f)) {
+      fails++;
+      continue;
+    }
+    const float h0 = q0 / k, h1 = q1 / k, h2 = q2 / k, h3 = q3 / k;
+    const Cx<float> whd[2][2] = {{{h0, -h3}, {-h2, -h1}}, {{h2, -h1}, {h0, h3}}};
+    Cx<float> v[2][2];
+    if (overrelax) {
+#pragma unroll
+      for (int r = 0; r < 2; r++)
+#pragma unroll
+        for (int q = 0; q < 2; q++) v[r][q] = whd[r][0] * whd[0][q] + whd[r][1] * whd[1][q];
+    } else {
+      const float b = 2.0f * beta * k / 3.0f;
+      const uint32_t c2 = (uint32_t)mu | ((uint32_t)sg << 2) | (TAG_HB << 8);
+      float y0;
+      if (!sample_y0_f(b, (uint32_t)s.lexi, sweep, c2, seed, &y0)) {
+        fails++;
+        continue;
+      }
+      double ud[2];
+      uniform2((uint32_t)s.lexi, sweep, (uint32_t)mu | ((uint32_t)sg << 2) | (TAG_DIR << 8), 0u, seed, ud);
+      const float ct = 2.0f * (float)ud[0] - 1.0f, stt = sqrtf(fmaxf(1.0f - ct * ct, 0.0f));
+      float sp, cp;
+      sincospif(2.0f * (float)ud[1], &sp, &cp);
+      const float rr = sqrtf(fmaxf(1.0f - y0 * y0, 0.0f));
+      const float y1 = rr * stt * cp, y2 = rr * stt * sp, y3 = rr * ct;
+      const Cx<float> Y[2][2] = {{{y0, y3}, {y2, y1}}, {{-y2, y1}, {y0, -y3}}};
+#pragma unroll
+      for (int r = 0; r < 2; r++)
+#pragma unroll
+        for (int q = 0; q < 2; q++) v[r][q] = Y[r][0] * whd[0][q] + Y[r][1] * whd[1][q];
+    }
+    Cx<float> ri[3], rj[3];
+#pragma unroll
+    for (int q = 0; q < 3; q++) {
+      ri[q] = v[0][0] * u.m[3 * i + q] + v[0][1] * u.m[3 * j + q];
+      rj[q] = v[1][0] * u.m[3 * i + q] + v[1][1] * u.m[3 * j + q];
+    }
+#pragma unroll
+    for (int q = 0; q < 3; q++) {
+      u.m[3 * i + q] = ri[q];
+      u.m[3 * j + q] = rj[q];
+    }
+  }
+  store_link_s(Uf, s, mu, u);
+  if (fails) atomicAdd(fail_count, fails);
+}
+
+// FP32 copy (18 reals) -> FP64 master
+__global__ void f32_to_master_kernel(GaugeView Uf, double2 *m, int Vh) {
+  const size_t nl = (size_t)2 * 4 * Vh;
+  const size_t l = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (l >= nl) return;
+  const int blk = (int)(l / Vh), cb = (int)(l % Vh);  // blk = parity * 4 + mu
+  Cx<float> u[9];
+  LinkIO<LQCD_F32, 18>::load(Uf, blk >> 2, blk & 3, cb, u);
+#pragma unroll
+  for (int k = 0; k < 9; k++) m[((size_t)blk * 9 + k) * Vh + cb] = make_double2(u[k].re, u[k].im);
+}
+
+// ---------------------------------------------------------------------------
 // momenta, Gaussian spinors, link update, reunitarisation
 // ---------------------------------------------------------------------------
 
@@ -871,10 +1048,10 @@ lqcd_status gauge_force_raw(lqcd_ctx *ctx, lqcd_gauge *U, double beta, double c1
     // plaquette staples of every link (6 x 144 B per link), then the force
     const size_t need = (size_t)4 * 6 * 9 * V * sizeof(double2);
     if (ctx->staple_cap < need) {
-      if (ctx->staples) cudaFreeAsync(ctx->staples, ctx->stream);
+      dfree(ctx, ctx->staples);
       ctx->staples = nullptr;
       ctx->staple_cap = 0;
-      LQCD_CUDA(ctx, cudaMallocAsync(&ctx->staples, need, ctx->stream));
+      LQCD_TRY(dalloc(ctx, &ctx->staples, need));
       ctx->staple_cap = need;
     }
     if (prec == LQCD_DF64) {
@@ -897,6 +1074,26 @@ lqcd_status gauge_force_raw(lqcd_ctx *ctx, lqcd_gauge *U, double beta, double c1
   gauge_force_kernel<<<nblk(V), 128, 0, ctx->stream>>>((const double2 *)U->master, U->g, beta, dSdw);
   LQCD_CUDA(ctx, cudaGetLastError());
   return LQCD_OK;
+}
+
+lqcd_status reunitarize_raw(lqcd_ctx *ctx, lqcd_gauge *U);
+
+// FP32 sweep: on the FP32 copy, then back into the FP64 field, reunitarised
+lqcd_status heatbath_f32_raw(lqcd_ctx *ctx, lqcd_gauge *U, double beta, uint64_t seed, uint64_t sweep, int n_or,
+                             unsigned int *fail_dev) {
+  GaugeView Uf;
+  LQCD_TRY(gauge_view(ctx, U, LQCD_F32, 18, &Uf));
+  for (int pass = 0; pass <= n_or; pass++)
+    for (int mu = 0; mu < 4; mu++)
+      for (int par = 0; par < 2; par++) {
+        heatbath_f32_kernel<<<nblk(U->g.Vh), 128, 0, ctx->stream>>>(Uf, U->g, mu, par, (float)beta, seed,
+                                                                    (uint32_t)sweep, pass > 0 ? 1 : 0, fail_dev);
+        LQCD_CUDA(ctx, cudaGetLastError());
+      }
+  f32_to_master_kernel<<<nblk(8L * U->g.Vh), 128, 0, ctx->stream>>>(Uf, (double2 *)U->master, U->g.Vh);
+  LQCD_CUDA(ctx, cudaGetLastError());
+  U->version++;
+  return reunitarize_raw(ctx, U);
 }
 
 lqcd_status heatbath_raw(lqcd_ctx *ctx, lqcd_gauge *U, double beta, uint64_t seed, uint64_t sweep, int n_or,

@@ -21,6 +21,8 @@ lqcd_status check_field(lqcd_ctx *ctx, const lqcd_field &f, const char *name, bo
 lqcd_status plaquette_sum(lqcd_ctx *ctx, const lqcd_gauge *U, double *sum_retr);
 lqcd_status gauge_force_raw(lqcd_ctx *ctx, lqcd_gauge *U, double beta, double c1, int prec, double *dSdw);
 lqcd_status rectangle_sum(lqcd_ctx *ctx, const lqcd_gauge *U, double *sum_retr);
+lqcd_status heatbath_f32_raw(lqcd_ctx *ctx, lqcd_gauge *U, double beta, uint64_t seed, uint64_t sweep, int n_or,
+                             unsigned int *fail_dev);
 lqcd_status heatbath_raw(lqcd_ctx *ctx, lqcd_gauge *U, double beta, uint64_t seed, uint64_t sweep, int n_or,
                          unsigned int *fail_dev);
 lqcd_status momenta_raw(lqcd_ctx *ctx, long V, double *P, uint64_t seed, uint32_t traj);
@@ -216,13 +218,15 @@ extern "C" int lqcd_gauge_force(lqcd_ctx *ctx, const lqcd_gauge *U, double beta,
 }
 
 extern "C" int lqcd_heatbath_sweep(lqcd_ctx *ctx, lqcd_gauge *U, double beta, uint64_t seed, uint64_t sweep_idx,
-                                   int n_or) {
+                                   int n_or, int prec) {
   if (!ctx) return LQCD_ERR_INVALID;
   LQCD_TRY(check_u(ctx, U));
   if (!(beta >= 0.0) || !std::isfinite(beta)) return fail(ctx, LQCD_ERR_INVALID, "beta must be finite, >= 0");
   if (n_or < 0 || n_or > 64) return fail(ctx, LQCD_ERR_INVALID, "n_or out of [0, 64]");
+  if (prec != LQCD_F64 && prec != LQCD_F32) return fail(ctx, LQCD_ERR_INVALID, "prec must be LQCD_F64 or LQCD_F32");
   unsigned int *fails = (unsigned int *)ctx->partials;  // scratch word; not read by anyone else
   LQCD_CUDA(ctx, cudaMemsetAsync(fails, 0, sizeof(unsigned int), ctx->stream));
+  if (prec == LQCD_F32) return heatbath_f32_raw(ctx, U, beta, seed, sweep_idx, n_or, fails);
   return heatbath_raw(ctx, U, beta, seed, sweep_idx, n_or, fails);
 }
 

@@ -12,10 +12,18 @@
 #include "../../include/lqcd.h"
 #include "common.cuh"
 
+// caller-provided device allocator (lqcd_set_allocator); NULL: cudaMallocAsync
+struct DevAllocator {
+  lqcd_alloc_fn alloc = nullptr;
+  lqcd_free_fn free = nullptr;
+  void *user = nullptr;
+};
+
 struct lqcd_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
   int num_sms = 152;
+  DevAllocator A;
   std::string err;
   // reduction workspace: partial sums [slots][nblocks] and per-slot results
   double *partials = nullptr;
@@ -50,12 +58,16 @@ struct lqcd_gauge {
     uint64_t version = 0;
   };
   std::vector<Copy> copies;  // derived precisions / formats
+  DevAllocator A;            // allocator of master and copies (the importing context's)
 };
 
 namespace lqcd {
 
 // status helpers
 lqcd_status fail(lqcd_ctx *ctx, lqcd_status s, const char *fmt, ...);
+// device memory through an allocator (the context's, or a gauge field's)
+lqcd_status raw_alloc(lqcd_ctx *ctx, const DevAllocator &A, void **p, size_t bytes);
+void raw_free(lqcd_ctx *ctx, const DevAllocator &A, void *p);
 lqcd_status cuda_check(lqcd_ctx *ctx, cudaError_t e, const char *what);
 #define LQCD_CUDA(ctx, call)                                           \
   do {                                                                 \

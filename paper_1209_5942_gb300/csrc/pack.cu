@@ -282,9 +282,8 @@ lqcd_status gauge_view(lqcd_ctx *ctx, lqcd_gauge *U, int prec, int recon, GaugeV
     c->prec = prec;
     c->recon = recon;
     void *p = nullptr;
-    if (cudaMalloc(&p, 2 * 4 * mu_stride) != cudaSuccess) {
+    if (raw_alloc(ctx, U->A, &p, 2 * 4 * mu_stride) != LQCD_OK) {
       U->copies.pop_back();
-      cudaGetLastError();
       return fail(ctx, LQCD_ERR_OOM, "gauge copy allocation of %zu bytes failed", 8 * mu_stride);
     }
     c->ptr = p;

@@ -92,6 +92,10 @@ class lqcd_hmc_stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+# caller allocator callbacks (lqcd_alloc_fn, lqcd_free_fn)
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
 # --- library loading ------------------------------------------------------------
 _lib = None
 _vp = ctypes.c_void_p
@@ -108,6 +112,7 @@ SIGNATURES = [
     ("lqcd_get_counters", _i, [_vp, _vp]),
     ("lqcd_set_autotune", _i, [_vp, _i, ctypes.c_char_p]),
     ("lqcd_set_launch_choice", _i, [_vp, _i]),
+    ("lqcd_set_allocator", _i, [_vp, _ALLOC_FN, _FREE_FN, _vp]),
     ("lqcd_reset_counters", _i, [_vp]),
     ("lqcd_field_bytes", ctypes.c_size_t, [ctypes.POINTER(lqcd_geom), _i, _i, _i,
                                            ctypes.POINTER(ctypes.c_size_t)]),
@@ -131,7 +136,7 @@ SIGNATURES = [
                                 ctypes.POINTER(lqcd_cg_stats), ctypes.POINTER(_d)]),
     ("lqcd_gauge_force", _i, [_vp, _vp, _d, _d, _i, _vp, ctypes.POINTER(_d)]),
     ("lqcd_plaquette", _i, [_vp, _vp, ctypes.POINTER(_d)]),
-    ("lqcd_heatbath_sweep", _i, [_vp, _vp, _d, ctypes.c_uint64, ctypes.c_uint64, _i]),
+    ("lqcd_heatbath_sweep", _i, [_vp, _vp, _d, ctypes.c_uint64, ctypes.c_uint64, _i, _i]),
     ("lqcd_momenta_gaussian", _i, [_vp, ctypes.POINTER(lqcd_geom), _vp, ctypes.c_uint64,
                                    ctypes.c_uint32]),
     ("lqcd_spinor_gaussian", _i, [_vp, ctypes.POINTER(lqcd_geom), lqcd_field, _i, ctypes.c_uint64,
@@ -220,16 +225,43 @@ def alloc_field(L, parity, prec, nrhs=1, device="cuda"):
     return data, scale
 
 
-class Context:
-    """An lqcd_ctx bound to a device and a stream (default: torch's current stream)."""
+class TorchAllocator:
+    """The (alloc, free) pair of lqcd_set_allocator backed by PyTorch's caching
+    allocator on one device and stream."""
 
-    def __init__(self, device: int = 0, stream: torch.cuda.Stream | None = None):
+    def __init__(self, device: int, stream: torch.cuda.Stream):
+        self.device, self.stream = device, stream
+
+        def _alloc(nbytes, user):
+            try:
+                return torch.cuda.caching_allocator_alloc(int(nbytes), self.device, self.stream)
+            except Exception:  # out of memory: the library reports LQCD_ERR_OOM
+                return None
+
+        def _free(ptr, user):
+            torch.cuda.caching_allocator_delete(ptr)
+
+        self.alloc_fn = _ALLOC_FN(_alloc)  # kept alive as long as this object
+        self.free_fn = _FREE_FN(_free)
+
+
+class Context:
+    """An lqcd_ctx bound to a device and a stream (default: torch's current
+    stream).  torch_allocator=True routes the library's device memory through
+    PyTorch's caching allocator (lqcd_set_allocator)."""
+
+    def __init__(self, device: int = 0, stream: torch.cuda.Stream | None = None, torch_allocator=False):
         self._h = _vp()
-        s = (stream or torch.cuda.current_stream(device)).cuda_stream
-        st = lib().lqcd_create(ctypes.byref(self._h), device, _vp(s))
+        self._allocator = None
+        stream = stream or torch.cuda.current_stream(device)
+        st = lib().lqcd_create(ctypes.byref(self._h), device, _vp(stream.cuda_stream))
         if st != LQCD_OK:
             raise LqcdError(st, "lqcd_create failed")
         self.device = device
+        if torch_allocator:
+            self._allocator = TorchAllocator(device, stream)
+            self.check(lib().lqcd_set_allocator(self._h, self._allocator.alloc_fn, self._allocator.free_fn,
+                                                None))
 
     @property
     def handle(self):
@@ -423,8 +455,8 @@ def lqcd_plaquette(ctx: Context, U: Gauge) -> float:
     return p.value
 
 
-def lqcd_heatbath_sweep(ctx: Context, U: Gauge, beta, seed, sweep_idx, n_or=0):
-    ctx.check(lib().lqcd_heatbath_sweep(ctx.handle, U.handle, beta, seed, sweep_idx, n_or))
+def lqcd_heatbath_sweep(ctx: Context, U: Gauge, beta, seed, sweep_idx, n_or=0, prec=LQCD_F64):
+    ctx.check(lib().lqcd_heatbath_sweep(ctx.handle, U.handle, beta, seed, sweep_idx, n_or, prec))
 
 
 def lqcd_momenta_gaussian(ctx: Context, L, P: torch.Tensor, seed, traj, antiperiodic_t=True):

@@ -1,0 +1,60 @@
+"""The caller-allocator hook of the C ABI (lqcd_set_allocator): with PyTorch's
+caching allocator behind it, the library's workspace, gauge fields and their
+derived copies come from torch's pool, are returned to it, and the results are
+those of a context that allocates by itself."""
+import pytest
+import torch
+
+from paper_1209_5942_gb300 import inputs, lqcd
+from tests.gpu_util import dev
+
+pytestmark = pytest.mark.gpu
+
+
+def _solve(ctx, L, U_d, b_d, kappa, mu):
+    G = lqcd.lqcd_gauge_import(ctx, U_d, L)
+    x = torch.zeros_like(b_d)
+    prm = lqcd.cg_params(tol=1e-10, outer_prec=lqcd.LQCD_DF64, inner_prec=lqcd.LQCD_F32, sloppy_recon=12)
+    st = lqcd.lqcd_cg_solve(ctx, G, lqcd.field(b_d, lqcd.LQCD_LAYOUT_LEXI), lqcd.field(x, lqcd.LQCD_LAYOUT_LEXI),
+                            kappa, mu, prm)
+    return G, x, st
+
+
+def test_torch_caching_allocator_backs_the_library():
+    from paper_1209_5942_gb300 import build
+    build.build()
+    L = (8, 8, 8, 8)
+    V = inputs.volume(L)
+    kappa, mu = 0.15, 0.01 / 0.3
+    U_d = dev(inputs.random_gauge(L, "near", seed=1201, eps=0.4))
+    b_d = dev(inputs.gaussian_spinor(L, 1202))
+    ref_ctx = lqcd.Context(0)
+    G0, x_ref, st_ref = _solve(ref_ctx, L, U_d, b_d, kappa, mu)
+    G0.free()
+    ref_ctx.close()
+    torch.cuda.synchronize()
+    base = torch.cuda.memory_allocated()
+
+    ctx = lqcd.Context(0, torch_allocator=True)
+    torch.cuda.synchronize()
+    assert torch.cuda.memory_allocated() > base  # the workspace came from torch's pool
+    G, x, st = _solve(ctx, L, U_d, b_d, kappa, mu)
+    torch.cuda.synchronize()
+    # master links (576 B per site) and the derived DF64 / F32 copies live in torch's pool
+    assert torch.cuda.memory_allocated() >= base + 576 * V + V * 16 * 2  # + x itself
+    assert st[0]["converged"] == 1 and st_ref[0]["converged"] == 1
+    assert torch.equal(x, x_ref)  # same kernels, same bits
+    del x
+    G.free()
+    ctx.close()
+    torch.cuda.synchronize()
+    assert torch.cuda.memory_allocated() == base  # everything went back
+
+
+def test_allocator_pair_must_be_complete():
+    ctx = lqcd.Context(0)
+    with pytest.raises(lqcd.LqcdError) as e:
+        ctx.check(lqcd.lib().lqcd_set_allocator(ctx.handle, lqcd.TorchAllocator(0, torch.cuda.current_stream()).alloc_fn,
+                                                None, None))
+    assert e.value.status == lqcd.LQCD_ERR_INVALID
+    ctx.check(lqcd.lib().lqcd_set_allocator(ctx.handle, None, None, None))  # back to the default

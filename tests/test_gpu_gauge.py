@@ -306,3 +306,65 @@ def test_hmc_2mn_pure_gauge_scaling(ctx, oracle):
                                         nsteps_f=2, nsteps_g=2, tau=1.0)
     assert abs(dHs[2] - dH_ref) < 1e-8 * max(1.0, abs(dH_ref))
     assert 3.0 < dHs[2] / dHs[4] < 5.3, dHs
+
+
+def test_f32_heatbath_strong_coupling(ctx):
+    """The single-precision heatbath (Sec. 5.1 measures the FP32 kernels):
+    <P> = beta/18 + beta^2/216 at beta = 0.3."""
+    L = (8, 8, 8, 8)
+    beta = 0.3
+    G = lqcd.lqcd_gauge_import(ctx, dev(inputs.random_gauge(L, "cold")), L)
+    vals = []
+    for s in range(80):
+        lqcd.lqcd_heatbath_sweep(ctx, G, beta, 78, s, prec=lqcd.LQCD_F32)
+        if s >= 10:
+            vals.append(lqcd.lqcd_plaquette(ctx, G))
+    vals = np.array(vals)
+    expect = beta / 18 + beta ** 2 / 216
+    err = vals.std() / np.sqrt(len(vals))
+    assert abs(vals.mean() - expect) < 4 * err + 2e-4
+
+
+def test_f32_heatbath_equilibrium_and_unitarity(ctx):
+    """At beta = 5.7 the FP32 and FP64 heatbaths reach the same plaquette; the
+    FP32 result is written back reunitarised in FP64."""
+    L = (8, 8, 8, 8)
+    means = {}
+    for prec in (lqcd.LQCD_F64, lqcd.LQCD_F32):
+        G = lqcd.lqcd_gauge_import(ctx, dev(inputs.random_gauge(L, "cold")), L)
+        vals = []
+        for s in range(70):
+            lqcd.lqcd_heatbath_sweep(ctx, G, 5.7, 79, s, n_or=1, prec=prec)
+            if s >= 30:
+                vals.append(lqcd.lqcd_plaquette(ctx, G))
+        means[prec] = np.mean(vals)
+        if prec == lqcd.LQCD_F32:
+            got = _export(ctx, G, L)
+            eye = np.eye(3)
+            assert np.max(np.abs(got @ np.conj(np.transpose(got, (0, 1, 3, 2))) - eye)) < 1e-13
+            assert np.max(np.abs(np.linalg.det(got) - 1)) < 1e-13
+        G.free()
+    assert 0.53 < means[lqcd.LQCD_F64] < 0.57
+    assert abs(means[lqcd.LQCD_F32] - means[lqcd.LQCD_F64]) < 4e-3, means
+
+
+def test_f32_overrelaxation_preserves_action(ctx):
+    L = (4, 4, 4, 4)
+    G = lqcd.lqcd_gauge_import(ctx, dev(inputs.random_gauge(L, "near", seed=37, eps=0.8)), L)
+    F = torch.zeros((4, inputs.volume(L), 8), dtype=torch.float64, device="cuda")
+    G2 = lqcd.lqcd_gauge_import(ctx, dev(inputs.random_gauge(L, "cold")), L)
+    lqcd.lqcd_heatbath_sweep(ctx, G, 5.7, 2, 0, prec=lqcd.LQCD_F32)
+    lqcd.lqcd_gauge_copy(ctx, G, G2)
+    lqcd.lqcd_heatbath_sweep(ctx, G, 5.7, 2, 1, n_or=0, prec=lqcd.LQCD_F32)
+    lqcd.lqcd_heatbath_sweep(ctx, G2, 5.7, 2, 1, n_or=2, prec=lqcd.LQCD_F32)
+    S1 = lqcd.lqcd_gauge_force(ctx, G, 5.7, F)
+    S2 = lqcd.lqcd_gauge_force(ctx, G2, 5.7, F)
+    assert abs(S2 - S1) < 1e-5 * abs(S1)
+
+
+def test_heatbath_rejects_other_precisions(ctx):
+    L = (4, 4, 4, 4)
+    G = lqcd.lqcd_gauge_import(ctx, dev(inputs.random_gauge(L, "cold")), L)
+    with pytest.raises(lqcd.LqcdError) as e:
+        lqcd.lqcd_heatbath_sweep(ctx, G, 5.7, 1, 0, prec=lqcd.LQCD_BF16S)
+    assert e.value.status == lqcd.LQCD_ERR_INVALID
