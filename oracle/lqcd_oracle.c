@@ -810,8 +810,12 @@ void or_gauge_dSdw_sym(const double *U, const int *L, double beta, double c1, do
 /* X must be supplied (already solved); output layout [mu][V][8].         */
 /* ------------------------------------------------------------------ */
 
-void or_fermion_dSdw(const double *U, const double *X, const int *L, int antiperiodic_t,
-                     double kappa, double mu_tm, int eo, double *out) {
+/* -2 Re[Y^+ dMhat X] / domega for given left and right vectors Y, X on the
+ * even sites (eo = 1; Y = Mhat X gives the force of phi^+ (Mhat^+ Mhat)^-1
+ * phi), or -2 Re[Y^+ dM X] on the full lattice (eo = 0).  Y = NULL: Y =
+ * Mhat X (or M X). */
+void or_fermion_dSdw_lr(const double *U, const double *Yin, const double *X, const int *L,
+                        int antiperiodic_t, double kappa, double mu_tm, int eo, double *out) {
   build_gammas();
   build_generators();
   long V = volume(L);
@@ -823,7 +827,12 @@ void or_fermion_dSdw(const double *U, const double *X, const int *L, int antiper
   if (eo) {
     double *Y = malloc(n * sizeof(double));
     double *t = malloc(n * sizeof(double));
-    or_apply_Mhat(U, X, Y, L, antiperiodic_t, kappa, mu_tm, 0); /* Y_e (odd zero) */
+    if (Yin) {
+      memcpy(Y, Yin, n * sizeof(double));
+      zero_parity(Y, L, 1);
+    } else {
+      or_apply_Mhat(U, X, Y, L, antiperiodic_t, kappa, mu_tm, 0); /* Y_e (odd zero) */
+    }
     /* W_o = A_o^-+ H^+ Y_e restricted to odd */
     or_hop(U, Y, t, L, antiperiodic_t, 1);
     zero_parity(t, L, 0);
@@ -842,7 +851,8 @@ void or_fermion_dSdw(const double *U, const double *X, const int *L, int antiper
     free(t);
     free(xe);
   } else {
-    or_apply_M(U, X, Lf, L, antiperiodic_t, kappa, mu_tm, 0);
+    if (Yin) memcpy(Lf, Yin, n * sizeof(double));
+    else or_apply_M(U, X, Lf, L, antiperiodic_t, kappa, mu_tm, 0);
     memcpy(Rf, X, n * sizeof(double));
     pref = 2.0 * kappa;
   }
@@ -894,6 +904,11 @@ void or_fermion_dSdw(const double *U, const double *X, const int *L, int antiper
     }
   free(Lf);
   free(Rf);
+}
+
+void or_fermion_dSdw(const double *U, const double *X, const int *L, int antiperiodic_t,
+                     double kappa, double mu_tm, int eo, double *out) {
+  or_fermion_dSdw_lr(U, NULL, X, L, antiperiodic_t, kappa, mu_tm, eo, out);
 }
 
 /* Pseudofermion action S_pf = phi^+ (Mhat^+ Mhat)^-1 phi = phi^+ X (eo = 1)

@@ -81,6 +81,8 @@ def _declare(L):
     L.or_gauge_dSdw.argtypes = [_dp, _ip, ctypes.c_double, _dp]
     L.or_fermion_dSdw.argtypes = [_dp, _dp, _ip, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                   ctypes.c_int, _dp]
+    L.or_fermion_dSdw_lr.argtypes = [_dp, _dp, _dp, _ip, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_int, _dp]
     L.or_pseudofermion_action.argtypes = [_dp, _dp, _dp, _ip, ctypes.c_int, ctypes.c_double,
                                           ctypes.c_double, ctypes.c_int, ctypes.c_double,
                                           ctypes.c_int]
@@ -285,6 +287,18 @@ def fermion_dSdw(U, X, L, kappa, mu, eo=True, antiperiodic_t=True) -> np.ndarray
     return out
 
 
+def fermion_dSdw_lr(U, Y, X, L, kappa, mu, eo=True, antiperiodic_t=True) -> np.ndarray:
+    """-2 Re[Y^+ dMhat(mu) X] / domega for given Y, X (Y = Mhat X: fermion_dSdw)."""
+    V = volume(L)
+    U = _cplx(U, (V, 4, 3, 3))
+    X = _cplx(X, (V, 4, 3))
+    Y = _cplx(Y, (V, 4, 3))
+    out = np.zeros((4, V, 8), np.float64)
+    lib().or_fermion_dSdw_lr(_p(U), _p(Y), _p(X), _dims(L), int(antiperiodic_t), kappa, mu, int(eo),
+                             _p(out))
+    return out
+
+
 def pseudofermion_action(U, phi, L, kappa, mu, eo=True, tol=1e-13, max_iter=100000,
                          antiperiodic_t=True):
     V = volume(L)
@@ -419,3 +433,27 @@ def hmc_md_2mn(U, P, phi, L, beta, kappa, mu, c1=TLSYM_C1, nf=1, nsteps_f=10, ns
     dH = lib().or_hmc_md_2mn(_p(U), _p(P), _p(phi), _dims(L), beta, c1, kappa, mu, int(nf),
                              int(nsteps_f), int(nsteps_g), lam, tau, tol, int(max_iter), _p(h))
     return U, P, dH, tuple(h)
+
+
+# -- mass preconditioning (Hasenbusch) with a heavier twisted mass (Sec. 2.2:
+# det D = det A det(D / A) with a second, heavier fermion matrix) -------------
+
+def hasenbusch_action(U, phi2, L, kappa, mu, mu2, tol=1e-13):
+    """S2 = phi2^+ W (Mhat^+ Mhat)^-1 W^+ phi2 with W = Mhat(mu2): the ratio
+    det(Mhat^+ Mhat) / det(W^+ W).  Returns (S2, X), X = (Mhat^+ Mhat)^-1 W^+ phi2."""
+    psi = apply_Mhat(U, phi2, L, kappa, mu2, dagger=True)
+    return pseudofermion_action(U, psi, L, kappa, mu, eo=True, tol=tol)
+
+
+def hasenbusch_dSdw(U, phi2, X, L, kappa, mu, mu2):
+    """dS2/domega = -2 Re[Y^+ dMhat(mu) X] + 2 Re[phi2^+ dW X], Y = Mhat(mu) X."""
+    return fermion_dSdw(U, X, L, kappa, mu, eo=True) + fermion_dSdw_lr(U, -np.asarray(phi2), X, L, kappa, mu2,
+                                                                       eo=True)
+
+
+def hasenbusch_source(U, eta, L, kappa, mu, mu2, tol=1e-13):
+    """phi2 = W^-+ Mhat^+ eta (even sites), so that S2 = eta^+ eta:
+    W^-+ = W (W^+ W)^-1."""
+    rhs = apply_Mhat(U, eta, L, kappa, mu, dagger=True)
+    _, Z = pseudofermion_action(U, rhs, L, kappa, mu2, eo=True, tol=tol)
+    return apply_Mhat(U, Z, L, kappa, mu2, dagger=False)

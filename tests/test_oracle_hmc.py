@@ -163,3 +163,38 @@ def test_hmc_reversibility_and_scaling(oracle):
         dHs.append(abs(d))
     ratio = dHs[0] / dHs[1]
     assert 3.0 < ratio < 5.3, (dHs, ratio)
+
+
+def test_hasenbusch_ratio_pins(oracle):
+    """Mass preconditioning with a heavier twisted mass mu2: with mu2 = mu the
+    ratio action is phi^+ phi exactly and its force vanishes (the two terms
+    cancel); the heatbath source gives S2 = eta^+ eta; central differences of
+    S2 on single links (one across the time boundary) match the force."""
+    import scipy.linalg
+    L = (2, 4, 2, 4)
+    V = inputs.volume(L)
+    kappa, mu, mu2 = 0.14, 0.05, 0.3
+    U = inputs.random_gauge(L, "near", seed=401, eps=0.4)
+    ev = ~oracle.parity_mask(L)
+    phi = inputs.gaussian_spinor(L, 402) * ev[:, None, None]
+    S_same, X_same = oracle.hasenbusch_action(U, phi, L, kappa, mu, mu, tol=1e-14)
+    assert abs(S_same - np.vdot(phi, phi).real) < 1e-10 * S_same
+    F_same = oracle.hasenbusch_dSdw(U, phi, X_same, L, kappa, mu, mu)
+    assert np.max(np.abs(F_same)) < 1e-9
+    eta = inputs.gaussian_spinor(L, 403) * ev[:, None, None]
+    phi2 = oracle.hasenbusch_source(U, eta, L, kappa, mu, mu2, tol=1e-14)
+    S2, _ = oracle.hasenbusch_action(U, phi2, L, kappa, mu, mu2, tol=1e-14)
+    assert abs(S2 - np.vdot(eta, eta).real) < 1e-9 * S2
+    S, X = oracle.hasenbusch_action(U, phi, L, kappa, mu, mu2, tol=1e-14)
+    F = oracle.hasenbusch_dSdw(U, phi, X, L, kappa, mu, mu2)
+    h = 1e-5
+    for (i, m) in [(0, 0), (9, 3), (V - 1, 3), (14, 1)]:
+        for a in (0, 3, 7):
+            Up, Um = U.copy(), U.copy()
+            T = oracle.generator(a)
+            Up[i, m] = scipy.linalg.expm(1j * h * T) @ U[i, m]
+            Um[i, m] = scipy.linalg.expm(-1j * h * T) @ U[i, m]
+            sp, _ = oracle.hasenbusch_action(Up, phi, L, kappa, mu, mu2, tol=1e-14)
+            sm, _ = oracle.hasenbusch_action(Um, phi, L, kappa, mu, mu2, tol=1e-14)
+            fd = (sp - sm) / (2 * h)
+            assert abs(fd - F[m, i, a]) < 1e-6 * max(1.0, abs(fd)), (i, m, a, fd, F[m, i, a])
