@@ -307,6 +307,18 @@ int lqcd_fermion_force(lqcd_ctx *ctx, const lqcd_gauge *U, lqcd_field phi, doubl
                        lqcd_field *X_cache, const lqcd_geom *geom, double kappa, double mu,
                        const lqcd_cg_params *params, lqcd_cg_stats *stats, double *S_out);
 
+/* Mass preconditioning with a heavier twisted mass (Sec. 2.2: det D =
+ * det A det(D / A) with a second fermion matrix A): for W = Mhat(mu2) the
+ * ratio action
+ *   S2 = phi2^+ W (Mhat^+ Mhat)^-1 W^+ phi2     (Mhat = Mhat(mu))
+ * and its derivative -2 Re[Y^+ dMhat(mu) X] + 2 Re[phi2^+ dW X] with
+ * X = (Mhat^+ Mhat)^-1 W^+ phi2 (CG with params), Y = Mhat X, into dSdw
+ * (device float64 [4][V][8]).  phi2: EO half field of the even sites,
+ * LQCD_F64.  *S_out (host, may be NULL) receives S2.  Synchronous. */
+int lqcd_fermion_force_ratio(lqcd_ctx *ctx, const lqcd_gauge *U, lqcd_field phi2, double *dSdw,
+                             const lqcd_geom *geom, double kappa, double mu, double mu2,
+                             const lqcd_cg_params *params, lqcd_cg_stats *stats, double *S_out);
+
 /* Gauge action (Sec. 2.1, eq. "S_tlsym")
  *   S_g = (beta/3) sum_x [ c0 sum_{mu<nu} (3 - Re Tr P_munu(x))
  *                        + c1 sum_{mu != nu} (3 - Re Tr R_munu(x)) ],
@@ -376,6 +388,11 @@ typedef struct {
   int32_t force_prec;  /* gauge-force arithmetic: LQCD_F64 (default) or LQCD_DF64
                           (float-float, FP64-class; H and dH stay IEEE FP64) */
   double lambda;       /* 2MN parameter; 0 selects 0.1931833275037836 */
+  double mu2;          /* mass preconditioning (nf = 1): 0 = off; else the heavier twisted
+                          mass of W = Mhat(mu2), S_f = phi1^+ (W^+ W)^-1 phi1
+                          + phi2^+ W (Mhat^+ Mhat)^-1 W^+ phi2 */
+  int32_t nsteps_mid;  /* 2MN with mu2: steps of the W force per outer position update */
+  int32_t reserved;
   lqcd_cg_params cg;   /* solver used for every force and action evaluation */
 } lqcd_hmc_params;
 enum { LQCD_LEAPFROG = 0, LQCD_2MN = 1 };
@@ -396,9 +413,14 @@ typedef struct {
  *     together:  P -= eps/2 dS; (U <- exp(i eps P) U; P -= eps dS) ...
  *   LQCD_2MN (Sec. 2.2 "2MN", "multiple timescales"; Sec. 5.3): the
  *     minimum-norm step  P -= l e dS; Q(e/2); P -= (1-2l) e dS; Q(e/2);
- *     P -= l e dS  on two scales: the fermion force with nsteps steps of
+ *     P -= l e dS  on nested scales: the fermion force with nsteps steps of
  *     e = tau/nsteps outside, and every position update Q(h) an inner 2MN
- *     integration of the gauge force over h with nsteps_gauge steps.
+ *     integration of the gauge force over h with nsteps_gauge steps.  With
+ *     mu2 != 0 (mass preconditioning, Sec. 2.2) the ratio force is outside
+ *     (nsteps), the W force in the middle (nsteps_mid per outer position
+ *     update) and the gauge force inside; eta2 for phi2 = W^-+ Mhat^+ eta2 is
+ *     drawn from the stream of seed ^ 0x9E3779B97F4A7C15.  Pure gauge (nf = 0)
+ *     runs the gauge scale alone with 2 nsteps nsteps_gauge steps.
  * Momentum updates at the same links are merged, so each force is
  * evaluated once per distinct field.  Synchronous. */
 int lqcd_hmc_trajectory(lqcd_ctx *ctx, lqcd_gauge *U, const lqcd_hmc_params *params,

@@ -667,9 +667,9 @@ __global__ void __launch_bounds__(128) heatbath_kernel(double2 *U, Geom g, int m
 
 // ---------------------------------------------------------------------------
 // The heatbath and overrelaxation in single precision (the paper's main
-// heatbath measurements are FP32): the same update, counters and random
-// numbers, on the FP32 copy of the links (18 reals), with FP32 staples, SU(2)
-// projection and sampling.  The caller writes the copy back into the FP64
+// heatbath measurements are FP32): the same update on the FP32 copy of the
+// links (18 reals), with FP32 staples, SU(2) projection and sampling, and
+// FP32 uniforms (24 bits) from the same Philox counters.  The caller writes the copy back into the FP64
 // field and reunitarises it in FP64.
 // ---------------------------------------------------------------------------
 struct M3s {
@@ -737,11 +737,23 @@ LQCD_DEV M3s staple_s(const GaugeView &Uf, const Geom &g, const int c[4], int mu
   return A;
 }
 
+// four uniforms in (0, 1) with 24 random bits each from one Philox block:
+// (k + 1/2) 2^-24, k the top 24 bits of each word (no FP64 arithmetic)
+LQCD_DEV void uniform4f(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint64_t seed, float u[4]) {
+  const U4 w = philox(U4{c0, c1, c2, c3}, (uint32_t)seed, (uint32_t)(seed >> 32));
+  u[0] = __fmaf_rn((float)(w.x >> 8), 0x1p-24f, 0x1p-25f);
+  u[1] = __fmaf_rn((float)(w.y >> 8), 0x1p-24f, 0x1p-25f);
+  u[2] = __fmaf_rn((float)(w.z >> 8), 0x1p-24f, 0x1p-25f);
+  u[3] = __fmaf_rn((float)(w.w >> 8), 0x1p-24f, 0x1p-25f);
+}
+
+// the exact SU(2) update in FP32: the same method as sample_y0, with the
+// uniforms of one Philox block (counter word 3 = attempt) per attempt
 LQCD_DEV bool sample_y0_f(float b, uint32_t c0, uint32_t c1, uint32_t c2, uint64_t seed, float *y0) {
   for (int n = 0; n < HB_MAX_ATTEMPTS; n++) {
-    double ud[2];
-    uniform2(c0, c1, c2, (uint32_t)(2 * n), seed, ud);
-    const float u0 = (float)ud[0], u1 = (float)ud[1];
+    float r[4];
+    uniform4f(c0, c1, c2, (uint32_t)n, seed, r);
+    const float u0 = r[0], u1 = r[1];
     if (b < (float)HB_B_SWITCH) {
       float y = b > 1e-30f ? 1.0f + log1pf(expm1f(-2.0f * b) * (1.0f - u0)) / b : 2.0f * u0 - 1.0f;
       if (u1 * u1 <= 1.0f - y * y) {
@@ -750,11 +762,9 @@ LQCD_DEV bool sample_y0_f(float b, uint32_t c0, uint32_t c1, uint32_t c2, uint64
       }
       continue;
     }
-    double vd[2];
-    uniform2(c0, c1, c2, (uint32_t)(2 * n + 1), seed, vd);
     const float cs = cospif(2.0f * u1);
-    const float lam2 = -(logf(u0) + cs * cs * logf((float)vd[0])) / (2.0f * b);
-    if ((float)vd[1] * (float)vd[1] <= 1.0f - lam2) {
+    const float lam2 = -(logf(u0) + cs * cs * logf(r[2])) / (2.0f * b);
+    if (r[3] * r[3] <= 1.0f - lam2) {
       *y0 = 1.0f - 2.0f * lam2;
       return true;
     }
@@ -801,11 +811,11 @@ __global__ void __launch_bounds__(128) heatbath_f32_kernel(GaugeView Uf, Geom g,
         fails++;
         continue;
       }
-      double ud[2];
-      uniform2((uint32_t)s.lexi, sweep, (uint32_t)mu | ((uint32_t)sg << 2) | (TAG_DIR << 8), 0u, seed, ud);
-      const float ct = 2.0f * (float)ud[0] - 1.0f, stt = sqrtf(fmaxf(1.0f - ct * ct, 0.0f));
+      float ud[4];
+      uniform4f((uint32_t)s.lexi, sweep, (uint32_t)mu | ((uint32_t)sg << 2) | (TAG_DIR << 8), 0u, seed, ud);
+      const float ct = 2.0f * ud[0] - 1.0f, stt = sqrtf(fmaxf(1.0f - ct * ct, 0.0f));
       float sp, cp;
-      sincospif(2.0f * (float)ud[1], &sp, &cp);
+      sincospif(2.0f * ud[1], &sp, &cp);
       const float rr = sqrtf(fmaxf(1.0f - y0 * y0, 0.0f));
       const float y1 = rr * stt * cp, y2 = rr * stt * sp, y3 = rr * ct;
       const Cx<float> Y[2][2] = {{{y0, y3}, {y2, y1}}, {{-y2, y1}, {y0, -y3}}};

@@ -8,6 +8,7 @@
 //   read as exp(-(H' - H))).
 // H, dH and every action are accumulated in FP64 on the device.
 #include <chrono>
+#include <functional>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -135,8 +136,10 @@ lqcd_status solve_normal(lqcd_ctx *ctx, lqcd_gauge *U, const HalfField &phi, con
 }
 
 // dS/dw of S = phi^+ (Mhat^+ Mhat)^-1 phi given X (F64 half fields) -> out [4][V][8]
-lqcd_status fermion_force_from_X(lqcd_ctx *ctx, lqcd_gauge *U, const HalfField &X, double kappa, double mu,
-                                 double *out) {
+// -2 Re[Y^+ dMhat(mu) X] / domega into out; Y = NULL: Y = Mhat X (the force of
+// phi^+ (Mhat^+ Mhat)^-1 phi)
+lqcd_status fermion_force_lr(lqcd_ctx *ctx, lqcd_gauge *U, const HalfField *Y, const HalfField &X, double kappa,
+                             double mu, double *out) {
   const Geom &g = U->g;
   const int Vh = g.Vh;
   size_t hb = spinor_half_bytes(LQCD_F64, Vh);
@@ -149,9 +152,10 @@ lqcd_status fermion_force_from_X(lqcd_ctx *ctx, lqcd_gauge *U, const HalfField &
   HalfField T = f64_half(tmp.p, Vh);
   Op op{ctx, g, {}, LQCD_F64, U->recon, kappa, mu};
   LQCD_TRY(gauge_view(ctx, U, LQCD_F64, U->recon, &op.U));
-  // Re = X_e;  Le = Y_e = Mhat X_e
+  // Re = X_e;  Le = Y_e (= Mhat X_e unless given)
   LQCD_CUDA(ctx, cudaMemcpyAsync(Re.ptr, X.ptr, hb, cudaMemcpyDeviceToDevice, ctx->stream));
-  LQCD_TRY(apply_schur(op, X, Le, T, 0, false, nullptr, nullptr, nullptr));
+  if (Y) LQCD_CUDA(ctx, cudaMemcpyAsync(Le.ptr, Y->ptr, hb, cudaMemcpyDeviceToDevice, ctx->stream));
+  else LQCD_TRY(apply_schur(op, X, Le, T, 0, false, nullptr, nullptr, nullptr));
   double a = 2.0 * kappa * mu, n = 1.0 / (1.0 + a * a);
   // Ro = Z_o = A_o^-1 H_oe X_e
   HopLaunch L;
@@ -290,6 +294,69 @@ extern "C" int lqcd_gauge_copy(lqcd_ctx *ctx, const lqcd_gauge *src, lqcd_gauge 
   return LQCD_OK;
 }
 
+lqcd_status fermion_force_from_X(lqcd_ctx *ctx, lqcd_gauge *U, const HalfField &X, double kappa, double mu,
+                                 double *out) {
+  return fermion_force_lr(ctx, U, nullptr, X, kappa, mu, out);
+}
+
+// Mass preconditioning with a heavier twisted mass mu2 (Sec. 2.2: det D =
+// det A det(D / A)): the ratio action S2 = phi2^+ W (Mhat^+ Mhat)^-1 W^+ phi2,
+// W = Mhat(mu2), and its derivative
+//   dS2 = -2 Re[Y^+ dMhat(mu) X] + 2 Re[phi2^+ dW X],
+//   X = (Mhat^+ Mhat)^-1 psi, psi = W^+ phi2, Y = Mhat X.
+// psi and X (F64 half fields) are outputs; S2 (host) = Re psi^+ X.
+lqcd_status ratio_solve(lqcd_ctx *ctx, lqcd_gauge *U, const HalfField &phi2, const HalfField &psi,
+                        const HalfField &X, double kappa, double mu, double mu2, const lqcd_cg_params &prm,
+                        lqcd_cg_stats *st, double *S2) {
+  const int Vh = U->g.Vh;
+  DBuf tmp(ctx);
+  LQCD_TRY(tmp.alloc(spinor_half_bytes(LQCD_F64, Vh)));
+  Op op{ctx, U->g, {}, LQCD_F64, U->recon, kappa, mu2};
+  LQCD_TRY(gauge_view(ctx, U, LQCD_F64, U->recon, &op.U));
+  LQCD_TRY(apply_schur(op, phi2, psi, f64_half(tmp.p, Vh), 0, true, nullptr, nullptr, nullptr));
+  LQCD_TRY(solve_normal(ctx, U, psi, X, kappa, mu, prm, st));
+  if (S2) LQCD_TRY(half_redot(ctx, Vh, psi, X, S2));
+  return LQCD_OK;
+}
+lqcd_status ratio_force(lqcd_ctx *ctx, lqcd_gauge *U, const HalfField &phi2, const HalfField &X, double kappa,
+                        double mu, double mu2, double *out) {
+  const long V = 2L * U->g.Vh;
+  DBuf f2(ctx);
+  LQCD_TRY(f2.alloc((size_t)32 * V * sizeof(double)));
+  LQCD_TRY(fermion_force_lr(ctx, U, nullptr, X, kappa, mu, out));
+  LQCD_TRY(fermion_force_lr(ctx, U, &phi2, X, kappa, mu2, (double *)f2.p));
+  return momenta_update_raw(ctx, V, out, (const double *)f2.p, 1.0);  // out -= G(phi2, X; mu2)
+}
+
+extern "C" int lqcd_fermion_force_ratio(lqcd_ctx *ctx, const lqcd_gauge *Uc, lqcd_field phi2, double *dSdw,
+                                        const lqcd_geom *geom, double kappa, double mu, double mu2,
+                                        const lqcd_cg_params *params, lqcd_cg_stats *stats, double *S_out) {
+  if (!ctx) return LQCD_ERR_INVALID;
+  LQCD_TRY(check_u(ctx, Uc));
+  LQCD_TRY(check_geom(ctx, geom));
+  if (!geom_equal(Uc->geom, *geom)) return fail(ctx, LQCD_ERR_INVALID, "geometry mismatch");
+  LQCD_TRY(check_field(ctx, phi2, "phi2", false));
+  if (phi2.prec != LQCD_F64 || phi2.nrhs != 1) return fail(ctx, LQCD_ERR_INVALID, "phi2 must be one F64 EO half field");
+  if (!dSdw || !aligned16(dSdw)) return fail(ctx, LQCD_ERR_INVALID, "dSdw: NULL or misaligned");
+  if (!params) return fail(ctx, LQCD_ERR_INVALID, "params is NULL");
+  if (params->outer_prec != LQCD_F64 && params->outer_prec != LQCD_DF64)
+    return fail(ctx, LQCD_ERR_INVALID, "outer_prec must be F64 or DF64");
+  if (!std::isfinite(kappa) || !std::isfinite(mu) || !std::isfinite(mu2))
+    return fail(ctx, LQCD_ERR_NONFINITE, "kappa/mu/mu2 not finite");
+  lqcd_gauge *U = const_cast<lqcd_gauge *>(Uc);
+  const int Vh = U->g.Vh;
+  DBuf pbuf(ctx), xbuf(ctx);
+  LQCD_TRY(pbuf.alloc(spinor_half_bytes(LQCD_F64, Vh)));
+  LQCD_TRY(xbuf.alloc(spinor_half_bytes(LQCD_F64, Vh)));
+  HalfField ph = f64_half(phi2.ptr, Vh), psi = f64_half(pbuf.p, Vh), X = f64_half(xbuf.p, Vh);
+  lqcd_cg_stats st;
+  std::memset(&st, 0, sizeof(st));
+  lqcd_status s = ratio_solve(ctx, U, ph, psi, X, kappa, mu, mu2, *params, &st, S_out);
+  if (stats) *stats = st;
+  if (s != LQCD_OK) return s;
+  return ratio_force(ctx, U, ph, X, kappa, mu, mu2, dSdw);
+}
+
 extern "C" int lqcd_fermion_force(lqcd_ctx *ctx, const lqcd_gauge *Uc, lqcd_field phi, double *dSdw,
                                   lqcd_field *X_cache, const lqcd_geom *geom, double kappa, double mu,
                                   const lqcd_cg_params *params, lqcd_cg_stats *stats, double *S_out) {
@@ -348,6 +415,9 @@ extern "C" int lqcd_hmc_trajectory(lqcd_ctx *ctx, lqcd_gauge *U, const lqcd_hmc_
     return fail(ctx, LQCD_ERR_INVALID, "c1 must be finite and lambda in [0, 0.5)");
   if (prm->force_prec != LQCD_F64 && prm->force_prec != LQCD_DF64)
     return fail(ctx, LQCD_ERR_INVALID, "force_prec must be LQCD_F64 or LQCD_DF64");
+  if (!std::isfinite(prm->mu2)) return fail(ctx, LQCD_ERR_NONFINITE, "mu2 not finite");
+  if (prm->mu2 != 0.0 && prm->integrator == LQCD_2MN && prm->nsteps_mid < 1)
+    return fail(ctx, LQCD_ERR_INVALID, "mass preconditioning with 2MN needs nsteps_mid >= 1");
   auto t0 = std::chrono::steady_clock::now();
   std::memset(stats, 0, sizeof(*stats));
   const Geom &g = U->g;
@@ -355,10 +425,12 @@ extern "C" int lqcd_hmc_trajectory(lqcd_ctx *ctx, lqcd_gauge *U, const lqcd_hmc_
   const long V = 2L * Vh;
   const size_t nP = (size_t)32 * V;
   const bool fermions = prm->nf != 0;
+  const bool hasen = fermions && prm->mu2 != 0.0;  // mass preconditioning
   const bool two_mn = prm->integrator == LQCD_2MN;
   const double lam = prm->lambda != 0.0 ? prm->lambda : 0.1931833275037836;
+  const double mu1 = hasen ? prm->mu2 : prm->mu;  // twisted mass of the first pseudofermion
   size_t hb = spinor_half_bytes(LQCD_F64, Vh);
-  DBuf P(ctx), F(ctx), eta(ctx), phi(ctx), X(ctx), tmp(ctx), save(ctx);
+  DBuf P(ctx), F(ctx), eta(ctx), phi(ctx), X(ctx), tmp(ctx), save(ctx), phi2(ctx), psi2(ctx), X2(ctx);
   LQCD_TRY(P.alloc(nP * sizeof(double)));
   LQCD_TRY(F.alloc(nP * sizeof(double)));
   LQCD_TRY(save.alloc((size_t)2 * 4 * 9 * Vh * 16));
@@ -368,56 +440,95 @@ extern "C" int lqcd_hmc_trajectory(lqcd_ctx *ctx, lqcd_gauge *U, const lqcd_hmc_
     LQCD_TRY(X.alloc(hb));
     LQCD_TRY(tmp.alloc(hb));
   }
+  if (hasen) {
+    LQCD_TRY(phi2.alloc(hb));
+    LQCD_TRY(psi2.alloc(hb));
+    LQCD_TRY(X2.alloc(hb));
+  }
   LQCD_CUDA(ctx, cudaMemcpyAsync(save.p, U->master, (size_t)2 * 4 * 9 * Vh * 16, cudaMemcpyDeviceToDevice,
                                  ctx->stream));
   const uint64_t seed = prm->seed;
   const uint32_t traj = prm->traj;
   LQCD_TRY(momenta_raw(ctx, V, (double *)P.p, seed, traj));
   HalfField Phi = f64_half(phi.p, Vh), Xh = f64_half(X.p, Vh);
-  Op op{ctx, g, {}, LQCD_F64, U->recon, prm->kappa, prm->mu};
+  HalfField Phi2 = f64_half(phi2.p, Vh), Psi2 = f64_half(psi2.p, Vh), X2h = f64_half(X2.p, Vh);
   int cg_iters = 0;
-  // X = (Mhat^+ Mhat)^-1 phi at the current links, solved once per field
-  uint64_t x_version = 0;
+  // X = (W^+ W)^-1 phi (W = Mhat(mu1)) at the current links, once per field
+  uint64_t x_version = 0, x2_version = 0;
+  double S2_cur = 0.0;
   auto solve_x = [&]() -> lqcd_status {
     if (x_version == U->version) return LQCD_OK;
     lqcd_cg_stats st;
     std::memset(&st, 0, sizeof(st));
-    LQCD_TRY(solve_normal(ctx, U, Phi, Xh, prm->kappa, prm->mu, prm->cg, &st));
+    LQCD_TRY(solve_normal(ctx, U, Phi, Xh, prm->kappa, mu1, prm->cg, &st));
     cg_iters += st.iters;
     x_version = U->version;
     return LQCD_OK;
   };
+  // the ratio pseudofermion: psi2 = W^+ phi2, X2 = (Mhat^+ Mhat)^-1 psi2
+  auto solve_x2 = [&]() -> lqcd_status {
+    if (x2_version == U->version) return LQCD_OK;
+    lqcd_cg_stats st;
+    std::memset(&st, 0, sizeof(st));
+    LQCD_TRY(ratio_solve(ctx, U, Phi2, Psi2, X2h, prm->kappa, prm->mu, prm->mu2, prm->cg, &st, &S2_cur));
+    cg_iters += st.iters;
+    x2_version = U->version;
+    return LQCD_OK;
+  };
   // Momentum kicks are collected and applied when the links are about to
-  // change (or at the end): P -= wg dS_g/dw + wf dS_f/dw, one force
-  // evaluation per field and kind.
-  double wg = 0.0, wf = 0.0;
+  // change (or at the end): P -= w[k] dS_k/dw for the gauge force (k = 0),
+  // the first pseudofermion (k = 1) and the ratio (k = 2); one evaluation
+  // per field and kind.
+  double w[3] = {0.0, 0.0, 0.0};
   auto flush = [&]() -> lqcd_status {
-    if (wg != 0.0) {
+    if (w[0] != 0.0) {
       LQCD_TRY(gauge_force_raw(ctx, U, prm->beta, prm->c1, prm->force_prec, (double *)F.p));
-      LQCD_TRY(momenta_update_raw(ctx, V, (double *)P.p, (const double *)F.p, wg));
-      wg = 0.0;
+      LQCD_TRY(momenta_update_raw(ctx, V, (double *)P.p, (const double *)F.p, w[0]));
     }
-    if (wf != 0.0 && fermions) {
+    if (w[1] != 0.0 && fermions) {
       LQCD_TRY(solve_x());
-      LQCD_TRY(fermion_force_from_X(ctx, U, Xh, prm->kappa, prm->mu, (double *)F.p));
-      LQCD_TRY(momenta_update_raw(ctx, V, (double *)P.p, (const double *)F.p, wf));
+      LQCD_TRY(fermion_force_from_X(ctx, U, Xh, prm->kappa, mu1, (double *)F.p));
+      LQCD_TRY(momenta_update_raw(ctx, V, (double *)P.p, (const double *)F.p, w[1]));
     }
-    wf = 0.0;
+    if (w[2] != 0.0 && hasen) {
+      LQCD_TRY(solve_x2());
+      LQCD_TRY(ratio_force(ctx, U, Phi2, X2h, prm->kappa, prm->mu, prm->mu2, (double *)F.p));
+      LQCD_TRY(momenta_update_raw(ctx, V, (double *)P.p, (const double *)F.p, w[2]));
+    }
+    w[0] = w[1] = w[2] = 0.0;
     return LQCD_OK;
   };
   auto drift = [&](double h) -> lqcd_status {
     LQCD_TRY(flush());
     return gauge_update_raw(ctx, U, (const double *)P.p, h);
   };
-  // inner 2MN integration of the gauge force over time h
-  auto inner = [&](double h) -> lqcd_status {
-    const double d = h / prm->nsteps_gauge;
-    for (int j = 0; j < prm->nsteps_gauge; j++) {
-      wg += lam * d;
-      LQCD_TRY(drift(0.5 * d));
-      wg += (1.0 - 2.0 * lam) * d;
-      LQCD_TRY(drift(0.5 * d));
-      wg += lam * d;
+  // 2MN on nested time scales: level 0 is the outermost force; each of its
+  // position updates over time h is the 2MN integration of the next level
+  // over h, down to the gauge force, whose position update is the link update
+  int kinds[3], steps[3], nlev = 0;
+  if (hasen) {
+    kinds[nlev] = 2;
+    steps[nlev++] = prm->nsteps;
+    kinds[nlev] = 1;
+    steps[nlev++] = prm->nsteps_mid > 0 ? prm->nsteps_mid : 1;
+  } else if (fermions) {
+    kinds[nlev] = 1;
+    steps[nlev++] = prm->nsteps;
+  }
+  kinds[nlev] = 0;
+  steps[nlev++] = (fermions || two_mn) ? prm->nsteps_gauge : prm->nsteps;
+  // pure gauge: the gauge scale alone, with the step size it has under an
+  // outer scale of nsteps steps (two position updates of e/2 each)
+  if (!fermions) steps[0] = two_mn ? 2 * prm->nsteps * prm->nsteps_gauge : prm->nsteps;
+  std::function<lqcd_status(int, double)> integrate = [&](int lev, double h) -> lqcd_status {
+    const double d = h / steps[lev];
+    auto sub = [&](double t) -> lqcd_status { return lev + 1 < nlev ? integrate(lev + 1, t) : drift(t); };
+    for (int j = 0; j < steps[lev]; j++) {
+      w[kinds[lev]] += lam * d;
+      LQCD_TRY(sub(0.5 * d));
+      w[kinds[lev]] += (1.0 - 2.0 * lam) * d;
+      LQCD_TRY(sub(0.5 * d));
+      w[kinds[lev]] += lam * d;
     }
     return LQCD_OK;
   };
@@ -425,14 +536,34 @@ extern "C" int lqcd_hmc_trajectory(lqcd_ctx *ctx, lqcd_gauge *U, const lqcd_hmc_
     *S = 0.0;
     if (!fermions) return LQCD_OK;
     LQCD_TRY(solve_x());
-    return half_redot(ctx, Vh, Phi, Xh, S);
+    LQCD_TRY(half_redot(ctx, Vh, Phi, Xh, S));
+    if (hasen) {
+      LQCD_TRY(solve_x2());
+      *S += S2_cur;
+    }
+    return LQCD_OK;
   };
   double Sf0 = 0.0, Sf1 = 0.0, Sg0, Sg1, K0, K1;
   if (fermions) {
+    // phi = W^+ eta with W = Mhat(mu1)
+    Op op1{ctx, g, {}, LQCD_F64, U->recon, prm->kappa, mu1};
+    LQCD_TRY(gauge_view(ctx, U, LQCD_F64, U->recon, &op1.U));
     LQCD_TRY(gaussian_spinor_raw(ctx, g, eta.p, 0, seed, traj));
-    LQCD_TRY(gauge_view(ctx, U, LQCD_F64, U->recon, &op.U));
-    LQCD_TRY(apply_schur(op, f64_half(eta.p, Vh), Phi, f64_half(tmp.p, Vh), 0, true, nullptr, nullptr,
+    LQCD_TRY(apply_schur(op1, f64_half(eta.p, Vh), Phi, f64_half(tmp.p, Vh), 0, true, nullptr, nullptr,
                          nullptr));
+    if (hasen) {
+      // phi2 = W^-+ Mhat^+ eta2 = W (W^+ W)^-1 Mhat^+ eta2, eta2 from the stream of seed ^ 0x9E3779B97F4A7C15
+      Op op{ctx, g, {}, LQCD_F64, U->recon, prm->kappa, prm->mu};
+      op.U = op1.U;
+      LQCD_TRY(gaussian_spinor_raw(ctx, g, eta.p, 0, seed ^ 0x9E3779B97F4A7C15ull, traj));
+      LQCD_TRY(apply_schur(op, f64_half(eta.p, Vh), Psi2, f64_half(tmp.p, Vh), 0, true, nullptr, nullptr,
+                           nullptr));
+      lqcd_cg_stats st;
+      std::memset(&st, 0, sizeof(st));
+      LQCD_TRY(solve_normal(ctx, U, Psi2, X2h, prm->kappa, prm->mu2, prm->cg, &st));
+      cg_iters += st.iters;
+      LQCD_TRY(apply_schur(op1, X2h, Phi2, f64_half(tmp.p, Vh), 0, false, nullptr, nullptr, nullptr));
+    }
   }
   LQCD_TRY(sumsq_raw(ctx, (const double *)P.p, nP, &K0));
   K0 *= 0.5;
@@ -441,20 +572,16 @@ extern "C" int lqcd_hmc_trajectory(lqcd_ctx *ctx, lqcd_gauge *U, const lqcd_hmc_
   const double H0 = K0 + Sg0 + Sf0;
   const double e = prm->tau / prm->nsteps;
   if (two_mn) {
-    for (int step = 0; step < prm->nsteps; step++) {
-      wf += lam * e;
-      LQCD_TRY(inner(0.5 * e));
-      wf += (1.0 - 2.0 * lam) * e;
-      LQCD_TRY(inner(0.5 * e));
-      wf += lam * e;
-    }
+    LQCD_TRY(integrate(0, prm->tau));
   } else {
     for (int step = 0; step < prm->nsteps; step++) {
-      wg += 0.5 * e;
-      wf += 0.5 * e;
+      w[0] += 0.5 * e;
+      w[1] += 0.5 * e;
+      w[2] += 0.5 * e;
       LQCD_TRY(drift(e));
-      wg += 0.5 * e;
-      wf += 0.5 * e;
+      w[0] += 0.5 * e;
+      w[1] += 0.5 * e;
+      w[2] += 0.5 * e;
     }
   }
   LQCD_TRY(flush());

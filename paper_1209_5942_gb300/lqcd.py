@@ -80,7 +80,8 @@ class lqcd_hmc_params(ctypes.Structure):
                 ("tau", ctypes.c_double), ("nsteps", ctypes.c_int32), ("nf", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("traj", ctypes.c_uint32), ("integrator", ctypes.c_int32),
                 ("c1", ctypes.c_double), ("nsteps_gauge", ctypes.c_int32), ("force_prec", ctypes.c_int32),
-                ("lam", ctypes.c_double), ("cg", lqcd_cg_params)]
+                ("lam", ctypes.c_double), ("mu2", ctypes.c_double), ("nsteps_mid", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("cg", lqcd_cg_params)]
 
 
 class lqcd_hmc_stats(ctypes.Structure):
@@ -134,6 +135,9 @@ SIGNATURES = [
     ("lqcd_fermion_force", _i, [_vp, _vp, lqcd_field, _vp, ctypes.POINTER(lqcd_field),
                                 ctypes.POINTER(lqcd_geom), _d, _d, ctypes.POINTER(lqcd_cg_params),
                                 ctypes.POINTER(lqcd_cg_stats), ctypes.POINTER(_d)]),
+    ("lqcd_fermion_force_ratio", _i, [_vp, _vp, lqcd_field, _vp, ctypes.POINTER(lqcd_geom), _d, _d, _d,
+                                      ctypes.POINTER(lqcd_cg_params), ctypes.POINTER(lqcd_cg_stats),
+                                      ctypes.POINTER(_d)]),
     ("lqcd_gauge_force", _i, [_vp, _vp, _d, _d, _i, _vp, ctypes.POINTER(_d)]),
     ("lqcd_plaquette", _i, [_vp, _vp, ctypes.POINTER(_d)]),
     ("lqcd_heatbath_sweep", _i, [_vp, _vp, _d, ctypes.c_uint64, ctypes.c_uint64, _i, _i]),
@@ -260,8 +264,7 @@ class Context:
         self.device = device
         if torch_allocator:
             self._allocator = TorchAllocator(device, stream)
-            self.check(lib().lqcd_set_allocator(self._h, self._allocator.alloc_fn, self._allocator.free_fn,
-                                                None))
+            lqcd_set_allocator(self, self._allocator.alloc_fn, self._allocator.free_fn)
 
     @property
     def handle(self):
@@ -328,6 +331,14 @@ def lqcd_create(device: int = 0, stream=None) -> Context:
 def lqcd_set_autotune(ctx: Context, enable=True, cache_path=None):
     ctx.check(lib().lqcd_set_autotune(ctx.handle, int(bool(enable)),
                                       cache_path.encode() if cache_path else None))
+
+
+def lqcd_set_allocator(ctx: Context, alloc_fn=None, free_fn=None):
+    """Sets the caller's (alloc, free) pair (ctypes callbacks of the lqcd_alloc_fn /
+    lqcd_free_fn types, e.g. a TorchAllocator's); None passes a NULL pointer."""
+    a = alloc_fn if alloc_fn is not None else _ALLOC_FN()
+    f = free_fn if free_fn is not None else _FREE_FN()
+    ctx.check(lib().lqcd_set_allocator(ctx.handle, a, f, None))
 
 
 def lqcd_set_launch_choice(ctx: Context, choice: int):
@@ -441,6 +452,18 @@ def lqcd_fermion_force(ctx: Context, U: Gauge, phi: lqcd_field, dSdw: torch.Tens
     return S.value, st.as_dict()
 
 
+def lqcd_fermion_force_ratio(ctx: Context, U: Gauge, phi2: lqcd_field, dSdw: torch.Tensor, kappa, mu, mu2,
+                             params: lqcd_cg_params):
+    """Returns (S2, stats); dSdw receives dS2/domega of the mass-preconditioning ratio."""
+    st = lqcd_cg_stats()
+    S = _d(0.0)
+    g = U.geom
+    ctx.check(lib().lqcd_fermion_force_ratio(ctx.handle, U.handle, phi2, _vp(dSdw.data_ptr()), ctypes.byref(g),
+                                             kappa, mu, mu2, ctypes.byref(params), ctypes.byref(st),
+                                             ctypes.byref(S)))
+    return S.value, st.as_dict()
+
+
 def lqcd_gauge_force(ctx: Context, U: Gauge, beta, dSdw: torch.Tensor, want_action=True, c1=0.0,
                      prec=LQCD_F64):
     S = _d(0.0)
@@ -499,12 +522,14 @@ TLSYM_C1 = -1.0 / 12.0
 
 
 def hmc_params(beta, kappa, mu, tau=1.0, nsteps=20, nf=1, seed=1, traj=0, cg=None,
-               integrator=LQCD_LEAPFROG, c1=0.0, nsteps_gauge=1, lam=0.0, force_prec=LQCD_F64):
+               integrator=LQCD_LEAPFROG, c1=0.0, nsteps_gauge=1, lam=0.0, force_prec=LQCD_F64, mu2=0.0,
+               nsteps_mid=1):
     p = lqcd_hmc_params()
     p.beta, p.kappa, p.mu, p.tau = beta, kappa, mu, tau
     p.nsteps, p.nf, p.seed, p.traj = nsteps, nf, seed, traj
     p.integrator, p.c1, p.nsteps_gauge, p.lam = integrator, c1, nsteps_gauge, lam
     p.force_prec = force_prec
+    p.mu2, p.nsteps_mid = mu2, nsteps_mid
     p.cg = cg if cg is not None else cg_params(tol=1e-10, outer_prec=LQCD_DF64,
                                                inner_prec=LQCD_F32)
     return p

@@ -53,8 +53,9 @@ def test_torch_caching_allocator_backs_the_library():
 
 def test_allocator_pair_must_be_complete():
     ctx = lqcd.Context(0)
+    ta = lqcd.TorchAllocator(0, torch.cuda.current_stream())
     with pytest.raises(lqcd.LqcdError) as e:
-        ctx.check(lqcd.lib().lqcd_set_allocator(ctx.handle, lqcd.TorchAllocator(0, torch.cuda.current_stream()).alloc_fn,
-                                                None, None))
+        lqcd.lqcd_set_allocator(ctx, ta.alloc_fn, None)
     assert e.value.status == lqcd.LQCD_ERR_INVALID
-    ctx.check(lqcd.lib().lqcd_set_allocator(ctx.handle, None, None, None))  # back to the default
+    lqcd.lqcd_set_allocator(ctx, None, None)  # back to the default
+    ctx.close()

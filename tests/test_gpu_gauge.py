@@ -368,3 +368,51 @@ def test_heatbath_rejects_other_precisions(ctx):
     with pytest.raises(lqcd.LqcdError) as e:
         lqcd.lqcd_heatbath_sweep(ctx, G, 5.7, 1, 0, prec=lqcd.LQCD_BF16S)
     assert e.value.status == lqcd.LQCD_ERR_INVALID
+
+
+def test_ratio_force_matches_oracle(ctx, oracle):
+    """Mass-preconditioning ratio S2 = phi2^+ W (Mhat^+ Mhat)^-1 W^+ phi2,
+    W = Mhat(mu2): action and force against the oracle's."""
+    L = (4, 4, 2, 4)
+    V = inputs.volume(L)
+    kappa, mu, mu2 = 0.14, 0.05, 0.3
+    U = inputs.random_gauge(L, "near", seed=46, eps=0.4)
+    G = lqcd.lqcd_gauge_import(ctx, dev(U), L)
+    ev = ~oracle.parity_mask(L)
+    phi2 = inputs.gaussian_spinor(L, 47) * ev[:, None, None]
+    keep, fphi = _even_half_field(ctx, L, phi2)
+    F = torch.zeros((4, V, 8), dtype=torch.float64, device="cuda")
+    prm = lqcd.cg_params(tol=1e-13, max_iter=50000)
+    S2, st = lqcd.lqcd_fermion_force_ratio(ctx, G, fphi, F, kappa, mu, mu2, prm)
+    Sref, X = oracle.hasenbusch_action(U, phi2, L, kappa, mu, mu2, tol=1e-14)
+    ref = oracle.hasenbusch_dSdw(U, phi2, X, L, kappa, mu, mu2)
+    assert abs(S2 - Sref) < 1e-10 * abs(Sref)
+    assert relerr(host(F), ref) < 1e-9
+
+
+def test_hmc_mass_preconditioning(ctx, oracle):
+    """HMC with mass preconditioning on three 2MN time scales (ratio, W, gauge):
+    the start Hamiltonian is K + S_g + eta1^+ eta1 + eta2^+ eta2 (both
+    pseudofermions drawn so), and dH is second order in the step size."""
+    L = (4, 4, 2, 4)
+    beta, kappa, mu, mu2, c1 = 3.9, 0.14, 0.05, 0.25, lqcd.TLSYM_C1
+    U = inputs.random_gauge(L, "near", seed=48, eps=0.3)
+    seed, traj = 91, 2
+    dHs = {}
+    for n in (2, 4):
+        G = lqcd.lqcd_gauge_import(ctx, dev(U), L)
+        prm = lqcd.hmc_params(beta, kappa, mu, tau=0.5, nsteps=n, nf=1, seed=seed, traj=traj,
+                              cg=lqcd.cg_params(tol=1e-13, max_iter=50000), integrator=lqcd.LQCD_2MN,
+                              c1=c1, nsteps_gauge=2, mu2=mu2, nsteps_mid=2)
+        st = lqcd.lqcd_hmc_trajectory(ctx, G, prm)
+        dHs[n] = st["dH"]
+        G.free()
+    ev = ~oracle.parity_mask(L)
+    eta1 = oracle.gaussian_spinor(L, seed, traj) * ev[:, None, None]
+    eta2 = oracle.gaussian_spinor(L, seed ^ 0x9E3779B97F4A7C15, traj) * ev[:, None, None]
+    P0 = oracle.momenta(L, seed, traj)
+    H0 = (0.5 * np.sum(P0 ** 2) + oracle.gauge_action_sym(U, L, beta, c1) + np.vdot(eta1, eta1).real
+          + np.vdot(eta2, eta2).real)
+    assert abs(st["H0"] - H0) < 1e-9 * abs(H0)
+    assert abs(dHs[2]) < 1.0
+    assert 3.0 < dHs[2] / dHs[4] < 5.3, dHs
