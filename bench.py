@@ -650,6 +650,19 @@ def run_config(args):
                                                                    nf=1, seed=6006, traj=t, cg=cg))
             (therm if t < args.therm else trajs).append(st)
         secs = [s["seconds"] for s in trajs[1:]] or [trajs[0]["seconds"]]
+        # the same ensemble continued with 2MN on three time scales and mass
+        # preconditioning (mu2 = 10 mu): ratio force 5 steps, W force 2, gauge 2
+        imp = []
+        for t in range(args.trajs):
+            imp.append(lqcd.lqcd_hmc_trajectory(ctx, G, lqcd.hmc_params(
+                beta, kappa, mu, tau=1.0, nsteps=5, nf=1, seed=6007, traj=t, cg=cg,
+                integrator=lqcd.LQCD_2MN, nsteps_gauge=2, mu2=10 * mu, nsteps_mid=2)))
+        isecs = [s["seconds"] for s in imp[1:]] or [imp[0]["seconds"]]
+        improved = {"integrator": "2MN ratio/W/gauge = 5/2/2 steps, mu2 = 10 mu",
+                    "s_per_trajectory": statistics.median(isecs), "dH": [s["dH"] for s in imp],
+                    "acceptance": sum(s["accepted"] for s in imp) / len(imp),
+                    "cg_iters_per_trajectory": [s["cg_iters"] for s in imp],
+                    "plaquette": [s["plaquette"] for s in imp]}
         config_line("Nf=2 HMC", None,
                     {"s_per_trajectory": statistics.median(secs),
                      "dH": [s["dH"] for s in trajs], "accepted": [s["accepted"] for s in trajs],
@@ -659,7 +672,8 @@ def run_config(args):
                      "plaquette": [s["plaquette"] for s in trajs], "plaquette_after_heatbath": plaq0,
                      "heatbath_s": thb, "thermalisation_trajectories": len(therm),
                      "thermalisation_dH": [s["dH"] for s in therm],
-                     "thermalisation_plaquette": [s["plaquette"] for s in therm]},
+                     "thermalisation_plaquette": [s["plaquette"] for s in therm],
+                     "mass_preconditioned_2mn": improved},
                     {"workload": f"16^3x32, beta=5.6, kappa=0.16, 2 kappa mu=0.005, {args.sweeps} "
                                  "heatbath sweeps from cold, leapfrog tau=1 20 steps, "
                                  "F32-inner/DF64 CG to 1e-10 per force"})

@@ -348,9 +348,10 @@ int lqcd_plaquette(lqcd_ctx *ctx, const lqcd_gauge *U, double *plaq_out);
  * replaced by its reflection v = (w^+/k)^2 (microcanonical: the action is
  * unchanged).  prec = LQCD_F64 updates the FP64 field in place (the SU(2)
  * left multiplications keep it unitary to rounding); prec = LQCD_F32 runs
- * the same sweep in single precision on the field's FP32 copy and writes the
- * result back into the FP64 field, reunitarised in FP64 (Sec. 5.1 measures
- * the single-precision kernels).  Other prec: LQCD_ERR_INVALID.
+ * the same sweep in single precision on the field's FP32 copy (12-real links
+ * with the third row rebuilt, Sec. 4.1, if the field was imported with
+ * recon = 12) and writes the result back into the FP64 field, reunitarised in
+ * FP64 (Sec. 5.1 measures the single-precision kernels).  Other prec: LQCD_ERR_INVALID.
  * Asynchronous. */
 int lqcd_heatbath_sweep(lqcd_ctx *ctx, lqcd_gauge *U, double beta, uint64_t seed,
                         uint64_t sweep_idx, int n_or, int prec);

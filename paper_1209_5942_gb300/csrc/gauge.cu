@@ -696,20 +696,26 @@ LQCD_DEV M3s sdag(const M3s &u) {
     for (int j = 0; j < 3; j++) d.m[3 * i + j] = conj(u.m[3 * j + i]);
   return d;
 }
+// FP32 links with 18 reals, or 12 (REC12, Sec. 4.1: the paper suggests it for
+// the heatbath too) with the third row rebuilt on load and not stored
+template <int RECON>
 LQCD_DEV M3s load_link_s(const GaugeView &Uf, const Pos &s, int mu) {
   M3s u;
-  LinkIO<LQCD_F32, 18>::load(Uf, s.p, mu, s.cb, u.m);
+  LinkIO<LQCD_F32, RECON>::load(Uf, s.p, mu, s.cb, u.m);
+  if (RECON == 12) reconstruct_row2(u.m);
   return u;
 }
+template <int RECON>
 LQCD_DEV void store_link_s(const GaugeView &Uf, const Pos &s, int mu, const M3s &u) {
   char *base = (char *)Uf.ptr + s.p * Uf.parity_stride + mu * Uf.mu_stride;
   float4 *b = (float4 *)base;
 #pragma unroll
-  for (int k = 0; k < 4; k++)
+  for (int k = 0; k < (RECON == 18 ? 4 : 3); k++)
     b[(size_t)k * Uf.Vh + s.cb] = make_float4(u.m[2 * k].re, u.m[2 * k].im, u.m[2 * k + 1].re, u.m[2 * k + 1].im);
-  ((float2 *)(base + (size_t)4 * Uf.Vh * 16))[s.cb] = make_float2(u.m[8].re, u.m[8].im);
+  if (RECON == 18) ((float2 *)(base + (size_t)4 * Uf.Vh * 16))[s.cb] = make_float2(u.m[8].re, u.m[8].im);
 }
 // staple sum as staple(), in FP32
+template <int RECON>
 LQCD_DEV M3s staple_s(const GaugeView &Uf, const Geom &g, const int c[4], int mu) {
   M3s A;
 #pragma unroll
@@ -724,13 +730,13 @@ LQCD_DEV M3s staple_s(const GaugeView &Uf, const Geom &g, const int c[4], int mu
     coords_shift(g, cmn, nu, -1);
     coords_shift(g, cpmmn, nu, -1);
     // upper: U_nu(x+mu) U_mu(x+nu)^+ U_nu(x)^+
-    M3s t = smul(smul(load_link_s(Uf, at(g, cpm), nu), sdag(load_link_s(Uf, at(g, cpn), mu))),
-                 sdag(load_link_s(Uf, at(g, c), nu)));
+    M3s t = smul(smul(load_link_s<RECON>(Uf, at(g, cpm), nu), sdag(load_link_s<RECON>(Uf, at(g, cpn), mu))),
+                 sdag(load_link_s<RECON>(Uf, at(g, c), nu)));
 #pragma unroll
     for (int k = 0; k < 9; k++) A.m[k] = A.m[k] + t.m[k];
     // lower: U_nu(x+mu-nu)^+ U_mu(x-nu)^+ U_nu(x-nu)
-    t = smul(sdag(smul(load_link_s(Uf, at(g, cmn), mu), load_link_s(Uf, at(g, cpmmn), nu))),
-             load_link_s(Uf, at(g, cmn), nu));
+    t = smul(sdag(smul(load_link_s<RECON>(Uf, at(g, cmn), mu), load_link_s<RECON>(Uf, at(g, cpmmn), nu))),
+             load_link_s<RECON>(Uf, at(g, cmn), nu));
 #pragma unroll
     for (int k = 0; k < 9; k++) A.m[k] = A.m[k] + t.m[k];
   }
@@ -772,6 +778,7 @@ LQCD_DEV bool sample_y0_f(float b, uint32_t c0, uint32_t c1, uint32_t c2, uint64
   return false;
 }
 
+template <int RECON>
 __global__ void __launch_bounds__(128) heatbath_f32_kernel(GaugeView Uf, Geom g, int mu, int par, float beta,
                                                            uint64_t seed, uint32_t sweep, int overrelax,
                                                            unsigned int *fail_count) {
@@ -780,8 +787,8 @@ __global__ void __launch_bounds__(128) heatbath_f32_kernel(GaugeView Uf, Geom g,
   Site st = site_of(g, par, cb);
   int c[4] = {st.x, st.y, st.z, st.t};
   Pos s = at(g, c);
-  const M3s A = staple_s(Uf, g, c, mu);
-  M3s u = load_link_s(Uf, s, mu);
+  const M3s A = staple_s<RECON>(Uf, g, c, mu);
+  M3s u = load_link_s<RECON>(Uf, s, mu);
   const int SG[3][2] = {{0, 1}, {1, 2}, {0, 2}};
   unsigned fails = 0;
   for (int sg = 0; sg < 3; sg++) {
@@ -836,18 +843,20 @@ __global__ void __launch_bounds__(128) heatbath_f32_kernel(GaugeView Uf, Geom g,
       u.m[3 * j + q] = rj[q];
     }
   }
-  store_link_s(Uf, s, mu, u);
+  store_link_s<RECON>(Uf, s, mu, u);
   if (fails) atomicAdd(fail_count, fails);
 }
 
-// FP32 copy (18 reals) -> FP64 master
+// FP32 copy -> FP64 master (REC12: third row rebuilt in FP32)
+template <int RECON>
 __global__ void f32_to_master_kernel(GaugeView Uf, double2 *m, int Vh) {
   const size_t nl = (size_t)2 * 4 * Vh;
   const size_t l = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (l >= nl) return;
   const int blk = (int)(l / Vh), cb = (int)(l % Vh);  // blk = parity * 4 + mu
   Cx<float> u[9];
-  LinkIO<LQCD_F32, 18>::load(Uf, blk >> 2, blk & 3, cb, u);
+  LinkIO<LQCD_F32, RECON>::load(Uf, blk >> 2, blk & 3, cb, u);
+  if (RECON == 12) reconstruct_row2(u);
 #pragma unroll
   for (int k = 0; k < 9; k++) m[((size_t)blk * 9 + k) * Vh + cb] = make_double2(u[k].re, u[k].im);
 }
@@ -1091,16 +1100,23 @@ lqcd_status reunitarize_raw(lqcd_ctx *ctx, lqcd_gauge *U);
 // FP32 sweep: on the FP32 copy, then back into the FP64 field, reunitarised
 lqcd_status heatbath_f32_raw(lqcd_ctx *ctx, lqcd_gauge *U, double beta, uint64_t seed, uint64_t sweep, int n_or,
                              unsigned int *fail_dev) {
+  // the link format follows the field's (18 reals, or REC12 if imported so)
+  const bool r12 = U->recon == 12;
   GaugeView Uf;
-  LQCD_TRY(gauge_view(ctx, U, LQCD_F32, 18, &Uf));
+  LQCD_TRY(gauge_view(ctx, U, LQCD_F32, r12 ? 12 : 18, &Uf));
   for (int pass = 0; pass <= n_or; pass++)
     for (int mu = 0; mu < 4; mu++)
       for (int par = 0; par < 2; par++) {
-        heatbath_f32_kernel<<<nblk(U->g.Vh), 128, 0, ctx->stream>>>(Uf, U->g, mu, par, (float)beta, seed,
-                                                                    (uint32_t)sweep, pass > 0 ? 1 : 0, fail_dev);
+        if (r12)
+          heatbath_f32_kernel<12><<<nblk(U->g.Vh), 128, 0, ctx->stream>>>(
+              Uf, U->g, mu, par, (float)beta, seed, (uint32_t)sweep, pass > 0 ? 1 : 0, fail_dev);
+        else
+          heatbath_f32_kernel<18><<<nblk(U->g.Vh), 128, 0, ctx->stream>>>(
+              Uf, U->g, mu, par, (float)beta, seed, (uint32_t)sweep, pass > 0 ? 1 : 0, fail_dev);
         LQCD_CUDA(ctx, cudaGetLastError());
       }
-  f32_to_master_kernel<<<nblk(8L * U->g.Vh), 128, 0, ctx->stream>>>(Uf, (double2 *)U->master, U->g.Vh);
+  if (r12) f32_to_master_kernel<12><<<nblk(8L * U->g.Vh), 128, 0, ctx->stream>>>(Uf, (double2 *)U->master, U->g.Vh);
+  else f32_to_master_kernel<18><<<nblk(8L * U->g.Vh), 128, 0, ctx->stream>>>(Uf, (double2 *)U->master, U->g.Vh);
   LQCD_CUDA(ctx, cudaGetLastError());
   U->version++;
   return reunitarize_raw(ctx, U);

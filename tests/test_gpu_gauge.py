@@ -308,12 +308,13 @@ def test_hmc_2mn_pure_gauge_scaling(ctx, oracle):
     assert 3.0 < dHs[2] / dHs[4] < 5.3, dHs
 
 
-def test_f32_heatbath_strong_coupling(ctx):
-    """The single-precision heatbath (Sec. 5.1 measures the FP32 kernels):
-    <P> = beta/18 + beta^2/216 at beta = 0.3."""
+@pytest.mark.parametrize("recon", [18, 12])
+def test_f32_heatbath_strong_coupling(ctx, recon):
+    """The single-precision heatbath (Sec. 5.1 measures the FP32 kernels), with
+    18-real and REC12 links: <P> = beta/18 + beta^2/216 at beta = 0.3."""
     L = (8, 8, 8, 8)
     beta = 0.3
-    G = lqcd.lqcd_gauge_import(ctx, dev(inputs.random_gauge(L, "cold")), L)
+    G = lqcd.lqcd_gauge_import(ctx, dev(inputs.random_gauge(L, "cold")), L, recon=recon)
     vals = []
     for s in range(80):
         lqcd.lqcd_heatbath_sweep(ctx, G, beta, 78, s, prec=lqcd.LQCD_F32)
