@@ -216,8 +216,7 @@ template <int P>
 // (each operand has its own right-hand-side stride: a for out, ax for x, ay for y)
 __global__ void __launch_bounds__(128) lincomb_kernel(VecArgs a, VecArgs ax, VecArgs ay, void *out,
                                                       float *os, const void *x, const float *xsc,
-                                                      const void *y, const float *ysc, HostC ca_up,
-                                                      HostC ca_dn, HostC cb_up, HostC cb_dn, int unit,
+                                                      const void *y, const float *ysc, Coef4 co, int unit,
                                                       double *partials) {
   using R = typename SpinorIO<P>::R;
   __shared__ double sh[8];
@@ -234,7 +233,7 @@ __global__ void __launch_bounds__(128) lincomb_kernel(VecArgs a, VecArgs ax, Vec
         for (int k = 0; k < 12; k++) X[k] = unit > 0 ? X[k] + Y[k] : X[k] - Y[k];
       }
     } else {
-      const Cx<R> au = cfrom<R>(ca_up), ad = cfrom<R>(ca_dn), bu = cfrom<R>(cb_up), bd = cfrom<R>(cb_dn);
+      const Cx<R> au = coef_of<R>(co, 0), ad = coef_of<R>(co, 1), bu = coef_of<R>(co, 2), bd = coef_of<R>(co, 3);
 #pragma unroll
       for (int k = 0; k < 12; k++) {
         Cx<R> o = (k < 6 ? au : ad) * X[k];
@@ -396,7 +395,7 @@ lqcd_status lincomb(lqcd_ctx *ctx, int Vh, const HalfField &out, const HalfField
   return dispatch_prec(ctx, out.prec, [&](auto P) {
     lincomb_kernel<decltype(P)::value><<<grid, 128, 0, ctx->stream>>>(
         a, ax, ay, out.ptr, out.scale, x.ptr, x.scale, y ? y->ptr : nullptr, y ? y->scale : nullptr,
-        ca_up, ca_dn, cb_up, cb_dn, unit, partials);
+        make_coef4(ca_up, ca_dn, cb_up, cb_dn), unit, partials);
   });
 }
 

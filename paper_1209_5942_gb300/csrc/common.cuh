@@ -47,17 +47,19 @@ LQCD_DEV Site site_of(const Geom& g, int p, int cb) {
   return s;
 }
 
-// checkerboard index of the neighbour x + dir*mu_hat (dir = +1 / -1)
+// checkerboard index of the neighbour x + dir*mu_hat (dir = +1 / -1); the
+// periodic wrap is a compare, and a step along y, z or t moves the row r by
+// 1, Ly or Ly*Lz (minus the extent times that across the boundary)
 LQCD_DEV int neighbour_cb(const Geom& g, const Site& s, int mu, int dir) {
-  int x = s.x, y = s.y, z = s.z, t = s.t;
-  switch (mu) {
-    case 0: x = (x + dir + g.L[0]) % g.L[0]; break;
-    case 1: y = (y + dir + g.L[1]) % g.L[1]; break;
-    case 2: z = (z + dir + g.L[2]) % g.L[2]; break;
-    default: t = (t + dir + g.L[3]) % g.L[3]; break;
+  if (mu == 0) {
+    const int x = dir > 0 ? (s.x + 1 == g.L[0] ? 0 : s.x + 1) : (s.x == 0 ? g.L[0] - 1 : s.x - 1);
+    return s.r * g.Lh0 + (x >> 1);
   }
-  int r = y + g.L[1] * (z + g.L[2] * t);
-  return r * g.Lh0 + (x >> 1);
+  const int c = mu == 1 ? s.y : mu == 2 ? s.z : s.t;
+  const int n = g.L[mu];
+  const int stride = mu == 1 ? 1 : mu == 2 ? g.L[1] : g.L[1] * g.L[2];
+  const int step = dir > 0 ? (c + 1 == n ? 1 - n : 1) : (c == 0 ? n - 1 : -1);
+  return (s.r + step * stride) * g.Lh0 + (s.x >> 1);
 }
 
 LQCD_DEV long lexi_index(const Geom& g, const Site& s) {
@@ -236,6 +238,29 @@ template <> LQCD_DEV float from_double<float>(double v) { return (float)v; }
 template <> LQCD_DEV df from_double<df>(double v) { return df_from_double(v); }
 template <class R> LQCD_DEV Cx<R> cfrom(HostC c) { return {from_double<R>(c.re), from_double<R>(c.im)}; }
 
+// Four complex coefficients prepared on the host in each arithmetic a kernel
+// may compute in (the same roundings as from_double), so that no thread
+// converts them: the double -> float-float split runs on the FP64 pipe.
+struct Coef4 {
+  HostC d[4];
+  Cx<float> f[4];
+  Cx<df> w[4];
+};
+inline Coef4 make_coef4(HostC a, HostC b, HostC c, HostC e) {
+  Coef4 r;
+  const HostC in[4] = {a, b, c, e};
+  for (int i = 0; i < 4; i++) {
+    r.d[i] = in[i];
+    r.f[i] = {(float)in[i].re, (float)in[i].im};
+    r.w[i] = {df_from_double(in[i].re), df_from_double(in[i].im)};
+  }
+  return r;
+}
+template <class R> LQCD_DEV Cx<R> coef_of(const Coef4 &c, int i);
+template <> LQCD_DEV Cx<double> coef_of<double>(const Coef4 &c, int i) { return {c.d[i].re, c.d[i].im}; }
+template <> LQCD_DEV Cx<float> coef_of<float>(const Coef4 &c, int i) { return c.f[i]; }
+template <> LQCD_DEV Cx<df> coef_of<df>(const Coef4 &c, int i) { return c.w[i]; }
+
 LQCD_DEV double to_double(double v) { return v; }
 LQCD_DEV double to_double(float v) { return (double)v; }
 LQCD_DEV double to_double(df v) { return df_to_double(v); }
@@ -318,19 +343,34 @@ LQCD_DEV Cx<df> cnormalise(Cx<df> a) {
   return {fast_two_sum(a.re.hi, a.re.lo), fast_two_sum(a.im.hi, a.im.lo)};
 }
 
-// |v|^2 of one site's n complex components, returned as a double.  FP64 and
-// float-float values are squared and summed in FP64.  FP32 values (the
-// sloppy formats, whose components carry 24-bit mantissas at best) are
-// squared and summed in FP32 with FMAs, relative error <= 2n u_32, and
-// converted once: the per-site FP64 conversions and products would otherwise
-// keep GB300's FP64 pipe (1/64 of the FP32 rate) busier than the stencil.
-// Cross-site sums are FP64 in every case.
+// |v|^2 of one site's n complex components, returned as a double.  FP64
+// values are squared and summed in FP64.  Float-float values are summed in
+// float-float: each square (hi + lo)^2 contributes its leading part hi*hi
+// exactly (TwoProduct) plus 2 hi lo (lo^2 < 2^-48 hi^2 is dropped), the
+// leading parts go through a TwoSum chain, and as all terms are positive
+// the relative error stays near 2^-44.  FP32 values (the sloppy formats,
+// whose components carry 24-bit mantissas at best) are squared and summed
+// in FP32 with FMAs, relative error <= 2n u_32.  Both are converted once:
+// per-component FP64 conversions and products would keep GB300's FP64 pipe
+// (1/64 of the FP32 rate) busier than the stencil.  Cross-site sums are
+// FP64 in every case.
 template <class R, int N> LQCD_DEV double site_norm2(const Cx<R> v[N]) {
   double t = 0.0;
 #pragma unroll
   for (int k = 0; k < N; k++) t += norm2_d(v[k]);
   return t;
 }
+template <int N> LQCD_DEV double df_site_norm2(const Cx<df> v[N]) {
+  DfAcc A = dfacc_first(v[0].re, v[0].re, false);
+  dfacc_add_prod(A, v[0].im, v[0].im, false);
+#pragma unroll
+  for (int k = 1; k < N; k++) {
+    dfacc_add_prod(A, v[k].re, v[k].re, false);
+    dfacc_add_prod(A, v[k].im, v[k].im, false);
+  }
+  return df_to_double(dfacc_result(A));
+}
+template <> LQCD_DEV double site_norm2<df, 12>(const Cx<df> v[12]) { return df_site_norm2<12>(v); }
 template <> LQCD_DEV double site_norm2<float, 12>(const Cx<float> v[12]) {
   float t = 0.0f;
 #pragma unroll

@@ -57,10 +57,13 @@ lqcd_status launch_hop(lqcd_ctx *ctx, const Geom &g, const HopLaunch &L, int *nb
   //  each with a full grid (one site per thread) or a persistent grid of 4 or
   //  8 blocks per SM, and for the memory-bound one-RHS-per-thread kernels both
   //  load orders.  The float-float kernel with 18-real links runs two threads
-  //  per site and is bounded to 128 threads per block.
+  //  per site and is bounded to 128 threads per block; it comes in scalar
+  //  and in packed FP32x2 arithmetic, the packed form also with its operands
+  //  staged through shared memory.
   struct Cand {
     short bx, by, gm, rt;
     bool lf, two;  // two: two sites per thread in packed FP32x2
+    char pk;       // float-float pair kernel: 0 scalar, 1 packed FP32x2, 2 packed + shared-memory staging
   };
   Cand cands[96];
   int ncand = 0, fallback = 0;
@@ -70,12 +73,14 @@ lqcd_status launch_hop(lqcd_ctx *ctx, const Geom &g, const HopLaunch &L, int *nb
   for (int gi = 0; gi < 3; gi++)
     for (int lf = 0; lf < (low ? 2 : 1); lf++) {
       if (pair) {
-        if (nrhs == 1) {
-          cands[ncand++] = {64, 1, GM[gi], 1, false};
-          cands[ncand++] = {128, 1, GM[gi], 1, false};
-        } else {
-          cands[ncand++] = {64, 1, GM[gi], 1, false};
-          cands[ncand++] = {64, 2, GM[gi], 1, false};
+        for (char pk = 0; pk < 3; pk++) {
+          if (nrhs == 1) {
+            cands[ncand++] = {64, 1, GM[gi], 1, false, false, pk};
+            cands[ncand++] = {128, 1, GM[gi], 1, false, false, pk};
+          } else {
+            cands[ncand++] = {64, 1, GM[gi], 1, false, false, pk};
+            cands[ncand++] = {64, 2, GM[gi], 1, false, false, pk};
+          }
         }
       } else if (nrhs == 1) {
         for (short bx : {64, 128, 256}) cands[ncand++] = {bx, 1, GM[gi], 1, lf != 0};
@@ -96,7 +101,7 @@ lqcd_status launch_hop(lqcd_ctx *ctx, const Geom &g, const HopLaunch &L, int *nb
   // 128-site blocks for one RHS, or with the most RHS per block for several
   for (int c = 0; c < ncand; c++) {
     const Cand &k = cands[c];
-    if (k.gm != 0 || k.lf || k.rt != 1 || k.two) continue;
+    if (k.gm != 0 || k.lf || k.rt != 1 || k.two || k.pk != 0) continue;
     if (nrhs == 1 ? k.bx == 128 : k.by >= cands[fallback].by) fallback = c;
   }
   auto go = [&](int ci, const HopArgs &args) {
@@ -113,13 +118,13 @@ lqcd_status launch_hop(lqcd_ctx *ctx, const Geom &g, const HopLaunch &L, int *nb
     cudaStream_t st = ctx->stream;
     switch (L.prec) {
       case LQCD_F64: hop_launch_f64(args, L.recon, grid, block, dag, red, st); break;
-      case LQCD_DF64: hop_launch_df64(args, L.recon, pair, grid, block, dag, red, st); break;
+      case LQCD_DF64: hop_launch_df64(args, L.recon, pair, k.pk, grid, block, dag, red, st); break;
       case LQCD_F32: hop_launch_f32(args, L.recon, grid, block, dag, red, k.lf, rt, k.two, st); break;
       default: hop_launch_h16(args, L.prec, grid, block, dag, red, k.lf, rt, k.two, st); break;
     }
   };
   char key[160];
-  snprintf(key, sizeof(key), "hop3|p%d|r%d|d%d|red%d|aux%d|%dx%dx%dx%d|n%d", L.prec, L.recon, (int)dag, (int)red,
+  snprintf(key, sizeof(key), "hop4|p%d|r%d|d%d|red%d|aux%d|%dx%dx%dx%d|n%d", L.prec, L.recon, (int)dag, (int)red,
            A.has_aux, g.L[0], g.L[1], g.L[2], g.L[3], nrhs);
   HopArgs At = A;
   At.halt = nullptr;  // timing launches run whatever the solver state
@@ -188,6 +193,7 @@ void hop_args_fill(const Geom &g, const HopLaunch &L, void *dst) {
   A.c_one = L.c_up.re == 1.0 && L.c_up.im == 0.0 && L.c_dn.re == 1.0 && L.c_dn.im == 0.0;
   A.d_up = L.d_up;
   A.d_dn = L.d_dn;
+  A.co = make_coef4(L.c_up, L.c_dn, L.d_up, L.d_dn);
   A.partials = L.partials;
   A.halt = nullptr;
 }

@@ -1,20 +1,39 @@
 // dslash_df64.cu -- float-float instantiations of the hop kernels: the
-// two-threads-per-site kernel for 18-real links and the one-thread kernel for
-// REC12 links.
+// two-threads-per-site kernel for 18-real links (scalar or packed FP32x2
+// arithmetic, the packed one also with its operands staged through shared
+// memory; all three give the same bits) and the one-thread kernel for REC12
+// links.
 #include "hop_kernels.cuh"
 
 namespace lqcd {
 
-void hop_launch_df64(const HopArgs &A, int recon, bool pair, dim3 grid, dim3 block, bool dag, bool red,
-                     cudaStream_t st) {
-  if (pair) {
+template <bool PK>
+static void launch_pair(const HopArgs &A, dim3 grid, dim3 block, bool dag, bool red, cudaStream_t st) {
+  if (dag) {
+    if (red) hop_df64_pair_kernel<true, true, PK><<<grid, block, 0, st>>>(A);
+    else hop_df64_pair_kernel<true, false, PK><<<grid, block, 0, st>>>(A);
+  } else {
+    if (red) hop_df64_pair_kernel<false, true, PK><<<grid, block, 0, st>>>(A);
+    else hop_df64_pair_kernel<false, false, PK><<<grid, block, 0, st>>>(A);
+  }
+}
+
+void hop_launch_df64(const HopArgs &A, int recon, bool pair, int mode, dim3 grid, dim3 block, bool dag,
+                     bool red, cudaStream_t st) {
+  if (pair && mode == 2) {
+    const size_t smem = (size_t)block.y * df_staged_words(block.x) * sizeof(float4);
     if (dag) {
-      if (red) hop_df64_pair_kernel<true, true><<<grid, block, 0, st>>>(A);
-      else hop_df64_pair_kernel<true, false><<<grid, block, 0, st>>>(A);
+      if (red) hop_df64_staged_kernel<true, true><<<grid, block, smem, st>>>(A);
+      else hop_df64_staged_kernel<true, false><<<grid, block, smem, st>>>(A);
     } else {
-      if (red) hop_df64_pair_kernel<false, true><<<grid, block, 0, st>>>(A);
-      else hop_df64_pair_kernel<false, false><<<grid, block, 0, st>>>(A);
+      if (red) hop_df64_staged_kernel<false, true><<<grid, block, smem, st>>>(A);
+      else hop_df64_staged_kernel<false, false><<<grid, block, smem, st>>>(A);
     }
+    return;
+  }
+  if (pair) {
+    if (mode == 1) launch_pair<true>(A, grid, block, dag, red, st);
+    else launch_pair<false>(A, grid, block, dag, red, st);
     return;
   }
   if (recon == 12) launch_t<LQCD_DF64, 12>(A, grid, block, dag, red, st);

@@ -154,9 +154,13 @@ struct HopArgs {
   int out_parity, nrhs, has_aux;
   int c_one;  // c_up = c_dn = 1: the epilogue skips the multiplication
   HostC c_up, c_dn, d_up, d_dn;
+  Coef4 co;  // c_up, c_dn, d_up, d_dn in every arithmetic
   double *partials;
   int *halt;
 };
+
+// coefficient i (0 c_up, 1 c_dn, 2 d_up, 3 d_dn) in the arithmetic R
+template <class R> LQCD_DEV Cx<R> hop_coef(const HopArgs &A, int i) { return coef_of<R>(A.co, i); }
 
 template <class R>
 LQCD_DEV void negate_if(Cx<R> v[6], bool neg) {
@@ -243,7 +247,7 @@ LQCD_DEV void hop_dir(const HopArgs &A, const Site &s, int p, int cb, const Spin
 template <int PREC, bool REDUCE>
 LQCD_DEV double hop_epilogue(const HopArgs &A, int cb, int rhs, const Cx<typename SpinorIO<PREC>::R> acc[12]) {
   using R = typename SpinorIO<PREC>::R;
-  const Cx<R> cu = cfrom<R>(A.c_up), cd = cfrom<R>(A.c_dn);
+  const Cx<R> cu = hop_coef<R>(A, 0), cd = hop_coef<R>(A, 1);
   Cx<R> res[12];
   if (A.c_one) {
 #pragma unroll
@@ -257,7 +261,7 @@ LQCD_DEV double hop_epilogue(const HopArgs &A, int cb, int rhs, const Cx<typenam
                     A.aux_scale ? (float *)A.aux_scale + rhs * A.aux_srs : nullptr, A.g.Vh};
     Cx<R> ax[12];
     SpinorIO<PREC>::load(vaux, cb, ax);
-    const Cx<R> du = cfrom<R>(A.d_up), dd = cfrom<R>(A.d_dn);
+    const Cx<R> du = hop_coef<R>(A, 2), dd = hop_coef<R>(A, 3);
 #pragma unroll
     for (int k = 0; k < 12; k++) res[k] = cmadd(k < 6 ? du : dd, ax[k], res[k]);
   }
@@ -526,62 +530,340 @@ inline void launch_pair2(const HopArgs &A, dim3 grid, dim3 block, bool dag, bool
 // Per thread this halves the dependent float-float chains and the register
 // footprint, so twice as many warps hide the FP32 latency.
 // ---------------------------------------------------------------------------
+// One (direction, sense) step of the float-float pair hop.  `sp(q)` yields
+// the neighbour's colour q of upper spin k (q < 3) or of the lower spin that
+// h_k pairs with it (q >= 3); `lk(e)` yields element e = 3*row + column of
+// U_mu(x) (forward) or U_mu(x - mu) (backward).
+template <int MU, int S, int DIR, class SP, class LK>
+LQCD_DEV void df_pair_step(const HopArgs &A, const Site &s, int k, SP sp, LK lk, Cx<df> up[3], Cx<df> lswap[3],
+                           Cx<df> lsame[3]) {
+  constexpr int sgn = DIR == 0 ? S : -S;  // projector sign: (1 - S g) forward, (1 + S g) backward
+  Cx<df> h[3];
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    float4 a = sp(c);
+    float4 b = sp(3 + c);
+    Cx<df> pa = {{a.x, a.z}, {a.y, a.w}}, pb = {{b.x, b.z}, {b.y, b.w}};
+    // h_k = p_k + f * p_lo with f = S*i (x), S*(+-1) (y), S*(+-i) (z), -S (t)
+    const bool neg = (MU == 0) ? sgn < 0 : (MU == 1) ? (k == 0 ? sgn < 0 : sgn > 0)
+                   : (MU == 2) ? (k == 0 ? sgn < 0 : sgn > 0) : sgn > 0;
+    Cx<df> t = (MU == 0 || MU == 2) ? times_i(pb) : pb;
+    h[c] = neg ? csub_lazy(pa, t) : cadd_lazy(pa, t);
+  }
+  Cx<df> v[3];
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    Cx<df> u3[3];
+#pragma unroll
+    for (int q = 0; q < 3; q++) {  // forward: row a of U; backward: column a
+      float4 w = lk(DIR == 0 ? 3 * a + q : 3 * q + a);
+      u3[q] = {{w.x, w.z}, {w.y, w.w}};
+    }
+    v[a] = DIR == 0 ? dfdot3<false, true>(u3[0], u3[1], u3[2], h[0], h[1], h[2])
+                    : dfdot3<true, true>(u3[0], u3[1], u3[2], h[0], h[1], h[2]);
+  }
+  if (MU == 3 && A.g.antiper && s.t == (DIR == 0 ? A.g.L[3] - 1 : 0)) {
+#pragma unroll
+    for (int a = 0; a < 3; a++) v[a] = -v[a];
+  }
+  // lower-spin factor of v_k: -sgn*i (x, to 3-k), (k==0 ? +sgn : -sgn) (y, to 3-k),
+  // (k==0 ? -sgn*i : +sgn*i) (z, to 2+k), -sgn (t, to 2+k)
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    up[a] = cadd_lazy(up[a], v[a]);
+    if (MU == 0) lswap[a] = sgn > 0 ? csub_lazy(lswap[a], times_i(v[a])) : cadd_lazy(lswap[a], times_i(v[a]));
+    else if (MU == 1) lswap[a] = ((k == 0) == (sgn > 0)) ? cadd_lazy(lswap[a], v[a]) : csub_lazy(lswap[a], v[a]);
+    else if (MU == 2)
+      lsame[a] = ((k == 0) == (sgn > 0)) ? csub_lazy(lsame[a], times_i(v[a])) : cadd_lazy(lsame[a], times_i(v[a]));
+    else lsame[a] = sgn > 0 ? csub_lazy(lsame[a], v[a]) : cadd_lazy(lsame[a], v[a]);
+  }
+}
+
+// global addresses of one step's operands: the neighbour's upper spin k and
+// paired lower spin (plane stride Vh), and the link (plane stride U.Vh)
+struct DfStepSrc {
+  const float4 *pk, *plo, *ub;
+};
+template <int MU, int DIR>
+LQCD_DEV DfStepSrc df_step_src(const HopArgs &A, const Site &s, int p, int cb, int k, const float4 *pin, int Vh) {
+  const int j = neighbour_cb(A.g, s, MU, DIR == 0 ? +1 : -1);
+  const int lo = (MU < 2) ? 3 - k : 2 + k;  // lower spin paired with upper k in h_k
+  const int lc = DIR == 0 ? cb : j;
+  const float4 *ub = (const float4 *)((const char *)A.U.ptr + (DIR == 0 ? p : p ^ 1) * A.U.parity_stride +
+                                      MU * A.U.mu_stride) + lc;
+  return {pin + (size_t)(3 * k) * Vh + j, pin + (size_t)(3 * lo) * Vh + j, ub};
+}
+
+template <int DIR>
+LQCD_DEV DfStepSrc df_step_src_rt(const HopArgs &A, const Site &s, int p, int cb, int k, int mu,
+                                  const float4 *pin, int Vh) {
+  const int j = neighbour_cb(A.g, s, mu, DIR == 0 ? +1 : -1);
+  const int lo = (mu < 2) ? 3 - k : 2 + k;
+  const int lc = DIR == 0 ? cb : j;
+  const float4 *ub = (const float4 *)((const char *)A.U.ptr + (DIR == 0 ? p : p ^ 1) * A.U.parity_stride +
+                                      mu * A.U.mu_stride) + lc;
+  return {pin + (size_t)(3 * k) * Vh + j, pin + (size_t)(3 * lo) * Vh + j, ub};
+}
+
 template <int MU, int S>
 LQCD_DEV void df_pair_dir(const HopArgs &A, const Site &s, int p, int cb, int k, const SpinorView &vin,
                           Cx<df> up[3], Cx<df> lswap[3], Cx<df> lsame[3]) {
   const float4 *pin = (const float4 *)vin.ptr;
-#pragma unroll
-  for (int dir = 0; dir < 2; dir++) {
-    const int sgn = dir == 0 ? S : -S;  // projector sign: (1 - S g) forward, (1 + S g) backward
-    const int j = neighbour_cb(A.g, s, MU, dir == 0 ? +1 : -1);
-    const int lo = (MU < 2) ? 3 - k : 2 + k;  // lower spin paired with upper k in h_k
-    Cx<df> h[3];
-#pragma unroll
-    for (int c = 0; c < 3; c++) {
-      float4 a = __ldg(pin + (size_t)(3 * k + c) * vin.Vh + j);
-      float4 b = __ldg(pin + (size_t)(3 * lo + c) * vin.Vh + j);
-      Cx<df> pa = {{a.x, a.z}, {a.y, a.w}}, pb = {{b.x, b.z}, {b.y, b.w}};
-      // h_k = p_k + f * p_lo with f = S*i (x), S*(+-1) (y), S*(+-i) (z), -S (t)
-      const bool neg = (MU == 0) ? sgn < 0 : (MU == 1) ? (k == 0 ? sgn < 0 : sgn > 0)
-                     : (MU == 2) ? (k == 0 ? sgn < 0 : sgn > 0) : sgn > 0;
-      Cx<df> t = (MU == 0 || MU == 2) ? times_i(pb) : pb;
-      h[c] = neg ? csub_lazy(pa, t) : cadd_lazy(pa, t);
-    }
-    const float4 *ub = (const float4 *)((const char *)A.U.ptr + (dir == 0 ? p : p ^ 1) * A.U.parity_stride +
-                                        MU * A.U.mu_stride);
-    const int lc = dir == 0 ? cb : j;
-    Cx<df> v[3];
-#pragma unroll
-    for (int a = 0; a < 3; a++) {
-      Cx<df> u3[3];
-#pragma unroll
-      for (int q = 0; q < 3; q++) {  // forward: row a of U; backward: column a
-        float4 w = __ldg(ub + (size_t)(dir == 0 ? 3 * a + q : 3 * q + a) * A.U.Vh + lc);
-        u3[q] = {{w.x, w.z}, {w.y, w.w}};
-      }
-      v[a] = dir == 0 ? dfdot3<false, true>(u3[0], u3[1], u3[2], h[0], h[1], h[2])
-                      : dfdot3<true, true>(u3[0], u3[1], u3[2], h[0], h[1], h[2]);
-    }
-    if (MU == 3 && A.g.antiper && s.t == (dir == 0 ? A.g.L[3] - 1 : 0)) {
-#pragma unroll
-      for (int a = 0; a < 3; a++) v[a] = -v[a];
-    }
-    // lower-spin factor of v_k: -sgn*i (x, to 3-k), (k==0 ? +sgn : -sgn) (y, to 3-k),
-    // (k==0 ? -sgn*i : +sgn*i) (z, to 2+k), -sgn (t, to 2+k)
-#pragma unroll
-    for (int a = 0; a < 3; a++) {
-      up[a] = cadd_lazy(up[a], v[a]);
-      if (MU == 0) lswap[a] = sgn > 0 ? csub_lazy(lswap[a], times_i(v[a])) : cadd_lazy(lswap[a], times_i(v[a]));
-      else if (MU == 1) lswap[a] = ((k == 0) == (sgn > 0)) ? cadd_lazy(lswap[a], v[a]) : csub_lazy(lswap[a], v[a]);
-      else if (MU == 2)
-        lsame[a] = ((k == 0) == (sgn > 0)) ? csub_lazy(lsame[a], times_i(v[a])) : cadd_lazy(lsame[a], times_i(v[a]));
-      else lsame[a] = sgn > 0 ? csub_lazy(lsame[a], v[a]) : cadd_lazy(lsame[a], v[a]);
-    }
+  const size_t Vh = vin.Vh, UVh = A.U.Vh;
+  {
+    const DfStepSrc f = df_step_src<MU, 0>(A, s, p, cb, k, pin, vin.Vh);
+    df_pair_step<MU, S, 0>(
+        A, s, k, [&](int q) { return __ldg(q < 3 ? f.pk + q * Vh : f.plo + (q - 3) * Vh); },
+        [&](int e) { return __ldg(f.ub + e * UVh); }, up, lswap, lsame);
+  }
+  {
+    const DfStepSrc b = df_step_src<MU, 1>(A, s, p, cb, k, pin, vin.Vh);
+    df_pair_step<MU, S, 1>(
+        A, s, k, [&](int q) { return __ldg(q < 3 ? b.pk + q * Vh : b.plo + (q - 3) * Vh); },
+        [&](int e) { return __ldg(b.ub + e * UVh); }, up, lswap, lsame);
   }
 }
 
-template <bool DAG, bool REDUCE>
-__global__ void __launch_bounds__(128) hop_df64_pair_kernel(HopArgs A) {
+// ---------------------------------------------------------------------------
+// The pair step in packed FP32x2 arithmetic.  A complex double-word is held
+// as df2 {hi = (re.hi, im.hi), lo = (re.lo, im.lo)} -- the order of its
+// 16-byte word -- and each __fadd2_rn / __fmul2_rn / __ffma2_rn does the
+// scalar operation of the real and the imaginary lane at once.  Every lane
+// performs exactly the operations of the scalar step, in the same order (a
+// negated factor is moved to the other operand, which rounds identically),
+// so the two forms give the same bits with about 40 % fewer instructions.
+// ---------------------------------------------------------------------------
+struct df2 {
+  float2 hi, lo;
+};
+LQCD_DEV df2 df2_of(float4 w) { return {make_float2(w.x, w.y), make_float2(w.z, w.w)}; }
+LQCD_DEV df2 df2_zero() { return {make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)}; }
+LQCD_DEV Cx<df> cx_of(df2 a) { return {{a.hi.x, a.lo.x}, {a.hi.y, a.lo.y}}; }
+LQCD_DEV df2 neg_p(df2 a) { return {neg2(a.hi), neg2(a.lo)}; }
+LQCD_DEV df2 times_i_p(df2 a) {  // (-im, re)
+  return {make_float2(-a.hi.y, a.hi.x), make_float2(-a.lo.y, a.lo.x)};
+}
+LQCD_DEV df2 times_mi_p(df2 a) {  // (im, -re)
+  return {make_float2(a.hi.y, -a.hi.x), make_float2(a.lo.y, -a.lo.x)};
+}
+// two_sum on each lane
+LQCD_DEV void two_sum_p(float2 a, float2 b, float2 &s, float2 &e) {
+  s = __fadd2_rn(a, b);
+  const float2 bb = __fadd2_rn(s, neg2(a));
+  e = __fadd2_rn(__fadd2_rn(a, neg2(__fadd2_rn(s, neg2(bb)))), __fadd2_rn(b, neg2(bb)));
+}
+// add_lazy on each lane
+LQCD_DEV df2 add_lazy_p(df2 a, df2 b) {
+  df2 r;
+  two_sum_p(a.hi, b.hi, r.hi, r.lo);
+  r.lo = __fadd2_rn(r.lo, __fadd2_rn(a.lo, b.lo));
+  return r;
+}
+// product of the broadcast double-word (ah, al) with both lanes of b: the
+// leading part p and its first-order error pe, as in dfacc_add_prod
+LQCD_DEV void prod_p(float ah, float al, df2 b, float2 &p, float2 &pe) {
+  const float2 h2 = make_float2(ah, ah), l2 = make_float2(al, al);
+  p = __fmul2_rn(h2, b.hi);
+  pe = __ffma2_rn(h2, b.hi, neg2(p));
+  pe = __ffma2_rn(h2, b.lo, pe);
+  pe = __ffma2_rn(l2, b.hi, pe);
+}
+LQCD_DEV void acc_p(df2 &A, float ah, float al, df2 b) {
+  float2 p, pe, t;
+  prod_p(ah, al, b, p, pe);
+  two_sum_p(A.hi, p, A.hi, t);
+  A.lo = __fadd2_rn(A.lo, __fadd2_rn(t, pe));
+}
+// dfdot3<CONJ, true> with lanes (re, im): x are the link words, y1 = h and
+// y2 = i h (CONJ: -i h), so that lane re takes x.re y.re then -+ x.im y.im
+// and lane im takes x.re y.im then +- x.im y.re, as the scalar form does
+LQCD_DEV df2 dfdot3_p(const float4 x[3], const df2 y1[3], const df2 y2[3]) {
+  df2 A;
+  prod_p(x[0].x, x[0].z, y1[0], A.hi, A.lo);
+  acc_p(A, x[0].y, x[0].w, y2[0]);
+#pragma unroll
+  for (int j = 1; j < 3; j++) {
+    acc_p(A, x[j].x, x[j].z, y1[j]);
+    acc_p(A, x[j].y, x[j].w, y2[j]);
+  }
+  return A;
+}
+// v times the unit f: 0 -> 1, 1 -> i, 2 -> -1, 3 -> -i
+template <int F> LQCD_DEV df2 unit_p(df2 v) {
+  return F == 0 ? v : F == 1 ? times_i_p(v) : F == 2 ? neg_p(v) : times_mi_p(v);
+}
+
+template <int MU, int S, int DIR, class SP, class LK>
+LQCD_DEV void df_pair_step_p(const HopArgs &A, const Site &s, int k, SP sp, LK lk, df2 up[3], df2 lswap[3],
+                             df2 lsame[3]) {
+  constexpr int sgn = DIR == 0 ? S : -S;
+  df2 y1[3], y2[3];
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    const df2 pa = df2_of(sp(c)), pb = df2_of(sp(3 + c));
+    const bool neg = (MU == 0) ? sgn < 0 : (MU == 1) ? (k == 0 ? sgn < 0 : sgn > 0)
+                   : (MU == 2) ? (k == 0 ? sgn < 0 : sgn > 0) : sgn > 0;
+    const df2 t = (MU == 0 || MU == 2) ? times_i_p(pb) : pb;
+    y1[c] = add_lazy_p(pa, neg ? neg_p(t) : t);
+    y2[c] = DIR == 0 ? times_i_p(y1[c]) : times_mi_p(y1[c]);
+  }
+  df2 v[3];
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    float4 x[3];
+#pragma unroll
+    for (int q = 0; q < 3; q++) x[q] = lk(DIR == 0 ? 3 * a + q : 3 * q + a);
+    v[a] = dfdot3_p(x, y1, y2);
+  }
+  if (MU == 3 && A.g.antiper && s.t == (DIR == 0 ? A.g.L[3] - 1 : 0)) {
+#pragma unroll
+    for (int a = 0; a < 3; a++) v[a] = neg_p(v[a]);
+  }
+  // the lower-spin factors of the scalar step as units: x: -sgn*i, y:
+  // (k==0) == (sgn>0) ? +1 : -1, z: (k==0) == (sgn>0) ? -i : +i, t: -sgn
+  const bool kp = (k == 0) == (sgn > 0);
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    up[a] = add_lazy_p(up[a], v[a]);
+    if (MU == 0) lswap[a] = add_lazy_p(lswap[a], sgn > 0 ? unit_p<3>(v[a]) : unit_p<1>(v[a]));
+    else if (MU == 1) lswap[a] = add_lazy_p(lswap[a], kp ? v[a] : unit_p<2>(v[a]));
+    else if (MU == 2) lsame[a] = add_lazy_p(lsame[a], kp ? unit_p<3>(v[a]) : unit_p<1>(v[a]));
+    else lsame[a] = add_lazy_p(lsame[a], sgn > 0 ? unit_p<2>(v[a]) : v[a]);
+  }
+}
+
+// The packed step for direction mu = 2h + (EV ? 0 : 1) with the pair index
+// h a runtime value: EV (x, z) pairs the spins through a factor i, odd
+// directions (y, t) through a real one, so one copy of the code serves a
+// pair of directions and the direction-dependent signs become exact
+// multiplications by +-1 (the bits do not change).  The lower-spin
+// contribution goes to `low`, which the caller maps to lswap (h = 0) or
+// lsame (h = 1).
+LQCD_DEV df2 scale_p(df2 a, float2 f) { return {__fmul2_rn(a.hi, f), __fmul2_rn(a.lo, f)}; }
+
+template <int S, int DIR, bool EV, class SP, class LK>
+LQCD_DEV void df_pair_step_h(const HopArgs &A, const Site &s, int k, int h, SP sp, LK lk, df2 up[3],
+                             df2 low[3]) {
+  constexpr int sgn = DIR == 0 ? S : -S;
+  const bool kneg = k == 0 ? sgn < 0 : sgn > 0;
+  // projection sign: x sgn<0, y kneg, z kneg, t sgn>0
+  const bool neg = EV ? (h == 0 ? sgn < 0 : kneg) : (h == 0 ? kneg : sgn > 0);
+  const float2 fp = neg ? make_float2(-1.0f, -1.0f) : make_float2(1.0f, 1.0f);
+  df2 y1[3], y2[3];
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    const df2 pa = df2_of(sp(c)), pb = df2_of(sp(3 + c));
+    y1[c] = add_lazy_p(pa, scale_p(EV ? times_i_p(pb) : pb, fp));
+    y2[c] = DIR == 0 ? times_i_p(y1[c]) : times_mi_p(y1[c]);
+  }
+  df2 v[3];
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    float4 x[3];
+#pragma unroll
+    for (int q = 0; q < 3; q++) x[q] = lk(DIR == 0 ? 3 * a + q : 3 * q + a);
+    v[a] = dfdot3_p(x, y1, y2);
+  }
+  if (!EV && h == 1 && A.g.antiper && s.t == (DIR == 0 ? A.g.L[3] - 1 : 0)) {
+#pragma unroll
+    for (int a = 0; a < 3; a++) v[a] = neg_p(v[a]);
+  }
+  // lower-spin unit (EV ? i : 1) times -1 when: x sgn>0, y !kp, z kp, t sgn>0
+  const bool kp = (k == 0) == (sgn > 0);
+  const bool lneg = EV ? (h == 0 ? sgn > 0 : kp) : (h == 0 ? !kp : sgn > 0);
+  const float2 fl = lneg ? make_float2(-1.0f, -1.0f) : make_float2(1.0f, 1.0f);
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    up[a] = add_lazy_p(up[a], v[a]);
+    low[a] = add_lazy_p(low[a], scale_p(EV ? times_i_p(v[a]) : v[a], fl));
+  }
+}
+
+template <int MU, int S>
+LQCD_DEV void df_pair_dir_p(const HopArgs &A, const Site &s, int p, int cb, int k, const SpinorView &vin,
+                            df2 up[3], df2 lswap[3], df2 lsame[3]) {
+  const float4 *pin = (const float4 *)vin.ptr;
+  const size_t Vh = vin.Vh, UVh = A.U.Vh;
+  {
+    const DfStepSrc f = df_step_src<MU, 0>(A, s, p, cb, k, pin, vin.Vh);
+    df_pair_step_p<MU, S, 0>(
+        A, s, k, [&](int q) { return __ldg(q < 3 ? f.pk + q * Vh : f.plo + (q - 3) * Vh); },
+        [&](int e) { return __ldg(f.ub + e * UVh); }, up, lswap, lsame);
+  }
+  {
+    const DfStepSrc b = df_step_src<MU, 1>(A, s, p, cb, k, pin, vin.Vh);
+    df_pair_step_p<MU, S, 1>(
+        A, s, k, [&](int q) { return __ldg(q < 3 ? b.pk + q * Vh : b.plo + (q - 3) * Vh); },
+        [&](int e) { return __ldg(b.ub + e * UVh); }, up, lswap, lsame);
+  }
+}
+
+// End of a float-float pair site: lower spin 2+k = own z,t partial + the
+// partner lane's x,y partial, renormalisation, the epilogue coefficients,
+// the store and (REDUCE) the fixed-order norm partial of each 32-site group.
+template <bool REDUCE>
+LQCD_DEV void df_pair_finish(const HopArgs &A, int base, int cb, int rhs, int k, bool active, Cx<df> up[3],
+                             Cx<df> lswap[3], Cx<df> lsame[3], double (*sh)[4]) {
+  double nrm = 0.0;
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    Cx<df> o;
+    o.re.hi = __shfl_xor_sync(0xffffffffu, lswap[a].re.hi, 1);
+    o.re.lo = __shfl_xor_sync(0xffffffffu, lswap[a].re.lo, 1);
+    o.im.hi = __shfl_xor_sync(0xffffffffu, lswap[a].im.hi, 1);
+    o.im.lo = __shfl_xor_sync(0xffffffffu, lswap[a].im.lo, 1);
+    lsame[a] = cnormalise(cadd_lazy(lsame[a], o));
+    up[a] = cnormalise(up[a]);
+  }
+  if (active) {
+    const Cx<df> cu = A.co.w[0], cd = A.co.w[1];
+    Cx<df> ru[3], rl[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      ru[a] = A.c_one ? up[a] : cu * up[a];
+      rl[a] = A.c_one ? lsame[a] : cd * lsame[a];
+    }
+    if (A.has_aux) {
+      const float4 *pa = (const float4 *)(A.aux + rhs * A.aux_rs);
+      const Cx<df> du = A.co.w[2], dd = A.co.w[3];
+#pragma unroll
+      for (int a = 0; a < 3; a++) {
+        float4 w1 = __ldg(pa + (size_t)(3 * k + a) * A.g.Vh + cb);
+        float4 w2 = __ldg(pa + (size_t)(3 * (2 + k) + a) * A.g.Vh + cb);
+        ru[a] = cmadd(du, Cx<df>{{w1.x, w1.z}, {w1.y, w1.w}}, ru[a]);
+        rl[a] = cmadd(dd, Cx<df>{{w2.x, w2.z}, {w2.y, w2.w}}, rl[a]);
+      }
+    }
+    float4 *po = (float4 *)(A.out + rhs * A.out_rs);
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      po[(size_t)(3 * k + a) * A.g.Vh + cb] = make_float4(ru[a].re.hi, ru[a].im.hi, ru[a].re.lo, ru[a].im.lo);
+      po[(size_t)(3 * (2 + k) + a) * A.g.Vh + cb] = make_float4(rl[a].re.hi, rl[a].im.hi, rl[a].re.lo, rl[a].im.lo);
+    }
+    if (REDUCE) {
+      const Cx<df> w[6] = {ru[0], ru[1], ru[2], rl[0], rl[1], rl[2]};
+      nrm = df_site_norm2<6>(w);
+    }
+  }
+  if (REDUCE) {
+    // 32 sites = 64 threads = two warps of one block row: warp sums, then
+    // the even warp adds its odd neighbour (fixed order)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nrm += __shfl_down_sync(0xffffffffu, nrm, o);
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.y][w] = nrm;
+    __syncthreads();
+    const int cb0 = base + ((threadIdx.x >> 6) << 5);  // first site of this 32-site group
+    if ((threadIdx.x & 63) == 0 && rhs < A.nrhs && cb0 < A.g.Vh) {
+      const int nw = (A.g.Vh + 31) >> 5;
+      A.partials[(size_t)rhs * nw + (cb0 >> 5)] = sh[threadIdx.y][w] + sh[threadIdx.y][w + 1];
+    }
+    __syncthreads();
+  }
+}
+
+template <bool DAG, bool REDUCE, bool PK>
+__global__ void __launch_bounds__(128, 4) hop_df64_pair_kernel(HopArgs A) {
   __shared__ double sh[8][4];
   if (A.halt && *(volatile int *)A.halt) return;
   const int rhs = blockIdx.z * blockDim.y + threadIdx.y;
@@ -591,75 +873,174 @@ __global__ void __launch_bounds__(128) hop_df64_pair_kernel(HopArgs A) {
   for (int base = blockIdx.x * sites_per_block; base < A.g.Vh; base += stride) {
     const int cb = base + (threadIdx.x >> 1);
     const bool active = cb < A.g.Vh && rhs < A.nrhs;
-    double nrm = 0.0;
     Cx<df> up[3], lswap[3], lsame[3];
+    constexpr int S = DAG ? -1 : 1;
+    if (PK) {
+      df2 pu[3], pw[3], pm[3];
 #pragma unroll
-    for (int a = 0; a < 3; a++) up[a] = lswap[a] = lsame[a] = czero<df>();
-    const int p = A.out_parity;
-    Site s{};
-    if (active) {
-      s = site_of(A.g, p, cb);
-      SpinorView vin{A.in + rhs * A.in_rs, nullptr, A.g.Vh};
-      constexpr int S = DAG ? -1 : 1;
-      df_pair_dir<0, S>(A, s, p, cb, k, vin, up, lswap, lsame);
-      df_pair_dir<1, S>(A, s, p, cb, k, vin, up, lswap, lsame);
-      df_pair_dir<2, S>(A, s, p, cb, k, vin, up, lswap, lsame);
-      df_pair_dir<3, S>(A, s, p, cb, k, vin, up, lswap, lsame);
-    }
-    // lower spin 2+k = own z,t partial + partner's x,y partial
-#pragma unroll
-    for (int a = 0; a < 3; a++) {
-      Cx<df> o;
-      o.re.hi = __shfl_xor_sync(0xffffffffu, lswap[a].re.hi, 1);
-      o.re.lo = __shfl_xor_sync(0xffffffffu, lswap[a].re.lo, 1);
-      o.im.hi = __shfl_xor_sync(0xffffffffu, lswap[a].im.hi, 1);
-      o.im.lo = __shfl_xor_sync(0xffffffffu, lswap[a].im.lo, 1);
-      lsame[a] = cnormalise(cadd_lazy(lsame[a], o));
-      up[a] = cnormalise(up[a]);
-    }
-    if (active) {
-      const Cx<df> cu = cfrom<df>(A.c_up), cd = cfrom<df>(A.c_dn);
-      Cx<df> ru[3], rl[3];
+      for (int a = 0; a < 3; a++) pu[a] = pw[a] = pm[a] = df2_zero();
+      if (active) {
+        const int p = A.out_parity;
+        const Site s = site_of(A.g, p, cb);
+        SpinorView vin{A.in + rhs * A.in_rs, nullptr, A.g.Vh};
+        df_pair_dir_p<0, S>(A, s, p, cb, k, vin, pu, pw, pm);
+        df_pair_dir_p<1, S>(A, s, p, cb, k, vin, pu, pw, pm);
+        df_pair_dir_p<2, S>(A, s, p, cb, k, vin, pu, pw, pm);
+        df_pair_dir_p<3, S>(A, s, p, cb, k, vin, pu, pw, pm);
+      }
 #pragma unroll
       for (int a = 0; a < 3; a++) {
-        ru[a] = A.c_one ? up[a] : cu * up[a];
-        rl[a] = A.c_one ? lsame[a] : cd * lsame[a];
+        up[a] = cx_of(pu[a]);
+        lswap[a] = cx_of(pw[a]);
+        lsame[a] = cx_of(pm[a]);
       }
-      if (A.has_aux) {
-        const float4 *pa = (const float4 *)(A.aux + rhs * A.aux_rs);
-        const Cx<df> du = cfrom<df>(A.d_up), dd = cfrom<df>(A.d_dn);
+    } else {
+#pragma unroll
+      for (int a = 0; a < 3; a++) up[a] = lswap[a] = lsame[a] = czero<df>();
+      if (active) {
+        const int p = A.out_parity;
+        const Site s = site_of(A.g, p, cb);
+        SpinorView vin{A.in + rhs * A.in_rs, nullptr, A.g.Vh};
+        df_pair_dir<0, S>(A, s, p, cb, k, vin, up, lswap, lsame);
+        df_pair_dir<1, S>(A, s, p, cb, k, vin, up, lswap, lsame);
+        df_pair_dir<2, S>(A, s, p, cb, k, vin, up, lswap, lsame);
+        df_pair_dir<3, S>(A, s, p, cb, k, vin, up, lswap, lsame);
+      }
+    }
+    df_pair_finish<REDUCE>(A, base, cb, rhs, k, active, up, lswap, lsame, sh);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Packed float-float pair hop with its operands staged through shared
+// memory, looping over the two pairs of directions (x, y) and (z, t) at run
+// time (two copies of the step code, not eight, keep the kernel inside the
+// instruction cache).  The eight
+// (direction, sense) steps of a site form a two-stage pipeline: while step i is computed from one buffer, 16-byte asynchronous
+// copies (cp.async) of step i+1's neighbour words and link words fill the
+// other, so the global-load latency is hidden behind a whole step of
+// float-float arithmetic without holding registers for loads in flight.
+// Per block row of bx threads (bx/2 sites) and stage: the 6 words of each
+// thread's spin pair and the 9 link words of each site, which the site's
+// two threads copy alternately (even elements: thread 0, odd: thread 1) and
+// both read.  Both threads of a site are lanes of one warp, so
+// cp.async.wait_group followed by __syncwarp makes the partner's words
+// visible, and the __syncwarp after each step keeps a buffer from being
+// refilled while it is still read.
+// ---------------------------------------------------------------------------
+LQCD_DEV void cp_async16(void *smem, const void *gmem) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem) : "memory");
+}
+LQCD_DEV void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> LQCD_DEV void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// 16-byte shared-memory words per block row of bx threads: 2 stages x (6 per thread + 9 per site)
+LQCD_HD int df_staged_words(int bx) { return 2 * (6 * bx + 9 * (bx / 2)); }
+
+struct DfStage {
+  float4 *sp;  // [2][6][bx]: this row's spinor words
+  float4 *lk;  // [2][9][bx/2]: this row's link words
+  int bx, ns, tx, site;
+};
+
+template <int DIR, int ST>
+LQCD_DEV void df_stage_issue(const HopArgs &A, const Site &s, int p, int cb, int k, int mu, const float4 *pin,
+                             const DfStage &B) {
+  const DfStepSrc f = df_step_src_rt<DIR>(A, s, p, cb, k, mu, pin, A.g.Vh);
+  const size_t Vh = A.g.Vh, UVh = A.U.Vh;
+  float4 *sp = B.sp + ST * 6 * B.bx + B.tx;
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    cp_async16(sp + c * B.bx, f.pk + c * Vh);
+    cp_async16(sp + (3 + c) * B.bx, f.plo + c * Vh);
+  }
+  float4 *lk = B.lk + ST * 9 * B.ns + B.site;
+#pragma unroll
+  for (int e = 0; e < 9; e += 2) {
+    const int el = e + k;
+    if (el < 9) cp_async16(lk + el * B.ns, f.ub + el * UVh);
+  }
+}
+
+// one step from stage ST: wait for its copies (all but the newest group),
+// compute, and release the buffer
+template <int S, int DIR, bool EV, int ST>
+LQCD_DEV void df_stage_compute(const HopArgs &A, const Site &s, int k, int h, bool active, const DfStage &B,
+                               df2 up[3], df2 low[3]) {
+  cp_async_wait<1>();
+  __syncwarp();
+  if (active) {
+    const float4 *sp = B.sp + ST * 6 * B.bx + B.tx;
+    const float4 *lk = B.lk + ST * 9 * B.ns + B.site;
+    df_pair_step_h<S, DIR, EV>(
+        A, s, k, h, [&](int q) { return sp[q * B.bx]; }, [&](int e) { return lk[e * B.ns]; }, up, low);
+  }
+  __syncwarp();
+}
+
+template <bool DAG, bool REDUCE>
+__global__ void __launch_bounds__(128, 4) hop_df64_staged_kernel(HopArgs A) {
+  __shared__ double sh[8][4];
+  extern __shared__ float4 stage_words[];
+  if (A.halt && *(volatile int *)A.halt) return;
+  const int rhs = blockIdx.z * blockDim.y + threadIdx.y;
+  const int k = threadIdx.x & 1;
+  const int bx = blockDim.x, ns = bx >> 1;
+  DfStage B;
+  B.sp = stage_words + threadIdx.y * df_staged_words(bx);
+  B.lk = B.sp + 12 * bx;
+  B.bx = bx;
+  B.ns = ns;
+  B.tx = threadIdx.x;
+  B.site = threadIdx.x >> 1;
+  const int stride = gridDim.x * ns;
+  constexpr int S = DAG ? -1 : 1;
+  for (int base = blockIdx.x * ns; base < A.g.Vh; base += stride) {
+    const int cb = base + (threadIdx.x >> 1);
+    const bool active = cb < A.g.Vh && rhs < A.nrhs;
+    df2 pu[3], low[3], pw[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) pu[a] = low[a] = pw[a] = df2_zero();
+    const int p = A.out_parity;
+    const Site s = active ? site_of(A.g, p, cb) : Site{};
+    const float4 *pin = (const float4 *)(A.in + (active ? rhs : 0) * A.in_rs);
+    if (active) df_stage_issue<0, 0>(A, s, p, cb, k, 0, pin, B);
+    cp_async_commit();
+    // per pair h of directions the steps (2h, fwd) (2h, bwd) (2h+1, fwd)
+    // (2h+1, bwd) alternate between stage 0 and stage 1; each step first
+    // issues the copies of the next one (an empty group after the last)
+#pragma unroll 1
+    for (int h = 0; h < 2; h++) {
+      const int me = 2 * h, mo = 2 * h + 1;
+      if (active) df_stage_issue<1, 1>(A, s, p, cb, k, me, pin, B);
+      cp_async_commit();
+      df_stage_compute<S, 0, true, 0>(A, s, k, h, active, B, pu, low);
+      if (active) df_stage_issue<0, 0>(A, s, p, cb, k, mo, pin, B);
+      cp_async_commit();
+      df_stage_compute<S, 1, true, 1>(A, s, k, h, active, B, pu, low);
+      if (active) df_stage_issue<1, 1>(A, s, p, cb, k, mo, pin, B);
+      cp_async_commit();
+      df_stage_compute<S, 0, false, 0>(A, s, k, h, active, B, pu, low);
+      if (active && h == 0) df_stage_issue<0, 0>(A, s, p, cb, k, 2, pin, B);
+      cp_async_commit();
+      df_stage_compute<S, 1, false, 1>(A, s, k, h, active, B, pu, low);
+      if (h == 0) {  // x and y done: their lower partial is lswap
 #pragma unroll
         for (int a = 0; a < 3; a++) {
-          float4 w1 = __ldg(pa + (size_t)(3 * k + a) * A.g.Vh + cb);
-          float4 w2 = __ldg(pa + (size_t)(3 * (2 + k) + a) * A.g.Vh + cb);
-          ru[a] = cmadd(du, Cx<df>{{w1.x, w1.z}, {w1.y, w1.w}}, ru[a]);
-          rl[a] = cmadd(dd, Cx<df>{{w2.x, w2.z}, {w2.y, w2.w}}, rl[a]);
+          pw[a] = low[a];
+          low[a] = df2_zero();
         }
       }
-      float4 *po = (float4 *)(A.out + rhs * A.out_rs);
-#pragma unroll
-      for (int a = 0; a < 3; a++) {
-        po[(size_t)(3 * k + a) * A.g.Vh + cb] = make_float4(ru[a].re.hi, ru[a].im.hi, ru[a].re.lo, ru[a].im.lo);
-        po[(size_t)(3 * (2 + k) + a) * A.g.Vh + cb] =
-            make_float4(rl[a].re.hi, rl[a].im.hi, rl[a].re.lo, rl[a].im.lo);
-        if (REDUCE) nrm += norm2_d(ru[a]) + norm2_d(rl[a]);
-      }
     }
-    if (REDUCE) {
-      // 32 sites = 64 threads = two warps of one block row: warp sums, then
-      // the even warp adds its odd neighbour (fixed order)
+    Cx<df> up[3], lswap[3], lsame[3];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) nrm += __shfl_down_sync(0xffffffffu, nrm, o);
-      const int w = threadIdx.x >> 5;
-      if ((threadIdx.x & 31) == 0) sh[threadIdx.y][w] = nrm;
-      __syncthreads();
-      const int cb0 = base + ((threadIdx.x >> 6) << 5);  // first site of this 32-site group
-      if ((threadIdx.x & 63) == 0 && rhs < A.nrhs && cb0 < A.g.Vh) {
-        const int nw = (A.g.Vh + 31) >> 5;
-        A.partials[(size_t)rhs * nw + (cb0 >> 5)] = sh[threadIdx.y][w] + sh[threadIdx.y][w + 1];
-      }
-      __syncthreads();
+    for (int a = 0; a < 3; a++) {
+      up[a] = cx_of(pu[a]);
+      lswap[a] = cx_of(pw[a]);
+      lsame[a] = cx_of(low[a]);
     }
+    df_pair_finish<REDUCE>(A, base, cb, rhs, k, active, up, lswap, lsame, sh);
   }
 }
 
@@ -722,8 +1103,10 @@ inline void launch_t(const HopArgs &A, dim3 grid, dim3 block, bool dag, bool red
 
 // per-precision launchers (dslash_f64.cu, dslash_df64.cu, dslash_f32.cu, dslash_h16.cu)
 void hop_launch_f64(const HopArgs &A, int recon, dim3 grid, dim3 block, bool dag, bool red, cudaStream_t st);
-void hop_launch_df64(const HopArgs &A, int recon, bool pair, dim3 grid, dim3 block, bool dag, bool red,
-                     cudaStream_t st);
+// pair: two threads per site (18-real links); mode 0 scalar, 1 packed FP32x2,
+// 2 packed with the operands staged through shared memory
+void hop_launch_df64(const HopArgs &A, int recon, bool pair, int mode, dim3 grid, dim3 block, bool dag,
+                     bool red, cudaStream_t st);
 // rt: right-hand sides per thread (1, 2, 4); two: two sites per thread (packed FP32x2)
 void hop_launch_f32(const HopArgs &A, int recon, dim3 grid, dim3 block, bool dag, bool red, bool lf, int rt,
                     bool two, cudaStream_t st);
