@@ -278,12 +278,19 @@ def test_full_size_24x48_apply_M(ctx, oracle):
     U, G = _gauge(ctx, L, kind="near", seed=2, eps=0.3)
     psi = inputs.gaussian_spinor(L, 21)
     ref = oracle.apply_M(U, psi, L, kappa, mu)
-    for prec in (lqcd.LQCD_F64, lqcd.LQCD_DF64):
+    # DF64 with 18-real links: the tuned launch, then the scalar, packed and
+    # packed + shared-memory-staged pair kernels (128-thread blocks, full grid)
+    for prec, choice in ((lqcd.LQCD_F64, -1), (lqcd.LQCD_DF64, -1), (lqcd.LQCD_DF64, 1),
+                         (lqcd.LQCD_DF64, 3), (lqcd.LQCD_DF64, 5)):
         _, _, fi = eo_full_from_lexi(ctx, L, psi, prec)
         od, osc = lqcd.alloc_field(L, lqcd.LQCD_FULL, prec)
         fo = lqcd.field(od, lqcd.LQCD_LAYOUT_EO, prec, 1, osc)
-        lqcd.lqcd_apply_M(ctx, G, fi, fo, kappa, mu, lqcd.LQCD_FULL)
-        assert relerr(lexi_from_eo_full(ctx, L, fo), ref) <= 1e-13
+        lqcd.lqcd_set_launch_choice(ctx, choice)
+        try:
+            lqcd.lqcd_apply_M(ctx, G, fi, fo, kappa, mu, lqcd.LQCD_FULL)
+        finally:
+            lqcd.lqcd_set_launch_choice(ctx, -1)
+        assert relerr(lexi_from_eo_full(ctx, L, fo), ref) <= 1e-13, (prec, choice)
 
 
 def test_invalid_arguments_rejected(ctx):
