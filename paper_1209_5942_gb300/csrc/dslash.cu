@@ -63,7 +63,8 @@ lqcd_status launch_hop(lqcd_ctx *ctx, const Geom &g, const HopLaunch &L, int *nb
   struct Cand {
     short bx, by, gm, rt;
     bool lf, two;  // two: two sites per thread in packed FP32x2
-    char pk;       // float-float pair kernel: 0 scalar, 1 packed FP32x2, 2 packed + shared-memory staging
+    char pk;       // float-float pair kernel: 0 scalar, 1 packed FP32x2, 2 packed + shared-memory
+                   // staging; 16-bit two-site kernel: 1 = operands staged in shared memory
   };
   Cand cands[96];
   int ncand = 0, fallback = 0;
@@ -97,6 +98,9 @@ lqcd_status launch_hop(lqcd_ctx *ctx, const Geom &g, const HopLaunch &L, int *nb
   // packed two-site kernel: blocks of 64 threads = 128 sites, one RHS per block row
   if (low)
     for (int gi = 0; gi < 3; gi++) cands[ncand++] = {64, 1, GM[gi], 1, false, true};
+  // for the 16-bit formats also with its operands staged through shared memory
+  if (L.prec == LQCD_BF16S || L.prec == LQCD_F16S)
+    for (int gi = 0; gi < 3; gi++) cands[ncand++] = {64, 1, GM[gi], 1, false, true, 1};
   // default without tuning: the full-grid, one-RHS-per-thread candidate with
   // 128-site blocks for one RHS, or with the most RHS per block for several
   for (int c = 0; c < ncand; c++) {
@@ -120,7 +124,7 @@ lqcd_status launch_hop(lqcd_ctx *ctx, const Geom &g, const HopLaunch &L, int *nb
       case LQCD_F64: hop_launch_f64(args, L.recon, grid, block, dag, red, st); break;
       case LQCD_DF64: hop_launch_df64(args, L.recon, pair, k.pk, grid, block, dag, red, st); break;
       case LQCD_F32: hop_launch_f32(args, L.recon, grid, block, dag, red, k.lf, rt, k.two, st); break;
-      default: hop_launch_h16(args, L.prec, grid, block, dag, red, k.lf, rt, k.two, st); break;
+      default: hop_launch_h16(args, L.prec, grid, block, dag, red, k.lf, rt, k.two, k.pk != 0, st); break;
     }
   };
   char key[160];

@@ -1,12 +1,30 @@
 // dslash_h16.cu -- BF16 / FP16 (per-site scaled spinors, REC12 links)
-// instantiations of the hop kernels (both load orders, and the
-// register-blocked multi-RHS kernel).
+// instantiations of the hop kernels (both load orders, the register-blocked
+// multi-RHS kernel, and the two-site packed kernel with direct loads or with
+// its operands staged through shared memory).
 #include "hop_kernels.cuh"
 
 namespace lqcd {
 
+template <int PREC>
+static void launch_h16_staged(const HopArgs &A, dim3 grid, dim3 block, bool dag, bool red, cudaStream_t st) {
+  const size_t smem = (size_t)h16_staged_bytes(block.x);
+  if (dag) {
+    if (red) hop_h16_staged_kernel<PREC, true, true><<<grid, block, smem, st>>>(A);
+    else hop_h16_staged_kernel<PREC, true, false><<<grid, block, smem, st>>>(A);
+  } else {
+    if (red) hop_h16_staged_kernel<PREC, false, true><<<grid, block, smem, st>>>(A);
+    else hop_h16_staged_kernel<PREC, false, false><<<grid, block, smem, st>>>(A);
+  }
+}
+
 void hop_launch_h16(const HopArgs &A, int prec, dim3 grid, dim3 block, bool dag, bool red, bool lf, int rt,
-                    bool two, cudaStream_t st) {
+                    bool two, bool staged, cudaStream_t st) {
+  if (two && staged) {
+    if (prec == LQCD_BF16S) launch_h16_staged<LQCD_BF16S>(A, grid, block, dag, red, st);
+    else launch_h16_staged<LQCD_F16S>(A, grid, block, dag, red, st);
+    return;
+  }
   if (two) {
     if (prec == LQCD_BF16S) launch_pair2<LQCD_BF16S, 12>(A, grid, block, dag, red, st);
     else launch_pair2<LQCD_F16S, 12>(A, grid, block, dag, red, st);

@@ -2,6 +2,7 @@
 // per-precision translation units dslash_*.cu; see dslash.cu for the design).
 #pragma once
 #include <cstdio>
+#include <type_traits>
 
 #include "internal.h"
 
@@ -161,6 +162,23 @@ struct HopArgs {
 
 // coefficient i (0 c_up, 1 c_dn, 2 d_up, 3 d_dn) in the arithmetic R
 template <class R> LQCD_DEV Cx<R> hop_coef(const HopArgs &A, int i) { return coef_of<R>(A.co, i); }
+
+// Asynchronous global -> shared copies (cp.async, 4, 8 or 16 bytes, both
+// addresses aligned to the size) and their group fences.
+LQCD_DEV void cp_async16(void *smem, const void *gmem) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem) : "memory");
+}
+LQCD_DEV void cp_async8(void *smem, const void *gmem) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gmem) : "memory");
+}
+LQCD_DEV void cp_async4(void *smem, const void *gmem) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gmem) : "memory");
+}
+LQCD_DEV void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> LQCD_DEV void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 template <class R>
 LQCD_DEV void negate_if(Cx<R> v[6], bool neg) {
@@ -401,7 +419,7 @@ __global__ void __launch_bounds__(128) hop_rt_kernel(HopArgs A) {
 // LF selects, for the memory-bound formats, whether both neighbours' loads of
 // a direction are issued before its arithmetic (the autotuner picks).
 template <int PREC, int RECON, bool DAG, bool REDUCE, bool LF>
-__global__ void __launch_bounds__(256) hop_kernel(HopArgs A) {
+__global__ void __launch_bounds__(256, (PREC == LQCD_BF16S || PREC == LQCD_F16S) ? 3 : 1) hop_kernel(HopArgs A) {
   if (A.halt && *(volatile int *)A.halt) return;
   const int rhs = blockIdx.z * blockDim.y + threadIdx.y;
   const int stride = gridDim.x * blockDim.x;
@@ -436,6 +454,29 @@ LQCD_DEV float2 load_nb2(const SpinorView &vin, int jA, int jB, Cx<float2> ps[12
   return make_float2(sa, sb);
 }
 
+// one (direction, sense) step of the two-site packed hop on loaded operands
+template <int RECON, int MU, int S, int DIR>
+LQCD_DEV void hop_step2(const HopArgs &A, const Site &sA, const Site &sB, Cx<float2> ps[12], float2 sc,
+                        Cx<float2> u[9], Cx<float2> acc[12]) {
+  Cx<float2> h[6], v[6];
+  const int tb = DIR == 0 ? A.g.L[3] - 1 : 0;
+  if (MU == 3 && A.g.antiper) {
+    if (sA.t == tb) sc.x = -sc.x;
+    if (sB.t == tb) sc.y = -sc.y;
+  }
+  if (DIR == 0) {
+    project<MU, S>(ps, h);
+    if (RECON == 12) reconstruct_row2(u);
+    mul_link(u, h, v);
+    accumulate_scaled<MU, S>(v, sc, acc);
+  } else {
+    project<MU, -S>(ps, h);
+    if (RECON == 12) reconstruct_row2(u);
+    mul_link_dag(u, h, v);
+    accumulate_scaled<MU, -S>(v, sc, acc);
+  }
+}
+
 template <int PREC, int RECON, int MU, int S>
 LQCD_DEV void hop_dir2(const HopArgs &A, const Site &sA, const Site &sB, int p, int cbA, int cbB,
                        const SpinorView &vin, Cx<float2> acc[12]) {
@@ -443,25 +484,14 @@ LQCD_DEV void hop_dir2(const HopArgs &A, const Site &sA, const Site &sB, int p, 
   for (int dir = 0; dir < 2; dir++) {
     const int d = dir == 0 ? +1 : -1;
     const int jA = neighbour_cb(A.g, sA, MU, d), jB = neighbour_cb(A.g, sB, MU, d);
-    Cx<float2> ps[12], h[6], v[6], u[9];
-    float2 sc = load_nb2<PREC>(vin, jA, jB, ps);
-    if (dir == 0) load_link2<PREC, RECON>(A.U, p, MU, cbA, cbB, u);
-    else load_link2<PREC, RECON>(A.U, p ^ 1, MU, jA, jB, u);
-    const int tb = dir == 0 ? A.g.L[3] - 1 : 0;
-    if (MU == 3 && A.g.antiper) {
-      if (sA.t == tb) sc.x = -sc.x;
-      if (sB.t == tb) sc.y = -sc.y;
-    }
+    Cx<float2> ps[12], u[9];
+    const float2 sc = load_nb2<PREC>(vin, jA, jB, ps);
     if (dir == 0) {
-      project<MU, S>(ps, h);
-      if (RECON == 12) reconstruct_row2(u);
-      mul_link(u, h, v);
-      accumulate_scaled<MU, S>(v, sc, acc);
+      load_link2<PREC, RECON>(A.U, p, MU, cbA, cbB, u);
+      hop_step2<RECON, MU, S, 0>(A, sA, sB, ps, sc, u, acc);
     } else {
-      project<MU, -S>(ps, h);
-      if (RECON == 12) reconstruct_row2(u);
-      mul_link_dag(u, h, v);
-      accumulate_scaled<MU, -S>(v, sc, acc);
+      load_link2<PREC, RECON>(A.U, p ^ 1, MU, jA, jB, u);
+      hop_step2<RECON, MU, S, 1>(A, sA, sB, ps, sc, u, acc);
     }
   }
 }
@@ -517,6 +547,148 @@ inline void launch_pair2(const HopArgs &A, dim3 grid, dim3 block, bool dag, bool
   } else {
     if (red) hop_pair2_kernel<PREC, RECON, false, true><<<grid, block, 0, st>>>(A);
     else hop_pair2_kernel<PREC, RECON, false, false><<<grid, block, 0, st>>>(A);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The two-site packed hop for the 16-bit formats (REC12 links) with its
+// operands staged through shared memory: each (direction, sense) step's
+// neighbour words, site scales and link words of both sites are copied by
+// cp.async one step ahead into the other of two buffers, so their latency
+// hides behind the previous step's arithmetic and no registers are held by
+// loads in flight.  Every thread stages and reads only its own words.  The
+// arithmetic is hop_step2's, so the results are bitwise those of hop_site.
+// Per thread and stage: 3 + 3 spinor words and 2 link words of 16 bytes, 2
+// link tails of 8 bytes and 2 scales (152 bytes).
+// ---------------------------------------------------------------------------
+LQCD_HD int h16_staged_bytes(int bx) { return 304 * bx; }
+
+struct H16Stage {
+  uint4 *w4;  // [2][8][bx]: spinor A (3), spinor B (3), link A, link B
+  uint2 *w2;  // [2][2][bx]: link tails A, B
+  float *wf;  // [2][2][bx]: scales A, B
+  int bx, tx;
+};
+
+template <int MU, int DIR, int ST>
+LQCD_DEV void h16_stage_issue(const HopArgs &A, const Site &sA, const Site &sB, int p, int cbA, int cbB,
+                              const SpinorView &vin, const H16Stage &B) {
+  const int d = DIR == 0 ? +1 : -1;
+  const int jA = neighbour_cb(A.g, sA, MU, d), jB = neighbour_cb(A.g, sB, MU, d);
+  const uint4 *pin = (const uint4 *)vin.ptr;
+  const size_t Vh = vin.Vh;
+  uint4 *w4 = B.w4 + ST * 8 * B.bx + B.tx;
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    cp_async16(w4 + k * B.bx, pin + k * Vh + jA);
+    cp_async16(w4 + (3 + k) * B.bx, pin + k * Vh + jB);
+  }
+  float *wf = B.wf + ST * 2 * B.bx + B.tx;
+  cp_async4(wf, vin.scale + jA);
+  cp_async4(wf + B.bx, vin.scale + jB);
+  const char *base = (const char *)A.U.ptr + (DIR == 0 ? p : p ^ 1) * A.U.parity_stride + MU * A.U.mu_stride;
+  const int lA = DIR == 0 ? cbA : jA, lB = DIR == 0 ? cbB : jB;
+  cp_async16(w4 + 6 * B.bx, (const uint4 *)base + lA);
+  cp_async16(w4 + 7 * B.bx, (const uint4 *)base + lB);
+  const uint2 *tail = (const uint2 *)(base + (size_t)A.U.Vh * 16);
+  uint2 *w2 = B.w2 + ST * 2 * B.bx + B.tx;
+  cp_async8(w2, tail + lA);
+  cp_async8(w2 + B.bx, tail + lB);
+}
+
+// N complex values of site A (words wa) and site B (words wb) as packed pairs
+template <class H, int N>
+LQCD_DEV void h16_unpack2(const uint32_t *wa, const uint32_t *wb, Cx<float2> *out) {
+#pragma unroll
+  for (int j = 0; j < N; j++)
+    out[j] = {make_float2(Half16<H>::to_f((uint16_t)(wa[j] & 0xFFFFu)), Half16<H>::to_f((uint16_t)(wb[j] & 0xFFFFu))),
+              make_float2(Half16<H>::to_f((uint16_t)(wa[j] >> 16)), Half16<H>::to_f((uint16_t)(wb[j] >> 16)))};
+}
+template <class H> LQCD_DEV void h16_unpack2(uint4 a, uint4 b, Cx<float2> *out) {
+  const uint32_t wa[4] = {a.x, a.y, a.z, a.w}, wb[4] = {b.x, b.y, b.z, b.w};
+  h16_unpack2<H, 4>(wa, wb, out);
+}
+
+template <class H, int STEP, int S>
+LQCD_DEV void h16_staged_steps(const HopArgs &A, const Site &sA, const Site &sB, int p, int cbA, int cbB,
+                               const SpinorView &vin, const H16Stage &B, Cx<float2> acc[12]) {
+  if constexpr (STEP < 8) {
+    constexpr int MU = STEP >> 1, DIR = STEP & 1, ST = STEP & 1;
+    constexpr int NMU = (STEP + 1) >> 1, NDIR = (STEP + 1) & 1;
+    if constexpr (STEP + 1 < 8) {
+      h16_stage_issue<NMU, NDIR, NDIR>(A, sA, sB, p, cbA, cbB, vin, B);
+      cp_async_commit();
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncwarp();
+    {
+      const uint4 *w4 = B.w4 + ST * 8 * B.bx + B.tx;
+      const uint2 *w2 = B.w2 + ST * 2 * B.bx + B.tx;
+      const float *wf = B.wf + ST * 2 * B.bx + B.tx;
+      Cx<float2> ps[12], u[9];
+#pragma unroll
+      for (int k = 0; k < 3; k++) h16_unpack2<H>(w4[k * B.bx], w4[(3 + k) * B.bx], ps + 4 * k);
+      h16_unpack2<H>(w4[6 * B.bx], w4[7 * B.bx], u);
+      const uint2 ta = w2[0], tb = w2[B.bx];
+      const uint32_t wa[2] = {ta.x, ta.y}, wb[2] = {tb.x, tb.y};
+      h16_unpack2<H, 2>(wa, wb, u + 4);
+      const float2 sc = make_float2(wf[0], wf[B.bx]);
+      hop_step2<12, MU, S, DIR>(A, sA, sB, ps, sc, u, acc);
+    }
+    __syncwarp();
+    h16_staged_steps<H, STEP + 1, S>(A, sA, sB, p, cbA, cbB, vin, B, acc);
+  }
+}
+
+template <int PREC, bool DAG, bool REDUCE>
+__global__ void __launch_bounds__(64, 6) hop_h16_staged_kernel(HopArgs A) {
+  using H = typename std::conditional<PREC == LQCD_BF16S, __nv_bfloat16, __half>::type;
+  extern __shared__ uint4 h16_words[];
+  if (A.halt && *(volatile int *)A.halt) return;
+  const int rhs = blockIdx.z;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int p = A.out_parity;
+  H16Stage B;
+  B.bx = blockDim.x;
+  B.tx = threadIdx.x;
+  B.w4 = h16_words;
+  B.w2 = (uint2 *)(B.w4 + 16 * B.bx);
+  B.wf = (float *)(B.w2 + 4 * B.bx);
+  const int stride = gridDim.x * 128;
+  for (int base = blockIdx.x * 128; base < A.g.Vh; base += stride) {
+    const int cbA = base + 64 * w + lane, cbB = cbA + 32;
+    const bool okA = cbA < A.g.Vh && rhs < A.nrhs, okB = cbB < A.g.Vh && rhs < A.nrhs;
+    // lanes past the end recompute a valid site and store nothing
+    const int cA = okA ? cbA : A.g.Vh - 1, cB = okB ? cbB : A.g.Vh - 1;
+    const int r = rhs < A.nrhs ? rhs : A.nrhs - 1;
+    const Site sA = site_of(A.g, p, cA), sB = site_of(A.g, p, cB);
+    SpinorView vin{A.in + r * A.in_rs, A.in_scale + r * A.in_srs, A.g.Vh};
+    Cx<float2> acc[12];
+#pragma unroll
+    for (int k = 0; k < 12; k++) acc[k] = czero<float2>();
+    constexpr int S = DAG ? -1 : 1;
+    h16_stage_issue<0, 0, 0>(A, sA, sB, p, cA, cB, vin, B);
+    cp_async_commit();
+    h16_staged_steps<H, 0, S>(A, sA, sB, p, cA, cB, vin, B, acc);
+    double nA = 0.0, nB = 0.0;
+    {
+      Cx<float> a[12];
+#pragma unroll
+      for (int k = 0; k < 12; k++) a[k] = lane_x(acc[k]);
+      if (okA) nA = hop_epilogue<PREC, REDUCE>(A, cbA, rhs, a);
+    }
+    {
+      Cx<float> b[12];
+#pragma unroll
+      for (int k = 0; k < 12; k++) b[k] = lane_y(acc[k]);
+      if (okB) nB = hop_epilogue<PREC, REDUCE>(A, cbB, rhs, b);
+    }
+    if (REDUCE) {
+      hop_warp_partial(A, cbA, rhs, nA);
+      hop_warp_partial(A, cbB, rhs, nB);
+    }
   }
 }
 
@@ -928,12 +1100,6 @@ __global__ void __launch_bounds__(128, 4) hop_df64_pair_kernel(HopArgs A) {
 // visible, and the __syncwarp after each step keeps a buffer from being
 // refilled while it is still read.
 // ---------------------------------------------------------------------------
-LQCD_DEV void cp_async16(void *smem, const void *gmem) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem) : "memory");
-}
-LQCD_DEV void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N> LQCD_DEV void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 // 16-byte shared-memory words per block row of bx threads: 2 stages x (6 per thread + 9 per site)
 LQCD_HD int df_staged_words(int bx) { return 2 * (6 * bx + 9 * (bx / 2)); }
@@ -1110,8 +1276,9 @@ void hop_launch_df64(const HopArgs &A, int recon, bool pair, int mode, dim3 grid
 // rt: right-hand sides per thread (1, 2, 4); two: two sites per thread (packed FP32x2)
 void hop_launch_f32(const HopArgs &A, int recon, dim3 grid, dim3 block, bool dag, bool red, bool lf, int rt,
                     bool two, cudaStream_t st);
+// staged: the two-site kernel with its operands staged through shared memory
 void hop_launch_h16(const HopArgs &A, int prec, dim3 grid, dim3 block, bool dag, bool red, bool lf, int rt,
-                    bool two, cudaStream_t st);
+                    bool two, bool staged, cudaStream_t st);
 void hop_batched_f64(int recon, bool dag, bool red, const HopArgs *d, const int2 *tl, int ntiles, int grid,
                      const int *halt, cudaStream_t st);
 void hop_batched_df64(int recon, bool dag, bool red, const HopArgs *d, const int2 *tl, int ntiles, int grid,
