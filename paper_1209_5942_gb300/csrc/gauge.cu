@@ -171,6 +171,16 @@ LQCD_DEV bool thread_site(const Geom &g, long tid, int *p, int *cb, int c[4]) {
   return true;
 }
 
+// thread -> (direction mu, site): consecutive threads take consecutive sites
+// of one direction, so the per-link kernels read and write link-ordered
+// planes contiguously and run one thread per link
+LQCD_DEV bool thread_link(const Geom &g, long tid, int *mu, int *p, int *cb, int c[4]) {
+  const long V = 2L * g.Vh;
+  if (tid >= 4 * V) return false;
+  *mu = (int)(tid / V);
+  return thread_site(g, tid - (long)(*mu) * V, p, cb, c);
+}
+
 LQCD_DEV double block_sum(double v, double *sh) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -240,11 +250,11 @@ LQCD_DEV M3 signed_link(const double2 *U, const Geom &g, const int c[4], int nu,
 
 __global__ void __launch_bounds__(128) staple6_kernel(const double2 *U, Geom g, double2 *S) {
   long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  int p, cb, c[4];
-  if (!thread_site(g, tid, &p, &cb, c)) return;
+  int mu, p, cb, c[4];
+  if (!thread_link(g, tid, &mu, &p, &cb, c)) return;
   const long V = 2L * g.Vh;
   const long lexi = at(g, c).lexi;
-  for (int mu = 0; mu < 4; mu++) {
+  {
     int cpm[4] = {c[0], c[1], c[2], c[3]};
     coords_shift(g, cpm, mu, +1);
     for (int nu = 0; nu < 4; nu++) {
@@ -274,13 +284,12 @@ LQCD_DEV void add_scaled(M3 &A, double c, const M3 &t) {
 __global__ void __launch_bounds__(128) gauge_force_sym_kernel(const double2 *U, const double2 *S, Geom g,
                                                               double beta, double c1, double *out) {
   long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  int p, cb, c[4];
-  if (!thread_site(g, tid, &p, &cb, c)) return;
+  int mu, p, cb, c[4];
+  if (!thread_link(g, tid, &mu, &p, &cb, c)) return;
   const long V = 2L * g.Vh;
   const Pos s0 = at(g, c);
   const double c0 = 1.0 - 8.0 * c1;
-#pragma unroll 1
-  for (int mu = 0; mu < 4; mu++) {
+  {
     int cpm[4] = {c[0], c[1], c[2], c[3]}, cmm[4] = {c[0], c[1], c[2], c[3]};
     coords_shift(g, cpm, mu, +1);
     coords_shift(g, cmm, mu, -1);
@@ -322,28 +331,57 @@ __global__ void __launch_bounds__(128) gauge_force_sym_kernel(const double2 *U, 
 // accuracy on the FP32 pipe, the hop's DF64 format): GB300's FP64 pipe runs at
 // 1/64 of the FP32 rate, and the tlSym force is ~10^4 flop per link.  Links
 // come from the DF64 copy of the field; 3x3 products use the error-free
-// complex dot product of the hop; W is converted to FP64 for the traces.
+// complex dot product of the hop (packed FP32x2); W is converted to FP64 for
+// the traces.
 // ---------------------------------------------------------------------------
 struct M3d {
   Cx<df> m[9];
 };
+// The 3x3 products run the packed FP32x2 form of the error-free complex dot
+// product (the bits of dfdot3, normalised): each column of b (row of a for
+// a b^+) and its product with i (or -i) are formed once and reused for the
+// three dot products that share it.
+LQCD_DEV float4 f4_of(Cx<df> z) { return make_float4(z.re.hi, z.im.hi, z.re.lo, z.im.lo); }
+LQCD_DEV df2 p_of(Cx<df> z) { return {make_float2(z.re.hi, z.im.hi), make_float2(z.re.lo, z.im.lo)}; }
+LQCD_DEV Cx<df> normalised_of(df2 a) {  // fast_two_sum on each lane
+  const float2 s = __fadd2_rn(a.hi, a.lo);
+  const float2 e = __fadd2_rn(a.lo, neg2(__fadd2_rn(s, neg2(a.hi))));
+  return {{s.x, e.x}, {s.y, e.y}};
+}
 LQCD_DEV M3d dmul(const M3d &a, const M3d &b) {  // a b
   M3d r;
 #pragma unroll
-  for (int i = 0; i < 3; i++)
+  for (int j = 0; j < 3; j++) {
+    df2 y1[3], y2[3];
 #pragma unroll
-    for (int j = 0; j < 3; j++)
-      r.m[3 * i + j] = dfdot3<false>(a.m[3 * i], a.m[3 * i + 1], a.m[3 * i + 2], b.m[j], b.m[3 + j], b.m[6 + j]);
+    for (int q = 0; q < 3; q++) {
+      y1[q] = p_of(b.m[3 * q + j]);
+      y2[q] = times_i_p(y1[q]);
+    }
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+      const float4 x[3] = {f4_of(a.m[3 * i]), f4_of(a.m[3 * i + 1]), f4_of(a.m[3 * i + 2])};
+      r.m[3 * i + j] = normalised_of(dfdot3_p(x, y1, y2));
+    }
+  }
   return r;
 }
 LQCD_DEV M3d dmul_nd(const M3d &a, const M3d &b) {  // a b^+
   M3d r;
 #pragma unroll
-  for (int i = 0; i < 3; i++)
+  for (int i = 0; i < 3; i++) {
+    df2 y1[3], y2[3];
 #pragma unroll
-    for (int j = 0; j < 3; j++)
-      r.m[3 * i + j] = dfdot3<true>(b.m[3 * j], b.m[3 * j + 1], b.m[3 * j + 2], a.m[3 * i], a.m[3 * i + 1],
-                                    a.m[3 * i + 2]);
+    for (int q = 0; q < 3; q++) {
+      y1[q] = p_of(a.m[3 * i + q]);
+      y2[q] = times_mi_p(y1[q]);
+    }
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+      const float4 x[3] = {f4_of(b.m[3 * j]), f4_of(b.m[3 * j + 1]), f4_of(b.m[3 * j + 2])};
+      r.m[3 * i + j] = normalised_of(dfdot3_p(x, y1, y2));
+    }
+  }
   return r;
 }
 LQCD_DEV M3d load_link_d(const GaugeView &Ud, const Pos &s, int mu) {
@@ -380,19 +418,21 @@ LQCD_DEV M3d load_stap_d(const float4 *S, long V, int mu, int k, long lexi) {
   }
   return r;
 }
-LQCD_DEV void add_lazy_m(M3d &A, const M3d &t) {
+LQCD_DEV void add_lazy_m(M3d &A, const M3d &t) {  // cadd_lazy on every entry, packed
 #pragma unroll
-  for (int e = 0; e < 9; e++) A.m[e] = cadd_lazy(A.m[e], t.m[e]);
+  for (int e = 0; e < 9; e++) {
+    const df2 r = add_lazy_p(p_of(A.m[e]), p_of(t.m[e]));
+    A.m[e] = {{r.hi.x, r.lo.x}, {r.hi.y, r.lo.y}};
+  }
 }
 
 __global__ void __launch_bounds__(128) staple6_df_kernel(GaugeView Ud, Geom g, float4 *S) {
   long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  int p, cb, c[4];
-  if (!thread_site(g, tid, &p, &cb, c)) return;
+  int mu, p, cb, c[4];
+  if (!thread_link(g, tid, &mu, &p, &cb, c)) return;
   const long V = 2L * g.Vh;
   const long lexi = at(g, c).lexi;
-#pragma unroll 1
-  for (int mu = 0; mu < 4; mu++) {
+  {
     int cpm[4] = {c[0], c[1], c[2], c[3]};
     coords_shift(g, cpm, mu, +1);
 #pragma unroll 1
@@ -410,16 +450,15 @@ __global__ void __launch_bounds__(128) staple6_df_kernel(GaugeView Ud, Geom g, f
 
 // dS/domega of c0 (plaquette) + c1 (rectangle) in float-float; c1 = 0 gives
 // the Wilson force from the plaquette staples alone
-__global__ void __launch_bounds__(128) gauge_force_df_kernel(GaugeView Ud, const float4 *S, Geom g, double beta,
+__global__ void __launch_bounds__(128, 3) gauge_force_df_kernel(GaugeView Ud, const float4 *S, Geom g, double beta,
                                                              double c1, double *out) {
   long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  int p, cb, c[4];
-  if (!thread_site(g, tid, &p, &cb, c)) return;
+  int mu, p, cb, c[4];
+  if (!thread_link(g, tid, &mu, &p, &cb, c)) return;
   const long V = 2L * g.Vh;
   const Pos s0 = at(g, c);
   const double c0 = 1.0 - 8.0 * c1;
-#pragma unroll 1
-  for (int mu = 0; mu < 4; mu++) {
+  {
     int cpm[4] = {c[0], c[1], c[2], c[3]}, cmm[4] = {c[0], c[1], c[2], c[3]};
     coords_shift(g, cpm, mu, +1);
     coords_shift(g, cmm, mu, -1);
@@ -503,11 +542,11 @@ __global__ void __launch_bounds__(128) rectangle_kernel(const double2 *U, Geom g
 // Wilson action (c1 = 0); the tlSym force is gauge_force_sym_kernel.
 __global__ void __launch_bounds__(128) gauge_force_kernel(const double2 *U, Geom g, double beta, double *out) {
   long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  int p, cb, c[4];
-  if (!thread_site(g, tid, &p, &cb, c)) return;
+  int mu, p, cb, c[4];
+  if (!thread_link(g, tid, &mu, &p, &cb, c)) return;
   long V = 2L * g.Vh;
   Pos s = at(g, c);
-  for (int mu = 0; mu < 4; mu++) {
+  {
     M3 A = staple(U, g, c, mu);
     M3 W = mmul(load_link(U, g, s, mu), A);
     const C *w = W.m;
@@ -930,9 +969,12 @@ LQCD_DEV void reunitarize(M3 &u) {
 }
 
 // exp(X) for X = i eps P (anti-Hermitian, traceless): X is scaled by 2^-s until
-// its Frobenius norm is below 1/2, the Taylor polynomial of degree 14 is
-// evaluated by Horner's rule (truncation error < 1e-20 at that norm), and the
-// result is squared s times.
+// its Frobenius norm r is at most 1/2, the Taylor polynomial is evaluated by
+// Horner's rule, and the result is squared s times.  The degree n is the
+// smallest (at most 15) whose first omitted term r^(n+1)/(n+1)! is below
+// 2^-60 (the remainder is below twice that, ~1e-18, against |exp X| ~ 1):
+// the molecular-dynamics steps give r of a few 10^-2 and a degree near 8,
+// half the products of a fixed degree.
 LQCD_DEV M3 expm_su3(const M3 &X0) {
   double nrm = 0.0;
 #pragma unroll
@@ -943,6 +985,8 @@ LQCD_DEV M3 expm_su3(const M3 &X0) {
     nrm *= 0.5;
     s++;
   }
+  int deg = 1;
+  for (double t = nrm * nrm * 0.5; deg < 15 && t >= 0x1p-60; t *= nrm / (deg + 1)) deg++;
   double sc = ldexp(1.0, -s);
   M3 X;
 #pragma unroll
@@ -951,7 +995,7 @@ LQCD_DEV M3 expm_su3(const M3 &X0) {
 #pragma unroll
   for (int k = 0; k < 9; k++) E.m[k] = czero<double>();
   E.m[0] = E.m[4] = E.m[8] = {1.0, 0.0};
-  for (int n = 14; n >= 1; n--) {  // E = 1 + X E / n
+  for (int n = deg; n >= 1; n--) {  // E = 1 + X E / n
     M3 T = mmul(X, E);
     double inv = 1.0 / n;
 #pragma unroll
@@ -986,11 +1030,11 @@ LQCD_DEV M3 algebra_matrix(const double *p, double eps) {
 
 __global__ void __launch_bounds__(128) gauge_update_kernel(double2 *U, Geom g, const double *P, double eps) {
   long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  int p, cb, c[4];
-  if (!thread_site(g, tid, &p, &cb, c)) return;
+  int mu, p, cb, c[4];
+  if (!thread_link(g, tid, &mu, &p, &cb, c)) return;
   long V = 2L * g.Vh;
   Pos s = at(g, c);
-  for (int mu = 0; mu < 4; mu++) {
+  {
     M3 E = expm_su3(algebra_matrix(P + ((size_t)mu * V + s.lexi) * 8, eps));
     M3 u = mmul(E, load_link(U, g, s, mu));
     reunitarize(u);
@@ -1076,21 +1120,21 @@ lqcd_status gauge_force_raw(lqcd_ctx *ctx, lqcd_gauge *U, double beta, double c1
     if (prec == LQCD_DF64) {
       GaugeView Ud;
       LQCD_TRY(gauge_view(ctx, U, LQCD_DF64, 18, &Ud));
-      staple6_df_kernel<<<nblk(V), 128, 0, ctx->stream>>>(Ud, U->g, (float4 *)ctx->staples);
-      gauge_force_df_kernel<<<nblk(V), 128, 0, ctx->stream>>>(Ud, (const float4 *)ctx->staples, U->g, beta, c1,
+      staple6_df_kernel<<<nblk(4 * V), 128, 0, ctx->stream>>>(Ud, U->g, (float4 *)ctx->staples);
+      gauge_force_df_kernel<<<nblk(4 * V), 128, 0, ctx->stream>>>(Ud, (const float4 *)ctx->staples, U->g, beta, c1,
                                                               dSdw);
       LQCD_CUDA(ctx, cudaGetLastError());
       return LQCD_OK;
     }
-    staple6_kernel<<<nblk(V), 128, 0, ctx->stream>>>((const double2 *)U->master, U->g,
+    staple6_kernel<<<nblk(4 * V), 128, 0, ctx->stream>>>((const double2 *)U->master, U->g,
                                                      (double2 *)ctx->staples);
-    gauge_force_sym_kernel<<<nblk(V), 128, 0, ctx->stream>>>((const double2 *)U->master,
+    gauge_force_sym_kernel<<<nblk(4 * V), 128, 0, ctx->stream>>>((const double2 *)U->master,
                                                              (const double2 *)ctx->staples, U->g, beta, c1,
                                                              dSdw);
     LQCD_CUDA(ctx, cudaGetLastError());
     return LQCD_OK;
   }
-  gauge_force_kernel<<<nblk(V), 128, 0, ctx->stream>>>((const double2 *)U->master, U->g, beta, dSdw);
+  gauge_force_kernel<<<nblk(4 * V), 128, 0, ctx->stream>>>((const double2 *)U->master, U->g, beta, dSdw);
   LQCD_CUDA(ctx, cudaGetLastError());
   return LQCD_OK;
 }
@@ -1150,7 +1194,7 @@ lqcd_status gaussian_spinor_raw(lqcd_ctx *ctx, const Geom &g, void *eo_full, int
 }
 
 lqcd_status gauge_update_raw(lqcd_ctx *ctx, lqcd_gauge *U, const double *P, double eps) {
-  gauge_update_kernel<<<nblk(2L * U->g.Vh), 128, 0, ctx->stream>>>((double2 *)U->master, U->g, P, eps);
+  gauge_update_kernel<<<nblk(8L * U->g.Vh), 128, 0, ctx->stream>>>((double2 *)U->master, U->g, P, eps);
   LQCD_CUDA(ctx, cudaGetLastError());
   U->version++;
   return LQCD_OK;

@@ -796,75 +796,6 @@ LQCD_DEV void df_pair_dir(const HopArgs &A, const Site &s, int p, int cb, int k,
   }
 }
 
-// ---------------------------------------------------------------------------
-// The pair step in packed FP32x2 arithmetic.  A complex double-word is held
-// as df2 {hi = (re.hi, im.hi), lo = (re.lo, im.lo)} -- the order of its
-// 16-byte word -- and each __fadd2_rn / __fmul2_rn / __ffma2_rn does the
-// scalar operation of the real and the imaginary lane at once.  Every lane
-// performs exactly the operations of the scalar step, in the same order (a
-// negated factor is moved to the other operand, which rounds identically),
-// so the two forms give the same bits with about 40 % fewer instructions.
-// ---------------------------------------------------------------------------
-struct df2 {
-  float2 hi, lo;
-};
-LQCD_DEV df2 df2_of(float4 w) { return {make_float2(w.x, w.y), make_float2(w.z, w.w)}; }
-LQCD_DEV df2 df2_zero() { return {make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)}; }
-LQCD_DEV Cx<df> cx_of(df2 a) { return {{a.hi.x, a.lo.x}, {a.hi.y, a.lo.y}}; }
-LQCD_DEV df2 neg_p(df2 a) { return {neg2(a.hi), neg2(a.lo)}; }
-LQCD_DEV df2 times_i_p(df2 a) {  // (-im, re)
-  return {make_float2(-a.hi.y, a.hi.x), make_float2(-a.lo.y, a.lo.x)};
-}
-LQCD_DEV df2 times_mi_p(df2 a) {  // (im, -re)
-  return {make_float2(a.hi.y, -a.hi.x), make_float2(a.lo.y, -a.lo.x)};
-}
-// two_sum on each lane
-LQCD_DEV void two_sum_p(float2 a, float2 b, float2 &s, float2 &e) {
-  s = __fadd2_rn(a, b);
-  const float2 bb = __fadd2_rn(s, neg2(a));
-  e = __fadd2_rn(__fadd2_rn(a, neg2(__fadd2_rn(s, neg2(bb)))), __fadd2_rn(b, neg2(bb)));
-}
-// add_lazy on each lane
-LQCD_DEV df2 add_lazy_p(df2 a, df2 b) {
-  df2 r;
-  two_sum_p(a.hi, b.hi, r.hi, r.lo);
-  r.lo = __fadd2_rn(r.lo, __fadd2_rn(a.lo, b.lo));
-  return r;
-}
-// product of the broadcast double-word (ah, al) with both lanes of b: the
-// leading part p and its first-order error pe, as in dfacc_add_prod
-LQCD_DEV void prod_p(float ah, float al, df2 b, float2 &p, float2 &pe) {
-  const float2 h2 = make_float2(ah, ah), l2 = make_float2(al, al);
-  p = __fmul2_rn(h2, b.hi);
-  pe = __ffma2_rn(h2, b.hi, neg2(p));
-  pe = __ffma2_rn(h2, b.lo, pe);
-  pe = __ffma2_rn(l2, b.hi, pe);
-}
-LQCD_DEV void acc_p(df2 &A, float ah, float al, df2 b) {
-  float2 p, pe, t;
-  prod_p(ah, al, b, p, pe);
-  two_sum_p(A.hi, p, A.hi, t);
-  A.lo = __fadd2_rn(A.lo, __fadd2_rn(t, pe));
-}
-// dfdot3<CONJ, true> with lanes (re, im): x are the link words, y1 = h and
-// y2 = i h (CONJ: -i h), so that lane re takes x.re y.re then -+ x.im y.im
-// and lane im takes x.re y.im then +- x.im y.re, as the scalar form does
-LQCD_DEV df2 dfdot3_p(const float4 x[3], const df2 y1[3], const df2 y2[3]) {
-  df2 A;
-  prod_p(x[0].x, x[0].z, y1[0], A.hi, A.lo);
-  acc_p(A, x[0].y, x[0].w, y2[0]);
-#pragma unroll
-  for (int j = 1; j < 3; j++) {
-    acc_p(A, x[j].x, x[j].z, y1[j]);
-    acc_p(A, x[j].y, x[j].w, y2[j]);
-  }
-  return A;
-}
-// v times the unit f: 0 -> 1, 1 -> i, 2 -> -1, 3 -> -i
-template <int F> LQCD_DEV df2 unit_p(df2 v) {
-  return F == 0 ? v : F == 1 ? times_i_p(v) : F == 2 ? neg_p(v) : times_mi_p(v);
-}
-
 template <int MU, int S, int DIR, class SP, class LK>
 LQCD_DEV void df_pair_step_p(const HopArgs &A, const Site &s, int k, SP sp, LK lk, df2 up[3], df2 lswap[3],
                              df2 lsame[3]) {
