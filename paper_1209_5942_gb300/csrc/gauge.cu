@@ -968,17 +968,20 @@ LQCD_DEV void reunitarize(M3 &u) {
   reconstruct_row2(u.m);
 }
 
-// exp(X) for X = i eps P (anti-Hermitian, traceless): X is scaled by 2^-s until
-// its Frobenius norm r is at most 1/2, the Taylor polynomial is evaluated by
-// Horner's rule, and the result is squared s times.  The degree n is the
-// smallest (at most 15) whose first omitted term r^(n+1)/(n+1)! is below
-// 2^-60 (the remainder is below twice that, ~1e-18, against |exp X| ~ 1):
-// the molecular-dynamics steps give r of a few 10^-2 and a degree near 8,
-// half the products of a fixed degree.
-LQCD_DEV M3 expm_su3(const M3 &X0) {
+// exp(i h) for a traceless Hermitian 3x3 h (the molecular-dynamics step
+// h = eps sum_a p^a lambda^a / 2).  h is scaled by 2^-s until its Frobenius
+// norm r is at most 1/2 (the result is squared s times).  By Cayley-Hamilton
+// h^3 = c1 h + c0 with c1 = tr(h^2)/2 and c0 = det h, so every power is
+// h^k = p_k + q_k h + r_k h^2 with the scalar recurrence
+//   (p, q, r)_{k+1} = (c0 r_k, p_k + c1 r_k, q_k),
+// and exp(i h) = a0 + a1 h + a2 h^2 with a_j = sum_k i^k / k! (p, q, r)_k.
+// The series is summed up to the smallest degree whose first omitted term
+// r^(n+1)/(n+1)! is below 2^-60 (the remainder is below twice that): one
+// 3x3 product (h^2) instead of one per Taylor degree.
+LQCD_DEV M3 expi_herm(const M3 &h0) {
   double nrm = 0.0;
 #pragma unroll
-  for (int k = 0; k < 9; k++) nrm += norm2_d(X0.m[k]);
+  for (int k = 0; k < 9; k++) nrm += norm2_d(h0.m[k]);
   nrm = sqrt(nrm);
   int s = 0;
   while (nrm > 0.5 && s < 60) {
@@ -986,46 +989,62 @@ LQCD_DEV M3 expm_su3(const M3 &X0) {
     s++;
   }
   int deg = 1;
-  for (double t = nrm * nrm * 0.5; deg < 15 && t >= 0x1p-60; t *= nrm / (deg + 1)) deg++;
-  double sc = ldexp(1.0, -s);
-  M3 X;
+  for (double t = nrm * nrm * 0.5; deg < 30 && t >= 0x1p-60; t *= nrm / (deg + 1)) deg++;
+  const double sc = ldexp(1.0, -s);
+  M3 h;
 #pragma unroll
-  for (int k = 0; k < 9; k++) X.m[k] = {X0.m[k].re * sc, X0.m[k].im * sc};
+  for (int k = 0; k < 9; k++) h.m[k] = {h0.m[k].re * sc, h0.m[k].im * sc};
+  const M3 h2 = mmul(h, h);
+  const double c1 = 0.5 * (h2.m[0].re + h2.m[4].re + h2.m[8].re);
+  const C dt = h.m[0] * (h.m[4] * h.m[8] - h.m[5] * h.m[7]) - h.m[1] * (h.m[3] * h.m[8] - h.m[5] * h.m[6]) +
+               h.m[2] * (h.m[3] * h.m[7] - h.m[4] * h.m[6]);
+  const double c0 = dt.re;  // det of a Hermitian matrix is real
+  // k = 0: h^0 = 1; the terms i^k / k! alternate between the real part
+  // (k even, sign (-1)^(k/2)) and the imaginary part (k odd)
+  double p = 1.0, q = 0.0, r = 0.0, w = 1.0;
+  double a0r = 1.0, a0i = 0.0, a1r = 0.0, a1i = 0.0, a2r = 0.0, a2i = 0.0;
+  for (int k = 1; k <= deg; k++) {
+    const double pn = c0 * r, qn = fma(c1, r, p), rn = q;
+    p = pn;
+    q = qn;
+    r = rn;
+    w /= k;
+    const double f = (k & 2) ? -w : w;  // i^k = f-sign times 1 (k even) or i (k odd)
+    if (k & 1) {
+      a0i = fma(f, p, a0i);
+      a1i = fma(f, q, a1i);
+      a2i = fma(f, r, a2i);
+    } else {
+      a0r = fma(f, p, a0r);
+      a1r = fma(f, q, a1r);
+      a2r = fma(f, r, a2r);
+    }
+  }
+  const C a1 = {a1r, a1i}, a2 = {a2r, a2i};
   M3 E;
 #pragma unroll
-  for (int k = 0; k < 9; k++) E.m[k] = czero<double>();
-  E.m[0] = E.m[4] = E.m[8] = {1.0, 0.0};
-  for (int n = deg; n >= 1; n--) {  // E = 1 + X E / n
-    M3 T = mmul(X, E);
-    double inv = 1.0 / n;
-#pragma unroll
-    for (int k = 0; k < 9; k++) E.m[k] = {T.m[k].re * inv, T.m[k].im * inv};
-    E.m[0].re += 1.0;
-    E.m[4].re += 1.0;
-    E.m[8].re += 1.0;
-  }
-  for (int q = 0; q < s; q++) E = mmul(E, E);
+  for (int k = 0; k < 9; k++) E.m[k] = a1 * h.m[k] + a2 * h2.m[k];
+  E.m[0] = E.m[0] + C{a0r, a0i};
+  E.m[4] = E.m[4] + C{a0r, a0i};
+  E.m[8] = E.m[8] + C{a0r, a0i};
+  for (int t = 0; t < s; t++) E = mmul(E, E);
   return E;
 }
 
-// i eps sum_a p^a lambda^a / 2
-LQCD_DEV M3 algebra_matrix(const double *p, double eps) {
-  const double h = 0.5 * eps, r3 = 0.57735026918962576451;
-  // H = sum p^a lambda^a / 2 (Hermitian); X = i eps H
-  C H[9];
-  H[0] = {p[2] + p[7] * r3, 0.0};
-  H[4] = {-p[2] + p[7] * r3, 0.0};
-  H[8] = {-2.0 * p[7] * r3, 0.0};
-  H[1] = {p[0], -p[1]};
-  H[3] = {p[0], p[1]};
-  H[2] = {p[3], -p[4]};
-  H[6] = {p[3], p[4]};
-  H[5] = {p[5], -p[6]};
-  H[7] = {p[5], p[6]};
-  M3 X;
-#pragma unroll
-  for (int k = 0; k < 9; k++) X.m[k] = {-h * H[k].im, h * H[k].re};
-  return X;
+// eps sum_a p^a lambda^a / 2 (Hermitian, traceless)
+LQCD_DEV M3 algebra_herm(const double *p, double eps) {
+  const double e = 0.5 * eps, r3 = 0.57735026918962576451;
+  M3 H;
+  H.m[0] = {e * (p[2] + p[7] * r3), 0.0};
+  H.m[4] = {e * (-p[2] + p[7] * r3), 0.0};
+  H.m[8] = {e * (-2.0 * p[7] * r3), 0.0};
+  H.m[1] = {e * p[0], -e * p[1]};
+  H.m[3] = {e * p[0], e * p[1]};
+  H.m[2] = {e * p[3], -e * p[4]};
+  H.m[6] = {e * p[3], e * p[4]};
+  H.m[5] = {e * p[5], -e * p[6]};
+  H.m[7] = {e * p[5], e * p[6]};
+  return H;
 }
 
 __global__ void __launch_bounds__(128) gauge_update_kernel(double2 *U, Geom g, const double *P, double eps) {
@@ -1035,7 +1054,7 @@ __global__ void __launch_bounds__(128) gauge_update_kernel(double2 *U, Geom g, c
   long V = 2L * g.Vh;
   Pos s = at(g, c);
   {
-    M3 E = expm_su3(algebra_matrix(P + ((size_t)mu * V + s.lexi) * 8, eps));
+    M3 E = expi_herm(algebra_herm(P + ((size_t)mu * V + s.lexi) * 8, eps));
     M3 u = mmul(E, load_link(U, g, s, mu));
     reunitarize(u);
     store_link(U, g, s, mu, u);
