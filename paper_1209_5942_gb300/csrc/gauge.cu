@@ -468,17 +468,36 @@ __global__ void __launch_bounds__(128, 3) gauge_force_df_kernel(GaugeView Ud, co
     M3d Wr, Wp;
 #pragma unroll
     for (int e = 0; e < 9; e++) Wr.m[e] = czero<df>();
+    // the three rectangles of each staple k share one copy of the product
+    // code: a run-time loop over the terms a b c (c daggered for the third)
+    // keeps the kernel inside the instruction cache
 #pragma unroll 1
-    for (int k = 0; k < 6; k++) {
-      if (c1 != 0.0) {
-        const M3d Sx = load_stap_d(S, V, mu, k, s0.lexi);
-        const int nu = (k >> 1) + ((k >> 1) >= mu ? 1 : 0), s = (k & 1) ? -1 : 1;
-        add_lazy_m(Wr, dmul(dmul(load_link_d(Ud, spm, mu), load_stap_d(S, V, mu, k, spm.lexi)), Sx));
-        add_lazy_m(Wr, dmul(dmul(Sx, load_stap_d(S, V, mu, k, smm.lexi)), load_link_d(Ud, smm, mu)));
-        int cps[4] = {c[0], c[1], c[2], c[3]};
-        coords_shift(g, cps, nu, s);
-        add_lazy_m(Wr, dmul_nd(dmul(signed_link_d(Ud, g, cpm, nu, s), load_stap_d(S, V, mu, k, at(g, cps).lexi)),
-                               signed_link_d(Ud, g, c, nu, s)));
+    for (int k = 0; k < 6 && c1 != 0.0; k++) {
+      const int nu = (k >> 1) + ((k >> 1) >= mu ? 1 : 0), s = (k & 1) ? -1 : 1;
+      int cps[4] = {c[0], c[1], c[2], c[3]};
+      coords_shift(g, cps, nu, s);
+#pragma unroll 1
+      for (int j = 0; j < 3; j++) {
+        M3d ab;
+        {
+          M3d a, b;
+          if (j == 0) {  // U_mu(x + mu) S(x + mu) S(x)
+            a = load_link_d(Ud, spm, mu);
+            b = load_stap_d(S, V, mu, k, spm.lexi);
+          } else if (j == 1) {  // S(x) S(x - mu) U_mu(x - mu)
+            a = load_stap_d(S, V, mu, k, s0.lexi);
+            b = load_stap_d(S, V, mu, k, smm.lexi);
+          } else {  // U_{s nu}(x + mu) S(x + s nu) U_{s nu}(x)^+
+            a = signed_link_d(Ud, g, cpm, nu, s);
+            b = load_stap_d(S, V, mu, k, at(g, cps).lexi);
+          }
+          ab = dmul(a, b);
+        }
+        M3d t;
+        if (j == 0) t = load_stap_d(S, V, mu, k, s0.lexi);
+        else if (j == 1) t = load_link_d(Ud, smm, mu);
+        else t = dagger_d(signed_link_d(Ud, g, c, nu, s));
+        add_lazy_m(Wr, dmul(ab, t));
       }
     }
 #pragma unroll
