@@ -327,7 +327,7 @@ def ctypes_byref(x):
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
 # half hop timed by time_half_hop, from one ncu capture of that launch
 # (profiles/hop_f64_24x48_ncu.md); valid only for the kernel as captured.
-NCU_TRAFFIC = {("hop_kernel prec=0 recon=18", (24, 24, 24, 48), 0, 18): 504886016.0}
+NCU_TRAFFIC = {("hop_kernel prec=0 recon=18", (24, 24, 24, 48), 0, 18): 504178432.0}
 
 
 def nvtx_push(name):

@@ -212,6 +212,41 @@ LQCD_DEV void acc_nb(Cx<typename SpinorIO<PREC>::R> v[6], float sc, bool neg,
   }
 }
 
+// acc (FIRST: =, else +=) f w for the unit f = +1, -1, +i, -i (F_P1 .. F_MI)
+template <int F, bool FIRST> LQCD_DEV void put_unit(Cx<double> &acc, Cx<double> w) {
+  const Cx<double> t = F == F_P1 ? w : F == F_M1 ? Cx<double>{-w.re, -w.im}
+                     : F == F_PI ? Cx<double>{-w.im, w.re} : Cx<double>{w.im, -w.re};
+  acc = FIRST ? t : acc + t;
+}
+// -x when flip, by the sign bit (integer work, off the FP64 pipe)
+LQCD_DEV double flip_sign(double x, bool flip) {
+  return __longlong_as_double(__double_as_longlong(x) ^ (flip ? (long long)0x8000000000000000ull : 0ll));
+}
+// upper spins (FIRST: =, else +=) sum; lower spins the -S B^+ d of
+// accumulate<MU, S> applied to d
+template <int MU, int S, bool FIRST>
+LQCD_DEV void accumulate_sd(const Cx<double> sum[6], const Cx<double> d[6], Cx<double> acc[12]) {
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    put_unit<F_P1, FIRST>(acc[c], sum[c]);
+    put_unit<F_P1, FIRST>(acc[3 + c], sum[3 + c]);
+    const Cx<double> d0 = d[c], d1 = d[3 + c];
+    if (MU == 0) {
+      put_unit<(S > 0 ? F_MI : F_PI), FIRST>(acc[6 + c], d1);
+      put_unit<(S > 0 ? F_MI : F_PI), FIRST>(acc[9 + c], d0);
+    } else if (MU == 1) {
+      put_unit<(S > 0 ? F_M1 : F_P1), FIRST>(acc[6 + c], d1);
+      put_unit<(S > 0 ? F_P1 : F_M1), FIRST>(acc[9 + c], d0);
+    } else if (MU == 2) {
+      put_unit<(S > 0 ? F_MI : F_PI), FIRST>(acc[6 + c], d0);
+      put_unit<(S > 0 ? F_PI : F_MI), FIRST>(acc[9 + c], d1);
+    } else {
+      put_unit<(S > 0 ? F_M1 : F_P1), FIRST>(acc[6 + c], d0);
+      put_unit<(S > 0 ? F_M1 : F_P1), FIRST>(acc[9 + c], d1);
+    }
+  }
+}
+
 template <int PREC, int RECON, int MU, int S, bool LF = true>
 LQCD_DEV void hop_dir(const HopArgs &A, const Site &s, int p, int cb, const SpinorView &vin,
                       Cx<typename SpinorIO<PREC>::R> acc[12]) {
@@ -236,6 +271,47 @@ LQCD_DEV void hop_dir(const HopArgs &A, const Site &s, int p, int cb, const Spin
     if (RECON == 12) reconstruct_row2(ub);
     mul_link_dag(ub, h, v);
     acc_nb<PREC, MU, -S>(v, scb, negb, acc);
+    return;
+  }
+  if constexpr (PREC == LQCD_F64) {
+    // FP64 (bound by GB300's FP64 pipe): the forward product a = U h_f, then
+    // d = a - b with b = U(x - mu)^+ h_b by one multiply-add chain started
+    // from a, and sum = a + b = 2a - d.  The upper spins take sum and the
+    // lower ones -S B^+ d (the two projectors differ only in the sign of their
+    // lower half): 12 fewer FP64 instructions per direction than two
+    // products and four sums, and the first direction assigns the
+    // accumulators instead of adding to zero.
+    Cx<R> a[6], d[6], sum[6];
+    {
+      const int j = neighbour_cb(A.g, s, MU, +1);
+      SpinorIO<PREC>::load(vin, j, ps);
+      project<MU, S>(ps, h);
+      LinkIO<PREC, RECON>::load(A.U, p, MU, cb, u);
+      if (RECON == 12) reconstruct_row2(u);
+      mul_link(u, h, a);
+      negate_if(a, negf);
+    }
+    {
+      const int j = neighbour_cb(A.g, s, MU, -1);
+      SpinorIO<PREC>::load(vin, j, ps);
+      project<MU, -S>(ps, h);
+      LinkIO<PREC, RECON>::load(A.U, p ^ 1, MU, j, u);
+      if (RECON == 12) reconstruct_row2(u);
+      // d = a - (negb ? -1 : 1) U^+ h: add conj(u) times h with its sign flipped unless negb
+#pragma unroll
+      for (int k = 0; k < 6; k++) h[k] = {flip_sign(h[k].re, !negb), flip_sign(h[k].im, !negb)};
+#pragma unroll
+      for (int k = 0; k < 2; k++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+          Cx<R> t = conj_madd(u[c], h[3 * k], a[3 * k + c]);
+          t = conj_madd(u[3 + c], h[3 * k + 1], t);
+          d[3 * k + c] = conj_madd(u[6 + c], h[3 * k + 2], t);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 6; k++) sum[k] = {fma(2.0, a[k].re, -d[k].re), fma(2.0, a[k].im, -d[k].im)};
+    accumulate_sd<MU, S, MU == 0>(sum, d, acc);
     return;
   }
   // forward: (1 - S gamma_mu) U_mu(x) in(x + mu)
