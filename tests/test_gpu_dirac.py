@@ -271,6 +271,40 @@ def test_df64_pair_kernels_on_a_ragged_lattice(ctx, oracle, nrhs):
         assert np.linalg.norm(res) <= 1e-10 * np.linalg.norm(bh[r])
 
 
+@pytest.mark.parametrize("inner", [lqcd.LQCD_BF16S, lqcd.LQCD_F16S])
+def test_16bit_kernels_on_a_ragged_lattice(ctx, oracle, inner):
+    """The 16-bit hop in every launch form the tuner can pick (one site per
+    thread in both load orders, two sites per thread in packed FP32x2 with
+    direct loads or with cp.async-staged operands) inside a mixed DF64/16-bit
+    CG on a lattice whose half volume (144) ends in a partial block of every
+    form: every choice gives the same bits and iteration counts, and the
+    solution meets the oracle's residual."""
+    L = (6, 4, 2, 6)
+    kappa, mu = 0.15, 0.01 / 0.3
+    U = inputs.random_gauge(L, "near", seed=27, eps=0.4)
+    G = lqcd.lqcd_gauge_import(ctx, dev(U), L, recon=12)
+    bh = inputs.gaussian_spinor(L, 28, nrhs=1)
+    b = dev(bh)
+    prm = lqcd.cg_params(tol=1e-10, outer_prec=lqcd.LQCD_DF64, inner_prec=inner, sloppy_recon=12)
+    outs = []
+    for choice in [-1] + list(range(24)):
+        x = torch.zeros_like(b)
+        lqcd.lqcd_set_launch_choice(ctx, choice)
+        try:
+            st = lqcd.lqcd_cg_solve(ctx, G, lqcd.field(b, lqcd.LQCD_LAYOUT_LEXI, nrhs=1),
+                                    lqcd.field(x, lqcd.LQCD_LAYOUT_LEXI, nrhs=1), kappa, mu, prm)
+        finally:
+            lqcd.lqcd_set_launch_choice(ctx, -1)
+        torch.cuda.synchronize()
+        outs.append((x.clone(), [s["iters"] for s in st]))
+    for x, its in outs[1:]:
+        assert its == outs[0][1]
+        assert torch.equal(x, outs[0][0])
+    x = host(outs[0][0])
+    res = bh[0] - oracle.apply_M(U, x[0], L, kappa, mu)
+    assert np.linalg.norm(res) <= 1e-10 * np.linalg.norm(bh[0])
+
+
 def test_full_size_24x48_apply_M(ctx, oracle):
     """The 24^3 x 48 workload: M and Mhat on every site against the oracle."""
     L = (24, 24, 24, 48)
