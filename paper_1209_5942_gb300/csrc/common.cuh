@@ -556,6 +556,11 @@ template <> struct SpinorIO<LQCD_F32> {
 template <class H> struct Half16;
 template <> struct Half16<__nv_bfloat16> {
   static LQCD_DEV float to_f(uint16_t u) { return __bfloat162float(__ushort_as_bfloat16(u)); }
+  // the (low, high) pair of one 32-bit word: a bf16 is the upper half of its
+  // float, so each value is one shift or mask (bitwise the same as to_f)
+  static LQCD_DEV float2 to_f2(uint32_t w) {
+    return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xFFFF0000u));
+  }
   static LQCD_DEV uint16_t from_f(float f) { return __bfloat16_as_ushort(__float2bfloat16_rn(f)); }
   // (lo, hi) rounded to nearest and packed in one conversion
   static LQCD_DEV uint32_t pack2(float lo, float hi) {
@@ -565,6 +570,12 @@ template <> struct Half16<__nv_bfloat16> {
 };
 template <> struct Half16<__half> {
   static LQCD_DEV float to_f(uint16_t u) { return __half2float(__ushort_as_half(u)); }
+  // the (low, high) pair of one 32-bit word in one conversion (exact, as to_f)
+  static LQCD_DEV float2 to_f2(uint32_t w) {
+    __half2 h;
+    *reinterpret_cast<uint32_t*>(&h) = w;
+    return __half22float2(h);
+  }
   static LQCD_DEV uint16_t from_f(float f) { return __half_as_ushort(__float2half_rn(f)); }
   static LQCD_DEV uint32_t pack2(float lo, float hi) {
     __half2 t = __floats2half2_rn(lo, hi);
@@ -585,8 +596,8 @@ template <class H> struct SpinorIO16 {
       uint32_t ww[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
       for (int j = 0; j < 4; j++) {
-        s[4 * k + j].re = Half16<H>::to_f((uint16_t)(ww[j] & 0xFFFFu));
-        s[4 * k + j].im = Half16<H>::to_f((uint16_t)(ww[j] >> 16));
+        const float2 f = Half16<H>::to_f2(ww[j]);
+        s[4 * k + j] = {f.x, f.y};
       }
     }
     return sc;
@@ -600,8 +611,8 @@ template <class H> struct SpinorIO16 {
       uint32_t ww[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
       for (int j = 0; j < 4; j++) {
-        s[4 * k + j].re = __fmul_rn(Half16<H>::to_f((uint16_t)(ww[j] & 0xFFFFu)), sc);
-        s[4 * k + j].im = __fmul_rn(Half16<H>::to_f((uint16_t)(ww[j] >> 16)), sc);
+        const float2 f = Half16<H>::to_f2(ww[j]);
+        s[4 * k + j] = {__fmul_rn(f.x, sc), __fmul_rn(f.y, sc)};
       }
     }
   }
@@ -690,8 +701,10 @@ template <class H> struct LinkIO16 {
     uint2 w2 = __ldg((const uint2*)(base + (size_t)g.Vh * 16) + cb);
     uint32_t ww[6] = {w.x, w.y, w.z, w.w, w2.x, w2.y};
 #pragma unroll
-    for (int k = 0; k < 6; k++)
-      u[k] = {Half16<H>::to_f((uint16_t)(ww[k] & 0xFFFFu)), Half16<H>::to_f((uint16_t)(ww[k] >> 16))};
+    for (int k = 0; k < 6; k++) {
+      const float2 f = Half16<H>::to_f2(ww[k]);
+      u[k] = {f.x, f.y};
+    }
   }
 };
 template <> struct LinkIO<LQCD_BF16S, 12> : LinkIO16<__nv_bfloat16> {};

@@ -676,9 +676,10 @@ LQCD_DEV void h16_stage_issue(const HopArgs &A, const Site &sA, const Site &sB, 
 template <class H, int N>
 LQCD_DEV void h16_unpack2(const uint32_t *wa, const uint32_t *wb, Cx<float2> *out) {
 #pragma unroll
-  for (int j = 0; j < N; j++)
-    out[j] = {make_float2(Half16<H>::to_f((uint16_t)(wa[j] & 0xFFFFu)), Half16<H>::to_f((uint16_t)(wb[j] & 0xFFFFu))),
-              make_float2(Half16<H>::to_f((uint16_t)(wa[j] >> 16)), Half16<H>::to_f((uint16_t)(wb[j] >> 16)))};
+  for (int j = 0; j < N; j++) {
+    const float2 a = Half16<H>::to_f2(wa[j]), b = Half16<H>::to_f2(wb[j]);
+    out[j] = {make_float2(a.x, b.x), make_float2(a.y, b.y)};
+  }
 }
 template <class H> LQCD_DEV void h16_unpack2(uint4 a, uint4 b, Cx<float2> *out) {
   const uint32_t wa[4] = {a.x, a.y, a.z, a.w}, wb[4] = {b.x, b.y, b.z, b.w};
