@@ -495,7 +495,7 @@ __global__ void __launch_bounds__(128) hop_rt_kernel(HopArgs A) {
 // LF selects, for the memory-bound formats, whether both neighbours' loads of
 // a direction are issued before its arithmetic (the autotuner picks).
 template <int PREC, int RECON, bool DAG, bool REDUCE, bool LF>
-__global__ void __launch_bounds__(256, (PREC == LQCD_BF16S || PREC == LQCD_F16S) ? 3 : 1) hop_kernel(HopArgs A) {
+__global__ void __launch_bounds__(256, (PREC == LQCD_BF16S || PREC == LQCD_F16S) ? 3 : PREC == LQCD_F32 ? 2 : 1) hop_kernel(HopArgs A) {
   if (A.halt && *(volatile int *)A.halt) return;
   const int rhs = blockIdx.z * blockDim.y + threadIdx.y;
   const int stride = gridDim.x * blockDim.x;
