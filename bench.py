@@ -21,7 +21,7 @@ true residual).  Prints ONE JSON line (rank 0):
 
 --impl reference times the oracle itself on the same workload (the paper has
 no runnable reference implementation).  --gpus N > 1 runs N independent
-replicas (the solve does not shard across GPUs in this build).
+replicas (the library solves each system on one GPU; there is no sharded solve).
 """
 from __future__ import annotations
 

@@ -77,7 +77,7 @@ typedef enum {
   LQCD_ERR_NONFINITE = -4,   /* NaN/Inf met in an input or a solver scalar */
   LQCD_ERR_TIMEOUT = -5,     /* a bounded device-side wait ran out */
   LQCD_ERR_OOM = -6,         /* device allocation failed */
-  LQCD_ERR_UNSUPPORTED = -7  /* valid request that this build does not implement */
+  LQCD_ERR_UNSUPPORTED = -7  /* valid request that the library does not implement */
 } lqcd_status;
 
 typedef enum { LQCD_FULL = 0, LQCD_EVEN = 1, LQCD_ODD = 2 } lqcd_parity;

@@ -837,7 +837,7 @@ LQCD_DEV bool sample_y0_f(float b, uint32_t c0, uint32_t c1, uint32_t c2, uint64
 }
 
 template <int RECON>
-__global__ void __launch_bounds__(128) heatbath_f32_kernel(GaugeView Uf, Geom g, int mu, int par, float beta,
+__global__ void __launch_bounds__(128, 5) heatbath_f32_kernel(GaugeView Uf, Geom g, int mu, int par, float beta,
                                                            uint64_t seed, uint32_t sweep, int overrelax,
                                                            unsigned int *fail_count) {
   int cb = blockIdx.x * blockDim.x + threadIdx.x;
