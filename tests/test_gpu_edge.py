@@ -67,6 +67,32 @@ def test_zero_right_hand_side(ctx, oracle, inner):
     assert np.linalg.norm(r) / np.linalg.norm(b[1]) <= 1e-10
 
 
+@pytest.mark.parametrize("prec", [lqcd.LQCD_F64, lqcd.LQCD_DF64, lqcd.LQCD_F32])
+def test_degenerate_parameters(ctx, oracle, prec):
+    """The method's degenerate points: kappa = 0 makes M the identity (no hop,
+    no twisted term), mu = 0 the plain Wilson operator, and the solve of M x
+    = b at kappa = 0 returns b itself."""
+    L = (4, 4, 2, 6)
+    U = inputs.random_gauge(L, "haar", seed=68)
+    G = lqcd.lqcd_gauge_import(ctx, dev(U), L)
+    psi = inputs.gaussian_spinor(L, 69)
+    tol = 2e-6 if prec == lqcd.LQCD_F32 else 1e-13
+    for kappa, mu in ((0.0, 0.7), (0.14, 0.0)):
+        ref = psi if kappa == 0.0 else oracle.apply_M(U, psi, L, kappa, mu)
+        _, _, fi = eo_full_from_lexi(ctx, L, psi, prec)
+        od, osc = lqcd.alloc_field(L, lqcd.LQCD_FULL, prec)
+        fo = lqcd.field(od, lqcd.LQCD_LAYOUT_EO, prec, 1, osc)
+        lqcd.lqcd_apply_M(ctx, G, fi, fo, kappa, mu)
+        assert relerr(lexi_from_eo_full(ctx, L, fo), ref) <= tol, (kappa, mu)
+    x = torch.zeros((inputs.volume(L), 4, 3), dtype=torch.complex128, device="cuda")
+    st = lqcd.lqcd_cg_solve(ctx, G, lqcd.field(dev(psi), lqcd.LQCD_LAYOUT_LEXI),
+                            lqcd.field(x, lqcd.LQCD_LAYOUT_LEXI), 0.0, 0.7,
+                            lqcd.cg_params(tol=1e-10, outer_prec=prec if prec != lqcd.LQCD_F32 else lqcd.LQCD_DF64,
+                                           inner_prec=prec))
+    assert st[0]["converged"] == 1
+    assert np.max(np.abs(host(x) - psi)) <= 1e-10 * np.max(np.abs(psi))
+
+
 def test_largest_workload_lattice(ctx, oracle):
     """32^3 x 64 (2097152 sites): M on every site against the oracle, F64 and DF64."""
     L = (32, 32, 32, 64)
