@@ -6,7 +6,8 @@
 // variant, lattice extents, number of right-hand sides, GPU) gets its launch
 // shape from a table: the first time a configuration is launched outside a
 // stream capture, each candidate shape is run once to warm up and three times
-// under CUDA events on the context's stream, and the fastest is kept.  The
+// under CUDA events on the context's stream, and the fastest is kept (inside
+// a capture an untuned hop configuration borrows a tuned sibling's choice).  The
 // table can be persisted as a small JSON object {"key": choice, ...} in the
 // file given to lqcd_set_autotune (or the LQCD_TUNE_CACHE environment
 // variable), so later processes skip the timing.
@@ -14,6 +15,7 @@
 #include <cstdlib>
 #include <fstream>
 #include <sstream>
+#include <string>
 
 #include "internal.h"
 
@@ -54,6 +56,32 @@ static void tune_save(lqcd_ctx *ctx) {
   std::rename(tmp.c_str(), ctx->tune_path.c_str());
 }
 
+// A hop configuration first met inside a stream capture (the reducing hop
+// of a CG iteration is launched only inside the captured iteration) cannot
+// be timed.  Its siblings -- the same kernel family, precision, links,
+// extents and RHS count, differing only in the dagger, reduction or
+// epilogue flags -- share its candidate list, so it takes the choice of the
+// nearest tuned sibling (flags flipped one at a time, then two, then all).
+static int sibling_choice(const lqcd_ctx *ctx, const std::string &key, int ncand) {
+  const char *flags[3] = {"|d", "|red", "|aux"};
+  size_t pos[3];
+  for (int f = 0; f < 3; f++) {
+    pos[f] = key.find(flags[f]);
+    if (pos[f] == std::string::npos) return -1;
+    pos[f] += std::char_traits<char>::length(flags[f]);
+    if (pos[f] >= key.size() || (key[pos[f]] != '0' && key[pos[f]] != '1')) return -1;
+  }
+  static const int order[7] = {1, 2, 4, 3, 5, 6, 7};  // bit f flips flag f; fewest flips first
+  for (int m : order) {
+    std::string k = key;
+    for (int f = 0; f < 3; f++)
+      if (m & (1 << f)) k[pos[f]] = k[pos[f]] == '0' ? '1' : '0';
+    auto it = ctx->tuned.find(k);
+    if (it != ctx->tuned.end() && it->second >= 0 && it->second < ncand) return it->second;
+  }
+  return -1;
+}
+
 int tune_choice(lqcd_ctx *ctx, const std::string &key0, int ncand, int fallback,
                 const std::function<void(int)> &run) {
   if (ctx->forced_choice >= 0) return ncand > 0 ? ctx->forced_choice % ncand : fallback;
@@ -64,7 +92,8 @@ int tune_choice(lqcd_ctx *ctx, const std::string &key0, int ncand, int fallback,
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(ctx->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
     cudaGetLastError();
-    return fallback;
+    const int sib = key0.compare(0, 4, "hop4") == 0 ? sibling_choice(ctx, key, ncand) : -1;
+    return sib >= 0 ? sib : fallback;
   }
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return fallback;
