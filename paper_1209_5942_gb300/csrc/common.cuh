@@ -165,14 +165,9 @@ LQCD_DEV float rfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 LQCD_DEV double rfma(double a, double b, double c) { return __fma_rn(a, b, c); }
 LQCD_DEV df rfma(df a, df b, df c) { return a * b + c; }
 
-// i * a and -i * a
+// i * a
 template <class R> LQCD_DEV Cx<R> times_i(Cx<R> a) { return {-a.im, a.re}; }
-template <class R> LQCD_DEV Cx<R> times_mi(Cx<R> a) { return {a.im, -a.re}; }
 template <class R> LQCD_DEV Cx<R> conj(Cx<R> a) { return {a.re, -a.im}; }
-// conj(a) * b
-template <class R> LQCD_DEV Cx<R> conj_mul(Cx<R> a, Cx<R> b) {
-  return {a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re};
-}
 // a * b + c
 template <class R> LQCD_DEV Cx<R> cmadd(Cx<R> a, Cx<R> b, Cx<R> c) {
   return {c.re + a.re * b.re - a.im * b.im, c.im + a.re * b.im + a.im * b.re};
@@ -236,7 +231,6 @@ template <class R> LQCD_DEV R from_double(double v);
 template <> LQCD_DEV double from_double<double>(double v) { return v; }
 template <> LQCD_DEV float from_double<float>(double v) { return (float)v; }
 template <> LQCD_DEV df from_double<df>(double v) { return df_from_double(v); }
-template <class R> LQCD_DEV Cx<R> cfrom(HostC c) { return {from_double<R>(c.re), from_double<R>(c.im)}; }
 
 // Four complex coefficients prepared on the host in each arithmetic a kernel
 // may compute in (the same roundings as from_double), so that no thread
@@ -450,8 +444,6 @@ template <> LQCD_DEV double site_norm2<float, 12>(const Cx<float> v[12]) {
   }
   return (double)t;
 }
-// |a|^2 for a df complex, summed in float-float before the FP64 conversion
-LQCD_DEV df norm2_df(Cx<df> a) { return a.re * a.re + a.im * a.im; }
 
 // Sum of v[0..nb) in a fixed order by one block of FIN_THREADS threads:
 // thread t adds v[t], v[t + FIN_THREADS], ... in that order (the loop is

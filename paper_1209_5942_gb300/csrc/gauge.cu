@@ -51,20 +51,6 @@ LQCD_DEV M3 mmul_nd(const M3 &a, const M3 &b) {
     }
   return r;
 }
-// a^+ * b
-LQCD_DEV M3 mmul_dn(const M3 &a, const M3 &b) {
-  M3 r;
-#pragma unroll
-  for (int i = 0; i < 3; i++)
-#pragma unroll
-    for (int j = 0; j < 3; j++) {
-      C s = conj(a.m[i]) * b.m[j];
-      s = conj_madd(a.m[3 + i], b.m[3 + j], s);
-      s = conj_madd(a.m[6 + i], b.m[6 + j], s);
-      r.m[3 * i + j] = s;
-    }
-  return r;
-}
 LQCD_DEV double re_trace(const M3 &a) { return a.m[0].re + a.m[4].re + a.m[8].re; }
 
 struct Pos {
