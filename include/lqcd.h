@@ -166,8 +166,11 @@ int lqcd_set_allocator(lqcd_ctx *ctx, lqcd_alloc_fn alloc, lqcd_free_fn free_fn,
  * configuration (kernel, precision, link format, variant, lattice extents,
  * number of right-hand sides, GPU) made outside a stream capture times every
  * candidate block shape with CUDA events on the context's stream and keeps the
- * fastest; results never depend on the shape.  enable = 0 uses the built-in
- * defaults for configurations not yet tuned.  cache_path (may be NULL) names a
+ * fastest; results never depend on the shape.  A hop configuration first met
+ * inside a capture (the solvers capture their iterations in CUDA graphs) takes
+ * the choice of a tuned configuration that differs from it only in the dagger,
+ * reduction or epilogue variant, else the built-in default.  enable = 0 uses
+ * the built-in defaults for configurations not yet tuned.  cache_path (may be NULL) names a
  * JSON file from which choices are loaded now and to which new ones are
  * written, so other processes skip the timing. */
 int lqcd_set_autotune(lqcd_ctx *ctx, int enable, const char *cache_path);
