@@ -1250,6 +1250,75 @@ int or_heatbath_sweep(double *U, const int *L, double beta, uint64_t seed, uint3
 }
 
 /* ------------------------------------------------------------------ */
+/* Overrelaxation (Sec. 2.2: the update routine of the heatbath figure is */
+/* either the exact SU(2) update or an overrelaxation step, which moves   */
+/* through configuration space faster; Sec. 5.1 measures both kernels).   */
+/* For one link U with staple sum A and each SU(2) subgroup (i, j) in the */
+/* heatbath's order, w_hat is the unit quaternion of block (i, j) of      */
+/* W = U A at the current U, exactly as in the heatbath, and the subgroup  */
+/* element is replaced by its reflection:  v = (w_hat^+)^2, U <- V U with  */
+/* v embedded at (i, j).  Then block (i, j) of V U A is v k w_hat =        */
+/* k w_hat^+, whose real trace equals that of k w_hat: Re Tr(U A), and so  */
+/* the action, is unchanged (microcanonical), and reflecting one subgroup */
+/* twice with the same staple gives back U.  No random numbers.           */
+/* ------------------------------------------------------------------ */
+
+/* Reflects the subgroups g in gmask (bit g, order g = 0, 1, 2) of one link
+ * (complex 3x3, row-major) for staple sum A; returns the number of
+ * subgroups skipped because their block has no quaternion part (k = 0). */
+int or_overrelax_link(double *link, const double *staple, int gmask) {
+  cplx *u = (cplx *)link;
+  const cplx *A = (const cplx *)staple;
+  int skipped = 0;
+  for (int g = 0; g < 3; g++) {
+    if (!(gmask & (1 << g))) continue;
+    int p = SUBGROUP[g][0], q = SUBGROUP[g][1];
+    cplx W[9];
+    mat_mul(u, A, W);
+    cplx wa = W[3 * p + p], wb = W[3 * p + q], wc = W[3 * q + p], wd = W[3 * q + q];
+    double q0 = 0.5 * creal(wa + wd), q3 = 0.5 * cimag(wa - wd);
+    double q1 = 0.5 * cimag(wb + wc), q2 = 0.5 * creal(wb - wc);
+    double k = sqrt(q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3);
+    if (!(k > 1e-300)) {
+      skipped++;
+      continue;
+    }
+    double h0 = q0 / k, h1 = q1 / k, h2 = q2 / k, h3 = q3 / k;
+    cplx Wh[2][2] = {{h0 + I * h3, h2 + I * h1}, {-h2 + I * h1, h0 - I * h3}};
+    cplx Whd[2][2];
+    for (int r = 0; r < 2; r++)
+      for (int c = 0; c < 2; c++) Whd[r][c] = conj(Wh[c][r]);
+    cplx Vm[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    for (int r = 0; r < 2; r++)
+      for (int c = 0; c < 2; c++) {
+        cplx v = Whd[r][0] * Whd[0][c] + Whd[r][1] * Whd[1][c];
+        Vm[3 * (r ? q : p) + (c ? q : p)] = v;
+      }
+    mat_mul(Vm, u, u);
+  }
+  return skipped;
+}
+
+/* One overrelaxation sweep in the heatbath's checkerboard order: for mu =
+ * 0..3, parity even, odd, every link of that class with all three
+ * subgroups.  Returns the number of skipped subgroups.                   */
+int or_overrelax_sweep(double *U, const int *L) {
+  long V = volume(L);
+  int skipped = 0;
+  for (int mu = 0; mu < 4; mu++)
+    for (int par = 0; par < 2; par++) {
+#pragma omp parallel for reduction(+ : skipped) schedule(static)
+      for (long i = 0; i < V; i++)
+        if (or_parity(i, L) == par) {
+          double A[18];
+          or_staple(U, L, i, mu, A);
+          skipped += or_overrelax_link((double *)link_mut(U, i, mu), A, 7);
+        }
+    }
+  return skipped;
+}
+
+/* ------------------------------------------------------------------ */
 /* HMC (Sec. 2.2): H = 1/2 sum p^2 + S_g + S_pf; leapfrog with n steps of   */
 /* size eps:                                                                */
 /*   p <- p + eps/2 F;  (U <- exp(i eps P) U; p <- p + eps F) x (n-1);       */

@@ -99,6 +99,10 @@ def _declare(L):
     L.or_su2_y0_samples.argtypes = [ctypes.c_double, ctypes.c_uint64, ctypes.c_int, _dp]
     L.or_heatbath_sweep.argtypes = [_dp, _ip, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint32]
     L.or_heatbath_sweep.restype = ctypes.c_int
+    L.or_overrelax_link.argtypes = [_dp, _dp, ctypes.c_int]
+    L.or_overrelax_link.restype = ctypes.c_int
+    L.or_overrelax_sweep.argtypes = [_dp, _ip]
+    L.or_overrelax_sweep.restype = ctypes.c_int
     L.or_hmc_md.argtypes = [_dp, _dp, _dp, _ip, ctypes.c_double, ctypes.c_double,
                             ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                             ctypes.c_double, ctypes.c_int, _dp]
@@ -381,6 +385,25 @@ def heatbath_sweep(U, L, beta, seed, sweep):
     return U, f
 
 
+def overrelax_link(link, staple_sum, gmask=7):
+    """Overrelaxation of one link (Sec. 2.2): the SU(2) subgroups in gmask
+    (bits 0, 1, 2 = (0,1), (1,2), (0,2)) reflected, v = (w_hat^+)^2.
+    Returns (link', skipped subgroups)."""
+    u = np.array(_cplx(link, (3, 3)), copy=True)
+    A = _cplx(staple_sum, (3, 3))
+    n = lib().or_overrelax_link(_p(u), _p(A), int(gmask))
+    return u, n
+
+
+def overrelax_sweep(U, L):
+    """One overrelaxation sweep in the heatbath's checkerboard order (Sec. 2.2).
+    Returns (U, skipped subgroups)."""
+    V = volume(L)
+    U = np.array(_cplx(U, (V, 4, 3, 3)), copy=True)
+    n = lib().or_overrelax_sweep(_p(U), _dims(L))
+    return U, n
+
+
 def hmc_md(U, P, phi, L, beta, kappa, mu, nf=1, nsteps=10, tau=1.0, tol=1e-12,
            max_iter=100000):
     """Leapfrog molecular dynamics (Sec. 2.2). Returns (U', P', dH, (H0, H1, Spf0))."""
@@ -457,3 +480,65 @@ def hasenbusch_source(U, eta, L, kappa, mu, mu2, tol=1e-13):
     rhs = apply_Mhat(U, eta, L, kappa, mu, dagger=True)
     _, Z = pseudofermion_action(U, rhs, L, kappa, mu2, eo=True, tol=tol)
     return apply_Mhat(U, Z, L, kappa, mu2, dagger=False)
+
+
+def hmc_md_2mn_hasenbusch(U, P, eta1, eta2, L, beta, kappa, mu, mu2, c1=TLSYM_C1, nsteps=2,
+                          nsteps_mid=2, nsteps_g=2, lam=OMELYAN_LAMBDA, tau=1.0, tol=1e-13, phis=None):
+    """Molecular dynamics of mass-preconditioned HMC (Sec. 2.2: det D =
+    det A det(D / A) with a heavier second fermion matrix A, and 2MN on
+    multiple time scales), written from the pinned oracle routines above.
+
+    Pseudofermions (reading G24): W = Mhat(mu2), phi1 = W^+ eta1 with
+    S1 = phi1^+ (W^+ W)^-1 phi1, and phi2 = W^-+ Mhat^+ eta2 with the ratio
+    S2 = phi2^+ W (Mhat^+ Mhat)^-1 W^+ phi2.  Three nested 2MN scales: the
+    ratio force outside (nsteps steps over tau), the W force in the middle
+    (nsteps_mid steps over each outer position update), the gauge force
+    inside (nsteps_g steps over each middle position update), whose position
+    update is U <- exp(i h P) U.  One 2MN step of size e for force F and
+    position update Q:  P -= lam e F; Q(e/2); P -= (1 - 2 lam) e F; Q(e/2);
+    P -= lam e F.  Every force is evaluated where the scheme needs it.
+    phis = (phi1, phi2) replaces the sources drawn from (eta1, eta2) (for the
+    reverse trajectory of a reversibility check).
+    Returns (U', P', dH, (H0, H1), (phi1, phi2))."""
+    V = volume(L)
+    U = np.array(_cplx(U, (V, 4, 3, 3)), copy=True)
+    P = np.array(P, dtype=np.float64, copy=True, order="C")
+    if phis is None:
+        phi1 = apply_Mhat(U, eta1, L, kappa, mu2, dagger=True)
+        phi2 = hasenbusch_source(U, eta2, L, kappa, mu, mu2, tol=tol)
+    else:
+        phi1, phi2 = phis
+
+    def hamiltonian(U, P):
+        S1, _ = pseudofermion_action(U, phi1, L, kappa, mu2, eo=True, tol=tol)
+        S2, _ = hasenbusch_action(U, phi2, L, kappa, mu, mu2, tol=tol)
+        return 0.5 * float(np.sum(P * P)) + gauge_action_sym(U, L, beta, c1) + S1 + S2
+
+    def force(level, U):
+        if level == 0:
+            _, X2 = hasenbusch_action(U, phi2, L, kappa, mu, mu2, tol=tol)
+            return hasenbusch_dSdw(U, phi2, X2, L, kappa, mu, mu2)
+        if level == 1:
+            _, X1 = pseudofermion_action(U, phi1, L, kappa, mu2, eo=True, tol=tol)
+            return fermion_dSdw(U, X1, L, kappa, mu2, eo=True)
+        return gauge_dSdw_sym(U, L, beta, c1)
+
+    steps = (nsteps, nsteps_mid, nsteps_g)
+
+    def position(level, U, h):
+        return integrate(level + 1, U, h) if level < 2 else update_links(U, P, L, h)
+
+    def integrate(level, U, h):
+        e = h / steps[level]
+        for _ in range(steps[level]):
+            P[...] -= lam * e * force(level, U)
+            U = position(level, U, 0.5 * e)
+            P[...] -= (1.0 - 2.0 * lam) * e * force(level, U)
+            U = position(level, U, 0.5 * e)
+            P[...] -= lam * e * force(level, U)
+        return U
+
+    H0 = hamiltonian(U, P)
+    U = integrate(0, U, tau)
+    H1 = hamiltonian(U, P)
+    return U, P, H1 - H0, (H0, H1), (phi1, phi2)

@@ -223,3 +223,31 @@ def test_cg_true_residual(oracle):
     assert it > 0 and res <= 1e-11
     r = b - oracle.apply_M(U, x, L, kappa, mu)
     assert np.linalg.norm(r) / np.linalg.norm(b) <= 1e-11
+
+
+def test_cg_fixed_iters_matches_cg_and_its_residual(oracle):
+    """The oracle's fixed-iteration CG (used only to time the CPU baseline)
+    is the even-odd CG on Mhat^+ Mhat x = Mhat^+ bhat: after N iterations its
+    iterate equals or_cg(eo=1)'s after N iterations, its reported residual is
+    the true normal-equation residual of that iterate, and with enough
+    iterations the iterate solves Mhat x = bhat."""
+    L = L44
+    kappa, mu = 0.15, 0.01 / 0.3
+    U = inputs.random_gauge(L, "haar", seed=73)
+    b = inputs.gaussian_spinor(L, 74)
+    bhat = oracle.eo_prepare(U, b, L, kappa, mu)
+    ev = ~oracle.parity_mask(L)
+    rhs = oracle.apply_Mhat(U, bhat, L, kappa, mu, dagger=True) * ev[:, None, None]
+    for n in (1, 7, 25):
+        xf, rf = oracle.cg_fixed_iters(U, bhat, L, kappa, mu, n)
+        xc, it, rc = oracle.cg(U, rhs, L, kappa, mu, tol=0.0, max_iter=n, eo=True)
+        assert it == -1  # ran all n iterations
+        assert np.max(np.abs(xf - xc)) <= 1e-13 * np.max(np.abs(xc))
+        assert abs(rf - rc) <= 1e-12 * rc
+        r = rhs - oracle.apply_Mhat(U, oracle.apply_Mhat(U, xf, L, kappa, mu), L, kappa, mu, dagger=True)
+        true = np.linalg.norm(r[ev]) / np.linalg.norm(rhs[ev])
+        assert abs(true - rf) <= 1e-9 * max(rf, 1e-12)
+    xf, rf = oracle.cg_fixed_iters(U, bhat, L, kappa, mu, 400)
+    assert rf < 1e-12
+    res = oracle.apply_Mhat(U, xf, L, kappa, mu) - bhat
+    assert np.linalg.norm(res[ev]) <= 1e-10 * np.linalg.norm(bhat[ev])

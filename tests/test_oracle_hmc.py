@@ -198,3 +198,51 @@ def test_hasenbusch_ratio_pins(oracle):
             sm, _ = oracle.hasenbusch_action(Um, phi, L, kappa, mu, mu2, tol=1e-14)
             fd = (sp - sm) / (2 * h)
             assert abs(fd - F[m, i, a]) < 1e-6 * max(1.0, abs(fd)), (i, m, a, fd, F[m, i, a])
+
+
+def test_mass_preconditioned_2mn_pins(oracle):
+    """The three-scale mass-preconditioned trajectory of the oracle:
+    (1) with mu2 = mu the ratio action is eta2^+ eta2 and its force vanishes,
+        so the outer scale only splits the time: the trajectory equals the
+        pinned two-scale 2MN of the W pseudofermion with 2 nsteps nsteps_mid
+        fermion steps (same links, same dH);
+    (2) H0 = K + S_g + eta1^+ eta1 + eta2^+ eta2 (both sources so drawn);
+    (3) reversible: flipping the final momenta and integrating again gives
+        back the start links;
+    (4) second order: dH falls ~4x when all step counts double."""
+    L = (2, 4, 2, 4)
+    beta, kappa, mu, mu2, c1 = 3.9, 0.14, 0.05, 0.25, oracle.TLSYM_C1
+    U = inputs.random_gauge(L, "near", seed=411, eps=0.3)
+    ev = ~oracle.parity_mask(L)
+    eta1 = inputs.gaussian_spinor(L, 412) * ev[:, None, None]
+    eta2 = inputs.gaussian_spinor(L, 413) * ev[:, None, None]
+    P0 = inputs.gaussian_algebra(L, 414)
+    tau = 0.5
+    # (1) reduction to the two-scale integrator at mu2 = mu (the middle scale then
+    #     carries the twisted mass mu itself)
+    Ua, Pa, dHa, _, _ = oracle.hmc_md_2mn_hasenbusch(U, P0, eta1, eta2, L, beta, kappa, mu, mu, c1=c1,
+                                                  nsteps=2, nsteps_mid=2, nsteps_g=2, tau=tau)
+    phi = oracle.apply_Mhat(U, eta1, L, kappa, mu, dagger=True)
+    Ub, Pb, dHb, _ = oracle.hmc_md_2mn(U, P0, phi, L, beta, kappa, mu, c1=c1, nf=1, nsteps_f=8,
+                                       nsteps_g=2, tau=tau, tol=1e-13)
+    assert np.max(np.abs(Ua - Ub)) < 1e-10
+    assert np.max(np.abs(Pa - Pb)) < 1e-8
+    assert abs(dHa - dHb) < 1e-8
+    # (2) start Hamiltonian
+    U1, P1, dH, (H0, H1), phis = oracle.hmc_md_2mn_hasenbusch(U, P0, eta1, eta2, L, beta, kappa, mu, mu2, c1=c1,
+                                                        nsteps=2, nsteps_mid=2, nsteps_g=2, tau=tau)
+    H0_expect = (0.5 * np.sum(P0 ** 2) + oracle.gauge_action_sym(U, L, beta, c1)
+                 + np.vdot(eta1, eta1).real + np.vdot(eta2, eta2).real)
+    assert abs(H0 - H0_expect) < 1e-9 * abs(H0_expect)
+    # (3) reversibility, with the pseudofermion fields of the forward trip
+    assert np.max(np.abs(U1 - U)) > 1e-3
+    Ur, Pr, dHr, _, _ = oracle.hmc_md_2mn_hasenbusch(U1, -P1, None, None, L, beta, kappa, mu, mu2, c1=c1,
+                                                     nsteps=2, nsteps_mid=2, nsteps_g=2, tau=tau, phis=phis)
+    assert np.max(np.abs(Ur - U)) < 1e-10
+    assert np.max(np.abs(Pr + P0)) < 1e-8
+    assert abs(dHr + dH) < 1e-8
+    # (4) second order
+    _, _, dH2, _, _ = oracle.hmc_md_2mn_hasenbusch(U, P0, eta1, eta2, L, beta, kappa, mu, mu2, c1=c1,
+                                                nsteps=4, nsteps_mid=2, nsteps_g=2, tau=tau)
+    assert abs(dH) < 1.0
+    assert 3.0 < dH / dH2 < 5.3, (dH, dH2)
