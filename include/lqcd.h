@@ -144,6 +144,16 @@ typedef struct {
 int lqcd_get_counters(const lqcd_ctx *ctx, lqcd_counters *out);
 int lqcd_reset_counters(lqcd_ctx *ctx);
 
+/* Measured arithmetic peaks of the context's GPU, for the roofline of the
+ * ALU-bound kernels (the IEEE-FP64 hop is bound by the FP64 pipe, the
+ * float-float hop by the FP32 pipe; Sec. 5.2 of the paper states its kernels'
+ * performance against peaks too): two microbenchmark launches of 8
+ * independent FMA chains per thread on 8 x 256 threads per SM, FP64 FMA and
+ * packed FP32x2 FMA, timed with CUDA events after a warm-up launch (about
+ * 30 ms in all).  *fp64_tflops and *fp32_tflops (host) receive 2 flops per FMA per
+ * second in TFLOP/s.  Synchronous.  NULL arguments: LQCD_ERR_INVALID. */
+int lqcd_measure_peaks(lqcd_ctx *ctx, double *fp64_tflops, double *fp32_tflops);
+
 /* Device memory.  By default the library allocates its workspace and gauge
  * fields with cudaMallocAsync / cudaFreeAsync on the context's stream.
  * lqcd_set_allocator routes every later device allocation of the context
@@ -302,9 +312,11 @@ int lqcd_cg_solve_batch(lqcd_ctx *ctx, int n, const lqcd_gauge *const *U, const 
 /* dS/domega for S = phi^+ (Mhat^+ Mhat)^-1 phi (phi: EO half field on the
  * even sites, LQCD_F64), through dD^-1 = -D^-1 dD D^-1:
  *   X = (Mhat^+ Mhat)^-1 phi (CG), Y = Mhat X, then one adjoint kernel over
- *   all links.  dSdw: device float64 [4][V][8].  If X_cache is non-NULL and
- *   X_cache->reserved == 1 the stored X is reused, otherwise X is solved and,
- *   when X_cache is non-NULL, stored there (reserved set to 1).
+ *   all links.  dSdw: device float64 [4][V][8], or NULL to compute the action
+ *   alone (no force kernel; S_out must then be non-NULL, else
+ *   LQCD_ERR_INVALID).  If X_cache is non-NULL and X_cache->reserved == 1 the
+ *   stored X is reused, otherwise X is solved and, when X_cache is non-NULL,
+ *   stored there (reserved set to 1).
  *   *S_out (host, may be NULL) receives S = Re phi^+ X.  Synchronous. */
 int lqcd_fermion_force(lqcd_ctx *ctx, const lqcd_gauge *U, lqcd_field phi, double *dSdw,
                        lqcd_field *X_cache, const lqcd_geom *geom, double kappa, double mu,
@@ -350,7 +362,10 @@ int lqcd_plaquette(lqcd_ctx *ctx, const lqcd_gauge *U, double *plaq_out);
  * LQCD_ERR_INVALID): the same checkerboard order, each SU(2) subgroup
  * replaced by its reflection v = (w^+/k)^2 (microcanonical: the action is
  * unchanged).  prec = LQCD_F64 updates the FP64 field in place (the SU(2)
- * left multiplications keep it unitary to rounding); prec = LQCD_F32 runs
+ * left multiplications keep it unitary to rounding; a field imported with
+ * recon = 12 is updated through its 12-real FP64 copy, the third row rebuilt
+ * on every load, Sec. 4.1, and written back with the third row rebuilt);
+ * prec = LQCD_F32 runs
  * the same sweep in single precision on the field's FP32 copy (12-real links
  * with the third row rebuilt, Sec. 4.1, if the field was imported with
  * recon = 12) and writes the result back into the FP64 field, reunitarised in
@@ -358,6 +373,15 @@ int lqcd_plaquette(lqcd_ctx *ctx, const lqcd_gauge *U, double *plaq_out);
  * Asynchronous. */
 int lqcd_heatbath_sweep(lqcd_ctx *ctx, lqcd_gauge *U, double beta, uint64_t seed,
                         uint64_t sweep_idx, int n_or, int prec);
+
+/* n_or overrelaxation passes alone (Sec. 2.2: the alternative update of the
+ * heatbath figure; 1 <= n_or <= 64, else LQCD_ERR_INVALID), in the
+ * checkerboard order of lqcd_heatbath_sweep, with the same arithmetic and link
+ * formats per prec: for each link and SU(2) subgroup (0,1), (1,2), (0,2) in
+ * turn, w_hat = the unit quaternion part of the subgroup block of U A (A the
+ * staple sum) and U <- V U with v = (w_hat^+)^2.  Deterministic (no random
+ * numbers); the action is unchanged to rounding.  Asynchronous. */
+int lqcd_overrelax_sweep(lqcd_ctx *ctx, lqcd_gauge *U, int n_or, int prec);
 
 /* Gaussian momenta p^a ~ N(0,1) into P (device float64 [4][V][8]) from the
  * Philox stream (site, traj, mu | 1<<8, k). Asynchronous. */
@@ -448,9 +472,12 @@ int lqcd_hmc_trajectory(lqcd_ctx *ctx, lqcd_gauge *U, const lqcd_hmc_params *par
  * the call returns without synchronising.  All calls share the one array,
  * which keeps the last call's partial sums (each call overwrites every slot
  * it reads, so nothing needs clearing): calls whose work overlaps on the GPU
- * race, so order them on one stream.  The first call made while a device is
- * current looks up the array's device address (cudaGetSymbolAddress); make
- * that first call before any stream capture. */
+ * race, so order them on one stream.  Every call made outside a stream
+ * capture looks up the array's device address afresh (cudaGetSymbolAddress),
+ * so calls after cudaDeviceReset, which reloads the module and moves the
+ * array, stay correct; a call whose stream is capturing reuses the address of
+ * the last call on the same device and returns LQCD_ERR_CUDA if there was
+ * none, so make one call on each device outside any capture first. */
 int lqcd_plaquette_noalloc(const void *U_lexi, const lqcd_geom *geom, double *plaq_dev,
                            void *cuda_stream);
 

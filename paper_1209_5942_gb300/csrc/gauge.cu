@@ -82,8 +82,10 @@ LQCD_DEV void store_link(double2 *master, const Geom &g, const Pos &s, int mu, c
 }
 LQCD_DEV Pos at(const Geom &g, const int c[4]) { return pos_of(g, c[0], c[1], c[2], c[3]); }
 
-// staple sum A_mu(x) with Re Tr(U_mu(x) A) = sum of the 6 plaquettes through U_mu(x)
-LQCD_DEV M3 staple(const double2 *U, const Geom &g, const int c[4], int mu) {
+// staple sum A_mu(x) with Re Tr(U_mu(x) A) = sum of the 6 plaquettes through
+// U_mu(x); ld(pos, nu) loads the link U_nu at pos
+template <class LD>
+LQCD_DEV M3 staple_with(LD ld, const Geom &g, const int c[4], int mu) {
   M3 A;
 #pragma unroll
   for (int k = 0; k < 9; k++) A.m[k] = czero<double>();
@@ -97,23 +99,27 @@ LQCD_DEV M3 staple(const double2 *U, const Geom &g, const int c[4], int mu) {
     coords_shift(g, cmn, nu, -1);
     coords_shift(g, cpmmn, nu, -1);
     // upper: U_nu(x+mu) U_mu(x+nu)^+ U_nu(x)^+
-    M3 t = mmul_nd(load_link(U, g, at(g, cpm), nu), load_link(U, g, at(g, cpn), mu));
-    t = mmul_nd(t, load_link(U, g, at(g, c), nu));
+    M3 t = mmul_nd(ld(at(g, cpm), nu), ld(at(g, cpn), mu));
+    t = mmul_nd(t, ld(at(g, c), nu));
 #pragma unroll
     for (int k = 0; k < 9; k++) A.m[k] = A.m[k] + t.m[k];
     // lower: U_nu(x+mu-nu)^+ U_mu(x-nu)^+ U_nu(x-nu)
-    M3 l1 = load_link(U, g, at(g, cpmmn), nu), l2 = load_link(U, g, at(g, cmn), mu);
+    M3 l1 = ld(at(g, cpmmn), nu), l2 = ld(at(g, cmn), mu);
     M3 w = mmul(l2, l1);  // (U_mu(x-nu) U_nu(x+mu-nu))^+ = l1^+ l2^+
     M3 wd;
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
       for (int j = 0; j < 3; j++) wd.m[3 * i + j] = conj(w.m[3 * j + i]);
-    t = mmul(wd, load_link(U, g, at(g, cmn), nu));
+    t = mmul(wd, ld(at(g, cmn), nu));
 #pragma unroll
     for (int k = 0; k < 9; k++) A.m[k] = A.m[k] + t.m[k];
   }
   return A;
+}
+
+LQCD_DEV M3 staple(const double2 *U, const Geom &g, const int c[4], int mu) {
+  return staple_with([&](const Pos &s, int nu) { return load_link(U, g, s, nu); }, g, c, mu);
 }
 
 // ---------------------------------------------------------------------------
@@ -640,7 +646,25 @@ LQCD_DEV bool sample_y0(double b, uint32_t c0, uint32_t c1, uint32_t c2, uint64_
   return false;
 }
 
-__global__ void __launch_bounds__(128) heatbath_kernel(double2 *U, Geom g, int mu, int par, double beta,
+// FP64 links of the heatbath: the master (18 reals) or, for a field imported
+// with recon = 12, its FP64 REC12 copy with the third row rebuilt on load
+// (Sec. 4.1; Sec. 6 suggests REC12 for the heatbath kernels as well)
+template <int RECON>
+LQCD_DEV M3 hb_load(const GaugeView &Uv, const Pos &s, int mu) {
+  M3 u;
+  LinkIO<LQCD_F64, RECON>::load(Uv, s.p, mu, s.cb, u.m);
+  if (RECON == 12) reconstruct_row2(u.m);
+  return u;
+}
+template <int RECON>
+LQCD_DEV void hb_store(const GaugeView &Uv, const Pos &s, int mu, const M3 &u) {
+  double2 *b = (double2 *)((char *)Uv.ptr + s.p * Uv.parity_stride + mu * Uv.mu_stride);
+#pragma unroll
+  for (int k = 0; k < (RECON == 18 ? 9 : 6); k++) b[(size_t)k * Uv.Vh + s.cb] = make_double2(u.m[k].re, u.m[k].im);
+}
+
+template <int RECON>
+__global__ void __launch_bounds__(128) heatbath_kernel(GaugeView Uv, Geom g, int mu, int par, double beta,
                                                        uint64_t seed, uint32_t sweep, int overrelax,
                                                        unsigned int *fail_count) {
   int cb = blockIdx.x * blockDim.x + threadIdx.x;
@@ -648,8 +672,8 @@ __global__ void __launch_bounds__(128) heatbath_kernel(double2 *U, Geom g, int m
   Site st = site_of(g, par, cb);
   int c[4] = {st.x, st.y, st.z, st.t};
   Pos s = at(g, c);
-  M3 A = staple(U, g, c, mu);
-  M3 u = load_link(U, g, s, mu);
+  M3 A = staple_with([&](const Pos &q, int nu) { return hb_load<RECON>(Uv, q, nu); }, g, c, mu);
+  M3 u = hb_load<RECON>(Uv, s, mu);
   const int SG[3][2] = {{0, 1}, {1, 2}, {0, 2}};
   unsigned fails = 0;
   for (int sg = 0; sg < 3; sg++) {
@@ -705,8 +729,21 @@ __global__ void __launch_bounds__(128) heatbath_kernel(double2 *U, Geom g, int m
       u.m[3 * j + q] = rj[q];
     }
   }
-  store_link(U, g, s, mu, u);
+  hb_store<RECON>(Uv, s, mu, u);
   if (fails) atomicAdd(fail_count, fails);
+}
+
+// FP64 REC12 copy -> FP64 master, the third row rebuilt
+__global__ void rec12_to_master_kernel(GaugeView Uv, double2 *m, int Vh) {
+  const size_t nl = (size_t)2 * 4 * Vh;
+  const size_t l = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (l >= nl) return;
+  const int blk = (int)(l / Vh), cb = (int)(l % Vh);  // blk = parity * 4 + mu
+  Cx<double> u[9];
+  LinkIO<LQCD_F64, 12>::load(Uv, blk >> 2, blk & 3, cb, u);
+  reconstruct_row2(u);
+#pragma unroll
+  for (int k = 0; k < 9; k++) m[((size_t)blk * 9 + k) * Vh + cb] = make_double2(u[k].re, u[k].im);
 }
 
 // ---------------------------------------------------------------------------
@@ -1165,14 +1202,15 @@ lqcd_status gauge_force_raw(lqcd_ctx *ctx, lqcd_gauge *U, double beta, double c1
 
 lqcd_status reunitarize_raw(lqcd_ctx *ctx, lqcd_gauge *U);
 
-// FP32 sweep: on the FP32 copy, then back into the FP64 field, reunitarised
-lqcd_status heatbath_f32_raw(lqcd_ctx *ctx, lqcd_gauge *U, double beta, uint64_t seed, uint64_t sweep, int n_or,
-                             unsigned int *fail_dev) {
+// FP32 sweep: on the FP32 copy, then back into the FP64 field, reunitarised.
+// Passes: one heatbath pass if hb, then n_or overrelaxation passes.
+lqcd_status heatbath_f32_raw(lqcd_ctx *ctx, lqcd_gauge *U, double beta, uint64_t seed, uint64_t sweep, int hb,
+                             int n_or, unsigned int *fail_dev) {
   // the link format follows the field's (18 reals, or REC12 if imported so)
   const bool r12 = U->recon == 12;
   GaugeView Uf;
   LQCD_TRY(gauge_view(ctx, U, LQCD_F32, r12 ? 12 : 18, &Uf));
-  for (int pass = 0; pass <= n_or; pass++)
+  for (int pass = hb ? 0 : 1; pass <= n_or; pass++)
     for (int mu = 0; mu < 4; mu++)
       for (int par = 0; par < 2; par++) {
         if (r12)
@@ -1190,17 +1228,33 @@ lqcd_status heatbath_f32_raw(lqcd_ctx *ctx, lqcd_gauge *U, double beta, uint64_t
   return reunitarize_raw(ctx, U);
 }
 
-lqcd_status heatbath_raw(lqcd_ctx *ctx, lqcd_gauge *U, double beta, uint64_t seed, uint64_t sweep, int n_or,
-                         unsigned int *fail_dev) {
-  for (int pass = 0; pass <= n_or; pass++)
+// FP64 sweep in place: on the master (18 reals), or for a field imported with
+// recon = 12 on its FP64 REC12 copy, whose first two rows are then written
+// back into the master with the third rebuilt.  Passes as heatbath_f32_raw.
+lqcd_status heatbath_raw(lqcd_ctx *ctx, lqcd_gauge *U, double beta, uint64_t seed, uint64_t sweep, int hb,
+                         int n_or, unsigned int *fail_dev) {
+  const bool r12 = U->recon == 12;
+  GaugeView Uv;
+  LQCD_TRY(gauge_view(ctx, U, LQCD_F64, r12 ? 12 : 18, &Uv));
+  for (int pass = hb ? 0 : 1; pass <= n_or; pass++)
     for (int mu = 0; mu < 4; mu++)
       for (int par = 0; par < 2; par++) {
-        heatbath_kernel<<<nblk(U->g.Vh), 128, 0, ctx->stream>>>((double2 *)U->master, U->g, mu, par, beta,
-                                                                seed, (uint32_t)sweep, pass > 0 ? 1 : 0,
-                                                                fail_dev);
+        if (r12)
+          heatbath_kernel<12><<<nblk(U->g.Vh), 128, 0, ctx->stream>>>(Uv, U->g, mu, par, beta, seed,
+                                                                      (uint32_t)sweep, pass > 0 ? 1 : 0, fail_dev);
+        else
+          heatbath_kernel<18><<<nblk(U->g.Vh), 128, 0, ctx->stream>>>(Uv, U->g, mu, par, beta, seed,
+                                                                      (uint32_t)sweep, pass > 0 ? 1 : 0, fail_dev);
         LQCD_CUDA(ctx, cudaGetLastError());
       }
+  if (r12) {
+    rec12_to_master_kernel<<<nblk(8L * U->g.Vh), 128, 0, ctx->stream>>>(Uv, (double2 *)U->master, U->g.Vh);
+    LQCD_CUDA(ctx, cudaGetLastError());
+  }
   U->version++;
+  if (r12)  // the REC12 copy holds the master's first two rows: still current
+    for (auto &k : U->copies)
+      if (k.prec == LQCD_F64 && k.recon == 12) k.version = U->version;
   return LQCD_OK;
 }
 

@@ -22,9 +22,9 @@ lqcd_status check_field(lqcd_ctx *ctx, const lqcd_field &f, const char *name, bo
 lqcd_status plaquette_sum(lqcd_ctx *ctx, const lqcd_gauge *U, double *sum_retr);
 lqcd_status gauge_force_raw(lqcd_ctx *ctx, lqcd_gauge *U, double beta, double c1, int prec, double *dSdw);
 lqcd_status rectangle_sum(lqcd_ctx *ctx, const lqcd_gauge *U, double *sum_retr);
-lqcd_status heatbath_f32_raw(lqcd_ctx *ctx, lqcd_gauge *U, double beta, uint64_t seed, uint64_t sweep, int n_or,
+lqcd_status heatbath_f32_raw(lqcd_ctx *ctx, lqcd_gauge *U, double beta, uint64_t seed, uint64_t sweep, int hb, int n_or,
                              unsigned int *fail_dev);
-lqcd_status heatbath_raw(lqcd_ctx *ctx, lqcd_gauge *U, double beta, uint64_t seed, uint64_t sweep, int n_or,
+lqcd_status heatbath_raw(lqcd_ctx *ctx, lqcd_gauge *U, double beta, uint64_t seed, uint64_t sweep, int hb, int n_or,
                          unsigned int *fail_dev);
 lqcd_status momenta_raw(lqcd_ctx *ctx, long V, double *P, uint64_t seed, uint32_t traj);
 lqcd_status gaussian_spinor_raw(lqcd_ctx *ctx, const Geom &g, void *eo_full, int parity, uint64_t seed,
@@ -230,8 +230,19 @@ extern "C" int lqcd_heatbath_sweep(lqcd_ctx *ctx, lqcd_gauge *U, double beta, ui
   if (prec != LQCD_F64 && prec != LQCD_F32) return fail(ctx, LQCD_ERR_INVALID, "prec must be LQCD_F64 or LQCD_F32");
   unsigned int *fails = (unsigned int *)ctx->partials;  // scratch word; not read by anyone else
   LQCD_CUDA(ctx, cudaMemsetAsync(fails, 0, sizeof(unsigned int), ctx->stream));
-  if (prec == LQCD_F32) return heatbath_f32_raw(ctx, U, beta, seed, sweep_idx, n_or, fails);
-  return heatbath_raw(ctx, U, beta, seed, sweep_idx, n_or, fails);
+  if (prec == LQCD_F32) return heatbath_f32_raw(ctx, U, beta, seed, sweep_idx, 1, n_or, fails);
+  return heatbath_raw(ctx, U, beta, seed, sweep_idx, 1, n_or, fails);
+}
+
+extern "C" int lqcd_overrelax_sweep(lqcd_ctx *ctx, lqcd_gauge *U, int n_or, int prec) {
+  if (!ctx) return LQCD_ERR_INVALID;
+  LQCD_TRY(check_u(ctx, U));
+  if (n_or < 1 || n_or > 64) return fail(ctx, LQCD_ERR_INVALID, "n_or out of [1, 64]");
+  if (prec != LQCD_F64 && prec != LQCD_F32) return fail(ctx, LQCD_ERR_INVALID, "prec must be LQCD_F64 or LQCD_F32");
+  unsigned int *fails = (unsigned int *)ctx->partials;  // scratch word; not read by anyone else
+  LQCD_CUDA(ctx, cudaMemsetAsync(fails, 0, sizeof(unsigned int), ctx->stream));
+  if (prec == LQCD_F32) return heatbath_f32_raw(ctx, U, 0.0, 0, 0, 0, n_or, fails);
+  return heatbath_raw(ctx, U, 0.0, 0, 0, 0, n_or, fails);
 }
 
 extern "C" int lqcd_momenta_gaussian(lqcd_ctx *ctx, const lqcd_geom *geom, double *P, uint64_t seed,
@@ -366,7 +377,8 @@ extern "C" int lqcd_fermion_force(lqcd_ctx *ctx, const lqcd_gauge *Uc, lqcd_fiel
   if (!geom_equal(Uc->geom, *geom)) return fail(ctx, LQCD_ERR_INVALID, "geometry mismatch");
   LQCD_TRY(check_field(ctx, phi, "phi", false));
   if (phi.prec != LQCD_F64 || phi.nrhs != 1) return fail(ctx, LQCD_ERR_INVALID, "phi must be one F64 EO half field");
-  if (!dSdw || !aligned16(dSdw)) return fail(ctx, LQCD_ERR_INVALID, "dSdw: NULL or misaligned");
+  if (!dSdw && !S_out) return fail(ctx, LQCD_ERR_INVALID, "dSdw and S_out are both NULL");
+  if (dSdw && !aligned16(dSdw)) return fail(ctx, LQCD_ERR_INVALID, "dSdw misaligned");
   if (!params) return fail(ctx, LQCD_ERR_INVALID, "params is NULL");
   if (params->outer_prec != LQCD_F64 && params->outer_prec != LQCD_DF64)
     return fail(ctx, LQCD_ERR_INVALID, "outer_prec must be F64 or DF64");
@@ -394,6 +406,7 @@ extern "C" int lqcd_fermion_force(lqcd_ctx *ctx, const lqcd_gauge *Uc, lqcd_fiel
     *stats = st;
   }
   if (S_out) LQCD_TRY(half_redot(ctx, Vh, ph, X, S_out));
+  if (!dSdw) return LQCD_OK;  // the action alone
   return fermion_force_from_X(ctx, U, X, kappa, mu, dSdw);
 }
 

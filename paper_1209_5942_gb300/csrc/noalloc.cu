@@ -20,9 +20,13 @@
 //   - all calls on a device share the one array: calls whose kernels overlap
 //     on the GPU (different streams, no ordering between them) race and give
 //     wrong results.  Order them on one stream or synchronise between them.
-//   - the array's device address is looked up with cudaGetSymbolAddress on the
-//     first call made while a given device is current, so that first call
-//     should come before any stream capture.
+//   - the array's device address is looked up with cudaGetSymbolAddress on
+//     every call made outside a stream capture, so a call after the device's
+//     primary context was torn down and recreated (cudaDeviceReset), which
+//     loads the module and its array afresh, never uses an address of the
+//     old context.  A call made while its stream is capturing uses the address
+//     of the last call on that device instead (no lookup inside a capture),
+//     so one call outside a capture must come first on each device.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -116,16 +120,23 @@ __global__ void plaquette_finish(const double *partials, int nb, double norm, do
 }
 
 std::mutex g_setup_mutex;
-void *g_scratch[256];  // device address of lqcd_noalloc_partials per device ordinal
+void *g_scratch[256];  // last looked-up device address of lqcd_noalloc_partials per device ordinal
 
-// Once per device, with that device current: the device address of the array.
-cudaError_t scratch_address(int dev, double **ptr) {
+// The device address of the array on the current device (dev): looked up on
+// every call outside a capture; inside a capture of `st` the last address
+// looked up on this device, or an error if there is none yet.
+cudaError_t scratch_address(int dev, cudaStream_t st, double **ptr) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(st, &cs);
+  if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch[dev]) {
+  if (cs == cudaStreamCaptureStatusNone) {
     void *p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, lqcd_noalloc_partials);
+    e = cudaGetSymbolAddress(&p, lqcd_noalloc_partials);
     if (e != cudaSuccess) return e;
     g_scratch[dev] = p;
+  } else if (!g_scratch[dev]) {
+    return cudaErrorStreamCaptureUnsupported;
   }
   *ptr = (double *)g_scratch[dev];
   return cudaSuccess;
@@ -149,12 +160,12 @@ extern "C" int lqcd_plaquette_noalloc(const void *U_lexi, const lqcd_geom *geom,
     cudaGetLastError();
     return LQCD_ERR_CUDA;
   }
+  cudaStream_t st = (cudaStream_t)cuda_stream;
   double *scratch = nullptr;
-  if (scratch_address(dev, &scratch) != cudaSuccess) {
+  if (scratch_address(dev, st, &scratch) != cudaSuccess) {
     cudaGetLastError();
     return LQCD_ERR_CUDA;
   }
-  cudaStream_t st = (cudaStream_t)cuda_stream;
   plaquette_lexi_partials<<<(unsigned)nb, LQCD_NOALLOC_BLOCK, 0, st>>>(
       (const double2 *)U_lexi, geom->L[0], geom->L[1], geom->L[2], geom->L[3], scratch);
   plaquette_finish<<<1, 256, 0, st>>>(scratch, (int)nb, 1.0 / (3.0 * 6.0 * (double)V), plaq_dev);

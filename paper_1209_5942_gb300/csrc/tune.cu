@@ -92,7 +92,7 @@ int tune_choice(lqcd_ctx *ctx, const std::string &key0, int ncand, int fallback,
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(ctx->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
     cudaGetLastError();
-    const int sib = key0.compare(0, 4, "hop4") == 0 ? sibling_choice(ctx, key, ncand) : -1;
+    const int sib = key0.compare(0, 3, "hop") == 0 ? sibling_choice(ctx, key, ncand) : -1;
     return sib >= 0 ? sib : fallback;
   }
   cudaEvent_t e0, e1;
@@ -103,6 +103,8 @@ int tune_choice(lqcd_ctx *ctx, const std::string &key0, int ncand, int fallback,
   }
   int best = fallback;
   float best_ms = 1e30f;
+  // the timing launches are not the caller's work: keep them out of the counters
+  const lqcd_counters saved = ctx->cnt;
   for (int c = 0; c < ncand; c++) {
     run(c);
     cudaEventRecord(e0, ctx->stream);
@@ -119,6 +121,7 @@ int tune_choice(lqcd_ctx *ctx, const std::string &key0, int ncand, int fallback,
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  ctx->cnt = saved;
   ctx->tuned[key] = best;
   tune_save(ctx);
   return best;

@@ -115,6 +115,7 @@ SIGNATURES = [
     ("lqcd_set_launch_choice", _i, [_vp, _i]),
     ("lqcd_set_allocator", _i, [_vp, _ALLOC_FN, _FREE_FN, _vp]),
     ("lqcd_reset_counters", _i, [_vp]),
+    ("lqcd_measure_peaks", _i, [_vp, ctypes.POINTER(_d), ctypes.POINTER(_d)]),
     ("lqcd_field_bytes", ctypes.c_size_t, [ctypes.POINTER(lqcd_geom), _i, _i, _i,
                                            ctypes.POINTER(ctypes.c_size_t)]),
     ("lqcd_gauge_import", _i, [_vp, _vp, ctypes.POINTER(lqcd_geom), _i, ctypes.POINTER(_vp)]),
@@ -141,6 +142,7 @@ SIGNATURES = [
     ("lqcd_gauge_force", _i, [_vp, _vp, _d, _d, _i, _vp, ctypes.POINTER(_d)]),
     ("lqcd_plaquette", _i, [_vp, _vp, ctypes.POINTER(_d)]),
     ("lqcd_heatbath_sweep", _i, [_vp, _vp, _d, ctypes.c_uint64, ctypes.c_uint64, _i, _i]),
+    ("lqcd_overrelax_sweep", _i, [_vp, _vp, _i, _i]),
     ("lqcd_momenta_gaussian", _i, [_vp, ctypes.POINTER(lqcd_geom), _vp, ctypes.c_uint64,
                                    ctypes.c_uint32]),
     ("lqcd_spinor_gaussian", _i, [_vp, ctypes.POINTER(lqcd_geom), lqcd_field, _i, ctypes.c_uint64,
@@ -333,6 +335,13 @@ def lqcd_set_autotune(ctx: Context, enable=True, cache_path=None):
                                       cache_path.encode() if cache_path else None))
 
 
+def lqcd_measure_peaks(ctx: Context) -> tuple[float, float]:
+    """(FP64 FMA, FP32 FMA) peak of the context's GPU in TFLOP/s, measured."""
+    a, b = _d(0.0), _d(0.0)
+    ctx.check(lib().lqcd_measure_peaks(ctx.handle, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
 def lqcd_set_allocator(ctx: Context, alloc_fn=None, free_fn=None):
     """Sets the caller's (alloc, free) pair (ctypes callbacks of the lqcd_alloc_fn /
     lqcd_free_fn types, e.g. a TorchAllocator's); None passes a NULL pointer."""
@@ -439,13 +448,15 @@ def lqcd_cg_solve_batch(ctx: Context, Us, bs, xs, kappas, mus, params: lqcd_cg_p
     return [s.as_dict() for s in stats]
 
 
-def lqcd_fermion_force(ctx: Context, U: Gauge, phi: lqcd_field, dSdw: torch.Tensor, kappa, mu,
+def lqcd_fermion_force(ctx: Context, U: Gauge, phi: lqcd_field, dSdw: torch.Tensor | None, kappa, mu,
                        params: lqcd_cg_params, X_cache: lqcd_field | None = None):
-    """Returns (S, stats); dSdw (float64 [4, V, 8] CUDA) receives dS/domega."""
+    """Returns (S, stats); dSdw (float64 [4, V, 8] CUDA) receives dS/domega
+    (None: the action alone)."""
     st = lqcd_cg_stats()
     S = _d(0.0)
     g = U.geom
-    ctx.check(lib().lqcd_fermion_force(ctx.handle, U.handle, phi, _vp(dSdw.data_ptr()),
+    ctx.check(lib().lqcd_fermion_force(ctx.handle, U.handle, phi,
+                                       _vp(dSdw.data_ptr()) if dSdw is not None else None,
                                        ctypes.byref(X_cache) if X_cache is not None else None,
                                        ctypes.byref(g), kappa, mu, ctypes.byref(params),
                                        ctypes.byref(st), ctypes.byref(S)))
@@ -480,6 +491,10 @@ def lqcd_plaquette(ctx: Context, U: Gauge) -> float:
 
 def lqcd_heatbath_sweep(ctx: Context, U: Gauge, beta, seed, sweep_idx, n_or=0, prec=LQCD_F64):
     ctx.check(lib().lqcd_heatbath_sweep(ctx.handle, U.handle, beta, seed, sweep_idx, n_or, prec))
+
+
+def lqcd_overrelax_sweep(ctx: Context, U: Gauge, n_or=1, prec=LQCD_F64):
+    ctx.check(lib().lqcd_overrelax_sweep(ctx.handle, U.handle, n_or, prec))
 
 
 def lqcd_momenta_gaussian(ctx: Context, L, P: torch.Tensor, seed, traj, antiperiodic_t=True):

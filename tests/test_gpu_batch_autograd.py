@@ -93,3 +93,39 @@ def test_fermion_action_autograd(ctx, oracle):
         assert abs(S.item() - Sref) < 1e-10 * abs(Sref)
         g = host(omega.grad)
         assert np.max(np.abs(g - 2.5 * ref)) < 1e-9 * np.max(np.abs(ref))
+    # omega != 0 is not the field the library evaluates: refused, not ignored
+    omega = torch.zeros((4, V, 8), dtype=torch.float64, device="cuda", requires_grad=True)
+    with torch.no_grad():
+        omega[1, 3, 2] = 1e-3
+    with pytest.raises(ValueError):
+        FermionAction.apply(omega, G, fphi, kappa, mu, prm, False)
+
+
+def test_fermion_action_recompute_keeps_no_gradient(ctx, oracle):
+    """With recompute=True the forward pass allocates no [4, V, 8] gradient
+    (torch's peak memory over the forward pass stays far below its size)
+    and the backward pass still gives the oracle's force."""
+    from paper_1209_5942_gb300.autograd import FermionAction
+    L = (8, 8, 8, 8)
+    V = inputs.volume(L)
+    kappa, mu = 0.13, 0.1
+    U = inputs.random_gauge(L, "near", seed=903, eps=0.4)
+    G = lqcd.lqcd_gauge_import(ctx, dev(U), L)
+    ev = ~oracle.parity_mask(L)
+    phi = inputs.gaussian_spinor(L, 904) * ev[:, None, None]
+    d, s, _ = eo_full_from_lexi(ctx, L, phi)
+    fphi, _ = half_views(L, d, s, lqcd.LQCD_F64)
+    prm = lqcd.cg_params(tol=1e-12, max_iter=50000)
+    omega = torch.zeros((4, V, 8), dtype=torch.float64, device="cuda", requires_grad=True)
+    grad_bytes = omega.numel() * 8
+    torch.cuda.synchronize()
+    torch.cuda.reset_peak_memory_stats()
+    m0 = torch.cuda.memory_allocated()
+    S = FermionAction.apply(omega, G, fphi, kappa, mu, prm, True)
+    torch.cuda.synchronize()
+    assert torch.cuda.max_memory_allocated() - m0 < grad_bytes // 4
+    S.backward()
+    Sref, X = oracle.pseudofermion_action(U, phi, L, kappa, mu, eo=True, tol=1e-13)
+    assert abs(S.item() - Sref) < 1e-9 * abs(Sref)
+    ref = oracle.fermion_dSdw(U, X, L, kappa, mu, eo=True)
+    assert np.max(np.abs(host(omega.grad) - ref)) < 1e-8 * np.max(np.abs(ref))

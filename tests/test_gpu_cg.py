@@ -159,6 +159,18 @@ def test_full_size_24x48_solve(ctx, oracle):
         x, st = _solve(ctx, G, L, b, kappa, mu, tol=1e-10, outer_prec=outer, inner_prec=inner)
         assert st[0]["converged"] == 1
         assert _true_resid(oracle, U, L, x, b, kappa, mu) <= 1e-10
+    G.free()
+    # the benchmark's own path: IEEE FP64 with 18-real links, and the mixed
+    # solve with IEEE-FP64 reliable updates and an FP32 REC12 inner operator
+    G18 = lqcd.lqcd_gauge_import(ctx, dev(U), L, recon=18)
+    for outer, inner, recon in ((lqcd.LQCD_F64, lqcd.LQCD_F64, 18), (lqcd.LQCD_F64, lqcd.LQCD_F32, 12)):
+        x, st = _solve(ctx, G18, L, b, kappa, mu, tol=1e-10, outer_prec=outer, inner_prec=inner,
+                       sloppy_recon=recon)
+        assert st[0]["converged"] == 1 and st[0]["true_resid"] <= 1e-10
+        res = _true_resid(oracle, U, L, x, b, kappa, mu)
+        assert res <= 1e-10
+        # the library's own FP64 true residual agrees with the oracle's
+        assert abs(res - st[0]["true_resid"]) < 1e-3 * res
 
 
 @pytest.mark.parametrize("outer,inner,recon", [

@@ -86,10 +86,13 @@ def test_gauge_update_matches_library_expm(ctx, oracle):
     assert np.max(np.abs(got[5, 2] - scipy.linalg.expm(1j * eps * H) @ U[5, 2])) < 1e-13
 
 
-def test_heatbath_sweep_matches_oracle(ctx, oracle):
+@pytest.mark.parametrize("recon", [18, 12])
+def test_heatbath_sweep_matches_oracle(ctx, oracle, recon):
+    """Three FP64 sweeps link by link; with recon = 12 the sweep runs on the
+    12-real FP64 copy, the third row rebuilt on every load (Sec. 4.1)."""
     L = (4, 4, 4, 4)
     U = inputs.random_gauge(L, "haar", seed=35)
-    G = lqcd.lqcd_gauge_import(ctx, dev(U), L)
+    G = lqcd.lqcd_gauge_import(ctx, dev(U), L, recon=recon)
     Uo = U.copy()
     for sweep in range(3):
         lqcd.lqcd_heatbath_sweep(ctx, G, 5.7, 4242, sweep)
@@ -126,18 +129,53 @@ def test_overrelaxation_preserves_action(ctx):
     G = lqcd.lqcd_gauge_import(ctx, dev(inputs.random_gauge(L, "near", seed=36, eps=0.8)), L)
     F = torch.zeros((4, inputs.volume(L), 8), dtype=torch.float64, device="cuda")
     lqcd.lqcd_heatbath_sweep(ctx, G, 5.7, 1, 0)
-    S0 = lqcd.lqcd_gauge_force(ctx, G, 5.7, F)
     p0 = lqcd.lqcd_plaquette(ctx, G)
     # one heatbath sweep followed by overrelaxation: compare against heatbath alone
     G2 = lqcd.lqcd_gauge_import(ctx, dev(inputs.random_gauge(L, "cold")), L)
     lqcd.lqcd_gauge_copy(ctx, G, G2)
     lqcd.lqcd_heatbath_sweep(ctx, G, 5.7, 1, 1, n_or=0)
     lqcd.lqcd_heatbath_sweep(ctx, G2, 5.7, 1, 1, n_or=2)
-    # overrelaxation is microcanonical: same action as the heatbath-only field
+    # overrelaxation is microcanonical: same action as the heatbath-only field ...
     S1 = lqcd.lqcd_gauge_force(ctx, G, 5.7, F)
     S2 = lqcd.lqcd_gauge_force(ctx, G2, 5.7, F)
     assert abs(S2 - S1) < 1e-8 * abs(S1)
     assert p0 > 0.3
+    # ... but not the identity: the links moved by O(1)
+    assert np.abs(_export(ctx, G, L) - _export(ctx, G2, L)).max() > 0.3
+
+
+@pytest.mark.parametrize("prec,recon,tol", [(lqcd.LQCD_F64, 18, 1e-12), (lqcd.LQCD_F64, 12, 1e-12),
+                                            (lqcd.LQCD_F32, 18, 5e-5), (lqcd.LQCD_F32, 12, 5e-5)])
+def test_overrelax_sweep_matches_oracle(ctx, oracle, prec, recon, tol):
+    """One overrelaxation sweep (Sec. 2.2) from a rough field made by the
+    oracle's heatbath, link by link against the oracle's sweep.  FP64: 1e-12.
+    FP32: staples, reflection and update in binary32 (unit roundoff 2^-24
+    ~ 6e-8; a staple entry sums 6 triple products, ~20 roundings, and three
+    subgroups compound), written back and reunitarised in FP64: 5e-5 ~ 800 u."""
+    L = (4, 4, 4, 4)
+    U = inputs.random_gauge(L, "haar", seed=38)
+    for s in range(3):
+        U, _ = oracle.heatbath_sweep(U, L, 5.7, 21, s)
+    G = lqcd.lqcd_gauge_import(ctx, dev(U), L, recon=recon)
+    lqcd.lqcd_overrelax_sweep(ctx, G, 1, prec)
+    got = _export(ctx, G, L)
+    ref, skipped = oracle.overrelax_sweep(U, L)
+    assert skipped == 0
+    err = np.abs(got - ref).max()
+    assert err < tol, err
+    assert np.abs(ref - U).max() > 0.3  # the sweep is not close to the identity
+    # two passes against two oracle sweeps
+    lqcd.lqcd_overrelax_sweep(ctx, G, 1, prec)
+    ref2, _ = oracle.overrelax_sweep(ref, L)
+    assert np.abs(_export(ctx, G, L) - ref2).max() < 2 * tol
+
+
+def test_overrelax_rejects_bad_arguments(ctx):
+    L = (4, 4, 4, 4)
+    G = lqcd.lqcd_gauge_import(ctx, dev(inputs.random_gauge(L, "cold")), L)
+    for n_or, prec in [(0, lqcd.LQCD_F64), (65, lqcd.LQCD_F64), (1, lqcd.LQCD_DF64)]:
+        with pytest.raises(lqcd.LqcdError):
+            lqcd.lqcd_overrelax_sweep(ctx, G, n_or, prec)
 
 
 def _even_half_field(ctx, L, psi_even):
@@ -167,6 +205,42 @@ def test_fermion_force_vs_oracle(ctx, oracle, outer, inner, recon):
     ref = oracle.fermion_dSdw(U, X, L, kappa, mu, eo=True)
     assert abs(S - Sref) < 1e-10 * abs(Sref)
     assert relerr(host(F), ref) < 1e-9
+
+
+@pytest.mark.parametrize("recon", [18, 12])
+def test_fermion_force_at_equal_X(ctx, oracle, recon):
+    """The force kernel alone at the oracle's X = (Mhat^+ Mhat)^-1 phi, handed
+    in through X_cache (reserved = 1: no solve runs), against the oracle's
+    force from the same X to 1e-12; then the store path: with reserved = 0 the
+    call solves, stores X and sets reserved, and the next call reuses it."""
+    L = (4, 4, 2, 4)
+    V = inputs.volume(L)
+    kappa, mu = 0.14, 0.1
+    U = inputs.random_gauge(L, "near", seed=37, eps=0.4)
+    G = lqcd.lqcd_gauge_import(ctx, dev(U), L, recon=recon)
+    ev = ~oracle.parity_mask(L)
+    phi = inputs.gaussian_spinor(L, 38) * ev[:, None, None]
+    Sref, X = oracle.pseudofermion_action(U, phi, L, kappa, mu, eo=True, tol=1e-14)
+    ref = oracle.fermion_dSdw(U, X, L, kappa, mu, eo=True)
+    keep, fphi = _even_half_field(ctx, L, phi)
+    keepx, fx = _even_half_field(ctx, L, X * ev[:, None, None])
+    fx.reserved = 1
+    F = torch.zeros((4, V, 8), dtype=torch.float64, device="cuda")
+    prm = lqcd.cg_params(tol=1e-13, max_iter=50000)
+    S, st = lqcd.lqcd_fermion_force(ctx, G, fphi, F, kappa, mu, prm, X_cache=fx)
+    assert st["iters"] == 0
+    assert relerr(host(F), ref) < 1e-12
+    assert abs(S - np.vdot(phi, X).real) < 1e-12 * abs(S)
+    # store path
+    keepy, fy = _even_half_field(ctx, L, np.zeros_like(phi))
+    F1 = torch.zeros_like(F)
+    S1, st1 = lqcd.lqcd_fermion_force(ctx, G, fphi, F1, kappa, mu, prm, X_cache=fy)
+    assert st1["iters"] > 0 and fy.reserved == 1
+    F2 = torch.zeros_like(F)
+    S2, st2 = lqcd.lqcd_fermion_force(ctx, G, fphi, F2, kappa, mu, prm, X_cache=fy)
+    assert st2["iters"] == 0 and S2 == S1
+    assert torch.equal(F1, F2)
+    assert relerr(host(F2), ref) < 1e-9
 
 
 def test_fermion_force_finite_difference_gpu(ctx, oracle):
@@ -361,6 +435,7 @@ def test_f32_overrelaxation_preserves_action(ctx):
     S1 = lqcd.lqcd_gauge_force(ctx, G, 5.7, F)
     S2 = lqcd.lqcd_gauge_force(ctx, G2, 5.7, F)
     assert abs(S2 - S1) < 1e-5 * abs(S1)
+    assert np.abs(_export(ctx, G, L) - _export(ctx, G2, L)).max() > 0.3  # the links moved
 
 
 def test_heatbath_rejects_other_precisions(ctx):
@@ -417,3 +492,32 @@ def test_hmc_mass_preconditioning(ctx, oracle):
     assert abs(st["H0"] - H0) < 1e-9 * abs(H0)
     assert abs(dHs[2]) < 1.0
     assert 3.0 < dHs[2] / dHs[4] < 5.3, dHs
+
+
+def test_hmc_mass_preconditioned_trajectory_matches_oracle(ctx, oracle):
+    """One mass-preconditioned trajectory (Sec. 2.2) on three nested 2MN time
+    scales -- ratio force outside, W = Mhat(mu2) force in the middle, tlSym
+    gauge force inside -- from the same links and Philox streams as the
+    oracle's three-scale integrator: H0, dH and the final links agree."""
+    L = (4, 4, 2, 4)
+    beta, kappa, mu, mu2, c1 = 3.9, 0.14, 0.05, 0.25, lqcd.TLSYM_C1
+    U = inputs.random_gauge(L, "near", seed=49, eps=0.3)
+    seed, traj = 93, 4
+    G = lqcd.lqcd_gauge_import(ctx, dev(U), L)
+    prm = lqcd.hmc_params(beta, kappa, mu, tau=0.5, nsteps=2, nf=1, seed=seed, traj=traj,
+                          cg=lqcd.cg_params(tol=1e-13, max_iter=50000), integrator=lqcd.LQCD_2MN,
+                          c1=c1, nsteps_gauge=2, mu2=mu2, nsteps_mid=2)
+    st = lqcd.lqcd_hmc_trajectory(ctx, G, prm)
+    ev = ~oracle.parity_mask(L)
+    eta1 = oracle.gaussian_spinor(L, seed, traj) * ev[:, None, None]
+    eta2 = oracle.gaussian_spinor(L, seed ^ 0x9E3779B97F4A7C15, traj) * ev[:, None, None]
+    P0 = oracle.momenta(L, seed, traj)
+    U1, P1, dH, (H0, H1), _ = oracle.hmc_md_2mn_hasenbusch(U, P0, eta1, eta2, L, beta, kappa, mu, mu2, c1=c1,
+                                                           nsteps=2, nsteps_mid=2, nsteps_g=2, tau=0.5,
+                                                           tol=1e-13)
+    assert abs(st["H0"] - H0) < 1e-9 * abs(H0)
+    assert abs(st["dH"] - dH) < 1e-7 * max(1.0, abs(dH))
+    if st["accepted"]:
+        assert relerr(_export(ctx, G, L), U1) < 1e-10
+    else:
+        assert np.array_equal(_export(ctx, G, L), U)
