@@ -11,8 +11,16 @@ true residual).  Prints ONE JSON line (rank 0):
            every kernel's inputs read once, outputs written once) over the
            device-timed region, summed over ranks / max time over ranks
   roofline the half-hop kernel timed alone with CUDA events on the library
-           stream; FP64 arithmetic is bound by the FP64 pipe (bound "alu"),
+           stream; FP64 arithmetic is bound by the FP64 pipe (bound "alu":
+           peak derived from this device's SM count and maximum clock, and
+           peak_measured from the library's FMA microbenchmark),
            float-float and lower precisions by HBM
+  cg       the FP64 solve's iterations and true residual, and
+           cg.variants: time to 1e-10 for every precision path on the same
+           system (FP64, FP64 outer / FP32 inner, float-float, float-float
+           outer with FP32 / FP16+scale / BF16+scale inner), and
+           cg.multi_rhs: the 12 point sources in one 12-RHS solve against 12
+           single-RHS solves
   e2e      the same metric through the public API with host buffers: links
            and source copied host->device, gauge import, solve, solution
            copied device->host, all inside the timed region
@@ -48,8 +56,7 @@ KAPPA = 0.16
 MU = 0.005 / (2 * 0.16)
 TOL = 1e-10
 SEED_U, SEED_B = 2001, 2002
-# FP64 peak of the FP64 pipe: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FP64_FMA_PER_CLK_PER_SM = 2  # GB300's FP64 pipe: 2 FP64 FMA per clock per SM
 PREC_NAMES = {"f64": 0, "df64": 1, "f32": 2, "bf16s": 3, "f16s": 4}
 
 
@@ -280,10 +287,19 @@ def run_gpu(args):
     peaks, peak_kind = measured_peaks()
     if args.traffic is None:
         args.traffic = NCU_TRAFFIC.get((hop["kernel"], tuple(L), inner, recon))
+    # FP64 pipe peak derived from this device's SM count and maximum SM clock,
+    # and the FMA rate measured by the library's microbenchmark on this GPU
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    max_mhz = clocks.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
+    fp64_derived = sms * FP64_FMA_PER_CLK_PER_SM * 2 * max_mhz * 1e6 / 1e12
+    fp64_meas, fp32_meas = lqcd.lqcd_measure_peaks(ctx)
     if inner == lqcd.LQCD_F64:
-        roof = {"bound": "alu", "achieved": hop["tflops"], "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": hop["tflops"] / FP64_PEAK_TFLOPS, "traffic": args.traffic,
-                "peak_kind": "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz",
+        roof = {"bound": "alu", "achieved": hop["tflops"], "peak": fp64_derived, "unit": "TFLOP/s",
+                "frac": hop["tflops"] / fp64_derived, "traffic": args.traffic,
+                "peak_kind": f"derived: {sms} SMs x {FP64_FMA_PER_CLK_PER_SM} FP64 FMA/clk x 2 x "
+                             f"{max_mhz:.0f} MHz",
+                "peak_measured": fp64_meas, "frac_of_measured": hop["tflops"] / fp64_meas,
+                "peak_measured_kind": "lqcd_measure_peaks: FP64 FMA chains, 8 x 256 threads per SM",
                 "hbm_GBs": hop["gbs"], "hbm_frac": hop["gbs"] / peaks["hbm_gbs"]}
     else:
         roof = {"bound": "hbm", "achieved": hop["gbs"], "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -293,6 +309,7 @@ def run_gpu(args):
     roof["bytes_per_launch"] = hop["bytes"]
     roof["ms_per_launch"] = hop["ms"]
 
+    roof["fp32_peak_measured_TFLOPs"] = fp32_meas
     line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
@@ -310,8 +327,10 @@ def run_gpu(args):
             "clocks": clocks}
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(U_h, b_h, args)
-    if rank == 0 and args.variants:
-        line["variants"] = run_variants(ctx, G, fb, fx, lqcd, torch, stream)
+    if rank == 0 and not args.no_variants:
+        t_f64 = ms / 1e3 / args.steps
+        line["cg"]["variants"] = run_variants(ctx, G, fb, fx, lqcd, torch, t_f64, args.variants)
+        line["cg"]["multi_rhs"] = run_multi_rhs(ctx, G, lqcd, torch)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
@@ -325,8 +344,9 @@ def ctypes_byref(x):
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
-# half hop timed by time_half_hop, from one ncu capture of that launch
-# (profiles/hop_f64_24x48_ncu.md); valid only for the kernel as captured.
+# half hop timed by time_half_hop, from one ncu capture of that launch (the
+# FP64 half hop on 24^3 x 48 with 18-real links); valid only for the kernel as
+# captured.
 NCU_TRAFFIC = {("hop_kernel prec=0 recon=18", (24, 24, 24, 48), 0, 18): 504178432.0}
 
 
@@ -437,31 +457,84 @@ def cpu_baseline(U_h, b_h, args):
                       f"{t:.1f} s; GB/s counted with the same algorithmic bytes per iteration"}
 
 
-def run_variants(ctx, G, fb, fx, lqcd, torch, stream):
-    """Time-to-1e-10 on the same system for the other precision paths (one warm-up
-    solve and one timed solve each)."""
+def _timed_solve(ctx, G, fb, fx, lqcd, torch, prm):
+    """One warm-up solve (autotuning, graph capture) and one solve timed with
+    CUDA events on the library stream; returns (seconds, stats)."""
+    lqcd.lqcd_cg_solve(ctx, G, fb, fx, KAPPA, MU, prm, allow_noconv=True)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    st = lqcd.lqcd_cg_solve(ctx, G, fb, fx, KAPPA, MU, prm, allow_noconv=True)
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3, st
+
+
+def run_variants(ctx, G, fb, fx, lqcd, torch, t_f64, with_bicgstab=False):
+    """Time to a 1e-10 true residual on the same 24^3 x 48 system for every
+    precision path: plain IEEE FP64, mixed with IEEE-FP64 reliable updates,
+    float-float, and float-float outer with FP32 / FP16+scale / BF16+scale
+    inner solves (inner operator on REC12 links).  Each entry carries the
+    library's recomputed IEEE-FP64 true residual."""
     out = {}
-    combos = [("f64", "f64"), ("df64", "df64"), ("df64", "f32"), ("df64", "bf16s"),
-              ("df64", "f16s"), ("f64", "f64", "bicgstab"), ("df64", "df64", "bicgstab"),
-              ("df64", "f32", "bicgstab")]
+    combos = [("f64", "f64", 18), ("f64", "f32", 12), ("df64", "df64", 18), ("df64", "f32", 12),
+              ("df64", "f16s", 12), ("df64", "bf16s", 12)]
+    if with_bicgstab:
+        combos += [("f64", "f64", 18, "bicgstab"), ("df64", "df64", 18, "bicgstab"),
+                   ("df64", "f32", 12, "bicgstab")]
     for combo in combos:
-        outer, inner = combo[:2]
-        bicg = len(combo) > 2
+        outer, inner, recon = combo[:3]
+        bicg = len(combo) > 3
         prm = lqcd.cg_params(tol=TOL, outer_prec=PREC_NAMES[outer], inner_prec=PREC_NAMES[inner],
-                             max_iter=50000, max_restarts=10,
+                             max_iter=50000 if not bicg else 4000, max_restarts=10, sloppy_recon=recon,
+                             check_every=20,
                              solver=lqcd.LQCD_SOLVER_BICGSTAB if bicg else lqcd.LQCD_SOLVER_CG)
         key = f"{outer}/{inner}" + ("/bicgstab" if bicg else "")
         try:
-            lqcd.lqcd_cg_solve(ctx, G, fb, fx, KAPPA, MU, prm)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            st = lqcd.lqcd_cg_solve(ctx, G, fb, fx, KAPPA, MU, prm)[0]
-            dt = time.perf_counter() - t0
-            out[key] = {"time_to_solution_s": dt, "iters": st["iters"],
+            t, st = _timed_solve(ctx, G, fb, fx, lqcd, torch, prm)
+            st = st[0]
+            out[key] = {"time_to_solution_s": t, "iters": st["iters"],
                         "reliable_updates": st["reliable_updates"], "restarts": st["restarts"],
-                        "true_resid": st["true_resid"]}
+                        "converged": st["converged"], "true_resid": st["true_resid"],
+                        "speedup_vs_f64_cg": t_f64 / t}
         except Exception as e:  # report, do not hide
             out[key] = {"error": str(e)}
+    return out
+
+
+def run_multi_rhs(ctx, G, lqcd, torch, nrhs=12):
+    """The 12 unit point sources (spin x colour at the origin) on the same
+    24^3 x 48 field: one 12-RHS solve against 12 single-RHS solves, in
+    float-float / FP32 mixed precision and in float-float."""
+    from paper_1209_5942_gb300 import inputs
+    b12 = inputs.point_sources(L)
+    out = {}
+    for outer, inner, recon in (("df64", "f32", 12), ("df64", "df64", 18)):
+        prm = lqcd.cg_params(tol=TOL, outer_prec=PREC_NAMES[outer], inner_prec=PREC_NAMES[inner],
+                             max_iter=50000, sloppy_recon=recon, check_every=20)
+        bd, _ = lqcd.alloc_field(L, lqcd.LQCD_FULL, lqcd.LQCD_F64, nrhs)
+        xd, _ = lqcd.alloc_field(L, lqcd.LQCD_FULL, lqcd.LQCD_F64, nrhs)
+        fb = lqcd.field(bd, lqcd.LQCD_LAYOUT_EO, nrhs=nrhs)
+        fx = lqcd.field(xd, lqcd.LQCD_LAYOUT_EO, nrhs=nrhs)
+        lqcd.lqcd_spinor_pack(ctx, L, torch.from_numpy(b12).cuda(), fb)
+        t_multi, st = _timed_solve(ctx, G, fb, fx, lqcd, torch, prm)
+        b1, _ = lqcd.alloc_field(L, lqcd.LQCD_FULL, lqcd.LQCD_F64)
+        x1, _ = lqcd.alloc_field(L, lqcd.LQCD_FULL, lqcd.LQCD_F64)
+        f1 = lqcd.field(b1, lqcd.LQCD_LAYOUT_EO)
+        g1 = lqcd.field(x1, lqcd.LQCD_LAYOUT_EO)
+        t_seq, st_seq = 0.0, []
+        for r in range(nrhs):
+            lqcd.lqcd_spinor_pack(ctx, L, torch.from_numpy(b12[r]).cuda(), f1)
+            t, s1 = _timed_solve(ctx, G, f1, g1, lqcd, torch, prm)
+            t_seq += t
+            st_seq.append(s1[0])
+        out[f"{outer}/{inner}"] = {
+            "nrhs": nrhs, "multi_rhs_s": t_multi, "sequential_s": t_seq, "speedup": t_seq / t_multi,
+            "iters_max": max(s["iters"] for s in st), "iters_max_sequential": max(s["iters"] for s in st_seq),
+            "true_resid_max": max(s["true_resid"] for s in st),
+            "converged": all(s["converged"] for s in st)}
+        del bd, xd, b1, x1
     return out
 
 
@@ -830,7 +903,9 @@ def main():
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per launch of the half hop, if captured")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--variants", action="store_true")
+    ap.add_argument("--variants", action="store_true", help="also BiCGStab variants")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the precision variants and the 12-RHS comparison")
     ap.add_argument("--config", default="2", choices=["1", "2", "3", "4a", "4b", "5", "C", "hb", "sweep"],
                     help="2 (default): the 24^3x48 contract line; others print their own line")
     ap.add_argument("--sweeps", type=int, default=200, help="heatbath sweeps for configs 3, 4a, 5")

@@ -166,13 +166,14 @@ def test_multi_rhs_dslash_matches_single(ctx, oracle):
                                    singles[r][1])
 
 
+@pytest.mark.parametrize("L", [(4, 4, 6, 8), (16, 8, 8, 4)])
 @pytest.mark.parametrize("nrhs", [1, 5, 12])
-def test_every_launch_shape_gives_the_same_bits(ctx, nrhs):
+def test_every_launch_shape_gives_the_same_bits(ctx, nrhs, L):
     """Every candidate the autotuner can pick (block shape, grid size, load
     order, RHS per thread) writes the same bits: the multi-RHS hop of each
     candidate equals the default launch in every precision, including ragged
-    RHS groups (5 = 2 + 2 + 1, 4 + 1)."""
-    L = (4, 4, 6, 8)
+    RHS groups (5 = 2 + 2 + 1, 4 + 1), on a small lattice and on one whose
+    half volume (2048) fills whole blocks of every shape."""
     U, G12 = _gauge(ctx, L, seed=21, recon=12)
     G18 = lqcd.lqcd_gauge_import(ctx, dev(U), L, recon=18)
     for prec, G in ((lqcd.LQCD_F64, G18), (lqcd.LQCD_DF64, G18), (lqcd.LQCD_DF64, G12),
@@ -210,18 +211,19 @@ def test_every_launch_shape_gives_the_same_bits(ctx, nrhs):
                 assert torch.equal(got[1], ref[1]), (prec, choice)
 
 
-def test_cg_iterates_do_not_depend_on_launch_shape(ctx):
+@pytest.mark.parametrize("L,choices", [((4, 4, 6, 8), (-1, 0, 7, 19, 33)),
+                                       ((16, 8, 8, 4), (-1, 0, 7, 19, 33, 39))])
+def test_cg_iterates_do_not_depend_on_launch_shape(ctx, L, choices):
     """A mixed-precision multi-RHS solve (reducing hops, per-warp partials)
     returns the same bits and iteration counts whatever launch the tuner
     picks."""
-    L = (4, 4, 6, 8)
     U, G = _gauge(ctx, L, seed=23, recon=12)
     nrhs = 3
     b = dev(inputs.gaussian_spinor(L, 24, nrhs=nrhs))
     prm = lqcd.cg_params(tol=1e-10, outer_prec=lqcd.LQCD_DF64, inner_prec=lqcd.LQCD_F32,
                          sloppy_recon=12)
     outs = []
-    for choice in (-1, 0, 7, 19, 33):
+    for choice in choices:
         x = torch.zeros_like(b)
         lqcd.lqcd_set_launch_choice(ctx, choice)
         try:
