@@ -15,6 +15,9 @@ true residual).  Prints ONE JSON line (rank 0):
            peak derived from this device's SM count and maximum clock, and
            peak_measured from the library's FMA microbenchmark),
            float-float and lower precisions by HBM
+  config3  the 32^3 x 64 heatbath workload: time to 1e-10 for FP64 and the
+           mixed paths (FP64 and float-float outer), and its 12 point
+           sources as one 12-RHS solve against 12 single solves
   cg       the FP64 solve's iterations and true residual, and
            cg.variants: time to 1e-10 for every precision path on the same
            system (FP64, FP64 outer / FP32 inner, float-float, float-float
@@ -331,6 +334,8 @@ def run_gpu(args):
         t_f64 = ms / 1e3 / args.steps
         line["cg"]["variants"] = run_variants(ctx, G, fb, fx, lqcd, torch, t_f64, args.variants)
         line["cg"]["multi_rhs"] = run_multi_rhs(ctx, G, lqcd, torch)
+        del G, Gh
+        line["config3"] = run_config3_block(ctx, lqcd, torch, args.sweeps)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
@@ -536,6 +541,46 @@ def run_multi_rhs(ctx, G, lqcd, torch, nrhs=12):
             "converged": all(s["converged"] for s in st)}
         del bd, xd, b1, x1
     return out
+
+
+def run_config3_block(ctx, lqcd, torch, sweeps):
+    """The mixed-precision workload on 32^3 x 64 (heatbath field at beta = 5.7
+    from a cold start, kappa = 0.157, 2 kappa mu = 0.003, Gaussian source):
+    time to a 1e-10 true residual for plain FP64 and for FP32 / BF16+scale /
+    FP16+scale inner solves with IEEE-FP64 reliable updates, the same with a
+    float-float outer, and on the same field the 12 unit point sources in one
+    12-RHS mixed solve against 12 single-RHS solves."""
+    from paper_1209_5942_gb300 import inputs
+    Lc = (32, 32, 32, 64)
+    kappa, mu = 0.157, 0.003 / (2 * 0.157)
+    G, thb, plaq = _heatbath_field(torch, lqcd, ctx, Lc, 5.7, sweeps, 3003)
+    b = inputs.gaussian_spinor(Lc, 3004)
+    sol = _solve_variants(torch, lqcd, ctx, G, Lc, b, kappa, mu,
+                          [("f64", "f64", 18), ("f64", "f32", 12), ("f64", "bf16s", 12), ("f64", "f16s", 12),
+                           ("df64", "df64", 18), ("df64", "f32", 12), ("df64", "bf16s", 12),
+                           ("df64", "f16s", 12)])
+    t64 = sol["f64/f64/rec18"].get("time_to_solution_s")
+    for v in sol.values():
+        if t64 and v.get("time_to_solution_s"):
+            v["speedup_vs_f64_cg"] = t64 / v["time_to_solution_s"]
+        v.pop("solve_GBs", None)
+    b12 = inputs.point_sources(Lc)
+    multi = _solve_variants(torch, lqcd, ctx, G, Lc, b12, kappa, mu, [("df64", "f32", 12)], nrhs=12)
+    seq_t, seq_it = 0.0, 0
+    for r in range(12):
+        v = list(_solve_variants(torch, lqcd, ctx, G, Lc, b12[r], kappa, mu, [("df64", "f32", 12)]).values())[0]
+        seq_t += v["time_to_solution_s"]
+        seq_it = max(seq_it, v["iters"])
+    m = multi["df64/f32/rec12"]
+    G.free()
+    return {"workload": f"32^3x64, {sweeps} CM heatbath sweeps beta=5.7 from cold (plaquette {plaq:.4f}), "
+                        "kappa=0.157, 2 kappa mu=0.003, Gaussian source, 1e-10 true residual",
+            "heatbath_s": thb, "solves": sol,
+            "multi_rhs_12_point_sources": {"multi_rhs_s": m["time_to_solution_s"], "sequential_s": seq_t,
+                                           "speedup": seq_t / m["time_to_solution_s"], "iters_max": m["iters"],
+                                           "iters_max_sequential": seq_it,
+                                           "true_resid_max": m["true_resid_max"],
+                                           "converged": m["converged"]}}
 
 
 # ------------------------------------------------------------------------------

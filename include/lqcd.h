@@ -260,7 +260,10 @@ typedef struct {
                              reliable-update residuals and of the plain solve */
   int32_t inner_prec;     /* == outer_prec: plain CG; LQCD_F32 / LQCD_BF16S /
                              LQCD_F16S: mixed precision with reliable updates */
-  double delta;           /* reliable-update trigger: ||s|| < delta * max ||s|| */
+  double delta;           /* reliable-update trigger: ||s|| < delta * max ||s||;
+                             <= 0 selects the inner format's default: 0.5 for
+                             LQCD_BF16S (whose 8-bit recursion stalls before a
+                             tenfold drop), 0.1 otherwise */
   int32_t max_restarts;   /* outer iterative-refinement cycles on the true residual */
   int32_t check_every;    /* host polls convergence every this many iterations */
   int32_t use_graph;      /* 1: capture check_every iterations in a CUDA graph */
@@ -395,6 +398,12 @@ int lqcd_spinor_gaussian(lqcd_ctx *ctx, const lqcd_geom *geom, lqcd_field eta, i
 /* U_mu(x) <- exp(i eps P_mu(x)) U_mu(x) for every link (exact 3x3 exponential
  * in FP64), then FP64 reunitarisation. Asynchronous. */
 int lqcd_gauge_update(lqcd_ctx *ctx, lqcd_gauge *U, const double *P, double eps);
+/* The same update in the arithmetic prec: LQCD_F64 (as lqcd_gauge_update) or
+ * LQCD_DF64 -- the algebra element, the exponential, E U and the
+ * reunitarisation in float-float (about 2^-46 relative, on the FP32 pipe;
+ * GB300's FP64 pipe is 1/64 of its rate), P read and U read and written in
+ * FP64.  Other prec: LQCD_ERR_INVALID.  Asynchronous. */
+int lqcd_gauge_update_prec(lqcd_ctx *ctx, lqcd_gauge *U, const double *P, double eps, int prec);
 /* P <- P - eps * dSdw (the leapfrog momentum step, F = -dS/domega). */
 int lqcd_momenta_update(lqcd_ctx *ctx, const lqcd_geom *geom, double *P, const double *dSdw,
                         double eps);
@@ -413,7 +422,8 @@ typedef struct {
   int32_t integrator;  /* LQCD_LEAPFROG or LQCD_2MN (two time scales) */
   double c1;           /* rectangle coefficient of the gauge action (0: Wilson) */
   int32_t nsteps_gauge;/* 2MN: inner gauge steps per outer position update (>= 1) */
-  int32_t force_prec;  /* gauge-force arithmetic: LQCD_F64 (default) or LQCD_DF64
+  int32_t force_prec;  /* arithmetic of the gauge force and of the link update
+                          U <- exp(i h P) U: LQCD_F64 (default) or LQCD_DF64
                           (float-float, FP64-class; H and dH stay IEEE FP64) */
   double lambda;       /* 2MN parameter; 0 selects 0.1931833275037836 */
   double mu2;          /* mass preconditioning (nf = 1): 0 = off; else the heavier twisted

@@ -62,6 +62,7 @@ enum { FIN_ALPHA = 0, FIN_SS = 1, FIN_BETA = 2, FIN_INIT_ZZ = 3, FIN_STORE = 4 }
 // not touch the solver state.
 __global__ void __launch_bounds__(FIN_THREADS) finalize_kernel(SolverHdr *h, int nrhs, const double *partials,
                                                               int nb, int op, double *out) {
+  pdl_wait();
   __shared__ double sh[33];
   __shared__ int last;
   const int r = blockIdx.x;  // one block per right-hand side
@@ -130,7 +131,8 @@ __global__ void __launch_bounds__(FIN_THREADS) finalize_kernel(SolverHdr *h, int
 
 
 static void launch_finalize(lqcd_ctx *ctx, SolverHdr *h, int nrhs, int nb, int op, double *out) {
-  finalize_kernel<<<nrhs, FIN_THREADS, 0, ctx->stream>>>(h, nrhs, ctx->partials, nb, op, out);
+  launch_pdl(finalize_kernel, dim3(nrhs), dim3(FIN_THREADS), 0, ctx->stream, h, nrhs, (const double *)ctx->partials,
+             nb, op, out);
   count_launch(ctx, 8.0 * nb * nrhs);
 }
 
@@ -165,6 +167,7 @@ __global__ void __launch_bounds__(128) cg_xs_kernel(VecArgs a, SolverHdr *h, voi
                                                     const void *p, const float *ps, void *s,
                                                     float *ss, const void *q, const float *qs,
                                                     double *partials) {
+  pdl_wait();
   using R = typename SpinorIO<P>::R;
   __shared__ double sh[8];
   if (*(volatile int *)&h->halt) return;
@@ -198,6 +201,7 @@ __global__ void __launch_bounds__(128) cg_xs_kernel(VecArgs a, SolverHdr *h, voi
 template <int P>
 __global__ void __launch_bounds__(128) cg_p_kernel(VecArgs a, SolverHdr *h, void *p, float *ps,
                                                    const void *z, const float *zs) {
+  pdl_wait();
   using R = typename SpinorIO<P>::R;
   if (*(volatile int *)&h->halt) return;
   int cb = blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y;
@@ -560,7 +564,7 @@ lqcd_status cgls_even(lqcd_ctx *ctx, lqcd_gauge *U, const Geom &g, double kappa,
   LQCD_CUDA(ctx, cudaMemcpyAsync(b2d, ctx->pinned, nrhs * sizeof(double), cudaMemcpyHostToDevice,
                                  ctx->stream));
   state_init_kernel<<<1, 64, 0, ctx->stream>>>(h, nrhs, mixed ? 1 : 0, b2d, prm.tol * 0.5,
-                                               prm.delta > 0 ? prm.delta : 0.1);
+                                               prm.delta > 0 ? prm.delta : default_delta(inner));
   LQCD_CUDA(ctx, cudaGetLastError());
   const HostC one{1, 0}, zero{0, 0}, mone{-1, 0};
   if (!normal) {
@@ -588,7 +592,7 @@ lqcd_status cgls_even(lqcd_ctx *ctx, lqcd_gauge *U, const Geom &g, double kappa,
       // CGLS: x += alpha p; s -= alpha q; z = Mhat^+ s
       count_launch(ctx, (double)Vh * nrhs * spinor_site_bytes(inner) * 6.0);
       LQCD_TRY(dispatch_prec(ctx, inner, [&](auto P) {
-        cg_xs_kernel<decltype(P)::value><<<vgrid, 128, 0, ctx->stream>>>(
+        launch_pdl(cg_xs_kernel<decltype(P)::value>, vgrid, dim3(128), 0, ctx->stream,
             va, h, X.ptr, X.scale, p.f.ptr, p.f.scale, s.f.ptr, s.f.scale, q.f.ptr, q.f.scale,
             ctx->partials);
       }));
@@ -600,7 +604,7 @@ lqcd_status cgls_even(lqcd_ctx *ctx, lqcd_gauge *U, const Geom &g, double kappa,
       LQCD_TRY(apply_schur(Oi, q.f, s.f, t.f, 0, true, nullptr, nullptr, &h->halt));
       count_launch(ctx, (double)Vh * nrhs * spinor_site_bytes(inner) * 6.0);
       LQCD_TRY(dispatch_prec(ctx, inner, [&](auto P) {
-        cg_xs_kernel<decltype(P)::value><<<vgrid, 128, 0, ctx->stream>>>(
+        launch_pdl(cg_xs_kernel<decltype(P)::value>, vgrid, dim3(128), 0, ctx->stream,
             va, h, X.ptr, X.scale, p.f.ptr, p.f.scale, z.f.ptr, z.f.scale, s.f.ptr, s.f.scale,
             ctx->partials);
       }));
@@ -609,8 +613,8 @@ lqcd_status cgls_even(lqcd_ctx *ctx, lqcd_gauge *U, const Geom &g, double kappa,
     }
     count_launch(ctx, (double)Vh * nrhs * spinor_site_bytes(inner) * 3.0);
     LQCD_TRY(dispatch_prec(ctx, inner, [&](auto P) {
-      cg_p_kernel<decltype(P)::value><<<vgrid, 128, 0, ctx->stream>>>(va, h, p.f.ptr, p.f.scale,
-                                                                       z.f.ptr, z.f.scale);
+      launch_pdl(cg_p_kernel<decltype(P)::value>, vgrid, dim3(128), 0, ctx->stream, va, h, p.f.ptr, p.f.scale,
+                 z.f.ptr, z.f.scale);
     }));
     LQCD_CUDA(ctx, cudaGetLastError());
     return LQCD_OK;
@@ -739,7 +743,7 @@ lqcd_status cgls_even(lqcd_ctx *ctx, lqcd_gauge *U, const Geom &g, double kappa,
       // FIN_BETA skips when halted: state_after_reliable clears halt unless all done
       count_launch(ctx, (double)Vh * nrhs * spinor_site_bytes(inner) * 3.0);
       LQCD_TRY(dispatch_prec(ctx, inner, [&](auto P) {
-        cg_p_kernel<decltype(P)::value><<<dim3(nbv, nrhs), 128, 0, ctx->stream>>>(
+        launch_pdl(cg_p_kernel<decltype(P)::value>, dim3(nbv, nrhs), dim3(128), 0, ctx->stream,
             va, h, p.f.ptr, p.f.scale, z.f.ptr, z.f.scale);
       }));
       LQCD_CUDA(ctx, cudaGetLastError());

@@ -17,6 +17,15 @@
 
 namespace lqcd {
 
+// Programmatic dependent launch (sm_90 and later): a kernel launched with the
+// programmatic-stream-serialization attribute (launch_pdl) may be scheduled
+// while its predecessor in the stream is still running, which hides the
+// launch latency between the short kernels of a solver iteration;
+// griddepcontrol.wait returns once the predecessor grid has completed and its
+// writes are visible.  Every kernel launched that way calls pdl_wait() before
+// its first global-memory access; launched normally it returns at once.
+LQCD_DEV void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+
 // ---------------------------------------------------------------------------
 // Geometry
 // ---------------------------------------------------------------------------

@@ -10,11 +10,11 @@ namespace lqcd {
 template <bool PK>
 static void launch_pair(const HopArgs &A, dim3 grid, dim3 block, bool dag, bool red, cudaStream_t st) {
   if (dag) {
-    if (red) hop_df64_pair_kernel<true, true, PK><<<grid, block, 0, st>>>(A);
-    else hop_df64_pair_kernel<true, false, PK><<<grid, block, 0, st>>>(A);
+    if (red) launch_pdl(hop_df64_pair_kernel<true, true, PK>, grid, block, 0, st, A);
+    else launch_pdl(hop_df64_pair_kernel<true, false, PK>, grid, block, 0, st, A);
   } else {
-    if (red) hop_df64_pair_kernel<false, true, PK><<<grid, block, 0, st>>>(A);
-    else hop_df64_pair_kernel<false, false, PK><<<grid, block, 0, st>>>(A);
+    if (red) launch_pdl(hop_df64_pair_kernel<false, true, PK>, grid, block, 0, st, A);
+    else launch_pdl(hop_df64_pair_kernel<false, false, PK>, grid, block, 0, st, A);
   }
 }
 
@@ -23,11 +23,11 @@ void hop_launch_df64(const HopArgs &A, int recon, bool pair, int mode, dim3 grid
   if (pair && mode == 2) {
     const size_t smem = (size_t)block.y * df_staged_words(block.x) * sizeof(float4);
     if (dag) {
-      if (red) hop_df64_staged_kernel<true, true><<<grid, block, smem, st>>>(A);
-      else hop_df64_staged_kernel<true, false><<<grid, block, smem, st>>>(A);
+      if (red) launch_pdl(hop_df64_staged_kernel<true, true>, grid, block, smem, st, A);
+      else launch_pdl(hop_df64_staged_kernel<true, false>, grid, block, smem, st, A);
     } else {
-      if (red) hop_df64_staged_kernel<false, true><<<grid, block, smem, st>>>(A);
-      else hop_df64_staged_kernel<false, false><<<grid, block, smem, st>>>(A);
+      if (red) launch_pdl(hop_df64_staged_kernel<false, true>, grid, block, smem, st, A);
+      else launch_pdl(hop_df64_staged_kernel<false, false>, grid, block, smem, st, A);
     }
     return;
   }

@@ -10,11 +10,11 @@ template <int PREC>
 static void launch_h16_staged(const HopArgs &A, dim3 grid, dim3 block, bool dag, bool red, cudaStream_t st) {
   const size_t smem = (size_t)h16_staged_bytes(block.x);
   if (dag) {
-    if (red) hop_h16_staged_kernel<PREC, true, true><<<grid, block, smem, st>>>(A);
-    else hop_h16_staged_kernel<PREC, true, false><<<grid, block, smem, st>>>(A);
+    if (red) launch_pdl(hop_h16_staged_kernel<PREC, true, true>, grid, block, smem, st, A);
+    else launch_pdl(hop_h16_staged_kernel<PREC, true, false>, grid, block, smem, st, A);
   } else {
-    if (red) hop_h16_staged_kernel<PREC, false, true><<<grid, block, smem, st>>>(A);
-    else hop_h16_staged_kernel<PREC, false, false><<<grid, block, smem, st>>>(A);
+    if (red) launch_pdl(hop_h16_staged_kernel<PREC, false, true>, grid, block, smem, st, A);
+    else launch_pdl(hop_h16_staged_kernel<PREC, false, false>, grid, block, smem, st, A);
   }
 }
 

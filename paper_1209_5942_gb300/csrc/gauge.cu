@@ -1103,6 +1103,139 @@ __global__ void __launch_bounds__(128) gauge_update_kernel(double2 *U, Geom g, c
   }
 }
 
+// ---------------------------------------------------------------------------
+// The same link update in float-float arithmetic on the FP32 pipe (GB300's
+// FP64 pipe runs at 1/64 of the FP32 rate, and the FP64 update above costs
+// ~450 FP64 operations per link): the algebra element, the Cayley-Hamilton
+// exponential (same recurrence and scaling as expi_herm, the series summed
+// until its first omitted term is below 2^-52), the product E U and the
+// reunitarisation are double-word (value hi + lo, ~2^-46 relative); P and U
+// are read from, and U written back to, the FP64 field, whose values hold
+// every double-word exactly.  Only those conversions use the FP64 pipe.
+// ---------------------------------------------------------------------------
+LQCD_DEV df df_of_d(double x) {
+  const float hi = __double2float_rn(x);
+  return {hi, __double2float_rn(__dsub_rn(x, (double)hi))};
+}
+LQCD_DEV double d_of_df(df v) { return __dadd_rn((double)v.hi, (double)v.lo); }
+LQCD_DEV Cx<df> cxd(double re, double im) { return {df_of_d(re), df_of_d(im)}; }
+LQCD_DEV Cx<df> cscale(Cx<df> a, df f) { return {a.re * f, a.im * f}; }
+LQCD_DEV df dsq(Cx<df> a) { return a.re * a.re + a.im * a.im; }
+
+// row *= 1/sqrt(|row|^2): a float rsqrt of the high part refined by one
+// Newton step in double-word arithmetic (relative error ~2^-46)
+LQCD_DEV void normalise_row(Cx<df> *r) {
+  const df n = dsq(r[0]) + dsq(r[1]) + dsq(r[2]);
+  const float y0 = rsqrtf(n.hi);
+  const df y = {y0, 0.0f};
+  // y1 = y (3 - n y^2) / 2
+  const df f = y * (df{1.5f, 0.0f} - (df{0.5f, 0.0f} * n) * (y * y));
+#pragma unroll
+  for (int k = 0; k < 3; k++) r[k] = cscale(r[k], f);
+}
+
+// exp(i h) for traceless Hermitian h in double-words (see expi_herm)
+LQCD_DEV M3d expi_herm_df(const M3d &h0) {
+  float nrm = 0.0f;
+#pragma unroll
+  for (int k = 0; k < 9; k++) nrm = fmaf(h0.m[k].re.hi, h0.m[k].re.hi, fmaf(h0.m[k].im.hi, h0.m[k].im.hi, nrm));
+  nrm = sqrtf(nrm);
+  int s = 0;
+  while (nrm > 0.5f && s < 60) {
+    nrm *= 0.5f;
+    s++;
+  }
+  int deg = 1;
+  for (float t = nrm * nrm * 0.5f; deg < 30 && t >= 0x1p-52f; t *= nrm / (deg + 1)) deg++;
+  const float sc = ldexpf(1.0f, -s);  // exact power of two
+  M3d h;
+#pragma unroll
+  for (int k = 0; k < 9; k++) h.m[k] = {{h0.m[k].re.hi * sc, h0.m[k].re.lo * sc}, {h0.m[k].im.hi * sc, h0.m[k].im.lo * sc}};
+  const M3d h2 = dmul(h, h);
+  const df c1 = df{0.5f, 0.0f} * (h2.m[0].re + h2.m[4].re + h2.m[8].re);
+  const Cx<df> dt = h.m[0] * (h.m[4] * h.m[8] - h.m[5] * h.m[7]) - h.m[1] * (h.m[3] * h.m[8] - h.m[5] * h.m[6]) +
+                    h.m[2] * (h.m[3] * h.m[7] - h.m[4] * h.m[6]);
+  const df c0 = dt.re;
+  df p = {1.0f, 0.0f}, q = {0.0f, 0.0f}, r = {0.0f, 0.0f}, w = {1.0f, 0.0f};
+  df a0r = {1.0f, 0.0f}, a0i = {0.0f, 0.0f}, a1r = {0.0f, 0.0f}, a1i = {0.0f, 0.0f}, a2r = {0.0f, 0.0f},
+     a2i = {0.0f, 0.0f};
+  for (int k = 1; k <= deg; k++) {
+    const df pn = c0 * r, qn = c1 * r + p, rn = q;
+    p = pn;
+    q = qn;
+    r = rn;
+    // w = 1/k! as a double-word: w /= k by one float-division estimate and a correction
+    const float kf = (float)k;
+    const float qh = w.hi / kf;
+    const df rem = w - df{qh, 0.0f} * df{kf, 0.0f};
+    w = fast_two_sum(qh, (rem.hi + rem.lo) / kf);
+    const df f = (k & 2) ? -w : w;
+    if (k & 1) {
+      a0i = f * p + a0i;
+      a1i = f * q + a1i;
+      a2i = f * r + a2i;
+    } else {
+      a0r = f * p + a0r;
+      a1r = f * q + a1r;
+      a2r = f * r + a2r;
+    }
+  }
+  const Cx<df> a0 = {a0r, a0i}, a1 = {a1r, a1i}, a2 = {a2r, a2i};
+  M3d E;
+#pragma unroll
+  for (int k = 0; k < 9; k++) E.m[k] = a1 * h.m[k] + a2 * h2.m[k];
+  E.m[0] = E.m[0] + a0;
+  E.m[4] = E.m[4] + a0;
+  E.m[8] = E.m[8] + a0;
+  for (int t = 0; t < s; t++) E = dmul(E, E);
+  return E;
+}
+
+__global__ void __launch_bounds__(128) gauge_update_df_kernel(double2 *U, Geom g, const double *P, double eps) {
+  long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  int mu, p, cb, c[4];
+  if (!thread_link(g, tid, &mu, &p, &cb, c)) return;
+  const long V = 2L * g.Vh;
+  const Pos s = at(g, c);
+  const double *pp = P + ((size_t)mu * V + s.lexi) * 8;
+  df pa[8];
+#pragma unroll
+  for (int a = 0; a < 8; a++) pa[a] = df_of_d(pp[a]);
+  // eps sum_a p^a lambda^a / 2, as algebra_herm
+  const df e = df_of_d(0.5 * eps), r3 = df_of_d(0.57735026918962576451);
+  const df z = {0.0f, 0.0f};
+  const df d8 = pa[7] * r3;
+  M3d H;
+  H.m[0] = {e * (pa[2] + d8), z};
+  H.m[4] = {e * (d8 - pa[2]), z};
+  H.m[8] = {-(e * (d8 + d8)), z};
+  H.m[1] = {e * pa[0], -(e * pa[1])};
+  H.m[3] = {e * pa[0], e * pa[1]};
+  H.m[2] = {e * pa[3], -(e * pa[4])};
+  H.m[6] = {e * pa[3], e * pa[4]};
+  H.m[5] = {e * pa[5], -(e * pa[6])};
+  H.m[7] = {e * pa[5], e * pa[6]};
+  const M3d E = expi_herm_df(H);
+  M3 u64 = load_link(U, g, s, mu);
+  M3d u;
+#pragma unroll
+  for (int k = 0; k < 9; k++) u.m[k] = cxd(u64.m[k].re, u64.m[k].im);
+  M3d v = dmul(E, u);
+  // reunitarise: row 0 normalised, row 1 orthogonalised and normalised,
+  // row 2 = conj(row0 x row1) (REC12, Sec. 4.1)
+  normalise_row(v.m);
+  Cx<df> d = {z, z};
+#pragma unroll
+  for (int k = 0; k < 3; k++) d = d + conj(v.m[k]) * v.m[3 + k];
+#pragma unroll
+  for (int k = 0; k < 3; k++) v.m[3 + k] = v.m[3 + k] - d * v.m[k];
+  normalise_row(v.m + 3);
+  reconstruct_row2(v.m);
+#pragma unroll
+  for (int k = 0; k < 9; k++) u64.m[k] = {d_of_df(v.m[k].re), d_of_df(v.m[k].im)};
+  store_link(U, g, s, mu, u64);
+}
+
 __global__ void reunitarize_kernel(double2 *U, Geom g) {
   long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
   int p, cb, c[4];
@@ -1271,8 +1404,11 @@ lqcd_status gaussian_spinor_raw(lqcd_ctx *ctx, const Geom &g, void *eo_full, int
   return LQCD_OK;
 }
 
-lqcd_status gauge_update_raw(lqcd_ctx *ctx, lqcd_gauge *U, const double *P, double eps) {
-  gauge_update_kernel<<<nblk(8L * U->g.Vh), 128, 0, ctx->stream>>>((double2 *)U->master, U->g, P, eps);
+lqcd_status gauge_update_raw(lqcd_ctx *ctx, lqcd_gauge *U, const double *P, double eps, int prec) {
+  if (prec == LQCD_DF64)
+    gauge_update_df_kernel<<<nblk(8L * U->g.Vh), 128, 0, ctx->stream>>>((double2 *)U->master, U->g, P, eps);
+  else
+    gauge_update_kernel<<<nblk(8L * U->g.Vh), 128, 0, ctx->stream>>>((double2 *)U->master, U->g, P, eps);
   LQCD_CUDA(ctx, cudaGetLastError());
   U->version++;
   return LQCD_OK;

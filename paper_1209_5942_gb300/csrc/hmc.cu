@@ -29,7 +29,7 @@ lqcd_status heatbath_raw(lqcd_ctx *ctx, lqcd_gauge *U, double beta, uint64_t see
 lqcd_status momenta_raw(lqcd_ctx *ctx, long V, double *P, uint64_t seed, uint32_t traj);
 lqcd_status gaussian_spinor_raw(lqcd_ctx *ctx, const Geom &g, void *eo_full, int parity, uint64_t seed,
                                 uint32_t traj);
-lqcd_status gauge_update_raw(lqcd_ctx *ctx, lqcd_gauge *U, const double *P, double eps);
+lqcd_status gauge_update_raw(lqcd_ctx *ctx, lqcd_gauge *U, const double *P, double eps, int prec);
 lqcd_status momenta_update_raw(lqcd_ctx *ctx, long V, double *P, const double *F, double eps);
 lqcd_status sumsq_raw(lqcd_ctx *ctx, const double *P, size_t n, double *out);
 lqcd_status metro_uniform(lqcd_ctx *ctx, uint64_t seed, uint32_t traj, double *u);
@@ -272,7 +272,16 @@ extern "C" int lqcd_gauge_update(lqcd_ctx *ctx, lqcd_gauge *U, const double *P, 
   LQCD_TRY(check_u(ctx, U));
   if (!P || !aligned16(P)) return fail(ctx, LQCD_ERR_INVALID, "P: NULL or misaligned");
   if (!std::isfinite(eps)) return fail(ctx, LQCD_ERR_NONFINITE, "eps not finite");
-  return gauge_update_raw(ctx, U, P, eps);
+  return gauge_update_raw(ctx, U, P, eps, LQCD_F64);
+}
+
+extern "C" int lqcd_gauge_update_prec(lqcd_ctx *ctx, lqcd_gauge *U, const double *P, double eps, int prec) {
+  if (!ctx) return LQCD_ERR_INVALID;
+  LQCD_TRY(check_u(ctx, U));
+  if (!P || !aligned16(P)) return fail(ctx, LQCD_ERR_INVALID, "P: NULL or misaligned");
+  if (!std::isfinite(eps)) return fail(ctx, LQCD_ERR_NONFINITE, "eps not finite");
+  if (prec != LQCD_F64 && prec != LQCD_DF64) return fail(ctx, LQCD_ERR_INVALID, "prec must be LQCD_F64 or LQCD_DF64");
+  return gauge_update_raw(ctx, U, P, eps, prec);
 }
 
 extern "C" int lqcd_momenta_update(lqcd_ctx *ctx, const lqcd_geom *geom, double *P, const double *dSdw,
@@ -513,7 +522,7 @@ extern "C" int lqcd_hmc_trajectory(lqcd_ctx *ctx, lqcd_gauge *U, const lqcd_hmc_
   };
   auto drift = [&](double h) -> lqcd_status {
     LQCD_TRY(flush());
-    return gauge_update_raw(ctx, U, (const double *)P.p, h);
+    return gauge_update_raw(ctx, U, (const double *)P.p, h, prm->force_prec);
   };
   // 2MN on nested time scales: level 0 is the outermost force; each of its
   // position updates over time h is the 2MN integration of the next level

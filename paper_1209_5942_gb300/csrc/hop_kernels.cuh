@@ -482,6 +482,7 @@ LQCD_DEV void hop_site_rt(const HopArgs &A, int cb, int rhs0) {
 // Blocks of 32 sites x blockDim.y RHS groups of RT; grid z covers the groups.
 template <int PREC, int RECON, bool DAG, bool REDUCE, int RT>
 __global__ void __launch_bounds__(128) hop_rt_kernel(HopArgs A) {
+  pdl_wait();
   if (A.halt && *(volatile int *)A.halt) return;
   const int rhs0 = (blockIdx.z * blockDim.y + threadIdx.y) * RT;
   if (rhs0 >= A.nrhs) return;  // whole warps: blockDim.x is 32
@@ -496,6 +497,7 @@ __global__ void __launch_bounds__(128) hop_rt_kernel(HopArgs A) {
 // a direction are issued before its arithmetic (the autotuner picks).
 template <int PREC, int RECON, bool DAG, bool REDUCE, bool LF>
 __global__ void __launch_bounds__(256, (PREC == LQCD_BF16S || PREC == LQCD_F16S) ? 3 : PREC == LQCD_F32 ? 2 : 1) hop_kernel(HopArgs A) {
+  pdl_wait();
   if (A.halt && *(volatile int *)A.halt) return;
   const int rhs = blockIdx.z * blockDim.y + threadIdx.y;
   const int stride = gridDim.x * blockDim.x;
@@ -574,6 +576,7 @@ LQCD_DEV void hop_dir2(const HopArgs &A, const Site &sA, const Site &sB, int p, 
 
 template <int PREC, int RECON, bool DAG, bool REDUCE>
 __global__ void __launch_bounds__(64) hop_pair2_kernel(HopArgs A) {
+  pdl_wait();
   if (A.halt && *(volatile int *)A.halt) return;
   const int rhs = blockIdx.z;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -618,11 +621,11 @@ __global__ void __launch_bounds__(64) hop_pair2_kernel(HopArgs A) {
 template <int PREC, int RECON>
 inline void launch_pair2(const HopArgs &A, dim3 grid, dim3 block, bool dag, bool red, cudaStream_t st) {
   if (dag) {
-    if (red) hop_pair2_kernel<PREC, RECON, true, true><<<grid, block, 0, st>>>(A);
-    else hop_pair2_kernel<PREC, RECON, true, false><<<grid, block, 0, st>>>(A);
+    if (red) launch_pdl(hop_pair2_kernel<PREC, RECON, true, true>, grid, block, 0, st, A);
+    else launch_pdl(hop_pair2_kernel<PREC, RECON, true, false>, grid, block, 0, st, A);
   } else {
-    if (red) hop_pair2_kernel<PREC, RECON, false, true><<<grid, block, 0, st>>>(A);
-    else hop_pair2_kernel<PREC, RECON, false, false><<<grid, block, 0, st>>>(A);
+    if (red) launch_pdl(hop_pair2_kernel<PREC, RECON, false, true>, grid, block, 0, st, A);
+    else launch_pdl(hop_pair2_kernel<PREC, RECON, false, false>, grid, block, 0, st, A);
   }
 }
 
@@ -721,6 +724,7 @@ LQCD_DEV void h16_staged_steps(const HopArgs &A, const Site &sA, const Site &sB,
 
 template <int PREC, bool DAG, bool REDUCE>
 __global__ void __launch_bounds__(64, 6) hop_h16_staged_kernel(HopArgs A) {
+  pdl_wait();
   using H = typename std::conditional<PREC == LQCD_BF16S, __nv_bfloat16, __half>::type;
   extern __shared__ uint4 h16_words[];
   if (A.halt && *(volatile int *)A.halt) return;
@@ -1044,6 +1048,7 @@ LQCD_DEV void df_pair_finish(const HopArgs &A, int base, int cb, int rhs, int k,
 
 template <bool DAG, bool REDUCE, bool PK>
 __global__ void __launch_bounds__(128, 4) hop_df64_pair_kernel(HopArgs A) {
+  pdl_wait();
   __shared__ double sh[8][4];
   if (A.halt && *(volatile int *)A.halt) return;
   const int rhs = blockIdx.z * blockDim.y + threadIdx.y;
@@ -1155,6 +1160,7 @@ LQCD_DEV void df_stage_compute(const HopArgs &A, const Site &s, int k, int h, bo
 
 template <bool DAG, bool REDUCE>
 __global__ void __launch_bounds__(128, 4) hop_df64_staged_kernel(HopArgs A) {
+  pdl_wait();
   __shared__ double sh[8][4];
   extern __shared__ float4 stage_words[];
   if (A.halt && *(volatile int *)A.halt) return;
@@ -1237,21 +1243,21 @@ __global__ void __launch_bounds__(128) hop_batched_kernel(const HopArgs *descs, 
 template <int PREC, int RECON, bool LF>
 inline void launch_t2(const HopArgs &A, dim3 grid, dim3 block, bool dag, bool red, cudaStream_t st) {
   if (dag) {
-    if (red) hop_kernel<PREC, RECON, true, true, LF><<<grid, block, 0, st>>>(A);
-    else hop_kernel<PREC, RECON, true, false, LF><<<grid, block, 0, st>>>(A);
+    if (red) launch_pdl(hop_kernel<PREC, RECON, true, true, LF>, grid, block, 0, st, A);
+    else launch_pdl(hop_kernel<PREC, RECON, true, false, LF>, grid, block, 0, st, A);
   } else {
-    if (red) hop_kernel<PREC, RECON, false, true, LF><<<grid, block, 0, st>>>(A);
-    else hop_kernel<PREC, RECON, false, false, LF><<<grid, block, 0, st>>>(A);
+    if (red) launch_pdl(hop_kernel<PREC, RECON, false, true, LF>, grid, block, 0, st, A);
+    else launch_pdl(hop_kernel<PREC, RECON, false, false, LF>, grid, block, 0, st, A);
   }
 }
 template <int PREC, int RECON, int RT>
 inline void launch_rt2(const HopArgs &A, dim3 grid, dim3 block, bool dag, bool red, cudaStream_t st) {
   if (dag) {
-    if (red) hop_rt_kernel<PREC, RECON, true, true, RT><<<grid, block, 0, st>>>(A);
-    else hop_rt_kernel<PREC, RECON, true, false, RT><<<grid, block, 0, st>>>(A);
+    if (red) launch_pdl(hop_rt_kernel<PREC, RECON, true, true, RT>, grid, block, 0, st, A);
+    else launch_pdl(hop_rt_kernel<PREC, RECON, true, false, RT>, grid, block, 0, st, A);
   } else {
-    if (red) hop_rt_kernel<PREC, RECON, false, true, RT><<<grid, block, 0, st>>>(A);
-    else hop_rt_kernel<PREC, RECON, false, false, RT><<<grid, block, 0, st>>>(A);
+    if (red) launch_pdl(hop_rt_kernel<PREC, RECON, false, true, RT>, grid, block, 0, st, A);
+    else launch_pdl(hop_rt_kernel<PREC, RECON, false, false, RT>, grid, block, 0, st, A);
   }
 }
 // RHS per thread: 2 or 4 (the register-blocked kernel), else the plain one

@@ -148,6 +148,7 @@ SIGNATURES = [
     ("lqcd_spinor_gaussian", _i, [_vp, ctypes.POINTER(lqcd_geom), lqcd_field, _i, ctypes.c_uint64,
                                   ctypes.c_uint32]),
     ("lqcd_gauge_update", _i, [_vp, _vp, _vp, _d]),
+    ("lqcd_gauge_update_prec", _i, [_vp, _vp, _vp, _d, _i]),
     ("lqcd_momenta_update", _i, [_vp, ctypes.POINTER(lqcd_geom), _vp, _vp, _d]),
     ("lqcd_momenta_kinetic", _i, [_vp, ctypes.POINTER(lqcd_geom), _vp, ctypes.POINTER(_d)]),
     ("lqcd_gauge_copy", _i, [_vp, _vp, _vp]),
@@ -404,7 +405,7 @@ def lqcd_apply_Mdag(ctx: Context, U: Gauge, inp: lqcd_field, out: lqcd_field, ka
                                     parity))
 
 
-def cg_params(tol=1e-10, max_iter=20000, outer_prec=LQCD_F64, inner_prec=None, delta=0.1,
+def cg_params(tol=1e-10, max_iter=20000, outer_prec=LQCD_F64, inner_prec=None, delta=0.0,
               max_restarts=5, check_every=10, use_graph=1, sloppy_recon=0, solver=LQCD_SOLVER_CG,
               inner_tol=0.0) -> lqcd_cg_params:
     p = lqcd_cg_params()
@@ -511,6 +512,10 @@ def lqcd_spinor_gaussian(ctx: Context, L, eta: lqcd_field, parity, seed, traj,
 
 def lqcd_gauge_update(ctx: Context, U: Gauge, P: torch.Tensor, eps):
     ctx.check(lib().lqcd_gauge_update(ctx.handle, U.handle, _vp(P.data_ptr()), eps))
+
+
+def lqcd_gauge_update_prec(ctx: Context, U: Gauge, P: torch.Tensor, eps, prec=LQCD_F64):
+    ctx.check(lib().lqcd_gauge_update_prec(ctx.handle, U.handle, _vp(P.data_ptr()), eps, prec))
 
 
 def lqcd_momenta_update(ctx: Context, L, P: torch.Tensor, dSdw: torch.Tensor, eps,

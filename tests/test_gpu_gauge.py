@@ -86,6 +86,29 @@ def test_gauge_update_matches_library_expm(ctx, oracle):
     assert np.max(np.abs(got[5, 2] - scipy.linalg.expm(1j * eps * H) @ U[5, 2])) < 1e-13
 
 
+@pytest.mark.parametrize("eps,scale", [(0.07, 3.0), (0.004, 1.0), (2.0, 1.0)])
+def test_gauge_update_df64_matches_oracle(ctx, oracle, eps, scale):
+    """U <- exp(i eps P) U in float-float against the oracle's FP64 update and
+    scipy's expm, for a molecular-dynamics step size, a tiny one, and a large
+    one that takes the scaling-and-squaring path; the result stays in SU(3)."""
+    L = (4, 4, 2, 4)
+    U = inputs.random_gauge(L, "haar", seed=33)
+    G = lqcd.lqcd_gauge_import(ctx, dev(U), L)
+    P = inputs.gaussian_algebra(L, 34) * scale
+    lqcd.lqcd_gauge_update_prec(ctx, G, dev(P), eps, lqcd.LQCD_DF64)
+    got = _export(ctx, G, L)
+    ref = oracle.update_links(U, P, L, eps)
+    assert relerr(got, ref) < 1e-13
+    T = np.stack([oracle.generator(a) for a in range(8)])
+    H = np.einsum("a,aij->ij", P[1, 7], T)
+    assert np.max(np.abs(got[7, 1] - scipy.linalg.expm(1j * eps * H) @ U[7, 1])) < 1e-13
+    eye = np.eye(3)
+    assert np.max(np.abs(got @ np.conj(np.transpose(got, (0, 1, 3, 2))) - eye)) < 1e-13
+    assert np.max(np.abs(np.linalg.det(got) - 1)) < 1e-13
+    with pytest.raises(lqcd.LqcdError):
+        lqcd.lqcd_gauge_update_prec(ctx, G, dev(P), eps, lqcd.LQCD_F32)
+
+
 @pytest.mark.parametrize("recon", [18, 12])
 def test_heatbath_sweep_matches_oracle(ctx, oracle, recon):
     """Three FP64 sweeps link by link; with recon = 12 the sweep runs on the
