@@ -352,7 +352,7 @@ def ctypes_byref(x):
 # half hop timed by time_half_hop, from one ncu capture of that launch (the
 # FP64 half hop on 24^3 x 48 with 18-real links); valid only for the kernel as
 # captured.
-NCU_TRAFFIC = {("hop_kernel prec=0 recon=18", (24, 24, 24, 48), 0, 18): 504178432.0}
+NCU_TRAFFIC = {("hop_kernel prec=0 recon=18", (24, 24, 24, 48), 0, 18): 503709952.0}
 
 
 def nvtx_push(name):
@@ -878,6 +878,26 @@ def run_config(args):
                     {"workload": "Cabibbo-Marinari heatbath and overrelaxation sweeps, FP64 and FP32 "
                                  "(FP32 times include the copy back into the FP64 field), beta=5.7, "
                                  "GFLOP/s with the paper's 3912 / 3846 flop per link"})
+    elif c == "hop12":
+        # the multi-RHS F32 half hop (12 RHS, REC12 and 18-real links) against the
+        # single-RHS hop on 24^3 x 48 and 32^3 x 64 near-identity fields; the
+        # 12-RHS launches of the last lattice run inside the NVTX range "hop_multi"
+        res = {}
+        for Lc in ((32, 32, 32, 64), (24, 24, 24, 48)):
+            U = torch.from_numpy(inputs.random_gauge(Lc, "near", seed=4100, eps=0.3)).cuda()
+            for recon in (12, 18):
+                G = lqcd.lqcd_gauge_import(ctx, U, Lc, recon=recon)
+                one = time_half_hop_L(ctx, G, lqcd, torch, Lc, lqcd.LQCD_F32)
+                multi = time_hop_multi(ctx, G, lqcd, torch, Lc, 12, nvtx=(Lc[0] == 24 and recon == 12))
+                res[f"{'x'.join(map(str, Lc))}/rec{recon}"] = {
+                    "single_ms": one["ms"], "single_GBs": one["gbs"], "multi12_ms": multi["ms"],
+                    "multi12_GBs": multi["gbs"], "multi12_pct_hbm": 100 * multi["gbs"] / peaks["hbm_gbs"],
+                    "speedup_vs_12_single": 12 * one["ms"] / multi["ms"],
+                    "bytes_per_rhs_site": multi["bytes_per_rhs_site"]}
+                G.free()
+        config_line("multi-RHS hop", None, {"hop": res},
+                    {"workload": "F32 half hop, 12 right-hand sides vs one, 24^3x48 and 32^3x64, "
+                                 "exp(i 0.3 H) links"})
     elif c == "sweep":
         res = {}
         for ns in (16, 24, 32, 48):
@@ -917,16 +937,21 @@ def time_half_hop_L(ctx, G, lqcd, torch, Lc, prec, reps=20):
     return {"ms": 1e3 * t, "gbs": cnt.hop_bytes / reps / t / 1e9, "tflops": cnt.hop_flops / reps / t / 1e12}
 
 
-def time_hop_multi(ctx, G, lqcd, torch, Lc, nrhs, prec=2, reps=10):
+def time_hop_multi(ctx, G, lqcd, torch, Lc, nrhs, prec=2, reps=10, nvtx=False):
     """Multi-RHS half hop: counted bytes read each link once for all RHS."""
     n_half, sb = lqcd.field_bytes(Lc, lqcd.LQCD_EVEN, prec, nrhs)
-    din = torch.zeros(n_half // 8, dtype=torch.float64, device="cuda")
+    gen = torch.Generator(device="cuda").manual_seed(11)
+    din = torch.randn(n_half // 4, dtype=torch.float32, device="cuda", generator=gen).view(torch.float64)
     dout = torch.zeros_like(din)
     fi = lqcd.field(din, lqcd.LQCD_LAYOUT_EO, prec, nrhs)
     fo = lqcd.field(dout, lqcd.LQCD_LAYOUT_EO, prec, nrhs)
     lqcd.lqcd_dslash(ctx, G, fi, fo, lqcd.LQCD_EVEN, 0)
     lqcd.lib().lqcd_reset_counters(ctx.handle)
+    if nvtx:  # ncu --nvtx --nvtx-include hop_multi/ captures these launches
+        nvtx_push("hop_multi")
     t, _ = _timed(torch, lambda: lqcd.lqcd_dslash(ctx, G, fi, fo, lqcd.LQCD_EVEN, 0), reps)
+    if nvtx:
+        nvtx_pop()
     cnt = lqcd.lqcd_counters()
     lqcd.lib().lqcd_get_counters(ctx.handle, ctypes_byref(cnt))
     per_rhs_site = cnt.hop_bytes / reps / cnt.hop_sites * reps
@@ -951,7 +976,7 @@ def main():
     ap.add_argument("--variants", action="store_true", help="also BiCGStab variants")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the precision variants and the 12-RHS comparison")
-    ap.add_argument("--config", default="2", choices=["1", "2", "3", "4a", "4b", "5", "C", "hb", "sweep"],
+    ap.add_argument("--config", default="2", choices=["1", "2", "3", "4a", "4b", "5", "C", "hb", "sweep", "hop12"],
                     help="2 (default): the 24^3x48 contract line; others print their own line")
     ap.add_argument("--sweeps", type=int, default=200, help="heatbath sweeps for configs 3, 4a, 5")
     ap.add_argument("--trajs", type=int, default=10, help="measured HMC trajectories for config 5")
