@@ -238,6 +238,51 @@ int lqcd_spinor_convert(lqcd_ctx *ctx, const lqcd_geom *geom, int parity, lqcd_f
 int lqcd_dslash(lqcd_ctx *ctx, const lqcd_gauge *U, lqcd_field in, lqcd_field out,
                 const lqcd_geom *geom, int out_parity, int dagger);
 
+/* ---------------------------------------------------------------- */
+/* Domain decomposition along t (Sec. 6: the hop over several GPUs)  */
+/* ---------------------------------------------------------------- */
+
+/* A lattice of extent Lt in t split into nt domains of Lt / nt slices (one per
+ * GPU or process).  Each domain is an ordinary field of this library on the
+ * LOCAL geometry (local->L[3] = Lt / nt, which must be even so that local and
+ * global parities agree; local->antiperiodic_t is ignored: the global
+ * fermion boundary sign is passed to lqcd_dd_pack).  Of the half hop only the
+ * t hops that cross a domain boundary need a neighbour's data, and only its
+ * spin projection: a "face" of Vs/2 = Lx Ly Lz / 2 sites x 6 complex numbers in
+ * the precision of the field ([6][Vs/2] words: complex128 for LQCD_F64,
+ * float-float {re_hi, im_hi, re_lo, im_lo} for LQCD_DF64, complex64 for
+ * LQCD_F32), indexed by a boundary site's checkerboard index within its t
+ * slice.  One half hop on every domain is
+ *   lqcd_dd_pack  (all domains) -> move the faces (caller: NCCL, peer copies)
+ *   -> lqcd_dd_dslash (all domains),
+ * and equals lqcd_dslash on the whole lattice.  Bytes of one face (0 for
+ * invalid input): */
+size_t lqcd_dd_face_bytes(const lqcd_geom *local, int prec);
+
+/* Writes the two faces of this domain for a half hop onto out_parity
+ * (dagger as in lqcd_dslash), from `in` (EO half field of the other parity,
+ * LQCD_F64 / LQCD_DF64 / LQCD_F32, nrhs = 1; other precisions:
+ * LQCD_ERR_UNSUPPORTED):
+ *   face_to_prev (for the previous domain): (1 - s gamma_t) psi(y) for the
+ *     sites y at local t = 0, projected to its two upper spin components;
+ *   face_to_next (for the next domain): U_t(y)^+ (1 + s gamma_t) psi(y) for the
+ *     sites y at local t = Lt/nt - 1, with this domain's links.
+ * negate_to_prev / negate_to_next != 0 multiply a face by -1: set them where
+ * its hop crosses the global t boundary of an antiperiodic lattice (the first
+ * domain's face_to_prev, the last domain's face_to_next).  Device buffers of
+ * lqcd_dd_face_bytes each, 16-byte aligned, not aliasing.  Asynchronous. */
+int lqcd_dd_pack(lqcd_ctx *ctx, const lqcd_gauge *U, lqcd_field in, void *face_to_prev, void *face_to_next,
+                 const lqcd_geom *local, int out_parity, int dagger, int negate_to_prev, int negate_to_next);
+
+/* The half hop of this domain: out = H in on the sites of out_parity, where
+ * the +t hop of a site at local t = Lt/nt - 1 takes face_from_next (the next
+ * domain's face_to_prev) times this domain's U_t(x), and the -t hop of a site
+ * at local t = 0 takes face_from_prev (the previous domain's face_to_next);
+ * with nt = 1 the domain's own faces give lqcd_dslash.  Same fields and
+ * errors as lqcd_dd_pack; in and out must not alias.  Asynchronous. */
+int lqcd_dd_dslash(lqcd_ctx *ctx, const lqcd_gauge *U, lqcd_field in, lqcd_field out, const void *face_from_next,
+                   const void *face_from_prev, const lqcd_geom *local, int out_parity, int dagger);
+
 /* parity = LQCD_FULL: out = M in on the whole lattice (fields LEXI or EO full).
  * parity = LQCD_EVEN: out = Mhat in on the even sites (EO half fields).
  * parity = LQCD_ODD : the odd-site Schur complement A_o - kappa^2 H_oe A_e^-1 H_eo.

@@ -417,6 +417,69 @@ extern "C" int lqcd_dslash(lqcd_ctx *ctx, const lqcd_gauge *U, lqcd_field in, lq
   return launch_hop(ctx, g, L, nullptr);
 }
 
+// ===========================================================================
+// Domain decomposition along t
+// ===========================================================================
+
+extern "C" size_t lqcd_dd_face_bytes(const lqcd_geom *local, int prec) {
+  if (!local || (prec != LQCD_F64 && prec != LQCD_DF64 && prec != LQCD_F32)) return 0;
+  for (int k = 0; k < 4; k++)
+    if (local->L[k] < 2 || (local->L[k] & 1)) return 0;
+  return (size_t)(local->L[0] / 2) * local->L[1] * local->L[2] * 6 * dd_face_word_bytes(prec);
+}
+
+static lqcd_status dd_common(lqcd_ctx *ctx, const lqcd_gauge *U, const lqcd_field &in, const lqcd_geom *local,
+                             int out_parity, int dagger, HopLaunch *L, Geom *g) {
+  LQCD_TRY(check_gauge(ctx, U, local));
+  LQCD_TRY(check_field(ctx, in, "in", false));
+  if (in.nrhs != 1) return fail(ctx, LQCD_ERR_UNSUPPORTED, "domain-decomposed hop: nrhs must be 1");
+  if (in.prec != LQCD_F64 && in.prec != LQCD_DF64 && in.prec != LQCD_F32)
+    return fail(ctx, LQCD_ERR_UNSUPPORTED, "domain-decomposed hop: precision must be F64, DF64 or F32");
+  if (out_parity != LQCD_EVEN && out_parity != LQCD_ODD)
+    return fail(ctx, LQCD_ERR_INVALID, "out_parity must be LQCD_EVEN or LQCD_ODD");
+  lqcd_geom lg = *local;
+  lg.antiperiodic_t = 0;  // the global boundary sign travels in the faces
+  *g = make_geom(lg);
+  L->prec = in.prec;
+  L->recon = link_recon_for(U, in.prec);
+  LQCD_TRY(gauge_view(ctx, const_cast<lqcd_gauge *>(U), in.prec, L->recon, &L->U));
+  L->in = to_half(in, *g, false);
+  L->out_parity = out_parity == LQCD_EVEN ? 0 : 1;
+  L->dagger = dagger ? 1 : 0;
+  return LQCD_OK;
+}
+
+extern "C" int lqcd_dd_pack(lqcd_ctx *ctx, const lqcd_gauge *U, lqcd_field in, void *face_to_prev,
+                            void *face_to_next, const lqcd_geom *local, int out_parity, int dagger,
+                            int negate_to_prev, int negate_to_next) {
+  if (!ctx) return LQCD_ERR_INVALID;
+  if (!face_to_prev || !face_to_next || ((uintptr_t)face_to_prev & 15u) || ((uintptr_t)face_to_next & 15u))
+    return fail(ctx, LQCD_ERR_INVALID, "faces: NULL or not 16-byte aligned");
+  HopLaunch L;
+  Geom g;
+  LQCD_TRY(dd_common(ctx, U, in, local, out_parity, dagger, &L, &g));
+  const size_t fb = lqcd_dd_face_bytes(local, in.prec);
+  if (ranges_overlap(face_to_prev, fb, face_to_next, fb)) return fail(ctx, LQCD_ERR_INVALID, "faces alias");
+  return dd_run(ctx, g, L, true, face_to_prev, face_to_next, negate_to_prev ? 1 : 0, negate_to_next ? 1 : 0);
+}
+
+extern "C" int lqcd_dd_dslash(lqcd_ctx *ctx, const lqcd_gauge *U, lqcd_field in, lqcd_field out,
+                              const void *face_from_next, const void *face_from_prev, const lqcd_geom *local,
+                              int out_parity, int dagger) {
+  if (!ctx) return LQCD_ERR_INVALID;
+  if (!face_from_next || !face_from_prev || ((uintptr_t)face_from_next & 15u) || ((uintptr_t)face_from_prev & 15u))
+    return fail(ctx, LQCD_ERR_INVALID, "faces: NULL or not 16-byte aligned");
+  HopLaunch L;
+  Geom g;
+  LQCD_TRY(dd_common(ctx, U, in, local, out_parity, dagger, &L, &g));
+  LQCD_TRY(check_field(ctx, out, "out", false));
+  if (out.prec != in.prec || out.nrhs != 1) return fail(ctx, LQCD_ERR_INVALID, "in/out precision or nrhs differ");
+  const size_t bytes = spinor_half_bytes(in.prec, g.Vh);
+  if (ranges_overlap(in.ptr, bytes, out.ptr, bytes)) return fail(ctx, LQCD_ERR_INVALID, "in and out alias");
+  L.out = to_half(out, g, false);
+  return dd_run(ctx, g, L, false, const_cast<void *>(face_from_next), const_cast<void *>(face_from_prev), 0, 0);
+}
+
 static int apply_impl(lqcd_ctx *ctx, const lqcd_gauge *U, lqcd_field in, lqcd_field out,
                       const lqcd_geom *geom, double kappa, double mu, int parity, bool dagger) {
   if (!ctx) return LQCD_ERR_INVALID;

@@ -176,6 +176,12 @@ struct HopLaunch {
 };
 lqcd_status launch_hop(lqcd_ctx *ctx, const Geom &g, const HopLaunch &L, int *nblocks_out);
 int hop_blocks(const Geom &g, int nrhs);
+// domain decomposition along t (dd.cu): pack = true writes the two faces
+// (f0 = for the previous domain, f1 = for the next; n0/n1: negate them),
+// pack = false runs the domain's half hop (f0 = face from the next domain,
+// f1 = face from the previous one)
+lqcd_status dd_run(lqcd_ctx *ctx, const Geom &g, const HopLaunch &L, bool pack, void *f0, void *f1, int n0, int n1);
+size_t dd_face_word_bytes(int prec);
 
 // Operators assembled from hop launches (cg.cu)
 struct Op {

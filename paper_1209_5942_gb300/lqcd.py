@@ -125,6 +125,9 @@ SIGNATURES = [
     ("lqcd_spinor_unpack", _i, [_vp, ctypes.POINTER(lqcd_geom), lqcd_field, _vp]),
     ("lqcd_spinor_convert", _i, [_vp, ctypes.POINTER(lqcd_geom), _i, lqcd_field, lqcd_field]),
     ("lqcd_dslash", _i, [_vp, _vp, lqcd_field, lqcd_field, ctypes.POINTER(lqcd_geom), _i, _i]),
+    ("lqcd_dd_face_bytes", ctypes.c_size_t, [ctypes.POINTER(lqcd_geom), _i]),
+    ("lqcd_dd_pack", _i, [_vp, _vp, lqcd_field, _vp, _vp, ctypes.POINTER(lqcd_geom), _i, _i, _i, _i]),
+    ("lqcd_dd_dslash", _i, [_vp, _vp, lqcd_field, lqcd_field, _vp, _vp, ctypes.POINTER(lqcd_geom), _i, _i]),
     ("lqcd_apply_M", _i, [_vp, _vp, lqcd_field, lqcd_field, ctypes.POINTER(lqcd_geom), _d, _d, _i]),
     ("lqcd_apply_Mdag", _i, [_vp, _vp, lqcd_field, lqcd_field, ctypes.POINTER(lqcd_geom), _d, _d,
                              _i]),
@@ -389,6 +392,25 @@ def lqcd_dslash(ctx: Context, U: Gauge, inp: lqcd_field, out: lqcd_field, out_pa
     g = U.geom
     ctx.check(lib().lqcd_dslash(ctx.handle, U.handle, inp, out, ctypes.byref(g), out_parity,
                                 int(dagger)))
+
+
+def lqcd_dd_face_bytes(L_local, prec) -> int:
+    return int(lib().lqcd_dd_face_bytes(ctypes.byref(geom(L_local, False)), prec))
+
+
+def lqcd_dd_pack(ctx: Context, U: Gauge, inp: lqcd_field, face_to_prev: torch.Tensor, face_to_next: torch.Tensor,
+                 out_parity, dagger=0, negate_to_prev=False, negate_to_next=False):
+    g = U.geom
+    ctx.check(lib().lqcd_dd_pack(ctx.handle, U.handle, inp, _vp(face_to_prev.data_ptr()),
+                                 _vp(face_to_next.data_ptr()), ctypes.byref(g), out_parity, int(dagger),
+                                 int(bool(negate_to_prev)), int(bool(negate_to_next))))
+
+
+def lqcd_dd_dslash(ctx: Context, U: Gauge, inp: lqcd_field, out: lqcd_field, face_from_next: torch.Tensor,
+                   face_from_prev: torch.Tensor, out_parity, dagger=0):
+    g = U.geom
+    ctx.check(lib().lqcd_dd_dslash(ctx.handle, U.handle, inp, out, _vp(face_from_next.data_ptr()),
+                                   _vp(face_from_prev.data_ptr()), ctypes.byref(g), out_parity, int(dagger)))
 
 
 def lqcd_apply_M(ctx: Context, U: Gauge, inp: lqcd_field, out: lqcd_field, kappa, mu,
