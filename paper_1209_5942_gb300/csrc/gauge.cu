@@ -442,14 +442,20 @@ __global__ void __launch_bounds__(128) staple6_df_kernel(GaugeView Ud, Geom g, f
 
 // dS/domega of c0 (plaquette) + c1 (rectangle) in float-float; c1 = 0 gives
 // the Wilson force from the plaquette staples alone
-__global__ void __launch_bounds__(128, 3) gauge_force_df_kernel(GaugeView Ud, const float4 *S, Geom g, double beta,
+// the force's constants as float-float (c0, c1, 1/sqrt 3) split on the host,
+// and the final factor beta/6 in FP64
+struct ForceConst {
+  df c0, c1, r3;
+  double f;
+};
+
+__global__ void __launch_bounds__(128, 3) gauge_force_df_kernel(GaugeView Ud, const float4 *S, Geom g, ForceConst cc,
                                                              double c1, double *out) {
   long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
   int mu, p, cb, c[4];
   if (!thread_link(g, tid, &mu, &p, &cb, c)) return;
   const long V = 2L * g.Vh;
   const Pos s0 = at(g, c);
-  const double c0 = 1.0 - 8.0 * c1;
   {
     int cpm[4] = {c[0], c[1], c[2], c[3]}, cmm[4] = {c[0], c[1], c[2], c[3]};
     coords_shift(g, cpm, mu, +1);
@@ -496,32 +502,28 @@ __global__ void __launch_bounds__(128, 3) gauge_force_df_kernel(GaugeView Ud, co
     for (int e = 0; e < 9; e++) Wp.m[e] = czero<df>();
 #pragma unroll 1
     for (int k = 0; k < 6; k++) add_lazy_m(Wp, load_stap_d(S, V, mu, k, s0.lexi));
-    // A = c0 Wp + c1 Wr, then W = U A in FP64 (one 3x3 product per link)
-    M3 A, u;
+    // A = c0 Wp + c1 Wr and W = U A in float-float as well (in FP64 this tail
+    // kept the FP64 pipe 27 % busy); only the eight traces become doubles
+    M3d A;
 #pragma unroll
     for (int e = 0; e < 9; e++) {
       const Cx<df> wp = cnormalise(Wp.m[e]), wr = cnormalise(Wr.m[e]);
-      A.m[e] = {c0 * df_to_double(wp.re) + c1 * df_to_double(wr.re), c0 * df_to_double(wp.im) + c1 * df_to_double(wr.im)};
+      A.m[e] = {cc.c0 * wp.re + cc.c1 * wr.re, cc.c0 * wp.im + cc.c1 * wr.im};
     }
-    {
-      const M3d ud = load_link_d(Ud, s0, mu);
-#pragma unroll
-      for (int e = 0; e < 9; e++) u.m[e] = {df_to_double(ud.m[e].re), df_to_double(ud.m[e].im)};
-    }
-    const M3 W = mmul(u, A);
-    const C *w = W.m;
-    double tr[8];
-    tr[0] = (w[3] + w[1]).im;
-    tr[1] = (times_i(w[1] - w[3])).im;
-    tr[2] = (w[0] - w[4]).im;
-    tr[3] = (w[6] + w[2]).im;
-    tr[4] = (times_i(w[2] - w[6])).im;
-    tr[5] = (w[7] + w[5]).im;
-    tr[6] = (times_i(w[5] - w[7])).im;
-    tr[7] = (w[0] + w[4] - w[8] - w[8]).im * 0.57735026918962576451;
+    const M3d W = dmul(load_link_d(Ud, s0, mu), A);
+    const Cx<df> *w = W.m;
+    df tr[8];
+    tr[0] = w[3].im + w[1].im;
+    tr[1] = w[1].re - w[3].re;  // Im(i (w1 - w3)) = Re(w1 - w3)
+    tr[2] = w[0].im - w[4].im;
+    tr[3] = w[6].im + w[2].im;
+    tr[4] = w[2].re - w[6].re;
+    tr[5] = w[7].im + w[5].im;
+    tr[6] = w[5].re - w[7].re;
+    tr[7] = (w[0].im + w[4].im - (w[8].im + w[8].im)) * cc.r3;
     double *o = out + ((size_t)mu * V + s0.lexi) * 8;
 #pragma unroll
-    for (int a = 0; a < 8; a++) o[a] = (beta / 3.0) * 0.5 * tr[a];
+    for (int a = 0; a < 8; a++) o[a] = cc.f * df_to_double(tr[a]);
   }
 }
 
@@ -1315,7 +1317,12 @@ lqcd_status gauge_force_raw(lqcd_ctx *ctx, lqcd_gauge *U, double beta, double c1
       GaugeView Ud;
       LQCD_TRY(gauge_view(ctx, U, LQCD_DF64, 18, &Ud));
       staple6_df_kernel<<<nblk(4 * V), 128, 0, ctx->stream>>>(Ud, U->g, (float4 *)ctx->staples);
-      gauge_force_df_kernel<<<nblk(4 * V), 128, 0, ctx->stream>>>(Ud, (const float4 *)ctx->staples, U->g, beta, c1,
+      ForceConst cc;
+      cc.c0 = df_from_double(1.0 - 8.0 * c1);
+      cc.c1 = df_from_double(c1);
+      cc.r3 = df_from_double(0.57735026918962576451);
+      cc.f = beta / 6.0;
+      gauge_force_df_kernel<<<nblk(4 * V), 128, 0, ctx->stream>>>(Ud, (const float4 *)ctx->staples, U->g, cc, c1,
                                                               dSdw);
       LQCD_CUDA(ctx, cudaGetLastError());
       return LQCD_OK;
