@@ -54,7 +54,10 @@ struct SolverHdr {
 // layout in device memory: SolverHdr, then RhsState[nrhs]
 LQCD_DEV RhsState *rhs_state(SolverHdr *h) { return (RhsState *)(h + 1); }
 
-enum { FIN_ALPHA = 0, FIN_SS = 1, FIN_BETA = 2, FIN_INIT_ZZ = 3, FIN_STORE = 4 };
+// FIN_SS_BETA: FIN_SS, then (by the last block, for every right-hand side,
+// unless the step halted the solve) FIN_BETA on the same sums -- the
+// normal-equation iteration reduces one vector for both
+enum { FIN_ALPHA = 0, FIN_SS = 1, FIN_BETA = 2, FIN_INIT_ZZ = 3, FIN_STORE = 4, FIN_SS_BETA = 5 };
 
 // One block per right-hand side finishes its reduction and applies the CG
 // scalar step `op`; the last block to finish (ticket) sets the flags over all
@@ -86,6 +89,7 @@ __global__ void __launch_bounds__(FIN_THREADS) finalize_kernel(SolverHdr *h, int
         else { R.alpha = 0.0; if (R.zz > 0.0) bad = 1; }
         break;
       case FIN_SS:
+      case FIN_SS_BETA:
         R.ss = v;
         if (!R.done) {
           R.iters += 1;
@@ -123,8 +127,15 @@ __global__ void __launch_bounds__(FIN_THREADS) finalize_kernel(SolverHdr *h, int
     h->iters = maxit;
     h->all_done = all_done;
     h->need_rel = any_rel;
-    if (op == FIN_SS && (all_done || any_rel)) h->halt = 1;
+    if ((op == FIN_SS || op == FIN_SS_BETA) && (all_done || any_rel)) h->halt = 1;
     if (*(volatile int *)&h->nonfinite) h->halt = 1;
+    if (op == FIN_SS_BETA && !h->halt)
+      for (int k = 0; k < nrhs; k++) {  // FIN_BETA with v = |z|^2 = ss
+        volatile RhsState &R = rs[k];
+        const double ss = R.ss, zz = R.zz;
+        R.beta = R.done ? 0.0 : (zz > 0.0 ? ss / zz : 0.0);
+        R.zz = ss;
+      }
     h->ticket = 0u;
   }
 }
@@ -608,8 +619,7 @@ lqcd_status cgls_even(lqcd_ctx *ctx, lqcd_gauge *U, const Geom &g, double kappa,
             va, h, X.ptr, X.scale, p.f.ptr, p.f.scale, z.f.ptr, z.f.scale, s.f.ptr, s.f.scale,
             ctx->partials);
       }));
-      launch_finalize(ctx, h, nrhs, nbw, FIN_SS, nullptr);
-      launch_finalize(ctx, h, nrhs, nbw, FIN_BETA, nullptr);
+      launch_finalize(ctx, h, nrhs, nbw, FIN_SS_BETA, nullptr);
     }
     count_launch(ctx, (double)Vh * nrhs * spinor_site_bytes(inner) * 3.0);
     LQCD_TRY(dispatch_prec(ctx, inner, [&](auto P) {
@@ -794,14 +804,109 @@ lqcd_status cgls_even(lqcd_ctx *ctx, lqcd_gauge *U, const Geom &g, double kappa,
 //            p = r + beta (p - omega v);  v = Mhat p;  alpha = rho' / (r0, v)
 //            s = r - alpha v;  t = Mhat s;  omega = (t, s) / (t, t)
 //            x += alpha p + omega s;  r = s - omega t
-// until |r| <= tol |b|.  The scalars are complex; the dot products are FP64
-// partial sums per block, finished on the host (three reads per iteration).
+// until |r| <= tol |b|.  The scalars are complex and stay on the device; the
+// dot products are FP64 partial sums per block finished in a fixed order.
 // ---------------------------------------------------------------------------
 
-// per block: Re, Im of sum conj(x) y and sum |y|^2  -> partials[3 * block + k]
+// ---------------------------------------------------------------------------
+// BiCGStab with every scalar on the device.  The complex scalars live in a
+// device BiState; each reduction (cdot_kernel: per-block partials of
+// conj(x) y and |y|^2) is finished by bicg_fin_kernel, one block that sums
+// the partials in a fixed order and applies the scalar step; the vector
+// kernels read the scalars they need.  check_every iterations are captured
+// once in a CUDA graph and replayed; the host reads the state after each
+// replay.  Every kernel returns at once when the state says halt.
+// ---------------------------------------------------------------------------
+struct Zd {
+  double re, im;
+};
+LQCD_HD Zd zmul(Zd a, Zd b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+LQCD_HD Zd zdiv(Zd a, Zd b) {  // a / b, scaled by the larger component of b
+  if (fabs(b.re) >= fabs(b.im)) {
+    const double r = b.im / b.re, d = b.re + b.im * r;
+    return {(a.re + a.im * r) / d, (a.im - a.re * r) / d};
+  }
+  const double r = b.re / b.im, d = b.re * r + b.im;
+  return {(a.re * r + a.im) / d, (a.im * r - a.re) / d};
+}
+LQCD_HD double zabs2(Zd a) { return a.re * a.re + a.im * a.im; }
+
+struct BiState {
+  Zd rho, rho_new, alpha, omega, beta;
+  double rr, rr0, stop2;
+  int it, first, halt, done, nonconv, bad, max_iter, pad;
+};
+enum { BI_RV = 0, BI_OMEGA = 1, BI_RHO = 2 };
+
+// one block: fixed-order sums of the three partial columns, then the step
+__global__ void __launch_bounds__(FIN_THREADS) bicg_fin_kernel(BiState *S, const double *partials, int nb, int op) {
+  pdl_wait();
+  __shared__ double sh[33];
+  if (*(volatile int *)&S->halt) return;
+  double v[3];
+  for (int k = 0; k < 3; k++) {
+    double t = 0.0;
+#pragma unroll 4
+    for (int j = threadIdx.x; j < nb; j += FIN_THREADS) t += partials[3 * j + k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) sh[w] = t;
+    __syncthreads();
+    if (w == 0) {
+      double r = sh[l];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+      if (l == 0) sh[32] = r;
+    }
+    __syncthreads();
+    v[k] = sh[32];
+    __syncthreads();
+  }
+  if (threadIdx.x != 0) return;
+  const Zd xy = {v[0], v[1]};
+  if (!isfinite(v[0]) || !isfinite(v[1]) || !isfinite(v[2])) {
+    S->bad = 1;
+    S->halt = 1;
+    return;
+  }
+  if (op == BI_RV) {  // alpha = rho / (r0, v);  rho <- rho_new
+    S->rho = S->rho_new;
+    if (zabs2(xy) == 0.0) {  // breakdown: the outer refinement restarts
+      S->halt = 1;
+      return;
+    }
+    S->alpha = zdiv(S->rho, xy);
+  } else if (op == BI_OMEGA) {  // omega = (t, s) / |t|^2 = conj((s, t)) / |t|^2
+    S->omega = v[2] > 0.0 ? Zd{xy.re / v[2], -xy.im / v[2]} : Zd{0.0, 0.0};
+  } else {  // rho_new = (r0, r), rr = |r|^2; stop, growth and breakdown tests; next beta
+    S->rho_new = xy;
+    S->rr = v[2];
+    S->it += 1;
+    S->first = 0;
+    if (v[2] <= S->stop2) {
+      S->done = 1;
+      S->halt = 1;
+    } else if (v[2] > 1e12 * S->rr0) {  // spectrum around the origin: diverging
+      S->nonconv = 1;
+      S->halt = 1;
+    } else if (zabs2(S->omega) == 0.0 || zabs2(xy) == 0.0) {
+      S->halt = 1;  // breakdown: the outer refinement restarts
+    } else if (S->it >= S->max_iter) {
+      S->nonconv = 1;
+      S->halt = 1;
+    } else {
+      S->beta = zmul(zdiv(xy, S->rho), zdiv(S->alpha, S->omega));
+    }
+  }
+}
+
+// per block: Re, Im of sum conj(x) y and sum |y|^2 -> partials[3 * block + k]
 template <int P>
-__global__ void __launch_bounds__(128) cdot_kernel(int Vh, const void *x, const float *xs, const void *y,
-                                                   const float *ys, double *partials) {
+__global__ void __launch_bounds__(128) bicg_dot_kernel(int Vh, const BiState *S, const void *x, const float *xs,
+                                                       const void *y, const float *ys, double *partials) {
+  pdl_wait();
+  if (S && *(volatile const int *)&S->halt) return;
   using R = typename SpinorIO<P>::R;
   __shared__ double sh[3][8];
   const int cb = blockIdx.x * blockDim.x + threadIdx.x;
@@ -829,33 +934,54 @@ __global__ void __launch_bounds__(128) cdot_kernel(int Vh, const void *x, const 
   }
 }
 
-// (x, y) and |y|^2 on the host (synchronous)
-static lqcd_status cdot(lqcd_ctx *ctx, int Vh, const HalfField &x, const HalfField &y, std::complex<double> *xy,
-                        double *yy) {
-  const int nb = (Vh + 127) / 128;
-  LQCD_TRY(ensure_partials(ctx, (size_t)3 * nb));
-  count_launch(ctx, (double)Vh * 2.0 * spinor_site_bytes(x.prec));
-  LQCD_TRY(dispatch_prec(ctx, x.prec, [&](auto P) {
-    cdot_kernel<decltype(P)::value><<<nb, 128, 0, ctx->stream>>>(Vh, x.ptr, x.scale, y.ptr, y.scale,
-                                                                 ctx->partials);
-  }));
-  LQCD_CUDA(ctx, cudaGetLastError());
-  LQCD_TRY(ensure_pinned(ctx, (size_t)3 * nb));
-  LQCD_CUDA(ctx, cudaMemcpyAsync(ctx->pinned, ctx->partials, sizeof(double) * 3 * nb, cudaMemcpyDeviceToHost,
-                                 ctx->stream));
-  LQCD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-  double a = 0.0, b = 0.0, c = 0.0;
-  for (int k = 0; k < nb; k++) {
-    a += ctx->pinned[3 * k];
-    b += ctx->pinned[3 * k + 1];
-    c += ctx->pinned[3 * k + 2];
-  }
-  if (xy) *xy = {a, b};
-  if (yy) *yy = c;
-  return LQCD_OK;
-}
+template <class R> LQCD_DEV Cx<R> zc(Zd z) { return {from_double<R>(z.re), from_double<R>(z.im)}; }
 
-static HostC hc(std::complex<double> z) { return HostC{z.real(), z.imag()}; }
+// MODE 0: p = r (first iteration) or p = r + beta (p - omega v)
+// MODE 1: s = r - alpha v
+// MODE 2: x += alpha p + omega s;  r = s - omega t
+template <int P, int MODE>
+__global__ void __launch_bounds__(128) bicg_vec_kernel(int Vh, const BiState *S, void *a0, float *a0s, void *a1,
+                                                       float *a1s, const void *b0, const float *b0s,
+                                                       const void *b1, const float *b1s, const void *b2,
+                                                       const float *b2s) {
+  pdl_wait();
+  if (*(volatile const int *)&S->halt) return;
+  using R = typename SpinorIO<P>::R;
+  const int cb = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cb >= Vh) return;
+  Cx<R> A[12], B[12], C[12];
+  if (MODE == 0) {  // a0 = p, b0 = r, b1 = v
+    SpinorIO<P>::load(SpinorView{(void *)b0, (float *)b0s, Vh}, cb, B);
+    if (!S->first) {
+      const Cx<R> be = zc<R>(S->beta), bo = zc<R>(zmul(S->beta, S->omega));
+      SpinorIO<P>::load(SpinorView{a0, a0s, Vh}, cb, A);
+      SpinorIO<P>::load(SpinorView{(void *)b1, (float *)b1s, Vh}, cb, C);
+#pragma unroll
+      for (int k = 0; k < 12; k++) B[k] = B[k] + (be * A[k] - bo * C[k]);
+    }
+    SpinorIO<P>::store(SpinorView{a0, a0s, Vh}, cb, B);
+  } else if (MODE == 1) {  // a0 = s, b0 = r, b1 = v
+    const Cx<R> al = zc<R>(S->alpha);
+    SpinorIO<P>::load(SpinorView{(void *)b0, (float *)b0s, Vh}, cb, B);
+    SpinorIO<P>::load(SpinorView{(void *)b1, (float *)b1s, Vh}, cb, C);
+#pragma unroll
+    for (int k = 0; k < 12; k++) B[k] = B[k] - al * C[k];
+    SpinorIO<P>::store(SpinorView{a0, a0s, Vh}, cb, B);
+  } else {  // a0 = x, a1 = r, b0 = p, b1 = s, b2 = t
+    const Cx<R> al = zc<R>(S->alpha), om = zc<R>(S->omega);
+    Cx<R> X[12];
+    SpinorIO<P>::load(SpinorView{a0, a0s, Vh}, cb, X);
+    SpinorIO<P>::load(SpinorView{(void *)b0, (float *)b0s, Vh}, cb, A);
+    SpinorIO<P>::load(SpinorView{(void *)b1, (float *)b1s, Vh}, cb, B);
+#pragma unroll
+    for (int k = 0; k < 12; k++) X[k] = X[k] + (al * A[k] + om * B[k]);
+    SpinorIO<P>::store(SpinorView{a0, a0s, Vh}, cb, X);
+    SpinorIO<P>::load(SpinorView{(void *)b2, (float *)b2s, Vh}, cb, C);
+#pragma unroll
+    for (int k = 0; k < 12; k++) B[k] = B[k] - om * C[k];
+    SpinorIO<P>::store(SpinorView{a1, a1s, Vh}, cb, B);
+  }
+}
 
 // Solves Mhat xo = bhat (outer-format fields, one RHS) with BiCGStab in the
 // inner format to the relative residual tol_rel * |b| / |bhat| of the
@@ -877,69 +1003,156 @@ lqcd_status bicgstab_even(lqcd_ctx *ctx, lqcd_gauge *U, const Geom &g, double ka
     X = xs.f;
   }
   const HostC one{1, 0}, zero{0, 0};
-  // x = 0, r = bhat
+  // x = 0, r = bhat, r0 = r
   if (mixed) LQCD_TRY(spinor_convert_raw(ctx, Vh, 1, bhat.ptr, bhat.scale, outer, r.f.ptr, r.f.scale, P));
   else LQCD_TRY(lincomb(ctx, Vh, r.f, bhat, nullptr, one, one, zero, zero, nullptr, nullptr));
   LQCD_TRY(lincomb(ctx, Vh, r0.f, r.f, nullptr, one, one, zero, zero, nullptr, nullptr));
-  std::complex<double> rho(1.0, 0.0), alpha(1.0, 0.0), omega(1.0, 0.0), rho_new, rv, ts;
-  double rr = 0.0, tt = 0.0;
-  LQCD_TRY(cdot(ctx, Vh, r0.f, r.f, &rho_new, &rr));
+  const int nb = (Vh + 127) / 128;
+  LQCD_TRY(ensure_partials(ctx, (size_t)3 * nb));
+  DBuf sbuf(ctx);
+  LQCD_TRY(sbuf.alloc(sizeof(BiState)));
+  BiState *S = (BiState *)sbuf.p;
+  const dim3 vgrid(nb);
+  cudaStream_t cst = ctx->stream;
+  auto dot = [&](const HalfField &a, const HalfField &b, const BiState *state) -> lqcd_status {
+    count_launch(ctx, (double)Vh * 2.0 * spinor_site_bytes(P));
+    return dispatch_prec(ctx, P, [&](auto PP) {
+      launch_pdl(bicg_dot_kernel<decltype(PP)::value>, vgrid, dim3(128), 0, ctx->stream, Vh, state,
+                 (const void *)a.ptr, (const float *)a.scale, (const void *)b.ptr, (const float *)b.scale,
+                 ctx->partials);
+    });
+  };
+  auto fin = [&](int op) -> lqcd_status {
+    launch_pdl(bicg_fin_kernel, dim3(1), dim3(FIN_THREADS), 0, ctx->stream, S, (const double *)ctx->partials, nb,
+               op);
+    count_launch(ctx, 24.0 * nb);
+    LQCD_CUDA(ctx, cudaGetLastError());
+    return LQCD_OK;
+  };
+  // rho_new = (r0, r), rr = |r|^2 on the host once: the stop criterion
+  LQCD_TRY(dot(r0.f, r.f, nullptr));
+  LQCD_TRY(ensure_pinned(ctx, (size_t)3 * nb));
+  LQCD_CUDA(ctx, cudaMemcpyAsync(ctx->pinned, ctx->partials, sizeof(double) * 3 * nb, cudaMemcpyDeviceToHost, cst));
+  LQCD_CUDA(ctx, cudaStreamSynchronize(cst));
+  double a = 0.0, b = 0.0, rr = 0.0;
+  for (int k = 0; k < nb; k++) {
+    a += ctx->pinned[3 * k];
+    b += ctx->pinned[3 * k + 1];
+    rr += ctx->pinned[3 * k + 2];
+  }
   // stop on |r|^2 <= (tol/2)^2 |b|^2 (|b| of the full system, as the CG does);
   // a mixed solve stops earlier, once |r| <= inner_tol times this cycle's |bhat|
-  const double rr0 = rr;
   double stop2 = 0.25 * prm.tol * prm.tol * b2;
   if (mixed) {
     const double itol = prm.inner_tol > 0.0 ? prm.inner_tol : 1e-5;
     stop2 = std::fmax(stop2, itol * itol * rr);
   }
-  int it = 0;
-  lqcd_status result = LQCD_OK;
-  while (rr > stop2) {
-    if (it >= prm.max_iter) {
-      result = LQCD_ERR_NOCONV;
-      break;
+  BiState hs{};
+  hs.rho = {1.0, 0.0};
+  hs.rho_new = {a, b};
+  hs.alpha = hs.omega = {1.0, 0.0};
+  hs.rr = hs.rr0 = rr;
+  hs.stop2 = stop2;
+  hs.first = 1;
+  hs.max_iter = prm.max_iter;
+  hs.halt = rr <= stop2 ? 1 : 0;
+  hs.done = hs.halt;
+  std::memcpy(ctx->pinned, &hs, sizeof(hs));
+  LQCD_CUDA(ctx, cudaMemcpyAsync(S, ctx->pinned, sizeof(hs), cudaMemcpyHostToDevice, cst));
+  auto iteration = [&]() -> lqcd_status {
+    LQCD_TRY(dispatch_prec(ctx, P, [&](auto PP) {  // p = r (+ beta (p - omega v))
+      launch_pdl(bicg_vec_kernel<decltype(PP)::value, 0>, vgrid, dim3(128), 0, ctx->stream, Vh, (const BiState *)S,
+                 p.f.ptr, p.f.scale, (void *)nullptr, (float *)nullptr, (const void *)r.f.ptr,
+                 (const float *)r.f.scale, (const void *)v.f.ptr, (const float *)v.f.scale, (const void *)nullptr,
+                 (const float *)nullptr);
+    }));
+    count_launch(ctx, (double)Vh * 4.0 * spinor_site_bytes(P));
+    LQCD_TRY(apply_schur(Oi, p.f, v.f, tmp.f, 0, false, nullptr, nullptr, &S->halt));
+    LQCD_TRY(dot(r0.f, v.f, S));
+    LQCD_TRY(fin(BI_RV));
+    LQCD_TRY(dispatch_prec(ctx, P, [&](auto PP) {  // s = r - alpha v
+      launch_pdl(bicg_vec_kernel<decltype(PP)::value, 1>, vgrid, dim3(128), 0, ctx->stream, Vh, (const BiState *)S,
+                 sv_.f.ptr, sv_.f.scale, (void *)nullptr, (float *)nullptr, (const void *)r.f.ptr,
+                 (const float *)r.f.scale, (const void *)v.f.ptr, (const float *)v.f.scale, (const void *)nullptr,
+                 (const float *)nullptr);
+    }));
+    count_launch(ctx, (double)Vh * 3.0 * spinor_site_bytes(P));
+    LQCD_TRY(apply_schur(Oi, sv_.f, t.f, tmp.f, 0, false, nullptr, nullptr, &S->halt));
+    LQCD_TRY(dot(sv_.f, t.f, S));
+    LQCD_TRY(fin(BI_OMEGA));
+    LQCD_TRY(dispatch_prec(ctx, P, [&](auto PP) {  // x += alpha p + omega s; r = s - omega t
+      launch_pdl(bicg_vec_kernel<decltype(PP)::value, 2>, vgrid, dim3(128), 0, ctx->stream, Vh, (const BiState *)S,
+                 X.ptr, X.scale, r.f.ptr, r.f.scale, (const void *)p.f.ptr, (const float *)p.f.scale,
+                 (const void *)sv_.f.ptr, (const float *)sv_.f.scale, (const void *)t.f.ptr,
+                 (const float *)t.f.scale);
+    }));
+    count_launch(ctx, (double)Vh * 6.0 * spinor_site_bytes(P));
+    LQCD_TRY(dot(r0.f, r.f, S));
+    return fin(BI_RHO);
+  };
+  const int chunk = prm.check_every > 0 ? prm.check_every : 10;
+  cudaGraphExec_t gexec = nullptr;
+  cudaGraph_t graph = nullptr;
+  lqcd_counters chunk_cnt{};
+  if (prm.use_graph) {
+    // one operator application outside the capture, so the autotuner times
+    // the hop configurations the captured iterations launch (v is
+    // overwritten before it is read)
+    LQCD_TRY(apply_schur(Oi, r.f, v.f, tmp.f, 0, false, nullptr, nullptr, nullptr));
+    cudaStream_t cap;
+    LQCD_CUDA(ctx, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    ctx->stream = cap;
+    const lqcd_counters before = ctx->cnt;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    lqcd_status cs = LQCD_OK;
+    if (e == cudaSuccess) {
+      for (int k = 0; k < chunk && cs == LQCD_OK; k++) cs = iteration();
+      e = cudaStreamEndCapture(cap, &graph);
     }
-    if (it == 0) {
-      LQCD_TRY(lincomb(ctx, Vh, p.f, r.f, nullptr, one, one, zero, zero, nullptr, nullptr));
-    } else {
-      const std::complex<double> beta = (rho_new / rho) * (alpha / omega);
-      // p = r + beta p - beta omega v
-      LQCD_TRY(lincomb(ctx, Vh, tmp.f, p.f, &v.f, hc(beta), hc(beta), hc(-beta * omega), hc(-beta * omega),
-                       nullptr, nullptr));
-      LQCD_TRY(lincomb(ctx, Vh, p.f, r.f, &tmp.f, one, one, one, one, nullptr, nullptr));
+    ctx->stream = cst;
+    cudaStreamDestroy(cap);
+    chunk_cnt.launches = ctx->cnt.launches - before.launches;
+    chunk_cnt.hop_launches = ctx->cnt.hop_launches - before.hop_launches;
+    chunk_cnt.bytes = ctx->cnt.bytes - before.bytes;
+    chunk_cnt.hop_bytes = ctx->cnt.hop_bytes - before.hop_bytes;
+    chunk_cnt.hop_flops = ctx->cnt.hop_flops - before.hop_flops;
+    chunk_cnt.hop_sites = ctx->cnt.hop_sites - before.hop_sites;
+    ctx->cnt = before;
+    if (e != cudaSuccess) return cuda_check(ctx, e, "graph capture");
+    if (cs != LQCD_OK) return cs;
+    e = cudaGraphInstantiate(&gexec, graph, 0);
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(graph);
+      return cuda_check(ctx, e, "graph instantiate");
     }
-    rho = rho_new;
-    LQCD_TRY(apply_schur(Oi, p.f, v.f, tmp.f, 0, false, nullptr, nullptr, nullptr));
-    LQCD_TRY(cdot(ctx, Vh, r0.f, v.f, &rv, nullptr));
-    if (std::abs(rv) == 0.0 || !std::isfinite(std::abs(rv))) break;  // breakdown: refinement restarts
-    alpha = rho / rv;
-    // s = r - alpha v
-    LQCD_TRY(lincomb(ctx, Vh, sv_.f, r.f, &v.f, one, one, hc(-alpha), hc(-alpha), nullptr, nullptr));
-    LQCD_TRY(apply_schur(Oi, sv_.f, t.f, tmp.f, 0, false, nullptr, nullptr, nullptr));
-    std::complex<double> st_;
-    LQCD_TRY(cdot(ctx, Vh, sv_.f, t.f, &st_, &tt));  // (s, t) and |t|^2
-    ts = std::conj(st_);
-    omega = tt > 0.0 ? ts / tt : std::complex<double>(0.0, 0.0);
-    // x += alpha p + omega s
-    LQCD_TRY(lincomb(ctx, Vh, X, X, &p.f, one, one, hc(alpha), hc(alpha), nullptr, nullptr));
-    LQCD_TRY(lincomb(ctx, Vh, X, X, &sv_.f, one, one, hc(omega), hc(omega), nullptr, nullptr));
-    // r = s - omega t
-    LQCD_TRY(lincomb(ctx, Vh, r.f, sv_.f, &t.f, one, one, hc(-omega), hc(-omega), nullptr, nullptr));
-    LQCD_TRY(cdot(ctx, Vh, r0.f, r.f, &rho_new, &rr));
-    ++it;
-    if (!std::isfinite(rr)) {
-      result = fail(ctx, LQCD_ERR_NONFINITE, "BiCGStab: non-finite residual after %d iterations", it);
-      break;
-    }
-    // BiCGStab needs a spectrum of Mhat that does not surround the origin (it
-    // does for near-free fields beyond kappa_c = 1/8): stop once the residual
-    // has grown a millionfold and report non-convergence
-    if (rr > 1e12 * rr0) {
-      result = LQCD_ERR_NOCONV;
-      break;
-    }
-    if (std::abs(omega) == 0.0 || std::abs(rho_new) == 0.0) break;  // breakdown: refinement restarts
   }
+  struct GraphGuard {
+    cudaGraphExec_t &e;
+    cudaGraph_t &g;
+    ~GraphGuard() {
+      if (e) cudaGraphExecDestroy(e);
+      if (g) cudaGraphDestroy(g);
+    }
+  } guard{gexec, graph};
+  lqcd_status result = LQCD_OK;
+  while (!hs.halt) {
+    if (gexec) {
+      LQCD_CUDA(ctx, cudaGraphLaunch(gexec, cst));
+      ctx->cnt.launches += chunk_cnt.launches;
+      ctx->cnt.hop_launches += chunk_cnt.hop_launches;
+      ctx->cnt.bytes += chunk_cnt.bytes;
+      ctx->cnt.hop_bytes += chunk_cnt.hop_bytes;
+      ctx->cnt.hop_flops += chunk_cnt.hop_flops;
+      ctx->cnt.hop_sites += chunk_cnt.hop_sites;
+    } else {
+      for (int k = 0; k < chunk; k++) LQCD_TRY(iteration());
+    }
+    LQCD_CUDA(ctx, cudaMemcpyAsync(ctx->pinned, S, sizeof(hs), cudaMemcpyDeviceToHost, cst));
+    LQCD_CUDA(ctx, cudaStreamSynchronize(cst));
+    std::memcpy(&hs, ctx->pinned, sizeof(hs));
+  }
+  if (hs.bad) result = fail(ctx, LQCD_ERR_NONFINITE, "BiCGStab: non-finite scalar after %d iterations", hs.it);
+  else if (hs.nonconv) result = LQCD_ERR_NOCONV;
   if (mixed) {
     dim3 g2((Vh + 127) / 128, 1);
     LQCD_TRY(dispatch_prec(ctx, outer, [&](auto PO) {
@@ -950,8 +1163,8 @@ lqcd_status bicgstab_even(lqcd_ctx *ctx, lqcd_gauge *U, const Geom &g, double ka
     }));
     LQCD_CUDA(ctx, cudaGetLastError());
   }
-  st->iters += it;
-  if (iters_used) *iters_used = it;
+  st->iters += hs.it;
+  if (iters_used) *iters_used = hs.it;
   return result;
 }
 

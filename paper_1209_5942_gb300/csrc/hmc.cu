@@ -51,14 +51,6 @@ static HalfField f64_half(void *ptr, int Vh) {
   return h;
 }
 
-struct DBuf {  // device scratch freed on scope exit
-  lqcd_ctx *ctx;
-  void *p = nullptr;
-  explicit DBuf(lqcd_ctx *c) : ctx(c) {}
-  ~DBuf() { dfree(ctx, p); }
-  lqcd_status alloc(size_t n) { return dalloc(ctx, &p, n); }
-};
-
 // |f|^2 of one F64 half field (synchronous)
 static lqcd_status half_norm2(lqcd_ctx *ctx, int Vh, const HalfField &f, double *out) {
   DBuf tmp(ctx);

@@ -111,6 +111,13 @@ lqcd_status dalloc(lqcd_ctx *ctx, void **p, size_t bytes);
 void dfree(lqcd_ctx *ctx, void *p);
 lqcd_status ensure_partials(lqcd_ctx *ctx, size_t doubles);
 lqcd_status ensure_pinned(lqcd_ctx *ctx, size_t doubles);
+struct DBuf {  // device scratch freed on scope exit
+  lqcd_ctx *ctx;
+  void *p = nullptr;
+  explicit DBuf(lqcd_ctx *c) : ctx(c) {}
+  ~DBuf() { dfree(ctx, p); }
+  lqcd_status alloc(size_t n) { return dalloc(ctx, &p, n); }
+};
 
 // A half field (one parity) with nrhs right-hand sides in the EO layout.
 struct HalfField {
