@@ -1193,7 +1193,13 @@ LQCD_DEV M3d expi_herm_df(const M3d &h0) {
   return E;
 }
 
-__global__ void __launch_bounds__(128) gauge_update_df_kernel(double2 *U, Geom g, const double *P, double eps) {
+// U is read from the field's float-float copy (no FP64 conversions) and the
+// result is written to both the FP64 master and that copy, which therefore
+// stays current (each FP64 <-> FP32 conversion and FP64 add runs on the FP64
+// pipe: read from the master and with the copy rebuilt afterwards they kept
+// it 69 % busy)
+__global__ void __launch_bounds__(128) gauge_update_df_kernel(double2 *U, GaugeView Ud, Geom g, const double *P,
+                                                              double eps) {
   long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
   int mu, p, cb, c[4];
   if (!thread_link(g, tid, &mu, &p, &cb, c)) return;
@@ -1218,11 +1224,7 @@ __global__ void __launch_bounds__(128) gauge_update_df_kernel(double2 *U, Geom g
   H.m[5] = {e * pa[5], -(e * pa[6])};
   H.m[7] = {e * pa[5], e * pa[6]};
   const M3d E = expi_herm_df(H);
-  M3 u64 = load_link(U, g, s, mu);
-  M3d u;
-#pragma unroll
-  for (int k = 0; k < 9; k++) u.m[k] = cxd(u64.m[k].re, u64.m[k].im);
-  M3d v = dmul(E, u);
+  M3d v = dmul(E, load_link_d(Ud, s, mu));
   // reunitarise: row 0 normalised, row 1 orthogonalised and normalised,
   // row 2 = conj(row0 x row1) (REC12, Sec. 4.1)
   normalise_row(v.m);
@@ -1233,9 +1235,13 @@ __global__ void __launch_bounds__(128) gauge_update_df_kernel(double2 *U, Geom g
   for (int k = 0; k < 3; k++) v.m[3 + k] = v.m[3 + k] - d * v.m[k];
   normalise_row(v.m + 3);
   reconstruct_row2(v.m);
+  M3 u64;
 #pragma unroll
   for (int k = 0; k < 9; k++) u64.m[k] = {d_of_df(v.m[k].re), d_of_df(v.m[k].im)};
   store_link(U, g, s, mu, u64);
+  float4 *w = (float4 *)((char *)Ud.ptr + s.p * Ud.parity_stride + mu * Ud.mu_stride);
+#pragma unroll
+  for (int k = 0; k < 9; k++) w[(size_t)k * Ud.Vh + s.cb] = f4_of(v.m[k]);
 }
 
 __global__ void reunitarize_kernel(double2 *U, Geom g) {
@@ -1412,10 +1418,17 @@ lqcd_status gaussian_spinor_raw(lqcd_ctx *ctx, const Geom &g, void *eo_full, int
 }
 
 lqcd_status gauge_update_raw(lqcd_ctx *ctx, lqcd_gauge *U, const double *P, double eps, int prec) {
-  if (prec == LQCD_DF64)
-    gauge_update_df_kernel<<<nblk(8L * U->g.Vh), 128, 0, ctx->stream>>>((double2 *)U->master, U->g, P, eps);
-  else
-    gauge_update_kernel<<<nblk(8L * U->g.Vh), 128, 0, ctx->stream>>>((double2 *)U->master, U->g, P, eps);
+  if (prec == LQCD_DF64) {
+    GaugeView Ud;
+    LQCD_TRY(gauge_view(ctx, U, LQCD_DF64, 18, &Ud));
+    gauge_update_df_kernel<<<nblk(8L * U->g.Vh), 128, 0, ctx->stream>>>((double2 *)U->master, Ud, U->g, P, eps);
+    LQCD_CUDA(ctx, cudaGetLastError());
+    U->version++;
+    for (auto &k : U->copies)  // written alongside the master: still current
+      if (k.prec == LQCD_DF64 && k.recon == 18) k.version = U->version;
+    return LQCD_OK;
+  }
+  gauge_update_kernel<<<nblk(8L * U->g.Vh), 128, 0, ctx->stream>>>((double2 *)U->master, U->g, P, eps);
   LQCD_CUDA(ctx, cudaGetLastError());
   U->version++;
   return LQCD_OK;

@@ -107,6 +107,19 @@ def test_gauge_update_df64_matches_oracle(ctx, oracle, eps, scale):
     assert np.max(np.abs(np.linalg.det(got) - 1)) < 1e-13
     with pytest.raises(lqcd.LqcdError):
         lqcd.lqcd_gauge_update_prec(ctx, G, dev(P), eps, lqcd.LQCD_F32)
+    # the float-float copy the update writes next to the FP64 field is current:
+    # a float-float hop on it equals the FP64 hop on the updated links
+    lqcd.lqcd_gauge_update_prec(ctx, G, dev(P), eps, lqcd.LQCD_DF64)
+    psi = inputs.gaussian_spinor(L, 35)
+    outs = {}
+    for prec in (lqcd.LQCD_F64, lqcd.LQCD_DF64):
+        data, scale, _ = eo_full_from_lexi(ctx, L, psi, prec)
+        fe, fo = half_views(L, data, scale, prec)
+        od, osc = lqcd.alloc_field(L, lqcd.LQCD_FULL, prec)
+        oe, oo = half_views(L, od, osc, prec)
+        lqcd.lqcd_dslash(ctx, G, fo, oe, lqcd.LQCD_EVEN, 0)
+        outs[prec] = lexi_from_eo_full(ctx, L, lqcd.field(od, lqcd.LQCD_LAYOUT_EO, prec, 1, osc))
+    assert relerr(outs[lqcd.LQCD_DF64], outs[lqcd.LQCD_F64]) < 1e-13
 
 
 @pytest.mark.parametrize("recon", [18, 12])
