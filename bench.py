@@ -15,6 +15,8 @@ true residual).  Prints ONE JSON line (rank 0):
            peak derived from this device's SM count and maximum clock, and
            peak_measured from the library's FMA microbenchmark),
            float-float and lower precisions by HBM
+  hmc      time per HMC trajectory, dH and acceptance: Nf=2 leapfrog on
+           16^3 x 32, and the paper's setup C (tlSym, 2MN) on 24^3 x 8
   config3  the 32^3 x 64 heatbath workload: time to 1e-10 for FP64 and the
            mixed paths (FP64 and float-float outer), and its 12 point
            sources as one 12-RHS solve against 12 single solves
@@ -336,6 +338,7 @@ def run_gpu(args):
         line["cg"]["multi_rhs"] = run_multi_rhs(ctx, G, lqcd, torch)
         del G, Gh
         line["config3"] = run_config3_block(ctx, lqcd, torch, args.sweeps)
+        line["hmc"] = run_hmc_block(ctx, lqcd, torch)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
@@ -581,6 +584,53 @@ def run_config3_block(ctx, lqcd, torch, sweeps):
                                            "iters_max_sequential": seq_it,
                                            "true_resid_max": m["true_resid_max"],
                                            "converged": m["converged"]}}
+
+
+def _trajectories(torch, lqcd, ctx, G, make_params, n_therm, n_meas):
+    out = []
+    for t in range(n_therm + n_meas):
+        st = lqcd.lqcd_hmc_trajectory(ctx, G, make_params(t))
+        if t >= n_therm:
+            out.append(st)
+    return {"s_per_trajectory": statistics.median(s["seconds"] for s in out),
+            "dH": [s["dH"] for s in out], "accepted": [s["accepted"] for s in out],
+            "cg_iters_per_trajectory": [s["cg_iters"] for s in out],
+            "plaquette": [s["plaquette"] for s in out], "thermalisation_trajectories": n_therm}
+
+
+def run_hmc_block(ctx, lqcd, torch):
+    """Two HMC workloads (time per trajectory with every force through the
+    library's solver and adjoint kernels; H and dH in FP64): the Nf = 2
+    twisted-mass leapfrog run on 16^3 x 32 (beta 5.6, kappa 0.16, 2 kappa mu
+    0.005, tau 1, 20 steps) and the paper's setup C on 24^3 x 8 (tlSym
+    beta 3.9, kappa 0.160856, a mu 0.1, 2MN 10 fermion x 10 gauge steps,
+    float-float gauge force and link update), each started from the
+    library's heatbath and thermalised with a few trajectories."""
+    cg = lqcd.cg_params(tol=1e-10, outer_prec=lqcd.LQCD_DF64, inner_prec=lqcd.LQCD_F32, sloppy_recon=18,
+                        check_every=20)
+    out = {}
+    L5 = (16, 16, 16, 32)
+    G, _, _ = _heatbath_field(torch, lqcd, ctx, L5, 5.6, 50, 5005)
+    out["nf2_leapfrog_16x32"] = _trajectories(
+        torch, lqcd, ctx, G,
+        lambda t: lqcd.hmc_params(5.6, 0.16, 0.005 / 0.32, tau=1.0, nsteps=20, nf=1, seed=6006, traj=t, cg=cg),
+        2, 3)
+    out["nf2_leapfrog_16x32"]["workload"] = ("16^3x32, Wilson beta=5.6, kappa=0.16, 2 kappa mu=0.005, leapfrog "
+                                            "tau=1 20 steps, 50 heatbath sweeps from cold, DF64/F32 CG to 1e-10")
+    G.free()
+    LC = (24, 24, 24, 8)
+    G, _, _ = _heatbath_field(torch, lqcd, ctx, LC, 6.0, 100, 5105)
+    out["setup_C_24x8"] = _trajectories(
+        torch, lqcd, ctx, G,
+        lambda t: lqcd.hmc_params(3.9, 0.160856, 0.1, tau=1.0, nsteps=10, nf=1, seed=6106, traj=t, cg=cg,
+                                  integrator=lqcd.LQCD_2MN, c1=lqcd.TLSYM_C1, nsteps_gauge=10,
+                                  force_prec=lqcd.LQCD_DF64),
+        2, 4)
+    out["setup_C_24x8"]["workload"] = ("24^3x8, tlSym beta=3.9, kappa=0.160856, a mu=0.1, 2MN 10 fermion x 10 gauge "
+                                      "steps, tau=1, float-float gauge force and link update, DF64/F32 CG to "
+                                      "1e-10; 100 Wilson heatbath sweeps at beta=6.0 from cold")
+    G.free()
+    return out
 
 
 # ------------------------------------------------------------------------------

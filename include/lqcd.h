@@ -505,7 +505,10 @@ typedef struct {
  *     drawn from the stream of seed ^ 0x9E3779B97F4A7C15.  Pure gauge (nf = 0)
  *     runs the gauge scale alone with 2 nsteps nsteps_gauge steps.
  * Momentum updates at the same links are merged, so each force is
- * evaluated once per distinct field.  Synchronous. */
+ * evaluated once per distinct field.  Every force solve after the first of a
+ * trajectory starts from the solution of the previous one (a chronological
+ * initial guess for the same pseudofermion); its stopping test stays relative
+ * to |phi|.  Synchronous. */
 int lqcd_hmc_trajectory(lqcd_ctx *ctx, lqcd_gauge *U, const lqcd_hmc_params *params,
                         lqcd_hmc_stats *stats);
 

@@ -83,9 +83,14 @@ static lqcd_status half_redot(lqcd_ctx *ctx, int Vh, const HalfField &a, const H
   return LQCD_OK;
 }
 
-// X_e = (Mhat^+ Mhat)^-1 phi_e (F64 half fields); solver statistics added to st
+// X_e = (Mhat^+ Mhat)^-1 phi_e (F64 half fields); solver statistics added to st.
+// guess: X holds a starting vector X0 (the HMC passes the solution of the
+// previous force evaluation of the same pseudofermion, a chronological
+// guess); the solve then runs on A d = phi - A X0 (A = Mhat^+ Mhat, residual
+// formed in the outer format) with the stopping test still relative to
+// |phi|, and returns X = X0 + d.
 lqcd_status solve_normal(lqcd_ctx *ctx, lqcd_gauge *U, const HalfField &phi, const HalfField &X, double kappa,
-                         double mu, const lqcd_cg_params &prm_in, lqcd_cg_stats *st) {
+                         double mu, const lqcd_cg_params &prm_in, lqcd_cg_stats *st, bool guess) {
   const Geom &g = U->g;
   const int Vh = g.Vh;
   lqcd_cg_params prm = prm_in;
@@ -96,25 +101,39 @@ lqcd_status solve_normal(lqcd_ctx *ctx, lqcd_gauge *U, const HalfField &phi, con
   if (!std::isfinite(phi2)) return fail(ctx, LQCD_ERR_NONFINITE, "pseudofermion field is not finite");
   std::vector<double> b2(1, phi2);
   const int outer = prm.outer_prec;
-  DBuf phio(ctx), xo(ctx);
+  const size_t hb = spinor_half_bytes(outer, Vh);
+  DBuf phio(ctx), xo(ctx), t1(ctx), t2(ctx);
   HalfField ph = phi, xx = X;
-  if (outer != LQCD_F64) {
-    size_t hb = spinor_half_bytes(outer, Vh);
+  auto outer_half = [&](DBuf &b) -> HalfField {
+    HalfField h = phi;
+    h.ptr = b.p;
+    h.prec = outer;
+    h.rhs_stride = hb;
+    return h;
+  };
+  if (outer != LQCD_F64 || guess) {
     LQCD_TRY(phio.alloc(hb));
     LQCD_TRY(xo.alloc(hb));
     LQCD_TRY(spinor_convert_raw(ctx, Vh, 1, phi.ptr, nullptr, LQCD_F64, phio.p, nullptr, outer));
-    ph.ptr = phio.p;
-    ph.prec = outer;
-    ph.rhs_stride = hb;
-    xx.ptr = xo.p;
-    xx.prec = outer;
-    xx.rhs_stride = hb;
+    ph = outer_half(phio);
+    xx = outer_half(xo);
   }
-  LQCD_CUDA(ctx, cudaMemsetAsync(xx.ptr, 0, xx.rhs_stride, ctx->stream));
   if (phi2 == 0.0) {
     LQCD_CUDA(ctx, cudaMemsetAsync(X.ptr, 0, X.rhs_stride, ctx->stream));
     return LQCD_OK;
   }
+  if (guess) {  // ph <- phi - Mhat^+ Mhat X0 in the outer format
+    LQCD_TRY(t1.alloc(hb));
+    LQCD_TRY(t2.alloc(hb));
+    Op op{ctx, g, {}, outer, U->recon, kappa, mu};
+    LQCD_TRY(gauge_view(ctx, U, outer, U->recon, &op.U));
+    const HalfField T1 = outer_half(t1), T2 = outer_half(t2);
+    LQCD_TRY(spinor_convert_raw(ctx, Vh, 1, X.ptr, nullptr, LQCD_F64, xo.p, nullptr, outer));
+    LQCD_TRY(apply_schur(op, xx, T1, T2, 0, false, nullptr, nullptr, nullptr));
+    LQCD_TRY(apply_schur(op, T1, xx, T2, 0, true, nullptr, nullptr, nullptr));
+    LQCD_TRY(lincomb(ctx, Vh, ph, ph, &xx, {1, 0}, {1, 0}, {-1, 0}, {-1, 0}, nullptr, nullptr));
+  }
+  LQCD_CUDA(ctx, cudaMemsetAsync(xx.ptr, 0, xx.rhs_stride, ctx->stream));
   lqcd_cg_stats s1;
   std::memset(&s1, 0, sizeof(s1));
   lqcd_status s = cgls_even(ctx, U, g, kappa, mu, prm, ph, xx, b2, &s1, 1, nullptr, true);
@@ -123,6 +142,13 @@ lqcd_status solve_normal(lqcd_ctx *ctx, lqcd_gauge *U, const HalfField &phi, con
     st->reliable_updates += s1.reliable_updates;
   }
   if (s != LQCD_OK) return s;
+  if (guess) {  // X = X0 + d (in FP64)
+    DBuf d64(ctx);
+    LQCD_TRY(d64.alloc(X.rhs_stride));
+    const HalfField D = f64_half(d64.p, Vh);
+    LQCD_TRY(spinor_convert_raw(ctx, Vh, 1, xx.ptr, nullptr, outer, d64.p, nullptr, LQCD_F64));
+    return lincomb(ctx, Vh, X, X, &D, {1, 0}, {1, 0}, {1, 0}, {1, 0}, nullptr, nullptr);
+  }
   if (outer != LQCD_F64) LQCD_TRY(spinor_convert_raw(ctx, Vh, 1, xx.ptr, nullptr, outer, X.ptr, nullptr, LQCD_F64));
   return LQCD_OK;
 }
@@ -319,14 +345,14 @@ lqcd_status fermion_force_from_X(lqcd_ctx *ctx, lqcd_gauge *U, const HalfField &
 // psi and X (F64 half fields) are outputs; S2 (host) = Re psi^+ X.
 lqcd_status ratio_solve(lqcd_ctx *ctx, lqcd_gauge *U, const HalfField &phi2, const HalfField &psi,
                         const HalfField &X, double kappa, double mu, double mu2, const lqcd_cg_params &prm,
-                        lqcd_cg_stats *st, double *S2) {
+                        lqcd_cg_stats *st, double *S2, bool guess) {
   const int Vh = U->g.Vh;
   DBuf tmp(ctx);
   LQCD_TRY(tmp.alloc(spinor_half_bytes(LQCD_F64, Vh)));
   Op op{ctx, U->g, {}, LQCD_F64, U->recon, kappa, mu2};
   LQCD_TRY(gauge_view(ctx, U, LQCD_F64, U->recon, &op.U));
   LQCD_TRY(apply_schur(op, phi2, psi, f64_half(tmp.p, Vh), 0, true, nullptr, nullptr, nullptr));
-  LQCD_TRY(solve_normal(ctx, U, psi, X, kappa, mu, prm, st));
+  LQCD_TRY(solve_normal(ctx, U, psi, X, kappa, mu, prm, st, guess));
   if (S2) LQCD_TRY(half_redot(ctx, Vh, psi, X, S2));
   return LQCD_OK;
 }
@@ -363,7 +389,7 @@ extern "C" int lqcd_fermion_force_ratio(lqcd_ctx *ctx, const lqcd_gauge *Uc, lqc
   HalfField ph = f64_half(phi2.ptr, Vh), psi = f64_half(pbuf.p, Vh), X = f64_half(xbuf.p, Vh);
   lqcd_cg_stats st;
   std::memset(&st, 0, sizeof(st));
-  lqcd_status s = ratio_solve(ctx, U, ph, psi, X, kappa, mu, mu2, *params, &st, S_out);
+  lqcd_status s = ratio_solve(ctx, U, ph, psi, X, kappa, mu, mu2, *params, &st, S_out, false);
   if (stats) *stats = st;
   if (s != LQCD_OK) return s;
   return ratio_force(ctx, U, ph, X, kappa, mu, mu2, dSdw);
@@ -399,7 +425,7 @@ extern "C" int lqcd_fermion_force(lqcd_ctx *ctx, const lqcd_gauge *Uc, lqcd_fiel
   lqcd_cg_stats st;
   std::memset(&st, 0, sizeof(st));
   if (!X_cache || X_cache->reserved != 1) {
-    lqcd_status s = solve_normal(ctx, U, ph, X, kappa, mu, *params, &st);
+    lqcd_status s = solve_normal(ctx, U, ph, X, kappa, mu, *params, &st, false);
     if (stats) *stats = st;
     if (s != LQCD_OK) return s;
     if (X_cache) X_cache->reserved = 1;
@@ -474,7 +500,8 @@ extern "C" int lqcd_hmc_trajectory(lqcd_ctx *ctx, lqcd_gauge *U, const lqcd_hmc_
     if (x_version == U->version) return LQCD_OK;
     lqcd_cg_stats st;
     std::memset(&st, 0, sizeof(st));
-    LQCD_TRY(solve_normal(ctx, U, Phi, Xh, prm->kappa, mu1, prm->cg, &st));
+    // from the second solve on, the previous field's X is the starting vector
+    LQCD_TRY(solve_normal(ctx, U, Phi, Xh, prm->kappa, mu1, prm->cg, &st, x_version != 0));
     cg_iters += st.iters;
     x_version = U->version;
     return LQCD_OK;
@@ -484,7 +511,8 @@ extern "C" int lqcd_hmc_trajectory(lqcd_ctx *ctx, lqcd_gauge *U, const lqcd_hmc_
     if (x2_version == U->version) return LQCD_OK;
     lqcd_cg_stats st;
     std::memset(&st, 0, sizeof(st));
-    LQCD_TRY(ratio_solve(ctx, U, Phi2, Psi2, X2h, prm->kappa, prm->mu, prm->mu2, prm->cg, &st, &S2_cur));
+    LQCD_TRY(ratio_solve(ctx, U, Phi2, Psi2, X2h, prm->kappa, prm->mu, prm->mu2, prm->cg, &st, &S2_cur,
+                         x2_version != 0));
     cg_iters += st.iters;
     x2_version = U->version;
     return LQCD_OK;
@@ -574,7 +602,7 @@ extern "C" int lqcd_hmc_trajectory(lqcd_ctx *ctx, lqcd_gauge *U, const lqcd_hmc_
                            nullptr));
       lqcd_cg_stats st;
       std::memset(&st, 0, sizeof(st));
-      LQCD_TRY(solve_normal(ctx, U, Psi2, X2h, prm->kappa, prm->mu2, prm->cg, &st));
+      LQCD_TRY(solve_normal(ctx, U, Psi2, X2h, prm->kappa, prm->mu2, prm->cg, &st, false));
       cg_iters += st.iters;
       LQCD_TRY(apply_schur(op1, X2h, Phi2, f64_half(tmp.p, Vh), 0, false, nullptr, nullptr, nullptr));
     }
