@@ -305,10 +305,11 @@ typedef struct {
                              reliable-update residuals and of the plain solve */
   int32_t inner_prec;     /* == outer_prec: plain CG; LQCD_F32 / LQCD_BF16S /
                              LQCD_F16S: mixed precision with reliable updates */
-  double delta;           /* reliable-update trigger: ||s|| < delta * max ||s||;
-                             <= 0 selects the inner format's default: 0.5 for
-                             LQCD_BF16S (whose 8-bit recursion stalls before a
-                             tenfold drop), 0.1 otherwise */
+  double delta;           /* reliable-update trigger: ||s|| < delta * max ||s||
+                             since the last update (<= 0 selects 0.1); with a
+                             LQCD_BF16S inner format the CG also updates every
+                             8 iterations, which bounds the drift of the 8-bit
+                             recursion from the true residual */
   int32_t max_restarts;   /* outer iterative-refinement cycles on the true residual */
   int32_t check_every;    /* host polls convergence every this many iterations */
   int32_t use_graph;      /* 1: capture check_every iterations in a CUDA graph */

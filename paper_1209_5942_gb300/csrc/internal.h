@@ -144,15 +144,6 @@ int tune_choice(lqcd_ctx *ctx, const std::string &key, int ncand, int fallback,
                 const std::function<void(int)> &run);
 void tune_load(lqcd_ctx *ctx);
 
-// Reliable-update trigger used when the caller passes delta <= 0: the sloppy
-// recursion of a mixed solve is trusted until |s| falls below delta times its
-// largest value since the last update.  A BF16 recursion (8-bit significand,
-// storage error ~2^-9 per operator application) stalls long before its
-// residual falls tenfold -- on the 32^3 x 64 heatbath field it took 699
-// iterations at delta = 0.1 against 209 for FP32, 349 at 0.3 and 236 at 0.5
-// -- so BF16 updates at half the residual; FP32 and FP16 (11-bit) keep 0.1.
-inline double default_delta(int inner_prec) { return inner_prec == LQCD_BF16S ? 0.5 : 0.1; }
-
 // work counters: one launch moving `bytes` algorithmic bytes
 inline void count_launch(lqcd_ctx *ctx, double bytes) {
   ctx->cnt.launches += 1;
