@@ -119,8 +119,11 @@ int lqcd_abi_version(void);
 
 /* Creates a context on CUDA device `device` that enqueues work on
  * `cuda_stream` (a cudaStream_t; NULL = the legacy default stream).  The
- * context owns a small workspace (reduction partials, device scalars, a
- * pinned host status word) allocated here with cudaMalloc. */
+ * context owns a stream-ordered device memory pool (see "Device memory") and
+ * a small workspace (reduction partials, device scalars, a pinned host status
+ * word) allocated here.  lqcd_destroy synchronises the stream, frees the
+ * workspace and destroys the pool; memory of gauge fields not yet freed stays
+ * valid until lqcd_gauge_free (through any context of the same device). */
 int lqcd_create(lqcd_ctx **ctx, int device, void *cuda_stream);
 int lqcd_destroy(lqcd_ctx *ctx);
 int lqcd_set_stream(lqcd_ctx *ctx, void *cuda_stream);
@@ -155,7 +158,15 @@ int lqcd_reset_counters(lqcd_ctx *ctx);
 int lqcd_measure_peaks(lqcd_ctx *ctx, double *fp64_tflops, double *fp32_tflops);
 
 /* Device memory.  By default the library allocates its workspace and gauge
- * fields with cudaMallocAsync / cudaFreeAsync on the context's stream.
+ * fields from the context's own stream-ordered pool
+ * (cudaMallocFromPoolAsync / cudaFreeAsync on the context's stream).  The
+ * pool keeps memory that was freed mapped for later allocations of the
+ * context (a solver's vectors, a re-imported gauge field) instead of
+ * returning it to the driver at every synchronisation; it grows to the
+ * context's peak use.  lqcd_trim_memory synchronises the stream and returns
+ * every unused byte of the pool to the driver; lqcd_memory_stats writes the
+ * bytes the pool holds (*reserved) and the bytes in live allocations (*used),
+ * both host uint64.  NULL arguments: LQCD_ERR_INVALID.
  * lqcd_set_allocator routes every later device allocation of the context
  * (workspace, solver vectors, gauge fields imported afterwards and their
  * derived copies) through alloc(bytes, user) and free(ptr, user) instead --
@@ -171,6 +182,8 @@ int lqcd_measure_peaks(lqcd_ctx *ctx, double *fp64_tflops, double *fp32_tflops);
 typedef void *(*lqcd_alloc_fn)(size_t bytes, void *user);
 typedef void (*lqcd_free_fn)(void *ptr, void *user);
 int lqcd_set_allocator(lqcd_ctx *ctx, lqcd_alloc_fn alloc, lqcd_free_fn free_fn, void *user);
+int lqcd_trim_memory(lqcd_ctx *ctx);
+int lqcd_memory_stats(lqcd_ctx *ctx, uint64_t *reserved, uint64_t *used);
 
 /* Launch-shape autotuner (on by default).  The first launch of each kernel
  * configuration (kernel, precision, link format, variant, lattice extents,

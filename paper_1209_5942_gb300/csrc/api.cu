@@ -72,7 +72,8 @@ lqcd_status raw_alloc(lqcd_ctx *ctx, const DevAllocator &A, void **p, size_t byt
     }
     return LQCD_OK;
   }
-  cudaError_t e = cudaMallocAsync(p, bytes, ctx->stream);
+  cudaError_t e = ctx->pool ? cudaMallocFromPoolAsync(p, bytes, ctx->pool, ctx->stream)
+                            : cudaMallocAsync(p, bytes, ctx->stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
     *p = nullptr;
@@ -208,6 +209,25 @@ extern "C" int lqcd_create(lqcd_ctx **out, int device, void *stream) {
     c->tune_path = tp;
     tune_load(c);
   }
+  {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    if (cudaMemPoolCreate(&c->pool, &props) != cudaSuccess) {
+      cudaGetLastError();
+      c->pool = nullptr;
+      lqcd_destroy(c);
+      return LQCD_ERR_CUDA;
+    }
+    uint64_t keep = UINT64_MAX;
+    if (cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess) {
+      cudaGetLastError();
+      lqcd_destroy(c);
+      return LQCD_ERR_CUDA;
+    }
+  }
   if (ensure_partials(c, 1 << 16) != LQCD_OK || ensure_pinned(c, 4096) != LQCD_OK) {
     lqcd_destroy(c);
     return LQCD_ERR_OOM;
@@ -235,7 +255,27 @@ extern "C" int lqcd_destroy(lqcd_ctx *ctx) {
   if (!ctx) return LQCD_ERR_INVALID;
   release_workspace(ctx);
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
+  // allocations still outstanding (gauge fields not yet freed) keep the
+  // pool's memory alive until they are freed
+  if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
   delete ctx;
+  return LQCD_OK;
+}
+
+extern "C" int lqcd_trim_memory(lqcd_ctx *ctx) {
+  if (!ctx) return LQCD_ERR_INVALID;
+  if (!ctx->pool) return LQCD_OK;
+  LQCD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  LQCD_CUDA(ctx, cudaMemPoolTrimTo(ctx->pool, 0));
+  return LQCD_OK;
+}
+
+extern "C" int lqcd_memory_stats(lqcd_ctx *ctx, uint64_t *reserved, uint64_t *used) {
+  if (!ctx || !reserved || !used) return LQCD_ERR_INVALID;
+  *reserved = *used = 0;
+  if (!ctx->pool) return LQCD_OK;
+  LQCD_CUDA(ctx, cudaMemPoolGetAttribute(ctx->pool, cudaMemPoolAttrReservedMemCurrent, reserved));
+  LQCD_CUDA(ctx, cudaMemPoolGetAttribute(ctx->pool, cudaMemPoolAttrUsedMemCurrent, used));
   return LQCD_OK;
 }
 

@@ -14,6 +14,7 @@
 // per system (fixed-order sums) with the last block deciding convergence and
 // reliable-update triggers for the batch.
 #include <chrono>
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -25,7 +26,8 @@ namespace lqcd {
 // solver state of one system (same meaning as in cg.cu)
 struct BState {
   double zz, qq, ss, alpha, beta, stop2, rel2, rmax2;
-  int done, iters, need_rel, pad;
+  int done, iters, need_rel;
+  int since, gap;  // iterations since the last reliable update, and its cap
 };
 struct BHdr {
   int halt, all_done, need_rel, nonfinite;
@@ -62,7 +64,8 @@ __global__ void __launch_bounds__(FIN_THREADS) bfinalize_kernel(BHdr *h, const d
           if (x <= R.stop2) R.done = 1;
           if (h->mixed && !R.done) {
             if (x > R.rmax2) R.rmax2 = x;
-            if (x < R.rel2 * R.rmax2) R.need_rel = 1;
+            R.since += 1;
+            if (x < R.rel2 * R.rmax2 || R.since >= R.gap) R.need_rel = 1;
           }
         }
         break;
@@ -156,7 +159,7 @@ __global__ void __launch_bounds__(128) bp_kernel(BHdr *h, const VecDesc *d, cons
   }
 }
 
-__global__ void bstate_init_kernel(BHdr *h, int nsys, int mixed, const double *stop2, double rel) {
+__global__ void bstate_init_kernel(BHdr *h, int nsys, int mixed, const double *stop2, double rel, int gap) {
   for (int k = threadIdx.x; k < nsys; k += blockDim.x) {
     BState &R = bstate(h)[k];
     R.zz = R.qq = R.ss = R.alpha = R.beta = 0.0;
@@ -166,6 +169,8 @@ __global__ void bstate_init_kernel(BHdr *h, int nsys, int mixed, const double *s
     R.done = 0;
     R.iters = 0;
     R.need_rel = 0;
+    R.since = 0;
+    R.gap = gap;
   }
   if (threadIdx.x == 0) {
     h->halt = h->all_done = h->need_rel = h->nonfinite = 0;
@@ -182,6 +187,7 @@ __global__ void bstate_after_reliable_kernel(BHdr *h, const double *ss2) {
     BState &R = bstate(h)[k];
     R.need_rel = 0;
     R.rmax2 = ss2[k];
+    R.since = 0;
     R.ss = ss2[k];
     if (ss2[k] > R.stop2) R.done = 0;
   }
@@ -499,7 +505,8 @@ lqcd_status cg_solve_batch_impl(lqcd_ctx *ctx, int n, lqcd_gauge *const *U, cons
     for (int k = 0; k < n; k++) ctx->pinned[k] = stop2[k];
     LQCD_CUDA(ctx, cudaMemcpyAsync(stopd.p, ctx->pinned, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream));
     bstate_init_kernel<<<1, 256, 0, ctx->stream>>>(h, n, mixed ? 1 : 0, (const double *)stopd.p,
-                                                   prm.delta > 0 ? prm.delta : 0.1);
+                                                   prm.delta > 0 ? prm.delta : 0.1,
+                                                   mixed && inner == LQCD_BF16S ? kBf16Gap : INT_MAX);
     count_launch(ctx, 0.0);
     // z = Mhat^+ s; zz; p = z
     LQCD_TRY(stage(2, true, false, nullptr));

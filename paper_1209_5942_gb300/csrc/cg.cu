@@ -60,14 +60,6 @@ LQCD_DEV RhsState *rhs_state(SolverHdr *h) { return (RhsState *)(h + 1); }
 // unless the step halted the solve) FIN_BETA on the same sums -- the
 // normal-equation iteration reduces one vector for both
 enum { FIN_ALPHA = 0, FIN_SS = 1, FIN_BETA = 2, FIN_INIT_ZZ = 3, FIN_STORE = 4, FIN_SS_BETA = 5 };
-// A BF16 recursion (8-bit significand, storage error ~2^-9 per operator
-// application) drifts from the true residual while its own |s| keeps
-// falling: on the 32^3 x 64 heatbath field it took 699 iterations at
-// delta = 0.1 against 209 for FP32, and a trigger on the stagnation of |s|
-// did not help, because |s| does not stagnate.  What bounds the drift is the
-// number of iterations between updates, so BF16 inner solves also update
-// after kBf16Gap iterations; other formats update only by delta.
-constexpr int kBf16Gap = 8;
 
 // One block per right-hand side finishes its reduction and applies the CG
 // scalar step `op`; the last block to finish (ticket) sets the flags over all

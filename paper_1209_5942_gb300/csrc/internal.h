@@ -13,7 +13,8 @@
 #include "../../include/lqcd.h"
 #include "common.cuh"
 
-// caller-provided device allocator (lqcd_set_allocator); NULL: cudaMallocAsync
+// caller-provided device allocator (lqcd_set_allocator); NULL: the context's
+// stream-ordered memory pool
 struct DevAllocator {
   lqcd_alloc_fn alloc = nullptr;
   lqcd_free_fn free = nullptr;
@@ -25,6 +26,12 @@ struct lqcd_ctx {
   cudaStream_t stream = nullptr;
   int num_sms = 152;
   DevAllocator A;
+  // Stream-ordered pool of the default allocator.  Its release threshold is
+  // unlimited: memory freed by one solve stays mapped for the next instead
+  // of going back to the driver at every synchronisation (which the device's
+  // default pool does, and which cost ~2 ms of page mapping per 24^3 x 48
+  // solve).  lqcd_trim_memory returns it; lqcd_destroy destroys the pool.
+  cudaMemPool_t pool = nullptr;
   std::string err;
   // reduction workspace: partial sums [slots][nblocks] and per-slot results
   double *partials = nullptr;
@@ -143,6 +150,16 @@ void hop_args_fill(const Geom &g, const HopLaunch &L, void *dst);
 int tune_choice(lqcd_ctx *ctx, const std::string &key, int ncand, int fallback,
                 const std::function<void(int)> &run);
 void tune_load(lqcd_ctx *ctx);
+
+// A BF16 recursion (8-bit significand, storage error ~2^-9 per operator
+// application) drifts from the true residual while its own |s| keeps
+// falling: on the 32^3 x 64 heatbath field it took 699 iterations at
+// delta = 0.1 against 209 for FP32, and a trigger on the stagnation of |s|
+// did not help, because |s| does not stagnate.  What bounds the drift is the
+// number of iterations between updates, so BF16 inner solves also update
+// after kBf16Gap iterations; other formats update only by delta.  Both CG
+// drivers (single and batched systems) use this gap.
+constexpr int kBf16Gap = 8;
 
 // work counters: one launch moving `bytes` algorithmic bytes
 inline void count_launch(lqcd_ctx *ctx, double bytes) {

@@ -116,6 +116,8 @@ SIGNATURES = [
     ("lqcd_set_allocator", _i, [_vp, _ALLOC_FN, _FREE_FN, _vp]),
     ("lqcd_reset_counters", _i, [_vp]),
     ("lqcd_measure_peaks", _i, [_vp, ctypes.POINTER(_d), ctypes.POINTER(_d)]),
+    ("lqcd_trim_memory", _i, [_vp]),
+    ("lqcd_memory_stats", _i, [_vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
     ("lqcd_field_bytes", ctypes.c_size_t, [ctypes.POINTER(lqcd_geom), _i, _i, _i,
                                            ctypes.POINTER(ctypes.c_size_t)]),
     ("lqcd_gauge_import", _i, [_vp, _vp, ctypes.POINTER(lqcd_geom), _i, ctypes.POINTER(_vp)]),
@@ -344,6 +346,18 @@ def lqcd_measure_peaks(ctx: Context) -> tuple[float, float]:
     a, b = _d(0.0), _d(0.0)
     ctx.check(lib().lqcd_measure_peaks(ctx.handle, ctypes.byref(a), ctypes.byref(b)))
     return a.value, b.value
+
+
+def lqcd_trim_memory(ctx: Context) -> None:
+    """Returns the unused memory of the context's pool to the driver."""
+    ctx.check(lib().lqcd_trim_memory(ctx.handle))
+
+
+def lqcd_memory_stats(ctx: Context) -> tuple[int, int]:
+    """(bytes the context's pool holds, bytes in live allocations)."""
+    r, u = ctypes.c_uint64(0), ctypes.c_uint64(0)
+    ctx.check(lib().lqcd_memory_stats(ctx.handle, ctypes.byref(r), ctypes.byref(u)))
+    return r.value, u.value
 
 
 def lqcd_set_allocator(ctx: Context, alloc_fn=None, free_fn=None):

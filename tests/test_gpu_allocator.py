@@ -59,3 +59,33 @@ def test_allocator_pair_must_be_complete():
     assert e.value.status == lqcd.LQCD_ERR_INVALID
     lqcd.lqcd_set_allocator(ctx, None, None)  # back to the default
     ctx.close()
+
+
+def test_context_pool_keeps_and_trims_memory():
+    """The default allocator: the context's pool keeps freed memory mapped for
+    the next import (its reserved bytes do not drop when a gauge field is
+    freed), serves the re-import from it, and lqcd_trim_memory returns what
+    no live allocation uses (a 16^4 field: 38 MB of links, more than one
+    chunk of the pool beside the workspace)."""
+    L = (16, 16, 16, 16)
+    V = inputs.volume(L)
+    U_d = dev(inputs.random_gauge(L, "near", seed=1203, eps=0.4))
+    ctx = lqcd.Context(0)
+    r0, u0 = lqcd.lqcd_memory_stats(ctx)
+    assert u0 > 0 and r0 >= u0  # the workspace
+    G = lqcd.lqcd_gauge_import(ctx, U_d, L)
+    torch.cuda.synchronize()
+    r1, u1 = lqcd.lqcd_memory_stats(ctx)
+    assert u1 >= u0 + 576 * V and r1 >= u1  # FP64 master links
+    G.free()
+    torch.cuda.synchronize()
+    r2, u2 = lqcd.lqcd_memory_stats(ctx)
+    assert u2 == u0 and r2 == r1  # freed, still held
+    G = lqcd.lqcd_gauge_import(ctx, U_d, L)
+    torch.cuda.synchronize()
+    assert lqcd.lqcd_memory_stats(ctx)[0] == r1  # served from the pool
+    G.free()
+    lqcd.lqcd_trim_memory(ctx)
+    r3, u3 = lqcd.lqcd_memory_stats(ctx)
+    assert u3 == u0 and r3 < r1
+    ctx.close()
