@@ -948,6 +948,33 @@ def run_config(args):
         config_line("multi-RHS hop", None, {"hop": res},
                     {"workload": "F32 half hop, 12 right-hand sides vs one, 24^3x48 and 32^3x64, "
                                  "exp(i 0.3 H) links"})
+    elif c == "mrhs":
+        # the default line's 12-RHS solve alone (24^3 x 48 bench field, 12 point
+        # sources, float-float outer / FP32 inner): one warm-up solve, then one
+        # solve inside the NVTX range "mrhs_solve" and one 12-RHS half hop
+        U = torch.from_numpy(make_inputs()[0]).cuda()
+        G = lqcd.lqcd_gauge_import(ctx, U, L, recon=18)
+        b12 = inputs.point_sources(L)
+        prm = lqcd.cg_params(tol=TOL, outer_prec=lqcd.LQCD_DF64, inner_prec=lqcd.LQCD_F32, max_iter=50000,
+                             sloppy_recon=12, check_every=20)
+        bd, _ = lqcd.alloc_field(L, lqcd.LQCD_FULL, lqcd.LQCD_F64, 12)
+        xd, _ = lqcd.alloc_field(L, lqcd.LQCD_FULL, lqcd.LQCD_F64, 12)
+        fb = lqcd.field(bd, lqcd.LQCD_LAYOUT_EO, nrhs=12)
+        fx = lqcd.field(xd, lqcd.LQCD_LAYOUT_EO, nrhs=12)
+        lqcd.lqcd_spinor_pack(ctx, L, torch.from_numpy(b12).cuda(), fb)
+        lqcd.lqcd_cg_solve(ctx, G, fb, fx, KAPPA, MU, prm)
+        lqcd.lib().lqcd_reset_counters(ctx.handle)
+        nvtx_push("mrhs_solve")
+        t, st = _timed(torch, lambda: lqcd.lqcd_cg_solve(ctx, G, fb, fx, KAPPA, MU, prm))
+        nvtx_pop()
+        cnt = lqcd.lqcd_counters()
+        lqcd.lib().lqcd_get_counters(ctx.handle, ctypes_byref(cnt))
+        config_line("12-RHS solve", None,
+                    {"solve_s": t, "iters_max": max(s["iters"] for s in st),
+                     "reliable_updates": max(s["reliable_updates"] for s in st),
+                     "true_resid_max": max(s["true_resid"] for s in st), "launches": int(cnt.launches)},
+                    {"workload": "24^3x48 exp(i 0.3 H) links, 12 point sources, DF64 outer / F32 inner, "
+                                 "REC12 sloppy links, 1e-10"})
     elif c == "sweep":
         res = {}
         for ns in (16, 24, 32, 48):
@@ -1026,7 +1053,7 @@ def main():
     ap.add_argument("--variants", action="store_true", help="also BiCGStab variants")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the precision variants and the 12-RHS comparison")
-    ap.add_argument("--config", default="2", choices=["1", "2", "3", "4a", "4b", "5", "C", "hb", "sweep", "hop12"],
+    ap.add_argument("--config", default="2", choices=["1", "2", "3", "4a", "4b", "5", "C", "hb", "sweep", "hop12", "mrhs"],
                     help="2 (default): the 24^3x48 contract line; others print their own line")
     ap.add_argument("--sweeps", type=int, default=200, help="heatbath sweeps for configs 3, 4a, 5")
     ap.add_argument("--trajs", type=int, default=10, help="measured HMC trajectories for config 5")

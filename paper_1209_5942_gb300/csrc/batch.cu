@@ -33,6 +33,7 @@ struct BHdr {
   int halt, all_done, need_rel, nonfinite;
   int iters, nsys, mixed;
   unsigned int ticket;
+  int loops, pad;  // pass counter of the graph's device-side loop
 };
 LQCD_DEV BState *bstate(BHdr *h) { return (BState *)(h + 1); }
 
@@ -178,6 +179,7 @@ __global__ void bstate_init_kernel(BHdr *h, int nsys, int mixed, const double *s
     h->nsys = nsys;
     h->mixed = mixed;
     h->ticket = 0u;
+    h->loops = 0;
   }
 }
 
@@ -517,7 +519,9 @@ lqcd_status cg_solve_batch_impl(lqcd_ctx *ctx, int n, lqcd_gauge *const *U, cons
     for (int k = 0; k < n; k++)
       LQCD_TRY(lincomb(ctx, S[k].Vh, S[k].p, S[k].z, nullptr, one, one, zero, zero, nullptr, nullptr));
 
+    IterWork work;
     auto iteration = [&]() -> lqcd_status {
+      const lqcd_counters c0 = ctx->cnt;
       LQCD_TRY(stage(0, false, false, &h->halt));
       count_hop(false, false);
       LQCD_TRY(stage(1, false, true, &h->halt));
@@ -528,6 +532,7 @@ lqcd_status cg_solve_batch_impl(lqcd_ctx *ctx, int n, lqcd_gauge *const *U, cons
       }));
       count_launch(ctx, sites_total * sbi * 6.0);
       fin(BF_SS);
+      const lqcd_counters cmid = ctx->cnt;  // a halted iteration stops here
       LQCD_TRY(stage(2, true, false, &h->halt));
       count_hop(false, false);
       LQCD_TRY(stage(3, true, true, &h->halt));
@@ -537,71 +542,38 @@ lqcd_status cg_solve_batch_impl(lqcd_ctx *ctx, int n, lqcd_gauge *const *U, cons
         bp_kernel<decltype(P)::value><<<grid, 128, 0, ctx->stream>>>(h, d_vdesc, d_tiles, ntiles);
       }));
       count_launch(ctx, sites_total * sbi * 3.0);
+      if (!work.known) {
+        work.full = cnt_sub(ctx->cnt, c0);
+        work.first = cnt_sub(cmid, c0);
+        work.known = true;
+      }
       return LQCD_OK;
     };
 
     const int chunk = prm.check_every > 0 ? prm.check_every : 10;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t gexec = nullptr;
-    lqcd_counters before = ctx->cnt, delta{};
-    if (prm.use_graph) {
-      cudaStream_t cap;
-      LQCD_CUDA(ctx, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
-      cudaStream_t saved = ctx->stream;
-      ctx->stream = cap;
-      lqcd_status cs = LQCD_OK;
-      cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
-      if (e == cudaSuccess) {
-        for (int i = 0; i < chunk && cs == LQCD_OK; i++) cs = iteration();
-        e = cudaStreamEndCapture(cap, &graph);
-      }
-      ctx->stream = saved;
-      cudaStreamDestroy(cap);
-      delta.launches = ctx->cnt.launches - before.launches;
-      delta.hop_launches = ctx->cnt.hop_launches - before.hop_launches;
-      delta.bytes = ctx->cnt.bytes - before.bytes;
-      delta.hop_bytes = ctx->cnt.hop_bytes - before.hop_bytes;
-      delta.hop_flops = ctx->cnt.hop_flops - before.hop_flops;
-      delta.hop_sites = ctx->cnt.hop_sites - before.hop_sites;
-      ctx->cnt = before;
-      if (e != cudaSuccess) return cuda_check(ctx, e, "batched graph capture");
-      if (cs != LQCD_OK) {
-        cudaGraphDestroy(graph);
-        return cs;
-      }
-      e = cudaGraphInstantiate(&gexec, graph, 0);
-      if (e != cudaSuccess) {
-        cudaGraphDestroy(graph);
-        return cuda_check(ctx, e, "batched graph instantiate");
-      }
-    }
-    struct G {
-      cudaGraph_t &g;
-      cudaGraphExec_t &e;
-      ~G() {
-        if (e) cudaGraphExecDestroy(e);
-        if (g) cudaGraphDestroy(g);
-      }
-    } gg{graph, gexec};
+    SolverGraph graph;
+    if (prm.use_graph) LQCD_TRY(build_solver_graph(ctx, chunk, &h->halt, &h->loops, iteration, &graph));
 
     BHdr hh;
     int reliable = 0, last_rel_iter = 0;
     std::vector<BState> bs(n);
+    int iters_seen = 0;  // h->iters at the last poll
     for (;;) {
-      if (gexec) {
-        LQCD_CUDA(ctx, cudaGraphLaunch(gexec, ctx->stream));
-        ctx->cnt.launches += delta.launches;
-        ctx->cnt.hop_launches += delta.hop_launches;
-        ctx->cnt.bytes += delta.bytes;
-        ctx->cnt.hop_bytes += delta.hop_bytes;
-        ctx->cnt.hop_flops += delta.hop_flops;
-        ctx->cnt.hop_sites += delta.hop_sites;
+      lqcd_counters chunk_launches{};
+      if (graph.exec) {
+        LQCD_CUDA(ctx, cudaGraphLaunch(graph.exec, ctx->stream));
       } else {
+        const lqcd_counters c0 = ctx->cnt;
         for (int i = 0; i < chunk; i++) LQCD_TRY(iteration());
+        chunk_launches = cnt_sub(ctx->cnt, c0);
+        ctx->cnt = c0;
       }
       LQCD_CUDA(ctx, cudaMemcpyAsync(ctx->pinned, h, sizeof(BHdr), cudaMemcpyDeviceToHost, ctx->stream));
       LQCD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
       std::memcpy(&hh, ctx->pinned, sizeof(hh));
+      if (graph.exec) chunk_launches = graph.launches(hh.iters - iters_seen);
+      count_chunk(ctx, work, chunk_launches, hh.iters - iters_seen, hh.halt != 0);
+      iters_seen = hh.iters;
       if (hh.nonfinite) return fail(ctx, LQCD_ERR_NONFINITE, "batched CG: non-finite scalar");
       const bool finished = hh.all_done != 0;
       // stalled low-precision recursion: force a reliable update and restart p

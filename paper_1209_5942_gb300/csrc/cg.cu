@@ -52,6 +52,7 @@ struct SolverHdr {
   int halt, all_done, need_rel, nonfinite;
   int iters, nrhs, mixed;
   unsigned ticket;  // blocks of the current finalize that have finished
+  int loops, pad;   // pass counter of the graph's device-side loop
 };
 // layout in device memory: SolverHdr, then RhsState[nrhs]
 LQCD_DEV RhsState *rhs_state(SolverHdr *h) { return (RhsState *)(h + 1); }
@@ -148,6 +149,107 @@ static void launch_finalize(lqcd_ctx *ctx, SolverHdr *h, int nrhs, int nb, int o
   launch_pdl(finalize_kernel, dim3(nrhs), dim3(FIN_THREADS), 0, ctx->stream, h, nrhs, (const double *)ctx->partials,
              nb, op, out);
   count_launch(ctx, 8.0 * nb * nrhs);
+}
+
+// Last kernel of a loop pass: ends the while loop once the solver halted or
+// after `cap` passes (the pass counter goes back to zero for the next launch).
+__global__ void loop_ctl_kernel(const int *halt, int *loops, cudaGraphConditionalHandle cond, int cap) {
+  const int n = *loops + 1;
+  if (*(volatile const int *)halt || n >= cap) {
+    *loops = 0;
+    cudaGraphSetConditional(cond, 0);
+  } else {
+    *loops = n;
+  }
+}
+
+// The device-side loop: a graph with one conditional while node (condition
+// 1 at every launch) whose body is captured from one iteration and the
+// control kernel.  Returns false (and leaves nothing behind) if the driver
+// rejects any step; *cs receives a failure of the iteration itself.
+static bool build_loop_graph(lqcd_ctx *ctx, cudaStream_t cap, int chunk, const int *halt, int *loops,
+                             const std::function<lqcd_status()> &iteration, SolverGraph *G, lqcd_status *cs) {
+  cudaGraph_t g = nullptr;
+  cudaGraphConditionalHandle cond;
+  bool ok = cudaGraphCreate(&g, 0) == cudaSuccess &&
+            cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+  // zero-filled storage: the parameter union has no default constructor and
+  // its unused bytes must be zero
+  alignas(cudaGraphNodeParams) unsigned char np_bytes[sizeof(cudaGraphNodeParams)] = {};
+  cudaGraphNodeParams &np = *reinterpret_cast<cudaGraphNodeParams *>(np_bytes);
+  if (ok) {
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = cond;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    ok = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np) == cudaSuccess;
+  }
+  if (ok) {
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    ok = cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
+         cudaSuccess;
+    if (ok) {
+      cudaStream_t saved = ctx->stream;
+      ctx->stream = cap;
+      *cs = iteration();
+      if (*cs == LQCD_OK) {
+        loop_ctl_kernel<<<1, 1, 0, cap>>>(halt, loops, cond, chunk);
+        count_launch(ctx, 0.0);
+      }
+      ctx->stream = saved;
+      cudaGraph_t out = body;
+      ok = cudaStreamEndCapture(cap, &out) == cudaSuccess && *cs == LQCD_OK;
+    }
+  }
+  if (ok) ok = cudaGraphInstantiate(&G->exec, g, 0) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    G->exec = nullptr;
+    if (g) cudaGraphDestroy(g);
+    return false;
+  }
+  G->graph = g;
+  G->loop = true;
+  return true;
+}
+
+lqcd_status build_solver_graph(lqcd_ctx *ctx, int chunk, const int *halt, int *loops,
+                               const std::function<lqcd_status()> &iteration, SolverGraph *G) {
+  cudaStream_t cap;
+  LQCD_CUDA(ctx, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+  const lqcd_counters before = ctx->cnt;
+  lqcd_status cs = LQCD_OK;
+  bool ok = build_loop_graph(ctx, cap, chunk, halt, loops, iteration, G, &cs);
+  if (!ok) {
+    // unrolled chunk of iterations
+    ctx->cnt = before;
+    cs = LQCD_OK;
+    cudaGraph_t g = nullptr;
+    cudaStream_t saved = ctx->stream;
+    ctx->stream = cap;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      for (int k = 0; k < chunk && cs == LQCD_OK; k++) cs = iteration();
+      e = cudaStreamEndCapture(cap, &g);
+    }
+    ctx->stream = saved;
+    if (e == cudaSuccess && cs == LQCD_OK) e = cudaGraphInstantiate(&G->exec, g, 0);
+    if (e != cudaSuccess || cs != LQCD_OK) {
+      G->exec = nullptr;
+      if (g) cudaGraphDestroy(g);
+      ctx->cnt = before;
+      cudaStreamDestroy(cap);
+      if (cs != LQCD_OK) return cs;
+      return cuda_check(ctx, e, "solver graph capture");
+    }
+    G->graph = g;
+  }
+  // the capture executed nothing: its launch counts are the per-pass increment
+  G->per_pass = cnt_sub(ctx->cnt, before);
+  ctx->cnt = before;
+  cudaStreamDestroy(cap);
+  return LQCD_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -300,6 +402,7 @@ __global__ void state_init_kernel(SolverHdr *h, int nrhs, int mixed, const doubl
     h->nrhs = nrhs;
     h->mixed = mixed;
     h->ticket = 0u;
+    h->loops = 0;
   }
   if (r < nrhs) {
     RhsState &R = rhs_state(h)[r];
@@ -603,7 +706,10 @@ lqcd_status cgls_even(lqcd_ctx *ctx, lqcd_gauge *U, const Geom &g, double kappa,
 
   VecArgs va = vargs(s.f, Vh);
   dim3 vgrid(nbv, nrhs);
+  IterWork work;
   auto iteration = [&]() -> lqcd_status {
+    const lqcd_counters c0 = ctx->cnt;
+    lqcd_counters cmid{};
     LQCD_TRY(apply_schur(Oi, p.f, q.f, t.f, 0, false, ctx->partials, &nb, &h->halt));
     launch_finalize(ctx, h, nrhs, nb, FIN_ALPHA, nullptr);
     if (!normal) {
@@ -615,6 +721,7 @@ lqcd_status cgls_even(lqcd_ctx *ctx, lqcd_gauge *U, const Geom &g, double kappa,
             ctx->partials);
       }));
       launch_finalize(ctx, h, nrhs, nbw, FIN_SS, nullptr);
+      cmid = ctx->cnt;  // a halted iteration stops here
       LQCD_TRY(apply_schur(Oi, s.f, z.f, t.f, 0, true, ctx->partials, &nb, &h->halt));
       launch_finalize(ctx, h, nrhs, nb, FIN_BETA, nullptr);
     } else {
@@ -627,6 +734,7 @@ lqcd_status cgls_even(lqcd_ctx *ctx, lqcd_gauge *U, const Geom &g, double kappa,
             ctx->partials);
       }));
       launch_finalize(ctx, h, nrhs, nbw, FIN_SS_BETA, nullptr);
+      cmid = ctx->cnt;  // a halted iteration stops here
     }
     count_launch(ctx, (double)Vh * nrhs * spinor_site_bytes(inner) * 3.0);
     LQCD_TRY(dispatch_prec(ctx, inner, [&](auto P) {
@@ -634,51 +742,17 @@ lqcd_status cgls_even(lqcd_ctx *ctx, lqcd_gauge *U, const Geom &g, double kappa,
                  z.f.ptr, z.f.scale);
     }));
     LQCD_CUDA(ctx, cudaGetLastError());
+    if (!work.known) {
+      work.full = cnt_sub(ctx->cnt, c0);
+      work.first = cnt_sub(cmid, c0);
+      work.known = true;
+    }
     return LQCD_OK;
   };
 
   const int chunk = prm.check_every > 0 ? prm.check_every : 10;
-  cudaGraphExec_t gexec = nullptr;
-  cudaGraph_t graph = nullptr;
-  lqcd_counters cnt_before{}, chunk_cnt{};
-  if (prm.use_graph) {
-    cudaStream_t cap;
-    LQCD_CUDA(ctx, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
-    cudaStream_t saved = ctx->stream;
-    ctx->stream = cap;
-    cnt_before = ctx->cnt;
-    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
-    lqcd_status cs = LQCD_OK;
-    if (e == cudaSuccess) {
-      for (int k = 0; k < chunk && cs == LQCD_OK; k++) cs = iteration();
-      e = cudaStreamEndCapture(cap, &graph);
-    }
-    ctx->stream = saved;
-    cudaStreamDestroy(cap);
-    // the capture executed nothing: keep its counts as the per-replay increment
-    chunk_cnt.launches = ctx->cnt.launches - cnt_before.launches;
-    chunk_cnt.hop_launches = ctx->cnt.hop_launches - cnt_before.hop_launches;
-    chunk_cnt.bytes = ctx->cnt.bytes - cnt_before.bytes;
-    chunk_cnt.hop_bytes = ctx->cnt.hop_bytes - cnt_before.hop_bytes;
-    chunk_cnt.hop_flops = ctx->cnt.hop_flops - cnt_before.hop_flops;
-    chunk_cnt.hop_sites = ctx->cnt.hop_sites - cnt_before.hop_sites;
-    ctx->cnt = cnt_before;
-    if (e != cudaSuccess) return cuda_check(ctx, e, "graph capture");
-    if (cs != LQCD_OK) return cs;
-    e = cudaGraphInstantiate(&gexec, graph, 0);
-    if (e != cudaSuccess) {
-      cudaGraphDestroy(graph);
-      return cuda_check(ctx, e, "graph instantiate");
-    }
-  }
-  struct GraphGuard {
-    cudaGraphExec_t &e;
-    cudaGraph_t &g;
-    ~GraphGuard() {
-      if (e) cudaGraphExecDestroy(e);
-      if (g) cudaGraphDestroy(g);
-    }
-  } guard{gexec, graph};
+  SolverGraph graph;
+  if (prm.use_graph) LQCD_TRY(build_solver_graph(ctx, chunk, &h->halt, &h->loops, iteration, &graph));
 
   SolverHdr hh;
   int reliable = 0;
@@ -686,21 +760,23 @@ lqcd_status cgls_even(lqcd_ctx *ctx, lqcd_gauge *U, const Geom &g, double kappa,
   const int kStallIters = 200;
   lqcd_status result = LQCD_OK;
   std::vector<double> ss2;
+  int iters_seen = 0;  // h->iters at the last poll
   for (;;) {
-    if (gexec) {
-      LQCD_CUDA(ctx, cudaGraphLaunch(gexec, ctx->stream));
-      ctx->cnt.launches += chunk_cnt.launches;
-      ctx->cnt.hop_launches += chunk_cnt.hop_launches;
-      ctx->cnt.bytes += chunk_cnt.bytes;
-      ctx->cnt.hop_bytes += chunk_cnt.hop_bytes;
-      ctx->cnt.hop_flops += chunk_cnt.hop_flops;
-      ctx->cnt.hop_sites += chunk_cnt.hop_sites;
+    lqcd_counters chunk_launches{};
+    if (graph.exec) {
+      LQCD_CUDA(ctx, cudaGraphLaunch(graph.exec, ctx->stream));
     } else {
+      const lqcd_counters c0 = ctx->cnt;
       for (int k = 0; k < chunk; k++) LQCD_TRY(iteration());
+      chunk_launches = cnt_sub(ctx->cnt, c0);
+      ctx->cnt = c0;
     }
     LQCD_CUDA(ctx, cudaMemcpyAsync(ctx->pinned, h, sizeof(SolverHdr), cudaMemcpyDeviceToHost, ctx->stream));
     LQCD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     std::memcpy(&hh, ctx->pinned, sizeof(hh));
+    if (graph.exec) chunk_launches = graph.launches(hh.iters - iters_seen);
+    count_chunk(ctx, work, chunk_launches, hh.iters - iters_seen, hh.halt != 0);
+    iters_seen = hh.iters;
     if (hh.nonfinite) {
       result = fail(ctx, LQCD_ERR_NONFINITE, "CG: non-finite or breakdown scalar after %d iterations", hh.iters);
       break;
@@ -841,7 +917,8 @@ LQCD_HD double zabs2(Zd a) { return a.re * a.re + a.im * a.im; }
 struct BiState {
   Zd rho, rho_new, alpha, omega, beta;
   double rr, rr0, stop2;
-  int it, first, halt, done, nonconv, bad, max_iter, pad;
+  int it, first, halt, done, nonconv, bad, max_iter;
+  int loops;  // pass counter of the graph's device-side loop
 };
 enum { BI_RV = 0, BI_OMEGA = 1, BI_RHO = 2 };
 
@@ -1066,7 +1143,9 @@ lqcd_status bicgstab_even(lqcd_ctx *ctx, lqcd_gauge *U, const Geom &g, double ka
   hs.done = hs.halt;
   std::memcpy(ctx->pinned, &hs, sizeof(hs));
   LQCD_CUDA(ctx, cudaMemcpyAsync(S, ctx->pinned, sizeof(hs), cudaMemcpyHostToDevice, cst));
+  IterWork work;  // BiCGStab halts at the end of an iteration (or on a breakdown)
   auto iteration = [&]() -> lqcd_status {
+    const lqcd_counters c0 = ctx->cnt;
     LQCD_TRY(dispatch_prec(ctx, P, [&](auto PP) {  // p = r (+ beta (p - omega v))
       launch_pdl(bicg_vec_kernel<decltype(PP)::value, 0>, vgrid, dim3(128), 0, ctx->stream, Vh, (const BiState *)S,
                  p.f.ptr, p.f.scale, (void *)nullptr, (float *)nullptr, (const void *)r.f.ptr,
@@ -1095,68 +1174,40 @@ lqcd_status bicgstab_even(lqcd_ctx *ctx, lqcd_gauge *U, const Geom &g, double ka
     }));
     count_launch(ctx, (double)Vh * 6.0 * spinor_site_bytes(P));
     LQCD_TRY(dot(r0.f, r.f, S));
-    return fin(BI_RHO);
+    LQCD_TRY(fin(BI_RHO));
+    if (!work.known) {
+      work.full = work.first = cnt_sub(ctx->cnt, c0);
+      work.known = true;
+    }
+    return LQCD_OK;
   };
   const int chunk = prm.check_every > 0 ? prm.check_every : 10;
-  cudaGraphExec_t gexec = nullptr;
-  cudaGraph_t graph = nullptr;
-  lqcd_counters chunk_cnt{};
+  SolverGraph graph;
   if (prm.use_graph) {
     // one operator application outside the capture, so the autotuner times
     // the hop configurations the captured iterations launch (v is
     // overwritten before it is read)
     LQCD_TRY(apply_schur(Oi, r.f, v.f, tmp.f, 0, false, nullptr, nullptr, nullptr));
-    cudaStream_t cap;
-    LQCD_CUDA(ctx, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
-    ctx->stream = cap;
-    const lqcd_counters before = ctx->cnt;
-    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
-    lqcd_status cs = LQCD_OK;
-    if (e == cudaSuccess) {
-      for (int k = 0; k < chunk && cs == LQCD_OK; k++) cs = iteration();
-      e = cudaStreamEndCapture(cap, &graph);
-    }
-    ctx->stream = cst;
-    cudaStreamDestroy(cap);
-    chunk_cnt.launches = ctx->cnt.launches - before.launches;
-    chunk_cnt.hop_launches = ctx->cnt.hop_launches - before.hop_launches;
-    chunk_cnt.bytes = ctx->cnt.bytes - before.bytes;
-    chunk_cnt.hop_bytes = ctx->cnt.hop_bytes - before.hop_bytes;
-    chunk_cnt.hop_flops = ctx->cnt.hop_flops - before.hop_flops;
-    chunk_cnt.hop_sites = ctx->cnt.hop_sites - before.hop_sites;
-    ctx->cnt = before;
-    if (e != cudaSuccess) return cuda_check(ctx, e, "graph capture");
-    if (cs != LQCD_OK) return cs;
-    e = cudaGraphInstantiate(&gexec, graph, 0);
-    if (e != cudaSuccess) {
-      cudaGraphDestroy(graph);
-      return cuda_check(ctx, e, "graph instantiate");
-    }
+    LQCD_TRY(build_solver_graph(ctx, chunk, &S->halt, &S->loops, iteration, &graph));
   }
-  struct GraphGuard {
-    cudaGraphExec_t &e;
-    cudaGraph_t &g;
-    ~GraphGuard() {
-      if (e) cudaGraphExecDestroy(e);
-      if (g) cudaGraphDestroy(g);
-    }
-  } guard{gexec, graph};
   lqcd_status result = LQCD_OK;
   while (!hs.halt) {
-    if (gexec) {
-      LQCD_CUDA(ctx, cudaGraphLaunch(gexec, cst));
-      ctx->cnt.launches += chunk_cnt.launches;
-      ctx->cnt.hop_launches += chunk_cnt.hop_launches;
-      ctx->cnt.bytes += chunk_cnt.bytes;
-      ctx->cnt.hop_bytes += chunk_cnt.hop_bytes;
-      ctx->cnt.hop_flops += chunk_cnt.hop_flops;
-      ctx->cnt.hop_sites += chunk_cnt.hop_sites;
+    const int it_seen = hs.it;
+    lqcd_counters chunk_launches{};
+    if (graph.exec) {
+      LQCD_CUDA(ctx, cudaGraphLaunch(graph.exec, cst));
     } else {
+      const lqcd_counters c0 = ctx->cnt;
       for (int k = 0; k < chunk; k++) LQCD_TRY(iteration());
+      chunk_launches = cnt_sub(ctx->cnt, c0);
+      ctx->cnt = c0;
     }
     LQCD_CUDA(ctx, cudaMemcpyAsync(ctx->pinned, S, sizeof(hs), cudaMemcpyDeviceToHost, cst));
     LQCD_CUDA(ctx, cudaStreamSynchronize(cst));
     std::memcpy(&hs, ctx->pinned, sizeof(hs));
+    if (graph.exec) chunk_launches = graph.launches(hs.it - it_seen);
+    // iterations that ran to their end (a breakdown's partial one is not counted)
+    count_chunk(ctx, work, chunk_launches, hs.it - it_seen, false);
   }
   if (hs.bad) result = fail(ctx, LQCD_ERR_NONFINITE, "BiCGStab: non-finite scalar after %d iterations", hs.it);
   else if (hs.nonconv) result = LQCD_ERR_NOCONV;

@@ -166,6 +166,77 @@ inline void count_launch(lqcd_ctx *ctx, double bytes) {
   ctx->cnt.launches += 1;
   ctx->cnt.bytes += bytes;
 }
+
+// Work of the iterations a chunk of captured solver iterations really ran.
+// Every kernel of a chunk returns at once after a device flag halts the
+// solve (convergence, a reliable update), so a chunk of k iterations does
+// the work of n <= k of them, the last one only up to the reduction that
+// set the flag.  `full` is one iteration's count and `first` its part up to
+// that reduction (both recorded while the first iteration is enqueued).
+// Launches are counted for the whole chunk: halted kernels still launch.
+struct IterWork {
+  lqcd_counters full{}, first{};
+  bool known = false;
+};
+inline lqcd_counters cnt_sub(const lqcd_counters &a, const lqcd_counters &b) {
+  lqcd_counters d{};
+  d.launches = a.launches - b.launches;
+  d.hop_launches = a.hop_launches - b.hop_launches;
+  d.bytes = a.bytes - b.bytes;
+  d.hop_bytes = a.hop_bytes - b.hop_bytes;
+  d.hop_flops = a.hop_flops - b.hop_flops;
+  d.hop_sites = a.hop_sites - b.hop_sites;
+  return d;
+}
+inline void add_work(lqcd_counters &c, const lqcd_counters &d, double times) {
+  c.bytes += times * d.bytes;
+  c.hop_bytes += times * d.hop_bytes;
+  c.hop_flops += times * d.hop_flops;
+  c.hop_sites += times * d.hop_sites;
+}
+// Executable graph of a solver's iterations (cg.cu).  Preferred form: a
+// conditional while node whose body is one iteration followed by a
+// one-thread control kernel, which ends the loop once the solver's halt word
+// is set or after `chunk` passes, so a launch runs exactly the iterations up
+// to the next halt (convergence, a reliable update) and no halted
+// iterations.  If the driver rejects that graph, `chunk` iterations unrolled
+// (whose kernels return at once after a halt).  per_pass: launch counts of
+// one loop pass, or of the whole unrolled chunk.
+struct SolverGraph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool loop = false;
+  lqcd_counters per_pass{};
+  SolverGraph() = default;
+  SolverGraph(const SolverGraph &) = delete;
+  SolverGraph &operator=(const SolverGraph &) = delete;
+  ~SolverGraph() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+  }
+  // launch counts of a launch that began n iterations
+  lqcd_counters launches(int n) const {
+    lqcd_counters c{};
+    const uint64_t k = loop ? (uint64_t)(n > 1 ? n : 1) : 1;
+    c.launches = k * per_pass.launches;
+    c.hop_launches = k * per_pass.hop_launches;
+    return c;
+  }
+};
+// halt, loops: device words of the solver's state (loops: the loop's pass
+// counter, zero between launches).  Counters are left as they were.
+lqcd_status build_solver_graph(lqcd_ctx *ctx, int chunk, const int *halt, int *loops,
+                               const std::function<lqcd_status()> &iteration, SolverGraph *G);
+
+// launches: the chunk's launch counts; n: iterations begun; halted: the last
+// of them stopped at its halting reduction
+inline void count_chunk(lqcd_ctx *ctx, const IterWork &w, const lqcd_counters &launches, int n, bool halted) {
+  ctx->cnt.launches += launches.launches;
+  ctx->cnt.hop_launches += launches.hop_launches;
+  if (n <= 0) return;
+  add_work(ctx->cnt, w.full, halted ? n - 1 : n);
+  if (halted) add_work(ctx->cnt, w.first, 1.0);
+}
 inline double spinor_site_bytes(int prec) {
   return (double)spinor_bytes_per_site(prec) + ((prec == LQCD_BF16S || prec == LQCD_F16S) ? 4.0 : 0.0);
 }

@@ -7,6 +7,8 @@ plain FP64, float-float, mixed FP32 / BF16 / FP16 inner solves with reliable
 updates, multi-RHS point sources, graph and non-graph execution, and the
 non-convergence status.
 """
+import ctypes
+
 import numpy as np
 import pytest
 import torch
@@ -224,3 +226,36 @@ def test_bicgstab_reports_divergence(ctx):
     assert st2[0]["converged"] == 1
     if not st[0]["converged"]:
         assert st[0]["true_resid"] > 1e-10
+
+
+@pytest.mark.parametrize("graph,check_every", [(1, 7), (0, 7), (1, 50)])
+def test_work_counters_count_executed_iterations(ctx, check_every, graph):
+    """The work counters credit the iterations the device ran, not the chunk
+    of check_every iterations the host enqueued (after the halting reduction
+    every kernel of a host-enqueued chunk returns at once).  A plain FP64 solve of n
+    iterations runs 4 half hops per iteration except the last (2: it halts
+    at the |s|^2 reduction), plus 2 for the first z = Mhat^+ s and 4 outside
+    the CG (source, reconstruction, the two halves of the true residual):
+    4 n + 4 half hops of Vh sites, whatever the chunking."""
+    L = (8, 8, 8, 8)
+    kappa, mu = 0.15, 0.01 / 0.3
+    U = inputs.random_gauge(L, "near", seed=1301, eps=0.4)
+    G = lqcd.lqcd_gauge_import(ctx, dev(U), L)
+    b = inputs.gaussian_spinor(L, 1302)
+    lqcd.lib().lqcd_reset_counters(ctx.handle)
+    _, st = _solve(ctx, G, L, b, kappa, mu, tol=1e-10, check_every=check_every, use_graph=graph)
+    torch.cuda.synchronize()
+    cnt = lqcd.lqcd_counters()
+    lqcd.lib().lqcd_get_counters(ctx.handle, ctypes.byref(cnt))
+    n = st[0]["iters"]
+    assert st[0]["converged"] == 1 and st[0]["restarts"] == 0
+    Vh = inputs.volume(L) // 2
+    assert cnt.hop_sites == Vh * (4 * n + 4)
+    # launches: every enqueued kernel.  The graph runs the iterations in a
+    # device-side while loop that ends at the halt, so it launches 4 half hops
+    # per iteration begun (plus 2 for the first z and the 4 outside the CG);
+    # host-enqueued chunks also launch the halted iterations' kernels.
+    if graph:
+        assert cnt.hop_launches == 4 * n + 6
+    else:
+        assert cnt.hop_launches == 4 * (-(-n // check_every) * check_every) + 6
