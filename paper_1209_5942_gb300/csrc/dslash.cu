@@ -65,6 +65,9 @@ lqcd_status launch_hop(lqcd_ctx *ctx, const Geom &g, const HopLaunch &L, int *nb
     bool lf, two;  // two: two sites per thread in packed FP32x2
     char pk;       // float-float pair kernel: 0 scalar, 1 packed FP32x2, 2 packed + shared-memory
                    // staging; 16-bit two-site kernel: 1 = operands staged in shared memory
+    char mr;       // links staged in shared memory for a group of RHS: 0 no, else the
+                   // reals kept per link (18, or 12 with the third row rebuilt per RHS)
+    short rg;      // with mr: right-hand sides per block
   };
   Cand cands[96];
   int ncand = 0, fallback = 0;
@@ -95,6 +98,20 @@ lqcd_status launch_hop(lqcd_ctx *ctx, const Geom &g, const HopLaunch &L, int *nb
       for (short rt : {2, 4})
         for (short by : {1, 2, 4})
           if (rt * by <= nrhs) cands[ncand++] = {32, by, GM[gi], rt, false};
+  // links staged in shared memory once per site for a group of rg RHS
+  // (blocks of 32 or 64 sites; the whole RHS set, half or a quarter of it)
+  if (low && nrhs > 1)
+    for (short bx : {32, 64})
+      for (char mr : {(char)18, (char)12}) {
+        if (mr == 12 && L.recon != 12) continue;
+        short prev = 0;
+        for (int q : {1, 2, 4}) {
+          const short rg = (short)((nrhs + q - 1) / q);
+          if (rg == prev || rg < 1) continue;
+          prev = rg;
+          cands[ncand++] = {bx, 1, 0, 1, false, false, 0, mr, rg};
+        }
+      }
   // packed two-site kernel: blocks of 64 threads = 128 sites, one RHS per block row
   if (low)
     for (int gi = 0; gi < 3; gi++) cands[ncand++] = {64, 1, GM[gi], 1, false, true};
@@ -110,6 +127,12 @@ lqcd_status launch_hop(lqcd_ctx *ctx, const Geom &g, const HopLaunch &L, int *nb
   }
   auto go = [&](int ci, const HopArgs &args) {
     const Cand &k = cands[ci];
+    if (k.mr) {
+      const dim3 block(k.bx, 1, 1), grid((g.Vh + k.bx - 1) / k.bx, (nrhs + k.rg - 1) / k.rg, 1);
+      if (L.prec == LQCD_F32) hop_launch_mrhs_f32(args, L.recon, k.mr, k.rg, grid, block, dag, red, ctx->stream);
+      else hop_launch_mrhs_h16(args, L.prec, k.mr, k.rg, grid, block, dag, red, ctx->stream);
+      return;
+    }
     const int rt = k.rt;
     dim3 block(k.bx, k.by, 1), grid;
     const int per_block = pair ? k.bx / 2 : (k.two ? 2 * k.bx : k.bx);  // sites per block row
@@ -128,7 +151,7 @@ lqcd_status launch_hop(lqcd_ctx *ctx, const Geom &g, const HopLaunch &L, int *nb
     }
   };
   char key[160];
-  snprintf(key, sizeof(key), "hop4|p%d|r%d|d%d|red%d|aux%d|%dx%dx%dx%d|n%d", L.prec, L.recon, (int)dag, (int)red,
+  snprintf(key, sizeof(key), "hop5|p%d|r%d|d%d|red%d|aux%d|%dx%dx%dx%d|n%d", L.prec, L.recon, (int)dag, (int)red,
            A.has_aux, g.L[0], g.L[1], g.L[2], g.L[3], nrhs);
   HopArgs At = A;
   At.halt = nullptr;  // timing launches run whatever the solver state

@@ -1,5 +1,6 @@
 // dslash_f32.cu -- FP32 instantiations of the hop kernels (both load orders,
-// and the register-blocked multi-RHS kernel).
+// the register-blocked multi-RHS kernel and the multi-RHS kernel with links
+// staged in shared memory).
 #include "hop_kernels.cuh"
 
 namespace lqcd {
@@ -18,6 +19,16 @@ void hop_launch_f32(const HopArgs &A, int recon, dim3 grid, dim3 block, bool dag
   }
   if (recon == 12) launch_t<LQCD_F32, 12>(A, grid, block, dag, red, st, lf);
   else launch_t<LQCD_F32, 18>(A, grid, block, dag, red, st, lf);
+}
+
+void hop_launch_mrhs_f32(const HopArgs &A, int recon, int srec, int rg, dim3 grid, dim3 block, bool dag, bool red,
+                         cudaStream_t st) {
+  if (recon == 12) {
+    if (srec == 12) launch_mrhs2<LQCD_F32, 12, 12>(A, rg, grid, block, dag, red, st);
+    else launch_mrhs2<LQCD_F32, 12, 18>(A, rg, grid, block, dag, red, st);
+  } else {
+    launch_mrhs2<LQCD_F32, 18, 18>(A, rg, grid, block, dag, red, st);
+  }
 }
 
 void hop_batched_f32(int recon, bool dag, bool red, const HopArgs *d, const int2 *tl, int ntiles, int grid,

@@ -1,6 +1,7 @@
 // dslash_h16.cu -- BF16 / FP16 (per-site scaled spinors, REC12 links)
 // instantiations of the hop kernels (both load orders, the register-blocked
-// multi-RHS kernel, and the two-site packed kernel with direct loads or with
+// multi-RHS kernel, the multi-RHS kernel with links staged in shared memory,
+// and the two-site packed kernel with direct loads or with
 // its operands staged through shared memory).
 #include "hop_kernels.cuh"
 
@@ -37,6 +38,17 @@ void hop_launch_h16(const HopArgs &A, int prec, dim3 grid, dim3 block, bool dag,
   }
   if (prec == LQCD_BF16S) launch_t<LQCD_BF16S, 12>(A, grid, block, dag, red, st, lf);
   else launch_t<LQCD_F16S, 12>(A, grid, block, dag, red, st, lf);
+}
+
+void hop_launch_mrhs_h16(const HopArgs &A, int prec, int srec, int rg, dim3 grid, dim3 block, bool dag, bool red,
+                         cudaStream_t st) {
+  if (prec == LQCD_BF16S) {
+    if (srec == 12) launch_mrhs2<LQCD_BF16S, 12, 12>(A, rg, grid, block, dag, red, st);
+    else launch_mrhs2<LQCD_BF16S, 12, 18>(A, rg, grid, block, dag, red, st);
+  } else {
+    if (srec == 12) launch_mrhs2<LQCD_F16S, 12, 12>(A, rg, grid, block, dag, red, st);
+    else launch_mrhs2<LQCD_F16S, 12, 18>(A, rg, grid, block, dag, red, st);
+  }
 }
 
 void hop_batched_h16(int prec, bool dag, bool red, const HopArgs *d, const int2 *tl, int ntiles, int grid,

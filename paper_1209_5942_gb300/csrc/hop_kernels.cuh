@@ -491,6 +491,124 @@ __global__ void __launch_bounds__(128) hop_rt_kernel(HopArgs A) {
     hop_site_rt<PREC, RECON, DAG, REDUCE, RT>(A, base + threadIdx.x, rhs0);
 }
 
+// ---------------------------------------------------------------------------
+// Multi-RHS hop with the links staged in shared memory (F32 and the 16-bit
+// formats).  A block owns NT consecutive output sites and a group of RG
+// right-hand sides.  Each thread first loads the eight links of its site
+// (the four forward ones at the site, the four backward ones at its
+// neighbours) once, rebuilds the third row where SREC = 18, and keeps them in
+// its own column of shared memory; it then runs the hop for every RHS of the
+// group in turn, reading the links back from shared memory, so that L2 serves
+// the link words once per site instead of once per RHS-site and only the
+// neighbour spinors are fetched per RHS.  SREC = 12 keeps two rows and
+// rebuilds the third for every RHS (less shared memory per thread, more
+// warps per SM).  The columns are thread-private, so no barrier is needed.
+// Every RHS goes through hop_site's operations in hop_site's order (the same
+// reconstruct, project, product and accumulation functions), so the results
+// are bitwise those of single-RHS launches.
+// ---------------------------------------------------------------------------
+template <int SREC> struct MrhsLinkCols {
+  static constexpr int NW = SREC == 18 ? 4 : 3;  // 16-byte words per link (+ one 8-byte word for 18)
+  static constexpr size_t bytes_per_thread = 8 * (NW * 16 + (SREC == 18 ? 8 : 0));
+};
+
+template <int PREC, int RECON, int SREC, int MU, int S>
+LQCD_DEV void mrhs_dir(const HopArgs &A, const float4 *W, const float2 *T8, int nt, int jf, int jb, bool negf,
+                       bool negb, const SpinorView &vin, Cx<float> acc[12]) {
+  constexpr int NW = MrhsLinkCols<SREC>::NW;
+  Cx<float> ps[12], pb[12], h[6], v[6], u[9];
+  // both neighbours' spinor loads in flight before any arithmetic
+  const float scf = load_nb<PREC>(vin, jf, ps);
+  const float scb = load_nb<PREC>(vin, jb, pb);
+#pragma unroll
+  for (int dir = 0; dir < 2; dir++) {
+    const int ds = 2 * MU + dir;
+#pragma unroll
+    for (int k = 0; k < NW; k++) {
+      const float4 w = W[(ds * NW + k) * nt];
+      u[2 * k] = {w.x, w.y};
+      u[2 * k + 1] = {w.z, w.w};
+    }
+    if constexpr (SREC == 18) {
+      const float2 e = T8[ds * nt];
+      u[8] = {e.x, e.y};
+    } else {
+      reconstruct_row2(u);
+    }
+    if (dir == 0) {
+      project<MU, S>(ps, h);
+      mul_link(u, h, v);
+      acc_nb<PREC, MU, S>(v, scf, negf, acc);
+    } else {
+      project<MU, -S>(pb, h);
+      mul_link_dag(u, h, v);
+      acc_nb<PREC, MU, -S>(v, scb, negb, acc);
+    }
+  }
+}
+
+// Blocks of 32 or 64 threads, bounded to 128 registers: the shared memory
+// allows 6 (18-real columns) or 8 (12-real) blocks of 64 sites per SM.
+template <int PREC, int RECON, int SREC, bool DAG, bool REDUCE>
+__global__ void __launch_bounds__(64, 8) hop_mrhs_kernel(HopArgs A, int rg) {
+  static_assert(SREC == 18 || RECON == 12, "12-real link columns need 12-real links");
+  constexpr int NW = MrhsLinkCols<SREC>::NW;
+  extern __shared__ float4 mrhs_cols[];
+  pdl_wait();
+  if (A.halt && *(volatile int *)A.halt) return;
+  const int nt = blockDim.x;
+  const int rhs0 = blockIdx.y * rg;
+  const int rhs1 = min(rhs0 + rg, A.nrhs);
+  const int p = A.out_parity;
+  const int cb = blockIdx.x * nt + threadIdx.x;
+  const bool active = cb < A.g.Vh;
+  // this thread's column: W[(ds * NW + k) * nt], T8[ds * nt]
+  const float4 *W = mrhs_cols + threadIdx.x;
+  const float2 *T8 = (const float2 *)(mrhs_cols + 8 * NW * nt) + threadIdx.x;
+  int jn[8];
+  bool negf = false, negb = false;
+  if (active) {
+    const Site s = site_of(A.g, p, cb);
+    negf = A.g.antiper && s.t == A.g.L[3] - 1;
+    negb = A.g.antiper && s.t == 0;
+    float4 *Ww = mrhs_cols + threadIdx.x;
+    float2 *Tw = (float2 *)(mrhs_cols + 8 * NW * nt) + threadIdx.x;
+#pragma unroll
+    for (int ds = 0; ds < 8; ds++) {
+      const int mu = ds >> 1;
+      jn[ds] = neighbour_cb(A.g, s, mu, (ds & 1) ? -1 : +1);
+      Cx<float> u[9];
+      LinkIO<PREC, RECON>::load(A.U, (ds & 1) ? p ^ 1 : p, mu, (ds & 1) ? jn[ds] : cb, u);
+      if (RECON == 12 && SREC == 18) reconstruct_row2(u);
+#pragma unroll
+      for (int k = 0; k < NW; k++)
+        Ww[(ds * NW + k) * nt] = make_float4(u[2 * k].re, u[2 * k].im, u[2 * k + 1].re, u[2 * k + 1].im);
+      if (SREC == 18) Tw[ds * nt] = make_float2(u[8].re, u[8].im);
+    }
+  }
+  constexpr int S = DAG ? -1 : 1;
+  for (int rhs = rhs0; rhs < rhs1; rhs++) {
+    double nrm = 0.0;
+    if (active) {
+      SpinorView vin{A.in + rhs * A.in_rs, A.in_scale ? A.in_scale + rhs * A.in_srs : nullptr, A.g.Vh};
+      Cx<float> acc[12];
+#pragma unroll
+      for (int k = 0; k < 12; k++) acc[k] = czero<float>();
+      mrhs_dir<PREC, RECON, SREC, 0, S>(A, W, T8, nt, jn[0], jn[1], false, false, vin, acc);
+      mrhs_dir<PREC, RECON, SREC, 1, S>(A, W, T8, nt, jn[2], jn[3], false, false, vin, acc);
+      mrhs_dir<PREC, RECON, SREC, 2, S>(A, W, T8, nt, jn[4], jn[5], false, false, vin, acc);
+      mrhs_dir<PREC, RECON, SREC, 3, S>(A, W, T8, nt, jn[6], jn[7], negf, negb, vin, acc);
+      nrm = hop_epilogue<PREC, REDUCE>(A, cb, rhs, acc);
+    }
+    if (REDUCE) hop_warp_partial(A, cb, rhs, nrm);
+  }
+}
+
+// shared memory of one hop_mrhs_kernel block of nt threads
+inline size_t mrhs_smem_bytes(int srec, int nt) {
+  return (size_t)nt * (srec == 18 ? MrhsLinkCols<18>::bytes_per_thread : MrhsLinkCols<12>::bytes_per_thread);
+}
+
 // Grid-stride over the output sites: a full grid (one site per thread) or a
 // smaller persistent grid, whichever the autotuner finds faster.
 // LF selects, for the memory-bound formats, whether both neighbours' loads of
@@ -1267,6 +1385,19 @@ inline void launch_rt(const HopArgs &A, int rt, dim3 grid, dim3 block, bool dag,
   else launch_rt2<PREC, RECON, 2>(A, grid, block, dag, red, st);
 }
 
+// the multi-RHS kernel with links staged in shared memory (srec reals per link)
+template <int PREC, int RECON, int SREC>
+inline void launch_mrhs2(const HopArgs &A, int rg, dim3 grid, dim3 block, bool dag, bool red, cudaStream_t st) {
+  const size_t smem = mrhs_smem_bytes(SREC, block.x);
+  if (dag) {
+    if (red) launch_pdl(hop_mrhs_kernel<PREC, RECON, SREC, true, true>, grid, block, smem, st, A, rg);
+    else launch_pdl(hop_mrhs_kernel<PREC, RECON, SREC, true, false>, grid, block, smem, st, A, rg);
+  } else {
+    if (red) launch_pdl(hop_mrhs_kernel<PREC, RECON, SREC, false, true>, grid, block, smem, st, A, rg);
+    else launch_pdl(hop_mrhs_kernel<PREC, RECON, SREC, false, false>, grid, block, smem, st, A, rg);
+  }
+}
+
 // the loads-first variant exists only for the memory-bound formats
 template <int PREC, int RECON>
 inline void launch_t(const HopArgs &A, dim3 grid, dim3 block, bool dag, bool red, cudaStream_t st,
@@ -1290,6 +1421,13 @@ void hop_launch_df64(const HopArgs &A, int recon, bool pair, int mode, dim3 grid
 // rt: right-hand sides per thread (1, 2, 4); two: two sites per thread (packed FP32x2)
 void hop_launch_f32(const HopArgs &A, int recon, dim3 grid, dim3 block, bool dag, bool red, bool lf, int rt,
                     bool two, cudaStream_t st);
+// multi-RHS kernel with the links staged in shared memory: srec reals kept per
+// link (18, or 12 for 12-real fields), rg right-hand sides per block, block.x
+// sites per block (at most 48 KB of shared memory)
+void hop_launch_mrhs_f32(const HopArgs &A, int recon, int srec, int rg, dim3 grid, dim3 block, bool dag, bool red,
+                         cudaStream_t st);
+void hop_launch_mrhs_h16(const HopArgs &A, int prec, int srec, int rg, dim3 grid, dim3 block, bool dag, bool red,
+                         cudaStream_t st);
 // staged: the two-site kernel with its operands staged through shared memory
 void hop_launch_h16(const HopArgs &A, int prec, dim3 grid, dim3 block, bool dag, bool red, bool lf, int rt,
                     bool two, bool staged, cudaStream_t st);

@@ -204,7 +204,7 @@ def test_every_launch_shape_gives_the_same_bits(ctx, nrhs, L):
             return dout.view(torch.uint8).clone(), (sout.view(torch.uint8).clone() if sb_half else None)
 
         ref = run(-1)
-        for choice in range(48):
+        for choice in range(64):
             got = run(choice)
             assert torch.equal(got[0], ref[0]), (prec, choice)
             if sb_half:
