@@ -77,7 +77,8 @@ typedef enum {
   LQCD_ERR_NONFINITE = -4,   /* NaN/Inf met in an input or a solver scalar */
   LQCD_ERR_TIMEOUT = -5,     /* a bounded device-side wait ran out */
   LQCD_ERR_OOM = -6,         /* device allocation failed */
-  LQCD_ERR_UNSUPPORTED = -7  /* valid request that the library does not implement */
+  LQCD_ERR_UNSUPPORTED = -7, /* valid request that the library does not implement */
+  LQCD_ERR_COMM = -8         /* a caller's communication hook reported a failure */
 } lqcd_status;
 
 typedef enum { LQCD_FULL = 0, LQCD_EVEN = 1, LQCD_ODD = 2 } lqcd_parity;
@@ -358,6 +359,48 @@ typedef struct {
 int lqcd_cg_solve(lqcd_ctx *ctx, const lqcd_gauge *U, lqcd_field b, lqcd_field x,
                   const lqcd_geom *geom, double kappa, double mu, const lqcd_cg_params *params,
                   lqcd_cg_stats *stats);
+
+/* Communication of a domain-decomposed solve (lqcd_dd_cg_solve), called by
+ * the library from the calling thread between its launches:
+ *   exchange(user): every held domain's to_prev and to_next faces are written
+ *     (the library's stream has been synchronised); the hook delivers each
+ *     to_prev face to the previous domain's from_next buffer and each to_next
+ *     face to the next domain's from_prev buffer, and returns once they are
+ *     in place;
+ *   allreduce(user, vals, n): sums n host doubles over all processes of the
+ *     solve, in place (NULL: a single process).
+ * Both return 0 on success; anything else ends the solve with LQCD_ERR_COMM. */
+typedef struct {
+  void *user;
+  int (*exchange)(void *user);
+  int (*allreduce)(void *user, double *vals, int n);
+} lqcd_dd_comm;
+
+/* The even-odd CG of lqcd_cg_solve (CGLS on Mhat^+ Mhat, source preparation,
+ * reconstruction, FP64 true residual and outer refinement; IEEE FP64, one
+ * right-hand side) on a lattice split along t into nt domains as for
+ * lqcd_dd_pack (Sec. 6 outlook: the solver over several GPUs).  This call
+ * holds nd consecutive domains, first_domain .. first_domain + nd - 1, each on
+ * the local geometry `local` (local->L[3] = Lt / nt, even; local must match
+ * the gauge fields' geometry): U[k] its gauge field, b[k] and x[k] EO full
+ * fields (LQCD_F64, nrhs = 1; x is overwritten), faces[4k .. 4k+3] its
+ * to_prev, to_next, from_next and from_prev face buffers (device,
+ * lqcd_dd_face_bytes(local, LQCD_F64) each, 16-byte aligned).  Every half hop
+ * packs the faces of all held domains, moves them and runs the domain hops
+ * with the operator's diagonal epilogue; every norm is summed in a fixed
+ * order on each domain, over the held domains in order, then over
+ * processes.  comm = NULL: the call holds every domain (nd = nt,
+ * first_domain = 0) and the library moves the faces by device copies;
+ * otherwise comm->exchange moves them and comm->allreduce sums the norms.
+ * antiperiodic_t: the fermion boundary of the whole lattice.  params: tol,
+ * max_iter, max_restarts (outer_prec and inner_prec LQCD_F64, solver CG,
+ * else LQCD_ERR_UNSUPPORTED).  stats: one entry; true_resid is that of the
+ * whole lattice.  Synchronous; LQCD_ERR_NOCONV (stats filled) when tol is not
+ * reached. */
+int lqcd_dd_cg_solve(lqcd_ctx *ctx, int nd, const lqcd_gauge *const *U, const lqcd_field *b,
+                     const lqcd_field *x, void *const *faces, const lqcd_geom *local, int first_domain,
+                     int nt, int antiperiodic_t, double kappa, double mu, const lqcd_cg_params *params,
+                     const lqcd_dd_comm *comm, lqcd_cg_stats *stats);
 
 /* Solves n independent systems M_k x_k = b_k on lattices of different sizes
  * (each b_k, x_k: FULL EO LQCD_F64 fields on U_k's geometry) with one

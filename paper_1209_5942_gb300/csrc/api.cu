@@ -520,6 +520,60 @@ extern "C" int lqcd_dd_dslash(lqcd_ctx *ctx, const lqcd_gauge *U, lqcd_field in,
   return dd_run(ctx, g, L, false, const_cast<void *>(face_from_next), const_cast<void *>(face_from_prev), 0, 0);
 }
 
+static lqcd_status check_cg_params(lqcd_ctx *ctx, const lqcd_cg_params *p);
+
+extern "C" int lqcd_dd_cg_solve(lqcd_ctx *ctx, int nd, const lqcd_gauge *const *U, const lqcd_field *b,
+                                const lqcd_field *x, void *const *faces, const lqcd_geom *local, int first_domain,
+                                int nt, int antiperiodic_t, double kappa, double mu, const lqcd_cg_params *params,
+                                const lqcd_dd_comm *comm, lqcd_cg_stats *stats) {
+  if (!ctx) return LQCD_ERR_INVALID;
+  if (!U || !b || !x || !faces || !local || !params || !stats)
+    return fail(ctx, LQCD_ERR_INVALID, "domain-decomposed CG: NULL argument");
+  if (nt < 1 || nd < 1 || first_domain < 0 || first_domain + nd > nt)
+    return fail(ctx, LQCD_ERR_INVALID, "domain-decomposed CG: domains %d..%d of %d", first_domain,
+                first_domain + nd - 1, nt);
+  if (!comm && (nd != nt || first_domain != 0))
+    return fail(ctx, LQCD_ERR_INVALID, "domain-decomposed CG without comm hooks must hold every domain");
+  if (comm && !comm->exchange) return fail(ctx, LQCD_ERR_INVALID, "domain-decomposed CG: no exchange hook");
+  LQCD_TRY(check_cg_params(ctx, params));
+  if (params->outer_prec != LQCD_F64 || params->inner_prec != LQCD_F64 || params->solver != LQCD_SOLVER_CG)
+    return fail(ctx, LQCD_ERR_UNSUPPORTED, "domain-decomposed CG: plain FP64 CG only");
+  if (!std::isfinite(kappa) || !std::isfinite(mu)) return fail(ctx, LQCD_ERR_NONFINITE, "kappa/mu not finite");
+  const size_t fb = lqcd_dd_face_bytes(local, LQCD_F64);
+  if (fb == 0) return fail(ctx, LQCD_ERR_INVALID, "domain-decomposed CG: bad local geometry");
+  lqcd_geom lg = *local;
+  lg.antiperiodic_t = 0;  // the global boundary sign travels in the faces
+  const Geom g = make_geom(lg);
+  const size_t full_bytes = 2 * spinor_half_bytes(LQCD_F64, g.Vh);
+  std::vector<GaugeView> views(nd);
+  std::vector<HalfField> bf(nd), xf(nd);
+  std::vector<void *> fv(4 * (size_t)nd);
+  int recon = 0;
+  for (int d = 0; d < nd; d++) {
+    LQCD_TRY(check_gauge(ctx, U[d], local));
+    if (d == 0) recon = U[0]->recon;
+    if (U[d]->recon != recon) return fail(ctx, LQCD_ERR_INVALID, "domain-decomposed CG: mixed link formats");
+    LQCD_TRY(gauge_view(ctx, const_cast<lqcd_gauge *>(U[d]), LQCD_F64, recon, &views[d]));
+    LQCD_TRY(check_field(ctx, b[d], "b", false));
+    LQCD_TRY(check_field(ctx, x[d], "x", false));
+    if (b[d].prec != LQCD_F64 || x[d].prec != LQCD_F64 || b[d].nrhs != 1 || x[d].nrhs != 1)
+      return fail(ctx, LQCD_ERR_INVALID, "domain-decomposed CG: b and x must be LQCD_F64 with nrhs = 1");
+    if (ranges_overlap(b[d].ptr, full_bytes, x[d].ptr, full_bytes))
+      return fail(ctx, LQCD_ERR_INVALID, "domain-decomposed CG: b and x alias");
+    bf[d] = to_half(b[d], g, true);
+    xf[d] = to_half(x[d], g, true);
+    for (int k = 0; k < 4; k++) {
+      void *f = faces[4 * d + k];
+      if (!f || ((uintptr_t)f & 15u)) return fail(ctx, LQCD_ERR_INVALID, "faces: NULL or not 16-byte aligned");
+      for (int j = 0; j < 4 * d + k; j++)
+        if (ranges_overlap(f, fb, faces[j], fb)) return fail(ctx, LQCD_ERR_INVALID, "face buffers alias");
+      fv[4 * d + k] = f;
+    }
+  }
+  return dd_cg_solve(ctx, nd, first_domain, nt, antiperiodic_t ? 1 : 0, g, recon, views, bf, xf, fv, fb, comm,
+                     kappa, mu, *params, stats);
+}
+
 static int apply_impl(lqcd_ctx *ctx, const lqcd_gauge *U, lqcd_field in, lqcd_field out,
                       const lqcd_geom *geom, double kappa, double mu, int parity, bool dagger) {
   if (!ctx) return LQCD_ERR_INVALID;

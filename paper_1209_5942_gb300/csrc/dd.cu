@@ -86,51 +86,56 @@ __global__ void __launch_bounds__(128) dd_pack_kernel(HopArgs A, int vsh, void *
 
 // The half hop on a domain: x, y, z hops as in hop_site, t hops inside the
 // domain from the input field, the two boundary ones from the faces.
-template <int PREC, int RECON, bool DAG>
+// REDUCE: also the per-warp |out|^2 partials of hop_warp_partial (all lanes
+// of a warp reach it, so inactive lanes do not return early).
+template <int PREC, int RECON, bool DAG, bool REDUCE>
 __global__ void __launch_bounds__(128) dd_hop_kernel(HopArgs A, int vsh, const void *from_next,
                                                      const void *from_prev) {
   using R = typename SpinorIO<PREC>::R;
   const int cb = blockIdx.x * blockDim.x + threadIdx.x;
-  if (cb >= A.g.Vh) return;
-  constexpr int S = DAG ? -1 : 1;
-  const int p = A.out_parity;
-  const Site s = site_of(A.g, p, cb);
-  const SpinorView vin{A.in, A.in_scale, A.g.Vh};
-  Cx<R> acc[12];
+  double nrm = 0.0;
+  if (cb < A.g.Vh) {
+    constexpr int S = DAG ? -1 : 1;
+    const int p = A.out_parity;
+    const Site s = site_of(A.g, p, cb);
+    const SpinorView vin{A.in, A.in_scale, A.g.Vh};
+    Cx<R> acc[12];
 #pragma unroll
-  for (int k = 0; k < 12; k++) acc[k] = czero<R>();
-  hop_dir<PREC, RECON, 0, S, false>(A, s, p, cb, vin, acc);
-  hop_dir<PREC, RECON, 1, S, false>(A, s, p, cb, vin, acc);
-  hop_dir<PREC, RECON, 2, S, false>(A, s, p, cb, vin, acc);
-  const int Lt = A.g.L[3];
-  Cx<R> ps[12], h[6], u[9], v[6];
-  // forward: (1 - S gamma_t) U_t(x) psi(x + t)
-  if (s.t == Lt - 1) {
-    const int j = cb - (Lt - 1) * vsh;
+    for (int k = 0; k < 12; k++) acc[k] = czero<R>();
+    hop_dir<PREC, RECON, 0, S, false>(A, s, p, cb, vin, acc);
+    hop_dir<PREC, RECON, 1, S, false>(A, s, p, cb, vin, acc);
+    hop_dir<PREC, RECON, 2, S, false>(A, s, p, cb, vin, acc);
+    const int Lt = A.g.L[3];
+    Cx<R> ps[12], h[6], u[9], v[6];
+    // forward: (1 - S gamma_t) U_t(x) psi(x + t)
+    if (s.t == Lt - 1) {
+      const int j = cb - (Lt - 1) * vsh;
 #pragma unroll
-    for (int k = 0; k < 6; k++) h[k] = FaceIO<PREC>::load(from_next, vsh, k, j);
-  } else {
-    SpinorIO<PREC>::load(vin, neighbour_cb(A.g, s, 3, +1), ps);
-    project<3, S>(ps, h);
-  }
-  LinkIO<PREC, RECON>::load(A.U, p, 3, cb, u);
-  if (RECON == 12) reconstruct_row2(u);
-  mul_link(u, h, v);
-  accumulate<3, S>(v, acc);
-  // backward: (1 + S gamma_t) U_t(x - t)^+ psi(x - t)
-  if (s.t == 0) {
-#pragma unroll
-    for (int k = 0; k < 6; k++) v[k] = FaceIO<PREC>::load(from_prev, vsh, k, cb);
-  } else {
-    const int jb = neighbour_cb(A.g, s, 3, -1);
-    SpinorIO<PREC>::load(vin, jb, ps);
-    project<3, -S>(ps, h);
-    LinkIO<PREC, RECON>::load(A.U, p ^ 1, 3, jb, u);
+      for (int k = 0; k < 6; k++) h[k] = FaceIO<PREC>::load(from_next, vsh, k, j);
+    } else {
+      SpinorIO<PREC>::load(vin, neighbour_cb(A.g, s, 3, +1), ps);
+      project<3, S>(ps, h);
+    }
+    LinkIO<PREC, RECON>::load(A.U, p, 3, cb, u);
     if (RECON == 12) reconstruct_row2(u);
-    mul_link_dag(u, h, v);
+    mul_link(u, h, v);
+    accumulate<3, S>(v, acc);
+    // backward: (1 + S gamma_t) U_t(x - t)^+ psi(x - t)
+    if (s.t == 0) {
+#pragma unroll
+      for (int k = 0; k < 6; k++) v[k] = FaceIO<PREC>::load(from_prev, vsh, k, cb);
+    } else {
+      const int jb = neighbour_cb(A.g, s, 3, -1);
+      SpinorIO<PREC>::load(vin, jb, ps);
+      project<3, -S>(ps, h);
+      LinkIO<PREC, RECON>::load(A.U, p ^ 1, 3, jb, u);
+      if (RECON == 12) reconstruct_row2(u);
+      mul_link_dag(u, h, v);
+    }
+    accumulate<3, -S>(v, acc);
+    nrm = hop_epilogue<PREC, REDUCE>(A, cb, 0, acc);
   }
-  accumulate<3, -S>(v, acc);
-  hop_epilogue<PREC, false>(A, cb, 0, acc);
+  if (REDUCE) hop_warp_partial(A, cb, 0, nrm);
 }
 
 template <int PREC, int RECON>
@@ -142,8 +147,16 @@ static void dd_launch(bool pack, bool dag, const HopArgs &A, int vsh, void *f0, 
     else dd_pack_kernel<PREC, RECON, 1><<<grid, 128, 0, st>>>(A, vsh, f0, f1, n0, n1);
   } else {
     const unsigned grid = (unsigned)((A.g.Vh + 127) / 128);
-    if (dag) dd_hop_kernel<PREC, RECON, true><<<grid, 128, 0, st>>>(A, vsh, f0, f1);
-    else dd_hop_kernel<PREC, RECON, false><<<grid, 128, 0, st>>>(A, vsh, f0, f1);
+    // the reducing form serves the FP64 domain-decomposed CG only
+    if constexpr (PREC == LQCD_F64) {
+      if (A.partials) {
+        if (dag) dd_hop_kernel<PREC, RECON, true, true><<<grid, 128, 0, st>>>(A, vsh, f0, f1);
+        else dd_hop_kernel<PREC, RECON, false, true><<<grid, 128, 0, st>>>(A, vsh, f0, f1);
+        return;
+      }
+    }
+    if (dag) dd_hop_kernel<PREC, RECON, true, false><<<grid, 128, 0, st>>>(A, vsh, f0, f1);
+    else dd_hop_kernel<PREC, RECON, false, false><<<grid, 128, 0, st>>>(A, vsh, f0, f1);
   }
 }
 

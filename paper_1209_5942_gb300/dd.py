@@ -17,8 +17,14 @@ as ``from_next``) and its ``to_next`` face to domain d+1 (``from_prev``).
 ``LocalExchange`` does this inside one process (all domains on one device,
 device copies); ``DistributedExchange`` with one domain per rank of a
 ``torch.distributed`` group (NCCL for CUDA tensors, gloo for CPU tensors).
-Nothing here does arithmetic of the method: every step of the hop runs in the
-library's kernels.
+The domain-decomposed FP64 CG (``lqcd_dd_cg_solve``) runs every half hop of
+its operator this way; its norms are summed over the domains held by the
+call and then over processes.  ``cg_solve_local_domains`` holds all domains in
+one call (the library moves the faces itself); ``cg_solve_distributed``
+holds one domain per rank and gives the library hooks that move the faces
+with ``DistributedExchange`` and sum the norms with ``all_reduce``.
+Nothing here does arithmetic of the method: every step of the hop and of
+the solver runs in the library's kernels.
 """
 from __future__ import annotations
 
@@ -148,3 +154,49 @@ def dslash_distributed(ctx, slabs: TimeSlabs, rank: int, gauge, inp, out, out_pa
     (exchange or DistributedExchange()).exchange(slabs, rank, to_prev, to_next, from_next, from_prev)
     lqcd.lqcd_dd_dslash(ctx, gauge, inp, out, from_next, from_prev, out_parity, dagger)
     return bufs
+
+
+def cg_solve_local_domains(ctx, slabs: TimeSlabs, gauges, bs, xs, kappa, mu, params, faces=None,
+                           allow_noconv=False):
+    """Domain-decomposed FP64 CG with every domain of `slabs` held in this
+    process (one device): gauges[d], bs[d], xs[d] (EO full fields of domain d
+    on the local geometry).  Returns the solve's stats."""
+    if faces is None:
+        faces = [face_buffers(slabs, lqcd.LQCD_F64) for _ in range(slabs.nt)]
+    return lqcd.lqcd_dd_cg_solve(ctx, gauges, bs, xs, faces, 0, slabs.nt, kappa, mu, params,
+                                 antiperiodic_t=slabs.antiperiodic_t, allow_noconv=allow_noconv)
+
+
+class DistributedComm:
+    """The communication hooks of a domain-decomposed solve with one domain
+    per rank of a torch.distributed group: exchange() moves this rank's faces
+    (DistributedExchange), allreduce(values) sums host floats over the group
+    (on the CPU for gloo, on the device for NCCL)."""
+
+    def __init__(self, slabs: TimeSlabs, rank: int, faces, group=None):
+        self.slabs, self.rank, self.faces, self.group = slabs, rank, faces, group
+        self._ex = DistributedExchange(group)
+
+    def exchange(self):
+        self._ex.exchange(self.slabs, self.rank, *self.faces)
+        if self.faces[0].is_cuda:
+            torch.cuda.current_stream().synchronize()
+
+    def allreduce(self, values):
+        import torch.distributed as dist
+        cpu = dist.get_backend(self.group) == "gloo"
+        t = torch.tensor(list(values), dtype=torch.float64, device="cpu" if cpu else self.faces[0].device)
+        dist.all_reduce(t, group=self.group)
+        return t.tolist()
+
+
+def cg_solve_distributed(ctx, slabs: TimeSlabs, rank: int, gauge, b, x, kappa, mu, params, group=None,
+                         faces=None, allow_noconv=False):
+    """Domain-decomposed FP64 CG with this rank's domain (rank = domain index)
+    in a torch.distributed job; NCCL moves the CUDA face buffers."""
+    if faces is None:
+        faces = face_buffers(slabs, lqcd.LQCD_F64)
+    comm = DistributedComm(slabs, rank, faces, group)
+    return lqcd.lqcd_dd_cg_solve(ctx, [gauge], [b], [x], [faces], rank, slabs.nt, kappa, mu, params,
+                                 antiperiodic_t=slabs.antiperiodic_t, exchange=comm.exchange,
+                                 allreduce=comm.allreduce, allow_noconv=allow_noconv)

@@ -24,6 +24,7 @@ LQCD_ERR_NONFINITE = -4
 LQCD_ERR_TIMEOUT = -5
 LQCD_ERR_OOM = -6
 LQCD_ERR_UNSUPPORTED = -7
+LQCD_ERR_COMM = -8
 
 LQCD_FULL, LQCD_EVEN, LQCD_ODD = 0, 1, 2
 LQCD_F64, LQCD_DF64, LQCD_F32, LQCD_BF16S, LQCD_F16S = 0, 1, 2, 3, 4
@@ -32,7 +33,7 @@ LQCD_SOLVER_CG, LQCD_SOLVER_BICGSTAB = 0, 1
 
 _STATUS_NAMES = {0: "LQCD_OK", -1: "LQCD_ERR_INVALID", -2: "LQCD_ERR_CUDA", -3: "LQCD_ERR_NOCONV",
                  -4: "LQCD_ERR_NONFINITE", -5: "LQCD_ERR_TIMEOUT", -6: "LQCD_ERR_OOM",
-                 -7: "LQCD_ERR_UNSUPPORTED"}
+                 -7: "LQCD_ERR_UNSUPPORTED", -8: "LQCD_ERR_COMM"}
 
 
 class LqcdError(RuntimeError):
@@ -97,6 +98,15 @@ class lqcd_hmc_stats(ctypes.Structure):
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 _FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 
+# communication hooks of the domain-decomposed solve (lqcd_dd_comm)
+_EXCHANGE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p)
+_ALLREDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int)
+
+
+class lqcd_dd_comm(ctypes.Structure):
+    _fields_ = [("user", ctypes.c_void_p), ("exchange", _EXCHANGE_FN), ("allreduce", _ALLREDUCE_FN)]
+
+
 # --- library loading ------------------------------------------------------------
 _lib = None
 _vp = ctypes.c_void_p
@@ -135,6 +145,10 @@ SIGNATURES = [
                              _i]),
     ("lqcd_cg_solve", _i, [_vp, _vp, lqcd_field, lqcd_field, ctypes.POINTER(lqcd_geom), _d, _d,
                            ctypes.POINTER(lqcd_cg_params), ctypes.POINTER(lqcd_cg_stats)]),
+    ("lqcd_dd_cg_solve", _i, [_vp, _i, ctypes.POINTER(_vp), ctypes.POINTER(lqcd_field),
+                              ctypes.POINTER(lqcd_field), ctypes.POINTER(_vp), ctypes.POINTER(lqcd_geom), _i, _i,
+                              _i, _d, _d, ctypes.POINTER(lqcd_cg_params), ctypes.POINTER(lqcd_dd_comm),
+                              ctypes.POINTER(lqcd_cg_stats)]),
     ("lqcd_cg_solve_batch", _i, [_vp, _i, ctypes.POINTER(_vp), ctypes.POINTER(lqcd_field),
                                  ctypes.POINTER(lqcd_field), ctypes.POINTER(_d), ctypes.POINTER(_d),
                                  ctypes.POINTER(lqcd_cg_params), ctypes.POINTER(lqcd_cg_stats)]),
@@ -468,6 +482,53 @@ def lqcd_cg_solve(ctx: Context, U: Gauge, b: lqcd_field, x: lqcd_field, kappa, m
                                   ctypes.byref(params), stats),
               allow=(LQCD_ERR_NOCONV,) if allow_noconv else ())
     return [s.as_dict() for s in stats]
+
+
+def lqcd_dd_cg_solve(ctx: Context, Us, bs, xs, faces, first_domain, nt, kappa, mu,
+                     params: lqcd_cg_params, antiperiodic_t=True, exchange=None, allreduce=None,
+                     allow_noconv=False):
+    """Domain-decomposed CG (include/lqcd.h): Us, bs, xs, faces for the held
+    domains (faces: 4 device tensors per domain); exchange() / allreduce(list of
+    floats) -> list: the communication hooks (None for all domains in this
+    call).  The hooks are called from inside the library call."""
+    nd = len(Us)
+    g = Us[0].geom
+    U_arr = (_vp * nd)(*[u.handle for u in Us])
+    b_arr = (lqcd_field * nd)(*bs)
+    x_arr = (lqcd_field * nd)(*xs)
+    f_arr = (_vp * (4 * nd))(*[t.data_ptr() for fs in faces for t in fs])
+    stats = lqcd_cg_stats()
+    comm_p = None
+    errors = []
+    if exchange is not None:
+        def _ex(_user):
+            try:
+                exchange()
+                return 0
+            except Exception as e:  # reported as LQCD_ERR_COMM; re-raised below
+                errors.append(e)
+                return 1
+
+        def _ar(_user, vals, n):
+            try:
+                if allreduce is not None:
+                    out = allreduce([vals[i] for i in range(n)])
+                    for i in range(n):
+                        vals[i] = float(out[i])
+                return 0
+            except Exception as e:
+                errors.append(e)
+                return 1
+        ex_cb, ar_cb = _EXCHANGE_FN(_ex), _ALLREDUCE_FN(_ar)
+        comm = lqcd_dd_comm(None, ex_cb, ar_cb)
+        comm_p = ctypes.byref(comm)
+    rc = lib().lqcd_dd_cg_solve(ctx.handle, nd, U_arr, b_arr, x_arr, f_arr, ctypes.byref(g), int(first_domain),
+                                int(nt), int(bool(antiperiodic_t)), kappa, mu, ctypes.byref(params), comm_p,
+                                ctypes.byref(stats))
+    if errors:
+        raise errors[0]
+    ctx.check(rc, allow=(LQCD_ERR_NOCONV,) if allow_noconv else ())
+    return stats.as_dict()
 
 
 def lqcd_cg_solve_batch(ctx: Context, Us, bs, xs, kappas, mus, params: lqcd_cg_params,

@@ -2,8 +2,10 @@
 time-slab geometry, the neighbours and global boundary signs, and the face
 exchange of DistributedExchange with 2 and 4 ranks, whose routing must give
 every domain the `to_prev` face of its next domain and the `to_next` face of
-its previous one (with two ranks both are the same peer).  The GPU kernels
-of the hop are checked against the oracle in tests/test_gpu_dd.py."""
+its previous one (with two ranks both are the same peer), and the hooks of
+the domain-decomposed solver (DistributedComm: the same exchange, and the sum
+of host values over the ranks).  The GPU kernels of the hop and the solver
+are checked against the oracle in tests/test_gpu_dd.py."""
 import os
 import socket
 
@@ -45,6 +47,14 @@ def _worker(rank, world, port, L, errq):
         exp_prev = torch.full((n,), 100.0 * prv + 2.0, dtype=torch.float64)
         assert torch.equal(from_next, exp_next), (rank, from_next[:3])
         assert torch.equal(from_prev, exp_prev), (rank, from_prev[:3])
+        # the solver's hooks: the same routing, and sums over the ranks
+        comm = dd.DistributedComm(slabs, rank, (to_prev, to_next, from_next, from_prev))
+        from_next.zero_()
+        from_prev.zero_()
+        comm.exchange()
+        assert torch.equal(from_next, exp_next) and torch.equal(from_prev, exp_prev), rank
+        sums = comm.allreduce([float(rank + 1), 0.5, -2.0 * rank])
+        assert sums == [world * (world + 1) / 2, 0.5 * world, -float(world * (world - 1))], (rank, sums)
         assert slabs.next(rank) == nxt and slabs.prev(rank) == prv
         assert slabs.negate_to_prev(rank) == (rank == 0)
         assert slabs.negate_to_next(rank) == (rank == world - 1)
