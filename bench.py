@@ -514,11 +514,12 @@ def run_variants(ctx, G, fb, fx, lqcd, torch, t_f64, with_bicgstab=False):
 def run_multi_rhs(ctx, G, lqcd, torch, nrhs=12):
     """The 12 unit point sources (spin x colour at the origin) on the same
     24^3 x 48 field: one 12-RHS solve against 12 single-RHS solves, in
-    float-float / FP32 mixed precision and in float-float."""
+    float-float / FP32 and float-float / BF16 mixed precision and in
+    float-float."""
     from paper_1209_5942_gb300 import inputs
     b12 = inputs.point_sources(L)
     out = {}
-    for outer, inner, recon in (("df64", "f32", 12), ("df64", "df64", 18)):
+    for outer, inner, recon in (("df64", "f32", 12), ("df64", "bf16s", 12), ("df64", "df64", 18)):
         prm = lqcd.cg_params(tol=TOL, outer_prec=PREC_NAMES[outer], inner_prec=PREC_NAMES[inner],
                              max_iter=50000, sloppy_recon=recon, check_every=20)
         bd, _ = lqcd.alloc_field(L, lqcd.LQCD_FULL, lqcd.LQCD_F64, nrhs)
@@ -929,16 +930,19 @@ def run_config(args):
                                  "(FP32 times include the copy back into the FP64 field), beta=5.7, "
                                  "GFLOP/s with the paper's 3912 / 3846 flop per link"})
     elif c == "hop12":
-        # the multi-RHS F32 half hop (12 RHS, REC12 and 18-real links) against the
-        # single-RHS hop on 24^3 x 48 and 32^3 x 64 near-identity fields; the
-        # 12-RHS launches of the last lattice run inside the NVTX range "hop_multi"
+        # the multi-RHS half hop (12 RHS; F32 with REC12 and 18-real links, or
+        # --prec bf16s / f16s with REC12) against the single-RHS hop on 24^3 x 48
+        # and 32^3 x 64 near-identity fields; the 12-RHS REC12 launches of the
+        # last lattice run inside the NVTX range "hop_multi"
         res = {}
+        hp = PREC_NAMES[args.prec] if args.prec in ("bf16s", "f16s") else lqcd.LQCD_F32
         for Lc in ((32, 32, 32, 64), (24, 24, 24, 48)):
             U = torch.from_numpy(inputs.random_gauge(Lc, "near", seed=4100, eps=0.3)).cuda()
-            for recon in (12, 18):
+            for recon in ((12, 18) if hp == lqcd.LQCD_F32 else (12,)):
                 G = lqcd.lqcd_gauge_import(ctx, U, Lc, recon=recon)
-                one = time_half_hop_L(ctx, G, lqcd, torch, Lc, lqcd.LQCD_F32)
-                multi = time_hop_multi(ctx, G, lqcd, torch, Lc, 12, nvtx=(Lc[0] == 24 and recon == 12))
+                one = time_half_hop_L(ctx, G, lqcd, torch, Lc, hp)
+                multi = time_hop_multi(ctx, G, lqcd, torch, Lc, 12, prec=hp,
+                                       nvtx=(Lc[0] == 24 and recon == 12))
                 res[f"{'x'.join(map(str, Lc))}/rec{recon}"] = {
                     "single_ms": one["ms"], "single_GBs": one["gbs"], "multi12_ms": multi["ms"],
                     "multi12_GBs": multi["gbs"], "multi12_pct_hbm": 100 * multi["gbs"] / peaks["hbm_gbs"],
@@ -946,8 +950,8 @@ def run_config(args):
                     "bytes_per_rhs_site": multi["bytes_per_rhs_site"]}
                 G.free()
         config_line("multi-RHS hop", None, {"hop": res},
-                    {"workload": "F32 half hop, 12 right-hand sides vs one, 24^3x48 and 32^3x64, "
-                                 "exp(i 0.3 H) links"})
+                    {"workload": f"{[k for k, v in PREC_NAMES.items() if v == hp][0]} half hop, 12 right-hand "
+                                 "sides vs one, 24^3x48 and 32^3x64, exp(i 0.3 H) links"})
     elif c == "mrhs":
         # the default line's 12-RHS solve alone (24^3 x 48 bench field, 12 point
         # sources, float-float outer / FP32 inner): one warm-up solve, then one
@@ -975,6 +979,47 @@ def run_config(args):
                      "true_resid_max": max(s["true_resid"] for s in st), "launches": int(cnt.launches)},
                     {"workload": "24^3x48 exp(i 0.3 H) links, 12 point sources, DF64 outer / F32 inner, "
                                  "REC12 sloppy links, 1e-10"})
+    elif c == "dd":
+        # the domain-decomposed FP64 CG (t split into nt domains held in one
+        # process, faces moved by device copies) against lqcd_cg_solve on the
+        # default 24^3 x 48 workload: the cost of the decomposition itself
+        # (face packs, split hops, one host synchronisation per norm)
+        from paper_1209_5942_gb300 import dd
+        U, b = make_inputs()
+        G = lqcd.lqcd_gauge_import(ctx, torch.from_numpy(U).cuda(), L, recon=18)
+        prm = lqcd.cg_params(tol=TOL, outer_prec=lqcd.LQCD_F64, max_iter=50000)
+        bd = torch.from_numpy(b).cuda()
+        x = torch.zeros_like(bd)
+        fb, fx = lqcd.field(bd, lqcd.LQCD_LAYOUT_LEXI), lqcd.field(x, lqcd.LQCD_LAYOUT_LEXI)
+        lqcd.lqcd_cg_solve(ctx, G, fb, fx, KAPPA, MU, prm)
+        t1, st1 = _timed(torch, lambda: lqcd.lqcd_cg_solve(ctx, G, fb, fx, KAPPA, MU, prm))
+        res = {"single_domain": {"solve_s": t1, "iters": st1[0]["iters"], "true_resid": st1[0]["true_resid"]}}
+        G.free()
+        for nt in (1, 2, 4):
+            slabs = dd.TimeSlabs(L, nt)
+            Ll = slabs.local_L
+            gs, bs, xs, keep = [], [], [], []
+            for d in range(nt):
+                gs.append(lqcd.lqcd_gauge_import(ctx, torch.from_numpy(U[slabs.block(d)]).cuda(), Ll, recon=18,
+                                                 antiperiodic_t=False))
+                bdd, _ = lqcd.alloc_field(Ll, lqcd.LQCD_FULL, lqcd.LQCD_F64)
+                xdd, _ = lqcd.alloc_field(Ll, lqcd.LQCD_FULL, lqcd.LQCD_F64)
+                f = lqcd.field(bdd, lqcd.LQCD_LAYOUT_EO)
+                lqcd.lqcd_spinor_pack(ctx, Ll, torch.from_numpy(b[slabs.block(d)]).cuda(), f, antiperiodic_t=False)
+                bs.append(f)
+                xs.append(lqcd.field(xdd, lqcd.LQCD_LAYOUT_EO))
+                keep.append((bdd, xdd))
+            faces = [dd.face_buffers(slabs, lqcd.LQCD_F64) for _ in range(nt)]
+            dd.cg_solve_local_domains(ctx, slabs, gs, bs, xs, KAPPA, MU, prm, faces=faces)
+            t, st = _timed(torch, lambda: dd.cg_solve_local_domains(ctx, slabs, gs, bs, xs, KAPPA, MU, prm,
+                                                                    faces=faces))
+            res[f"nt{nt}"] = {"solve_s": t, "iters": st["iters"], "true_resid": st["true_resid"],
+                              "vs_single_domain": t / t1}
+            for G_ in gs:
+                G_.free()
+        config_line("domain-decomposed CG", None, {"dd": res},
+                    {"workload": "24^3x48 exp(i 0.3 H) links, kappa=0.16, 2 kappa mu=0.005, FP64 CG to 1e-10; "
+                                 "t split into nt domains on one GPU (faces by device copies)"})
     elif c == "sweep":
         res = {}
         for ns in (16, 24, 32, 48):
@@ -1018,10 +1063,15 @@ def time_hop_multi(ctx, G, lqcd, torch, Lc, nrhs, prec=2, reps=10, nvtx=False):
     """Multi-RHS half hop: counted bytes read each link once for all RHS."""
     n_half, sb = lqcd.field_bytes(Lc, lqcd.LQCD_EVEN, prec, nrhs)
     gen = torch.Generator(device="cuda").manual_seed(11)
-    din = torch.randn(n_half // 4, dtype=torch.float32, device="cuda", generator=gen).view(torch.float64)
+    din = torch.randn(n_half // 4, dtype=torch.float32, device="cuda", generator=gen)
+    if sb:  # 16-bit formats: finite stored values below 1, unit site scales
+        din = (din.view(torch.int32) & 0x3F7F3F7F).view(torch.float32)
+    din = din.view(torch.float64)
     dout = torch.zeros_like(din)
-    fi = lqcd.field(din, lqcd.LQCD_LAYOUT_EO, prec, nrhs)
-    fo = lqcd.field(dout, lqcd.LQCD_LAYOUT_EO, prec, nrhs)
+    s_in = torch.ones(max(sb // 4, 1), dtype=torch.float32, device="cuda") if sb else None
+    s_out = torch.zeros_like(s_in) if sb else None
+    fi = lqcd.field(din, lqcd.LQCD_LAYOUT_EO, prec, nrhs, s_in)
+    fo = lqcd.field(dout, lqcd.LQCD_LAYOUT_EO, prec, nrhs, s_out)
     lqcd.lqcd_dslash(ctx, G, fi, fo, lqcd.LQCD_EVEN, 0)
     lqcd.lib().lqcd_reset_counters(ctx.handle)
     if nvtx:  # ncu --nvtx --nvtx-include hop_multi/ captures these launches
@@ -1053,7 +1103,8 @@ def main():
     ap.add_argument("--variants", action="store_true", help="also BiCGStab variants")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the precision variants and the 12-RHS comparison")
-    ap.add_argument("--config", default="2", choices=["1", "2", "3", "4a", "4b", "5", "C", "hb", "sweep", "hop12", "mrhs"],
+    ap.add_argument("--config", default="2", choices=["1", "2", "3", "4a", "4b", "5", "C", "hb", "sweep", "hop12", "mrhs",
+                                                     "dd"],
                     help="2 (default): the 24^3x48 contract line; others print their own line")
     ap.add_argument("--sweeps", type=int, default=200, help="heatbath sweeps for configs 3, 4a, 5")
     ap.add_argument("--trajs", type=int, default=10, help="measured HMC trajectories for config 5")
