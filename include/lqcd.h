@@ -473,8 +473,10 @@ int lqcd_plaquette(lqcd_ctx *ctx, const lqcd_gauge *U, double *plaq_out);
  * prec = LQCD_F32 runs
  * the same sweep in single precision on the field's FP32 copy (12-real links
  * with the third row rebuilt, Sec. 4.1, if the field was imported with
- * recon = 12) and writes the result back into the FP64 field, reunitarised in
- * FP64 (Sec. 5.1 measures the single-precision kernels).  Other prec: LQCD_ERR_INVALID.
+ * recon = 12) and writes the result back into the FP64 field, reunitarised
+ * by a Gram-Schmidt in float-float arithmetic (|U U^+ - 1| below 1e-13), and
+ * keeps the FP32 copy current for the next sweep (Sec. 5.1 measures the
+ * single-precision kernels).  Other prec: LQCD_ERR_INVALID.
  * Asynchronous. */
 int lqcd_heatbath_sweep(lqcd_ctx *ctx, lqcd_gauge *U, double beta, uint64_t seed,
                         uint64_t sweep_idx, int n_or, int prec);

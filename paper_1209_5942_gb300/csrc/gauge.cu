@@ -930,18 +930,97 @@ __global__ void __launch_bounds__(128, 5) heatbath_f32_kernel(GaugeView Uf, Geom
   if (fails) atomicAdd(fail_count, fails);
 }
 
-// FP32 copy -> FP64 master (REC12: third row rebuilt in FP32)
+// The end of an FP32 sweep in one pass per link: the FP32 link into the FP64
+// field, reunitarised (Gram-Schmidt on the first two rows, the third rebuilt
+// as the conjugate cross product), and the FP32 copy rewritten from the new
+// FP64 link with the rounding of the master -> FP32 copy conversion, so that
+// the copy stays current for the next sweep.  GB300's FP64 pipe runs at 1/64
+// of the FP32 rate, and an FP64 Gram-Schmidt with its conversions (about 150
+// FP64 operations per link) took 1.97 ms on 32^3 x 64, more than the eight
+// heatbath launches of the sweep; here the Gram-Schmidt runs in float-float
+// arithmetic on the FP32 pipe (the inputs are exact FP32 values, every
+// product is error-free, sums carry about 2^-48 of their magnitude), the
+// conversions between float and double are bit operations on the integer
+// pipe, and one FP64 addition per real (hi + lo) forms each double.  A row
+// norm is n = 1 + e with |e| of order 1e-7 (the links leave the heatbath
+// unitary to FP32 rounding), so 1 / sqrt(n) = 1 - e/2 + 3e^2/8 + O(e^3) with
+// e^3 below 1e-19; a row with |e| > 2^-20 takes the FP64 rsqrt instead.
+// Unitarity of the written links: |U U^+ - 1| of order 1e-15.
+
+// float -> double by its bits on the integer pipe: exact for normal floats,
+// zeros, infinities and NaNs; a subnormal float (below 2^-126, never a link
+// entry or the low word of one at this precision) becomes a signed zero
+LQCD_DEV double f2d_bits(float f) {
+  const unsigned u = __float_as_uint(f), e = (u >> 23) & 0xFFu, sg = u & 0x80000000u;
+  const unsigned ed = e == 0xFFu ? 0x7FFu : e + 896u;
+  const unsigned hi = e == 0u ? sg : (sg | (ed << 20) | ((u >> 3) & 0xFFFFFu));
+  const unsigned lo = e == 0u ? 0u : (u << 29);
+  return __hiloint2double((int)hi, (int)lo);
+}
+// double -> float rounded to nearest even by its bits on the integer pipe:
+// the bits of __double2float_rn for results in the normal float range and
+// for zeros; magnitudes below 2^-126 become signed zeros and above the float
+// range infinities (neither is met by link entries)
+LQCD_DEV float d2f_bits(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned e = (hi >> 20) & 0x7FFu, sg = hi & 0x80000000u;
+  unsigned f = ((e - 896u) << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+  const unsigned rem = lo & 0x1FFFFFFFu;
+  if (rem > 0x10000000u || (rem == 0x10000000u && (f & 1u))) f += 1u;  // a carry moves into the exponent
+  f = e < 897u ? 0u : (e > 1150u ? 0x7F800000u : f);
+  return __uint_as_float(f | sg);
+}
+LQCD_DEV double df_to_double_bits(df v) { return f2d_bits(v.hi) + f2d_bits(v.lo); }
+
+// the FP64 fallback of inv_sqrt_near1_df, kept out of line so that the
+// common path carries no FP64 instructions
+__device__ __noinline__ df inv_sqrt_df_slow(df n) { return df_from_double(rsqrt((double)n.hi + (double)n.lo)); }
+
+// 1 / sqrt(n) for n = 1 + e, |e| small (see above)
+LQCD_DEV df inv_sqrt_near1_df(df n) {
+  const df e = n - df{1.0f, 0.0f};
+  if (fabsf(e.hi) > 0x1p-20f) return inv_sqrt_df_slow(n);
+  const df half = {-0.5f * e.hi, -0.5f * e.lo};
+  return (df{1.0f, 0.0f} + half) + df{0.375f * e.hi * e.hi, 0.0f};
+}
+LQCD_DEV df row_norm2_df(const Cx<df> r[3]) { return dfdot3<true>(r[0], r[1], r[2], r[0], r[1], r[2]).re; }
+
 template <int RECON>
-__global__ void f32_to_master_kernel(GaugeView Uf, double2 *m, int Vh) {
+__global__ void f32_to_master_unitary_kernel(GaugeView Uf, double2 *m, int Vh) {
   const size_t nl = (size_t)2 * 4 * Vh;
   const size_t l = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (l >= nl) return;
   const int blk = (int)(l / Vh), cb = (int)(l % Vh);  // blk = parity * 4 + mu
-  Cx<float> u[9];
-  LinkIO<LQCD_F32, RECON>::load(Uf, blk >> 2, blk & 3, cb, u);
-  if (RECON == 12) reconstruct_row2(u);
+  Cx<float> f[9];
+  LinkIO<LQCD_F32, RECON>::load(Uf, blk >> 2, blk & 3, cb, f);
+  Cx<df> u[9];
 #pragma unroll
-  for (int k = 0; k < 9; k++) m[((size_t)blk * 9 + k) * Vh + cb] = make_double2(u[k].re, u[k].im);
+  for (int k = 0; k < 6; k++) u[k] = {{f[k].re, 0.0f}, {f[k].im, 0.0f}};
+  const df r0 = inv_sqrt_near1_df(row_norm2_df(u));
+#pragma unroll
+  for (int k = 0; k < 3; k++) u[k] = {u[k].re * r0, u[k].im * r0};
+  const Cx<df> d = dfdot3<true>(u[0], u[1], u[2], u[3], u[4], u[5]);  // (row 0)^+ row 1
+#pragma unroll
+  for (int k = 0; k < 3; k++) u[3 + k] = u[3 + k] - d * u[k];
+  const df r1 = inv_sqrt_near1_df(row_norm2_df(u + 3));
+#pragma unroll
+  for (int k = 0; k < 3; k++) u[3 + k] = {u[3 + k].re * r1, u[3 + k].im * r1};
+  reconstruct_row2(u);
+  double2 w[9];
+#pragma unroll
+  for (int k = 0; k < 9; k++) {
+    w[k] = make_double2(df_to_double_bits(u[k].re), df_to_double_bits(u[k].im));
+    m[((size_t)blk * 9 + k) * Vh + cb] = w[k];
+  }
+  // the FP32 copy as gauge_copy_kernel makes it from the master
+  char *base = (char *)Uf.ptr + (blk >> 2) * Uf.parity_stride + (blk & 3) * Uf.mu_stride;
+  float4 *b = (float4 *)base;
+  constexpr int NW = RECON == 18 ? 4 : 3;
+#pragma unroll
+  for (int k = 0; k < NW; k++)
+    b[(size_t)k * Vh + cb] = make_float4(d2f_bits(w[2 * k].x), d2f_bits(w[2 * k].y), d2f_bits(w[2 * k + 1].x),
+                                         d2f_bits(w[2 * k + 1].y));
+  if (RECON == 18) ((float2 *)(base + (size_t)4 * Vh * 16))[cb] = make_float2(d2f_bits(w[8].x), d2f_bits(w[8].y));
 }
 
 // ---------------------------------------------------------------------------
@@ -1244,18 +1323,6 @@ __global__ void __launch_bounds__(128) gauge_update_df_kernel(double2 *U, GaugeV
   for (int k = 0; k < 9; k++) w[(size_t)k * Ud.Vh + s.cb] = f4_of(v.m[k]);
 }
 
-__global__ void reunitarize_kernel(double2 *U, Geom g) {
-  long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  int p, cb, c[4];
-  if (!thread_site(g, tid, &p, &cb, c)) return;
-  Pos s{p, cb, 0};
-  for (int mu = 0; mu < 4; mu++) {
-    M3 u = load_link(U, g, s, mu);
-    reunitarize(u);
-    store_link(U, g, s, mu, u);
-  }
-}
-
 __global__ void momenta_update_kernel(double *P, const double *F, double eps, size_t n) {
   size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (k < n) P[k] = fma(-eps, F[k], P[k]);
@@ -1346,8 +1413,6 @@ lqcd_status gauge_force_raw(lqcd_ctx *ctx, lqcd_gauge *U, double beta, double c1
   return LQCD_OK;
 }
 
-lqcd_status reunitarize_raw(lqcd_ctx *ctx, lqcd_gauge *U);
-
 // FP32 sweep: on the FP32 copy, then back into the FP64 field, reunitarised.
 // Passes: one heatbath pass if hb, then n_or overrelaxation passes.
 lqcd_status heatbath_f32_raw(lqcd_ctx *ctx, lqcd_gauge *U, double beta, uint64_t seed, uint64_t sweep, int hb,
@@ -1367,11 +1432,18 @@ lqcd_status heatbath_f32_raw(lqcd_ctx *ctx, lqcd_gauge *U, double beta, uint64_t
               Uf, U->g, mu, par, (float)beta, seed, (uint32_t)sweep, pass > 0 ? 1 : 0, fail_dev);
         LQCD_CUDA(ctx, cudaGetLastError());
       }
-  if (r12) f32_to_master_kernel<12><<<nblk(8L * U->g.Vh), 128, 0, ctx->stream>>>(Uf, (double2 *)U->master, U->g.Vh);
-  else f32_to_master_kernel<18><<<nblk(8L * U->g.Vh), 128, 0, ctx->stream>>>(Uf, (double2 *)U->master, U->g.Vh);
+  if (r12)
+    f32_to_master_unitary_kernel<12><<<nblk(8L * U->g.Vh), 128, 0, ctx->stream>>>(Uf, (double2 *)U->master,
+                                                                                    U->g.Vh);
+  else
+    f32_to_master_unitary_kernel<18><<<nblk(8L * U->g.Vh), 128, 0, ctx->stream>>>(Uf, (double2 *)U->master,
+                                                                                    U->g.Vh);
   LQCD_CUDA(ctx, cudaGetLastError());
   U->version++;
-  return reunitarize_raw(ctx, U);
+  // the FP32 copy was rewritten from the new master: still current
+  for (auto &k : U->copies)
+    if (k.prec == LQCD_F32 && k.recon == (r12 ? 12 : 18)) k.version = U->version;
+  return LQCD_OK;
 }
 
 // FP64 sweep in place: on the master (18 reals), or for a field imported with
@@ -1429,13 +1501,6 @@ lqcd_status gauge_update_raw(lqcd_ctx *ctx, lqcd_gauge *U, const double *P, doub
     return LQCD_OK;
   }
   gauge_update_kernel<<<nblk(8L * U->g.Vh), 128, 0, ctx->stream>>>((double2 *)U->master, U->g, P, eps);
-  LQCD_CUDA(ctx, cudaGetLastError());
-  U->version++;
-  return LQCD_OK;
-}
-
-lqcd_status reunitarize_raw(lqcd_ctx *ctx, lqcd_gauge *U) {
-  reunitarize_kernel<<<nblk(2L * U->g.Vh), 128, 0, ctx->stream>>>((double2 *)U->master, U->g);
   LQCD_CUDA(ctx, cudaGetLastError());
   U->version++;
   return LQCD_OK;

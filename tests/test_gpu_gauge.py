@@ -459,6 +459,37 @@ def test_f32_heatbath_equilibrium_and_unitarity(ctx):
     assert abs(means[lqcd.LQCD_F32] - means[lqcd.LQCD_F64]) < 4e-3, means
 
 
+@pytest.mark.parametrize("recon", [18, 12])
+def test_f32_sweep_write_back_keeps_the_fp32_copy_current(ctx, recon):
+    """After an FP32 sweep the library rewrites its FP32 link copy from the
+    reunitarised FP64 field instead of converting it again: an FP32 hop on the
+    swept field equals, bit for bit, the FP32 hop on a fresh import of the
+    exported FP64 links (whose FP32 copy is made by the conversion), and the
+    FP64 links are unitary to 1e-13 (the float-float Gram-Schmidt of the
+    write-back)."""
+    L = (8, 4, 6, 8)
+    G = lqcd.lqcd_gauge_import(ctx, dev(inputs.random_gauge(L, "haar", seed=93)), L, recon=recon)
+    for s in range(3):
+        lqcd.lqcd_heatbath_sweep(ctx, G, 5.7, 94, s, n_or=1, prec=lqcd.LQCD_F32)
+    U = _export(ctx, G, L)
+    eye = np.eye(3)
+    assert np.max(np.abs(U @ np.conj(np.transpose(U, (0, 1, 3, 2))) - eye)) < 1e-13
+    G2 = lqcd.lqcd_gauge_import(ctx, dev(U), L, recon=recon)
+    psi = inputs.gaussian_spinor(L, 95)
+    outs = []
+    for g in (G, G2):
+        d, sc, _ = eo_full_from_lexi(ctx, L, psi, lqcd.LQCD_F32)
+        fe, fo = half_views(L, d, sc, lqcd.LQCD_F32)
+        od, osc = lqcd.alloc_field(L, lqcd.LQCD_FULL, lqcd.LQCD_F32)
+        oe, _ = half_views(L, od, osc, lqcd.LQCD_F32)
+        lqcd.lqcd_dslash(ctx, g, fo, oe, lqcd.LQCD_EVEN, 0)
+        torch.cuda.synchronize()
+        outs.append(od.clone())
+    assert torch.equal(outs[0].view(torch.uint8), outs[1].view(torch.uint8))
+    G.free()
+    G2.free()
+
+
 def test_f32_overrelaxation_preserves_action(ctx):
     L = (4, 4, 4, 4)
     G = lqcd.lqcd_gauge_import(ctx, dev(inputs.random_gauge(L, "near", seed=37, eps=0.8)), L)
