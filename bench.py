@@ -913,7 +913,7 @@ def run_config(args):
             for s_ in range(5):
                 lqcd.lqcd_heatbath_sweep(ctx, G, 5.7, 9, s_)
             row = {}
-            for pn in ("f64", "f32"):
+            for pn in ("f64", "df64", "f32"):
                 pr = PREC_NAMES[pn]
                 th, _ = _timed(torch, lambda: lqcd.lqcd_heatbath_sweep(ctx, G, 5.7, 9, 100, prec=pr), 5)
                 tho, _ = _timed(torch, lambda: lqcd.lqcd_heatbath_sweep(ctx, G, 5.7, 9, 101, n_or=4, prec=pr), 5)
@@ -926,8 +926,9 @@ def run_config(args):
             res["x".join(map(str, Lc))] = row
             G.free()
         config_line("heatbath", None, {"hb": res},
-                    {"workload": "Cabibbo-Marinari heatbath and overrelaxation sweeps, FP64 and FP32 "
-                                 "(FP32 times include the copy back into the FP64 field), beta=5.7, "
+                    {"workload": "Cabibbo-Marinari heatbath and overrelaxation sweeps, FP64, FP64 with "
+                                 "float-float staples (df64) and FP32 (FP32 times include the write-back "
+                                 "into the FP64 field), beta=5.7, "
                                  "GFLOP/s with the paper's 3912 / 3846 flop per link"})
     elif c == "hop12":
         # the multi-RHS half hop (12 RHS; F32 with REC12 and 18-real links, or

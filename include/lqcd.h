@@ -470,7 +470,11 @@ int lqcd_plaquette(lqcd_ctx *ctx, const lqcd_gauge *U, double *plaq_out);
  * left multiplications keep it unitary to rounding; a field imported with
  * recon = 12 is updated through its 12-real FP64 copy, the third row rebuilt
  * on every load, Sec. 4.1, and written back with the third row rebuilt);
- * prec = LQCD_F32 runs
+ * prec = LQCD_DF64 runs the FP64 sweep with its staple sums in float-float
+ * arithmetic on the FP32 pipe (2^-46 relative, from the field's 18-real
+ * float-float copy, which the sweep keeps current; the SU(2) samplers, the
+ * subgroup products and the links stay in IEEE FP64; 18-real links whatever
+ * the import format); prec = LQCD_F32 runs
  * the same sweep in single precision on the field's FP32 copy (12-real links
  * with the third row rebuilt, Sec. 4.1, if the field was imported with
  * recon = 12) and writes the result back into the FP64 field, reunitarised

@@ -665,19 +665,18 @@ LQCD_DEV void hb_store(const GaugeView &Uv, const Pos &s, int mu, const M3 &u) {
   for (int k = 0; k < (RECON == 18 ? 9 : 6); k++) b[(size_t)k * Uv.Vh + s.cb] = make_double2(u.m[k].re, u.m[k].im);
 }
 
-template <int RECON>
-__global__ void __launch_bounds__(128) heatbath_kernel(GaugeView Uv, Geom g, int mu, int par, double beta,
-                                                       uint64_t seed, uint32_t sweep, int overrelax,
-                                                       unsigned int *fail_count) {
-  int cb = blockIdx.x * blockDim.x + threadIdx.x;
-  if (cb >= g.Vh) return;
-  Site st = site_of(g, par, cb);
-  int c[4] = {st.x, st.y, st.z, st.t};
-  Pos s = at(g, c);
-  M3 A = staple_with([&](const Pos &q, int nu) { return hb_load<RECON>(Uv, q, nu); }, g, c, mu);
-  M3 u = hb_load<RECON>(Uv, s, mu);
-  const int SG[3][2] = {{0, 1}, {1, 2}, {0, 2}};
+// The Cabibbo-Marinari update of one link u with staple sum A: for each of
+// the three SU(2) subgroups a Kennedy-Pendleton heatbath draw (or, with
+// overrelax, the reflection v = (w_hat^+)^2) left-multiplied onto u.  Returns
+// the number of subgroup updates skipped (degenerate staple or sampler
+// failure).
+LQCD_DEV unsigned hb_update_link(M3 &u, const M3 &A, double beta, const Pos &s, int mu, uint32_t sweep,
+                                 uint64_t seed, int overrelax) {
   unsigned fails = 0;
+  const int SG[3][2] = {{0, 1}, {1, 2}, {0, 2}};
+  // unrolled: the subgroup's rows i, j are then compile-time indices and u,
+  // W stay in registers instead of local memory
+#pragma unroll
   for (int sg = 0; sg < 3; sg++) {
     const int i = SG[sg][0], j = SG[sg][1];
     M3 W = mmul(u, A);
@@ -731,6 +730,21 @@ __global__ void __launch_bounds__(128) heatbath_kernel(GaugeView Uv, Geom g, int
       u.m[3 * j + q] = rj[q];
     }
   }
+  return fails;
+}
+
+template <int RECON>
+__global__ void __launch_bounds__(128) heatbath_kernel(GaugeView Uv, Geom g, int mu, int par, double beta,
+                                                       uint64_t seed, uint32_t sweep, int overrelax,
+                                                       unsigned int *fail_count) {
+  int cb = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cb >= g.Vh) return;
+  Site st = site_of(g, par, cb);
+  int c[4] = {st.x, st.y, st.z, st.t};
+  Pos s = at(g, c);
+  M3 A = staple_with([&](const Pos &q, int nu) { return hb_load<RECON>(Uv, q, nu); }, g, c, mu);
+  M3 u = hb_load<RECON>(Uv, s, mu);
+  const unsigned fails = hb_update_link(u, A, beta, s, mu, sweep, seed, overrelax);
   hb_store<RECON>(Uv, s, mu, u);
   if (fails) atomicAdd(fail_count, fails);
 }
@@ -1021,6 +1035,60 @@ __global__ void f32_to_master_unitary_kernel(GaugeView Uf, double2 *m, int Vh) {
     b[(size_t)k * Vh + cb] = make_float4(d2f_bits(w[2 * k].x), d2f_bits(w[2 * k].y), d2f_bits(w[2 * k + 1].x),
                                          d2f_bits(w[2 * k + 1].y));
   if (RECON == 18) ((float2 *)(base + (size_t)4 * Vh * 16))[cb] = make_float2(d2f_bits(w[8].x), d2f_bits(w[8].y));
+}
+
+// The FP64-class heatbath with its staple sum in float-float: the twelve
+// 3x3 products of the six staples (about half the FP64 work of a link update)
+// run as error-free complex dot products on the FP32 pipe from the field's
+// float-float copy, and the sum is handed to the FP64 update (the SU(2)
+// samplers, the subgroup products and the link itself stay in IEEE FP64).
+// The staple differs from the FP64 one by rounding of order 2^-46 relative;
+// the link is written into the FP64 field and, as df_from_double would split
+// it, into the float-float copy, which the next class of the sweep reads.
+LQCD_DEV M3 staple_df(const GaugeView &Ud, const Geom &g, const int c[4], int mu) {
+  M3d A;
+#pragma unroll
+  for (int e = 0; e < 9; e++) A.m[e] = czero<df>();
+  int cpm[4] = {c[0], c[1], c[2], c[3]};
+  coords_shift(g, cpm, mu, +1);
+#pragma unroll 1
+  for (int k = 0; k < 6; k++) {
+    const int nu = (k >> 1) + ((k >> 1) >= mu ? 1 : 0), sg = (k & 1) ? -1 : 1;
+    int cps[4] = {c[0], c[1], c[2], c[3]};
+    coords_shift(g, cps, nu, sg);
+    // U_{s nu}(x + mu) U_mu(x + s nu)^+ U_{s nu}(x)^+
+    M3d t = dmul_nd(signed_link_d(Ud, g, cpm, nu, sg), load_link_d(Ud, at(g, cps), mu));
+    t = dmul_nd(t, signed_link_d(Ud, g, c, nu, sg));
+    add_lazy_m(A, t);
+  }
+  M3 r;
+#pragma unroll
+  for (int e = 0; e < 9; e++) r.m[e] = {df_to_double_bits(A.m[e].re), df_to_double_bits(A.m[e].im)};
+  return r;
+}
+// df_from_double on the integer pipe: the high word rounded to nearest, the
+// low word the rounded remainder (one FP64 subtraction)
+LQCD_DEV float4 df_word_of(C z) {
+  const float rh = d2f_bits(z.re), ih = d2f_bits(z.im);
+  return make_float4(rh, ih, d2f_bits(z.re - f2d_bits(rh)), d2f_bits(z.im - f2d_bits(ih)));
+}
+
+__global__ void __launch_bounds__(128) heatbath_df_kernel(GaugeView Um, GaugeView Ud, Geom g, int mu, int par,
+                                                          double beta, uint64_t seed, uint32_t sweep,
+                                                          int overrelax, unsigned int *fail_count) {
+  int cb = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cb >= g.Vh) return;
+  Site st = site_of(g, par, cb);
+  int c[4] = {st.x, st.y, st.z, st.t};
+  Pos s = at(g, c);
+  const M3 A = staple_df(Ud, g, c, mu);
+  M3 u = hb_load<18>(Um, s, mu);
+  const unsigned fails = hb_update_link(u, A, beta, s, mu, sweep, seed, overrelax);
+  hb_store<18>(Um, s, mu, u);
+  float4 *w = (float4 *)((char *)Ud.ptr + s.p * Ud.parity_stride + mu * Ud.mu_stride);
+#pragma unroll
+  for (int e = 0; e < 9; e++) w[(size_t)e * Ud.Vh + s.cb] = df_word_of(u.m[e]);
+  if (fails) atomicAdd(fail_count, fails);
 }
 
 // ---------------------------------------------------------------------------
@@ -1443,6 +1511,27 @@ lqcd_status heatbath_f32_raw(lqcd_ctx *ctx, lqcd_gauge *U, double beta, uint64_t
   // the FP32 copy was rewritten from the new master: still current
   for (auto &k : U->copies)
     if (k.prec == LQCD_F32 && k.recon == (r12 ? 12 : 18)) k.version = U->version;
+  return LQCD_OK;
+}
+
+// FP64-class sweep with float-float staples (heatbath_df_kernel) on the
+// master and the float-float copy, which stays current.  Passes as
+// heatbath_f32_raw.
+lqcd_status heatbath_df_raw(lqcd_ctx *ctx, lqcd_gauge *U, double beta, uint64_t seed, uint64_t sweep, int hb,
+                            int n_or, unsigned int *fail_dev) {
+  GaugeView Um, Ud;
+  LQCD_TRY(gauge_view(ctx, U, LQCD_F64, 18, &Um));
+  LQCD_TRY(gauge_view(ctx, U, LQCD_DF64, 18, &Ud));
+  for (int pass = hb ? 0 : 1; pass <= n_or; pass++)
+    for (int mu = 0; mu < 4; mu++)
+      for (int par = 0; par < 2; par++) {
+        heatbath_df_kernel<<<nblk(U->g.Vh), 128, 0, ctx->stream>>>(Um, Ud, U->g, mu, par, beta, seed,
+                                                                  (uint32_t)sweep, pass > 0 ? 1 : 0, fail_dev);
+        LQCD_CUDA(ctx, cudaGetLastError());
+      }
+  U->version++;
+  for (auto &k : U->copies)
+    if (k.prec == LQCD_DF64 && k.recon == 18) k.version = U->version;
   return LQCD_OK;
 }
 

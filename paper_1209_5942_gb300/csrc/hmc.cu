@@ -26,6 +26,8 @@ lqcd_status heatbath_f32_raw(lqcd_ctx *ctx, lqcd_gauge *U, double beta, uint64_t
                              unsigned int *fail_dev);
 lqcd_status heatbath_raw(lqcd_ctx *ctx, lqcd_gauge *U, double beta, uint64_t seed, uint64_t sweep, int hb, int n_or,
                          unsigned int *fail_dev);
+lqcd_status heatbath_df_raw(lqcd_ctx *ctx, lqcd_gauge *U, double beta, uint64_t seed, uint64_t sweep, int hb, int n_or,
+                         unsigned int *fail_dev);
 lqcd_status momenta_raw(lqcd_ctx *ctx, long V, double *P, uint64_t seed, uint32_t traj);
 lqcd_status gaussian_spinor_raw(lqcd_ctx *ctx, const Geom &g, void *eo_full, int parity, uint64_t seed,
                                 uint32_t traj);
@@ -245,10 +247,12 @@ extern "C" int lqcd_heatbath_sweep(lqcd_ctx *ctx, lqcd_gauge *U, double beta, ui
   LQCD_TRY(check_u(ctx, U));
   if (!(beta >= 0.0) || !std::isfinite(beta)) return fail(ctx, LQCD_ERR_INVALID, "beta must be finite, >= 0");
   if (n_or < 0 || n_or > 64) return fail(ctx, LQCD_ERR_INVALID, "n_or out of [0, 64]");
-  if (prec != LQCD_F64 && prec != LQCD_F32) return fail(ctx, LQCD_ERR_INVALID, "prec must be LQCD_F64 or LQCD_F32");
+  if (prec != LQCD_F64 && prec != LQCD_F32 && prec != LQCD_DF64)
+    return fail(ctx, LQCD_ERR_INVALID, "prec must be LQCD_F64, LQCD_DF64 or LQCD_F32");
   unsigned int *fails = (unsigned int *)ctx->partials;  // scratch word; not read by anyone else
   LQCD_CUDA(ctx, cudaMemsetAsync(fails, 0, sizeof(unsigned int), ctx->stream));
   if (prec == LQCD_F32) return heatbath_f32_raw(ctx, U, beta, seed, sweep_idx, 1, n_or, fails);
+  if (prec == LQCD_DF64) return heatbath_df_raw(ctx, U, beta, seed, sweep_idx, 1, n_or, fails);
   return heatbath_raw(ctx, U, beta, seed, sweep_idx, 1, n_or, fails);
 }
 
@@ -256,10 +260,12 @@ extern "C" int lqcd_overrelax_sweep(lqcd_ctx *ctx, lqcd_gauge *U, int n_or, int 
   if (!ctx) return LQCD_ERR_INVALID;
   LQCD_TRY(check_u(ctx, U));
   if (n_or < 1 || n_or > 64) return fail(ctx, LQCD_ERR_INVALID, "n_or out of [1, 64]");
-  if (prec != LQCD_F64 && prec != LQCD_F32) return fail(ctx, LQCD_ERR_INVALID, "prec must be LQCD_F64 or LQCD_F32");
+  if (prec != LQCD_F64 && prec != LQCD_F32 && prec != LQCD_DF64)
+    return fail(ctx, LQCD_ERR_INVALID, "prec must be LQCD_F64, LQCD_DF64 or LQCD_F32");
   unsigned int *fails = (unsigned int *)ctx->partials;  // scratch word; not read by anyone else
   LQCD_CUDA(ctx, cudaMemsetAsync(fails, 0, sizeof(unsigned int), ctx->stream));
   if (prec == LQCD_F32) return heatbath_f32_raw(ctx, U, 0.0, 0, 0, 0, n_or, fails);
+  if (prec == LQCD_DF64) return heatbath_df_raw(ctx, U, 0.0, 0, 0, 0, n_or, fails);
   return heatbath_raw(ctx, U, 0.0, 0, 0, 0, n_or, fails);
 }
 

@@ -144,6 +144,48 @@ def test_heatbath_sweep_matches_oracle(ctx, oracle, recon):
     assert np.max(np.abs(got @ np.conj(np.transpose(got, (0, 1, 3, 2))) - eye)) < 1e-12
 
 
+@pytest.mark.parametrize("recon", [18, 12])
+def test_heatbath_df64_staples_match_oracle(ctx, oracle, recon):
+    """The FP64-class sweep with its staples in float-float (prec = LQCD_DF64:
+    twelve 3x3 products per link on the FP32 pipe, the SU(2) samplers and the
+    update in IEEE FP64): three sweeps link by link against the oracle, as the
+    FP64 sweep; the staples round at 2^-46 relative instead of 2^-53, so a
+    rejection decision flips only where a uniform falls that close to its
+    threshold."""
+    L = (4, 4, 4, 4)
+    U = inputs.random_gauge(L, "haar", seed=35)
+    G = lqcd.lqcd_gauge_import(ctx, dev(U), L, recon=recon)
+    Uo = U.copy()
+    for sweep in range(3):
+        lqcd.lqcd_heatbath_sweep(ctx, G, 5.7, 4242, sweep, prec=lqcd.LQCD_DF64)
+        Uo, fails = oracle.heatbath_sweep(Uo, L, 5.7, 4242, sweep)
+        assert fails == 0
+    got = _export(ctx, G, L)
+    diff = np.abs(got - Uo).max(axis=(2, 3))
+    flips = int(np.sum(diff > 1e-9))
+    assert flips <= max(2, diff.size // 500), flips
+    assert np.median(diff) < 1e-12
+    eye = np.eye(3)
+    assert np.max(np.abs(got @ np.conj(np.transpose(got, (0, 1, 3, 2))) - eye)) < 1e-12
+
+
+def test_heatbath_df64_equilibrium_plaquette(ctx):
+    """The float-float-staple sweep and the FP64 sweep reach the same
+    plaquette at beta = 5.7 (40 measured sweeps after 30)."""
+    L = (8, 8, 8, 8)
+    means = {}
+    for prec in (lqcd.LQCD_F64, lqcd.LQCD_DF64):
+        G = lqcd.lqcd_gauge_import(ctx, dev(inputs.random_gauge(L, "cold")), L)
+        vals = []
+        for s in range(70):
+            lqcd.lqcd_heatbath_sweep(ctx, G, 5.7, 97, s, n_or=1, prec=prec)
+            if s >= 30:
+                vals.append(lqcd.lqcd_plaquette(ctx, G))
+        means[prec] = np.mean(vals)
+        G.free()
+    assert abs(means[lqcd.LQCD_DF64] - means[lqcd.LQCD_F64]) < 4e-3, means
+
+
 def test_heatbath_strong_coupling_gpu(ctx):
     """<P> = beta/18 + beta^2/216 at beta = 0.3 (SU(3) strong coupling)."""
     L = (8, 8, 8, 8)
@@ -181,10 +223,14 @@ def test_overrelaxation_preserves_action(ctx):
 
 
 @pytest.mark.parametrize("prec,recon,tol", [(lqcd.LQCD_F64, 18, 1e-12), (lqcd.LQCD_F64, 12, 1e-12),
+                                            (lqcd.LQCD_DF64, 18, 1e-11), (lqcd.LQCD_DF64, 12, 1e-11),
                                             (lqcd.LQCD_F32, 18, 5e-5), (lqcd.LQCD_F32, 12, 5e-5)])
 def test_overrelax_sweep_matches_oracle(ctx, oracle, prec, recon, tol):
     """One overrelaxation sweep (Sec. 2.2) from a rough field made by the
     oracle's heatbath, link by link against the oracle's sweep.  FP64: 1e-12.
+    FP64 with float-float staples: the staple rounds at 2^-46 instead of
+    2^-53 relative (2^7 larger), and the reflection divides the subgroup block
+    by its norm: 1e-11.
     FP32: staples, reflection and update in binary32 (unit roundoff 2^-24
     ~ 6e-8; a staple entry sums 6 triple products, ~20 roundings, and three
     subgroups compound), written back and reunitarised in FP64: 5e-5 ~ 800 u."""
@@ -209,7 +255,7 @@ def test_overrelax_sweep_matches_oracle(ctx, oracle, prec, recon, tol):
 def test_overrelax_rejects_bad_arguments(ctx):
     L = (4, 4, 4, 4)
     G = lqcd.lqcd_gauge_import(ctx, dev(inputs.random_gauge(L, "cold")), L)
-    for n_or, prec in [(0, lqcd.LQCD_F64), (65, lqcd.LQCD_F64), (1, lqcd.LQCD_DF64)]:
+    for n_or, prec in [(0, lqcd.LQCD_F64), (65, lqcd.LQCD_F64), (1, lqcd.LQCD_BF16S)]:
         with pytest.raises(lqcd.LqcdError):
             lqcd.lqcd_overrelax_sweep(ctx, G, n_or, prec)
 
