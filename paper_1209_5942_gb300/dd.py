@@ -170,15 +170,24 @@ def cg_solve_local_domains(ctx, slabs: TimeSlabs, gauges, bs, xs, kappa, mu, par
 class DistributedComm:
     """The communication hooks of a domain-decomposed solve with one domain
     per rank of a torch.distributed group: exchange() moves this rank's faces
-    (DistributedExchange), allreduce(values) sums host floats over the group
-    (on the CPU for gloo, on the device for NCCL)."""
+    (DistributedExchange; device faces through host copies for gloo),
+    allreduce(values) sums host floats over the group (on the CPU for gloo,
+    on the device for NCCL)."""
 
     def __init__(self, slabs: TimeSlabs, rank: int, faces, group=None):
         self.slabs, self.rank, self.faces, self.group = slabs, rank, faces, group
         self._ex = DistributedExchange(group)
 
     def exchange(self):
-        self._ex.exchange(self.slabs, self.rank, *self.faces)
+        import torch.distributed as dist
+        if self.faces[0].is_cuda and dist.get_backend(self.group) == "gloo":
+            # gloo moves host memory: stage the device faces through the host
+            host = [f.cpu() for f in self.faces]
+            self._ex.exchange(self.slabs, self.rank, *host)
+            self.faces[2].copy_(host[2])
+            self.faces[3].copy_(host[3])
+        else:
+            self._ex.exchange(self.slabs, self.rank, *self.faces)
         if self.faces[0].is_cuda:
             torch.cuda.current_stream().synchronize()
 
