@@ -320,7 +320,9 @@ typedef struct {
   int32_t inner_prec;     /* == outer_prec: plain CG; LQCD_F32 / LQCD_BF16S /
                              LQCD_F16S: mixed precision with reliable updates */
   double delta;           /* reliable-update trigger: ||s|| < delta * max ||s||
-                             since the last update (<= 0 selects 0.1); with a
+                             since the last update (<= 0 selects 0.003 for an
+                             LQCD_F32 inner format, whose updates cost more than
+                             its drift, and 0.1 for the 16-bit ones); with a
                              LQCD_BF16S inner format the CG also updates every
                              8 iterations, which bounds the drift of the 8-bit
                              recursion from the true residual */

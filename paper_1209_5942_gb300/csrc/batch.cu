@@ -507,7 +507,7 @@ lqcd_status cg_solve_batch_impl(lqcd_ctx *ctx, int n, lqcd_gauge *const *U, cons
     for (int k = 0; k < n; k++) ctx->pinned[k] = stop2[k];
     LQCD_CUDA(ctx, cudaMemcpyAsync(stopd.p, ctx->pinned, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream));
     bstate_init_kernel<<<1, 256, 0, ctx->stream>>>(h, n, mixed ? 1 : 0, (const double *)stopd.p,
-                                                   prm.delta > 0 ? prm.delta : 0.1,
+                                                   prm.delta > 0 ? prm.delta : default_delta(inner),
                                                    mixed && inner == LQCD_BF16S ? kBf16Gap : INT_MAX);
     count_launch(ctx, 0.0);
     // z = Mhat^+ s; zz; p = z

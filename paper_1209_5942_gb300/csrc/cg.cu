@@ -684,7 +684,7 @@ lqcd_status cgls_even(lqcd_ctx *ctx, lqcd_gauge *U, const Geom &g, double kappa,
   LQCD_CUDA(ctx, cudaMemcpyAsync(b2d, ctx->pinned, nrhs * sizeof(double), cudaMemcpyHostToDevice,
                                  ctx->stream));
   state_init_kernel<<<1, 64, 0, ctx->stream>>>(h, nrhs, mixed ? 1 : 0, b2d, prm.tol * 0.5,
-                                               prm.delta > 0 ? prm.delta : 0.1,
+                                               prm.delta > 0 ? prm.delta : default_delta(inner),
                                                mixed && inner == LQCD_BF16S ? kBf16Gap : INT_MAX);
   LQCD_CUDA(ctx, cudaGetLastError());
   const HostC one{1, 0}, zero{0, 0}, mone{-1, 0};

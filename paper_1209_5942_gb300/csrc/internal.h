@@ -161,6 +161,18 @@ void tune_load(lqcd_ctx *ctx);
 // drivers (single and batched systems) use this gap.
 constexpr int kBf16Gap = 8;
 
+// Reliable-update trigger when the caller leaves delta <= 0.  A reliable
+// update costs two outer-precision (IEEE FP64 or float-float) Schur
+// operators, and GB300's FP64 pipe runs at 1/64 of the FP32 rate, so with an
+// FP32 recursion, whose residual stays faithful over a long drop, fewer
+// updates pay: on the 24^3 x 48 bench field and the 32^3 x 64 heatbath field
+// delta = 0.003 kept the iteration counts of delta = 0.1 with 4 updates
+// instead of 10 (DF64/F32 15.9 -> 13.5 ms and 146 -> 139 ms, FP64/F32 23.4 ->
+// 16.4 ms and 169 -> 148 ms, the 12-RHS DF64/F32 solve 139 -> 115 ms).  The
+// 16-bit recursions keep 0.1: with FP16 a smaller delta took the heatbath
+// field from 231 to 317-781 iterations.
+inline double default_delta(int inner) { return inner == LQCD_F32 ? 0.003 : 0.1; }
+
 // work counters: one launch moving `bytes` algorithmic bytes
 inline void count_launch(lqcd_ctx *ctx, double bytes) {
   ctx->cnt.launches += 1;
