@@ -353,7 +353,9 @@ typedef struct {
  * BiCGStab runs in inner_prec to inner_tol per cycle and the FP64 true
  * residual drives outer refinement), with source preparation
  *   bhat_e = b_e + kappa H_eo A_o^-1 b_o
- * and reconstruction x_o = A_o^-1 (b_o + kappa H_oe x_e).  nrhs > 1 solves
+ * and reconstruction x_o = A_o^-1 (b_o + kappa H_oe x_e), both in the outer
+ * format (IEEE FP64 or float-float); the true residual ||b - M x|| / ||b||
+ * is always recomputed in IEEE FP64.  nrhs > 1 solves
  * the right-hand sides together (one multi-RHS operator per iteration,
  * per-RHS scalars and convergence); stats then points to nrhs entries.
  * Synchronous: returns after the true residual is known.  Returns

@@ -1264,14 +1264,30 @@ lqcd_status cg_solve_eo(lqcd_ctx *ctx, lqcd_gauge *U, const HalfField &b_full, c
   Vec rhs_e, rhs_o, t_o, bhat64, corr_e, corr_o, res_e, res_o, xo_outer, bhat_outer;
   LQCD_TRY(rhs_e.alloc(ctx, LQCD_F64, Vh, nrhs));
   LQCD_TRY(rhs_o.alloc(ctx, LQCD_F64, Vh, nrhs));
-  LQCD_TRY(t_o.alloc(ctx, LQCD_F64, Vh, nrhs));
-  LQCD_TRY(bhat64.alloc(ctx, LQCD_F64, Vh, nrhs));
+  if (outer == LQCD_F64) {
+    LQCD_TRY(t_o.alloc(ctx, LQCD_F64, Vh, nrhs));
+    LQCD_TRY(bhat64.alloc(ctx, LQCD_F64, Vh, nrhs));
+  }
   LQCD_TRY(corr_e.alloc(ctx, LQCD_F64, Vh, nrhs));
   LQCD_TRY(corr_o.alloc(ctx, LQCD_F64, Vh, nrhs));
   LQCD_TRY(res_e.alloc(ctx, LQCD_F64, Vh, nrhs));
   LQCD_TRY(res_o.alloc(ctx, LQCD_F64, Vh, nrhs));
   LQCD_TRY(xo_outer.alloc(ctx, outer, Vh, nrhs));
-  if (outer != LQCD_F64) LQCD_TRY(bhat_outer.alloc(ctx, outer, Vh, nrhs));
+  // With a float-float outer format the source preparation and the
+  // reconstruction run in float-float too (the CG works on bhat in that format,
+  // and x_o enters the IEEE-FP64 true residual, whose check decides); their
+  // half hops then cost a quarter of the FP64 ones on GB300.
+  const bool prep_outer = outer != LQCD_F64;
+  Vec rhs_e_w, rhs_o_w, t_o_w, corr_o_w;
+  GaugeView Uw{};
+  if (prep_outer) {
+    LQCD_TRY(bhat_outer.alloc(ctx, outer, Vh, nrhs));
+    LQCD_TRY(rhs_e_w.alloc(ctx, outer, Vh, nrhs));
+    LQCD_TRY(rhs_o_w.alloc(ctx, outer, Vh, nrhs));
+    LQCD_TRY(t_o_w.alloc(ctx, outer, Vh, nrhs));
+    LQCD_TRY(corr_o_w.alloc(ctx, outer, Vh, nrhs));
+    LQCD_TRY(gauge_view(ctx, U, outer, U->recon, &Uw));
+  }
   LQCD_TRY(lincomb(ctx, Vh, rhs_e.f, be, nullptr, one, one, zero, zero, nullptr, nullptr));
   LQCD_TRY(lincomb(ctx, Vh, rhs_o.f, bo, nullptr, one, one, zero, zero, nullptr, nullptr));
   TmCoef c = tm_coef(kappa, mu, false);
@@ -1279,25 +1295,33 @@ lqcd_status cg_solve_eo(lqcd_ctx *ctx, lqcd_gauge *U, const HalfField &b_full, c
   double worst = 0.0;
   for (int cycle = 0;; cycle++) {
     // bhat_e = rhs_e + kappa H_eo A_o^-1 rhs_o
-    LQCD_TRY(lincomb(ctx, Vh, t_o.f, rhs_o.f, nullptr, c.Ai_up, c.Ai_dn, zero, zero, nullptr, nullptr));
     HopLaunch Ls;
-    Ls.prec = LQCD_F64;
     Ls.recon = U->recon;
-    Ls.U = O64.U;
-    Ls.in = t_o.f;
-    Ls.out = bhat64.f;
-    Ls.aux = rhs_e.f;
     Ls.has_aux = true;
     Ls.out_parity = 0;
     Ls.c_up = Ls.c_dn = {kappa, 0.0};
     Ls.d_up = Ls.d_dn = one;
-    LQCD_TRY(launch_hop(ctx, g, Ls, nullptr));
-    HalfField bh = bhat64.f;
-    if (outer != LQCD_F64) {
-      LQCD_TRY(spinor_convert_raw(ctx, Vh, nrhs, bhat64.f.ptr, nullptr, LQCD_F64, bhat_outer.f.ptr,
-                                  nullptr, outer));
+    HalfField bh;
+    if (prep_outer) {
+      LQCD_TRY(spinor_convert_raw(ctx, Vh, nrhs, rhs_e.f.ptr, nullptr, LQCD_F64, rhs_e_w.f.ptr, nullptr, outer));
+      LQCD_TRY(spinor_convert_raw(ctx, Vh, nrhs, rhs_o.f.ptr, nullptr, LQCD_F64, rhs_o_w.f.ptr, nullptr, outer));
+      LQCD_TRY(lincomb(ctx, Vh, t_o_w.f, rhs_o_w.f, nullptr, c.Ai_up, c.Ai_dn, zero, zero, nullptr, nullptr));
+      Ls.prec = outer;
+      Ls.U = Uw;
+      Ls.in = t_o_w.f;
+      Ls.out = bhat_outer.f;
+      Ls.aux = rhs_e_w.f;
       bh = bhat_outer.f;
+    } else {
+      LQCD_TRY(lincomb(ctx, Vh, t_o.f, rhs_o.f, nullptr, c.Ai_up, c.Ai_dn, zero, zero, nullptr, nullptr));
+      Ls.prec = LQCD_F64;
+      Ls.U = O64.U;
+      Ls.in = t_o.f;
+      Ls.out = bhat64.f;
+      Ls.aux = rhs_e.f;
+      bh = bhat64.f;
     }
+    LQCD_TRY(launch_hop(ctx, g, Ls, nullptr));
     LQCD_CUDA(ctx, cudaMemsetAsync(xo_outer.f.ptr, 0, xo_outer.f.rhs_stride * nrhs, ctx->stream));
     int used = 0;
     lqcd_status s = prm.solver == LQCD_SOLVER_BICGSTAB
@@ -1305,18 +1329,18 @@ lqcd_status cg_solve_eo(lqcd_ctx *ctx, lqcd_gauge *U, const HalfField &b_full, c
                         : cgls_even(ctx, U, g, kappa, mu, prm, bh, xo_outer.f, b2, st, nrhs, &used, false);
     if (s != LQCD_OK && s != LQCD_ERR_NOCONV) return s;
     // corr_e = x_e (F64); corr_o = A_o^-1 (rhs_o + kappa H_oe corr_e)
-    if (outer != LQCD_F64)
+    if (prep_outer)
       LQCD_TRY(spinor_convert_raw(ctx, Vh, nrhs, xo_outer.f.ptr, nullptr, outer, corr_e.f.ptr, nullptr,
                                   LQCD_F64));
     else
       LQCD_TRY(lincomb(ctx, Vh, corr_e.f, xo_outer.f, nullptr, one, one, zero, zero, nullptr, nullptr));
     HopLaunch Lr;
-    Lr.prec = LQCD_F64;
+    Lr.prec = prep_outer ? outer : LQCD_F64;
     Lr.recon = U->recon;
-    Lr.U = O64.U;
-    Lr.in = corr_e.f;
-    Lr.out = corr_o.f;
-    Lr.aux = rhs_o.f;
+    Lr.U = prep_outer ? Uw : O64.U;
+    Lr.in = prep_outer ? xo_outer.f : corr_e.f;
+    Lr.out = prep_outer ? corr_o_w.f : corr_o.f;
+    Lr.aux = prep_outer ? rhs_o_w.f : rhs_o.f;
     Lr.has_aux = true;
     Lr.out_parity = 1;
     Lr.c_up = {kappa * c.Ai_up.re, kappa * c.Ai_up.im};
@@ -1324,6 +1348,8 @@ lqcd_status cg_solve_eo(lqcd_ctx *ctx, lqcd_gauge *U, const HalfField &b_full, c
     Lr.d_up = c.Ai_up;
     Lr.d_dn = c.Ai_dn;
     LQCD_TRY(launch_hop(ctx, g, Lr, nullptr));
+    if (prep_outer)
+      LQCD_TRY(spinor_convert_raw(ctx, Vh, nrhs, corr_o_w.f.ptr, nullptr, outer, corr_o.f.ptr, nullptr, LQCD_F64));
     // x += corr
     LQCD_TRY(lincomb(ctx, Vh, xe, xe, &corr_e.f, one, one, one, one, nullptr, nullptr));
     LQCD_TRY(lincomb(ctx, Vh, xodd, xodd, &corr_o.f, one, one, one, one, nullptr, nullptr));
