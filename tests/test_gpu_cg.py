@@ -97,6 +97,36 @@ def test_multi_rhs_point_sources(ctx, oracle):
             assert _true_resid(oracle, U, L, x[r], b[r], kappa, mu) <= 1e-10
 
 
+@pytest.mark.parametrize("inner", [lqcd.LQCD_BF16S, lqcd.LQCD_F16S])
+def test_multi_rhs_16bit_inner_any_launch(ctx, oracle, inner):
+    """12 point sources with a 16-bit inner recursion, whose 12-RHS hops the
+    tuner may run as the kernel with links staged in shared memory (reducing
+    variants included): with the launch left to the tuner and with each
+    staged-link candidate forced (the 12-RHS 16-bit candidate list puts them
+    at 39-50), every solution reaches the oracle's true residual and the
+    solutions are the same bits."""
+    L = (4, 4, 4, 8)
+    kappa, mu = 0.157, 0.003 / 0.314
+    U = inputs.random_gauge(L, "near", seed=1211, eps=0.4)
+    G = lqcd.lqcd_gauge_import(ctx, dev(U), L, recon=12)
+    b = inputs.point_sources(L)
+    ref = None
+    for choice in (-1, 39, 41, 44, 47, 50):
+        lqcd.lqcd_set_launch_choice(ctx, choice)
+        try:
+            x, st = _solve(ctx, G, L, b, kappa, mu, nrhs=12, tol=1e-10, outer_prec=lqcd.LQCD_DF64,
+                           inner_prec=inner)
+        finally:
+            lqcd.lqcd_set_launch_choice(ctx, -1)
+        assert all(s["converged"] == 1 for s in st), (choice, st)
+        if ref is None:
+            ref = x
+            for r in range(12):
+                assert _true_resid(oracle, U, L, x[r], b[r], kappa, mu) <= 1e-10
+        else:
+            assert np.array_equal(x, ref), choice
+
+
 def test_multi_rhs_equals_single(ctx):
     """Batched right-hand sides give the single-RHS solutions bit for bit
     (same kernels, same reduction order per right-hand side)."""
