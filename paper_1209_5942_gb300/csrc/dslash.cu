@@ -59,7 +59,7 @@ lqcd_status launch_hop(lqcd_ctx *ctx, const Geom &g, const HopLaunch &L, int *nb
   //  load orders.  The float-float kernel with 18-real links runs two threads
   //  per site and is bounded to 128 threads per block; it comes in scalar
   //  and in packed FP32x2 arithmetic, the packed form also with its operands
-  //  staged through shared memory.
+  //  staged through shared memory (bounded to 128 or to 96 registers).
   struct Cand {
     short bx, by, gm, rt;
     bool lf, two;  // two: two sites per thread in packed FP32x2
@@ -77,7 +77,7 @@ lqcd_status launch_hop(lqcd_ctx *ctx, const Geom &g, const HopLaunch &L, int *nb
   for (int gi = 0; gi < 3; gi++)
     for (int lf = 0; lf < (low ? 2 : 1); lf++) {
       if (pair) {
-        for (char pk = 0; pk < 3; pk++) {
+        for (char pk = 0; pk < 4; pk++) {
           if (nrhs == 1) {
             cands[ncand++] = {64, 1, GM[gi], 1, false, false, pk};
             cands[ncand++] = {128, 1, GM[gi], 1, false, false, pk};
@@ -151,7 +151,7 @@ lqcd_status launch_hop(lqcd_ctx *ctx, const Geom &g, const HopLaunch &L, int *nb
     }
   };
   char key[160];
-  snprintf(key, sizeof(key), "hop5|p%d|r%d|d%d|red%d|aux%d|%dx%dx%dx%d|n%d", L.prec, L.recon, (int)dag, (int)red,
+  snprintf(key, sizeof(key), "hop6|p%d|r%d|d%d|red%d|aux%d|%dx%dx%dx%d|n%d", L.prec, L.recon, (int)dag, (int)red,
            A.has_aux, g.L[0], g.L[1], g.L[2], g.L[3], nrhs);
   HopArgs At = A;
   At.halt = nullptr;  // timing launches run whatever the solver state

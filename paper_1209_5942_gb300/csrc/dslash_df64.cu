@@ -20,8 +20,18 @@ static void launch_pair(const HopArgs &A, dim3 grid, dim3 block, bool dag, bool 
 
 void hop_launch_df64(const HopArgs &A, int recon, bool pair, int mode, dim3 grid, dim3 block, bool dag,
                      bool red, cudaStream_t st) {
-  if (pair && mode == 2) {
+  if (pair && (mode == 2 || mode == 3)) {
     const size_t smem = (size_t)block.y * df_staged_words(block.x) * sizeof(float4);
+    if (mode == 3) {
+      if (dag) {
+        if (red) launch_pdl(hop_df64_staged_kernel<true, true, 5>, grid, block, smem, st, A);
+        else launch_pdl(hop_df64_staged_kernel<true, false, 5>, grid, block, smem, st, A);
+      } else {
+        if (red) launch_pdl(hop_df64_staged_kernel<false, true, 5>, grid, block, smem, st, A);
+        else launch_pdl(hop_df64_staged_kernel<false, false, 5>, grid, block, smem, st, A);
+      }
+      return;
+    }
     if (dag) {
       if (red) launch_pdl(hop_df64_staged_kernel<true, true>, grid, block, smem, st, A);
       else launch_pdl(hop_df64_staged_kernel<true, false>, grid, block, smem, st, A);

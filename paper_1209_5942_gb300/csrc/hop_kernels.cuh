@@ -1276,8 +1276,11 @@ LQCD_DEV void df_stage_compute(const HopArgs &A, const Site &s, int k, int h, bo
   __syncwarp();
 }
 
-template <bool DAG, bool REDUCE>
-__global__ void __launch_bounds__(128, 4) hop_df64_staged_kernel(HopArgs A) {
+// MINB: blocks of 128 threads per SM the register bound allows (4: 128
+// registers; 5: 96 registers, more warps for the fixed-latency chains of the
+// error-free sums at the cost of a few spilled values; the tuner picks)
+template <bool DAG, bool REDUCE, int MINB = 4>
+__global__ void __launch_bounds__(128, MINB) hop_df64_staged_kernel(HopArgs A) {
   pdl_wait();
   __shared__ double sh[8][4];
   extern __shared__ float4 stage_words[];
@@ -1415,7 +1418,8 @@ inline void launch_t(const HopArgs &A, dim3 grid, dim3 block, bool dag, bool red
 // per-precision launchers (dslash_f64.cu, dslash_df64.cu, dslash_f32.cu, dslash_h16.cu)
 void hop_launch_f64(const HopArgs &A, int recon, dim3 grid, dim3 block, bool dag, bool red, cudaStream_t st);
 // pair: two threads per site (18-real links); mode 0 scalar, 1 packed FP32x2,
-// 2 packed with the operands staged through shared memory
+// 2 packed with the operands staged through shared memory, 3 the same bounded
+// to 96 registers
 void hop_launch_df64(const HopArgs &A, int recon, bool pair, int mode, dim3 grid, dim3 block, bool dag,
                      bool red, cudaStream_t st);
 // rt: right-hand sides per thread (1, 2, 4); two: two sites per thread (packed FP32x2)
