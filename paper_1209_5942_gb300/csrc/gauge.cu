@@ -888,6 +888,8 @@ __global__ void __launch_bounds__(128, 5) heatbath_f32_kernel(GaugeView Uf, Geom
   M3s u = load_link_s<RECON>(Uf, s, mu);
   const int SG[3][2] = {{0, 1}, {1, 2}, {0, 2}};
   unsigned fails = 0;
+  // unrolled: compile-time rows i, j keep u and W in registers
+#pragma unroll
   for (int sg = 0; sg < 3; sg++) {
     const int i = SG[sg][0], j = SG[sg][1];
     const M3s W = smul(u, A);
@@ -899,7 +901,8 @@ __global__ void __launch_bounds__(128, 5) heatbath_f32_kernel(GaugeView Uf, Geom
       fails++;
       continue;
     }
-    const float h0 = q0 / k, h1 = q1 / k, h2 = q2 / k, h3 = q3 / k;
+    const float ik = 1.0f / k;  // one division for the four components
+    const float h0 = q0 * ik, h1 = q1 * ik, h2 = q2 * ik, h3 = q3 * ik;
     const Cx<float> whd[2][2] = {{{h0, -h3}, {-h2, -h1}}, {{h2, -h1}, {h0, h3}}};
     Cx<float> v[2][2];
     if (overrelax) {
