@@ -983,10 +983,11 @@ def run_config(args):
                     {"workload": "24^3x48 exp(i 0.3 H) links, 12 point sources, DF64 outer / F32 inner, "
                                  "REC12 sloppy links, 1e-10"})
     elif c == "dd":
-        # the domain-decomposed FP64 CG (t split into nt domains held in one
-        # process, faces moved by device copies) against lqcd_cg_solve on the
-        # default 24^3 x 48 workload: the cost of the decomposition itself
-        # (face packs, split hops, one host synchronisation per norm)
+        # the domain-decomposed CG (t split into nt domains held in one
+        # process, faces moved by device copies), FP64 and with an F32 or
+        # float-float inner solve (defect correction), against lqcd_cg_solve
+        # on the default 24^3 x 48 workload: the cost of the decomposition
+        # itself (face packs, split hops, one host synchronisation per norm)
         from paper_1209_5942_gb300 import dd
         U, b = make_inputs()
         G = lqcd.lqcd_gauge_import(ctx, torch.from_numpy(U).cuda(), L, recon=18)
@@ -997,7 +998,17 @@ def run_config(args):
         lqcd.lqcd_cg_solve(ctx, G, fb, fx, KAPPA, MU, prm)
         t1, st1 = _timed(torch, lambda: lqcd.lqcd_cg_solve(ctx, G, fb, fx, KAPPA, MU, prm))
         res = {"single_domain": {"solve_s": t1, "iters": st1[0]["iters"], "true_resid": st1[0]["true_resid"]}}
+        prm_m = lqcd.cg_params(tol=TOL, outer_prec=lqcd.LQCD_F64, inner_prec=lqcd.LQCD_F32, max_iter=50000)
+        lqcd.lqcd_cg_solve(ctx, G, fb, fx, KAPPA, MU, prm_m)
+        tm, stm = _timed(torch, lambda: lqcd.lqcd_cg_solve(ctx, G, fb, fx, KAPPA, MU, prm_m))
+        res["single_domain_f64/f32"] = {"solve_s": tm, "iters": stm[0]["iters"],
+                                        "true_resid": stm[0]["true_resid"]}
         G.free()
+        dd_prms = {"f64": prm,
+                   "f64/f32": lqcd.cg_params(tol=TOL, outer_prec=lqcd.LQCD_F64, inner_prec=lqcd.LQCD_F32,
+                                             max_iter=50000, max_restarts=10),
+                   "f64/df64": lqcd.cg_params(tol=TOL, outer_prec=lqcd.LQCD_F64, inner_prec=lqcd.LQCD_DF64,
+                                              max_iter=50000)}
         for nt in (1, 2, 4):
             slabs = dd.TimeSlabs(L, nt)
             Ll = slabs.local_L
@@ -1013,15 +1024,18 @@ def run_config(args):
                 xs.append(lqcd.field(xdd, lqcd.LQCD_LAYOUT_EO))
                 keep.append((bdd, xdd))
             faces = [dd.face_buffers(slabs, lqcd.LQCD_F64) for _ in range(nt)]
-            dd.cg_solve_local_domains(ctx, slabs, gs, bs, xs, KAPPA, MU, prm, faces=faces)
-            t, st = _timed(torch, lambda: dd.cg_solve_local_domains(ctx, slabs, gs, bs, xs, KAPPA, MU, prm,
-                                                                    faces=faces))
-            res[f"nt{nt}"] = {"solve_s": t, "iters": st["iters"], "true_resid": st["true_resid"],
-                              "vs_single_domain": t / t1}
+            for name, pv in dd_prms.items():
+                dd.cg_solve_local_domains(ctx, slabs, gs, bs, xs, KAPPA, MU, pv, faces=faces)
+                t, st = _timed(torch, lambda: dd.cg_solve_local_domains(ctx, slabs, gs, bs, xs, KAPPA, MU, pv,
+                                                                        faces=faces))
+                key = f"nt{nt}" if name == "f64" else f"nt{nt}_{name}"
+                res[key] = {"solve_s": t, "iters": st["iters"], "restarts": st["restarts"],
+                            "true_resid": st["true_resid"], "vs_single_domain": t / t1}
             for G_ in gs:
                 G_.free()
         config_line("domain-decomposed CG", None, {"dd": res},
-                    {"workload": "24^3x48 exp(i 0.3 H) links, kappa=0.16, 2 kappa mu=0.005, FP64 CG to 1e-10; "
+                    {"workload": "24^3x48 exp(i 0.3 H) links, kappa=0.16, 2 kappa mu=0.005, CG to 1e-10 "
+                                 "(FP64, or FP64 outer with an F32 / float-float inner solve); "
                                  "t split into nt domains on one GPU (faces by device copies)"})
     elif c == "sweep":
         res = {}

@@ -331,9 +331,10 @@ typedef struct {
   int32_t use_graph;      /* 1: capture check_every iterations in a CUDA graph */
   int32_t sloppy_recon;   /* 18 or 12: link format of the inner operator */
   int32_t solver;         /* LQCD_SOLVER_CG (default) or LQCD_SOLVER_BICGSTAB */
-  double inner_tol;       /* BiCGStab with inner_prec != outer_prec: relative
-                             residual each refinement cycle reaches in the inner
-                             format (0 selects 1e-5) */
+  double inner_tol;       /* BiCGStab with inner_prec != outer_prec, and the
+                             domain-decomposed CG with an F32 inner format:
+                             relative residual each refinement cycle reaches
+                             in the inner format (0 selects 1e-5) */
 } lqcd_cg_params;
 enum { LQCD_SOLVER_CG = 0, LQCD_SOLVER_BICGSTAB = 1 };
 
@@ -366,23 +367,25 @@ int lqcd_cg_solve(lqcd_ctx *ctx, const lqcd_gauge *U, lqcd_field b, lqcd_field x
 
 /* Communication of a domain-decomposed solve (lqcd_dd_cg_solve), called by
  * the library from the calling thread between its launches:
- *   exchange(user): every held domain's to_prev and to_next faces are written
- *     (the library's stream has been synchronised); the hook delivers each
- *     to_prev face to the previous domain's from_next buffer and each to_next
- *     face to the next domain's from_prev buffer, and returns once they are
- *     in place;
+ *   exchange(user, bytes): every held domain's to_prev and to_next faces are
+ *     written in their leading `bytes` bytes (lqcd_dd_face_bytes of the
+ *     format of that half hop: LQCD_F64 for the FP64 steps, the inner format
+ *     for the inner ones; the library's stream has been synchronised); the
+ *     hook delivers those bytes of each to_prev face to the previous domain's
+ *     from_next buffer and of each to_next face to the next domain's
+ *     from_prev buffer, and returns once they are in place;
  *   allreduce(user, vals, n): sums n host doubles over all processes of the
  *     solve, in place (NULL: a single process).
  * Both return 0 on success; anything else ends the solve with LQCD_ERR_COMM. */
 typedef struct {
   void *user;
-  int (*exchange)(void *user);
+  int (*exchange)(void *user, size_t bytes);
   int (*allreduce)(void *user, double *vals, int n);
 } lqcd_dd_comm;
 
 /* The even-odd CG of lqcd_cg_solve (CGLS on Mhat^+ Mhat, source preparation,
- * reconstruction, FP64 true residual and outer refinement; IEEE FP64, one
- * right-hand side) on a lattice split along t into nt domains as for
+ * reconstruction, FP64 true residual and outer refinement; one right-hand
+ * side) on a lattice split along t into nt domains as for
  * lqcd_dd_pack (Sec. 6 outlook: the solver over several GPUs).  This call
  * holds nd consecutive domains, first_domain .. first_domain + nd - 1, each on
  * the local geometry `local` (local->L[3] = Lt / nt, even; local must match
@@ -393,12 +396,18 @@ typedef struct {
  * packs the faces of all held domains, moves them and runs the domain hops
  * with the operator's diagonal epilogue; every norm is summed in a fixed
  * order on each domain, over the held domains in order, then over
- * processes.  comm = NULL: the call holds every domain (nd = nt,
- * first_domain = 0) and the library moves the faces by device copies;
- * otherwise comm->exchange moves them and comm->allreduce sums the norms.
- * antiperiodic_t: the fermion boundary of the whole lattice.  params: tol,
- * max_iter, max_restarts (outer_prec and inner_prec LQCD_F64, solver CG,
- * else LQCD_ERR_UNSUPPORTED).  stats: one entry; true_resid is that of the
+ * processes.  Mixed precision (Sec. 3) as defect correction: with inner_prec
+ * LQCD_F32 or LQCD_DF64 each refinement cycle runs the CGLS in that format
+ * (links in sloppy_recon's format, 0: the field's) on its cycle's prepared
+ * residual, until the residual has dropped by inner_tol (F32; 0 selects
+ * 1e-5) or, for LQCD_DF64, to the tolerance; the source preparation, the
+ * correction, the reconstruction and the true residual stay IEEE FP64.
+ * comm = NULL: the call holds every domain (nd = nt, first_domain = 0) and
+ * the library moves the faces by device copies; otherwise comm->exchange
+ * moves them and comm->allreduce sums the norms.  antiperiodic_t: the
+ * fermion boundary of the whole lattice.  params: tol, max_iter,
+ * max_restarts, inner_tol, sloppy_recon (outer_prec LQCD_F64, inner_prec
+ * LQCD_F64, LQCD_DF64 or LQCD_F32, solver CG, else LQCD_ERR_UNSUPPORTED).  stats: one entry; true_resid is that of the
  * whole lattice.  Synchronous; LQCD_ERR_NOCONV (stats filled) when tol is not
  * reached. */
 int lqcd_dd_cg_solve(lqcd_ctx *ctx, int nd, const lqcd_gauge *const *U, const lqcd_field *b,

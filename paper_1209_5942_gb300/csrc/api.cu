@@ -536,8 +536,11 @@ extern "C" int lqcd_dd_cg_solve(lqcd_ctx *ctx, int nd, const lqcd_gauge *const *
     return fail(ctx, LQCD_ERR_INVALID, "domain-decomposed CG without comm hooks must hold every domain");
   if (comm && !comm->exchange) return fail(ctx, LQCD_ERR_INVALID, "domain-decomposed CG: no exchange hook");
   LQCD_TRY(check_cg_params(ctx, params));
-  if (params->outer_prec != LQCD_F64 || params->inner_prec != LQCD_F64 || params->solver != LQCD_SOLVER_CG)
-    return fail(ctx, LQCD_ERR_UNSUPPORTED, "domain-decomposed CG: plain FP64 CG only");
+  const int inner = params->inner_prec;
+  if (params->outer_prec != LQCD_F64 || params->solver != LQCD_SOLVER_CG ||
+      (inner != LQCD_F64 && inner != LQCD_DF64 && inner != LQCD_F32))
+    return fail(ctx, LQCD_ERR_UNSUPPORTED,
+                "domain-decomposed CG: CG with outer_prec F64 and inner_prec F64, DF64 or F32");
   if (!std::isfinite(kappa) || !std::isfinite(mu)) return fail(ctx, LQCD_ERR_NONFINITE, "kappa/mu not finite");
   const size_t fb = lqcd_dd_face_bytes(local, LQCD_F64);
   if (fb == 0) return fail(ctx, LQCD_ERR_INVALID, "domain-decomposed CG: bad local geometry");
@@ -545,15 +548,19 @@ extern "C" int lqcd_dd_cg_solve(lqcd_ctx *ctx, int nd, const lqcd_gauge *const *
   lg.antiperiodic_t = 0;  // the global boundary sign travels in the faces
   const Geom g = make_geom(lg);
   const size_t full_bytes = 2 * spinor_half_bytes(LQCD_F64, g.Vh);
-  std::vector<GaugeView> views(nd);
+  std::vector<GaugeView> views(nd), views_i(inner == LQCD_F64 ? 0 : nd);
   std::vector<HalfField> bf(nd), xf(nd);
   std::vector<void *> fv(4 * (size_t)nd);
-  int recon = 0;
+  int recon = 0, recon_i = 0;
   for (int d = 0; d < nd; d++) {
     LQCD_TRY(check_gauge(ctx, U[d], local));
-    if (d == 0) recon = U[0]->recon;
+    if (d == 0) {
+      recon = U[0]->recon;
+      recon_i = params->sloppy_recon ? params->sloppy_recon : recon;
+    }
     if (U[d]->recon != recon) return fail(ctx, LQCD_ERR_INVALID, "domain-decomposed CG: mixed link formats");
     LQCD_TRY(gauge_view(ctx, const_cast<lqcd_gauge *>(U[d]), LQCD_F64, recon, &views[d]));
+    if (inner != LQCD_F64) LQCD_TRY(gauge_view(ctx, const_cast<lqcd_gauge *>(U[d]), inner, recon_i, &views_i[d]));
     LQCD_TRY(check_field(ctx, b[d], "b", false));
     LQCD_TRY(check_field(ctx, x[d], "x", false));
     if (b[d].prec != LQCD_F64 || x[d].prec != LQCD_F64 || b[d].nrhs != 1 || x[d].nrhs != 1)
@@ -570,8 +577,8 @@ extern "C" int lqcd_dd_cg_solve(lqcd_ctx *ctx, int nd, const lqcd_gauge *const *
       fv[4 * d + k] = f;
     }
   }
-  return dd_cg_solve(ctx, nd, first_domain, nt, antiperiodic_t ? 1 : 0, g, recon, views, bf, xf, fv, fb, comm,
-                     kappa, mu, *params, stats);
+  return dd_cg_solve(ctx, nd, first_domain, nt, antiperiodic_t ? 1 : 0, g, recon, views, recon_i, views_i, bf, xf,
+                     fv, fb, comm, kappa, mu, *params, stats);
 }
 
 static int apply_impl(lqcd_ctx *ctx, const lqcd_gauge *U, lqcd_field in, lqcd_field out,

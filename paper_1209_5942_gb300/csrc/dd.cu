@@ -147,13 +147,10 @@ static void dd_launch(bool pack, bool dag, const HopArgs &A, int vsh, void *f0, 
     else dd_pack_kernel<PREC, RECON, 1><<<grid, 128, 0, st>>>(A, vsh, f0, f1, n0, n1);
   } else {
     const unsigned grid = (unsigned)((A.g.Vh + 127) / 128);
-    // the reducing form serves the FP64 domain-decomposed CG only
-    if constexpr (PREC == LQCD_F64) {
-      if (A.partials) {
-        if (dag) dd_hop_kernel<PREC, RECON, true, true><<<grid, 128, 0, st>>>(A, vsh, f0, f1);
-        else dd_hop_kernel<PREC, RECON, false, true><<<grid, 128, 0, st>>>(A, vsh, f0, f1);
-        return;
-      }
+    if (A.partials) {  // the reducing form (norms of the domain-decomposed CG)
+      if (dag) dd_hop_kernel<PREC, RECON, true, true><<<grid, 128, 0, st>>>(A, vsh, f0, f1);
+      else dd_hop_kernel<PREC, RECON, false, true><<<grid, 128, 0, st>>>(A, vsh, f0, f1);
+      return;
     }
     if (dag) dd_hop_kernel<PREC, RECON, true, false><<<grid, 128, 0, st>>>(A, vsh, f0, f1);
     else dd_hop_kernel<PREC, RECON, false, false><<<grid, 128, 0, st>>>(A, vsh, f0, f1);

@@ -8,8 +8,13 @@
 // arithmetic, the source preparation bhat_e = b_e + kappa H_eo A_o^-1 b_o, the
 // reconstruction x_o = A_o^-1 (b_o + kappa H_oe x_e) and the FP64 true
 // residual with outer refinement follow the single-domain solver in cg.cu
-// (plain FP64, one right-hand side), with host-side scalars: a decomposed
-// solve synchronises on every norm anyway, to sum it over processes.
+// (one right-hand side), with host-side scalars: a decomposed solve
+// synchronises on every norm anyway, to sum it over processes.  Mixed
+// precision (Sec. 3: the bulk of the work in a cheaper format, the accuracy
+// restored in FP64) takes the form of defect correction: each refinement
+// cycle runs the CGLS in the inner format (F32 or float-float) on its cycle's
+// prepared residual until that residual has dropped by inner_tol, and the
+// correction, the reconstruction and the true residual are formed in FP64.
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -46,8 +51,9 @@ Tm tm_of(double kappa, double mu, bool dagger) {
 }
 HostC scaled(HostC c, double f) { return {f * c.re, f * c.im}; }
 
-// one FP64 half field per held domain; alloc() makes it own its memory, a
-// view of the caller's fields (f filled directly) frees nothing
+// one half field per held domain (FP64 unless alloc() is given another
+// format); alloc() makes it own its memory, a view of the caller's fields (f
+// filled directly) frees nothing
 struct DVec {
   lqcd_ctx *ctx = nullptr;
   std::vector<HalfField> f;
@@ -58,13 +64,13 @@ struct DVec {
     if (ctx)
       for (auto &h : f) dfree(ctx, h.ptr);
   }
-  lqcd_status alloc(lqcd_ctx *c, int nd, int Vh) {
+  lqcd_status alloc(lqcd_ctx *c, int nd, int Vh, int prec = LQCD_F64) {
     ctx = c;
     f.resize(nd);
     for (auto &h : f) {
-      h.prec = LQCD_F64;
+      h.prec = prec;
       h.nrhs = 1;
-      h.rhs_stride = spinor_half_bytes(LQCD_F64, Vh);
+      h.rhs_stride = spinor_half_bytes(prec, Vh);
       LQCD_TRY(dalloc(c, &h.ptr, h.rhs_stride));
       LQCD_CUDA(c, cudaMemsetAsync(h.ptr, 0, h.rhs_stride, c->stream));
     }
@@ -76,10 +82,10 @@ struct Dd {
   lqcd_ctx *ctx;
   int nd, first, nt, antiper;
   Geom g;  // local geometry; the global boundary sign travels in the faces
-  int recon;
-  std::vector<GaugeView> U;
-  std::vector<void *> faces;  // [4 nd]: to_prev, to_next, from_next, from_prev
-  size_t fb;
+  int recon, recon_i;
+  std::vector<GaugeView> U, Ui;  // FP64 links; links of the inner format
+  std::vector<void *> faces;     // [4 nd]: to_prev, to_next, from_next, from_prev
+  size_t fb;                     // bytes of an FP64 face (16-byte words)
   const lqcd_dd_comm *comm;
   double kappa, mu;
   double *dsum;  // device [nd]
@@ -101,44 +107,48 @@ struct Dd {
     return LQCD_OK;
   }
 
-  // the faces written by the packs reach their neighbours
-  lqcd_status exchange() {
+  // the faces written by the packs (in the format prec) reach their neighbours
+  lqcd_status exchange(int prec) {
+    const size_t nb = fb / 16 * dd_face_word_bytes(prec);
     if (comm) {
       LQCD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-      if (comm->exchange(comm->user) != 0)
+      if (comm->exchange(comm->user, nb) != 0)
         return fail(ctx, LQCD_ERR_COMM, "domain-decomposed CG: the exchange hook failed");
       return LQCD_OK;
     }
     for (int d = 0; d < nd; d++) {
       const int nx = (d + 1) % nt, pv = (d + nt - 1) % nt;
-      LQCD_CUDA(ctx, cudaMemcpyAsync(face(d, 2), face(nx, 0), fb, cudaMemcpyDeviceToDevice, ctx->stream));
-      LQCD_CUDA(ctx, cudaMemcpyAsync(face(d, 3), face(pv, 1), fb, cudaMemcpyDeviceToDevice, ctx->stream));
+      LQCD_CUDA(ctx, cudaMemcpyAsync(face(d, 2), face(nx, 0), nb, cudaMemcpyDeviceToDevice, ctx->stream));
+      LQCD_CUDA(ctx, cudaMemcpyAsync(face(d, 3), face(pv, 1), nb, cudaMemcpyDeviceToDevice, ctx->stream));
     }
     return LQCD_OK;
   }
 
-  // out_p = c * H in + d * aux on every held domain (aux optional); norm:
-  // |out|^2 over the whole lattice
+  // out_p = c * H in + d * aux on every held domain (aux optional), in the
+  // format of the fields (FP64 or the inner one); norm: |out|^2 over the whole
+  // lattice
   lqcd_status hop(const DVec &in, const DVec &out, const DVec *aux, int p, bool dagger, HostC c_up, HostC c_dn,
                   HostC d_up, HostC d_dn, double *norm) {
+    const int prec = in.f[0].prec;
+    const bool f64 = prec == LQCD_F64;
     for (int d = 0; d < nd; d++) {
       HopLaunch L;
-      L.prec = LQCD_F64;
-      L.recon = recon;
-      L.U = U[d];
+      L.prec = prec;
+      L.recon = f64 ? recon : recon_i;
+      L.U = f64 ? U[d] : Ui[d];
       L.in = in.f[d];
       L.out_parity = p;
       L.dagger = dagger ? 1 : 0;
       const int gd = first + d;
       LQCD_TRY(dd_run(ctx, g, L, true, face(d, 0), face(d, 1), antiper && gd == 0, antiper && gd == nt - 1));
     }
-    LQCD_TRY(exchange());
+    LQCD_TRY(exchange(prec));
     const int nw = (g.Vh + 31) / 32;
     for (int d = 0; d < nd; d++) {
       HopLaunch L;
-      L.prec = LQCD_F64;
-      L.recon = recon;
-      L.U = U[d];
+      L.prec = prec;
+      L.recon = f64 ? recon : recon_i;
+      L.U = f64 ? U[d] : Ui[d];
       L.in = in.f[d];
       L.out = out.f[d];
       L.out_parity = p;
@@ -172,6 +182,14 @@ struct Dd {
     return norm ? total(norm) : LQCD_OK;
   }
 
+  // out = in converted to out's format on every held domain
+  lqcd_status convert(const DVec &in, const DVec &out) {
+    for (int d = 0; d < nd; d++)
+      LQCD_TRY(spinor_convert_raw(ctx, g.Vh, 1, in.f[d].ptr, in.f[d].scale, in.f[d].prec, out.f[d].ptr,
+                                  out.f[d].scale, out.f[d].prec));
+    return LQCD_OK;
+  }
+
   // out_e = Mhat in_e (dagger: Mhat^+), as apply_schur: -kappa^2 folded into
   // the first hop, the second adds A in_e
   lqcd_status mhat(const DVec &in, const DVec &out, const DVec &tmp_o, bool dagger, double *norm) {
@@ -186,7 +204,8 @@ struct Dd {
 }  // namespace
 
 lqcd_status dd_cg_solve(lqcd_ctx *ctx, int nd, int first, int nt, int antiper, const Geom &g, int recon,
-                        const std::vector<GaugeView> &U, const std::vector<HalfField> &b_full,
+                        const std::vector<GaugeView> &U, int recon_i, const std::vector<GaugeView> &Ui,
+                        const std::vector<HalfField> &b_full,
                         const std::vector<HalfField> &x_full, const std::vector<void *> &faces, size_t fb,
                         const lqcd_dd_comm *comm, double kappa, double mu, const lqcd_cg_params &prm,
                         lqcd_cg_stats *st) {
@@ -197,7 +216,12 @@ lqcd_status dd_cg_solve(lqcd_ctx *ctx, int nd, int first, int nt, int antiper, c
   LQCD_TRY(dsum.alloc(sizeof(double) * nd));
   const int nb = (Vh + 127) / 128 > (Vh + 31) / 32 ? (Vh + 127) / 128 : (Vh + 31) / 32;
   LQCD_TRY(ensure_partials(ctx, (size_t)nb));
-  Dd S{ctx, nd, first, nt, antiper, g, recon, U, faces, fb, comm, kappa, mu, (double *)dsum.p};
+  Dd S{ctx, nd, first, nt, antiper, g, recon, recon_i, U, Ui, faces, fb, comm, kappa, mu, (double *)dsum.p};
+  const int inner = prm.inner_prec;
+  const bool mixed = inner != LQCD_F64;
+  // a mixed cycle stops once its residual has dropped by itol (F32; a
+  // float-float recursion runs to the tolerance itself)
+  const double itol = !mixed || inner == LQCD_DF64 ? 0.0 : prm.inner_tol > 0.0 ? prm.inner_tol : 1e-5;
   // views of the caller's even and odd halves
   DVec be, bo, xe, xo;
   be.f.resize(nd);
@@ -219,9 +243,17 @@ lqcd_status dd_cg_solve(lqcd_ctx *ctx, int nd, int first, int nt, int antiper, c
     h.ptr = (char *)x_full[d].ptr + hb;
     xo.f[d] = h;
   }
-  DVec rhs_e, rhs_o, t_o, bhat, xs, s, p, q, z, corr_o, res_e, res_o;
-  for (DVec *v : {&rhs_e, &rhs_o, &t_o, &bhat, &xs, &s, &p, &q, &z, &corr_o, &res_e, &res_o})
-    LQCD_TRY(v->alloc(ctx, nd, Vh));
+  // FP64: the prepared source, reconstruction and true residual; the CGLS
+  // vectors in the inner format (xs64, ti: separate only when mixed)
+  DVec rhs_e, rhs_o, t_o, bhat, corr_o, res_e, res_o, xs, s, p, q, z, xs64_, ti_;
+  for (DVec *v : {&rhs_e, &rhs_o, &t_o, &bhat, &corr_o, &res_e, &res_o}) LQCD_TRY(v->alloc(ctx, nd, Vh));
+  for (DVec *v : {&xs, &s, &p, &q, &z}) LQCD_TRY(v->alloc(ctx, nd, Vh, inner));
+  if (mixed) {
+    LQCD_TRY(xs64_.alloc(ctx, nd, Vh));
+    LQCD_TRY(ti_.alloc(ctx, nd, Vh, inner));
+  }
+  const DVec &xs64 = mixed ? xs64_ : xs, &ti = mixed ? ti_ : t_o;
+  const size_t hbi = spinor_half_bytes(inner, Vh);
   const HostC one{1.0, 0.0}, zero{0.0, 0.0}, mone{-1.0, 0.0};
   lqcd_status result = LQCD_OK;
   for (int d = 0; d < nd; d++) {
@@ -241,16 +273,18 @@ lqcd_status dd_cg_solve(lqcd_ctx *ctx, int nd, int first, int nt, int antiper, c
     lqcd_status e = S.lin(t_o, rhs_o, nullptr, c.Ai_up, c.Ai_dn, zero, zero, nullptr);
     if (e == LQCD_OK)
       e = S.hop(t_o, bhat, &rhs_e, 0, false, {kappa, 0.0}, {kappa, 0.0}, one, one, nullptr);
-    // CGLS on Mhat^+ Mhat: xs = 0, s = bhat, z = p = Mhat^+ s
+    // CGLS on Mhat^+ Mhat in the inner format: xs = 0, s = bhat, z = p = Mhat^+ s
     double ss = 0.0, zz = 0.0, qq = 0.0;
     for (int d = 0; d < nd && e == LQCD_OK; d++)
-      if (cudaMemsetAsync(xs.f[d].ptr, 0, hb, ctx->stream) != cudaSuccess)
+      if (cudaMemsetAsync(xs.f[d].ptr, 0, hbi, ctx->stream) != cudaSuccess)
         e = cuda_check(ctx, cudaGetLastError(), "cudaMemsetAsync");
-    if (e == LQCD_OK) e = S.lin(s, bhat, nullptr, one, one, zero, zero, &ss);
-    if (e == LQCD_OK && ss > stop2) e = S.mhat(s, z, t_o, true, &zz);
-    if (e == LQCD_OK && ss > stop2) e = S.lin(p, z, nullptr, one, one, zero, zero, nullptr);
-    while (e == LQCD_OK && ss > stop2 && st->iters < prm.max_iter) {
-      e = S.mhat(p, q, t_o, false, &qq);
+    if (e == LQCD_OK && mixed) e = S.convert(bhat, s);
+    if (e == LQCD_OK) e = S.lin(s, mixed ? s : bhat, nullptr, one, one, zero, zero, &ss);
+    const double istop2 = std::fmax(stop2, itol * itol * ss);
+    if (e == LQCD_OK && ss > istop2) e = S.mhat(s, z, ti, true, &zz);
+    if (e == LQCD_OK && ss > istop2) e = S.lin(p, z, nullptr, one, one, zero, zero, nullptr);
+    while (e == LQCD_OK && ss > istop2 && st->iters < prm.max_iter) {
+      e = S.mhat(p, q, ti, false, &qq);
       if (e != LQCD_OK) break;
       if (!(qq > 0.0) || !std::isfinite(qq)) {
         if (!std::isfinite(qq)) e = fail(ctx, LQCD_ERR_NONFINITE, "domain-decomposed CG: |Mhat p|^2 not finite");
@@ -261,19 +295,20 @@ lqcd_status dd_cg_solve(lqcd_ctx *ctx, int nd, int first, int nt, int antiper, c
       if (e == LQCD_OK) e = S.lin(s, s, &q, one, one, {-alpha, 0.0}, {-alpha, 0.0}, &ss);
       if (e != LQCD_OK) break;
       st->iters++;
-      if (ss <= stop2) break;
+      if (ss <= istop2) break;
       double zz1 = 0.0;
-      e = S.mhat(s, z, t_o, true, &zz1);
+      e = S.mhat(s, z, ti, true, &zz1);
       if (e != LQCD_OK) break;
       const double beta = zz1 / zz;
       zz = zz1;
       e = S.lin(p, z, &p, one, one, {beta, 0.0}, {beta, 0.0}, nullptr);
     }
-    // corr_o = A_o^-1 (rhs_o + kappa H_oe xs); x += corr
+    // corr_o = A_o^-1 (rhs_o + kappa H_oe xs) in FP64; x += corr
+    if (e == LQCD_OK && mixed) e = S.convert(xs, xs64);
     if (e == LQCD_OK)
-      e = S.hop(xs, corr_o, &rhs_o, 1, false, scaled(c.Ai_up, kappa), scaled(c.Ai_dn, kappa), c.Ai_up, c.Ai_dn,
+      e = S.hop(xs64, corr_o, &rhs_o, 1, false, scaled(c.Ai_up, kappa), scaled(c.Ai_dn, kappa), c.Ai_up, c.Ai_dn,
                 nullptr);
-    if (e == LQCD_OK) e = S.lin(xe, xe, &xs, one, one, one, one, nullptr);
+    if (e == LQCD_OK) e = S.lin(xe, xe, &xs64, one, one, one, one, nullptr);
     if (e == LQCD_OK) e = S.lin(xo, xo, &corr_o, one, one, one, one, nullptr);
     // true residual: rhs = b - M x, M x = A x - kappa H x on both parities
     if (e == LQCD_OK) e = S.hop(xo, res_e, &xe, 0, false, {-kappa, 0.0}, {-kappa, 0.0}, c.A_up, c.A_dn, nullptr);

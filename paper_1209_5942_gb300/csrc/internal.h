@@ -280,11 +280,13 @@ int hop_blocks(const Geom &g, int nrhs);
 // f1 = face from the previous one)
 lqcd_status dd_run(lqcd_ctx *ctx, const Geom &g, const HopLaunch &L, bool pack, void *f0, void *f1, int n0, int n1);
 size_t dd_face_word_bytes(int prec);
-// domain-decomposed FP64 CG (dd_cg.cu): nd held domains, the first of global
-// index `first` of nt; b_full / x_full: EO full fields of each held domain;
-// faces: 4 per held domain (to_prev, to_next, from_next, from_prev)
+// domain-decomposed CG (dd_cg.cu): nd held domains, the first of global
+// index `first` of nt; U: FP64 links, Ui: links of the inner format
+// (prm.inner_prec F64: unused); b_full / x_full: EO full fields of each held
+// domain; faces: 4 per held domain (to_prev, to_next, from_next, from_prev)
 lqcd_status dd_cg_solve(lqcd_ctx *ctx, int nd, int first, int nt, int antiper, const Geom &g, int recon,
-                        const std::vector<GaugeView> &U, const std::vector<HalfField> &b_full,
+                        const std::vector<GaugeView> &U, int recon_i, const std::vector<GaugeView> &Ui,
+                        const std::vector<HalfField> &b_full,
                         const std::vector<HalfField> &x_full, const std::vector<void *> &faces, size_t fb,
                         const lqcd_dd_comm *comm, double kappa, double mu, const lqcd_cg_params &prm,
                         lqcd_cg_stats *st);

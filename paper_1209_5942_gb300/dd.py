@@ -158,8 +158,9 @@ def dslash_distributed(ctx, slabs: TimeSlabs, rank: int, gauge, inp, out, out_pa
 
 def cg_solve_local_domains(ctx, slabs: TimeSlabs, gauges, bs, xs, kappa, mu, params, faces=None,
                            allow_noconv=False):
-    """Domain-decomposed FP64 CG with every domain of `slabs` held in this
-    process (one device): gauges[d], bs[d], xs[d] (EO full fields of domain d
+    """Domain-decomposed CG (FP64, or mixed with an F32 / float-float inner
+    format as params say) with every domain of `slabs` held in this process
+    (one device): gauges[d], bs[d], xs[d] (EO full fields of domain d
     on the local geometry).  Returns the solve's stats."""
     if faces is None:
         faces = [face_buffers(slabs, lqcd.LQCD_F64) for _ in range(slabs.nt)]
@@ -169,8 +170,9 @@ def cg_solve_local_domains(ctx, slabs: TimeSlabs, gauges, bs, xs, kappa, mu, par
 
 class DistributedComm:
     """The communication hooks of a domain-decomposed solve with one domain
-    per rank of a torch.distributed group: exchange() moves this rank's faces
-    (DistributedExchange; device faces through host copies for gloo),
+    per rank of a torch.distributed group: exchange(nbytes) moves the leading
+    nbytes of this rank's faces (all of them if None; DistributedExchange,
+    device faces through host copies for gloo),
     allreduce(values) sums host floats over the group (on the CPU for gloo,
     on the device for NCCL)."""
 
@@ -178,17 +180,20 @@ class DistributedComm:
         self.slabs, self.rank, self.faces, self.group = slabs, rank, faces, group
         self._ex = DistributedExchange(group)
 
-    def exchange(self):
+    def exchange(self, nbytes=None):
         import torch.distributed as dist
-        if self.faces[0].is_cuda and dist.get_backend(self.group) == "gloo":
+        faces = self.faces
+        if nbytes is not None:  # the face of a lower format fills the buffers' leading bytes
+            faces = [f.view(torch.uint8)[:nbytes] for f in faces]
+        if faces[0].is_cuda and dist.get_backend(self.group) == "gloo":
             # gloo moves host memory: stage the device faces through the host
-            host = [f.cpu() for f in self.faces]
+            host = [f.cpu() for f in faces]
             self._ex.exchange(self.slabs, self.rank, *host)
-            self.faces[2].copy_(host[2])
-            self.faces[3].copy_(host[3])
+            faces[2].copy_(host[2])
+            faces[3].copy_(host[3])
         else:
-            self._ex.exchange(self.slabs, self.rank, *self.faces)
-        if self.faces[0].is_cuda:
+            self._ex.exchange(self.slabs, self.rank, *faces)
+        if faces[0].is_cuda:
             torch.cuda.current_stream().synchronize()
 
     def allreduce(self, values):
@@ -201,8 +206,9 @@ class DistributedComm:
 
 def cg_solve_distributed(ctx, slabs: TimeSlabs, rank: int, gauge, b, x, kappa, mu, params, group=None,
                          faces=None, allow_noconv=False):
-    """Domain-decomposed FP64 CG with this rank's domain (rank = domain index)
-    in a torch.distributed job; NCCL moves the CUDA face buffers."""
+    """Domain-decomposed CG (FP64 or mixed, as params say) with this rank's
+    domain (rank = domain index) in a torch.distributed job; NCCL moves the
+    CUDA face buffers."""
     if faces is None:
         faces = face_buffers(slabs, lqcd.LQCD_F64)
     comm = DistributedComm(slabs, rank, faces, group)

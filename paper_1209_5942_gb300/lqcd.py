@@ -99,7 +99,7 @@ _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 _FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 
 # communication hooks of the domain-decomposed solve (lqcd_dd_comm)
-_EXCHANGE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p)
+_EXCHANGE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t)
 _ALLREDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int)
 
 
@@ -488,9 +488,10 @@ def lqcd_dd_cg_solve(ctx: Context, Us, bs, xs, faces, first_domain, nt, kappa, m
                      params: lqcd_cg_params, antiperiodic_t=True, exchange=None, allreduce=None,
                      allow_noconv=False):
     """Domain-decomposed CG (include/lqcd.h): Us, bs, xs, faces for the held
-    domains (faces: 4 device tensors per domain); exchange() / allreduce(list of
-    floats) -> list: the communication hooks (None for all domains in this
-    call).  The hooks are called from inside the library call."""
+    domains (faces: 4 device tensors per domain); exchange(nbytes) (move the
+    leading nbytes of each face) / allreduce(list of floats) -> list: the
+    communication hooks (None for all domains in this call).  The hooks are
+    called from inside the library call."""
     nd = len(Us)
     g = Us[0].geom
     U_arr = (_vp * nd)(*[u.handle for u in Us])
@@ -501,9 +502,9 @@ def lqcd_dd_cg_solve(ctx: Context, Us, bs, xs, faces, first_domain, nt, kappa, m
     comm_p = None
     errors = []
     if exchange is not None:
-        def _ex(_user):
+        def _ex(_user, nbytes):
             try:
-                exchange()
+                exchange(int(nbytes))
                 return 0
             except Exception as e:  # reported as LQCD_ERR_COMM; re-raised below
                 errors.append(e)

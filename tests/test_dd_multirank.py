@@ -3,8 +3,9 @@ time-slab geometry, the neighbours and global boundary signs, and the face
 exchange of DistributedExchange with 2 and 4 ranks, whose routing must give
 every domain the `to_prev` face of its next domain and the `to_next` face of
 its previous one (with two ranks both are the same peer), and the hooks of
-the domain-decomposed solver (DistributedComm: the same exchange, and the sum
-of host values over the ranks).  The GPU kernels of the hop and the solver
+the domain-decomposed solver (DistributedComm: the same exchange, of the
+whole buffers or of their leading bytes, and the sum of host values over the
+ranks).  The GPU kernels of the hop and the solver
 are checked against the oracle in tests/test_gpu_dd.py."""
 import os
 import socket
@@ -53,6 +54,13 @@ def _worker(rank, world, port, L, errq):
         from_prev.zero_()
         comm.exchange()
         assert torch.equal(from_next, exp_next) and torch.equal(from_prev, exp_prev), rank
+        # a face of a lower format: only the leading bytes move, the rest of
+        # the receive buffers is left as it was
+        from_next.fill_(-7.0)
+        from_prev.fill_(-7.0)
+        comm.exchange(40 * 8)
+        assert torch.equal(from_next[:40], exp_next[:40]) and torch.equal(from_prev[:40], exp_prev[:40]), rank
+        assert bool((from_next[40:] == -7.0).all()) and bool((from_prev[40:] == -7.0).all()), rank
         sums = comm.allreduce([float(rank + 1), 0.5, -2.0 * rank])
         assert sums == [world * (world + 1) / 2, 0.5 * world, -float(world * (world - 1))], (rank, sums)
         assert slabs.next(rank) == nxt and slabs.prev(rank) == prv

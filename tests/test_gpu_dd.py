@@ -118,7 +118,7 @@ def test_dd_rejects_bad_input(ctx):
 
 
 # ---------------------------------------------------------------------------
-# The domain-decomposed FP64 CG (lqcd_dd_cg_solve)
+# The domain-decomposed CG (lqcd_dd_cg_solve), FP64 and mixed precision
 # ---------------------------------------------------------------------------
 
 def _dd_solve(ctx, U, b, L, nt, kappa, mu, antiper=True, recon=18, hooks=None, **kw):
@@ -194,22 +194,27 @@ def test_dd_cg_iterations_match_the_single_domain_solver(ctx, oracle):
         assert relerr(x, host(xg)) < 1e-8
 
 
-def test_dd_cg_with_caller_hooks_equals_library_moves(ctx):
+@pytest.mark.parametrize("inner", [lqcd.LQCD_F64, lqcd.LQCD_F32])
+def test_dd_cg_with_caller_hooks_equals_library_moves(ctx, inner):
     """The same solve with the faces moved and the norms summed by the
     caller's hooks (as a multi-process job would, here device copies in one
-    process) gives the same bits; every half hop calls the exchange hook and
-    every norm the allreduce hook."""
+    process, of the leading bytes the library names only) gives the same
+    bits; every half hop calls the exchange hook and every norm the allreduce
+    hook; a mixed solve asks for FP64 faces in its FP64 steps and for F32
+    faces (half the bytes) in its inner ones."""
     L = (4, 4, 4, 8)
     kappa, mu = 0.15, 0.01 / 0.3
     U = inputs.random_gauge(L, "haar", seed=85)
     b = inputs.gaussian_spinor(L, 86)
-    calls = {"ex": 0, "ar": 0}
+    calls = {"ex": 0, "ar": 0, "bytes": set()}
 
     def hooks(slabs, faces):
-        def exchange():
+        def exchange(nbytes):
             calls["ex"] += 1
-            dd.LocalExchange().exchange(slabs, [f[0] for f in faces], [f[1] for f in faces],
-                                        [f[2] for f in faces], [f[3] for f in faces])
+            calls["bytes"].add(nbytes)
+            lead = [[f.view(torch.uint8)[:nbytes] for f in fs] for fs in faces]
+            dd.LocalExchange().exchange(slabs, [f[0] for f in lead], [f[1] for f in lead],
+                                        [f[2] for f in lead], [f[3] for f in lead])
             torch.cuda.synchronize()
 
         def allreduce(vals):
@@ -217,10 +222,50 @@ def test_dd_cg_with_caller_hooks_equals_library_moves(ctx):
             return vals
         return exchange, allreduce
 
-    x0, st0 = _dd_solve(ctx, U, b, L, 2, kappa, mu, tol=1e-10)
-    x1, st1 = _dd_solve(ctx, U, b, L, 2, kappa, mu, hooks=hooks, tol=1e-10)
+    x0, st0 = _dd_solve(ctx, U, b, L, 2, kappa, mu, tol=1e-10, inner_prec=inner)
+    x1, st1 = _dd_solve(ctx, U, b, L, 2, kappa, mu, hooks=hooks, tol=1e-10, inner_prec=inner)
     assert st0["iters"] == st1["iters"] and np.array_equal(x0, x1)
     assert calls["ex"] >= 4 * st1["iters"] and calls["ar"] >= 3 * st1["iters"]
+    fb64 = lqcd.lqcd_dd_face_bytes(dd.TimeSlabs(L, 2).local_L, lqcd.LQCD_F64)
+    assert calls["bytes"] == ({fb64} if inner == lqcd.LQCD_F64 else {fb64, fb64 // 2})
+
+
+@pytest.mark.parametrize("inner", [lqcd.LQCD_F32, lqcd.LQCD_DF64])
+@pytest.mark.parametrize("L,nt", [((4, 4, 4, 8), 1), ((4, 4, 4, 8), 2), ((4, 4, 4, 8), 4), ((6, 4, 2, 12), 3)])
+def test_dd_mixed_cg_matches_oracle(ctx, oracle, L, nt, inner):
+    """Mixed precision in the decomposed solve (defect correction with an F32
+    or float-float inner CGLS): the oracle's true residual 1e-10 on the whole
+    lattice and the oracle's own solution, for 18 and 12 real links, 12-real
+    inner links under an 18-real field, and antiperiodic and periodic time;
+    the F32 solve needs refinement cycles (each gains 1e-5 at most)."""
+    kappa, mu = 0.15, 0.01 / 0.3
+    U = inputs.random_gauge(L, "haar", seed=81)
+    b = inputs.gaussian_spinor(L, 82)
+    xr = {ap: oracle.solve(U, b, L, kappa, mu, tol=1e-13, antiperiodic_t=ap) for ap in (True, False)}
+    for recon, sloppy, antiper in ((18, 0, True), (12, 0, True), (18, 12, True), (18, 0, False)):
+        x, st = _dd_solve(ctx, U, b, L, nt, kappa, mu, antiper=antiper, recon=recon, tol=1e-10,
+                          inner_prec=inner, sloppy_recon=sloppy)
+        assert st["converged"] == 1 and st["true_resid"] <= 1e-10, (recon, sloppy, antiper, st)
+        assert _oracle_resid(oracle, U, L, x, b, kappa, mu, antiper) <= 1e-10
+        assert np.linalg.norm(x - xr[antiper]) / np.linalg.norm(xr[antiper]) < 1e-7, (recon, sloppy, antiper)
+        if inner == lqcd.LQCD_F32:
+            assert st["restarts"] >= 1, st
+
+
+def test_dd_mixed_cg_iterations_near_the_fp64_solve(ctx):
+    """On a bench-like field (near-identity links, kappa = 0.16) the F32 inner
+    solve with defect correction takes at most 1.5 times the FP64 solve's
+    iterations to the same tolerance, and the float-float one at most 1.1
+    times; every solve reaches 1e-10."""
+    L = (8, 4, 4, 8)
+    kappa, mu = 0.16, 0.005 / 0.32
+    U = inputs.random_gauge(L, "near", seed=83, eps=0.3)
+    b = inputs.gaussian_spinor(L, 84)
+    _, s64 = _dd_solve(ctx, U, b, L, 2, kappa, mu, tol=1e-10)
+    for inner, bound in ((lqcd.LQCD_F32, 1.5), (lqcd.LQCD_DF64, 1.1)):
+        _, st = _dd_solve(ctx, U, b, L, 2, kappa, mu, tol=1e-10, inner_prec=inner)
+        assert st["true_resid"] <= 1e-10, (inner, st)
+        assert st["iters"] <= bound * s64["iters"] + 2, (inner, st["iters"], s64["iters"])
 
 
 def test_dd_cg_reports_hook_failures_and_bad_requests(ctx):
@@ -229,7 +274,7 @@ def test_dd_cg_reports_hook_failures_and_bad_requests(ctx):
     b = inputs.gaussian_spinor(L, 88)
 
     def failing(slabs, faces):
-        def exchange():
+        def exchange(nbytes):
             raise RuntimeError("peer lost")
         return exchange, None
 
@@ -245,13 +290,14 @@ def test_dd_cg_reports_hook_failures_and_bad_requests(ctx):
     with pytest.raises(lqcd.LqcdError) as e:  # one of two domains, no hooks
         lqcd.lqcd_dd_cg_solve(ctx, [G], [fb], [fx], faces, 0, 2, 0.15, 0.1, lqcd.cg_params())
     assert e.value.status == lqcd.LQCD_ERR_INVALID
-    with pytest.raises(lqcd.LqcdError) as e:  # mixed precision is not offered here
-        lqcd.lqcd_dd_cg_solve(ctx, [G], [fb], [fx], faces, 0, 1, 0.15, 0.1,
-                              lqcd.cg_params(inner_prec=lqcd.LQCD_F32))
-    assert e.value.status == lqcd.LQCD_ERR_UNSUPPORTED
+    for bad in (dict(inner_prec=lqcd.LQCD_BF16S), dict(outer_prec=lqcd.LQCD_DF64, inner_prec=lqcd.LQCD_F32),
+                dict(solver=lqcd.LQCD_SOLVER_BICGSTAB)):
+        with pytest.raises(lqcd.LqcdError) as e:  # 16-bit inner, float-float outer, BiCGStab: not offered
+            lqcd.lqcd_dd_cg_solve(ctx, [G], [fb], [fx], faces, 0, 1, 0.15, 0.1, lqcd.cg_params(**bad))
+        assert e.value.status == lqcd.LQCD_ERR_UNSUPPORTED, bad
 
 
-def _dd_rank(rank, world, port, L, kappa, mu, q):
+def _dd_rank(rank, world, port, L, kappa, mu, inner, q):
     """One rank of a two-process decomposed solve: its own CUDA context on the
     same GPU, gloo for the face exchange (through host copies) and the norm
     sums, so no kernel waits on the other process."""
@@ -271,7 +317,8 @@ def _dd_rank(rank, world, port, L, kappa, mu, q):
         _, _, fb = eo_full_from_lexi_local(ctx, Ll, b[slabs.block(rank)], lqcd.LQCD_F64)
         xd, _ = lqcd.alloc_field(Ll, lqcd.LQCD_FULL, lqcd.LQCD_F64)
         fx = lqcd.field(xd, lqcd.LQCD_LAYOUT_EO)
-        st = dd.cg_solve_distributed(ctx, slabs, rank, G, fb, fx, kappa, mu, lqcd.cg_params(tol=1e-10))
+        st = dd.cg_solve_distributed(ctx, slabs, rank, G, fb, fx, kappa, mu,
+                                     lqcd.cg_params(tol=1e-10, inner_prec=inner))
         torch.cuda.synchronize()
         o = torch.zeros((1, slabs.local_volume, 4, 3), dtype=torch.complex128, device="cuda")
         lqcd.lqcd_spinor_unpack(ctx, Ll, fx, o, antiperiodic_t=False)
@@ -282,11 +329,13 @@ def _dd_rank(rank, world, port, L, kappa, mu, q):
         q.put((rank, None, repr(e)))
 
 
-def test_dd_cg_two_processes_with_gloo(ctx, oracle):
+@pytest.mark.parametrize("inner", [lqcd.LQCD_F64, lqcd.LQCD_F32])
+def test_dd_cg_two_processes_with_gloo(ctx, oracle, inner):
     """The decomposed solve as a two-process job (one domain per rank, the
-    solver's hooks from DistributedComm over gloo): the assembled solution
-    reaches the oracle's true residual 1e-10 on the whole lattice, and both
-    ranks report the same iterations and residual."""
+    solver's hooks from DistributedComm over gloo), FP64 and with an F32
+    inner solve: the assembled solution reaches the oracle's true residual
+    1e-10 on the whole lattice, and both ranks report the same iterations and
+    residual."""
     import socket
     import torch.multiprocessing as mp
     s_ = socket.socket()
@@ -297,7 +346,7 @@ def test_dd_cg_two_processes_with_gloo(ctx, oracle):
     kappa, mu = 0.15, 0.01 / 0.3
     mpc = mp.get_context("spawn")
     q = mpc.Queue()
-    procs = [mpc.Process(target=_dd_rank, args=(r, 2, port, L, kappa, mu, q)) for r in range(2)]
+    procs = [mpc.Process(target=_dd_rank, args=(r, 2, port, L, kappa, mu, inner, q)) for r in range(2)]
     for p_ in procs:
         p_.start()
     got = {}
