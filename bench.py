@@ -1009,11 +1009,11 @@ def run_config(args):
                                              max_iter=50000, max_restarts=10),
                    "f64/df64": lqcd.cg_params(tol=TOL, outer_prec=lqcd.LQCD_F64, inner_prec=lqcd.LQCD_DF64,
                                               max_iter=50000)}
-        for nt in (1, 2, 4):
-            slabs = dd.TimeSlabs(L, nt)
+        for nz, nt in ((1, 1), (1, 2), (1, 4), (2, 2)):
+            slabs = dd.DomainGrid(L, nz, nt)
             Ll = slabs.local_L
             gs, bs, xs, keep = [], [], [], []
-            for d in range(nt):
+            for d in range(slabs.ndomains):
                 gs.append(lqcd.lqcd_gauge_import(ctx, torch.from_numpy(U[slabs.block(d)]).cuda(), Ll, recon=18,
                                                  antiperiodic_t=False))
                 bdd, _ = lqcd.alloc_field(Ll, lqcd.LQCD_FULL, lqcd.LQCD_F64)
@@ -1023,12 +1023,13 @@ def run_config(args):
                 bs.append(f)
                 xs.append(lqcd.field(xdd, lqcd.LQCD_LAYOUT_EO))
                 keep.append((bdd, xdd))
-            faces = [dd.face_buffers(slabs, lqcd.LQCD_F64) for _ in range(nt)]
+            faces = [dd.domain_faces(slabs, lqcd.LQCD_F64) for _ in range(slabs.ndomains)]
             for name, pv in dd_prms.items():
                 dd.cg_solve_local_domains(ctx, slabs, gs, bs, xs, KAPPA, MU, pv, faces=faces)
                 t, st = _timed(torch, lambda: dd.cg_solve_local_domains(ctx, slabs, gs, bs, xs, KAPPA, MU, pv,
                                                                         faces=faces))
-                key = f"nt{nt}" if name == "f64" else f"nt{nt}_{name}"
+                grid = f"nt{nt}" if nz == 1 else f"nz{nz}nt{nt}"
+                key = grid if name == "f64" else f"{grid}_{name}"
                 res[key] = {"solve_s": t, "iters": st["iters"], "restarts": st["restarts"],
                             "true_resid": st["true_resid"], "vs_single_domain": t / t1}
             for G_ in gs:
@@ -1036,7 +1037,7 @@ def run_config(args):
         config_line("domain-decomposed CG", None, {"dd": res},
                     {"workload": "24^3x48 exp(i 0.3 H) links, kappa=0.16, 2 kappa mu=0.005, CG to 1e-10 "
                                  "(FP64, or FP64 outer with an F32 / float-float inner solve); "
-                                 "t split into nt domains on one GPU (faces by device copies)"})
+                                 "t split into nt domains (nz x nt: z and t) on one GPU (faces by device copies)"})
     elif c == "sweep":
         res = {}
         for ns in (16, 24, 32, 48):

@@ -67,7 +67,7 @@
 extern "C" {
 #endif
 
-#define LQCD_ABI_VERSION 1
+#define LQCD_ABI_VERSION 2
 
 typedef enum {
   LQCD_OK = 0,
@@ -253,7 +253,8 @@ int lqcd_dslash(lqcd_ctx *ctx, const lqcd_gauge *U, lqcd_field in, lqcd_field ou
                 const lqcd_geom *geom, int out_parity, int dagger);
 
 /* ---------------------------------------------------------------- */
-/* Domain decomposition along t (Sec. 6: the hop over several GPUs)  */
+/* Domain decomposition along t and z (Sec. 6: the hop over several */
+/* GPUs)                                                             */
 /* ---------------------------------------------------------------- */
 
 /* A lattice of extent Lt in t split into nt domains of Lt / nt slices (one per
@@ -296,6 +297,34 @@ int lqcd_dd_pack(lqcd_ctx *ctx, const lqcd_gauge *U, lqcd_field in, void *face_t
  * errors as lqcd_dd_pack; in and out must not alias.  Asynchronous. */
 int lqcd_dd_dslash(lqcd_ctx *ctx, const lqcd_gauge *U, lqcd_field in, lqcd_field out, const void *face_from_next,
                    const void *face_from_prev, const lqcd_geom *local, int out_parity, int dagger);
+
+/* Split along z as well: a grid of nz x nt domains, domain dz + nz dt
+ * holding z in [dz Lz/nz, (dz+1) Lz/nz) and t in [dt Lt/nt, (dt+1) Lt/nt),
+ * on the local geometry (Lx, Ly, Lz/nz, Lt/nt), both split extents even.
+ * The z hops that cross a domain boundary take faces as the t hops do: along
+ * mu = 2 a face holds Lx Ly (Lt/nt) / 2 sites x 6 complex numbers, indexed by
+ * (x/2) + Lx/2 (y + Ly t) within the boundary z slice (along mu = 3 by
+ * (x/2) + Lx/2 (y + Ly z) within the t slice, as above).  z is periodic: no z
+ * face is negated.  Bytes of one face along mu = 2 or 3 (0 for invalid
+ * input; lqcd_dd_face_bytes is mu = 3): */
+size_t lqcd_dd_face_bytes_dir(const lqcd_geom *local, int mu, int prec);
+
+/* lqcd_dd_pack for the two faces along mu = 2 (z: the sites at local z = 0
+ * and, times U_z^+, at z = Lz/nz - 1) or mu = 3 (t: lqcd_dd_pack itself);
+ * buffers of lqcd_dd_face_bytes_dir(local, mu, prec) each.  Same fields and
+ * errors as lqcd_dd_pack; mu other than 2 or 3: LQCD_ERR_INVALID. */
+int lqcd_dd_pack_dir(lqcd_ctx *ctx, const lqcd_gauge *U, lqcd_field in, int mu, void *face_to_prev,
+                     void *face_to_next, const lqcd_geom *local, int out_parity, int dagger, int negate_to_prev,
+                     int negate_to_next);
+
+/* The half hop of a domain of an nz x nt grid: lqcd_dd_dslash with the t
+ * faces t_from_next / t_from_prev, and the z hops across the domain's z
+ * boundaries from z_from_next (the next z domain's z face_to_prev) and
+ * z_from_prev (the previous one's face_to_next); both z faces NULL: z is not
+ * split (lqcd_dd_dslash).  Asynchronous. */
+int lqcd_dd_dslash_zt(lqcd_ctx *ctx, const lqcd_gauge *U, lqcd_field in, lqcd_field out, const void *t_from_next,
+                      const void *t_from_prev, const void *z_from_next, const void *z_from_prev,
+                      const lqcd_geom *local, int out_parity, int dagger);
 
 /* parity = LQCD_FULL: out = M in on the whole lattice (fields LEXI or EO full).
  * parity = LQCD_EVEN: out = Mhat in on the even sites (EO half fields).
@@ -367,32 +396,37 @@ int lqcd_cg_solve(lqcd_ctx *ctx, const lqcd_gauge *U, lqcd_field b, lqcd_field x
 
 /* Communication of a domain-decomposed solve (lqcd_dd_cg_solve), called by
  * the library from the calling thread between its launches:
- *   exchange(user, bytes): every held domain's to_prev and to_next faces are
- *     written in their leading `bytes` bytes (lqcd_dd_face_bytes of the
- *     format of that half hop: LQCD_F64 for the FP64 steps, the inner format
- *     for the inner ones; the library's stream has been synchronised); the
- *     hook delivers those bytes of each to_prev face to the previous domain's
- *     from_next buffer and of each to_next face to the next domain's
- *     from_prev buffer, and returns once they are in place;
+ *   exchange(user, t_bytes, z_bytes): every held domain's to_prev and to_next
+ *     faces are written in their leading t_bytes (t faces) and z_bytes (z
+ *     faces; 0 when z is not split) bytes: lqcd_dd_face_bytes_dir of the
+ *     format of that half hop, LQCD_F64 for the FP64 steps and the inner
+ *     format for the inner ones (the library's stream has been
+ *     synchronised); the hook delivers those bytes of each to_prev face to
+ *     the from_next buffer of the previous domain along the same direction
+ *     and of each to_next face to the next domain's from_prev buffer, and
+ *     returns once they are in place;
  *   allreduce(user, vals, n): sums n host doubles over all processes of the
  *     solve, in place (NULL: a single process).
  * Both return 0 on success; anything else ends the solve with LQCD_ERR_COMM. */
 typedef struct {
   void *user;
-  int (*exchange)(void *user, size_t bytes);
+  int (*exchange)(void *user, size_t t_bytes, size_t z_bytes);
   int (*allreduce)(void *user, double *vals, int n);
 } lqcd_dd_comm;
 
 /* The even-odd CG of lqcd_cg_solve (CGLS on Mhat^+ Mhat, source preparation,
  * reconstruction, FP64 true residual and outer refinement; one right-hand
- * side) on a lattice split along t into nt domains as for
- * lqcd_dd_pack (Sec. 6 outlook: the solver over several GPUs).  This call
- * holds nd consecutive domains, first_domain .. first_domain + nd - 1, each on
- * the local geometry `local` (local->L[3] = Lt / nt, even; local must match
- * the gauge fields' geometry): U[k] its gauge field, b[k] and x[k] EO full
- * fields (LQCD_F64, nrhs = 1; x is overwritten), faces[4k .. 4k+3] its
- * to_prev, to_next, from_next and from_prev face buffers (device,
- * lqcd_dd_face_bytes(local, LQCD_F64) each, 16-byte aligned).  Every half hop
+ * side) on a lattice split into an nz x nt grid of domains as for
+ * lqcd_dd_dslash_zt (nz = 1: along t only; Sec. 6 outlook: the solver over
+ * several GPUs).  This call holds nd consecutive domains, first_domain ..
+ * first_domain + nd - 1 (domain dz + nz dt), each on the local geometry
+ * `local` (local->L[2] = Lz / nz, local->L[3] = Lt / nt, both even; local
+ * must match the gauge fields' geometry): U[k] its gauge field, b[k] and x[k]
+ * EO full fields (LQCD_F64, nrhs = 1; x is overwritten), and its face
+ * buffers (device, 16-byte aligned, lqcd_dd_face_bytes_dir(local, mu,
+ * LQCD_F64) each): with F = 4 (nz = 1) or 8, faces[F k .. F k + 3] its t
+ * to_prev, to_next, from_next and from_prev faces and, if nz > 1,
+ * faces[F k + 4 .. F k + 7] the same four along z.  Every half hop
  * packs the faces of all held domains, moves them and runs the domain hops
  * with the operator's diagonal epilogue; every norm is summed in a fixed
  * order on each domain, over the held domains in order, then over
@@ -402,17 +436,17 @@ typedef struct {
  * residual, until the residual has dropped by inner_tol (F32; 0 selects
  * 1e-5) or, for LQCD_DF64, to the tolerance; the source preparation, the
  * correction, the reconstruction and the true residual stay IEEE FP64.
- * comm = NULL: the call holds every domain (nd = nt, first_domain = 0) and
+ * comm = NULL: the call holds every domain (nd = nz nt, first_domain = 0) and
  * the library moves the faces by device copies; otherwise comm->exchange
  * moves them and comm->allreduce sums the norms.  antiperiodic_t: the
  * fermion boundary of the whole lattice.  params: tol, max_iter,
  * max_restarts, inner_tol, sloppy_recon (outer_prec LQCD_F64, inner_prec
- * LQCD_F64, LQCD_DF64 or LQCD_F32, solver CG, else LQCD_ERR_UNSUPPORTED).  stats: one entry; true_resid is that of the
- * whole lattice.  Synchronous; LQCD_ERR_NOCONV (stats filled) when tol is not
- * reached. */
+ * LQCD_F64, LQCD_DF64 or LQCD_F32, solver CG, else LQCD_ERR_UNSUPPORTED).
+ * stats: one entry; true_resid is that of the whole lattice.  Synchronous;
+ * LQCD_ERR_NOCONV (stats filled) when tol is not reached. */
 int lqcd_dd_cg_solve(lqcd_ctx *ctx, int nd, const lqcd_gauge *const *U, const lqcd_field *b,
                      const lqcd_field *x, void *const *faces, const lqcd_geom *local, int first_domain,
-                     int nt, int antiperiodic_t, double kappa, double mu, const lqcd_cg_params *params,
+                     int nz, int nt, int antiperiodic_t, double kappa, double mu, const lqcd_cg_params *params,
                      const lqcd_dd_comm *comm, lqcd_cg_stats *stats);
 
 /* Solves n independent systems M_k x_k = b_k on lattices of different sizes

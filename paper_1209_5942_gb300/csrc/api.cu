@@ -458,15 +458,21 @@ extern "C" int lqcd_dslash(lqcd_ctx *ctx, const lqcd_gauge *U, lqcd_field in, lq
 }
 
 // ===========================================================================
-// Domain decomposition along t
+// Domain decomposition along t and z
 // ===========================================================================
 
-extern "C" size_t lqcd_dd_face_bytes(const lqcd_geom *local, int prec) {
-  if (!local || (prec != LQCD_F64 && prec != LQCD_DF64 && prec != LQCD_F32)) return 0;
+extern "C" size_t lqcd_dd_face_bytes_dir(const lqcd_geom *local, int mu, int prec) {
+  if (!local || (prec != LQCD_F64 && prec != LQCD_DF64 && prec != LQCD_F32) || (mu != 2 && mu != 3)) return 0;
   for (int k = 0; k < 4; k++)
     if (local->L[k] < 2 || (local->L[k] & 1)) return 0;
-  return (size_t)(local->L[0] / 2) * local->L[1] * local->L[2] * 6 * dd_face_word_bytes(prec);
+  return (size_t)(local->L[0] / 2) * local->L[1] * local->L[mu == 3 ? 2 : 3] * 6 * dd_face_word_bytes(prec);
 }
+
+extern "C" size_t lqcd_dd_face_bytes(const lqcd_geom *local, int prec) {
+  return lqcd_dd_face_bytes_dir(local, 3, prec);
+}
+
+static bool bad_face(const void *f) { return !f || ((uintptr_t)f & 15u); }
 
 static lqcd_status dd_common(lqcd_ctx *ctx, const lqcd_gauge *U, const lqcd_field &in, const lqcd_geom *local,
                              int out_parity, int dagger, HopLaunch *L, Geom *g) {
@@ -489,26 +495,37 @@ static lqcd_status dd_common(lqcd_ctx *ctx, const lqcd_gauge *U, const lqcd_fiel
   return LQCD_OK;
 }
 
-extern "C" int lqcd_dd_pack(lqcd_ctx *ctx, const lqcd_gauge *U, lqcd_field in, void *face_to_prev,
-                            void *face_to_next, const lqcd_geom *local, int out_parity, int dagger,
-                            int negate_to_prev, int negate_to_next) {
+extern "C" int lqcd_dd_pack_dir(lqcd_ctx *ctx, const lqcd_gauge *U, lqcd_field in, int mu, void *face_to_prev,
+                                void *face_to_next, const lqcd_geom *local, int out_parity, int dagger,
+                                int negate_to_prev, int negate_to_next) {
   if (!ctx) return LQCD_ERR_INVALID;
-  if (!face_to_prev || !face_to_next || ((uintptr_t)face_to_prev & 15u) || ((uintptr_t)face_to_next & 15u))
+  if (mu != 2 && mu != 3) return fail(ctx, LQCD_ERR_INVALID, "faces along mu = 2 (z) or 3 (t)");
+  if (bad_face(face_to_prev) || bad_face(face_to_next))
     return fail(ctx, LQCD_ERR_INVALID, "faces: NULL or not 16-byte aligned");
   HopLaunch L;
   Geom g;
   LQCD_TRY(dd_common(ctx, U, in, local, out_parity, dagger, &L, &g));
-  const size_t fb = lqcd_dd_face_bytes(local, in.prec);
+  const size_t fb = lqcd_dd_face_bytes_dir(local, mu, in.prec);
   if (ranges_overlap(face_to_prev, fb, face_to_next, fb)) return fail(ctx, LQCD_ERR_INVALID, "faces alias");
-  return dd_run(ctx, g, L, true, face_to_prev, face_to_next, negate_to_prev ? 1 : 0, negate_to_next ? 1 : 0);
+  return dd_pack(ctx, g, L, mu, face_to_prev, face_to_next, negate_to_prev ? 1 : 0, negate_to_next ? 1 : 0);
 }
 
-extern "C" int lqcd_dd_dslash(lqcd_ctx *ctx, const lqcd_gauge *U, lqcd_field in, lqcd_field out,
-                              const void *face_from_next, const void *face_from_prev, const lqcd_geom *local,
-                              int out_parity, int dagger) {
+extern "C" int lqcd_dd_pack(lqcd_ctx *ctx, const lqcd_gauge *U, lqcd_field in, void *face_to_prev,
+                            void *face_to_next, const lqcd_geom *local, int out_parity, int dagger,
+                            int negate_to_prev, int negate_to_next) {
+  return lqcd_dd_pack_dir(ctx, U, in, 3, face_to_prev, face_to_next, local, out_parity, dagger, negate_to_prev,
+                          negate_to_next);
+}
+
+extern "C" int lqcd_dd_dslash_zt(lqcd_ctx *ctx, const lqcd_gauge *U, lqcd_field in, lqcd_field out,
+                                 const void *t_from_next, const void *t_from_prev, const void *z_from_next,
+                                 const void *z_from_prev, const lqcd_geom *local, int out_parity, int dagger) {
   if (!ctx) return LQCD_ERR_INVALID;
-  if (!face_from_next || !face_from_prev || ((uintptr_t)face_from_next & 15u) || ((uintptr_t)face_from_prev & 15u))
+  if (bad_face(t_from_next) || bad_face(t_from_prev))
     return fail(ctx, LQCD_ERR_INVALID, "faces: NULL or not 16-byte aligned");
+  if ((z_from_next == nullptr) != (z_from_prev == nullptr) ||
+      (z_from_next && (bad_face(z_from_next) || bad_face(z_from_prev))))
+    return fail(ctx, LQCD_ERR_INVALID, "z faces: both NULL, or both 16-byte aligned");
   HopLaunch L;
   Geom g;
   LQCD_TRY(dd_common(ctx, U, in, local, out_parity, dagger, &L, &g));
@@ -517,22 +534,29 @@ extern "C" int lqcd_dd_dslash(lqcd_ctx *ctx, const lqcd_gauge *U, lqcd_field in,
   const size_t bytes = spinor_half_bytes(in.prec, g.Vh);
   if (ranges_overlap(in.ptr, bytes, out.ptr, bytes)) return fail(ctx, LQCD_ERR_INVALID, "in and out alias");
   L.out = to_half(out, g, false);
-  return dd_run(ctx, g, L, false, const_cast<void *>(face_from_next), const_cast<void *>(face_from_prev), 0, 0);
+  return dd_hop(ctx, g, L, t_from_next, t_from_prev, z_from_next, z_from_prev);
+}
+
+extern "C" int lqcd_dd_dslash(lqcd_ctx *ctx, const lqcd_gauge *U, lqcd_field in, lqcd_field out,
+                              const void *face_from_next, const void *face_from_prev, const lqcd_geom *local,
+                              int out_parity, int dagger) {
+  return lqcd_dd_dslash_zt(ctx, U, in, out, face_from_next, face_from_prev, nullptr, nullptr, local, out_parity,
+                           dagger);
 }
 
 static lqcd_status check_cg_params(lqcd_ctx *ctx, const lqcd_cg_params *p);
 
 extern "C" int lqcd_dd_cg_solve(lqcd_ctx *ctx, int nd, const lqcd_gauge *const *U, const lqcd_field *b,
                                 const lqcd_field *x, void *const *faces, const lqcd_geom *local, int first_domain,
-                                int nt, int antiperiodic_t, double kappa, double mu, const lqcd_cg_params *params,
-                                const lqcd_dd_comm *comm, lqcd_cg_stats *stats) {
+                                int nz, int nt, int antiperiodic_t, double kappa, double mu,
+                                const lqcd_cg_params *params, const lqcd_dd_comm *comm, lqcd_cg_stats *stats) {
   if (!ctx) return LQCD_ERR_INVALID;
   if (!U || !b || !x || !faces || !local || !params || !stats)
     return fail(ctx, LQCD_ERR_INVALID, "domain-decomposed CG: NULL argument");
-  if (nt < 1 || nd < 1 || first_domain < 0 || first_domain + nd > nt)
-    return fail(ctx, LQCD_ERR_INVALID, "domain-decomposed CG: domains %d..%d of %d", first_domain,
-                first_domain + nd - 1, nt);
-  if (!comm && (nd != nt || first_domain != 0))
+  if (nz < 1 || nt < 1 || nd < 1 || first_domain < 0 || first_domain + nd > nz * nt)
+    return fail(ctx, LQCD_ERR_INVALID, "domain-decomposed CG: domains %d..%d of %d x %d", first_domain,
+                first_domain + nd - 1, nz, nt);
+  if (!comm && (nd != nz * nt || first_domain != 0))
     return fail(ctx, LQCD_ERR_INVALID, "domain-decomposed CG without comm hooks must hold every domain");
   if (comm && !comm->exchange) return fail(ctx, LQCD_ERR_INVALID, "domain-decomposed CG: no exchange hook");
   LQCD_TRY(check_cg_params(ctx, params));
@@ -542,15 +566,17 @@ extern "C" int lqcd_dd_cg_solve(lqcd_ctx *ctx, int nd, const lqcd_gauge *const *
     return fail(ctx, LQCD_ERR_UNSUPPORTED,
                 "domain-decomposed CG: CG with outer_prec F64 and inner_prec F64, DF64 or F32");
   if (!std::isfinite(kappa) || !std::isfinite(mu)) return fail(ctx, LQCD_ERR_NONFINITE, "kappa/mu not finite");
-  const size_t fb = lqcd_dd_face_bytes(local, LQCD_F64);
-  if (fb == 0) return fail(ctx, LQCD_ERR_INVALID, "domain-decomposed CG: bad local geometry");
+  const size_t fb_t = lqcd_dd_face_bytes_dir(local, 3, LQCD_F64), fb_z = lqcd_dd_face_bytes_dir(local, 2, LQCD_F64);
+  if (fb_t == 0) return fail(ctx, LQCD_ERR_INVALID, "domain-decomposed CG: bad local geometry");
   lqcd_geom lg = *local;
   lg.antiperiodic_t = 0;  // the global boundary sign travels in the faces
   const Geom g = make_geom(lg);
   const size_t full_bytes = 2 * spinor_half_bytes(LQCD_F64, g.Vh);
+  const int nf = nz > 1 ? 8 : 4;  // faces per held domain: t, then z
   std::vector<GaugeView> views(nd), views_i(inner == LQCD_F64 ? 0 : nd);
   std::vector<HalfField> bf(nd), xf(nd);
-  std::vector<void *> fv(4 * (size_t)nd);
+  std::vector<void *> fv((size_t)nf * nd);
+  auto fsize = [&](int i) { return i % nf < 4 ? fb_t : fb_z; };
   int recon = 0, recon_i = 0;
   for (int d = 0; d < nd; d++) {
     LQCD_TRY(check_gauge(ctx, U[d], local));
@@ -569,16 +595,18 @@ extern "C" int lqcd_dd_cg_solve(lqcd_ctx *ctx, int nd, const lqcd_gauge *const *
       return fail(ctx, LQCD_ERR_INVALID, "domain-decomposed CG: b and x alias");
     bf[d] = to_half(b[d], g, true);
     xf[d] = to_half(x[d], g, true);
-    for (int k = 0; k < 4; k++) {
-      void *f = faces[4 * d + k];
-      if (!f || ((uintptr_t)f & 15u)) return fail(ctx, LQCD_ERR_INVALID, "faces: NULL or not 16-byte aligned");
-      for (int j = 0; j < 4 * d + k; j++)
-        if (ranges_overlap(f, fb, faces[j], fb)) return fail(ctx, LQCD_ERR_INVALID, "face buffers alias");
-      fv[4 * d + k] = f;
+    for (int k = 0; k < nf; k++) {
+      const int i = nf * d + k;
+      void *f = faces[i];
+      if (bad_face(f)) return fail(ctx, LQCD_ERR_INVALID, "faces: NULL or not 16-byte aligned");
+      for (int j = 0; j < i; j++)
+        if (ranges_overlap(f, fsize(i), faces[j], fsize(j)))
+          return fail(ctx, LQCD_ERR_INVALID, "face buffers alias");
+      fv[i] = f;
     }
   }
-  return dd_cg_solve(ctx, nd, first_domain, nt, antiperiodic_t ? 1 : 0, g, recon, views, recon_i, views_i, bf, xf,
-                     fv, fb, comm, kappa, mu, *params, stats);
+  return dd_cg_solve(ctx, nd, first_domain, nz, nt, antiperiodic_t ? 1 : 0, g, recon, views, recon_i, views_i, bf,
+                     xf, fv, comm, kappa, mu, *params, stats);
 }
 
 static int apply_impl(lqcd_ctx *ctx, const lqcd_gauge *U, lqcd_field in, lqcd_field out,

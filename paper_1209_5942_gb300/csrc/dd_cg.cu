@@ -1,8 +1,8 @@
 // dd_cg.cu -- the even-odd CG (CGLS on Mhat^+ Mhat, Sec. 2.1) on a lattice
-// split along t into domains (the paper's Sec. 6 outlook: the solver over
-// several GPUs).  Each half hop of the operator is the domain-decomposed hop
-// of dd.cu: pack the two faces of every held domain, move the faces, run the
-// domain hops with the operator's diagonal epilogue.  Every norm is a
+// split into a grid of domains along t and z (the paper's Sec. 6 outlook: the
+// solver over several GPUs).  Each half hop of the operator is the
+// domain-decomposed hop of dd.cu: pack the faces of every held domain, move
+// the faces, run the domain hops with the operator's diagonal epilogue.  Every norm is a
 // fixed-order sum on each domain, summed over the held domains in order on
 // the host, then over processes by the caller's allreduce hook.  The solver
 // arithmetic, the source preparation bhat_e = b_e + kappa H_eo A_o^-1 b_o, the
@@ -80,17 +80,32 @@ struct DVec {
 
 struct Dd {
   lqcd_ctx *ctx;
-  int nd, first, nt, antiper;
+  int nd, first, nz, nt, antiper;  // held domains first.. of the nz x nt grid (domain dz + nz dt)
   Geom g;  // local geometry; the global boundary sign travels in the faces
   int recon, recon_i;
   std::vector<GaugeView> U, Ui;  // FP64 links; links of the inner format
-  std::vector<void *> faces;     // [4 nd]: to_prev, to_next, from_next, from_prev
-  size_t fb;                     // bytes of an FP64 face (16-byte words)
+  // per held domain: to_prev, to_next, from_next, from_prev along t, then
+  // (nz > 1) along z
+  std::vector<void *> faces;
   const lqcd_dd_comm *comm;
   double kappa, mu;
   double *dsum;  // device [nd]
 
-  void *face(int d, int k) const { return faces[4 * d + k]; }
+  int nf() const { return nz > 1 ? 8 : 4; }
+  void *face(int d, int k) const { return faces[(size_t)nf() * d + k]; }
+  // neighbours of global domain gd along t (mu = 3) or z (mu = 2)
+  int next(int gd, int mu) const {
+    const int dz = gd % nz, dt = gd / nz;
+    return mu == 3 ? dz + nz * ((dt + 1) % nt) : (dz + 1) % nz + nz * dt;
+  }
+  int prev(int gd, int mu) const {
+    const int dz = gd % nz, dt = gd / nz;
+    return mu == 3 ? dz + nz * ((dt + nt - 1) % nt) : (dz + nz - 1) % nz + nz * dt;
+  }
+  // bytes of one face along mu in the format prec
+  size_t face_bytes(int mu, int prec) const {
+    return (size_t)dd_face_sites(g, mu) * 6 * dd_face_word_bytes(prec);
+  }
 
   // per-domain sums in dsum[0..nd) -> the total over all domains of all processes
   lqcd_status total(double *out) {
@@ -107,20 +122,25 @@ struct Dd {
     return LQCD_OK;
   }
 
-  // the faces written by the packs (in the format prec) reach their neighbours
+  // the faces written by the packs (in the format prec) reach their
+  // neighbours; without hooks every domain is held here (global = local index)
   lqcd_status exchange(int prec) {
-    const size_t nb = fb / 16 * dd_face_word_bytes(prec);
+    const size_t nb_t = face_bytes(3, prec), nb_z = nz > 1 ? face_bytes(2, prec) : 0;
     if (comm) {
       LQCD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-      if (comm->exchange(comm->user, nb) != 0)
+      if (comm->exchange(comm->user, nb_t, nb_z) != 0)
         return fail(ctx, LQCD_ERR_COMM, "domain-decomposed CG: the exchange hook failed");
       return LQCD_OK;
     }
-    for (int d = 0; d < nd; d++) {
-      const int nx = (d + 1) % nt, pv = (d + nt - 1) % nt;
-      LQCD_CUDA(ctx, cudaMemcpyAsync(face(d, 2), face(nx, 0), nb, cudaMemcpyDeviceToDevice, ctx->stream));
-      LQCD_CUDA(ctx, cudaMemcpyAsync(face(d, 3), face(pv, 1), nb, cudaMemcpyDeviceToDevice, ctx->stream));
-    }
+    for (int d = 0; d < nd; d++)
+      for (int mu = 3; mu >= (nz > 1 ? 2 : 3); mu--) {
+        const int o = mu == 3 ? 0 : 4;
+        const size_t nb = mu == 3 ? nb_t : nb_z;
+        LQCD_CUDA(ctx, cudaMemcpyAsync(face(d, o + 2), face(next(d, mu), o + 0), nb, cudaMemcpyDeviceToDevice,
+                                       ctx->stream));
+        LQCD_CUDA(ctx, cudaMemcpyAsync(face(d, o + 3), face(prev(d, mu), o + 1), nb, cudaMemcpyDeviceToDevice,
+                                       ctx->stream));
+      }
     return LQCD_OK;
   }
 
@@ -139,8 +159,9 @@ struct Dd {
       L.in = in.f[d];
       L.out_parity = p;
       L.dagger = dagger ? 1 : 0;
-      const int gd = first + d;
-      LQCD_TRY(dd_run(ctx, g, L, true, face(d, 0), face(d, 1), antiper && gd == 0, antiper && gd == nt - 1));
+      const int dt = (first + d) / nz;
+      LQCD_TRY(dd_pack(ctx, g, L, 3, face(d, 0), face(d, 1), antiper && dt == 0, antiper && dt == nt - 1));
+      if (nz > 1) LQCD_TRY(dd_pack(ctx, g, L, 2, face(d, 4), face(d, 5), 0, 0));
     }
     LQCD_TRY(exchange(prec));
     const int nw = (g.Vh + 31) / 32;
@@ -162,7 +183,8 @@ struct Dd {
         L.d_dn = d_dn;
       }
       L.partials = norm ? ctx->partials : nullptr;
-      LQCD_TRY(dd_run(ctx, g, L, false, face(d, 2), face(d, 3), 0, 0));
+      LQCD_TRY(dd_hop(ctx, g, L, face(d, 2), face(d, 3), nz > 1 ? face(d, 6) : nullptr,
+                      nz > 1 ? face(d, 7) : nullptr));
       if (norm) dd_sum_kernel<<<1, 256, 0, ctx->stream>>>(ctx->partials, nw, dsum + d);
     }
     LQCD_CUDA(ctx, cudaGetLastError());
@@ -203,12 +225,11 @@ struct Dd {
 
 }  // namespace
 
-lqcd_status dd_cg_solve(lqcd_ctx *ctx, int nd, int first, int nt, int antiper, const Geom &g, int recon,
+lqcd_status dd_cg_solve(lqcd_ctx *ctx, int nd, int first, int nz, int nt, int antiper, const Geom &g, int recon,
                         const std::vector<GaugeView> &U, int recon_i, const std::vector<GaugeView> &Ui,
-                        const std::vector<HalfField> &b_full,
-                        const std::vector<HalfField> &x_full, const std::vector<void *> &faces, size_t fb,
-                        const lqcd_dd_comm *comm, double kappa, double mu, const lqcd_cg_params &prm,
-                        lqcd_cg_stats *st) {
+                        const std::vector<HalfField> &b_full, const std::vector<HalfField> &x_full,
+                        const std::vector<void *> &faces, const lqcd_dd_comm *comm, double kappa, double mu,
+                        const lqcd_cg_params &prm, lqcd_cg_stats *st) {
   const auto t0 = std::chrono::steady_clock::now();
   std::memset(st, 0, sizeof(*st));
   const int Vh = g.Vh;
@@ -216,7 +237,7 @@ lqcd_status dd_cg_solve(lqcd_ctx *ctx, int nd, int first, int nt, int antiper, c
   LQCD_TRY(dsum.alloc(sizeof(double) * nd));
   const int nb = (Vh + 127) / 128 > (Vh + 31) / 32 ? (Vh + 127) / 128 : (Vh + 31) / 32;
   LQCD_TRY(ensure_partials(ctx, (size_t)nb));
-  Dd S{ctx, nd, first, nt, antiper, g, recon, recon_i, U, Ui, faces, fb, comm, kappa, mu, (double *)dsum.p};
+  Dd S{ctx, nd, first, nz, nt, antiper, g, recon, recon_i, U, Ui, faces, comm, kappa, mu, (double *)dsum.p};
   const int inner = prm.inner_prec;
   const bool mixed = inner != LQCD_F64;
   // a mixed cycle stops once its residual has dropped by itol (F32; a

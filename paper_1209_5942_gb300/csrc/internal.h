@@ -274,22 +274,26 @@ struct HopLaunch {
 };
 lqcd_status launch_hop(lqcd_ctx *ctx, const Geom &g, const HopLaunch &L, int *nblocks_out);
 int hop_blocks(const Geom &g, int nrhs);
-// domain decomposition along t (dd.cu): pack = true writes the two faces
-// (f0 = for the previous domain, f1 = for the next; n0/n1: negate them),
-// pack = false runs the domain's half hop (f0 = face from the next domain,
-// f1 = face from the previous one)
-lqcd_status dd_run(lqcd_ctx *ctx, const Geom &g, const HopLaunch &L, bool pack, void *f0, void *f1, int n0, int n1);
+// domain decomposition along t and z (dd.cu): dd_pack writes the two faces
+// along mu = 2 (z) or 3 (t) (f0 = for the previous domain, f1 = for the next;
+// n0/n1: negate them); dd_hop runs the domain's half hop with the faces
+// received from the next and previous domains along t and, if z_next is not
+// null, along z
+lqcd_status dd_pack(lqcd_ctx *ctx, const Geom &g, const HopLaunch &L, int mu, void *f0, void *f1, int n0, int n1);
+lqcd_status dd_hop(lqcd_ctx *ctx, const Geom &g, const HopLaunch &L, const void *t_next, const void *t_prev,
+                   const void *z_next, const void *z_prev);
 size_t dd_face_word_bytes(int prec);
-// domain-decomposed CG (dd_cg.cu): nd held domains, the first of global
-// index `first` of nt; U: FP64 links, Ui: links of the inner format
-// (prm.inner_prec F64: unused); b_full / x_full: EO full fields of each held
-// domain; faces: 4 per held domain (to_prev, to_next, from_next, from_prev)
-lqcd_status dd_cg_solve(lqcd_ctx *ctx, int nd, int first, int nt, int antiper, const Geom &g, int recon,
+int dd_face_sites(const Geom &g, int mu);  // sites of one parity in a boundary slice along mu
+// domain-decomposed CG (dd_cg.cu): nd held domains of an nz x nt grid
+// (domain dz + nz dt), the first of global index `first`; U: FP64 links, Ui:
+// links of the inner format (prm.inner_prec F64: unused); b_full / x_full: EO
+// full fields of each held domain; faces: per held domain to_prev, to_next,
+// from_next, from_prev along t, then (nz > 1) the same four along z
+lqcd_status dd_cg_solve(lqcd_ctx *ctx, int nd, int first, int nz, int nt, int antiper, const Geom &g, int recon,
                         const std::vector<GaugeView> &U, int recon_i, const std::vector<GaugeView> &Ui,
-                        const std::vector<HalfField> &b_full,
-                        const std::vector<HalfField> &x_full, const std::vector<void *> &faces, size_t fb,
-                        const lqcd_dd_comm *comm, double kappa, double mu, const lqcd_cg_params &prm,
-                        lqcd_cg_stats *st);
+                        const std::vector<HalfField> &b_full, const std::vector<HalfField> &x_full,
+                        const std::vector<void *> &faces, const lqcd_dd_comm *comm, double kappa, double mu,
+                        const lqcd_cg_params &prm, lqcd_cg_stats *st);
 
 // Operators assembled from hop launches (cg.cu)
 struct Op {

@@ -99,7 +99,7 @@ _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 _FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 
 # communication hooks of the domain-decomposed solve (lqcd_dd_comm)
-_EXCHANGE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t)
+_EXCHANGE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_size_t)
 _ALLREDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int)
 
 
@@ -140,6 +140,10 @@ SIGNATURES = [
     ("lqcd_dd_face_bytes", ctypes.c_size_t, [ctypes.POINTER(lqcd_geom), _i]),
     ("lqcd_dd_pack", _i, [_vp, _vp, lqcd_field, _vp, _vp, ctypes.POINTER(lqcd_geom), _i, _i, _i, _i]),
     ("lqcd_dd_dslash", _i, [_vp, _vp, lqcd_field, lqcd_field, _vp, _vp, ctypes.POINTER(lqcd_geom), _i, _i]),
+    ("lqcd_dd_face_bytes_dir", ctypes.c_size_t, [ctypes.POINTER(lqcd_geom), _i, _i]),
+    ("lqcd_dd_pack_dir", _i, [_vp, _vp, lqcd_field, _i, _vp, _vp, ctypes.POINTER(lqcd_geom), _i, _i, _i, _i]),
+    ("lqcd_dd_dslash_zt", _i, [_vp, _vp, lqcd_field, lqcd_field, _vp, _vp, _vp, _vp, ctypes.POINTER(lqcd_geom),
+                               _i, _i]),
     ("lqcd_apply_M", _i, [_vp, _vp, lqcd_field, lqcd_field, ctypes.POINTER(lqcd_geom), _d, _d, _i]),
     ("lqcd_apply_Mdag", _i, [_vp, _vp, lqcd_field, lqcd_field, ctypes.POINTER(lqcd_geom), _d, _d,
                              _i]),
@@ -147,7 +151,7 @@ SIGNATURES = [
                            ctypes.POINTER(lqcd_cg_params), ctypes.POINTER(lqcd_cg_stats)]),
     ("lqcd_dd_cg_solve", _i, [_vp, _i, ctypes.POINTER(_vp), ctypes.POINTER(lqcd_field),
                               ctypes.POINTER(lqcd_field), ctypes.POINTER(_vp), ctypes.POINTER(lqcd_geom), _i, _i,
-                              _i, _d, _d, ctypes.POINTER(lqcd_cg_params), ctypes.POINTER(lqcd_dd_comm),
+                              _i, _i, _d, _d, ctypes.POINTER(lqcd_cg_params), ctypes.POINTER(lqcd_dd_comm),
                               ctypes.POINTER(lqcd_cg_stats)]),
     ("lqcd_cg_solve_batch", _i, [_vp, _i, ctypes.POINTER(_vp), ctypes.POINTER(lqcd_field),
                                  ctypes.POINTER(lqcd_field), ctypes.POINTER(_d), ctypes.POINTER(_d),
@@ -426,6 +430,10 @@ def lqcd_dd_face_bytes(L_local, prec) -> int:
     return int(lib().lqcd_dd_face_bytes(ctypes.byref(geom(L_local, False)), prec))
 
 
+def lqcd_dd_face_bytes_dir(L_local, mu, prec) -> int:
+    return int(lib().lqcd_dd_face_bytes_dir(ctypes.byref(geom(L_local, False)), int(mu), prec))
+
+
 def lqcd_dd_pack(ctx: Context, U: Gauge, inp: lqcd_field, face_to_prev: torch.Tensor, face_to_next: torch.Tensor,
                  out_parity, dagger=0, negate_to_prev=False, negate_to_next=False):
     g = U.geom
@@ -434,11 +442,30 @@ def lqcd_dd_pack(ctx: Context, U: Gauge, inp: lqcd_field, face_to_prev: torch.Te
                                  int(bool(negate_to_prev)), int(bool(negate_to_next))))
 
 
+def lqcd_dd_pack_dir(ctx: Context, U: Gauge, inp: lqcd_field, mu, face_to_prev: torch.Tensor,
+                     face_to_next: torch.Tensor, out_parity, dagger=0, negate_to_prev=False, negate_to_next=False):
+    g = U.geom
+    ctx.check(lib().lqcd_dd_pack_dir(ctx.handle, U.handle, inp, int(mu), _vp(face_to_prev.data_ptr()),
+                                     _vp(face_to_next.data_ptr()), ctypes.byref(g), out_parity, int(dagger),
+                                     int(bool(negate_to_prev)), int(bool(negate_to_next))))
+
+
 def lqcd_dd_dslash(ctx: Context, U: Gauge, inp: lqcd_field, out: lqcd_field, face_from_next: torch.Tensor,
                    face_from_prev: torch.Tensor, out_parity, dagger=0):
     g = U.geom
     ctx.check(lib().lqcd_dd_dslash(ctx.handle, U.handle, inp, out, _vp(face_from_next.data_ptr()),
                                    _vp(face_from_prev.data_ptr()), ctypes.byref(g), out_parity, int(dagger)))
+
+
+def lqcd_dd_dslash_zt(ctx: Context, U: Gauge, inp: lqcd_field, out: lqcd_field, t_from_next: torch.Tensor,
+                      t_from_prev: torch.Tensor, z_from_next, z_from_prev, out_parity, dagger=0):
+    """z_from_next / z_from_prev: tensors, or None for a lattice not split along z."""
+    g = U.geom
+    zn = None if z_from_next is None else _vp(z_from_next.data_ptr())
+    zp = None if z_from_prev is None else _vp(z_from_prev.data_ptr())
+    ctx.check(lib().lqcd_dd_dslash_zt(ctx.handle, U.handle, inp, out, _vp(t_from_next.data_ptr()),
+                                      _vp(t_from_prev.data_ptr()), zn, zp, ctypes.byref(g), out_parity,
+                                      int(dagger)))
 
 
 def lqcd_apply_M(ctx: Context, U: Gauge, inp: lqcd_field, out: lqcd_field, kappa, mu,
@@ -486,25 +513,29 @@ def lqcd_cg_solve(ctx: Context, U: Gauge, b: lqcd_field, x: lqcd_field, kappa, m
 
 def lqcd_dd_cg_solve(ctx: Context, Us, bs, xs, faces, first_domain, nt, kappa, mu,
                      params: lqcd_cg_params, antiperiodic_t=True, exchange=None, allreduce=None,
-                     allow_noconv=False):
-    """Domain-decomposed CG (include/lqcd.h): Us, bs, xs, faces for the held
-    domains (faces: 4 device tensors per domain); exchange(nbytes) (move the
-    leading nbytes of each face) / allreduce(list of floats) -> list: the
-    communication hooks (None for all domains in this call).  The hooks are
-    called from inside the library call."""
+                     allow_noconv=False, nz=1):
+    """Domain-decomposed CG (include/lqcd.h) on an nz x nt grid of domains:
+    Us, bs, xs, faces for the held domains (faces: 4 device tensors per
+    domain along t, then 4 along z when nz > 1); exchange(t_bytes, z_bytes)
+    (move the leading bytes of each t and z face) / allreduce(list of floats)
+    -> list: the communication hooks (None for all domains in this call).
+    The hooks are called from inside the library call."""
     nd = len(Us)
     g = Us[0].geom
     U_arr = (_vp * nd)(*[u.handle for u in Us])
     b_arr = (lqcd_field * nd)(*bs)
     x_arr = (lqcd_field * nd)(*xs)
-    f_arr = (_vp * (4 * nd))(*[t.data_ptr() for fs in faces for t in fs])
+    ptrs = [t.data_ptr() for fs in faces for t in fs]
+    if len(ptrs) != (8 if nz > 1 else 4) * nd:
+        raise ValueError("faces: 4 tensors per domain (8 when nz > 1)")
+    f_arr = (_vp * len(ptrs))(*ptrs)
     stats = lqcd_cg_stats()
     comm_p = None
     errors = []
     if exchange is not None:
-        def _ex(_user, nbytes):
+        def _ex(_user, t_bytes, z_bytes):
             try:
-                exchange(int(nbytes))
+                exchange(int(t_bytes), int(z_bytes))
                 return 0
             except Exception as e:  # reported as LQCD_ERR_COMM; re-raised below
                 errors.append(e)
@@ -524,8 +555,8 @@ def lqcd_dd_cg_solve(ctx: Context, Us, bs, xs, faces, first_domain, nt, kappa, m
         comm = lqcd_dd_comm(None, ex_cb, ar_cb)
         comm_p = ctypes.byref(comm)
     rc = lib().lqcd_dd_cg_solve(ctx.handle, nd, U_arr, b_arr, x_arr, f_arr, ctypes.byref(g), int(first_domain),
-                                int(nt), int(bool(antiperiodic_t)), kappa, mu, ctypes.byref(params), comm_p,
-                                ctypes.byref(stats))
+                                int(nz), int(nt), int(bool(antiperiodic_t)), kappa, mu, ctypes.byref(params),
+                                comm_p, ctypes.byref(stats))
     if errors:
         raise errors[0]
     ctx.check(rc, allow=(LQCD_ERR_NOCONV,) if allow_noconv else ())

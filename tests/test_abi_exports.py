@@ -23,7 +23,7 @@ def test_library_exports_every_declared_symbol():
 def test_abi_version_and_host_side_calls():
     build.build()
     lib = lqcd.lib()
-    assert lib.lqcd_abi_version() == 1
+    assert lib.lqcd_abi_version() == 2
     # pure host-side helpers work without a GPU
     n, sb = lqcd.field_bytes((4, 4, 4, 8), lqcd.LQCD_FULL, lqcd.LQCD_F64)
     assert n == 4 * 4 * 4 * 8 * 192 and sb == 0
