@@ -1003,6 +1003,8 @@ def run_config(args):
         tm, stm = _timed(torch, lambda: lqcd.lqcd_cg_solve(ctx, G, fb, fx, KAPPA, MU, prm_m))
         res["single_domain_f64/f32"] = {"solve_s": tm, "iters": stm[0]["iters"],
                                         "true_resid": stm[0]["true_resid"]}
+        hop_single = {pn: time_hop_multi(ctx, G, lqcd, torch, L, 1, PREC_NAMES[pn], reps=20)
+                      for pn in ("f64", "df64", "f32")}
         G.free()
         dd_prms = {"f64": prm,
                    "f64/f32": lqcd.cg_params(tol=TOL, outer_prec=lqcd.LQCD_F64, inner_prec=lqcd.LQCD_F32,
@@ -1032,6 +1034,12 @@ def run_config(args):
                 key = grid if name == "f64" else f"{grid}_{name}"
                 res[key] = {"solve_s": t, "iters": st["iters"], "restarts": st["restarts"],
                             "true_resid": st["true_resid"], "vs_single_domain": t / t1}
+            if nt > 1:  # the domain kernels alone, against the undivided lattice's hop
+                for pn in ("f64", "df64", "f32"):
+                    k = time_dd_kernels(ctx, dd, slabs, gs, lqcd, torch, PREC_NAMES[pn], label=f"dd_hops_{grid}_{pn}")
+                    k["hop_pct_hbm"] = 100 * k["hop_GBs"] / peaks["hbm_gbs"]
+                    k["single_domain_hop_ms"] = hop_single[pn]["ms"]
+                    res[f"{grid}_kernels_{pn}"] = k
             for G_ in gs:
                 G_.free()
         config_line("domain-decomposed CG", None, {"dd": res},
@@ -1075,6 +1083,54 @@ def time_half_hop_L(ctx, G, lqcd, torch, Lc, prec, reps=20):
     cnt = lqcd.lqcd_counters()
     lqcd.lib().lqcd_get_counters(ctx.handle, ctypes_byref(cnt))
     return {"ms": 1e3 * t, "gbs": cnt.hop_bytes / reps / t / 1e9, "tflops": cnt.hop_flops / reps / t / 1e12}
+
+
+def time_dd_kernels(ctx, dd, slabs, gauges, lqcd, torch, prec, reps=20, label=None):
+    """The domain-decomposed half hop's kernels on every domain of `slabs`
+    (one device): the domain hops alone (the faces already in place) and the
+    face packs alone, each timed with CUDA events over `reps` half hops;
+    GB/s from the library's counted algorithmic bytes.  label: the timed hops
+    run inside the NVTX range "<label>" (for an ncu capture of that launch)."""
+    Ll = slabs.local_L
+    n_half, _ = lqcd.field_bytes(Ll, lqcd.LQCD_EVEN, prec, 1)
+    gen = torch.Generator(device="cuda").manual_seed(13)
+    keep, ins, outs = [], [], []
+    for _ in range(slabs.ndomains):
+        din = torch.randn(n_half // 4, dtype=torch.float32, device="cuda", generator=gen).view(torch.float64)
+        dout = torch.zeros_like(din)
+        keep.append((din, dout))
+        ins.append(lqcd.field(din, lqcd.LQCD_LAYOUT_EO, prec))
+        outs.append(lqcd.field(dout, lqcd.LQCD_LAYOUT_EO, prec))
+    faces = [dd.domain_faces(slabs, prec) for _ in range(slabs.ndomains)]
+    dd.dslash_local_domains(ctx, slabs, gauges, ins, outs, lqcd.LQCD_EVEN, 0, bufs=faces)
+
+    def hops():
+        for d in range(slabs.ndomains):
+            z = faces[d][6:8] if slabs.nz > 1 else (None, None)
+            lqcd.lqcd_dd_dslash_zt(ctx, gauges[d], ins[d], outs[d], faces[d][2], faces[d][3], z[0], z[1],
+                                   lqcd.LQCD_EVEN, 0)
+
+    def packs():
+        for d in range(slabs.ndomains):
+            for k, mu in enumerate(slabs.dirs):
+                lqcd.lqcd_dd_pack_dir(ctx, gauges[d], ins[d], mu, faces[d][4 * k], faces[d][4 * k + 1],
+                                      lqcd.LQCD_EVEN, 0, slabs.negate_to_prev(d, mu), slabs.negate_to_next(d, mu))
+
+    out = {}
+    for name, fn in (("hop", hops), ("pack", packs)):
+        fn()
+        torch.cuda.synchronize()
+        c0, c1 = lqcd.lqcd_counters(), lqcd.lqcd_counters()
+        lqcd.lib().lqcd_get_counters(ctx.handle, ctypes_byref(c0))
+        if label and name == "hop":
+            nvtx_push(label)
+        t, _ = _timed(torch, fn, reps)
+        if label and name == "hop":
+            nvtx_pop()
+        lqcd.lib().lqcd_get_counters(ctx.handle, ctypes_byref(c1))
+        out[f"{name}_ms"] = 1e3 * t
+        out[f"{name}_GBs"] = (c1.bytes - c0.bytes) / reps / t / 1e9
+    return out
 
 
 def time_hop_multi(ctx, G, lqcd, torch, Lc, nrhs, prec=2, reps=10, nvtx=False):
