@@ -68,6 +68,7 @@ lqcd_status launch_hop(lqcd_ctx *ctx, const Geom &g, const HopLaunch &L, int *nb
     char mr;       // links staged in shared memory for a group of RHS: 0 no, else the
                    // reals kept per link (18, or 12 with the third row rebuilt per RHS)
     short rg;      // with mr: right-hand sides per block
+    bool ri;       // F32, several RHS: RHS interleaved with the site blocks (hop_ri_kernel)
   };
   Cand cands[96];
   int ncand = 0, fallback = 0;
@@ -112,6 +113,10 @@ lqcd_status launch_hop(lqcd_ctx *ctx, const Geom &g, const HopLaunch &L, int *nb
           cands[ncand++] = {bx, 1, 0, 1, false, false, 0, mr, rg};
         }
       }
+  // F32: the RHS interleaved with the site blocks, blocks of 32 or 64 sites
+  if (L.prec == LQCD_F32 && nrhs > 1)
+    for (int gi = 0; gi < 3; gi++)
+      for (short bx : {32, 64}) cands[ncand++] = {bx, 1, GM[gi], 1, true, false, 0, 0, 0, true};
   // packed two-site kernel: blocks of 64 threads = 128 sites, one RHS per block row
   if (low)
     for (int gi = 0; gi < 3; gi++) cands[ncand++] = {64, 1, GM[gi], 1, false, true};
@@ -133,6 +138,17 @@ lqcd_status launch_hop(lqcd_ctx *ctx, const Geom &g, const HopLaunch &L, int *nb
       else hop_launch_mrhs_h16(args, L.prec, k.mr, k.rg, grid, block, dag, red, ctx->stream);
       return;
     }
+    if (k.ri) {
+      // one block per (site block, RHS), RHS fastest; a persistent grid keeps
+      // whole groups of nrhs blocks
+      unsigned gx = (unsigned)((g.Vh + k.bx - 1) / k.bx) * (unsigned)nrhs;
+      if (k.gm > 0) {
+        const unsigned cap = (unsigned)(ctx->num_sms * k.gm) / nrhs * nrhs;
+        if (cap >= (unsigned)nrhs && gx > cap) gx = cap;
+      }
+      hop_launch_f32_ri(args, L.recon, dim3(gx, 1, 1), dim3(k.bx, 1, 1), dag, red, ctx->stream);
+      return;
+    }
     const int rt = k.rt;
     dim3 block(k.bx, k.by, 1), grid;
     const int per_block = pair ? k.bx / 2 : (k.two ? 2 * k.bx : k.bx);  // sites per block row
@@ -151,7 +167,7 @@ lqcd_status launch_hop(lqcd_ctx *ctx, const Geom &g, const HopLaunch &L, int *nb
     }
   };
   char key[160];
-  snprintf(key, sizeof(key), "hop6|p%d|r%d|d%d|red%d|aux%d|%dx%dx%dx%d|n%d", L.prec, L.recon, (int)dag, (int)red,
+  snprintf(key, sizeof(key), "hop7|p%d|r%d|d%d|red%d|aux%d|%dx%dx%dx%d|n%d", L.prec, L.recon, (int)dag, (int)red,
            A.has_aux, g.L[0], g.L[1], g.L[2], g.L[3], nrhs);
   HopArgs At = A;
   At.halt = nullptr;  // timing launches run whatever the solver state

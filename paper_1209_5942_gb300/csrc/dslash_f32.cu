@@ -1,6 +1,7 @@
 // dslash_f32.cu -- FP32 instantiations of the hop kernels (both load orders,
-// the register-blocked multi-RHS kernel and the multi-RHS kernel with links
-// staged in shared memory).
+// the register-blocked multi-RHS kernel, the multi-RHS kernel with links
+// staged in shared memory and the one with RHS interleaved with the site
+// blocks).
 #include "hop_kernels.cuh"
 
 namespace lqcd {
@@ -19,6 +20,11 @@ void hop_launch_f32(const HopArgs &A, int recon, dim3 grid, dim3 block, bool dag
   }
   if (recon == 12) launch_t<LQCD_F32, 12>(A, grid, block, dag, red, st, lf);
   else launch_t<LQCD_F32, 18>(A, grid, block, dag, red, st, lf);
+}
+
+void hop_launch_f32_ri(const HopArgs &A, int recon, dim3 grid, dim3 block, bool dag, bool red, cudaStream_t st) {
+  if (recon == 12) launch_ri<LQCD_F32, 12>(A, grid, block, dag, red, st);
+  else launch_ri<LQCD_F32, 18>(A, grid, block, dag, red, st);
 }
 
 void hop_launch_mrhs_f32(const HopArgs &A, int recon, int srec, int rg, dim3 grid, dim3 block, bool dag, bool red,

@@ -623,6 +623,22 @@ __global__ void __launch_bounds__(256, (PREC == LQCD_BF16S || PREC == LQCD_F16S)
     hop_site<PREC, RECON, DAG, REDUCE, LF>(A, base + threadIdx.x, rhs);
 }
 
+// Several right-hand sides with the RHS interleaved with the site blocks:
+// block b runs RHS b % nrhs of site block b / nrhs (grid-stride over the site
+// blocks; gridDim.x a multiple of nrhs), so the blocks resident at one time
+// cover a few site blocks for every RHS, and the links one RHS reads from HBM
+// are still in L2 when the others read them.  The same hop_site per (site,
+// RHS), so the results are bitwise those of hop_kernel.
+template <int PREC, int RECON, bool DAG, bool REDUCE>
+__global__ void __launch_bounds__(256, 2) hop_ri_kernel(HopArgs A) {
+  pdl_wait();
+  if (A.halt && *(volatile int *)A.halt) return;
+  const int rhs = blockIdx.x % A.nrhs;
+  const int stride = (gridDim.x / A.nrhs) * blockDim.x;
+  for (int base = (blockIdx.x / A.nrhs) * blockDim.x; base < A.g.Vh; base += stride)
+    hop_site<PREC, RECON, DAG, REDUCE, true>(A, base + threadIdx.x, rhs);
+}
+
 // ---------------------------------------------------------------------------
 // Two output sites per thread in packed FP32x2 arithmetic (F32 and 16-bit
 // formats): lane x of every float2 belongs to site cb, lane y to site cb + 32,
@@ -1371,6 +1387,16 @@ inline void launch_t2(const HopArgs &A, dim3 grid, dim3 block, bool dag, bool re
     else launch_pdl(hop_kernel<PREC, RECON, false, false, LF>, grid, block, 0, st, A);
   }
 }
+template <int PREC, int RECON>
+inline void launch_ri(const HopArgs &A, dim3 grid, dim3 block, bool dag, bool red, cudaStream_t st) {
+  if (dag) {
+    if (red) launch_pdl(hop_ri_kernel<PREC, RECON, true, true>, grid, block, 0, st, A);
+    else launch_pdl(hop_ri_kernel<PREC, RECON, true, false>, grid, block, 0, st, A);
+  } else {
+    if (red) launch_pdl(hop_ri_kernel<PREC, RECON, false, true>, grid, block, 0, st, A);
+    else launch_pdl(hop_ri_kernel<PREC, RECON, false, false>, grid, block, 0, st, A);
+  }
+}
 template <int PREC, int RECON, int RT>
 inline void launch_rt2(const HopArgs &A, dim3 grid, dim3 block, bool dag, bool red, cudaStream_t st) {
   if (dag) {
@@ -1425,6 +1451,9 @@ void hop_launch_df64(const HopArgs &A, int recon, bool pair, int mode, dim3 grid
 // rt: right-hand sides per thread (1, 2, 4); two: two sites per thread (packed FP32x2)
 void hop_launch_f32(const HopArgs &A, int recon, dim3 grid, dim3 block, bool dag, bool red, bool lf, int rt,
                     bool two, cudaStream_t st);
+// several RHS interleaved with the site blocks (hop_ri_kernel; grid.x a
+// multiple of A.nrhs)
+void hop_launch_f32_ri(const HopArgs &A, int recon, dim3 grid, dim3 block, bool dag, bool red, cudaStream_t st);
 // multi-RHS kernel with the links staged in shared memory: srec reals kept per
 // link (18, or 12 for 12-real fields), rg right-hand sides per block, block.x
 // sites per block (at most 48 KB of shared memory)
