@@ -8,13 +8,13 @@ namespace lqcd {
 template <int PREC, int RECON>
 static void dd_pack_launch(int mu, bool dag, const HopArgs &A, int n, void *f0, void *f1, int n0, int n1,
                            cudaStream_t st) {
-  const dim3 grid((unsigned)((n + 127) / 128), 2);
+  const dim3 grid((unsigned)((n + 127) / 128), 2), block(128);
   if (mu == 3) {
-    if (dag) dd_pack_kernel<PREC, RECON, 3, -1><<<grid, 128, 0, st>>>(A, n, f0, f1, n0, n1);
-    else dd_pack_kernel<PREC, RECON, 3, 1><<<grid, 128, 0, st>>>(A, n, f0, f1, n0, n1);
+    if (dag) launch_pdl(dd_pack_kernel<PREC, RECON, 3, -1>, grid, block, 0, st, A, n, f0, f1, n0, n1);
+    else launch_pdl(dd_pack_kernel<PREC, RECON, 3, 1>, grid, block, 0, st, A, n, f0, f1, n0, n1);
   } else {
-    if (dag) dd_pack_kernel<PREC, RECON, 2, -1><<<grid, 128, 0, st>>>(A, n, f0, f1, n0, n1);
-    else dd_pack_kernel<PREC, RECON, 2, 1><<<grid, 128, 0, st>>>(A, n, f0, f1, n0, n1);
+    if (dag) launch_pdl(dd_pack_kernel<PREC, RECON, 2, -1>, grid, block, 0, st, A, n, f0, f1, n0, n1);
+    else launch_pdl(dd_pack_kernel<PREC, RECON, 2, 1>, grid, block, 0, st, A, n, f0, f1, n0, n1);
   }
 }
 

@@ -84,6 +84,7 @@ template <int MU> LQCD_DEV int face_site(const Geom &g, int j, int c) {
 template <int PREC, int RECON, int MU, int S>
 __global__ void __launch_bounds__(128) dd_pack_kernel(HopArgs A, int n, void *to_prev, void *to_next,
                                                       int neg_prev, int neg_next) {
+  pdl_wait();
   using R = typename SpinorIO<PREC>::R;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
@@ -154,6 +155,7 @@ LQCD_DEV void dd_dir(const HopArgs &A, const Site &s, int p, int cb, const Spino
 // return early).
 template <int PREC, int RECON, bool DAG, bool REDUCE, bool SZ>
 __global__ void __launch_bounds__(128) dd_hop_kernel(HopArgs A, DdFaces F) {
+  pdl_wait();
   using R = typename SpinorIO<PREC>::R;
   const int cb = blockIdx.x * blockDim.x + threadIdx.x;
   double nrm = 0.0;
@@ -178,12 +180,14 @@ __global__ void __launch_bounds__(128) dd_hop_kernel(HopArgs A, DdFaces F) {
 template <int PREC, int RECON, bool SZ>
 void dd_hop_launch(bool dag, const HopArgs &A, const DdFaces &F, cudaStream_t st) {
   const unsigned grid = (unsigned)((A.g.Vh + 127) / 128);
+  // programmatic dependent launches (the kernels wait for their predecessor
+  // in pdl_wait), so a launch overlaps the tail of the kernel before it
   if (A.partials) {  // the reducing form (norms of the domain-decomposed CG)
-    if (dag) dd_hop_kernel<PREC, RECON, true, true, SZ><<<grid, 128, 0, st>>>(A, F);
-    else dd_hop_kernel<PREC, RECON, false, true, SZ><<<grid, 128, 0, st>>>(A, F);
+    if (dag) launch_pdl(dd_hop_kernel<PREC, RECON, true, true, SZ>, dim3(grid), dim3(128), 0, st, A, F);
+    else launch_pdl(dd_hop_kernel<PREC, RECON, false, true, SZ>, dim3(grid), dim3(128), 0, st, A, F);
   } else {
-    if (dag) dd_hop_kernel<PREC, RECON, true, false, SZ><<<grid, 128, 0, st>>>(A, F);
-    else dd_hop_kernel<PREC, RECON, false, false, SZ><<<grid, 128, 0, st>>>(A, F);
+    if (dag) launch_pdl(dd_hop_kernel<PREC, RECON, true, false, SZ>, dim3(grid), dim3(128), 0, st, A, F);
+    else launch_pdl(dd_hop_kernel<PREC, RECON, false, false, SZ>, dim3(grid), dim3(128), 0, st, A, F);
   }
 }
 
